@@ -1,0 +1,184 @@
+/*
+ * gf.h -- C ABI of the GB300 library for quasi-periodic Green's functions by
+ * the FFT-based method of B. Zhang & R. Zhang (arXiv:1801.05977).
+ *
+ * The problem (Sec. 1): for a wave number k > 0 and quasi-periodicity alpha,
+ *   2D  G(x)    = (i/4 pi)   sum_n   beta_n^{-1}  exp(i alpha_n x1 + i beta_n |x2|)          Eq. (ei)
+ *   3D  G_d(x)  = (i/8 pi^2) sum_n1,n2 beta_n^{-1} exp(i alpha_n . x' + i beta_n |x3|)      Eq. (he)
+ *   Maxwell     GG(x) = G_d(x) I + k^{-2} grad grad (G_d(x) I)                             Eq. (me)
+ * with alpha_n = alpha + n, beta_n = sqrt(k^2 - |alpha_n|^2) (Im beta >= 0),
+ * period 2 pi in x1 (and x2), and no Wood anomaly (beta_n != 0).
+ *
+ * The method (Algorithms 1, 2, 3): split G into a closed-form singular part
+ * near the lattice point and a smooth periodic remainder L; generate L's
+ * Fourier coefficients (Eqs. (fck-coef), (fcl-coef)-(fcf2-coef) in 2D,
+ * (kdj1) and (fj) in 3D, -c^p c^q multipliers for Maxwell, Sec. 4), synthesise
+ * L on a uniform grid by inverse FFT, and at each target reduce to the unit
+ * cell, interpolate L by tensor cubics, add the singular part back and apply
+ * the quasi-periodic phase; targets with |x_last| > c use the eigen-series.
+ *
+ * Conventions shared by every entry point:
+ *   - All device pointers are plain CUDA device addresses (for example from
+ *     torch tensors); host pointers are ordinary host memory (pinned memory
+ *     makes the host variants faster).  No entry point takes ownership of a
+ *     caller buffer.
+ *   - `cuda_stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued on it and the call returns without
+ *     synchronising, except where a function says otherwise.
+ *   - Every function returns a gf_status; nothing throws across the ABI.  On
+ *     failure gf_last_error() returns a thread-local description.
+ *   - Complex outputs are interleaved (re, im): complex128 for GF_FP64 plans,
+ *     complex64 for GF_FP32_SPLIT plans.
+ */
+#ifndef GF_H_
+#define GF_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gf_plan_s *gf_plan_t;
+
+typedef enum {
+    GF_OK = 0,
+    GF_ERR_ARG = 1,          /* invalid argument (size, pointer, parameter range) */
+    GF_ERR_WOOD = 2,         /* some beta_n vanishes (Sec. 1: "away from Wood anomalies") */
+    GF_ERR_RESONANCE = 3,    /* beta = +-j_last pi / c~ for some j, policy GF_FAIL (Sec. 2.1, 3.1) */
+    GF_ERR_NOMEM = 4,        /* device allocation failed */
+    GF_ERR_CUDA = 5,         /* a CUDA runtime call failed */
+    GF_ERR_TIMEOUT = 6,      /* a bounded device wait ran out */
+    GF_ERR_UNSUPPORTED = 7   /* valid request this build does not implement */
+} gf_status;
+
+enum { GF_FP64 = 0, GF_FP32_SPLIT = 1 };          /* gf_trunc_t.precision */
+enum { GF_HELMHOLTZ = 0, GF_MAXWELL = 1 };        /* gf_trunc_t.kind */
+enum { GF_PERTURB_CTILDE = 0, GF_FAIL = 1 };      /* gf_trunc_t.resonance_policy */
+enum {                                            /* gf_eval_points `which` */
+    GF_OUT_G = 0,         /* 2D plans: G, 1 entry */
+    GF_OUT_GD = 1,        /* 3D plans: G_d, 1 entry */
+    GF_OUT_MAXWELL6 = 2,  /* Maxwell plans: GG_xx, GG_yy, GG_zz, GG_xy, GG_xz, GG_yz */
+    GF_OUT_MAXWELL7 = 3   /* Maxwell plans: the six entries above, then G_d */
+};
+
+/* Method parameters.  Defaults (gf_trunc_default): c = 0.6, c~ = 1 (Sec. 5),
+ * eps = 0.45, series_tol = 0 (automatic), quad_nodes = 64, GF_FP64,
+ * GF_HELMHOLTZ, GF_PERTURB_CTILDE.
+ *   c          |x_last| <= c: grid + interpolation; > c: eigen-series (Alg. 1-3, step 2b)
+ *   c_tilde    half period of the artificial periodisation in x_last (c < c~); the cutoff
+ *              X(t) falls from 1 at t = c to 0 at t = (c + c~)/2 (Sec. 2.1)
+ *   eps        singular cutoff Y_eps: 1 on [0, eps], 0 beyond 2 eps (Sec. 2.2, 3.2);
+ *              requires 2 eps < min(c~, pi)
+ *   series_tol far-series truncation: terms with |alpha_n|^2 <= k^2 + (T/|x_last|)^2,
+ *              T = ln(1/series_tol) + 3, are summed; <= 0 selects 1e-16 for GF_FP64
+ *              and 1e-8 for GF_FP32_SPLIT
+ *   quad_nodes Gauss-Legendre nodes for the 1D integrals in the coefficients
+ *   precision  GF_FP64: everything in double.  GF_FP32_SPLIT: grid synthesis,
+ *              interpolation and series in float; coefficients, singular part,
+ *              reduction and phase in double.
+ *   kind       GF_MAXWELL (3D only) stores seven fields per node: the six combined
+ *              fields (delta_pq - c^p c^q / k^2) L_d (Sec. 4; one interpolation per
+ *              tensor entry) and L_d itself (for G_d)
+ */
+typedef struct {
+    double c, c_tilde, eps;
+    double series_tol;
+    int quad_nodes;
+    int precision;
+    int kind;
+    int resonance_policy;
+} gf_trunc_t;
+
+/* Fill *t with the defaults listed above.  Returns GF_ERR_ARG if t is NULL. */
+gf_status gf_trunc_default(gf_trunc_t *t);
+
+/* Build a plan (Algorithms 1-3, step 1 "Preparation"): check the parameters,
+ * generate the remainder's Fourier coefficients on S_N in double precision and
+ * synthesise the grid by inverse FFT on the device.
+ *   dim        2 (G, Sec. 2) or 3 (G_d / GG, Secs. 3-4)
+ *   k          wave number, > 0
+ *   alpha      dim-1 doubles (host memory)
+ *   M          dim ints (host memory): grid points per axis (x1, x2[, x3]) = the
+ *              paper's 2N; each a power of two in [8, 1024]
+ *   trunc      parameters, NULL for the defaults
+ *   cuda_stream  stream on which the synthesis kernels run
+ *   out        receives the plan handle; the plan owns its device memory
+ * Device memory is allocated synchronously; the coefficient and FFT kernels
+ * are enqueued on cuda_stream (the plan is usable by later work on that stream).
+ * Errors: GF_ERR_ARG (bad sizes/parameters), GF_ERR_WOOD, GF_ERR_RESONANCE,
+ * GF_ERR_NOMEM, GF_ERR_CUDA.  On error *out is set to NULL. */
+gf_status gf_plan(int dim, double k, const double *alpha, const int *M,
+                  const gf_trunc_t *trunc, void *cuda_stream, gf_plan_t *out);
+
+/* Copy the synthesised remainder grid L_N (Eqs. (fcln), (ln)) to dev_out in
+ * node order [field][l3][l2][l1] (l_i = 0..M_i-1 is the node x_i = l_i h_i
+ * modulo the period, h = 2 pi / M in-plane and 2 c~ / M_last in x_last).  One
+ * field for Helmholtz plans; for Maxwell plans seven: the six combined fields
+ * (delta_pq - c^p c^q / k^2) L_d in the order xx, yy, zz, xy, xz, yz, then L_d.
+ * out_bytes must be >= gf_grid_bytes(plan).  Errors: GF_ERR_ARG, GF_ERR_CUDA. */
+gf_status gf_eval_grid(gf_plan_t plan, void *dev_out, size_t out_bytes, void *cuda_stream);
+
+/* Bytes gf_eval_grid writes (0 for a NULL plan). */
+size_t gf_grid_bytes(gf_plan_t plan);
+
+/* Evaluate at n targets (Algorithms 1-3, step 2 "Calculation").
+ *   dev_xyz   n * dim doubles, row-major [n][dim], device memory
+ *   which     GF_OUT_G (2D), GF_OUT_GD (3D Helmholtz), GF_OUT_MAXWELL6/7 (Maxwell)
+ *   dev_out   n * entries complex values, [n][entries], device memory
+ * The plan keeps a per-plan scratch list of far-branch targets (grown on
+ * demand, synchronously); calls on the same plan must therefore not overlap
+ * in time (issue them on one stream).  Non-finite targets give NaN outputs;
+ * targets on a lattice point give non-finite outputs.
+ * Errors: GF_ERR_ARG (n < 0, NULL pointers with n > 0, `which` not valid for the
+ * plan), GF_ERR_NOMEM, GF_ERR_CUDA. */
+gf_status gf_eval_points(gf_plan_t plan, const double *dev_xyz, int64_t n, int which,
+                         void *dev_out, void *cuda_stream);
+
+/* As gf_eval_points, with HOST input and output buffers: copies the targets to
+ * the device, evaluates and copies the results back, all on cuda_stream, then
+ * synchronises the stream.  Staging buffers are cached in the plan. */
+gf_status gf_eval_points_host(gf_plan_t plan, const double *host_xyz, int64_t n, int which,
+                              void *host_out, void *cuda_stream);
+
+/* Plan facts (host memory).  Returns GF_ERR_ARG on NULL arguments. */
+typedef struct {
+    int dim, M[3], nfields, precision, kind;
+    double k, alpha[2];
+    double c, c_tilde, eps, series_tol;  /* c_tilde after any resonance perturbation */
+    int quad_nodes;
+    int series_n1_lo, series_n1_hi, series_n2_lo, series_n2_hi; /* far-series index box */
+    size_t grid_device_bytes;            /* padded gather grid held by the plan */
+} gf_plan_info_t;
+gf_status gf_plan_get_info(gf_plan_t plan, gf_plan_info_t *info);
+
+/* Release the plan and its device memory (synchronises the device first).
+ * NULL is accepted. */
+gf_status gf_destroy(gf_plan_t plan);
+
+/* Static description of a status code. */
+const char *gf_status_string(gf_status s);
+
+/* Thread-local description of the last failure in this thread ("" if none). */
+const char *gf_last_error(void);
+
+/* Number of kernels the library enqueued from this process so far (all
+ * threads); used to report launch counts. */
+int64_t gf_launch_count(void);
+
+/* Per-phase device timing (tracing).  With gf_set_phase_timing(1), plans
+ * created afterwards record CUDA events around their phases on the stream they
+ * run on: synthesis (coefficients + all inverse-FFT passes), the far-series
+ * table, and, for each gf_eval_points call, the near kernel and the far
+ * kernel.  gf_plan_phase_ms synchronises on those events and writes
+ * ms[0] synthesis, ms[1] far-series table, ms[2] near kernel, ms[3] far
+ * kernel of the latest plan build / evaluation (-1 where nothing was
+ * recorded).  Timing is off by default; turning it off affects later plans. */
+gf_status gf_set_phase_timing(int on);
+gf_status gf_plan_phase_ms(gf_plan_t plan, float ms[4]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GF_H_ */

@@ -1,0 +1,145 @@
+// Internal declarations of the GB300 library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gf.h"
+
+#define GF_PI 3.14159265358979323846
+
+// ---------------------------------------------------------------------------
+// complex helpers (double2 / float2)
+// ---------------------------------------------------------------------------
+template <typename R> struct cplx_t;
+template <> struct cplx_t<double> { typedef double2 T; };
+template <> struct cplx_t<float> { typedef float2 T; };
+
+__host__ __device__ inline double2 cmk(double r, double i) { return make_double2(r, i); }
+__host__ __device__ inline float2 cmk(float r, float i) { return make_float2(r, i); }
+__host__ __device__ inline double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline double2 cmul(double2 a, double2 b)
+{
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ inline float2 cmul(float2 a, float2 b)
+{
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ inline double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__host__ __device__ inline float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__host__ __device__ inline double2 cdiv(double2 a, double2 b)
+{
+    // a / b with Smith's scaling
+    if (fabs(b.x) >= fabs(b.y)) {
+        double r = b.y / b.x, d = b.x + b.y * r;
+        return make_double2((a.x + a.y * r) / d, (a.y - a.x * r) / d);
+    }
+    double r = b.x / b.y, d = b.y + b.x * r;
+    return make_double2((a.x * r + a.y) / d, (a.y * r - a.x) / d);
+}
+
+// ---------------------------------------------------------------------------
+// Order-8 smoothstep (C^8 at both ends), the profile of both cutoffs X and
+// Y_eps: S(s) = s^9 P(-s) on [0, 1/2] with P(y) = sum_n a_n y^n,
+// a_n = C(8+n, n) C(17, 8-n); S(s) = 1 - S(1-s) on the other half.
+// S'(s) = 218790 (s(1-s))^8, S''(s) = 8 * 218790 (s(1-s))^7 (1-2s).
+// ---------------------------------------------------------------------------
+__host__ __device__ inline double smooth8_lo(double s)
+{
+    const double y = -s;
+    double p = 12870.0;
+    p = fma(p, y, 109395.0);
+    p = fma(p, y, 408408.0);
+    p = fma(p, y, 875160.0);
+    p = fma(p, y, 1178100.0);
+    p = fma(p, y, 1021020.0);
+    p = fma(p, y, 556920.0);
+    p = fma(p, y, 175032.0);
+    p = fma(p, y, 24310.0);
+    double s3 = s * s * s;
+    return s3 * s3 * s3 * p;
+}
+__host__ __device__ inline double smooth8(double s)
+{
+    if (s <= 0.0) return 0.0;
+    if (s >= 1.0) return 1.0;
+    return s <= 0.5 ? smooth8_lo(s) : 1.0 - smooth8_lo(1.0 - s);
+}
+__host__ __device__ inline double smooth8_d1(double s)
+{
+    if (s <= 0.0 || s >= 1.0) return 0.0;
+    double u = s * (1.0 - s), u2 = u * u, u4 = u2 * u2;
+    return 218790.0 * u4 * u4;
+}
+__host__ __device__ inline double smooth8_d2(double s)
+{
+    if (s <= 0.0 || s >= 1.0) return 0.0;
+    double u = s * (1.0 - s), u2 = u * u, u4 = u2 * u2;
+    return 8.0 * 218790.0 * u4 * u2 * u * (1.0 - 2.0 * s);
+}
+
+// ---------------------------------------------------------------------------
+// Parameters of the synthesis kernels (coefficients + inverse FFT), by value.
+// ---------------------------------------------------------------------------
+struct SynthArgs {
+    int dim;            // 2 or 3
+    int M1, M2, M3;     // grid points per axis (2D: M3 = 1)
+    int Mlast;          // points on the last axis (x2 in 2D, x3 in 3D)
+    int lgMlast;
+    int Q;              // Gauss nodes
+    int nf;             // stored fields: 1 (Helmholtz) or 7 (Maxwell: 6 combined + L_d)
+    int TJ;             // columns per CTA in the first pass (power of two)
+    double k, a1, a2;   // wave number, alpha
+    double ct;          // c~ (possibly perturbed)
+    double invV;        // 1 / |D|: 1/(8 pi^2 c~) in 3D, 1/(4 pi c~) in 2D
+    const double *tW;   // [Q] w_m hw X'(t_m) on [c, (c+c~)/2]
+    const double *tt;   // [Q] t_m
+    const double2 *E;   // [Mlast][Q] e^{i q_b t_m}, q_b = freq(b) pi / c~
+    const double *rr;   // [Q] r_m on [eps, 2 eps]
+    const double2 *B;   // [Q] 3D: w_m hw e^{i k r_m}(2 i k Y'(r_m) + Y''(r_m))
+    const double *Pw0;  // [Q] 2D: w_m hw Phi_1(r_m) r_m      (J0 weights)
+    const double *Pw1;  // [Q] 2D: w_m hw Phi_1(r_m) r_m^2    (J1 weights)
+    double F10;         // 2D: sqrt(V) F1-hat_0
+    void *work;         // [nf][Mlast][M2][M1] complex (3D) or [M2][M1] (2D), working precision
+    void *grid;         // padded gather grid
+    int P1, P2, P3;     // padded extents (M + 3 per periodic axis; P3 = 1 in 2D)
+};
+
+// Far-series table entry: beta_n and 1/beta_n for one in-plane index n.
+struct BetaEntry {
+    double br, bi, ibr, ibi;
+};
+struct BetaEntryF {
+    float br, bi, ibr, ibi;
+};
+
+struct EvalArgs {
+    int dim;
+    int M1, M2, M3;
+    int P1, P2, P3;
+    int nf;             // stored fields per node
+    int which;
+    double k, a1, a2;
+    double c, ct, eps;
+    double h1, h2, h3;  // node spacings
+    double T;           // ln(1/series_tol) + 3
+    const void *grid;
+    const double *x;    // [n][dim]
+    void *out;          // [n][entries]
+    int64_t n;
+    int *far_idx;       // scratch: far-branch target indices
+    int *far_count;     // scratch: number of far targets
+    const void *btab;   // far-series table [n1][n2] (BetaEntry or BetaEntryF)
+    int n1lo, n1hi, n2lo, n2hi;
+};
+
+// launch helpers implemented in synth.cu / eval.cu
+cudaError_t gf_launch_synth(const SynthArgs &a, int precision, cudaStream_t s);
+cudaError_t gf_launch_extract(const SynthArgs &a, int precision, void *dev_out, cudaStream_t s);
+cudaError_t gf_launch_beta_table(const EvalArgs &a, int precision, cudaStream_t s);
+cudaError_t gf_launch_eval(const EvalArgs &a, int precision, cudaStream_t s, cudaEvent_t ev_mid);
+
+void gf_count_launch(int n);

@@ -1,0 +1,586 @@
+// Host side of the C ABI (include/gf.h): argument checks, the Wood and
+// resonance checks of Secs. 1, 2.1 and 3.1, the small host tables (Gauss
+// nodes and cutoff weights), device memory, and the launches.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+#include "gf_internal.cuh"
+
+namespace {
+
+thread_local char g_err[512] = "";
+std::atomic<int64_t> g_launches{0};
+std::atomic<int> g_timing{0};
+
+gf_status fail(gf_status s, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+#define CU(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail(e_ == cudaErrorMemoryAllocation ? GF_ERR_NOMEM : GF_ERR_CUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                        \
+    } while (0)
+
+bool pow2_in(int m, int lo, int hi) { return m >= lo && m <= hi && (m & (m - 1)) == 0; }
+
+// Gauss-Legendre nodes/weights on [-1, 1]: Newton iteration on P_Q from the
+// Chebyshev-like first guess, P_Q and P_Q' by the Bonnet recurrence.
+void gauss_legendre(int Q, std::vector<double> &x, std::vector<double> &w)
+{
+    x.assign(Q, 0.0);
+    w.assign(Q, 0.0);
+    for (int i = 0; i < (Q + 1) / 2; ++i) {
+        double z = cos(GF_PI * (4.0 * i + 3.0) / (4.0 * Q + 2.0));
+        double pd = 1.0;
+        for (int it = 0; it < 64; ++it) {
+            double pm = 1.0, pc = z;
+            for (int n = 1; n < Q; ++n) {
+                double pn = ((2 * n + 1) * z * pc - n * pm) / (n + 1);
+                pm = pc;
+                pc = pn;
+            }
+            pd = Q * (pm - z * pc) / (1.0 - z * z);
+            double dz = pc / pd;
+            z -= dz;
+            if (fabs(dz) <= 1e-17) break;
+        }
+        double pm = 1.0, pc = z;
+        for (int n = 1; n < Q; ++n) {
+            double pn = ((2 * n + 1) * z * pc - n * pm) / (n + 1);
+            pm = pc;
+            pc = pn;
+        }
+        pd = Q * (pm - z * pc) / (1.0 - z * z);
+        double wt = 2.0 / ((1.0 - z * z) * pd * pd);
+        x[i] = -z;
+        x[Q - 1 - i] = z;
+        w[i] = wt;
+        w[Q - 1 - i] = wt;
+    }
+}
+
+double chi_d1(double t, double c, double ct)
+{
+    double w = 0.5 * (ct - c);
+    return -smooth8_d1((t - c) / w) / w;
+}
+double yps0(double r, double eps) { return 1.0 - smooth8((r - eps) / eps); }
+double yps1(double r, double eps) { return -smooth8_d1((r - eps) / eps) / eps; }
+double yps2(double r, double eps) { return -smooth8_d2((r - eps) / eps) / (eps * eps); }
+
+}  // namespace
+
+struct gf_plan_s {
+    int dim = 3, M[3] = {1, 1, 1}, nf = 1, precision = GF_FP64, kind = GF_HELMHOLTZ;
+    double k = 1, alpha[2] = {0, 0};
+    gf_trunc_t tr{};
+    double T = 0;
+    int P1 = 1, P2 = 1, P3 = 1;
+    size_t elem = 16;                 // bytes per complex value
+    void *grid = nullptr;             // padded gather grid
+    size_t grid_bytes = 0;
+    void *tables = nullptr;           // synthesis tables
+    void *btab = nullptr;             // far-series beta table
+    int n1lo = 0, n1hi = -1, n2lo = 0, n2hi = -1;
+    SynthArgs sa{};
+    // eval scratch (far list + counter) and host-call staging, grown on demand
+    std::mutex mu;
+    int *far_idx = nullptr;
+    int *far_count = nullptr;
+    int64_t far_cap = 0;
+    void *stage_x = nullptr, *stage_out = nullptr;
+    size_t stage_x_cap = 0, stage_out_cap = 0;
+    // phase timing: [0] synth start, [1] synth end, [2] table end, [3] near start, [4] near end, [5] far end
+    bool timing = false;
+    cudaEvent_t ev[6] = {};
+    bool ev_plan = false, ev_eval = false;
+};
+
+void gf_count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+extern "C" {
+
+int64_t gf_launch_count(void) { return g_launches.load(); }
+
+const char *gf_last_error(void) { return g_err; }
+
+const char *gf_status_string(gf_status s)
+{
+    switch (s) {
+    case GF_OK: return "ok";
+    case GF_ERR_ARG: return "invalid argument";
+    case GF_ERR_WOOD: return "Wood anomaly: some beta_n vanishes";
+    case GF_ERR_RESONANCE: return "resonance: beta = +-j pi / c~ for some j";
+    case GF_ERR_NOMEM: return "out of device memory";
+    case GF_ERR_CUDA: return "CUDA error";
+    case GF_ERR_TIMEOUT: return "device wait timed out";
+    case GF_ERR_UNSUPPORTED: return "unsupported request";
+    }
+    return "unknown status";
+}
+
+gf_status gf_trunc_default(gf_trunc_t *t)
+{
+    if (!t) return fail(GF_ERR_ARG, "gf_trunc_default: NULL");
+    t->c = 0.6;
+    t->c_tilde = 1.0;
+    t->eps = 0.45;
+    t->series_tol = 0.0;
+    t->quad_nodes = 64;
+    t->precision = GF_FP64;
+    t->kind = GF_HELMHOLTZ;
+    t->resonance_policy = GF_PERTURB_CTILDE;
+    return GF_OK;
+}
+
+gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf_trunc_t *trunc,
+                  void *cuda_stream, gf_plan_t *out)
+{
+    if (!out) return fail(GF_ERR_ARG, "gf_plan: out is NULL");
+    *out = nullptr;
+    g_err[0] = 0;
+    if (dim != 2 && dim != 3) return fail(GF_ERR_ARG, "gf_plan: dim must be 2 or 3 (got %d)", dim);
+    if (!alpha || !M) return fail(GF_ERR_ARG, "gf_plan: alpha and M must not be NULL");
+    if (!(k > 0.0) || !isfinite(k)) return fail(GF_ERR_ARG, "gf_plan: k must be finite and > 0");
+    for (int i = 0; i < dim - 1; ++i)
+        if (!isfinite(alpha[i])) return fail(GF_ERR_ARG, "gf_plan: alpha must be finite");
+    for (int i = 0; i < dim; ++i)
+        if (!pow2_in(M[i], 8, 1024)) return fail(GF_ERR_ARG, "gf_plan: M[%d] = %d is not a power of two in [8, 1024]", i, M[i]);
+    gf_trunc_t tr;
+    gf_trunc_default(&tr);
+    if (trunc) tr = *trunc;
+    if (!(tr.c > 0.0) || !(tr.c_tilde > tr.c) || !isfinite(tr.c_tilde))
+        return fail(GF_ERR_ARG, "gf_plan: need 0 < c < c_tilde");
+    if (!(tr.eps > 0.0) || !(2.0 * tr.eps < tr.c_tilde) || !(2.0 * tr.eps < GF_PI))
+        return fail(GF_ERR_ARG, "gf_plan: need 0 < 2 eps < min(c_tilde, pi)");
+    if (tr.quad_nodes < 8 || tr.quad_nodes > 512) return fail(GF_ERR_ARG, "gf_plan: quad_nodes must be in [8, 512]");
+    if (tr.precision != GF_FP64 && tr.precision != GF_FP32_SPLIT) return fail(GF_ERR_ARG, "gf_plan: bad precision");
+    if (tr.kind != GF_HELMHOLTZ && tr.kind != GF_MAXWELL) return fail(GF_ERR_ARG, "gf_plan: bad kind");
+    if (tr.kind == GF_MAXWELL && dim != 3) return fail(GF_ERR_ARG, "gf_plan: the Maxwell tensor needs dim = 3");
+    if (!(tr.series_tol > 0.0)) tr.series_tol = tr.precision == GF_FP64 ? 1e-16 : 1e-8;
+    if (!(tr.series_tol < 1.0)) return fail(GF_ERR_ARG, "gf_plan: series_tol must be < 1");
+    const double a1 = alpha[0], a2 = dim == 3 ? alpha[1] : 0.0;
+
+    // Wood anomaly (Sec. 1): beta_n = 0 for some n.  Only |alpha_n| ~ k matters.
+    {
+        int R = (int)ceil(k) + 2;
+        int r2 = dim == 3 ? R : 0;
+        double bmin = 1e300;
+        for (int n1 = -R - (int)fabs(a1); n1 <= R + (int)fabs(a1); ++n1)
+            for (int n2 = -r2 - (int)fabs(a2); n2 <= r2 + (int)fabs(a2); ++n2) {
+                double c1 = a1 + n1, c2 = a2 + n2;
+                double aa = sqrt(c1 * c1 + c2 * c2);
+                double b = sqrt(fabs((k - aa) * (k + aa)));
+                if (b < bmin) bmin = b;
+            }
+        if (bmin < 1e-8 * k) return fail(GF_ERR_WOOD, "gf_plan: |beta_n| = %.3g < 1e-8 k (Wood anomaly)", bmin);
+    }
+    // Resonance beta_{j'} = +-q_{j_last} (Secs. 2.1, 3.1): perturb c~ or fail.
+    const int Mlast = M[dim - 1];
+    const double ct0 = tr.c_tilde;
+    for (int attempt = 0;; ++attempt) {
+        double worst = 1e300;
+        int N1 = M[0] / 2, N2 = dim == 3 ? M[1] / 2 : 1;
+        for (int j1 = -N1; j1 < N1; ++j1)
+            for (int j2 = (dim == 3 ? -N2 : 0); j2 < (dim == 3 ? N2 : 1); ++j2) {
+                double c1 = a1 + j1, c2 = a2 + j2;
+                double A2 = c1 * c1 + c2 * c2;
+                if (A2 >= k * k) continue;  // evanescent beta cannot equal a real q
+                for (int j3 = 0; j3 <= Mlast / 2; ++j3) {
+                    double q = j3 * GF_PI / tr.c_tilde;
+                    double d = fabs(k * k - A2 - q * q);
+                    if (d < worst) worst = d;
+                }
+            }
+        if (worst >= 1e-6 * k * k) break;
+        if (tr.resonance_policy == GF_FAIL)
+            return fail(GF_ERR_RESONANCE, "gf_plan: |beta^2 - q^2| = %.3g < 1e-6 k^2", worst);
+        if (attempt >= 100) return fail(GF_ERR_RESONANCE, "gf_plan: could not perturb c_tilde away from resonance");
+        // c~ -> c~0 (1 + 1e-3 m), m = 1, 2, ... (the paper: "avoided by a perturbation of c~")
+        tr.c_tilde = ct0 * (1.0 + 1e-3 * (attempt + 1));
+    }
+
+    gf_plan_s *p = new gf_plan_s();
+    p->dim = dim;
+    p->k = k;
+    p->alpha[0] = a1;
+    p->alpha[1] = a2;
+    for (int i = 0; i < 3; ++i) p->M[i] = i < dim ? M[i] : 1;
+    p->tr = tr;
+    p->precision = tr.precision;
+    p->kind = tr.kind;
+    p->nf = tr.kind == GF_MAXWELL ? 7 : 1;
+    p->elem = tr.precision == GF_FP64 ? 16 : 8;
+    p->T = log(1.0 / tr.series_tol) + 3.0;
+    p->P1 = p->M[0] + 3;
+    p->P2 = dim == 3 ? p->M[1] + 3 : p->M[1] + 3;
+    p->P3 = dim == 3 ? p->M[2] + 3 : 1;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (g_timing.load()) {
+        p->timing = true;
+        for (int i = 0; i < 6; ++i)
+            if (cudaEventCreate(&p->ev[i]) != cudaSuccess) p->timing = false;
+    }
+
+    // ---- host tables
+    const int Q = tr.quad_nodes;
+    std::vector<double> gx, gw;
+    gauss_legendre(Q, gx, gw);
+    const double c = tr.c, ct = tr.c_tilde, eps = tr.eps, cm = 0.5 * (c + ct);
+    std::vector<double> tt(Q), tW(Q), rr(Q), P0(Q, 0.0), P1(Q, 0.0);
+    std::vector<double2> B(Q), E((size_t)Mlast * Q);
+    {
+        double hw = 0.5 * (cm - c), mid = 0.5 * (cm + c);
+        for (int m = 0; m < Q; ++m) {
+            tt[m] = mid + hw * gx[m];
+            tW[m] = gw[m] * hw * chi_d1(tt[m], c, ct);
+        }
+        double hr = 0.5 * eps, midr = 1.5 * eps;
+        for (int m = 0; m < Q; ++m) {
+            double r = midr + hr * gx[m];
+            rr[m] = r;
+            double wr = gw[m] * hr;
+            // w e^{ikr}(2ik Y' + Y'')
+            double y1 = yps1(r, eps), y2 = yps2(r, eps);
+            double cr = cos(k * r), sr = sin(k * r);
+            double2 f = make_double2(y2, 2.0 * k * y1);
+            B[m] = make_double2(wr * (cr * f.x - sr * f.y), wr * (cr * f.y + sr * f.x));
+            // Phi_1(r) = (2 + ln r) Y'/r + Y'' ln r
+            double ph1 = (2.0 + log(r)) * y1 / r + y2 * log(r);
+            P0[m] = wr * ph1 * r;
+            P1[m] = wr * ph1 * r * r;
+        }
+        for (int b = 0; b < Mlast; ++b) {
+            int jl = b < Mlast / 2 ? b : b - Mlast;
+            double q = (double)jl * GF_PI / ct;
+            for (int m = 0; m < Q; ++m) E[(size_t)b * Q + m] = make_double2(cos(q * tt[m]), sin(q * tt[m]));
+        }
+    }
+    double F10 = 0.0;
+    if (dim == 2) {
+        // sqrt(V) F1-hat_0 = -int_0^{2eps} t ln t Y dt; [0, eps] in closed form
+        double s = 0.5 * eps * eps * log(eps) - 0.25 * eps * eps;
+        double hr = 0.5 * eps, midr = 1.5 * eps;
+        for (int m = 0; m < Q; ++m) {
+            double t = midr + hr * gx[m];
+            s += gw[m] * hr * t * log(t) * yps0(t, eps);
+        }
+        F10 = -s;
+    }
+
+    // ---- device memory
+    const size_t nodes_padded = (size_t)p->P1 * p->P2 * p->P3;
+    p->grid_bytes = nodes_padded * p->nf * p->elem;
+    const size_t tab_bytes = sizeof(double) * 5 * Q + sizeof(double2) * (Q + E.size());
+    const size_t ncells = (size_t)p->M[0] * p->M[1] * p->M[2];
+    const size_t work_bytes = ncells * p->nf * p->elem;
+    void *work = nullptr;
+    gf_status st_err = GF_OK;
+    do {
+        cudaError_t e;
+        if ((e = cudaMalloc(&p->grid, p->grid_bytes)) != cudaSuccess ||
+            (e = cudaMalloc(&p->tables, tab_bytes)) != cudaSuccess ||
+            (e = cudaMallocAsync(&work, work_bytes, st)) != cudaSuccess) {
+            st_err = fail(e == cudaErrorMemoryAllocation ? GF_ERR_NOMEM : GF_ERR_CUDA, "gf_plan: cudaMalloc: %s",
+                          cudaGetErrorString(e));
+            break;
+        }
+        char *tb = (char *)p->tables;
+        double *d_tt = (double *)tb, *d_tW = d_tt + Q, *d_rr = d_tW + Q, *d_P0 = d_rr + Q, *d_P1 = d_P0 + Q;
+        double2 *d_B = (double2 *)(d_P1 + Q), *d_E = d_B + Q;
+        if ((e = cudaMemcpy(d_tt, tt.data(), sizeof(double) * Q, cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (e = cudaMemcpy(d_tW, tW.data(), sizeof(double) * Q, cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (e = cudaMemcpy(d_rr, rr.data(), sizeof(double) * Q, cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (e = cudaMemcpy(d_P0, P0.data(), sizeof(double) * Q, cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (e = cudaMemcpy(d_P1, P1.data(), sizeof(double) * Q, cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (e = cudaMemcpy(d_B, B.data(), sizeof(double2) * Q, cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (e = cudaMemcpy(d_E, E.data(), sizeof(double2) * E.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
+            st_err = fail(GF_ERR_CUDA, "gf_plan: table upload: %s", cudaGetErrorString(e));
+            break;
+        }
+        SynthArgs &sa = p->sa;
+        sa.dim = dim;
+        sa.M1 = p->M[0];
+        sa.M2 = p->M[1];
+        sa.M3 = dim == 3 ? p->M[2] : 1;
+        sa.Mlast = Mlast;
+        sa.lgMlast = 0;
+        while ((1 << sa.lgMlast) < Mlast) ++sa.lgMlast;
+        sa.Q = Q;
+        sa.nf = p->nf;
+        sa.k = k;
+        sa.a1 = a1;
+        sa.a2 = a2;
+        sa.ct = ct;
+        sa.invV = dim == 3 ? 1.0 / (8.0 * GF_PI * GF_PI * ct) : 1.0 / (4.0 * GF_PI * ct);
+        sa.tW = d_tW;
+        sa.tt = d_tt;
+        sa.E = d_E;
+        sa.rr = d_rr;
+        sa.B = d_B;
+        sa.Pw0 = d_P0;
+        sa.Pw1 = d_P1;
+        sa.F10 = F10;
+        sa.work = work;
+        sa.grid = p->grid;
+        sa.P1 = p->P1;
+        sa.P2 = p->P2;
+        sa.P3 = p->P3;
+        if (p->timing) cudaEventRecord(p->ev[0], st);
+        if ((e = gf_launch_synth(sa, p->precision, st)) != cudaSuccess) {
+            st_err = fail(GF_ERR_CUDA, "gf_plan: synthesis launch: %s", cudaGetErrorString(e));
+            break;
+        }
+        // far-series table: index box covering |alpha_n|^2 <= k^2 + (T/c)^2
+        if (dim == 3) {
+            double Rc = sqrt(k * k + (p->T / c) * (p->T / c));
+            p->n1lo = (int)floor(-a1 - Rc) - 1;
+            p->n1hi = (int)ceil(-a1 + Rc) + 1;
+            p->n2lo = (int)floor(-a2 - Rc) - 1;
+            p->n2hi = (int)ceil(-a2 + Rc) + 1;
+            size_t ne = (size_t)(p->n1hi - p->n1lo + 1) * (p->n2hi - p->n2lo + 1);
+            size_t eb = p->precision == GF_FP64 ? sizeof(BetaEntry) : sizeof(BetaEntryF);
+            if ((e = cudaMalloc(&p->btab, ne * eb)) != cudaSuccess) {
+                st_err = fail(GF_ERR_NOMEM, "gf_plan: cudaMalloc(beta table): %s", cudaGetErrorString(e));
+                break;
+            }
+            EvalArgs ea{};
+            ea.k = k;
+            ea.a1 = a1;
+            ea.a2 = a2;
+            ea.n1lo = p->n1lo;
+            ea.n1hi = p->n1hi;
+            ea.n2lo = p->n2lo;
+            ea.n2hi = p->n2hi;
+            ea.btab = p->btab;
+            if (p->timing) cudaEventRecord(p->ev[1], st);
+            if ((e = gf_launch_beta_table(ea, p->precision, st)) != cudaSuccess) {
+                st_err = fail(GF_ERR_CUDA, "gf_plan: beta table launch: %s", cudaGetErrorString(e));
+                break;
+            }
+            if (p->timing) cudaEventRecord(p->ev[2], st);
+        } else if (p->timing) {
+            cudaEventRecord(p->ev[1], st);
+            cudaEventRecord(p->ev[2], st);
+        }
+        p->ev_plan = p->timing;
+        // the work buffer is released in stream order once the synthesis is done
+        if ((e = cudaFreeAsync(work, st)) != cudaSuccess) {
+            st_err = fail(GF_ERR_CUDA, "gf_plan: cudaFreeAsync: %s", cudaGetErrorString(e));
+            break;
+        }
+        work = nullptr;
+        p->sa.work = nullptr;
+    } while (0);
+    if (st_err != GF_OK) {
+        if (work) cudaFreeAsync(work, st);
+        gf_destroy(p);
+        return st_err;
+    }
+    *out = p;
+    return GF_OK;
+}
+
+size_t gf_grid_bytes(gf_plan_t p)
+{
+    if (!p) return 0;
+    return (size_t)p->M[0] * p->M[1] * p->M[2] * p->nf * p->elem;
+}
+
+gf_status gf_eval_grid(gf_plan_t p, void *dev_out, size_t out_bytes, void *cuda_stream)
+{
+    if (!p || !dev_out) return fail(GF_ERR_ARG, "gf_eval_grid: NULL argument");
+    if (out_bytes < gf_grid_bytes(p)) return fail(GF_ERR_ARG, "gf_eval_grid: out_bytes %zu < %zu", out_bytes, gf_grid_bytes(p));
+    CU(gf_launch_extract(p->sa, p->precision, dev_out, (cudaStream_t)cuda_stream));
+    return GF_OK;
+}
+
+static gf_status ensure_scratch(gf_plan_t p, int64_t n)
+{
+    if (p->far_cap >= n && p->far_count) return GF_OK;
+    int64_t cap = p->far_cap;
+    if (cap < 1024) cap = 1024;
+    while (cap < n) cap *= 2;
+    if (p->far_idx) {
+        CU(cudaDeviceSynchronize());
+        cudaFree(p->far_idx);
+        p->far_idx = nullptr;
+        p->far_cap = 0;
+    }
+    if (!p->far_count) CU(cudaMalloc(&p->far_count, sizeof(int)));
+    CU(cudaMalloc(&p->far_idx, sizeof(int) * cap));
+    p->far_cap = cap;
+    return GF_OK;
+}
+
+gf_status gf_eval_points(gf_plan_t p, const double *dev_xyz, int64_t n, int which, void *dev_out,
+                         void *cuda_stream)
+{
+    if (!p) return fail(GF_ERR_ARG, "gf_eval_points: NULL plan");
+    if (n < 0 || n > (int64_t)0x7fffffff) return fail(GF_ERR_ARG, "gf_eval_points: n = %lld out of range", (long long)n);
+    if (n == 0) return GF_OK;
+    if (!dev_xyz || !dev_out) return fail(GF_ERR_ARG, "gf_eval_points: NULL buffer");
+    bool ok = (p->dim == 2 && which == GF_OUT_G) || (p->dim == 3 && p->kind == GF_HELMHOLTZ && which == GF_OUT_GD) ||
+              (p->kind == GF_MAXWELL && (which == GF_OUT_MAXWELL6 || which == GF_OUT_MAXWELL7));
+    if (!ok) return fail(GF_ERR_ARG, "gf_eval_points: output kind %d does not match the plan", which);
+    std::lock_guard<std::mutex> lk(p->mu);
+    gf_status s = ensure_scratch(p, n);
+    if (s != GF_OK) return s;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    CU(cudaMemsetAsync(p->far_count, 0, sizeof(int), st));
+    EvalArgs a{};
+    a.dim = p->dim;
+    a.M1 = p->M[0];
+    a.M2 = p->M[1];
+    a.M3 = p->M[2];
+    a.P1 = p->P1;
+    a.P2 = p->P2;
+    a.P3 = p->P3;
+    a.nf = p->nf;
+    a.which = which;
+    a.k = p->k;
+    a.a1 = p->alpha[0];
+    a.a2 = p->alpha[1];
+    a.c = p->tr.c;
+    a.ct = p->tr.c_tilde;
+    a.eps = p->tr.eps;
+    a.h1 = 2.0 * GF_PI / p->M[0];
+    a.h2 = p->dim == 3 ? 2.0 * GF_PI / p->M[1] : 2.0 * p->tr.c_tilde / p->M[1];
+    a.h3 = p->dim == 3 ? 2.0 * p->tr.c_tilde / p->M[2] : 1.0;
+    a.T = p->T;
+    a.grid = p->grid;
+    a.x = dev_xyz;
+    a.out = dev_out;
+    a.n = n;
+    a.far_idx = p->far_idx;
+    a.far_count = p->far_count;
+    a.btab = p->btab;
+    a.n1lo = p->n1lo;
+    a.n1hi = p->n1hi;
+    a.n2lo = p->n2lo;
+    a.n2hi = p->n2hi;
+    if (p->timing) cudaEventRecord(p->ev[3], st);
+    CU(gf_launch_eval(a, p->precision, st, p->timing ? p->ev[4] : nullptr));
+    if (p->timing) {
+        cudaEventRecord(p->ev[5], st);
+        p->ev_eval = true;
+    }
+    return GF_OK;
+}
+
+gf_status gf_set_phase_timing(int on)
+{
+    g_timing.store(on ? 1 : 0);
+    return GF_OK;
+}
+
+gf_status gf_plan_phase_ms(gf_plan_t p, float ms[4])
+{
+    if (!p || !ms) return fail(GF_ERR_ARG, "gf_plan_phase_ms: NULL argument");
+    for (int i = 0; i < 4; ++i) ms[i] = -1.0f;
+    if (p->ev_plan) {
+        CU(cudaEventSynchronize(p->ev[2]));
+        CU(cudaEventElapsedTime(&ms[0], p->ev[0], p->ev[1]));
+        CU(cudaEventElapsedTime(&ms[1], p->ev[1], p->ev[2]));
+    }
+    if (p->ev_eval) {
+        CU(cudaEventSynchronize(p->ev[5]));
+        CU(cudaEventElapsedTime(&ms[2], p->ev[3], p->ev[4]));
+        CU(cudaEventElapsedTime(&ms[3], p->ev[4], p->ev[5]));
+    }
+    return GF_OK;
+}
+
+gf_status gf_eval_points_host(gf_plan_t p, const double *host_xyz, int64_t n, int which, void *host_out,
+                              void *cuda_stream)
+{
+    if (!p) return fail(GF_ERR_ARG, "gf_eval_points_host: NULL plan");
+    if (n < 0) return fail(GF_ERR_ARG, "gf_eval_points_host: n < 0");
+    if (n == 0) return GF_OK;
+    if (!host_xyz || !host_out) return fail(GF_ERR_ARG, "gf_eval_points_host: NULL buffer");
+    int ne = which == GF_OUT_MAXWELL6 ? 6 : which == GF_OUT_MAXWELL7 ? 7 : 1;
+    size_t xb = sizeof(double) * p->dim * (size_t)n, ob = p->elem * ne * (size_t)n;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    {
+        std::lock_guard<std::mutex> lk(p->mu);
+        if (p->stage_x_cap < xb) {
+            CU(cudaDeviceSynchronize());
+            if (p->stage_x) cudaFree(p->stage_x);
+            p->stage_x = nullptr;
+            CU(cudaMalloc(&p->stage_x, xb));
+            p->stage_x_cap = xb;
+        }
+        if (p->stage_out_cap < ob) {
+            CU(cudaDeviceSynchronize());
+            if (p->stage_out) cudaFree(p->stage_out);
+            p->stage_out = nullptr;
+            CU(cudaMalloc(&p->stage_out, ob));
+            p->stage_out_cap = ob;
+        }
+    }
+    CU(cudaMemcpyAsync(p->stage_x, host_xyz, xb, cudaMemcpyHostToDevice, st));
+    gf_status s = gf_eval_points(p, (const double *)p->stage_x, n, which, p->stage_out, cuda_stream);
+    if (s != GF_OK) return s;
+    CU(cudaMemcpyAsync(host_out, p->stage_out, ob, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    return GF_OK;
+}
+
+gf_status gf_plan_get_info(gf_plan_t p, gf_plan_info_t *info)
+{
+    if (!p || !info) return fail(GF_ERR_ARG, "gf_plan_get_info: NULL argument");
+    memset(info, 0, sizeof(*info));
+    info->dim = p->dim;
+    for (int i = 0; i < 3; ++i) info->M[i] = p->M[i];
+    info->nfields = p->nf;
+    info->precision = p->precision;
+    info->kind = p->kind;
+    info->k = p->k;
+    info->alpha[0] = p->alpha[0];
+    info->alpha[1] = p->alpha[1];
+    info->c = p->tr.c;
+    info->c_tilde = p->tr.c_tilde;
+    info->eps = p->tr.eps;
+    info->series_tol = p->tr.series_tol;
+    info->quad_nodes = p->tr.quad_nodes;
+    info->series_n1_lo = p->n1lo;
+    info->series_n1_hi = p->n1hi;
+    info->series_n2_lo = p->n2lo;
+    info->series_n2_hi = p->n2hi;
+    info->grid_device_bytes = p->grid_bytes;
+    return GF_OK;
+}
+
+gf_status gf_destroy(gf_plan_t p)
+{
+    if (!p) return GF_OK;
+    cudaDeviceSynchronize();
+    if (p->grid) cudaFree(p->grid);
+    if (p->tables) cudaFree(p->tables);
+    if (p->btab) cudaFree(p->btab);
+    if (p->far_idx) cudaFree(p->far_idx);
+    if (p->far_count) cudaFree(p->far_count);
+    if (p->stage_x) cudaFree(p->stage_x);
+    if (p->stage_out) cudaFree(p->stage_out);
+    for (int i = 0; i < 6; ++i)
+        if (p->ev[i]) cudaEventDestroy(p->ev[i]);
+    delete p;
+    return GF_OK;
+}
+
+}  // extern "C"

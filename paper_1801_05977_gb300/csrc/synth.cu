@@ -1,0 +1,373 @@
+// Plan-time device work (Algorithms 1-3, step 1): remainder Fourier
+// coefficients (Eqs. (fck-coef), (fcl-coef)-(fcf2-coef), (kdj1), (fj), and the
+// Maxwell multipliers of Sec. 4) generated in double precision and fused into
+// the first inverse-FFT pass, then the remaining inverse-FFT passes, the last
+// of which scatters the grid into the padded gather layout used at evaluation.
+//
+// Inverse DFT convention (Eqs. (fcln), (ln)): with C_j = sqrt(V) L-hat_j,
+//   L_N(x_l) = V^{-1} sum_{j in S_N} C_j exp(2 pi i sum_i j_i l_i / M_i),
+// node index l standing for x = l h (mod period).  Each pass is a radix-2
+// Stockham autosort transform held in shared memory (one CTA owns a batch of
+// whole lines, so every pass reads and writes global memory exactly once).
+#include "gf_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ int freq_of(int b, int M) { return b < (M >> 1) ? b : b - M; }
+
+// beta branch of Sec. 1: sqrt(k^2 - a2) if a2 <= k^2, else i sqrt(a2 - k^2),
+// with k^2 - a2 formed as (k - a)(k + a).
+__device__ __forceinline__ double2 beta_of(double k, double a2)
+{
+    double a = sqrt(a2);
+    if (a <= k) return make_double2(sqrt((k - a) * (k + a)), 0.0);
+    return make_double2(0.0, sqrt((a - k) * (a + k)));
+}
+
+// Radix-2 Stockham autosort inverse transform (+ sign, unnormalised) of
+// `nlines` contiguous lines of length n = 2^lg held in shared memory x; y is
+// scratch of the same size.  tw[m] = exp(2 pi i m / n), m < n/2.  Returns the
+// buffer holding the result.  All threads of the CTA must call it.
+template <typename C>
+__device__ C *stockham_inverse(C *x, C *y, int n, int lg, int nlines, const C *tw)
+{
+    const int half = n >> 1;
+    const int total = nlines * half;
+    for (int Ns = 1, s = 0; Ns < n; Ns <<= 1, ++s) {
+        for (int it = threadIdx.x; it < total; it += blockDim.x) {
+            int L = it >> (lg - 1);
+            int j = it & (half - 1);
+            int k = j & (Ns - 1);
+            C *xl = x + L * n;
+            C *yl = y + L * n;
+            C v0 = xl[j];
+            C v1 = cmul(xl[j + half], tw[k << (lg - 1 - s)]);
+            int d = ((j - k) << 1) + k;
+            yl[d] = cadd(v0, v1);
+            yl[d + Ns] = csub(v0, v1);
+        }
+        __syncthreads();
+        C *t = x;
+        x = y;
+        y = t;
+    }
+    return x;
+}
+
+template <typename R>
+__device__ void load_twiddles(typename cplx_t<R>::T *tw, int n)
+{
+    for (int i = threadIdx.x; i < (n >> 1); i += blockDim.x) {
+        double s, c;
+        sincospi(2.0 * (double)i / (double)n, &s, &c);
+        tw[i] = cmk((R)c, (R)s);
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) synth_first_pass(SynthArgs a)
+{
+    typedef typename cplx_t<R>::T C;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n = a.Mlast, lg = a.lgMlast, TJ = a.TJ, Q = a.Q, nf = a.nf;
+    double2 *Av = reinterpret_cast<double2 *>(smem);   // [TJ][Q]
+    double2 *betas = Av + TJ * Q;                        // [TJ]
+    C *tw = reinterpret_cast<C *>(betas + TJ);           // [n/2]
+    C *buf0 = tw + (n >> 1);                             // [nf][TJ][n]
+    C *buf1 = buf0 + nf * TJ * n;
+    double *A2s = reinterpret_cast<double *>(buf1 + nf * TJ * n); // [TJ]
+    const int ncols = (a.dim == 3) ? a.M1 * a.M2 : a.M1;
+    const int col0 = blockIdx.x * TJ;
+
+    load_twiddles<R>(tw, n);
+    for (int t = threadIdx.x; t < TJ; t += blockDim.x) {
+        int col = col0 + t;
+        double A2;
+        if (a.dim == 3) {
+            int jx = freq_of(col % a.M1, a.M1), jy = freq_of(col / a.M1, a.M2);
+            double x1 = a.a1 + jx, x2 = a.a2 + jy;
+            A2 = x1 * x1 + x2 * x2;
+        } else {
+            int jx = freq_of(col, a.M1);
+            double x1 = a.a1 + jx;
+            A2 = x1 * x1;
+        }
+        A2s[t] = A2;
+        betas[t] = beta_of(a.k, A2);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < TJ * Q; i += blockDim.x) {
+        int t = i / Q, m = i - t * Q;
+        double2 b = betas[t];
+        double tm = a.tt[m];
+        double2 e;
+        if (b.y == 0.0) {
+            double s, c;
+            sincos(b.x * tm, &s, &c);
+            e = make_double2(c, s);
+        } else {
+            e = make_double2(exp(-b.y * tm), 0.0);
+        }
+        Av[i] = cscale(e, a.tW[m]);
+    }
+    __syncthreads();
+
+    const double k2 = a.k * a.k;
+    for (int i = threadIdx.x; i < TJ * n; i += blockDim.x) {
+        int t = i >> lg, b = i & (n - 1);
+        int col = col0 + t;
+        int jl = freq_of(b, n);
+        double q = (double)jl * GF_PI / a.ct;
+        double2 beta = betas[t];
+        double A2 = A2s[t];
+        const double2 *Am = Av + t * Q;
+        const double2 *Em = a.E + (size_t)b * Q;
+        // I1 = sum A conj(E), I2 = sum A E, from four real sums
+        double s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0;
+        for (int m = 0; m < Q; ++m) {
+            double2 A = Am[m], E = Em[m];
+            s1 = fma(A.x, E.x, s1);
+            s2 = fma(A.y, E.y, s2);
+            s3 = fma(A.x, E.y, s3);
+            s4 = fma(A.y, E.x, s4);
+        }
+        double2 I1 = make_double2(s1 + s2, s4 - s3);
+        double2 I2 = make_double2(s1 - s2, s3 + s4);
+        double2 tb = cscale(beta, 2.0);
+        double2 T1 = cdiv(I1, cmul(tb, make_double2(q - beta.x, -beta.y)));
+        double2 T2 = cdiv(I2, cmul(tb, make_double2(q + beta.x, beta.y)));
+        double D = A2 + q * q - k2;
+        double2 Cj;
+        if (a.dim == 3) {
+            double s = sqrt(A2 + q * q);
+            double hr = 0.0, hi = 0.0;
+            for (int m = 0; m < Q; ++m) {
+                double r = a.rr[m];
+                double ker = (s == 0.0) ? r : sin(s * r) / s;
+                double2 B = a.B[m];
+                hr = fma(B.x, ker, hr);
+                hi = fma(B.y, ker, hi);
+            }
+            Cj = make_double2(hr / D + T1.x - T2.x, hi / D + T1.y - T2.y);
+        } else {
+            int jx = freq_of(col, a.M1);
+            double2 K = make_double2(1.0 / D + T1.x - T2.x, T1.y - T2.y);
+            double eta2 = (double)jx * jx + q * q;
+            double2 F1, F2;
+            if (eta2 == 0.0) {
+                F1 = make_double2(a.F10, 0.0);
+                F2 = make_double2(0.0, 0.0);
+            } else {
+                double eta = sqrt(eta2);
+                double S0 = 0.0, S1 = 0.0;
+                for (int m = 0; m < Q; ++m) {
+                    double z = eta * a.rr[m];
+                    S0 = fma(a.Pw0[m], j0(z), S0);
+                    S1 = fma(a.Pw1[m], j1(z), S1);
+                }
+                // F1 = (1 + Phi1-hat/(2 pi))/eta^2,  Phi1-hat/(2 pi) = S0
+                F1 = make_double2((1.0 + S0) / eta2, 0.0);
+                // F2 = (-2 i j1 F1 + Phi2-hat/(2 pi))/eta^2,  Phi2-hat/(2 pi) = -i (j1/eta) S1
+                F2 = make_double2(0.0, (-2.0 * jx * F1.x - ((double)jx / eta) * S1) / eta2);
+            }
+            // C = K - F1 + i alpha F2
+            Cj = make_double2(K.x - F1.x - a.a1 * F2.y, K.y - F1.y + a.a1 * F2.x);
+        }
+        Cj = cscale(Cj, a.invV);
+        if (nf == 1) {
+            buf0[t * n + b] = cmk((R)Cj.x, (R)Cj.y);
+        } else {
+            // Maxwell (Sec. 4): combined fields (delta_pq - c^p c^q / k^2) C, c = (alpha1+j1, alpha2+j2, q),
+            // order xx, yy, zz, xy, xz, yz, then the plain field C (for G_d).
+            int jx = freq_of(col % a.M1, a.M1), jy = freq_of(col / a.M1, a.M2);
+            double cv0 = a.a1 + jx, cv1 = a.a2 + jy, cv2 = q;
+            double f[7] = {1.0 - cv0 * cv0 / k2, 1.0 - cv1 * cv1 / k2, 1.0 - cv2 * cv2 / k2,
+                           -cv0 * cv1 / k2,      -cv0 * cv2 / k2,      -cv1 * cv2 / k2, 1.0};
+#pragma unroll
+            for (int e = 0; e < 7; ++e) buf0[(e * TJ + t) * n + b] = cmk((R)(f[e] * Cj.x), (R)(f[e] * Cj.y));
+        }
+    }
+    __syncthreads();
+    C *res = stockham_inverse(buf0, buf1, n, lg, nf * TJ, tw);
+    C *W = reinterpret_cast<C *>(a.work);
+    const int tot = nf * n * TJ;
+    for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+        int t = i % TJ;
+        int rest = i / TJ;
+        int l = rest & (n - 1);
+        int f = rest >> lg;
+        W[((size_t)f * n + l) * ncols + col0 + t] = res[(f * TJ + t) * n + l];
+    }
+}
+
+// Middle pass (3D only): inverse transform along x2 for fixed (field, l3, b1-tile).
+template <typename R>
+__global__ void __launch_bounds__(256) synth_x2_pass(SynthArgs a, int TJ, int lg2)
+{
+    typedef typename cplx_t<R>::T C;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n = a.M2;
+    C *tw = reinterpret_cast<C *>(smem);
+    C *buf0 = tw + (n >> 1);
+    C *buf1 = buf0 + TJ * n;
+    const int b10 = blockIdx.x * TJ, l3 = blockIdx.y, f = blockIdx.z;
+    C *W = reinterpret_cast<C *>(a.work) + ((size_t)f * a.M3 + l3) * (size_t)a.M2 * a.M1;
+    load_twiddles<R>(tw, n);
+    for (int i = threadIdx.x; i < TJ * n; i += blockDim.x) {
+        int t = i % TJ, b2 = i / TJ;
+        buf0[t * n + b2] = W[(size_t)b2 * a.M1 + b10 + t];
+    }
+    __syncthreads();
+    C *res = stockham_inverse(buf0, buf1, n, lg2, TJ, tw);
+    for (int i = threadIdx.x; i < TJ * n; i += blockDim.x) {
+        int t = i % TJ, l2 = i / TJ;
+        W[(size_t)l2 * a.M1 + b10 + t] = res[t * n + l2];
+    }
+}
+
+__device__ __forceinline__ int pad_dests(int a_node, int M, int *p)
+{
+    // padded index p = a + 1 for a in [-1, M+1]; node a is periodic mod M
+    int nd = 0;
+    p[nd++] = a_node + 1;
+    if (a_node <= 1) p[nd++] = a_node + 1 + M;
+    if (a_node == M - 1) p[nd++] = 0;
+    return nd;
+}
+
+// Last pass: inverse transform along x1 of one row (all fields), then scatter
+// into the padded, field-interleaved gather grid G[p3][p2][p1][f], where
+// padded index p = a + 1 holds node a = (l + M/2) mod M, i.e. x = -pi + a h
+// (x3: -c~ + a h3), with one halo node before and two after on every
+// periodic axis so that a cubic stencil never wraps.
+template <typename R>
+__global__ void __launch_bounds__(256) synth_x1_pass(SynthArgs a, int lg1)
+{
+    typedef typename cplx_t<R>::T C;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n = a.M1, nf = a.nf;
+    C *tw = reinterpret_cast<C *>(smem);
+    C *buf0 = tw + (n >> 1);
+    C *buf1 = buf0 + nf * n;
+    const int row = blockIdx.x;  // 3D: l3 * M2 + l2; 2D: l2
+    const size_t fstride = (size_t)a.Mlast * (a.dim == 3 ? a.M2 : 1) * a.M1;
+    const C *W = reinterpret_cast<const C *>(a.work);
+    load_twiddles<R>(tw, n);
+    for (int i = threadIdx.x; i < nf * n; i += blockDim.x) {
+        int f = i / n, b1 = i - f * n;
+        buf0[i] = W[f * fstride + (size_t)row * n + b1];
+    }
+    __syncthreads();
+    C *res = stockham_inverse(buf0, buf1, n, lg1, nf, tw);
+    int l2, l3;
+    if (a.dim == 3) {
+        l3 = row / a.M2;
+        l2 = row - l3 * a.M2;
+    } else {
+        l3 = 0;
+        l2 = row;
+    }
+    int p2[3], p3[3];
+    int n2 = pad_dests((l2 + (a.M2 >> 1)) % a.M2, a.M2, p2);
+    int n3 = 1;
+    p3[0] = 0;
+    if (a.dim == 3) n3 = pad_dests((l3 + (a.M3 >> 1)) % a.M3, a.M3, p3);
+    C *G = reinterpret_cast<C *>(a.grid);
+    const int rowlen = a.P1 * nf;
+    for (int d3 = 0; d3 < n3; ++d3)
+        for (int d2 = 0; d2 < n2; ++d2) {
+            C *dst = G + ((size_t)p3[d3] * a.P2 + p2[d2]) * rowlen;
+            for (int i = threadIdx.x; i < rowlen; i += blockDim.x) {
+                int p1 = i / nf, f = i - p1 * nf;
+                int a1 = (p1 - 1 + n) % n;
+                int l1 = (a1 + (n >> 1)) % n;
+                dst[i] = res[f * n + l1];
+            }
+        }
+}
+
+// gf_eval_grid: padded gather grid -> node order [f][l3][l2][l1]
+template <typename R>
+__global__ void extract_grid(SynthArgs a, void *out)
+{
+    typedef typename cplx_t<R>::T C;
+    const C *G = reinterpret_cast<const C *>(a.grid);
+    C *o = reinterpret_cast<C *>(out);
+    const size_t per = (size_t)a.M1 * a.M2 * (a.dim == 3 ? a.M3 : 1);
+    const size_t total = per * a.nf;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        int f = (int)(i / per);
+        size_t r = i - (size_t)f * per;
+        int l1 = (int)(r % a.M1);
+        size_t r2 = r / a.M1;
+        int l2 = (int)(r2 % a.M2);
+        int l3 = (int)(r2 / a.M2);
+        int p1 = (l1 + (a.M1 >> 1)) % a.M1 + 1;
+        int p2 = (l2 + (a.M2 >> 1)) % a.M2 + 1;
+        int p3 = a.dim == 3 ? (l3 + (a.M3 >> 1)) % a.M3 + 1 : 0;
+        o[i] = G[(((size_t)p3 * a.P2 + p2) * a.P1 + p1) * a.nf + f];
+    }
+}
+
+int ilog2(int n)
+{
+    int l = 0;
+    while ((1 << l) < n) ++l;
+    return l;
+}
+
+template <typename R>
+cudaError_t launch_synth_t(const SynthArgs &a0, cudaStream_t s)
+{
+    typedef typename cplx_t<R>::T C;
+    SynthArgs a = a0;
+    const int ncols = (a.dim == 3) ? a.M1 * a.M2 : a.M1;
+    // first pass: TJ columns per CTA, bounded by shared memory
+    size_t fixed = sizeof(C) * (a.Mlast / 2);
+    int TJ = 8;
+    while (TJ > 1 && (TJ > ncols ||
+                      fixed + TJ * (sizeof(double2) * a.Q + sizeof(double2) + sizeof(double)) +
+                              2 * sizeof(C) * a.nf * TJ * a.Mlast >
+                          160 * 1024))
+        TJ >>= 1;
+    a.TJ = TJ;
+    size_t sm1 = fixed + TJ * (sizeof(double2) * a.Q + sizeof(double2) + sizeof(double)) +
+                 2 * sizeof(C) * a.nf * TJ * a.Mlast;
+    cudaError_t e = cudaFuncSetAttribute(synth_first_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+    if (e != cudaSuccess) return e;
+    synth_first_pass<R><<<ncols / TJ, 256, sm1, s>>>(a);
+    gf_count_launch(1);
+    if (a.dim == 3) {
+        int TJ2 = 8;
+        while (TJ2 > 1 && (TJ2 > a.M1 || sizeof(C) * (a.M2 / 2 + 2 * TJ2 * a.M2) > 160 * 1024)) TJ2 >>= 1;
+        size_t sm2 = sizeof(C) * (a.M2 / 2 + 2 * TJ2 * a.M2);
+        e = cudaFuncSetAttribute(synth_x2_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+        if (e != cudaSuccess) return e;
+        synth_x2_pass<R><<<dim3(a.M1 / TJ2, a.M3, a.nf), 256, sm2, s>>>(a, TJ2, ilog2(a.M2));
+        gf_count_launch(1);
+    }
+    size_t sm3 = sizeof(C) * (a.M1 / 2 + 2 * a.nf * a.M1);
+    e = cudaFuncSetAttribute(synth_x1_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
+    if (e != cudaSuccess) return e;
+    int rows = (a.dim == 3) ? a.M3 * a.M2 : a.M2;
+    synth_x1_pass<R><<<rows, 256, sm3, s>>>(a, ilog2(a.M1));
+    gf_count_launch(1);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t gf_launch_synth(const SynthArgs &a, int precision, cudaStream_t s)
+{
+    return precision == GF_FP64 ? launch_synth_t<double>(a, s) : launch_synth_t<float>(a, s);
+}
+
+cudaError_t gf_launch_extract(const SynthArgs &a, int precision, void *dev_out, cudaStream_t s)
+{
+    if (precision == GF_FP64)
+        extract_grid<double><<<1024, 256, 0, s>>>(a, dev_out);
+    else
+        extract_grid<float><<<1024, 256, 0, s>>>(a, dev_out);
+    gf_count_launch(1);
+    return cudaGetLastError();
+}

@@ -1,0 +1,195 @@
+"""Thin ctypes binding of the C ABI in include/gf.h (argument marshalling only).
+
+Every step of the method runs in the CUDA library (_build/libgf.so); torch is
+used for device memory and streams.  There is no CPU fallback: if the library
+is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+GF_OK, GF_ERR_ARG, GF_ERR_WOOD, GF_ERR_RESONANCE, GF_ERR_NOMEM, GF_ERR_CUDA, GF_ERR_TIMEOUT, GF_ERR_UNSUPPORTED = range(8)
+GF_FP64, GF_FP32_SPLIT = 0, 1
+GF_HELMHOLTZ, GF_MAXWELL = 0, 1
+GF_PERTURB_CTILDE, GF_FAIL = 0, 1
+GF_OUT_G, GF_OUT_GD, GF_OUT_MAXWELL6, GF_OUT_MAXWELL7 = 0, 1, 2, 3
+N_ENTRIES = {GF_OUT_G: 1, GF_OUT_GD: 1, GF_OUT_MAXWELL6: 6, GF_OUT_MAXWELL7: 7}
+
+
+class GfError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"[{status}] {msg}")
+        self.status = status
+
+
+class Trunc(ctypes.Structure):
+    _fields_ = [("c", ctypes.c_double), ("c_tilde", ctypes.c_double), ("eps", ctypes.c_double),
+                ("series_tol", ctypes.c_double), ("quad_nodes", ctypes.c_int), ("precision", ctypes.c_int),
+                ("kind", ctypes.c_int), ("resonance_policy", ctypes.c_int)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("M", ctypes.c_int * 3), ("nfields", ctypes.c_int),
+                ("precision", ctypes.c_int), ("kind", ctypes.c_int), ("k", ctypes.c_double),
+                ("alpha", ctypes.c_double * 2), ("c", ctypes.c_double), ("c_tilde", ctypes.c_double),
+                ("eps", ctypes.c_double), ("series_tol", ctypes.c_double), ("quad_nodes", ctypes.c_int),
+                ("series_n1_lo", ctypes.c_int), ("series_n1_hi", ctypes.c_int), ("series_n2_lo", ctypes.c_int),
+                ("series_n2_hi", ctypes.c_int), ("grid_device_bytes", ctypes.c_size_t)]
+
+
+EXPORTS = ["gf_trunc_default", "gf_plan", "gf_eval_grid", "gf_grid_bytes", "gf_eval_points",
+           "gf_eval_points_host", "gf_plan_get_info", "gf_destroy", "gf_status_string", "gf_last_error",
+           "gf_launch_count", "gf_set_phase_timing", "gf_plan_phase_ms"]
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """Load libgf.so (building it first if needed and possible)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"CUDA library not found at {_build.LIB}; run __graft_entry__.build()")
+    L = ctypes.CDLL(_build.LIB)
+    vp, i32, i64, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
+    L.gf_trunc_default.argtypes = [ctypes.POINTER(Trunc)]
+    L.gf_plan.argtypes = [i32, d, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
+                          ctypes.POINTER(Trunc), vp, ctypes.POINTER(vp)]
+    L.gf_eval_grid.argtypes = [vp, vp, sz, vp]
+    L.gf_grid_bytes.argtypes = [vp]
+    L.gf_grid_bytes.restype = sz
+    L.gf_eval_points.argtypes = [vp, vp, i64, i32, vp, vp]
+    L.gf_eval_points_host.argtypes = [vp, vp, i64, i32, vp, vp]
+    L.gf_plan_get_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
+    L.gf_destroy.argtypes = [vp]
+    L.gf_status_string.argtypes = [i32]
+    L.gf_status_string.restype = ctypes.c_char_p
+    L.gf_last_error.restype = ctypes.c_char_p
+    L.gf_launch_count.restype = i64
+    L.gf_set_phase_timing.argtypes = [i32]
+    L.gf_plan_phase_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+    for name in ("gf_trunc_default", "gf_plan", "gf_eval_grid", "gf_eval_points", "gf_eval_points_host",
+                 "gf_plan_get_info", "gf_destroy", "gf_set_phase_timing", "gf_plan_phase_ms"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != GF_OK:
+        L = lib(False)
+        raise GfError(status, f"{L.gf_status_string(status).decode()}: {L.gf_last_error().decode()}")
+
+
+def trunc_default(**kw) -> Trunc:
+    t = Trunc()
+    _check(lib().gf_trunc_default(ctypes.byref(t)))
+    for k, v in kw.items():
+        setattr(t, k, v)
+    return t
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def launch_count() -> int:
+    return int(lib().gf_launch_count())
+
+
+def set_phase_timing(on: bool):
+    _check(lib().gf_set_phase_timing(1 if on else 0))
+
+
+class Plan:
+    """A prepared (k, alpha, grid) problem: gf_plan / gf_eval_grid / gf_eval_points."""
+
+    def __init__(self, dim: int, k: float, alpha, M, trunc: Trunc | None = None, stream=None, **trunc_kw):
+        L = lib()
+        if trunc is None:
+            trunc = trunc_default(**trunc_kw)
+        al = (ctypes.c_double * 2)(*(list(alpha) + [0.0] * (2 - len(alpha))))
+        mm = (ctypes.c_int * 3)(*(list(M) + [1] * (3 - len(M))))
+        h = ctypes.c_void_p()
+        _check(L.gf_plan(int(dim), float(k), al, mm, ctypes.byref(trunc), _stream_ptr(stream), ctypes.byref(h)))
+        self._h = h
+        self.dim = dim
+        self.info = self.get_info()
+
+    def get_info(self) -> PlanInfo:
+        info = PlanInfo()
+        _check(lib().gf_plan_get_info(self._h, ctypes.byref(info)))
+        return info
+
+    @property
+    def precision(self) -> int:
+        return self.info.precision
+
+    @property
+    def complex_dtype(self):
+        import torch
+        return torch.complex128 if self.precision == GF_FP64 else torch.complex64
+
+    def eval_grid(self, stream=None):
+        """Remainder grid L_N in node order, shape (nfields, [M3,] M2, M1)."""
+        import torch
+        i = self.info
+        shape = (i.nfields,) + tuple(int(m) for m in reversed(i.M[: self.dim]))
+        out = torch.empty(shape, dtype=self.complex_dtype, device="cuda")
+        nbytes = out.numel() * out.element_size()
+        _check(lib().gf_eval_grid(self._h, ctypes.c_void_p(out.data_ptr()), nbytes, _stream_ptr(stream)))
+        return out
+
+    def eval_points_into(self, x, out, which: int, stream=None):
+        """x: float64 CUDA tensor (n, dim); out: complex CUDA tensor (n, entries)."""
+        n = x.shape[0]
+        _check(lib().gf_eval_points(self._h, ctypes.c_void_p(x.data_ptr()), n, int(which),
+                                    ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        return out
+
+    def eval_points(self, x, which: int, stream=None):
+        import torch
+        assert x.is_cuda and x.dtype == torch.float64 and x.is_contiguous() and x.shape[1] == self.dim
+        out = torch.empty((x.shape[0], N_ENTRIES[which]), dtype=self.complex_dtype, device=x.device)
+        return self.eval_points_into(x, out, which, stream)
+
+    def eval_points_host(self, x: np.ndarray, out: np.ndarray, which: int, stream=None):
+        """Host buffers in and out (numpy or pinned torch CPU tensors)."""
+        xp = x.ctypes.data if isinstance(x, np.ndarray) else x.data_ptr()
+        op = out.ctypes.data if isinstance(out, np.ndarray) else out.data_ptr()
+        n = x.shape[0]
+        _check(lib().gf_eval_points_host(self._h, ctypes.c_void_p(xp), n, int(which), ctypes.c_void_p(op),
+                                         _stream_ptr(stream)))
+        return out
+
+    def phase_ms(self):
+        """(synthesis, far table, near kernel, far kernel) device ms of the latest run."""
+        ms = (ctypes.c_float * 4)()
+        _check(lib().gf_plan_phase_ms(self._h, ms))
+        return tuple(float(v) for v in ms)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().gf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
