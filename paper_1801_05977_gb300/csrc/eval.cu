@@ -97,6 +97,13 @@ __device__ __forceinline__ void push_far(bool isfar, int i, int *list, int *coun
     if (isfar) list[base + __popc(mask & ((1u << lane) - 1u))] = i;
 }
 
+__device__ __forceinline__ int far_bucket(double z, double c)
+{
+    double r = (double)GF_FAR_BUCKETS * c / z;
+    int b = (int)r;
+    return b < GF_FAR_BUCKETS - 1 ? b : GF_FAR_BUCKETS - 1;
+}
+
 // ---------------------------------------------------------------------------
 // 3D near kernel.  NF = 1: Helmholtz (field L_d).  NF = 7: Maxwell
 // (fields 0..5 = (delta_pq - c^p c^q/k^2) L_d, field 6 = L_d).
@@ -106,6 +113,9 @@ template <typename R, int NF>
 __global__ void __launch_bounds__(256) near3d(EvalArgs a)
 {
     typedef typename cplx_t<R>::T C;
+    __shared__ int hist[GF_FAR_BUCKETS];
+    for (int b = threadIdx.x; b < GF_FAR_BUCKETS; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
     const C *G = reinterpret_cast<const C *>(a.grid);
     C *out = reinterpret_cast<C *>(a.out);
     const int ne = n_entries(a.which);
@@ -122,6 +132,7 @@ __global__ void __launch_bounds__(256) near3d(EvalArgs a)
         bool finite = isfinite(x1) && isfinite(x2) && isfinite(x3);
         bool isfar = valid && finite && fabs(x3) > a.c;
         push_far(isfar, (int)i, a.far_idx, a.far_count);
+        if (isfar) atomicAdd(&hist[far_bucket(fabs(x3), a.c)], 1);
         if (!valid || isfar) continue;
         C *o = out + i * ne;
         if (!finite) {
@@ -224,6 +235,9 @@ __global__ void __launch_bounds__(256) near3d(EvalArgs a)
             }
         }
     }
+    __syncthreads();
+    for (int b = threadIdx.x; b < GF_FAR_BUCKETS; b += blockDim.x)
+        if (hist[b]) atomicAdd(&a.far_count[1 + b], hist[b]);
 }
 
 // ---------------------------------------------------------------------------
@@ -292,8 +306,50 @@ __global__ void __launch_bounds__(256) near2d(EvalArgs a)
 }
 
 // ---------------------------------------------------------------------------
-// Far-series table: beta_n and 1/beta_n on the index box (plan time, double).
+// Counting-sort scatter of the far list by |x3| bucket, largest truncation
+// radius first (bucket NB-1 first), so that warps see homogeneous lanes and
+// the heaviest targets are scheduled first.
 // ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) far_scatter(EvalArgs a)
+{
+    __shared__ int off[GF_FAR_BUCKETS];
+    if (threadIdx.x == 0) {
+        int s = 0;
+        for (int b = GF_FAR_BUCKETS - 1; b >= 0; --b) {
+            off[b] = s;
+            s += a.far_count[1 + b];
+        }
+    }
+    __syncthreads();
+    const int count = a.far_count[0];
+    int *cursor = a.far_count + 1 + GF_FAR_BUCKETS;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        int idx = a.far_idx[i];
+        double z = fabs(a.x[3 * (size_t)idx + 2]);
+        int b = far_bucket(z, a.c);
+        int pos = off[b] + atomicAdd(&cursor[b], 1);
+        a.far_sorted[pos] = idx;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Far-series tables.  beta_table: |beta_n| and 1/|beta_n| for evanescent n
+// (beta_n = i |beta_n|); zeros for propagating n, whose terms are summed from
+// the short list PropEntry instead.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void set_entry(BetaEntry &e, double b, double ib)
+{
+    e.b = b;
+    e.ib = ib;
+}
+__device__ __forceinline__ void set_entry(BetaEntryF &e, double b, double ib)
+{
+    e.bl2 = (float)(b * 1.4426950408889634);  // b log2(e)
+    e.ib = (float)ib;
+    e.b = (float)b;
+    e.pad = 0.f;
+}
+
 template <typename E>
 __global__ void beta_table(EvalArgs a, E *tab)
 {
@@ -302,21 +358,14 @@ __global__ void beta_table(EvalArgs a, E *tab)
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += gridDim.x * blockDim.x) {
         int n1 = a.n1lo + i / W2, n2 = a.n2lo + i % W2;
         double c1 = a.a1 + n1, c2 = a.a2 + n2;
-        double A2 = c1 * c1 + c2 * c2;
-        double aa = sqrt(A2);
-        double br = 0, bi = 0;
-        if (aa <= a.k)
-            br = sqrt((a.k - aa) * (a.k + aa));
-        else
-            bi = sqrt((aa - a.k) * (aa + a.k));
-        // 1/beta: real beta -> 1/br; imaginary beta = i bi -> -i/bi
-        double ibr = br != 0.0 ? 1.0 / br : 0.0;
-        double ibi = bi != 0.0 ? -1.0 / bi : 0.0;
+        double aa = sqrt(c1 * c1 + c2 * c2);
         E e;
-        e.br = br;
-        e.bi = bi;
-        e.ibr = ibr;
-        e.ibi = ibi;
+        if (aa <= a.k) {
+            set_entry(e, 0.0, 0.0);
+        } else {
+            double b = sqrt((aa - a.k) * (aa + a.k));
+            set_entry(e, b, 1.0 / b);
+        }
         tab[i] = e;
     }
 }
@@ -327,11 +376,69 @@ __device__ __forceinline__ double warp_max(double v)
     return v;
 }
 
+// e^{-y} for y >= 0 by Tang's table-driven method (ACM TOMS 15, 1989):
+// y = j/64 + r with j = rint(64 y) and |r| <= 1/128; e^{-y} = T[j] e^{-r}, with
+// T[j] = e^{-j/64} a plan table and e^{-r} its Taylor polynomial of degree 6
+// (truncation below 2.5e-19 relative).  j is clamped to the table; callers
+// discard terms whose y lies beyond it.
+__device__ __forceinline__ double exp_neg_tab(double y, const double *__restrict__ T, int jmax)
+{
+    const double MAGIC = 6755399441055744.0;  // 1.5 * 2^52: rint by addition
+    double t = fma(y, 64.0, MAGIC);
+    int j = __double2loint(t);
+    double r = fma(t - MAGIC, -0.015625, y);
+    double p = fma(r, 1.0 / 720.0, -1.0 / 120.0);
+    p = fma(p, r, 1.0 / 24.0);
+    p = fma(p, r, -1.0 / 6.0);
+    p = fma(p, r, 0.5);
+    p = fma(p, r, -1.0);
+    p = fma(p, r, 1.0);
+    return __ldg(T + min(j, jmax)) * p;
+}
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Per-lane set-up of a far target (double): reduced t, lattice index m, z, sign.
+struct FarLane {
+    double t1, m1, t2, m2, z, sg, R2;
+    int idx;
+    bool valid;
+};
+
+__device__ __forceinline__ FarLane far_lane(const EvalArgs &a, int slot, int count)
+{
+    FarLane L;
+    L.valid = slot < count;
+    L.idx = L.valid ? a.far_sorted[slot] : 0;
+    double x1 = 0, x2 = 0, x3 = 1;
+    if (L.valid) {
+        x1 = a.x[3 * (size_t)L.idx];
+        x2 = a.x[3 * (size_t)L.idx + 1];
+        x3 = a.x[3 * (size_t)L.idx + 2];
+    }
+    reduce_period(x1, L.t1, L.m1);
+    reduce_period(x2, L.t2, L.m2);
+    L.z = fabs(x3);
+    L.sg = x3 >= 0.0 ? 1.0 : -1.0;
+    double Tz = a.T / L.z;
+    L.R2 = L.valid ? a.k * a.k + Tz * Tz : 0.0;
+    return L;
+}
+
 // ---------------------------------------------------------------------------
-// 3D far kernel, double precision (GF_FP64 plans).
-// G_d = e^{i2pi<alpha.m>} (i/8pi^2) sum_n beta_n^{-1} e^{i alpha_n.t + i beta_n |x3|};
-// Maxwell entries multiply each term by (delta_pq - c^p c^q / k^2),
-// c = (alpha1+n1, alpha2+n2, beta_n sgn x3).
+// 3D far kernel, double precision.  Series (he), and for Maxwell the second
+// derivatives (each term times delta_pq - c^p c^q/k^2, c = (alpha_n, beta sgn x3)):
+//   S = sum_n beta_n^{-1} e^{i beta_n |x3|} e^{i alpha_n . t},  G_d = e^{i2pi<alpha.m>} (i/8pi^2) S.
+// Propagating n (|alpha_n| < k, a handful) are summed from a list.  For the
+// evanescent n, beta = i b and 1/beta = -i/b, so with w = e^{-bz}/b (real) the
+// row n1 contributes -i e^{i(c1 t1 + c2a t2)} sum_{n2} w v^{n2-n2a}, v = e^{i t2},
+// the inner sum by Horner's rule: 4 flops per term besides w.
+// Every lane keeps only its own truncation set |alpha_n|^2 <= k^2 + (T/z)^2.
 // ---------------------------------------------------------------------------
 template <int NF>
 __global__ void __launch_bounds__(128) far3d_f64(EvalArgs a)
@@ -340,110 +447,151 @@ __global__ void __launch_bounds__(128) far3d_f64(EvalArgs a)
     double2 *out = reinterpret_cast<double2 *>(a.out);
     const int ne = n_entries(a.which);
     const int W2 = a.n2hi - a.n2lo + 1;
-    const int count = *a.far_count;
+    const int count = a.far_count[0];
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    const double k2 = a.k * a.k, ik2 = 1.0 / k2;
+    const double ik2 = 1.0 / (a.k * a.k);
+    const double *T = a.exptab;
+    const int jmax = a.exptab_n - 1;
     for (int w = gw; w * 32 < count; w += nw) {
-        int slot = w * 32 + lane;
-        bool valid = slot < count;
-        int idx = valid ? a.far_idx[slot] : 0;
-        double x1 = 0, x2 = 0, x3 = 1;
-        if (valid) {
-            x1 = a.x[3 * (size_t)idx];
-            x2 = a.x[3 * (size_t)idx + 1];
-            x3 = a.x[3 * (size_t)idx + 2];
-        }
-        double t1, m1, t2, m2;
-        reduce_period(x1, t1, m1);
-        reduce_period(x2, t2, m2);
-        double z = fabs(x3), sg = x3 >= 0.0 ? 1.0 : -1.0;
-        double Tz = a.T / z;
-        double R2 = valid ? k2 + Tz * Tz : 0.0;
-        double R2m = warp_max(R2);
-        double Rm = sqrt(R2m);
-        int n1a = max(a.n1lo, (int)floor(-a.a1 - Rm) - 1), n1b = min(a.n1hi, (int)ceil(-a.a1 + Rm) + 1);
-        double s2, c2;
-        sincos(t2, &s2, &c2);
-        const double2 step = make_double2(c2, s2);
-        double acc[NF][2];
+        FarLane L = far_lane(a, w * 32 + lane, count);
+        const double R2m = warp_max(L.R2);
+        const float R2f = (float)L.R2;
+        const double Rm = sqrt(R2m);
+        double sv, cv;
+        sincos(L.t2, &sv, &cv);
+        // propagating terms: P[e] (complex), e = 0 G_d, 1..6 tensor entries
+        double P[NF][2];
+        double S[NF == 1 ? 1 : 7][2];
 #pragma unroll
-        for (int e = 0; e < NF; ++e) acc[e][0] = acc[e][1] = 0.0;
-        for (int n1 = n1a; n1 <= n1b; ++n1) {
-            double c1 = a.a1 + n1;
-            double rem = R2m - c1 * c1;
-            if (rem < 0.0) continue;
-            double sr = sqrt(rem);
-            int n2a = max(a.n2lo, (int)floor(-a.a2 - sr)), n2b = min(a.n2hi, (int)ceil(-a.a2 + sr));
-            double sp, cp;
-            sincos(c1 * t1 + (a.a2 + n2a) * t2, &sp, &cp);
-            double2 p = make_double2(cp, sp);
-            const BetaEntry *row = tab + (size_t)(n1 - a.n1lo) * W2 - a.n2lo;
-            for (int n2 = n2a; n2 <= n2b; ++n2) {
-                double c2v = a.a2 + n2;
-                double A2 = c1 * c1 + c2v * c2v;
-                BetaEntry be = row[n2];
-                if (valid && A2 <= R2) {
-                    double2 ez;
-                    if (be.bi == 0.0) {
-                        double sz, cz;
-                        sincos(be.br * z, &sz, &cz);
-                        ez = make_double2(cz, sz);
-                    } else {
-                        ez = make_double2(exp(-be.bi * z), 0.0);
-                    }
-                    double2 term = cmul(cmul(make_double2(be.ibr, be.ibi), ez), p);
-                    if (NF == 1) {
-                        acc[0][0] += term.x;
-                        acc[0][1] += term.y;
-                    } else {
-                        // c3 = beta sgn: c3^2 = beta^2, c1 c3 = c1 beta sgn, ...
-                        double2 b = make_double2(be.br * sg, be.bi * sg);
-                        double2 b2 = make_double2(be.br * be.br - be.bi * be.bi, 2.0 * be.br * be.bi);
-                        double2 f[6] = {make_double2(1.0 - c1 * c1 * ik2, 0.0), make_double2(1.0 - c2v * c2v * ik2, 0.0),
-                                        make_double2(1.0 - b2.x * ik2, -b2.y * ik2), make_double2(-c1 * c2v * ik2, 0.0),
-                                        make_double2(-c1 * b.x * ik2, -c1 * b.y * ik2),
-                                        make_double2(-c2v * b.x * ik2, -c2v * b.y * ik2)};
+        for (int e = 0; e < NF; ++e) P[e][0] = P[e][1] = 0.0;
 #pragma unroll
-                        for (int e = 0; e < 6; ++e) {
-                            double2 tf = cmul(f[e], term);
-                            acc[e][0] += tf.x;
-                            acc[e][1] += tf.y;
-                        }
-                        acc[6][0] += term.x;
-                        acc[6][1] += term.y;
-                    }
+        for (int e = 0; e < (NF == 1 ? 1 : 7); ++e) S[e][0] = S[e][1] = 0.0;
+        for (int q = 0; q < a.nprop; ++q) {
+            const PropEntry pe = a.prop[q];
+            double sz, cz, sp, cp;
+            sincos(pe.br * L.z, &sz, &cz);
+            sincos(pe.c1 * L.t1 + pe.c2 * L.t2, &sp, &cp);
+            double tx = pe.ibr * (cz * cp - sz * sp), ty = pe.ibr * (cz * sp + sz * cp);
+            P[0][0] += tx;
+            P[0][1] += ty;
+            if (NF > 1) {
+                double b3 = pe.br * L.sg;
+                double f[6] = {1.0 - pe.c1 * pe.c1 * ik2, 1.0 - pe.c2 * pe.c2 * ik2, 1.0 - b3 * b3 * ik2,
+                               -pe.c1 * pe.c2 * ik2, -pe.c1 * b3 * ik2, -pe.c2 * b3 * ik2};
+#pragma unroll
+                for (int e = 0; e < 6; ++e) {
+                    P[1 + e][0] += f[e] * tx;
+                    P[1 + e][1] += f[e] * ty;
                 }
-                p = cmul(p, step);
             }
         }
-        if (!valid) continue;
-        double2 lat = lattice_phase(a.a1, m1, a.a2, m2);
-        double2 pre = cmul(lat, make_double2(0.0, 1.0 / (8.0 * GF_PI * GF_PI)));
-        double2 *o = out + (size_t)idx * ne;
+        // evanescent rows
+        const int n1a = max(a.n1lo, (int)floor(-a.a1 - Rm) - 1), n1b = min(a.n1hi, (int)ceil(-a.a1 + Rm) + 1);
+        for (int n1 = n1a; n1 <= n1b; ++n1) {
+            const double c1 = a.a1 + n1;
+            const double rem = R2m - c1 * c1;
+            if (rem < 0.0) continue;
+            const double sr = sqrt(rem);
+            const int n2a = max(a.n2lo, (int)floor(-a.a2 - sr)), n2b = min(a.n2hi, (int)ceil(-a.a2 + sr));
+            if (n2a > n2b) continue;
+            const BetaEntry *row = tab + (size_t)(n1 - a.n1lo) * W2 - a.n2lo;
+            const float c1f = (float)c1;
+            const float c1sq = c1f * c1f;
+            float c2f = (float)(a.a2 + n2b);
+            // Horner accumulators (re, im): 1 sum for G_d; 6 for Maxwell
+            double h[NF == 1 ? 1 : 6][2];
+#pragma unroll
+            for (int e = 0; e < (NF == 1 ? 1 : 6); ++e) h[e][0] = h[e][1] = 0.0;
+            double c2 = a.a2 + n2b;
+            for (int n2 = n2b; n2 >= n2a; --n2, c2f -= 1.0f, c2 -= 1.0) {
+                const BetaEntry be = row[n2];
+                const bool ok = fmaf(c2f, c2f, c1sq) <= R2f;
+                const double e = exp_neg_tab(be.b * L.z, T, jmax);
+                double wv[NF == 1 ? 1 : 6];
+                if (NF == 1) {
+                    wv[0] = ok ? e * be.ib : 0.0;
+                } else {
+                    // propagating n carry ib = 0 in the table and are summed separately
+                    const bool ev = ok && be.ib != 0.0;
+                    const double ibe = ev ? e * be.ib : 0.0;
+                    const double ee = ev ? e : 0.0;
+                    wv[0] = ibe;             // A = sum ib e
+                    wv[1] = c2 * ibe;        // B = sum c2 ib e
+                    wv[2] = c2 * wv[1];      // C = sum c2^2 ib e
+                    wv[3] = be.b * ee;       // D = sum b e
+                    wv[4] = ee;              // E = sum e
+                    wv[5] = c2 * ee;         // F = sum c2 e
+                }
+#pragma unroll
+                for (int e2 = 0; e2 < (NF == 1 ? 1 : 6); ++e2) {
+                    const double nx = fma(h[e2][0], cv, fma(-h[e2][1], sv, wv[e2]));
+                    const double ny = fma(h[e2][0], sv, h[e2][1] * cv);
+                    h[e2][0] = nx;
+                    h[e2][1] = ny;
+                }
+            }
+            double sp, cp;
+            sincos(c1 * L.t1 + (a.a2 + n2a) * L.t2, &sp, &cp);
+            // rotate each row sum by the row phase
+            double r[NF == 1 ? 1 : 6][2];
+#pragma unroll
+            for (int e2 = 0; e2 < (NF == 1 ? 1 : 6); ++e2) {
+                r[e2][0] = cp * h[e2][0] - sp * h[e2][1];
+                r[e2][1] = cp * h[e2][1] + sp * h[e2][0];
+            }
+            if (NF == 1) {
+                S[0][0] += r[0][0];
+                S[0][1] += r[0][1];
+            } else {
+                // row c1 fixed: G: A; xx: (1 - c1^2/k^2) A; yy: A - C/k^2; zz: A + D/k^2;
+                // xy: -(c1/k^2) B; xz: -(c1/k^2) E (real factor); yz: -(1/k^2) F (real factor)
+                const double fxx = 1.0 - c1 * c1 * ik2;
+                S[0][0] += r[0][0];
+                S[0][1] += r[0][1];
+                S[1][0] += fxx * r[0][0];
+                S[1][1] += fxx * r[0][1];
+                S[2][0] += r[0][0] - ik2 * r[2][0];
+                S[2][1] += r[0][1] - ik2 * r[2][1];
+                S[3][0] += r[0][0] + ik2 * r[3][0];
+                S[3][1] += r[0][1] + ik2 * r[3][1];
+                S[4][0] += -c1 * ik2 * r[1][0];
+                S[4][1] += -c1 * ik2 * r[1][1];
+                S[5][0] += -c1 * ik2 * r[4][0];
+                S[5][1] += -c1 * ik2 * r[4][1];
+                S[6][0] += -ik2 * r[5][0];
+                S[6][1] += -ik2 * r[5][1];
+            }
+        }
+        if (!L.valid) continue;
+        const double2 lat = lattice_phase(a.a1, L.m1, a.a2, L.m2);
+        const double2 pre = cmul(lat, make_double2(0.0, 1.0 / (8.0 * GF_PI * GF_PI)));
+        double2 *o = out + (size_t)L.idx * ne;
+        // evanescent sums carry the factor -i (from 1/beta = -i/b), except the
+        // xz, yz entries whose factor (-i)(-i sgn) = -sgn is real
         if (NF == 1) {
-            o[0] = cmul(pre, make_double2(acc[0][0], acc[0][1]));
+            o[0] = cmul(pre, make_double2(P[0][0] + S[0][1], P[0][1] - S[0][0]));
         } else {
-            for (int e = 0; e < 6; ++e) o[e] = cmul(pre, make_double2(acc[e][0], acc[e][1]));
-            if (a.which == GF_OUT_MAXWELL7) o[6] = cmul(pre, make_double2(acc[6][0], acc[6][1]));
+            const int map[6] = {1, 2, 3, 4, 5, 6};  // S index of xx, yy, zz, xy, xz, yz
+            for (int e = 0; e < 6; ++e) {
+                const double *s = S[map[e]];
+                double2 v;
+                if (e < 4)
+                    v = make_double2(P[1 + e][0] + s[1], P[1 + e][1] - s[0]);
+                else
+                    v = make_double2(P[1 + e][0] + L.sg * s[0], P[1 + e][1] + L.sg * s[1]);
+                o[e] = cmul(pre, v);
+            }
+            if (a.which == GF_OUT_MAXWELL7) o[6] = cmul(pre, make_double2(P[0][0] + S[0][1], P[0][1] - S[0][0]));
         }
     }
 }
 
 // ---------------------------------------------------------------------------
-// 3D far kernel, split precision: per-target quantities (reduction, lattice
-// phase, row phases) in double, the series terms and sums in float.
+// 3D far kernel, split precision: the same sums in float with the hardware
+// ex2; per-target reduction, lattice phase and the final scaling in double.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float2 row_phase_f32(double arg)
-{
-    // reduce in double, evaluate in float
-    double r = arg - TWO_PI * rint(arg * (1.0 / TWO_PI));
-    float s, c;
-    __sincosf((float)r, &s, &c);
-    return make_float2(c, s);
-}
-
 template <int NF>
 __global__ void __launch_bounds__(128) far3d_f32(EvalArgs a)
 {
@@ -451,94 +599,132 @@ __global__ void __launch_bounds__(128) far3d_f32(EvalArgs a)
     float2 *out = reinterpret_cast<float2 *>(a.out);
     const int ne = n_entries(a.which);
     const int W2 = a.n2hi - a.n2lo + 1;
-    const int count = *a.far_count;
+    const int count = a.far_count[0];
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    const double k2 = a.k * a.k;
-    const float ik2 = (float)(1.0 / k2);
+    const float ik2 = (float)(1.0 / (a.k * a.k));
+    const float a2f = (float)a.a2;
     for (int w = gw; w * 32 < count; w += nw) {
-        int slot = w * 32 + lane;
-        bool valid = slot < count;
-        int idx = valid ? a.far_idx[slot] : 0;
-        double x1 = 0, x2 = 0, x3 = 1;
-        if (valid) {
-            x1 = a.x[3 * (size_t)idx];
-            x2 = a.x[3 * (size_t)idx + 1];
-            x3 = a.x[3 * (size_t)idx + 2];
-        }
-        double t1, m1, t2, m2;
-        reduce_period(x1, t1, m1);
-        reduce_period(x2, t2, m2);
-        double zd = fabs(x3);
-        float z = (float)zd, sg = x3 >= 0.0 ? 1.f : -1.f;
-        double Tz = a.T / zd;
-        double R2 = valid ? k2 + Tz * Tz : 0.0;
-        double R2m = warp_max(R2);
-        double Rm = sqrt(R2m);
-        float R2f = (float)R2;
-        int n1a = max(a.n1lo, (int)floor(-a.a1 - Rm) - 1), n1b = min(a.n1hi, (int)ceil(-a.a1 + Rm) + 1);
-        float s2, c2;
-        __sincosf((float)t2, &s2, &c2);
-        const float2 step = make_float2(c2, s2);
-        float acc[NF][2];
+        FarLane L = far_lane(a, w * 32 + lane, count);
+        const double R2m = warp_max(L.R2);
+        const float R2f = (float)L.R2;
+        const double Rm = sqrt(R2m);
+        const float z = (float)L.z, t1 = (float)L.t1, t2 = (float)L.t2, sg = (float)L.sg;
+        float sv, cv;
+        sincosf(t2, &sv, &cv);
+        float P[NF][2];
+        float S[NF == 1 ? 1 : 7][2];
 #pragma unroll
-        for (int e = 0; e < NF; ++e) acc[e][0] = acc[e][1] = 0.f;
-        for (int n1 = n1a; n1 <= n1b; ++n1) {
-            double c1d = a.a1 + n1;
-            double rem = R2m - c1d * c1d;
-            if (rem < 0.0) continue;
-            double sr = sqrt(rem);
-            int n2a = max(a.n2lo, (int)floor(-a.a2 - sr)), n2b = min(a.n2hi, (int)ceil(-a.a2 + sr));
-            float2 p = row_phase_f32(c1d * t1 + (a.a2 + n2a) * t2);
-            float c1 = (float)c1d;
-            const BetaEntryF *row = tab + (size_t)(n1 - a.n1lo) * W2 - a.n2lo;
-            for (int n2 = n2a; n2 <= n2b; ++n2) {
-                float c2v = (float)(a.a2 + n2);
-                float A2 = c1 * c1 + c2v * c2v;
-                BetaEntryF be = row[n2];
-                if (valid && A2 <= R2f) {
-                    float2 ez;
-                    if (be.bi == 0.f) {
-                        float sz, cz;
-                        sincosf(be.br * z, &sz, &cz);
-                        ez = make_float2(cz, sz);
-                    } else {
-                        ez = make_float2(__expf(-be.bi * z), 0.f);
-                    }
-                    float2 term = cmul(cmul(make_float2(be.ibr, be.ibi), ez), p);
-                    if (NF == 1) {
-                        acc[0][0] += term.x;
-                        acc[0][1] += term.y;
-                    } else {
-                        float2 b = make_float2(be.br * sg, be.bi * sg);
-                        float2 b2 = make_float2(be.br * be.br - be.bi * be.bi, 2.f * be.br * be.bi);
-                        float2 f[6] = {make_float2(1.f - c1 * c1 * ik2, 0.f), make_float2(1.f - c2v * c2v * ik2, 0.f),
-                                       make_float2(1.f - b2.x * ik2, -b2.y * ik2), make_float2(-c1 * c2v * ik2, 0.f),
-                                       make_float2(-c1 * b.x * ik2, -c1 * b.y * ik2),
-                                       make_float2(-c2v * b.x * ik2, -c2v * b.y * ik2)};
+        for (int e = 0; e < NF; ++e) P[e][0] = P[e][1] = 0.f;
 #pragma unroll
-                        for (int e = 0; e < 6; ++e) {
-                            float2 tf = cmul(f[e], term);
-                            acc[e][0] += tf.x;
-                            acc[e][1] += tf.y;
-                        }
-                        acc[6][0] += term.x;
-                        acc[6][1] += term.y;
-                    }
+        for (int e = 0; e < (NF == 1 ? 1 : 7); ++e) S[e][0] = S[e][1] = 0.f;
+        for (int q = 0; q < a.nprop; ++q) {
+            const PropEntry pe = a.prop[q];
+            float br = (float)pe.br, ibr = (float)pe.ibr, c1 = (float)pe.c1, c2 = (float)pe.c2;
+            float sz, cz, sp, cp;
+            sincosf(br * z, &sz, &cz);
+            sincosf(c1 * t1 + c2 * t2, &sp, &cp);
+            float tx = ibr * (cz * cp - sz * sp), ty = ibr * (cz * sp + sz * cp);
+            P[0][0] += tx;
+            P[0][1] += ty;
+            if (NF > 1) {
+                float b3 = br * sg;
+                float f[6] = {1.f - c1 * c1 * ik2, 1.f - c2 * c2 * ik2, 1.f - b3 * b3 * ik2,
+                              -c1 * c2 * ik2, -c1 * b3 * ik2, -c2 * b3 * ik2};
+#pragma unroll
+                for (int e = 0; e < 6; ++e) {
+                    P[1 + e][0] += f[e] * tx;
+                    P[1 + e][1] += f[e] * ty;
                 }
-                p = cmul(p, step);
             }
         }
-        if (!valid) continue;
-        double2 lat = lattice_phase(a.a1, m1, a.a2, m2);
-        double2 pre = cmul(lat, make_double2(0.0, 1.0 / (8.0 * GF_PI * GF_PI)));
-        float2 *o = out + (size_t)idx * ne;
+        const int n1a = max(a.n1lo, (int)floor(-a.a1 - Rm) - 1), n1b = min(a.n1hi, (int)ceil(-a.a1 + Rm) + 1);
+        for (int n1 = n1a; n1 <= n1b; ++n1) {
+            const double c1d = a.a1 + n1;
+            const double rem = R2m - c1d * c1d;
+            if (rem < 0.0) continue;
+            const double sr = sqrt(rem);
+            const int n2a = max(a.n2lo, (int)floor(-a.a2 - sr)), n2b = min(a.n2hi, (int)ceil(-a.a2 + sr));
+            if (n2a > n2b) continue;
+            const BetaEntryF *row = tab + (size_t)(n1 - a.n1lo) * W2 - a.n2lo;
+            const float c1 = (float)c1d;
+            const float c1sq = c1 * c1;
+            float c2 = a2f + (float)n2b;
+            float h[NF == 1 ? 1 : 6][2];
+#pragma unroll
+            for (int e = 0; e < (NF == 1 ? 1 : 6); ++e) h[e][0] = h[e][1] = 0.f;
+            for (int n2 = n2b; n2 >= n2a; --n2, c2 -= 1.0f) {
+                const BetaEntryF be = row[n2];
+                // propagating n carry ib = 0 in the table and are summed separately
+                const bool ok = fmaf(c2, c2, c1sq) <= R2f && be.ib != 0.f;
+                const float e = ok ? ex2_approx(-be.bl2 * z) : 0.f;
+                float wv[NF == 1 ? 1 : 6];
+                if (NF == 1) {
+                    wv[0] = e * be.ib;
+                } else {
+                    wv[0] = e * be.ib;
+                    wv[1] = c2 * wv[0];
+                    wv[2] = c2 * wv[1];
+                    wv[3] = be.b * e;
+                    wv[4] = e;
+                    wv[5] = c2 * e;
+                }
+#pragma unroll
+                for (int e2 = 0; e2 < (NF == 1 ? 1 : 6); ++e2) {
+                    const float nx = fmaf(h[e2][0], cv, fmaf(-h[e2][1], sv, wv[e2]));
+                    const float ny = fmaf(h[e2][0], sv, h[e2][1] * cv);
+                    h[e2][0] = nx;
+                    h[e2][1] = ny;
+                }
+            }
+            float sp, cp;
+            sincosf(c1 * t1 + (a2f + (float)n2a) * t2, &sp, &cp);
+            float r[NF == 1 ? 1 : 6][2];
+#pragma unroll
+            for (int e2 = 0; e2 < (NF == 1 ? 1 : 6); ++e2) {
+                r[e2][0] = cp * h[e2][0] - sp * h[e2][1];
+                r[e2][1] = cp * h[e2][1] + sp * h[e2][0];
+            }
+            if (NF == 1) {
+                S[0][0] += r[0][0];
+                S[0][1] += r[0][1];
+            } else {
+                const float fxx = 1.f - c1 * c1 * ik2;
+                S[0][0] += r[0][0];
+                S[0][1] += r[0][1];
+                S[1][0] += fxx * r[0][0];
+                S[1][1] += fxx * r[0][1];
+                S[2][0] += r[0][0] - ik2 * r[2][0];
+                S[2][1] += r[0][1] - ik2 * r[2][1];
+                S[3][0] += r[0][0] + ik2 * r[3][0];
+                S[3][1] += r[0][1] + ik2 * r[3][1];
+                S[4][0] += -c1 * ik2 * r[1][0];
+                S[4][1] += -c1 * ik2 * r[1][1];
+                S[5][0] += -c1 * ik2 * r[4][0];
+                S[5][1] += -c1 * ik2 * r[4][1];
+                S[6][0] += -ik2 * r[5][0];
+                S[6][1] += -ik2 * r[5][1];
+            }
+        }
+        if (!L.valid) continue;
+        const double2 lat = lattice_phase(a.a1, L.m1, a.a2, L.m2);
+        const double2 pre = cmul(lat, make_double2(0.0, 1.0 / (8.0 * GF_PI * GF_PI)));
+        float2 *o = out + (size_t)L.idx * ne;
         if (NF == 1) {
-            store_out(o, cmul(pre, make_double2(acc[0][0], acc[0][1])));
+            store_out(o, cmul(pre, make_double2(P[0][0] + S[0][1], P[0][1] - S[0][0])));
         } else {
-            for (int e = 0; e < 6; ++e) store_out(o + e, cmul(pre, make_double2(acc[e][0], acc[e][1])));
-            if (a.which == GF_OUT_MAXWELL7) store_out(o + 6, cmul(pre, make_double2(acc[6][0], acc[6][1])));
+            for (int e = 0; e < 6; ++e) {
+                const float *s = S[1 + e];
+                double2 v;
+                if (e < 4)
+                    v = make_double2(P[1 + e][0] + s[1], P[1 + e][1] - s[0]);
+                else
+                    v = make_double2(P[1 + e][0] + sg * s[0], P[1 + e][1] + sg * s[1]);
+                store_out(o + e, cmul(pre, v));
+            }
+            if (a.which == GF_OUT_MAXWELL7)
+                store_out(o + 6, cmul(pre, make_double2(P[0][0] + S[0][1], P[0][1] - S[0][0])));
         }
     }
 }
@@ -614,6 +800,7 @@ cudaError_t launch_eval_t(const EvalArgs &a, cudaStream_t s, cudaEvent_t ev_mid)
     } else if (a.nf == 1) {
         near3d<R, 1><<<(int)blocks, 256, 0, s>>>(a);
         if (ev_mid) cudaEventRecord(ev_mid, s);
+        far_scatter<<<nsm * 2, 256, 0, s>>>(a);
         if (sizeof(R) == 8)
             far3d_f64<1><<<farblocks, 128, 0, s>>>(a);
         else
@@ -621,12 +808,13 @@ cudaError_t launch_eval_t(const EvalArgs &a, cudaStream_t s, cudaEvent_t ev_mid)
     } else {
         near3d<R, 7><<<(int)blocks, 256, 0, s>>>(a);
         if (ev_mid) cudaEventRecord(ev_mid, s);
+        far_scatter<<<nsm * 2, 256, 0, s>>>(a);
         if (sizeof(R) == 8)
             far3d_f64<7><<<farblocks, 128, 0, s>>>(a);
         else
             far3d_f32<7><<<farblocks, 128, 0, s>>>(a);
     }
-    gf_count_launch(2);
+    gf_count_launch(a.dim == 2 ? 2 : 3);
     return cudaGetLastError();
 }
 
@@ -635,9 +823,9 @@ cudaError_t launch_eval_t(const EvalArgs &a, cudaStream_t s, cudaEvent_t ev_mid)
 cudaError_t gf_launch_beta_table(const EvalArgs &a, int precision, cudaStream_t s)
 {
     if (precision == GF_FP64)
-        beta_table<BetaEntry><<<256, 256, 0, s>>>(a, (BetaEntry *)a.btab);
+        beta_table<BetaEntry><<<256, 256, 0, s>>>(a, (BetaEntry *)const_cast<void *>(a.btab));
     else
-        beta_table<BetaEntryF><<<256, 256, 0, s>>>(a, (BetaEntryF *)a.btab);
+        beta_table<BetaEntryF><<<256, 256, 0, s>>>(a, (BetaEntryF *)const_cast<void *>(a.btab));
     gf_count_launch(1);
     return cudaGetLastError();
 }

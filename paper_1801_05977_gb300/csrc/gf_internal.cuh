@@ -100,6 +100,9 @@ struct SynthArgs {
     const double2 *E;   // [Mlast][Q] e^{i q_b t_m}, q_b = freq(b) pi / c~
     const double *rr;   // [Q] r_m on [eps, 2 eps]
     const double2 *B;   // [Q] 3D: w_m hw e^{i k r_m}(2 i k Y'(r_m) + Y''(r_m))
+    const double2 *hcheb; // 3D: Chebyshev coefficients of h(s) per panel [hnpan][hdeg + 1]
+    int hdeg, hnpan;
+    double hpan;        // panel width in s
     const double *Pw0;  // [Q] 2D: w_m hw Phi_1(r_m) r_m      (J0 weights)
     const double *Pw1;  // [Q] 2D: w_m hw Phi_1(r_m) r_m^2    (J1 weights)
     double F10;         // 2D: sqrt(V) F1-hat_0
@@ -108,12 +111,17 @@ struct SynthArgs {
     int P1, P2, P3;     // padded extents (M + 3 per periodic axis; P3 = 1 in 2D)
 };
 
-// Far-series table entry: beta_n and 1/beta_n for one in-plane index n.
+// Far-series table entry for one in-plane index n: b = |beta_n| and 1/b for
+// evanescent n (beta_n = i b); zeros for propagating n (|alpha_n| <= k).
 struct BetaEntry {
-    double br, bi, ibr, ibi;
+    double b, ib;
 };
 struct BetaEntryF {
-    float br, bi, ibr, ibi;
+    float bl2, ib, b, pad;  // b log2(e), 1/b, b
+};
+// Propagating index n: in-plane wave vector alpha_n, real beta_n and 1/beta_n.
+struct PropEntry {
+    double c1, c2, br, ibr;
 };
 
 struct EvalArgs {
@@ -130,11 +138,21 @@ struct EvalArgs {
     const double *x;    // [n][dim]
     void *out;          // [n][entries]
     int64_t n;
-    int *far_idx;       // scratch: far-branch target indices
-    int *far_count;     // scratch: number of far targets
+    int *far_idx;       // scratch: far-branch target indices, in append order
+    int *far_sorted;    // scratch: the same indices ordered by |x_last| bucket (3D)
+    int *far_count;     // scratch counters: [0] far count, [1..NB] bucket sizes, [NB+1..2NB] cursors
     const void *btab;   // far-series table [n1][n2] (BetaEntry or BetaEntryF)
     int n1lo, n1hi, n2lo, n2hi;
+    const PropEntry *prop;  // propagating indices (|alpha_n| <= k)
+    int nprop;
+    const double *exptab;   // e^{-j/64}, j = 0 .. exptab_n - 1
+    int exptab_n;
 };
+
+// Far targets are bucketed by b = floor(NB c / |x_last|) (clamped to NB-1) so
+// that the lanes of a warp share nearly the same series truncation radius.
+#define GF_FAR_BUCKETS 64
+#define GF_SCRATCH_COUNTERS (1 + 2 * GF_FAR_BUCKETS)
 
 // launch helpers implemented in synth.cu / eval.cu
 cudaError_t gf_launch_synth(const SynthArgs &a, int precision, cudaStream_t s);

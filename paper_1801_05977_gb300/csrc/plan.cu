@@ -96,12 +96,16 @@ struct gf_plan_s {
     size_t grid_bytes = 0;
     void *tables = nullptr;           // synthesis tables
     void *btab = nullptr;             // far-series beta table
+    PropEntry *prop = nullptr;        // propagating indices
+    int nprop = 0;
+    double *exptab = nullptr;         // e^{-j/64}
+    int exptab_n = 0;
     int n1lo = 0, n1hi = -1, n2lo = 0, n2hi = -1;
     SynthArgs sa{};
     // eval scratch (far list + counter) and host-call staging, grown on demand
     std::mutex mu;
-    int *far_idx = nullptr;
-    int *far_count = nullptr;
+    int *far_idx = nullptr;      // [2 * cap]: append-order list, then bucket-sorted list
+    int *far_count = nullptr;    // [GF_SCRATCH_COUNTERS]
     int64_t far_cap = 0;
     void *stage_x = nullptr, *stage_out = nullptr;
     size_t stage_x_cap = 0, stage_out_cap = 0;
@@ -271,6 +275,43 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
             for (int m = 0; m < Q; ++m) E[(size_t)b * Q + m] = make_double2(cos(q * tt[m]), sin(q * tt[m]));
         }
     }
+    // 3D: piecewise Chebyshev interpolant of h(s) = sum_m B_m sin(s r_m)/s on
+    // [0, s_max], s_max >= max_j |xi_j|; degree 14, panels of width 2.
+    const int hdeg = 14;
+    const double hpan = 2.0;
+    int hnpan = 1;
+    std::vector<double2> hcheb;
+    if (dim == 3) {
+        double m1 = fabs(a1) + M[0] / 2 + 1, m2 = fabs(a2) + M[1] / 2 + 1, m3 = (M[2] / 2 + 1) * GF_PI / ct;
+        double smax = sqrt(m1 * m1 + m2 * m2 + m3 * m3) + hpan;
+        hnpan = (int)ceil(smax / hpan) + 1;
+        hcheb.assign((size_t)hnpan * (hdeg + 1), make_double2(0, 0));
+        const int nn = hdeg + 1;
+        std::vector<double2> fv(nn);
+        for (int pn = 0; pn < hnpan; ++pn) {
+            double cen = (pn + 0.5) * hpan, hh = 0.5 * hpan;
+            for (int kk = 0; kk < nn; ++kk) {
+                double s = cen + hh * cos(GF_PI * (kk + 0.5) / nn);
+                double hr = 0.0, hi = 0.0;
+                for (int m = 0; m < Q; ++m) {
+                    double ker = (s == 0.0) ? rr[m] : sin(s * rr[m]) / s;
+                    hr += B[m].x * ker;
+                    hi += B[m].y * ker;
+                }
+                fv[kk] = make_double2(hr, hi);
+            }
+            for (int jj = 0; jj < nn; ++jj) {
+                double cr = 0.0, ci = 0.0;
+                for (int kk = 0; kk < nn; ++kk) {
+                    double w = cos(GF_PI * jj * (kk + 0.5) / nn);
+                    cr += fv[kk].x * w;
+                    ci += fv[kk].y * w;
+                }
+                double sc = (jj == 0 ? 1.0 : 2.0) / nn;
+                hcheb[(size_t)pn * nn + jj] = make_double2(cr * sc, ci * sc);
+            }
+        }
+    }
     double F10 = 0.0;
     if (dim == 2) {
         // sqrt(V) F1-hat_0 = -int_0^{2eps} t ln t Y dt; [0, eps] in closed form
@@ -286,7 +327,7 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
     // ---- device memory
     const size_t nodes_padded = (size_t)p->P1 * p->P2 * p->P3;
     p->grid_bytes = nodes_padded * p->nf * p->elem;
-    const size_t tab_bytes = sizeof(double) * 5 * Q + sizeof(double2) * (Q + E.size());
+    const size_t tab_bytes = sizeof(double) * 5 * Q + sizeof(double2) * (Q + E.size() + hcheb.size());
     const size_t ncells = (size_t)p->M[0] * p->M[1] * p->M[2];
     const size_t work_bytes = ncells * p->nf * p->elem;
     void *work = nullptr;
@@ -302,14 +343,17 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
         }
         char *tb = (char *)p->tables;
         double *d_tt = (double *)tb, *d_tW = d_tt + Q, *d_rr = d_tW + Q, *d_P0 = d_rr + Q, *d_P1 = d_P0 + Q;
-        double2 *d_B = (double2 *)(d_P1 + Q), *d_E = d_B + Q;
+        double2 *d_B = (double2 *)(d_P1 + Q), *d_E = d_B + Q, *d_H = d_E + E.size();
         if ((e = cudaMemcpy(d_tt, tt.data(), sizeof(double) * Q, cudaMemcpyHostToDevice)) != cudaSuccess ||
             (e = cudaMemcpy(d_tW, tW.data(), sizeof(double) * Q, cudaMemcpyHostToDevice)) != cudaSuccess ||
             (e = cudaMemcpy(d_rr, rr.data(), sizeof(double) * Q, cudaMemcpyHostToDevice)) != cudaSuccess ||
             (e = cudaMemcpy(d_P0, P0.data(), sizeof(double) * Q, cudaMemcpyHostToDevice)) != cudaSuccess ||
             (e = cudaMemcpy(d_P1, P1.data(), sizeof(double) * Q, cudaMemcpyHostToDevice)) != cudaSuccess ||
             (e = cudaMemcpy(d_B, B.data(), sizeof(double2) * Q, cudaMemcpyHostToDevice)) != cudaSuccess ||
-            (e = cudaMemcpy(d_E, E.data(), sizeof(double2) * E.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
+            (e = cudaMemcpy(d_E, E.data(), sizeof(double2) * E.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (!hcheb.empty() &&
+             (e = cudaMemcpy(d_H, hcheb.data(), sizeof(double2) * hcheb.size(), cudaMemcpyHostToDevice)) !=
+                 cudaSuccess)) {
             st_err = fail(GF_ERR_CUDA, "gf_plan: table upload: %s", cudaGetErrorString(e));
             break;
         }
@@ -333,6 +377,10 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
         sa.E = d_E;
         sa.rr = d_rr;
         sa.B = d_B;
+        sa.hcheb = d_H;
+        sa.hdeg = hdeg;
+        sa.hnpan = hnpan;
+        sa.hpan = hpan;
         sa.Pw0 = d_P0;
         sa.Pw1 = d_P1;
         sa.F10 = F10;
@@ -357,6 +405,34 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
             size_t eb = p->precision == GF_FP64 ? sizeof(BetaEntry) : sizeof(BetaEntryF);
             if ((e = cudaMalloc(&p->btab, ne * eb)) != cudaSuccess) {
                 st_err = fail(GF_ERR_NOMEM, "gf_plan: cudaMalloc(beta table): %s", cudaGetErrorString(e));
+                break;
+            }
+            // propagating indices (|alpha_n| <= k) and the exponential table e^{-j/64}
+            std::vector<PropEntry> prop;
+            for (int n1 = p->n1lo; n1 <= p->n1hi; ++n1)
+                for (int n2 = p->n2lo; n2 <= p->n2hi; ++n2) {
+                    double c1 = a1 + n1, c2 = a2 + n2;
+                    double aa = sqrt(c1 * c1 + c2 * c2);
+                    if (aa <= k) {
+                        double br = sqrt((k - aa) * (k + aa));
+                        prop.push_back(PropEntry{c1, c2, br, 1.0 / br});
+                    }
+                }
+            p->nprop = (int)prop.size();
+            p->exptab_n = 64 * ((int)ceil(p->T) + 2) + 1;
+            std::vector<double> et(p->exptab_n);
+            for (int j = 0; j < p->exptab_n; ++j) et[j] = exp(-(double)j / 64.0);
+            if ((e = cudaMalloc(&p->prop, sizeof(PropEntry) * (prop.size() + 1))) != cudaSuccess ||
+                (e = cudaMalloc(&p->exptab, sizeof(double) * et.size())) != cudaSuccess) {
+                st_err = fail(GF_ERR_NOMEM, "gf_plan: cudaMalloc(series tables): %s", cudaGetErrorString(e));
+                break;
+            }
+            if ((!prop.empty() &&
+                 (e = cudaMemcpy(p->prop, prop.data(), sizeof(PropEntry) * prop.size(), cudaMemcpyHostToDevice)) !=
+                     cudaSuccess) ||
+                (e = cudaMemcpy(p->exptab, et.data(), sizeof(double) * et.size(), cudaMemcpyHostToDevice)) !=
+                    cudaSuccess) {
+                st_err = fail(GF_ERR_CUDA, "gf_plan: series table upload: %s", cudaGetErrorString(e));
                 break;
             }
             EvalArgs ea{};
@@ -422,8 +498,8 @@ static gf_status ensure_scratch(gf_plan_t p, int64_t n)
         p->far_idx = nullptr;
         p->far_cap = 0;
     }
-    if (!p->far_count) CU(cudaMalloc(&p->far_count, sizeof(int)));
-    CU(cudaMalloc(&p->far_idx, sizeof(int) * cap));
+    if (!p->far_count) CU(cudaMalloc(&p->far_count, sizeof(int) * GF_SCRATCH_COUNTERS));
+    CU(cudaMalloc(&p->far_idx, sizeof(int) * 2 * cap));
     p->far_cap = cap;
     return GF_OK;
 }
@@ -442,7 +518,7 @@ gf_status gf_eval_points(gf_plan_t p, const double *dev_xyz, int64_t n, int whic
     gf_status s = ensure_scratch(p, n);
     if (s != GF_OK) return s;
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    CU(cudaMemsetAsync(p->far_count, 0, sizeof(int), st));
+    CU(cudaMemsetAsync(p->far_count, 0, sizeof(int) * GF_SCRATCH_COUNTERS, st));
     EvalArgs a{};
     a.dim = p->dim;
     a.M1 = p->M[0];
@@ -468,12 +544,17 @@ gf_status gf_eval_points(gf_plan_t p, const double *dev_xyz, int64_t n, int whic
     a.out = dev_out;
     a.n = n;
     a.far_idx = p->far_idx;
+    a.far_sorted = p->far_idx + p->far_cap;
     a.far_count = p->far_count;
     a.btab = p->btab;
     a.n1lo = p->n1lo;
     a.n1hi = p->n1hi;
     a.n2lo = p->n2lo;
     a.n2hi = p->n2hi;
+    a.prop = p->prop;
+    a.nprop = p->nprop;
+    a.exptab = p->exptab;
+    a.exptab_n = p->exptab_n;
     if (p->timing) cudaEventRecord(p->ev[3], st);
     CU(gf_launch_eval(a, p->precision, st, p->timing ? p->ev[4] : nullptr));
     if (p->timing) {
@@ -573,6 +654,8 @@ gf_status gf_destroy(gf_plan_t p)
     if (p->grid) cudaFree(p->grid);
     if (p->tables) cudaFree(p->tables);
     if (p->btab) cudaFree(p->btab);
+    if (p->prop) cudaFree(p->prop);
+    if (p->exptab) cudaFree(p->exptab);
     if (p->far_idx) cudaFree(p->far_idx);
     if (p->far_count) cudaFree(p->far_count);
     if (p->stage_x) cudaFree(p->stage_x);

@@ -139,15 +139,25 @@ __global__ void __launch_bounds__(256) synth_first_pass(SynthArgs a)
         double D = A2 + q * q - k2;
         double2 Cj;
         if (a.dim == 3) {
+            // h(s) = sum_m B_m sin(s r_m)/s, read from its piecewise Chebyshev
+            // interpolant (Clenshaw); h has bandwidth 2 eps in s, so degree 14 on
+            // panels of width 2 reproduces the quadrature to rounding.
             double s = sqrt(A2 + q * q);
-            double hr = 0.0, hi = 0.0;
-            for (int m = 0; m < Q; ++m) {
-                double r = a.rr[m];
-                double ker = (s == 0.0) ? r : sin(s * r) / s;
-                double2 B = a.B[m];
-                hr = fma(B.x, ker, hr);
-                hi = fma(B.y, ker, hi);
+            int pnl = min((int)(s / a.hpan), a.hnpan - 1);
+            double x = (s - (pnl + 0.5) * a.hpan) * (2.0 / a.hpan);
+            const double2 *cc = a.hcheb + (size_t)pnl * (a.hdeg + 1);
+            double b1r = 0.0, b1i = 0.0, b2r = 0.0, b2i = 0.0;
+            for (int kk = a.hdeg; kk >= 1; --kk) {
+                double2 ck = cc[kk];
+                double tr = fma(2.0 * x, b1r, ck.x - b2r);
+                double ti = fma(2.0 * x, b1i, ck.y - b2i);
+                b2r = b1r;
+                b2i = b1i;
+                b1r = tr;
+                b1i = ti;
             }
+            double hr = fma(x, b1r, cc[0].x - b2r);
+            double hi = fma(x, b1i, cc[0].y - b2i);
             Cj = make_double2(hr / D + T1.x - T2.x, hi / D + T1.y - T2.y);
         } else {
             int jx = freq_of(col, a.M1);
