@@ -189,7 +189,8 @@ def run_gpu(args):
     gf.set_phase_timing(True)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    x_np = W.targets_3d(N_TARGETS, seed=rank)
+    n_targets = args.targets
+    x_np = W.targets_3d(n_targets, seed=rank)
     x = torch.from_numpy(x_np).to(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -200,7 +201,7 @@ def run_gpu(args):
 
     def run_path(precision: int, steps: int, warmup: int, tol: float):
         cdt = torch.complex128 if precision == gf.GF_FP64 else torch.complex64
-        out = torch.empty((N_TARGETS, 1), dtype=cdt, device=dev)
+        out = torch.empty((n_targets, 1), dtype=cdt, device=dev)
         kw = dict(precision=precision, series_tol=tol)
         for _ in range(warmup):
             p = gf.Plan(3, K_WAVE, ALPHA, GRID, **kw)
@@ -225,9 +226,14 @@ def run_gpu(args):
         return out, times, phases, launches
 
     tol64 = 1e-16
+    if args.paths == "split":
+        run_path(gf.GF_FP32_SPLIT, args.steps, args.warmup, 1e-8)
+        return 0
     with ClockSampler(local) as clk:
         out64, t64, ph64, launches = run_path(gf.GF_FP64, args.steps, args.warmup, tol64)
     clocks = clk.summary()
+    if args.paths == "fp64":
+        return 0
     out32, t32, ph32, _ = run_path(gf.GF_FP32_SPLIT, args.steps, args.warmup, 1e-8)
 
     ms64 = float(np.mean(t64))
@@ -236,13 +242,13 @@ def run_gpu(args):
         tt = torch.tensor([ms64, ms32], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ms64, ms32 = float(tt[0]), float(tt[1])
-    value = world * N_TARGETS / (ms64 * 1e-3)
+    value = world * n_targets / (ms64 * 1e-3)
 
     # e2e through the host-buffer entry point (pinned buffers, copies inside the timed region)
     x_pin = torch.from_numpy(x_np).pin_memory()
-    o_pin = torch.empty((N_TARGETS, 1), dtype=torch.complex128).pin_memory()
+    o_pin = torch.empty((n_targets, 1), dtype=torch.complex128).pin_memory()
     e2e_t = []
-    for i in range(args.warmup + args.steps):
+    for i in range(0 if args.no_e2e else args.warmup + args.steps):
         flush.zero_()
         barrier()
         t0 = time.perf_counter()
@@ -253,7 +259,7 @@ def run_gpu(args):
         p.close()
         if i >= args.warmup:
             e2e_t.append(dt)
-    e2e_s = float(np.mean(e2e_t))
+    e2e_s = float(np.mean(e2e_t)) if e2e_t else float("nan")
     if world > 1:
         tt = torch.tensor([e2e_s], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -285,11 +291,11 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms64, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "global_batch": world * N_TARGETS, "precision": "fp64 (complex128)",
+        "config": {"workload": WORKLOAD, "global_batch": world * n_targets, "precision": "fp64 (complex128)",
                    "series_tol": tol64, "parallelism": f"replicas{world}", "l2": "flushed (256 MiB write) between steps"},
         "phases_ms": {"synthesis": synth_ms, "near": near_ms, "far": far_ms,
                       "far_series_terms": terms},
-        "split": {"value": world * N_TARGETS / (ms32 * 1e-3), "ms_per_step": ms32, "dtype": "f32/f64 split",
+        "split": {"value": world * n_targets / (ms32 * 1e-3), "ms_per_step": ms32, "dtype": "f32/f64 split",
                   "series_tol": 1e-8, "max_err_vs_fp64_normwise": split_err,
                   "phases_ms": {"synthesis": float(np.mean([p[0] for p in ph32])),
                                 "near": float(np.mean([p[2] for p in ph32])),
@@ -298,8 +304,8 @@ def run_gpu(args):
                      "unit": "TFLOP/s", "frac": achieved / peak_fp64, "traffic": None,
                      "note": "FP64 pipe; achieved counts 18 algorithmic FP64 flops per series term (exp not "
                              "counted); peak = nominal GB300 FP64 (no measured FP64 peak available)"},
-        "e2e": {"value": world * N_TARGETS / e2e_s, "unit": "evals/s",
-                "h2d_bytes_per_step": int(x_np.nbytes), "d2h_bytes_per_step": int(N_TARGETS * 16)},
+        "e2e": {"value": world * n_targets / e2e_s, "unit": "evals/s",
+                "h2d_bytes_per_step": int(x_np.nbytes), "d2h_bytes_per_step": int(n_targets * 16)},
         "gpu_launches": launches,
         "clocks": clocks,
         "cpu_baseline": cpu,
@@ -319,6 +325,11 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=20000)
     ap.add_argument("--ref-sample", type=int, default=5000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--targets", type=int, default=N_TARGETS,
+                    help="targets per step (the benchmark workload is 1e6; smaller only for profiling captures)")
+    ap.add_argument("--paths", default="both", choices=["both", "fp64", "split"],
+                    help="which precision paths to run (profiling captures run one)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
