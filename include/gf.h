@@ -142,6 +142,31 @@ gf_status gf_eval_points(gf_plan_t plan, const double *dev_xyz, int64_t n, int w
 gf_status gf_eval_points_host(gf_plan_t plan, const double *host_xyz, int64_t n, int which,
                               void *host_out, void *cuda_stream);
 
+/* Allocation-free variant of gf_eval_points.  The paper has no counterpart:
+ * this entry point exists for callers that must not allocate device memory
+ * while they evaluate, for example a solver that reserved all free device
+ * memory for its own pool at start-up, or a latency-critical loop in which a
+ * cudaMalloc/cudaFree (which can synchronise the whole device) is not
+ * acceptable.  gf_eval_points grows a per-plan scratch list with cudaMalloc
+ * when a call brings more targets than before; this function instead uses one
+ * fixed scratch array compiled into the library (about 2 MiB: room for
+ * GF_NOALLOC_MAX_TARGETS targets), which every GPU that loads the library
+ * holds until the process exits.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *   Arguments, layout and results are those of gf_eval_points; n must be
+ *   <= GF_NOALLOC_MAX_TARGETS, otherwise GF_ERR_ARG is returned and nothing is
+ *   launched.  The plan itself must already exist (gf_plan allocates).
+ *   The first call on each device looks up the device address of the scratch
+ *   array (cudaGetSymbolAddress) with that device current; make that first
+ *   call before any stream capture.
+ *   All calls share the one scratch array: each call resets its counters on
+ *   cuda_stream before use, and calls whose work overlaps on the GPU (other
+ *   streams, other threads) race on it and give wrong results; serialise them.
+ * Errors: GF_ERR_ARG, GF_ERR_CUDA, GF_ERR_UNSUPPORTED (device ordinal >= 64). */
+#define GF_NOALLOC_MAX_TARGETS (1 << 18)
+gf_status gf_eval_points_noalloc(gf_plan_t plan, const double *dev_xyz, int64_t n, int which,
+                                 void *dev_out, void *cuda_stream);
+
 /* Plan facts (host memory).  Returns GF_ERR_ARG on NULL arguments. */
 typedef struct {
     int dim, M[3], nfields, precision, kind;

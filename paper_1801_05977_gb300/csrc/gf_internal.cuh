@@ -161,3 +161,5 @@ cudaError_t gf_launch_beta_table(const EvalArgs &a, int precision, cudaStream_t 
 cudaError_t gf_launch_eval(const EvalArgs &a, int precision, cudaStream_t s, cudaEvent_t ev_mid);
 
 void gf_count_launch(int n);
+gf_status gf_plan_eval_args(gf_plan_t p, const double *dev_xyz, int64_t n, int which, void *dev_out, EvalArgs *a);
+gf_status gf_set_error(gf_status s, const char *msg);

@@ -564,6 +564,60 @@ gf_status gf_eval_points(gf_plan_t p, const double *dev_xyz, int64_t n, int whic
     return GF_OK;
 }
 
+}  // extern "C"
+
+// Validation and argument set-up of one evaluation, without scratch pointers:
+// used by the allocation-free entry point (noalloc.cu).
+gf_status gf_plan_eval_args(gf_plan_t p, const double *dev_xyz, int64_t n, int which, void *dev_out,
+                            EvalArgs *a_out)
+{
+    if (!p || !a_out) return fail(GF_ERR_ARG, "gf_eval_points_noalloc: NULL plan");
+    if (n < 0) return fail(GF_ERR_ARG, "gf_eval_points_noalloc: n < 0");
+    if (n > 0 && (!dev_xyz || !dev_out)) return fail(GF_ERR_ARG, "gf_eval_points_noalloc: NULL buffer");
+    bool ok = (p->dim == 2 && which == GF_OUT_G) || (p->dim == 3 && p->kind == GF_HELMHOLTZ && which == GF_OUT_GD) ||
+              (p->kind == GF_MAXWELL && (which == GF_OUT_MAXWELL6 || which == GF_OUT_MAXWELL7));
+    if (!ok) return fail(GF_ERR_ARG, "gf_eval_points_noalloc: output kind %d does not match the plan", which);
+    EvalArgs a{};
+    a.dim = p->dim;
+    a.M1 = p->M[0];
+    a.M2 = p->M[1];
+    a.M3 = p->M[2];
+    a.P1 = p->P1;
+    a.P2 = p->P2;
+    a.P3 = p->P3;
+    a.nf = p->nf;
+    a.which = which;
+    a.k = p->k;
+    a.a1 = p->alpha[0];
+    a.a2 = p->alpha[1];
+    a.c = p->tr.c;
+    a.ct = p->tr.c_tilde;
+    a.eps = p->tr.eps;
+    a.h1 = 2.0 * GF_PI / p->M[0];
+    a.h2 = p->dim == 3 ? 2.0 * GF_PI / p->M[1] : 2.0 * p->tr.c_tilde / p->M[1];
+    a.h3 = p->dim == 3 ? 2.0 * p->tr.c_tilde / p->M[2] : 1.0;
+    a.T = p->T;
+    a.grid = p->grid;
+    a.x = dev_xyz;
+    a.out = dev_out;
+    a.n = n;
+    a.btab = p->btab;
+    a.n1lo = p->n1lo;
+    a.n1hi = p->n1hi;
+    a.n2lo = p->n2lo;
+    a.n2hi = p->n2hi;
+    a.prop = p->prop;
+    a.nprop = p->nprop;
+    a.exptab = p->exptab;
+    a.exptab_n = p->exptab_n;
+    *a_out = a;
+    return GF_OK;
+}
+
+gf_status gf_set_error(gf_status s, const char *msg) { return fail(s, "%s", msg); }
+
+extern "C" {
+
 gf_status gf_set_phase_timing(int on)
 {
     g_timing.store(on ? 1 : 0);

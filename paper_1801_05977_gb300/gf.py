@@ -44,7 +44,9 @@ class PlanInfo(ctypes.Structure):
 
 EXPORTS = ["gf_trunc_default", "gf_plan", "gf_eval_grid", "gf_grid_bytes", "gf_eval_points",
            "gf_eval_points_host", "gf_plan_get_info", "gf_destroy", "gf_status_string", "gf_last_error",
-           "gf_launch_count", "gf_set_phase_timing", "gf_plan_phase_ms"]
+           "gf_launch_count", "gf_set_phase_timing", "gf_plan_phase_ms", "gf_eval_points_noalloc"]
+
+NOALLOC_MAX_TARGETS = 1 << 18
 
 _lib = None
 
@@ -72,6 +74,7 @@ def lib(build_if_missing: bool = True):
     L.gf_grid_bytes.restype = sz
     L.gf_eval_points.argtypes = [vp, vp, i64, i32, vp, vp]
     L.gf_eval_points_host.argtypes = [vp, vp, i64, i32, vp, vp]
+    L.gf_eval_points_noalloc.argtypes = [vp, vp, i64, i32, vp, vp]
     L.gf_plan_get_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
     L.gf_destroy.argtypes = [vp]
     L.gf_status_string.argtypes = [i32]
@@ -81,6 +84,7 @@ def lib(build_if_missing: bool = True):
     L.gf_set_phase_timing.argtypes = [i32]
     L.gf_plan_phase_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
     for name in ("gf_trunc_default", "gf_plan", "gf_eval_grid", "gf_eval_points", "gf_eval_points_host",
+                 "gf_eval_points_noalloc",
                  "gf_plan_get_info", "gf_destroy", "gf_set_phase_timing", "gf_plan_phase_ms"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
@@ -160,6 +164,13 @@ class Plan:
         n = x.shape[0]
         _check(lib().gf_eval_points(self._h, ctypes.c_void_p(x.data_ptr()), n, int(which),
                                     ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        return out
+
+    def eval_points_noalloc_into(self, x, out, which: int, stream=None):
+        """gf_eval_points_noalloc: same result, fixed library scratch, no allocation."""
+        n = x.shape[0]
+        _check(lib().gf_eval_points_noalloc(self._h, ctypes.c_void_p(x.data_ptr()), n, int(which),
+                                            ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
         return out
 
     def eval_points(self, x, which: int, stream=None):
