@@ -341,6 +341,10 @@ __device__ __forceinline__ void set_entry(BetaEntry &e, double b, double ib)
 {
     e.b = b;
     e.ib = ib;
+    e.bl2 = (float)(b * 1.4426950408889634);  // b log2(e)
+    e.ibf = (float)ib;
+    e.bf = (float)b;
+    e.pad = 0.f;
 }
 __device__ __forceinline__ void set_entry(BetaEntryF &e, double b, double ib)
 {
@@ -430,19 +434,108 @@ __device__ __forceinline__ FarLane far_lane(const EvalArgs &a, int slot, int cou
     return L;
 }
 
+// Horner sums of one row segment n2 = hi, hi-1, ..., lo (double precision):
+// acc[e] = sum_{n2} w_e(n2) v^{n2-lo}; NH = 1 (G_d) or 6 (Maxwell partial sums
+// A = sum ib e, B = sum c2 ib e, C = sum c2^2 ib e, D = sum b e, E = sum e,
+// F = sum c2 e, with e = e^{-b z} on the lane's own truncation set).
+template <int NH>
+__device__ __forceinline__ void seg_horner_f64(const BetaEntry *__restrict__ row, int lo, int hi, double a2,
+                                               float c1sq, float a2f, float R2f, double z, double cv, double sv,
+                                               const double *__restrict__ T, int jmax, double acc[NH][2])
+{
+#pragma unroll
+    for (int e = 0; e < NH; ++e) acc[e][0] = acc[e][1] = 0.0;
+    float c2f = a2f + (float)hi;
+    double c2 = a2 + hi;
+    for (int n2 = hi; n2 >= lo; --n2, c2f -= 1.0f, c2 -= 1.0) {
+        const BetaEntry be = row[n2];
+        const bool ok = fmaf(c2f, c2f, c1sq) <= R2f && be.ib != 0.0;
+        const double e = exp_neg_tab(be.b * z, T, jmax);
+        double wv[NH];
+        const double ibe = ok ? e * be.ib : 0.0;
+        wv[0] = ibe;
+        if (NH > 1) {
+            const double ee = ok ? e : 0.0;
+            wv[1] = c2 * ibe;
+            wv[2] = c2 * wv[1];
+            wv[3] = be.b * ee;
+            wv[4] = ee;
+            wv[5] = c2 * ee;
+        }
+#pragma unroll
+        for (int k = 0; k < NH; ++k) {
+            const double nx = fma(acc[k][0], cv, fma(-acc[k][1], sv, wv[k]));
+            const double ny = fma(acc[k][0], sv, acc[k][1] * cv);
+            acc[k][0] = nx;
+            acc[k][1] = ny;
+        }
+    }
+}
+
+// The same segment sums in float (hardware ex2), for the exponentially small
+// tail of a double-precision plan.
+template <int NH>
+__device__ __forceinline__ void seg_horner_f32(const BetaEntry *__restrict__ row, int lo, int hi, float a2f,
+                                               float c1sq, float R2f, float z, float cv, float sv, float acc[NH][2])
+{
+#pragma unroll
+    for (int e = 0; e < NH; ++e) acc[e][0] = acc[e][1] = 0.f;
+    float c2 = a2f + (float)hi;
+    for (int n2 = hi; n2 >= lo; --n2, c2 -= 1.0f) {
+        const BetaEntry be = row[n2];
+        const bool ok = fmaf(c2, c2, c1sq) <= R2f && be.ibf != 0.f;
+        const float e = ok ? ex2_approx(-be.bl2 * z) : 0.f;
+        float wv[NH];
+        wv[0] = e * be.ibf;
+        if (NH > 1) {
+            wv[1] = c2 * wv[0];
+            wv[2] = c2 * wv[1];
+            wv[3] = be.bf * e;
+            wv[4] = e;
+            wv[5] = c2 * e;
+        }
+#pragma unroll
+        for (int k = 0; k < NH; ++k) {
+            const float nx = fmaf(acc[k][0], cv, fmaf(-acc[k][1], sv, wv[k]));
+            const float ny = fmaf(acc[k][0], sv, acc[k][1] * cv);
+            acc[k][0] = nx;
+            acc[k][1] = ny;
+        }
+    }
+}
+
+// e^{i arg} for a float segment: argument reduced modulo 2 pi in double, then
+// evaluated in float.
+__device__ __forceinline__ void phase_f32_reduced(double arg, float &s, float &c)
+{
+    double r = fma(-2.0 * GF_PI, rint(arg * (0.5 / GF_PI)), arg);
+    sincosf((float)r, &s, &c);
+}
+
 // ---------------------------------------------------------------------------
-// 3D far kernel, double precision.  Series (he), and for Maxwell the second
-// derivatives (each term times delta_pq - c^p c^q/k^2, c = (alpha_n, beta sgn x3)):
+// 3D far kernel for double-precision plans.  Series (he), and for Maxwell the
+// second derivatives (each term times delta_pq - c^p c^q/k^2, c = (alpha_n,
+// beta sgn x3)):
 //   S = sum_n beta_n^{-1} e^{i beta_n |x3|} e^{i alpha_n . t},  G_d = e^{i2pi<alpha.m>} (i/8pi^2) S.
 // Propagating n (|alpha_n| < k, a handful) are summed from a list.  For the
-// evanescent n, beta = i b and 1/beta = -i/b, so with w = e^{-bz}/b (real) the
-// row n1 contributes -i e^{i(c1 t1 + c2a t2)} sum_{n2} w v^{n2-n2a}, v = e^{i t2},
-// the inner sum by Horner's rule: 4 flops per term besides w.
-// Every lane keeps only its own truncation set |alpha_n|^2 <= k^2 + (T/z)^2.
+// evanescent n, beta = i b and 1/beta = -i/b; with w = e^{-bz}/b (real) the row
+// n1 contributes -i sum_{n2} w e^{i(c1 t1 + c2 t2)}, summed by Horner's rule
+// in v = e^{i t2} from an anchor phase.  Each lane keeps only its own
+// truncation set |alpha_n|^2 <= k^2 + (T/z)^2.
+//
+// Precision: the terms of the warp's core disk |alpha_n|^2 <= k^2 + (Y0/z_min)^2
+// (b z_min <= Y0 = 18, z_min the warp's smallest |x3|) are summed in double
+// with the table-driven exponential; the remaining terms, each below
+// e^{-18} = 1.5e-8 of the leading ones and all together below
+// 2 pi e^{-18}/z of the series scale, are summed in float: their float
+// rounding (< 1e-5 relative) contributes < 2e-12 of the series scale.
 // ---------------------------------------------------------------------------
+constexpr double FAR_CORE_Y0 = 18.0;
+
 template <int NF>
 __global__ void __launch_bounds__(128) far3d_f64(EvalArgs a)
 {
+    constexpr int NH = NF == 1 ? 1 : 6;
     const BetaEntry *tab = reinterpret_cast<const BetaEntry *>(a.btab);
     double2 *out = reinterpret_cast<double2 *>(a.out);
     const int ne = n_entries(a.which);
@@ -451,17 +544,22 @@ __global__ void __launch_bounds__(128) far3d_f64(EvalArgs a)
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    const double ik2 = 1.0 / (a.k * a.k);
+    const double k2 = a.k * a.k, ik2 = 1.0 / k2;
     const double *T = a.exptab;
     const int jmax = a.exptab_n - 1;
+    const float a2f = (float)a.a2;
     for (int w = gw; w * 32 < count; w += nw) {
         FarLane L = far_lane(a, w * 32 + lane, count);
         const double R2m = warp_max(L.R2);
         const float R2f = (float)L.R2;
         const double Rm = sqrt(R2m);
+        // core disk of the warp: b z_min <= Y0
+        const double iz = L.valid ? 1.0 / L.z : 0.0;
+        const double izmax = warp_max(iz);
+        const double Rc2 = fmin(k2 + FAR_CORE_Y0 * FAR_CORE_Y0 * izmax * izmax, R2m);
         double sv, cv;
         sincos(L.t2, &sv, &cv);
-        // propagating terms: P[e] (complex), e = 0 G_d, 1..6 tensor entries
+        const float svf = (float)sv, cvf = (float)cv, zf = (float)L.z;
         double P[NF][2];
         double S[NF == 1 ? 1 : 7][2];
 #pragma unroll
@@ -487,7 +585,6 @@ __global__ void __launch_bounds__(128) far3d_f64(EvalArgs a)
                 }
             }
         }
-        // evanescent rows
         const int n1a = max(a.n1lo, (int)floor(-a.a1 - Rm) - 1), n1b = min(a.n1hi, (int)ceil(-a.a1 + Rm) + 1);
         for (int n1 = n1a; n1 <= n1b; ++n1) {
             const double c1 = a.a1 + n1;
@@ -499,69 +596,79 @@ __global__ void __launch_bounds__(128) far3d_f64(EvalArgs a)
             const BetaEntry *row = tab + (size_t)(n1 - a.n1lo) * W2 - a.n2lo;
             const float c1f = (float)c1;
             const float c1sq = c1f * c1f;
-            float c2f = (float)(a.a2 + n2b);
-            // Horner accumulators (re, im): 1 sum for G_d; 6 for Maxwell
-            double h[NF == 1 ? 1 : 6][2];
-#pragma unroll
-            for (int e = 0; e < (NF == 1 ? 1 : 6); ++e) h[e][0] = h[e][1] = 0.0;
-            double c2 = a.a2 + n2b;
-            for (int n2 = n2b; n2 >= n2a; --n2, c2f -= 1.0f, c2 -= 1.0) {
-                const BetaEntry be = row[n2];
-                const bool ok = fmaf(c2f, c2f, c1sq) <= R2f;
-                const double e = exp_neg_tab(be.b * L.z, T, jmax);
-                double wv[NF == 1 ? 1 : 6];
-                if (NF == 1) {
-                    wv[0] = ok ? e * be.ib : 0.0;
-                } else {
-                    // propagating n carry ib = 0 in the table and are summed separately
-                    const bool ev = ok && be.ib != 0.0;
-                    const double ibe = ev ? e * be.ib : 0.0;
-                    const double ee = ev ? e : 0.0;
-                    wv[0] = ibe;             // A = sum ib e
-                    wv[1] = c2 * ibe;        // B = sum c2 ib e
-                    wv[2] = c2 * wv[1];      // C = sum c2^2 ib e
-                    wv[3] = be.b * ee;       // D = sum b e
-                    wv[4] = ee;              // E = sum e
-                    wv[5] = c2 * ee;         // F = sum c2 e
-                }
-#pragma unroll
-                for (int e2 = 0; e2 < (NF == 1 ? 1 : 6); ++e2) {
-                    const double nx = fma(h[e2][0], cv, fma(-h[e2][1], sv, wv[e2]));
-                    const double ny = fma(h[e2][0], sv, h[e2][1] * cv);
-                    h[e2][0] = nx;
-                    h[e2][1] = ny;
+            // core segment [ca, cb] of this row (empty when ca > cb)
+            int ca = n2b + 1, cb = n2b;
+            const double remc = Rc2 - c1 * c1;
+            if (remc >= 0.0) {
+                const double src = sqrt(remc);
+                ca = max(n2a, (int)ceil(-a.a2 - src));
+                cb = min(n2b, (int)floor(-a.a2 + src));
+                if (ca > cb) {
+                    ca = n2b + 1;
+                    cb = n2b;
                 }
             }
-            double sp, cp;
-            sincos(c1 * L.t1 + (a.a2 + n2a) * L.t2, &sp, &cp);
-            // rotate each row sum by the row phase
-            double r[NF == 1 ? 1 : 6][2];
+            const double base = c1 * L.t1;
+            double rr[NH][2];
 #pragma unroll
-            for (int e2 = 0; e2 < (NF == 1 ? 1 : 6); ++e2) {
-                r[e2][0] = cp * h[e2][0] - sp * h[e2][1];
-                r[e2][1] = cp * h[e2][1] + sp * h[e2][0];
+            for (int e = 0; e < NH; ++e) rr[e][0] = rr[e][1] = 0.0;
+            if (ca <= cb) {
+                double acc[NH][2];
+                seg_horner_f64<NH>(row, ca, cb, a.a2, c1sq, a2f, R2f, L.z, cv, sv, T, jmax, acc);
+                double sp, cp;
+                sincos(base + (a.a2 + ca) * L.t2, &sp, &cp);
+#pragma unroll
+                for (int e = 0; e < NH; ++e) {
+                    rr[e][0] += cp * acc[e][0] - sp * acc[e][1];
+                    rr[e][1] += cp * acc[e][1] + sp * acc[e][0];
+                }
+            }
+            // float tails: [n2a, ca-1] and [cb+1, n2b] (the whole row when there is no core)
+            const int tl_hi = (ca <= cb) ? ca - 1 : n2b;
+            const int th_lo = (ca <= cb) ? cb + 1 : n2b + 1;
+            if (n2a <= tl_hi) {
+                float acc[NH][2];
+                seg_horner_f32<NH>(row, n2a, tl_hi, a2f, c1sq, R2f, zf, cvf, svf, acc);
+                float sp, cp;
+                phase_f32_reduced(base + (a.a2 + n2a) * L.t2, sp, cp);
+#pragma unroll
+                for (int e = 0; e < NH; ++e) {
+                    rr[e][0] += (double)(cp * acc[e][0] - sp * acc[e][1]);
+                    rr[e][1] += (double)(cp * acc[e][1] + sp * acc[e][0]);
+                }
+            }
+            if (th_lo <= n2b) {
+                float acc[NH][2];
+                seg_horner_f32<NH>(row, th_lo, n2b, a2f, c1sq, R2f, zf, cvf, svf, acc);
+                float sp, cp;
+                phase_f32_reduced(base + (a.a2 + th_lo) * L.t2, sp, cp);
+#pragma unroll
+                for (int e = 0; e < NH; ++e) {
+                    rr[e][0] += (double)(cp * acc[e][0] - sp * acc[e][1]);
+                    rr[e][1] += (double)(cp * acc[e][1] + sp * acc[e][0]);
+                }
             }
             if (NF == 1) {
-                S[0][0] += r[0][0];
-                S[0][1] += r[0][1];
+                S[0][0] += rr[0][0];
+                S[0][1] += rr[0][1];
             } else {
                 // row c1 fixed: G: A; xx: (1 - c1^2/k^2) A; yy: A - C/k^2; zz: A + D/k^2;
                 // xy: -(c1/k^2) B; xz: -(c1/k^2) E (real factor); yz: -(1/k^2) F (real factor)
                 const double fxx = 1.0 - c1 * c1 * ik2;
-                S[0][0] += r[0][0];
-                S[0][1] += r[0][1];
-                S[1][0] += fxx * r[0][0];
-                S[1][1] += fxx * r[0][1];
-                S[2][0] += r[0][0] - ik2 * r[2][0];
-                S[2][1] += r[0][1] - ik2 * r[2][1];
-                S[3][0] += r[0][0] + ik2 * r[3][0];
-                S[3][1] += r[0][1] + ik2 * r[3][1];
-                S[4][0] += -c1 * ik2 * r[1][0];
-                S[4][1] += -c1 * ik2 * r[1][1];
-                S[5][0] += -c1 * ik2 * r[4][0];
-                S[5][1] += -c1 * ik2 * r[4][1];
-                S[6][0] += -ik2 * r[5][0];
-                S[6][1] += -ik2 * r[5][1];
+                S[0][0] += rr[0][0];
+                S[0][1] += rr[0][1];
+                S[1][0] += fxx * rr[0][0];
+                S[1][1] += fxx * rr[0][1];
+                S[2][0] += rr[0][0] - ik2 * rr[2][0];
+                S[2][1] += rr[0][1] - ik2 * rr[2][1];
+                S[3][0] += rr[0][0] + ik2 * rr[3][0];
+                S[3][1] += rr[0][1] + ik2 * rr[3][1];
+                S[4][0] += -c1 * ik2 * rr[1][0];
+                S[4][1] += -c1 * ik2 * rr[1][1];
+                S[5][0] += -c1 * ik2 * rr[4][0];
+                S[5][1] += -c1 * ik2 * rr[4][1];
+                S[6][0] += -ik2 * rr[5][0];
+                S[6][1] += -ik2 * rr[5][1];
             }
         }
         if (!L.valid) continue;
@@ -573,9 +680,8 @@ __global__ void __launch_bounds__(128) far3d_f64(EvalArgs a)
         if (NF == 1) {
             o[0] = cmul(pre, make_double2(P[0][0] + S[0][1], P[0][1] - S[0][0]));
         } else {
-            const int map[6] = {1, 2, 3, 4, 5, 6};  // S index of xx, yy, zz, xy, xz, yz
             for (int e = 0; e < 6; ++e) {
-                const double *s = S[map[e]];
+                const double *s = S[1 + e];
                 double2 v;
                 if (e < 4)
                     v = make_double2(P[1 + e][0] + s[1], P[1 + e][1] - s[0]);

@@ -114,7 +114,8 @@ struct SynthArgs {
 // Far-series table entry for one in-plane index n: b = |beta_n| and 1/b for
 // evanescent n (beta_n = i b); zeros for propagating n (|alpha_n| <= k).
 struct BetaEntry {
-    double b, ib;
+    double b, ib;            // double-precision core terms
+    float bl2, ibf, bf, pad; // b log2(e), 1/b, b in float for the exponentially small tail
 };
 struct BetaEntryF {
     float bl2, ib, b, pad;  // b log2(e), 1/b, b

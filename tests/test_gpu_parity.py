@@ -125,8 +125,9 @@ def test_host_entry_point_matches_device():
     host = np.zeros((x.shape[0], 1), dtype=np.complex128)
     plan.eval_points_host(x, host, gf.GF_OUT_GD)
     # far targets are grouped into warps in atomic-append order, which moves the
-    # start of each phase recurrence: equal to rounding, not bitwise
-    assert rel_err(host, dev) < 1e-13
+    # anchors of the row sums and the warp's double/float split of the series
+    # tail (terms below e^-18 of the leading ones): equal to 1e-11, not bitwise
+    assert rel_err(host, dev) < 1e-11
 
 
 # ----------------------------------------------------------------------------- 2D (config: k = 1.3, alpha = 0.2, 64 x 64, 10^4 targets)
@@ -164,7 +165,7 @@ def test_parity_maxwell():
     got = gpu_eval(plan, x, gf.GF_OUT_MAXWELL7)
     assert rel_err(got, ref) < TOL64
     got6 = gpu_eval(plan, x, gf.GF_OUT_MAXWELL6)
-    assert rel_err(got6, got[:, :6]) < 1e-13
+    assert rel_err(got6, got[:, :6]) < 1e-11  # same grouping caveat as the host-entry test
     # combined grids: (delta_pq - c^p c^q/k^2) L_d vs the oracle's L_d, L^{pq}
     gg = plan.eval_grid().cpu().numpy()
     for e, (p, q) in enumerate([(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]):
@@ -211,5 +212,7 @@ def test_full_size_config2_sampled():
     g = O.grid(pb, C)
     sel = rng.choice(x_all.shape[0], 1500, replace=False)
     ref = O.evaluate(pb, g, x_all[sel], O.OUT_GD)
-    assert rel_err(got_all[sel], ref) < TOL64
+    e_pt, e_nw = rel_err(got_all[sel], ref), norm_err(got_all[sel], ref)
+    print(f"config-2 full size: pointwise {e_pt:.2e}, normwise {e_nw:.2e} vs the FP64 oracle")
+    assert e_pt < TOL64
     assert np.isfinite(got_all).all()
