@@ -287,6 +287,7 @@ def run_gpu(args):
     d = (out32.to(torch.complex128) - out64).abs()
     split_err = float(d.max() / out64.abs().max())
 
+    batched = None if args.no_batch else run_batched(args, dev, flush)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -317,6 +318,7 @@ def run_gpu(args):
                              "from unit counts and clock (152 SMs x 2 FP64 lanes x 2 flop x 2.07 GHz; FMA probe 1.21)"},
         "e2e": {"value": world * n_targets / e2e_s, "unit": "evals/s",
                 "h2d_bytes_per_step": int(x_np.nbytes), "d2h_bytes_per_step": int(n_targets * 16)},
+        "batched": batched,
         "gpu_launches": launches,
         "clocks": clocks,
         "cpu_baseline": cpu,
@@ -325,6 +327,71 @@ def run_gpu(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def run_batched(args, dev, flush):
+    """Batched sweep: 256 (alpha, k) pairs, k ~ U[0.5, 5], alpha ~ U[-1/2, 1/2]^2
+    (Wood gap 1e-3), grid per pair clamp(nextpow2(ceil(32 k)), 32, 256)^2 x 64,
+    1e5 targets per pair, split precision.  Timed: the whole sweep (synthesis of
+    every pair + evaluation of every target) as one CUDA graph, against the
+    plain path called pair after pair (gf_plan + gf_eval_points)."""
+    import torch
+
+    from paper_1801_05977_gb300 import gf
+
+    npairs, per = args.batch_pairs, args.batch_targets
+    pr = W.sweep_pairs(npairs, seed=0)
+    k = pr[:, 2].copy()
+    al = pr[:, :2].copy()
+    m = np.clip(2 ** np.ceil(np.log2(np.ceil(32 * k))), 32, 256).astype(np.int32)
+    M = np.stack([m, m, np.full(npairs, 64, np.int32)], axis=1)
+    xs = [W.targets_3d(per, seed=1000 + i) for i in range(npairs)]
+    off = np.arange(npairs + 1, dtype=np.int64) * per
+    x = torch.from_numpy(np.concatenate(xs)).to(dev)
+    out = torch.empty((npairs * per, 1), dtype=torch.complex64, device=dev)
+    t0 = time.perf_counter()
+    batch = gf.Batch(k, al, M, precision=gf.GF_FP32_SPLIT)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    tune = batch.autotune(x, off, out, gf.GF_OUT_GD)
+    s = torch.cuda.Stream(device=dev)
+    times = []
+    l0 = gf.launch_count()
+    with torch.cuda.stream(s):
+        for i in range(args.warmup + args.steps):
+            flush.zero_()
+            s.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            batch.run_graph(x, off, out, gf.GF_OUT_GD, stream=s)
+            e1.record(s)
+            s.synchronize()
+            if i >= args.warmup:
+                times.append(e0.elapsed_time(e1))
+    graph_launches = (gf.launch_count() - l0) / (args.warmup + args.steps)
+    ms_b = float(np.mean(times))
+    # plain path, pair after pair (one pass)
+    ref = torch.empty_like(out)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(npairs):
+        p = gf.Plan(3, float(k[i]), tuple(al[i]), tuple(int(v) for v in M[i]), precision=gf.GF_FP32_SPLIT)
+        p.eval_points_into(x[off[i]:off[i + 1]], ref[off[i]:off[i + 1]], gf.GF_OUT_GD)
+        torch.cuda.synchronize()
+        p.close()
+    t_seq = time.perf_counter() - t0
+    d = (out - ref).abs().max().item() / ref.abs().max().item()
+    batch.close()
+    total = npairs * per
+    return {"value": total / (ms_b * 1e-3), "unit": "evals/s", "ms_per_step": ms_b, "pairs": npairs,
+            "targets_per_pair": per, "grid_points_per_pair": "clamp(nextpow2(ceil(32k)),32,256)^2 x 64",
+            "precision": "f32/f64 split", "launch": "one CUDA graph: 3 synthesis + memset + 3 eval kernels",
+            "graph_kernels_per_step": graph_launches, "tuning": {"tj_max": tune[0], "far_block": tune[1],
+                                                                  "far_ctas_per_sm": tune[2]},
+            "sequential_plain": {"value": total / t_seq, "s_per_sweep": t_seq,
+                                 "how": "gf_plan + gf_eval_points pair after pair, wall clock"},
+            "speedup_vs_sequential": (total / (ms_b * 1e-3)) / (total / t_seq),
+            "setup_s": t_setup, "max_err_vs_sequential_normwise": d}
 
 
 def main():
@@ -341,6 +408,9 @@ def main():
     ap.add_argument("--paths", default="both", choices=["both", "fp64", "split"],
                     help="which precision paths to run (profiling captures run one)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling captures)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-sweep leg")
+    ap.add_argument("--batch-pairs", type=int, default=256)
+    ap.add_argument("--batch-targets", type=int, default=100_000)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -167,6 +167,60 @@ gf_status gf_eval_points_host(gf_plan_t plan, const double *host_xyz, int64_t n,
 gf_status gf_eval_points_noalloc(gf_plan_t plan, const double *dev_xyz, int64_t n, int which,
                                  void *dev_out, void *cuda_stream);
 
+/* ---------------------------------------------------------------------------
+ * Batched (alpha, k) sweeps.  Many plans with their own k, alpha and grid
+ * (Algorithms 1-3 applied pair by pair, as in a Bloch or frequency sweep) run
+ * as batched persistent launches over a (pair, block) work list: three
+ * launches re-synthesise every pair's grid, a counter reset and three
+ * launches evaluate every pair's targets.  3D plans only (Secs. 3-4).
+ * ------------------------------------------------------------------------- */
+typedef struct gf_batch_s *gf_batch_t;
+
+/* Build one plan per pair (as gf_plan; grids are synthesised once on
+ * cuda_stream) plus the batch's work arena and launch tables.
+ *   npairs  number of pairs, >= 1
+ *   k       [npairs] wave numbers;  alpha [npairs][2];  M [npairs][3]  (host memory)
+ *   trunc   shared parameters (precision, kind, ...), NULL for the defaults
+ * Errors: as gf_plan for any pair (the message names the pair), GF_ERR_NOMEM. */
+gf_status gf_plan_batch(int npairs, const double *k, const double *alpha, const int *M,
+                        const gf_trunc_t *trunc, void *cuda_stream, gf_batch_t *out);
+
+/* Re-run the synthesis (coefficients + inverse FFTs) of every pair: three
+ * batched persistent launches on cuda_stream. */
+gf_status gf_batch_synthesize(gf_batch_t batch, void *cuda_stream);
+
+/* Evaluate every pair at its own targets.  dev_xyz holds all targets,
+ * [offsets[npairs]][3] doubles, pair p owning rows offsets[p] .. offsets[p+1]-1;
+ * dev_out receives [offsets[npairs]][entries] complex values in the same rows.
+ * offsets is host memory (npairs + 1 entries, offsets[0] = 0, non-decreasing).
+ * The batch owns the scratch (grown synchronously when a call brings more
+ * targets than before); calls on one batch must not overlap in time. */
+gf_status gf_batch_eval_points(gf_batch_t batch, const double *dev_xyz, const int64_t *offsets, int which,
+                               void *dev_out, void *cuda_stream);
+
+/* Choose the launch shapes (first-pass columns per CTA; far-kernel block size
+ * and CTAs per SM) by timing candidates on this batch and these targets, then
+ * keep them for this batch and for later batches of the same shape in this
+ * process.  Synchronises the stream; overwrites dev_out. */
+gf_status gf_batch_autotune(gf_batch_t batch, const double *dev_xyz, const int64_t *offsets, int which,
+                            void *dev_out, void *cuda_stream);
+
+/* The chosen shapes: out[0] first-pass columns per CTA (cap), out[1] far-kernel
+ * block size, out[2] far-kernel 128-thread CTAs per SM. */
+gf_status gf_batch_get_tuning(gf_batch_t batch, int out[3]);
+
+/* Synthesis + evaluation of the whole sweep as one CUDA graph: captured on
+ * cuda_stream (which must not be the legacy default stream) at the first call
+ * for given (dev_xyz, offsets, which, dev_out), then replayed. */
+gf_status gf_batch_run_graph(gf_batch_t batch, const double *dev_xyz, const int64_t *offsets, int which,
+                             void *dev_out, void *cuda_stream);
+
+/* Borrow the plan of pair i (owned by the batch; do not destroy it). */
+gf_status gf_batch_get_plan(gf_batch_t batch, int i, gf_plan_t *out);
+
+/* Release the batch, its plans and graphs (synchronises the device).  NULL is accepted. */
+gf_status gf_batch_destroy(gf_batch_t batch);
+
 /* Plan facts (host memory).  Returns GF_ERR_ARG on NULL arguments. */
 typedef struct {
     int dim, M[3], nfields, precision, kind;

@@ -110,17 +110,13 @@ __device__ __forceinline__ int far_bucket(double z, double c)
 // R = storage/accumulation type of the grid (double: GF_FP64, float: split).
 // ---------------------------------------------------------------------------
 template <typename R, int NF>
-__global__ void __launch_bounds__(256) near3d(EvalArgs a)
+__device__ void near3d_tiles(const EvalArgs &a, int64_t base0, int64_t stride, int *hist)
 {
     typedef typename cplx_t<R>::T C;
-    __shared__ int hist[GF_FAR_BUCKETS];
-    for (int b = threadIdx.x; b < GF_FAR_BUCKETS; b += blockDim.x) hist[b] = 0;
-    __syncthreads();
     const C *G = reinterpret_cast<const C *>(a.grid);
     C *out = reinterpret_cast<C *>(a.out);
     const int ne = n_entries(a.which);
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < a.n; base += stride) {
+    for (int64_t base = base0; base < a.n; base += stride) {
         const int64_t i = base + threadIdx.x;
         bool valid = i < a.n;
         double x1 = 0, x2 = 0, x3 = 0;
@@ -235,9 +231,52 @@ __global__ void __launch_bounds__(256) near3d(EvalArgs a)
             }
         }
     }
+}
+
+template <typename R, int NF>
+__global__ void __launch_bounds__(256) near3d(EvalArgs a)
+{
+    __shared__ int hist[GF_FAR_BUCKETS];
+    for (int b = threadIdx.x; b < GF_FAR_BUCKETS; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    near3d_tiles<R, NF>(a, (int64_t)blockIdx.x * blockDim.x, (int64_t)gridDim.x * blockDim.x, hist);
     __syncthreads();
     for (int b = threadIdx.x; b < GF_FAR_BUCKETS; b += blockDim.x)
         if (hist[b]) atomicAdd(&a.far_count[1 + b], hist[b]);
+}
+
+// Batched near kernel: persistent CTAs walk the (pair, 256-target tile) list.
+__device__ __forceinline__ int batch_pair_e(const int *prefix, int np, int vb)
+{
+    int lo = 0, hi = np - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= vb)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename R, int NF>
+__global__ void __launch_bounds__(256) near3d_batch(const EvalArgs *args, const int *prefix, int np)
+{
+    __shared__ int hist[GF_FAR_BUCKETS];
+    __shared__ EvalArgs sa;
+    const int total = prefix[np];
+    for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
+        const int p = batch_pair_e(prefix, np, vb);
+        if (threadIdx.x == 0) sa = args[p];
+        for (int b = threadIdx.x; b < GF_FAR_BUCKETS; b += blockDim.x) hist[b] = 0;
+        __syncthreads();
+        const int64_t base = (int64_t)(vb - prefix[p]) * blockDim.x;
+        near3d_tiles<R, NF>(sa, base, sa.n + blockDim.x, hist);
+        __syncthreads();
+        for (int b = threadIdx.x; b < GF_FAR_BUCKETS; b += blockDim.x)
+            if (hist[b]) atomicAdd(&sa.far_count[1 + b], hist[b]);
+        __syncthreads();
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -310,9 +349,8 @@ __global__ void __launch_bounds__(256) near2d(EvalArgs a)
 // radius first (bucket NB-1 first), so that warps see homogeneous lanes and
 // the heaviest targets are scheduled first.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) far_scatter(EvalArgs a)
+__device__ void far_scatter_body(const EvalArgs &a, int blk, int nblk, int *off)
 {
-    __shared__ int off[GF_FAR_BUCKETS];
     if (threadIdx.x == 0) {
         int s = 0;
         for (int b = GF_FAR_BUCKETS - 1; b >= 0; --b) {
@@ -323,12 +361,31 @@ __global__ void __launch_bounds__(256) far_scatter(EvalArgs a)
     __syncthreads();
     const int count = a.far_count[0];
     int *cursor = a.far_count + 1 + GF_FAR_BUCKETS;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+    for (int i = blk * blockDim.x + threadIdx.x; i < count; i += nblk * blockDim.x) {
         int idx = a.far_idx[i];
         double z = fabs(a.x[3 * (size_t)idx + 2]);
         int b = far_bucket(z, a.c);
         int pos = off[b] + atomicAdd(&cursor[b], 1);
         a.far_sorted[pos] = idx;
+    }
+}
+
+__global__ void __launch_bounds__(256) far_scatter(EvalArgs a)
+{
+    __shared__ int off[GF_FAR_BUCKETS];
+    far_scatter_body(a, blockIdx.x, gridDim.x, off);
+}
+
+// batched: `per` CTAs per pair, persistent over the np * per work list
+__global__ void __launch_bounds__(256) far_scatter_batch(const EvalArgs *args, int np, int per)
+{
+    __shared__ int off[GF_FAR_BUCKETS];
+    __shared__ EvalArgs sa;
+    for (int vb = blockIdx.x; vb < np * per; vb += gridDim.x) {
+        if (threadIdx.x == 0) sa = args[vb / per];
+        __syncthreads();
+        far_scatter_body(sa, vb % per, per, off);
+        __syncthreads();
     }
 }
 
@@ -532,23 +589,21 @@ __device__ __forceinline__ void phase_f32_reduced(double arg, float &s, float &c
 // ---------------------------------------------------------------------------
 constexpr double FAR_CORE_Y0 = 18.0;
 
+// One warp, one chunk w of 32 consecutive entries of the sorted far list.
 template <int NF>
-__global__ void __launch_bounds__(128) far3d_f64(EvalArgs a)
+__device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count)
 {
     constexpr int NH = NF == 1 ? 1 : 6;
     const BetaEntry *tab = reinterpret_cast<const BetaEntry *>(a.btab);
     double2 *out = reinterpret_cast<double2 *>(a.out);
     const int ne = n_entries(a.which);
     const int W2 = a.n2hi - a.n2lo + 1;
-    const int count = a.far_count[0];
     const int lane = threadIdx.x & 31;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
     const double k2 = a.k * a.k, ik2 = 1.0 / k2;
     const double *T = a.exptab;
     const int jmax = a.exptab_n - 1;
     const float a2f = (float)a.a2;
-    for (int w = gw; w * 32 < count; w += nw) {
+    {
         FarLane L = far_lane(a, w * 32 + lane, count);
         const double R2m = warp_max(L.R2);
         const float R2f = (float)L.R2;
@@ -671,7 +726,7 @@ __global__ void __launch_bounds__(128) far3d_f64(EvalArgs a)
                 S[6][1] += -ik2 * rr[5][1];
             }
         }
-        if (!L.valid) continue;
+        if (!L.valid) return;
         const double2 lat = lattice_phase(a.a1, L.m1, a.a2, L.m2);
         const double2 pre = cmul(lat, make_double2(0.0, 1.0 / (8.0 * GF_PI * GF_PI)));
         double2 *o = out + (size_t)L.idx * ne;
@@ -694,24 +749,30 @@ __global__ void __launch_bounds__(128) far3d_f64(EvalArgs a)
     }
 }
 
+template <int NF>
+__global__ void __launch_bounds__(128) far3d_f64(EvalArgs a)
+{
+    const int count = a.far_count[0];
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int w = gw; w * 32 < count; w += nw) far3d_f64_chunk<NF>(a, w, count);
+}
+
 // ---------------------------------------------------------------------------
 // 3D far kernel, split precision: the same sums in float with the hardware
 // ex2; per-target reduction, lattice phase and the final scaling in double.
 // ---------------------------------------------------------------------------
 template <int NF>
-__global__ void __launch_bounds__(128) far3d_f32(EvalArgs a)
+__device__ void far3d_f32_chunk(const EvalArgs &a, int w, int count)
 {
     const BetaEntryF *tab = reinterpret_cast<const BetaEntryF *>(a.btab);
     float2 *out = reinterpret_cast<float2 *>(a.out);
     const int ne = n_entries(a.which);
     const int W2 = a.n2hi - a.n2lo + 1;
-    const int count = a.far_count[0];
     const int lane = threadIdx.x & 31;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
     const float ik2 = (float)(1.0 / (a.k * a.k));
     const float a2f = (float)a.a2;
-    for (int w = gw; w * 32 < count; w += nw) {
+    {
         FarLane L = far_lane(a, w * 32 + lane, count);
         const double R2m = warp_max(L.R2);
         const float R2f = (float)L.R2;
@@ -813,7 +874,7 @@ __global__ void __launch_bounds__(128) far3d_f32(EvalArgs a)
                 S[6][1] += -ik2 * r[5][1];
             }
         }
-        if (!L.valid) continue;
+        if (!L.valid) return;
         const double2 lat = lattice_phase(a.a1, L.m1, a.a2, L.m2);
         const double2 pre = cmul(lat, make_double2(0.0, 1.0 / (8.0 * GF_PI * GF_PI)));
         float2 *o = out + (size_t)L.idx * ne;
@@ -832,6 +893,41 @@ __global__ void __launch_bounds__(128) far3d_f32(EvalArgs a)
             if (a.which == GF_OUT_MAXWELL7)
                 store_out(o + 6, cmul(pre, make_double2(P[0][0] + S[0][1], P[0][1] - S[0][0])));
         }
+    }
+}
+
+template <int NF>
+__global__ void __launch_bounds__(128) far3d_f32(EvalArgs a)
+{
+    const int count = a.far_count[0];
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int w = gw; w * 32 < count; w += nw) far3d_f32_chunk<NF>(a, w, count);
+}
+
+// Batched far kernel: one persistent launch for all pairs.  The chunks of all
+// pairs form one global list (pair after pair); warp gw takes the chunks whose
+// global index is congruent to gw modulo the number of warps, so no pair
+// waits for another and the load stays balanced across pair boundaries.
+template <typename R, int NF>
+__global__ void far3d_batch(const EvalArgs *args, int np)
+{
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    int g0 = 0;
+    for (int p = 0; p < np; ++p) {
+        const EvalArgs &a = args[p];
+        const int count = a.far_count[0];
+        const int nch = (count + 31) >> 5;
+        int c = (gw - g0) % nw;
+        if (c < 0) c += nw;
+        for (; c < nch; c += nw) {
+            if (sizeof(R) == 8)
+                far3d_f64_chunk<NF>(a, c, count);
+            else
+                far3d_f32_chunk<NF>(a, c, count);
+        }
+        g0 = (g0 + nch) % nw;
     }
 }
 
@@ -924,7 +1020,28 @@ cudaError_t launch_eval_t(const EvalArgs &a, cudaStream_t s, cudaEvent_t ev_mid)
     return cudaGetLastError();
 }
 
+template <typename R>
+cudaError_t launch_eval_batch_t(const EvalBatch &b, cudaStream_t s)
+{
+    if (b.nf == 1) {
+        near3d_batch<R, 1><<<b.grid_near, 256, 0, s>>>(b.args, b.prefix, b.np);
+        far_scatter_batch<<<b.grid_scatter, 256, 0, s>>>(b.args, b.np, b.scatter_per_pair);
+        far3d_batch<R, 1><<<b.grid_far, b.block_far, 0, s>>>(b.args, b.np);
+    } else {
+        near3d_batch<R, 7><<<b.grid_near, 256, 0, s>>>(b.args, b.prefix, b.np);
+        far_scatter_batch<<<b.grid_scatter, 256, 0, s>>>(b.args, b.np, b.scatter_per_pair);
+        far3d_batch<R, 7><<<b.grid_far, b.block_far, 0, s>>>(b.args, b.np);
+    }
+    gf_count_launch(3);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t gf_launch_eval_batch(const EvalBatch &b, int precision, cudaStream_t s)
+{
+    return precision == GF_FP64 ? launch_eval_batch_t<double>(b, s) : launch_eval_batch_t<float>(b, s);
+}
 
 cudaError_t gf_launch_beta_table(const EvalArgs &a, int precision, cudaStream_t s)
 {

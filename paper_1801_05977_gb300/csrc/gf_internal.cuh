@@ -106,6 +106,7 @@ struct SynthArgs {
     const double *Pw0;  // [Q] 2D: w_m hw Phi_1(r_m) r_m      (J0 weights)
     const double *Pw1;  // [Q] 2D: w_m hw Phi_1(r_m) r_m^2    (J1 weights)
     double F10;         // 2D: sqrt(V) F1-hat_0
+    int TJ2, lg1, lg2;  // x2-pass columns per CTA; log2 M1, log2 M2
     void *work;         // [nf][Mlast][M2][M1] complex (3D) or [M2][M1] (2D), working precision
     void *grid;         // padded gather grid
     int P1, P2, P3;     // padded extents (M + 3 per periodic axis; P3 = 1 in 2D)
@@ -155,12 +156,37 @@ struct EvalArgs {
 #define GF_FAR_BUCKETS 64
 #define GF_SCRATCH_COUNTERS (1 + 2 * GF_FAR_BUCKETS)
 
+// A sweep of plans run as batched persistent launches: per-pass virtual-block
+// prefix sums over the pairs (device arrays of np + 1 ints), the per-pair
+// arguments (device array), persistent grid sizes and shared-memory sizes.
+struct SynthBatch {
+    const SynthArgs *args;
+    const int *prefix[3];
+    int np;
+    int grid[3];
+    size_t smem[3];
+};
+struct EvalBatch {
+    const EvalArgs *args;   // per pair: x, out, n and scratch pointers filled in
+    const int *prefix;      // near-kernel tiles (256 targets) per pair, prefix sums (np + 1)
+    int np;
+    int nf;
+    int grid_near, grid_scatter, grid_far, block_far;
+    int scatter_per_pair;
+};
+
 // launch helpers implemented in synth.cu / eval.cu
 cudaError_t gf_launch_synth(const SynthArgs &a, int precision, cudaStream_t s);
 cudaError_t gf_launch_extract(const SynthArgs &a, int precision, void *dev_out, cudaStream_t s);
+void gf_synth_config(SynthArgs &a, int precision, int tj_max, size_t smem[3]);
+cudaError_t gf_launch_synth_batch(const SynthBatch &b, int precision, cudaStream_t s);
+cudaError_t gf_launch_eval_batch(const EvalBatch &b, int precision, cudaStream_t s);
 cudaError_t gf_launch_beta_table(const EvalArgs &a, int precision, cudaStream_t s);
 cudaError_t gf_launch_eval(const EvalArgs &a, int precision, cudaStream_t s, cudaEvent_t ev_mid);
 
 void gf_count_launch(int n);
 gf_status gf_plan_eval_args(gf_plan_t p, const double *dev_xyz, int64_t n, int which, void *dev_out, EvalArgs *a);
 gf_status gf_set_error(gf_status s, const char *msg);
+SynthArgs gf_plan_synth_args(gf_plan_t p);
+size_t gf_plan_work_bytes(gf_plan_t p);
+int gf_plan_precision(gf_plan_t p);

@@ -616,6 +616,12 @@ gf_status gf_plan_eval_args(gf_plan_t p, const double *dev_xyz, int64_t n, int w
 
 gf_status gf_set_error(gf_status s, const char *msg) { return fail(s, "%s", msg); }
 
+// Synthesis arguments of a plan (batched sweeps re-run the synthesis of many
+// plans with their own work buffers) and the bytes of its work buffer.
+SynthArgs gf_plan_synth_args(gf_plan_t p) { return p->sa; }
+size_t gf_plan_work_bytes(gf_plan_t p) { return (size_t)p->M[0] * p->M[1] * p->M[2] * p->nf * p->elem; }
+int gf_plan_precision(gf_plan_t p) { return p->precision; }
+
 extern "C" {
 
 gf_status gf_set_phase_timing(int on)

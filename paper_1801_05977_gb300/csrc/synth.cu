@@ -65,10 +65,9 @@ __device__ void load_twiddles(typename cplx_t<R>::T *tw, int n)
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256) synth_first_pass(SynthArgs a)
+__device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char *smem)
 {
     typedef typename cplx_t<R>::T C;
-    extern __shared__ __align__(16) unsigned char smem[];
     const int n = a.Mlast, lg = a.lgMlast, TJ = a.TJ, Q = a.Q, nf = a.nf;
     double2 *Av = reinterpret_cast<double2 *>(smem);   // [TJ][Q]
     double2 *betas = Av + TJ * Q;                        // [TJ]
@@ -77,7 +76,7 @@ __global__ void __launch_bounds__(256) synth_first_pass(SynthArgs a)
     C *buf1 = buf0 + nf * TJ * n;
     double *A2s = reinterpret_cast<double *>(buf1 + nf * TJ * n); // [TJ]
     const int ncols = (a.dim == 3) ? a.M1 * a.M2 : a.M1;
-    const int col0 = blockIdx.x * TJ;
+    const int col0 = blk * TJ;
 
     load_twiddles<R>(tw, n);
     for (int t = threadIdx.x; t < TJ; t += blockDim.x) {
@@ -212,15 +211,14 @@ __global__ void __launch_bounds__(256) synth_first_pass(SynthArgs a)
 
 // Middle pass (3D only): inverse transform along x2 for fixed (field, l3, b1-tile).
 template <typename R>
-__global__ void __launch_bounds__(256) synth_x2_pass(SynthArgs a, int TJ, int lg2)
+__device__ void synth_x2_body(const SynthArgs &a, int bx, int l3, int f, unsigned char *smem)
 {
     typedef typename cplx_t<R>::T C;
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int n = a.M2;
+    const int n = a.M2, TJ = a.TJ2, lg2 = a.lg2;
     C *tw = reinterpret_cast<C *>(smem);
     C *buf0 = tw + (n >> 1);
     C *buf1 = buf0 + TJ * n;
-    const int b10 = blockIdx.x * TJ, l3 = blockIdx.y, f = blockIdx.z;
+    const int b10 = bx * TJ;
     C *W = reinterpret_cast<C *>(a.work) + ((size_t)f * a.M3 + l3) * (size_t)a.M2 * a.M1;
     load_twiddles<R>(tw, n);
     for (int i = threadIdx.x; i < TJ * n; i += blockDim.x) {
@@ -251,15 +249,14 @@ __device__ __forceinline__ int pad_dests(int a_node, int M, int *p)
 // (x3: -c~ + a h3), with one halo node before and two after on every
 // periodic axis so that a cubic stencil never wraps.
 template <typename R>
-__global__ void __launch_bounds__(256) synth_x1_pass(SynthArgs a, int lg1)
+__device__ void synth_x1_body(const SynthArgs &a, int row, unsigned char *smem)
 {
     typedef typename cplx_t<R>::T C;
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int n = a.M1, nf = a.nf;
+    const int n = a.M1, nf = a.nf, lg1 = a.lg1;
     C *tw = reinterpret_cast<C *>(smem);
     C *buf0 = tw + (n >> 1);
     C *buf1 = buf0 + nf * n;
-    const int row = blockIdx.x;  // 3D: l3 * M2 + l2; 2D: l2
+    // row: 3D: l3 * M2 + l2; 2D: l2
     const size_t fstride = (size_t)a.Mlast * (a.dim == 3 ? a.M2 : 1) * a.M1;
     const C *W = reinterpret_cast<const C *>(a.work);
     load_twiddles<R>(tw, n);
@@ -296,6 +293,94 @@ __global__ void __launch_bounds__(256) synth_x1_pass(SynthArgs a, int lg1)
         }
 }
 
+template <typename R>
+__global__ void __launch_bounds__(256) synth_first_pass(SynthArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    synth_first_pass_body<R>(a, blockIdx.x, smem);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) synth_x2_pass(SynthArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    synth_x2_body<R>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) synth_x1_pass(SynthArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    synth_x1_body<R>(a, blockIdx.x, smem);
+}
+
+// pair of virtual block vb: largest p with prefix[p] <= vb
+__device__ __forceinline__ int batch_pair(const int *prefix, int np, int vb)
+{
+    int lo = 0, hi = np - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= vb)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Batched synthesis passes: one persistent launch per pass walks the
+// (pair, block) work list of all plans of a sweep; prefix[p] is the first
+// virtual block of pair p (prefix[np] = total).
+template <typename R>
+__global__ void __launch_bounds__(256) synth_first_pass_batch(const SynthArgs *args, const int *prefix, int np)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ SynthArgs sa;
+    const int total = prefix[np];
+    for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
+        const int p = batch_pair(prefix, np, vb);
+        if (threadIdx.x == 0) sa = args[p];
+        __syncthreads();
+        synth_first_pass_body<R>(sa, vb - prefix[p], smem);
+        __syncthreads();
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) synth_x2_pass_batch(const SynthArgs *args, const int *prefix, int np)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ SynthArgs sa;
+    const int total = prefix[np];
+    for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
+        const int p = batch_pair(prefix, np, vb);
+        if (threadIdx.x == 0) sa = args[p];
+        __syncthreads();
+        int loc = vb - prefix[p];
+        const int nbx = sa.M1 / sa.TJ2;
+        const int bx = loc % nbx;
+        loc /= nbx;
+        const int l3 = loc % sa.M3, f = loc / sa.M3;
+        synth_x2_body<R>(sa, bx, l3, f, smem);
+        __syncthreads();
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) synth_x1_pass_batch(const SynthArgs *args, const int *prefix, int np)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ SynthArgs sa;
+    const int total = prefix[np];
+    for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
+        const int p = batch_pair(prefix, np, vb);
+        if (threadIdx.x == 0) sa = args[p];
+        __syncthreads();
+        synth_x1_body<R>(sa, vb - prefix[p], smem);
+        __syncthreads();
+    }
+}
+
 // gf_eval_grid: padded gather grid -> node order [f][l3][l2][l1]
 template <typename R>
 __global__ void extract_grid(SynthArgs a, void *out)
@@ -326,42 +411,71 @@ int ilog2(int n)
     return l;
 }
 
+// Tile choices and shared-memory sizes of the three passes for one plan
+// (tj_max caps the first pass's columns per CTA; the batch autotuner varies it).
 template <typename R>
-cudaError_t launch_synth_t(const SynthArgs &a0, cudaStream_t s)
+void synth_config_t(SynthArgs &a, int tj_max, size_t sm[3])
 {
     typedef typename cplx_t<R>::T C;
-    SynthArgs a = a0;
     const int ncols = (a.dim == 3) ? a.M1 * a.M2 : a.M1;
-    // first pass: TJ columns per CTA, bounded by shared memory
     size_t fixed = sizeof(C) * (a.Mlast / 2);
-    int TJ = 8;
+    int TJ = tj_max;
     while (TJ > 1 && (TJ > ncols ||
                       fixed + TJ * (sizeof(double2) * a.Q + sizeof(double2) + sizeof(double)) +
                               2 * sizeof(C) * a.nf * TJ * a.Mlast >
                           160 * 1024))
         TJ >>= 1;
     a.TJ = TJ;
-    size_t sm1 = fixed + TJ * (sizeof(double2) * a.Q + sizeof(double2) + sizeof(double)) +
-                 2 * sizeof(C) * a.nf * TJ * a.Mlast;
-    cudaError_t e = cudaFuncSetAttribute(synth_first_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+    sm[0] = fixed + TJ * (sizeof(double2) * a.Q + sizeof(double2) + sizeof(double)) + 2 * sizeof(C) * a.nf * TJ * a.Mlast;
+    int TJ2 = 8;
+    while (TJ2 > 1 && (TJ2 > a.M1 || sizeof(C) * (a.M2 / 2 + 2 * TJ2 * a.M2) > 160 * 1024)) TJ2 >>= 1;
+    a.TJ2 = TJ2;
+    a.lg2 = ilog2(a.M2);
+    a.lg1 = ilog2(a.M1);
+    sm[1] = a.dim == 3 ? sizeof(C) * (a.M2 / 2 + 2 * TJ2 * a.M2) : 0;
+    sm[2] = sizeof(C) * (a.M1 / 2 + 2 * a.nf * a.M1);
+}
+
+template <typename R>
+cudaError_t launch_synth_t(const SynthArgs &a0, cudaStream_t s)
+{
+    SynthArgs a = a0;
+    size_t sm[3];
+    synth_config_t<R>(a, 8, sm);
+    const int ncols = (a.dim == 3) ? a.M1 * a.M2 : a.M1;
+    cudaError_t e = cudaFuncSetAttribute(synth_first_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[0]);
     if (e != cudaSuccess) return e;
-    synth_first_pass<R><<<ncols / TJ, 256, sm1, s>>>(a);
+    synth_first_pass<R><<<ncols / a.TJ, 256, sm[0], s>>>(a);
     gf_count_launch(1);
     if (a.dim == 3) {
-        int TJ2 = 8;
-        while (TJ2 > 1 && (TJ2 > a.M1 || sizeof(C) * (a.M2 / 2 + 2 * TJ2 * a.M2) > 160 * 1024)) TJ2 >>= 1;
-        size_t sm2 = sizeof(C) * (a.M2 / 2 + 2 * TJ2 * a.M2);
-        e = cudaFuncSetAttribute(synth_x2_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+        e = cudaFuncSetAttribute(synth_x2_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[1]);
         if (e != cudaSuccess) return e;
-        synth_x2_pass<R><<<dim3(a.M1 / TJ2, a.M3, a.nf), 256, sm2, s>>>(a, TJ2, ilog2(a.M2));
+        synth_x2_pass<R><<<dim3(a.M1 / a.TJ2, a.M3, a.nf), 256, sm[1], s>>>(a);
         gf_count_launch(1);
     }
-    size_t sm3 = sizeof(C) * (a.M1 / 2 + 2 * a.nf * a.M1);
-    e = cudaFuncSetAttribute(synth_x1_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
+    e = cudaFuncSetAttribute(synth_x1_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[2]);
     if (e != cudaSuccess) return e;
     int rows = (a.dim == 3) ? a.M3 * a.M2 : a.M2;
-    synth_x1_pass<R><<<rows, 256, sm3, s>>>(a, ilog2(a.M1));
+    synth_x1_pass<R><<<rows, 256, sm[2], s>>>(a);
     gf_count_launch(1);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_synth_batch_t(const SynthBatch &b, cudaStream_t s)
+{
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(synth_first_pass_batch<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)b.smem[0])) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(synth_x2_pass_batch<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)b.smem[1])) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(synth_x1_pass_batch<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)b.smem[2])) != cudaSuccess)
+        return e;
+    synth_first_pass_batch<R><<<b.grid[0], 256, b.smem[0], s>>>(b.args, b.prefix[0], b.np);
+    synth_x2_pass_batch<R><<<b.grid[1], 256, b.smem[1], s>>>(b.args, b.prefix[1], b.np);
+    synth_x1_pass_batch<R><<<b.grid[2], 256, b.smem[2], s>>>(b.args, b.prefix[2], b.np);
+    gf_count_launch(3);
     return cudaGetLastError();
 }
 
@@ -370,6 +484,19 @@ cudaError_t launch_synth_t(const SynthArgs &a0, cudaStream_t s)
 cudaError_t gf_launch_synth(const SynthArgs &a, int precision, cudaStream_t s)
 {
     return precision == GF_FP64 ? launch_synth_t<double>(a, s) : launch_synth_t<float>(a, s);
+}
+
+void gf_synth_config(SynthArgs &a, int precision, int tj_max, size_t smem[3])
+{
+    if (precision == GF_FP64)
+        synth_config_t<double>(a, tj_max, smem);
+    else
+        synth_config_t<float>(a, tj_max, smem);
+}
+
+cudaError_t gf_launch_synth_batch(const SynthBatch &b, int precision, cudaStream_t s)
+{
+    return precision == GF_FP64 ? launch_synth_batch_t<double>(b, s) : launch_synth_batch_t<float>(b, s);
 }
 
 cudaError_t gf_launch_extract(const SynthArgs &a, int precision, void *dev_out, cudaStream_t s)

@@ -44,7 +44,9 @@ class PlanInfo(ctypes.Structure):
 
 EXPORTS = ["gf_trunc_default", "gf_plan", "gf_eval_grid", "gf_grid_bytes", "gf_eval_points",
            "gf_eval_points_host", "gf_plan_get_info", "gf_destroy", "gf_status_string", "gf_last_error",
-           "gf_launch_count", "gf_set_phase_timing", "gf_plan_phase_ms", "gf_eval_points_noalloc"]
+           "gf_launch_count", "gf_set_phase_timing", "gf_plan_phase_ms", "gf_eval_points_noalloc",
+           "gf_plan_batch", "gf_batch_synthesize", "gf_batch_eval_points", "gf_batch_autotune",
+           "gf_batch_get_tuning", "gf_batch_run_graph", "gf_batch_get_plan", "gf_batch_destroy"]
 
 NOALLOC_MAX_TARGETS = 1 << 18
 
@@ -75,6 +77,14 @@ def lib(build_if_missing: bool = True):
     L.gf_eval_points.argtypes = [vp, vp, i64, i32, vp, vp]
     L.gf_eval_points_host.argtypes = [vp, vp, i64, i32, vp, vp]
     L.gf_eval_points_noalloc.argtypes = [vp, vp, i64, i32, vp, vp]
+    P = ctypes.POINTER
+    L.gf_plan_batch.argtypes = [i32, P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_int), P(Trunc), vp, P(vp)]
+    L.gf_batch_synthesize.argtypes = [vp, vp]
+    for nm in ("gf_batch_eval_points", "gf_batch_autotune", "gf_batch_run_graph"):
+        getattr(L, nm).argtypes = [vp, vp, P(ctypes.c_int64), i32, vp, vp]
+    L.gf_batch_get_tuning.argtypes = [vp, P(ctypes.c_int)]
+    L.gf_batch_get_plan.argtypes = [vp, i32, P(vp)]
+    L.gf_batch_destroy.argtypes = [vp]
     L.gf_plan_get_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
     L.gf_destroy.argtypes = [vp]
     L.gf_status_string.argtypes = [i32]
@@ -84,7 +94,9 @@ def lib(build_if_missing: bool = True):
     L.gf_set_phase_timing.argtypes = [i32]
     L.gf_plan_phase_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
     for name in ("gf_trunc_default", "gf_plan", "gf_eval_grid", "gf_eval_points", "gf_eval_points_host",
-                 "gf_eval_points_noalloc",
+                 "gf_eval_points_noalloc", "gf_plan_batch", "gf_batch_synthesize", "gf_batch_eval_points",
+                 "gf_batch_autotune", "gf_batch_get_tuning", "gf_batch_run_graph", "gf_batch_get_plan",
+                 "gf_batch_destroy",
                  "gf_plan_get_info", "gf_destroy", "gf_set_phase_timing", "gf_plan_phase_ms"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
@@ -197,6 +209,74 @@ class Plan:
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             lib().gf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """A sweep of 3D plans run as batched persistent launches (gf_plan_batch ...)."""
+
+    def __init__(self, k, alpha, M, trunc: Trunc | None = None, stream=None, **trunc_kw):
+        L = lib()
+        if trunc is None:
+            trunc = trunc_default(**trunc_kw)
+        k = np.ascontiguousarray(k, dtype=np.float64)
+        alpha = np.ascontiguousarray(alpha, dtype=np.float64).reshape(-1, 2)
+        M = np.ascontiguousarray(M, dtype=np.int32).reshape(-1, 3)
+        self.np = k.shape[0]
+        assert alpha.shape[0] == self.np and M.shape[0] == self.np
+        h = ctypes.c_void_p()
+        _check(L.gf_plan_batch(self.np, k.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                               alpha.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                               M.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ctypes.byref(trunc),
+                               _stream_ptr(stream), ctypes.byref(h)))
+        self._h = h
+        self.precision = trunc.precision
+
+    @property
+    def complex_dtype(self):
+        import torch
+        return torch.complex128 if self.precision == GF_FP64 else torch.complex64
+
+    def _off(self, offsets):
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        assert off.shape[0] == self.np + 1
+        self._off_keep = off
+        return off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+
+    def synthesize(self, stream=None):
+        _check(lib().gf_batch_synthesize(self._h, _stream_ptr(stream)))
+
+    def eval_points_into(self, x, offsets, out, which: int, stream=None):
+        _check(lib().gf_batch_eval_points(self._h, ctypes.c_void_p(x.data_ptr()), self._off(offsets), int(which),
+                                          ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        return out
+
+    def autotune(self, x, offsets, out, which: int, stream=None):
+        _check(lib().gf_batch_autotune(self._h, ctypes.c_void_p(x.data_ptr()), self._off(offsets), int(which),
+                                       ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        t = (ctypes.c_int * 3)()
+        _check(lib().gf_batch_get_tuning(self._h, t))
+        return tuple(t)
+
+    def run_graph(self, x, offsets, out, which: int, stream=None):
+        _check(lib().gf_batch_run_graph(self._h, ctypes.c_void_p(x.data_ptr()), self._off(offsets), int(which),
+                                        ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        return out
+
+    def plan_handle(self, i: int):
+        h = ctypes.c_void_p()
+        _check(lib().gf_batch_get_plan(self._h, int(i), ctypes.byref(h)))
+        return h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().gf_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

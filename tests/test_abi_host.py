@@ -86,3 +86,21 @@ def test_null_handles_are_rejected():
     assert L.gf_destroy(None) == gf.GF_OK
     assert L.gf_grid_bytes(None) == 0
     assert L.gf_status_string(gf.GF_ERR_WOOD).decode().startswith("Wood")
+
+
+def test_batch_rejects_bad_arguments():
+    L = gf.lib()
+    t = gf.trunc_default()
+    h = ctypes.c_void_p()
+    k = (ctypes.c_double * 2)(2.5, 1.1)
+    al = (ctypes.c_double * 4)(0.1, 0.3, 0.1, 0.0)
+    M = (ctypes.c_int * 6)(16, 16, 16, 16, 16, 16)
+    assert L.gf_plan_batch(0, k, al, M, ctypes.byref(t), None, ctypes.byref(h)) == gf.GF_ERR_ARG
+    assert L.gf_plan_batch(2, None, al, M, ctypes.byref(t), None, ctypes.byref(h)) == gf.GF_ERR_ARG
+    # the first pair is valid only on a GPU; put the Wood pair first so no device work happens
+    k2 = (ctypes.c_double * 2)(1.1, 2.5)
+    al2 = (ctypes.c_double * 4)(0.1, 0.0, 0.1, 0.3)
+    st = L.gf_plan_batch(2, k2, al2, M, ctypes.byref(t), None, ctypes.byref(h))
+    assert st == gf.GF_ERR_WOOD and "pair 0" in L.gf_last_error().decode()
+    assert L.gf_batch_destroy(None) == gf.GF_OK
+    assert L.gf_batch_eval_points(None, None, None, 1, None, None) == gf.GF_ERR_ARG
