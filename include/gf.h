@@ -60,7 +60,10 @@ enum {                                            /* gf_eval_points `which` */
     GF_OUT_G = 0,         /* 2D plans: G, 1 entry */
     GF_OUT_GD = 1,        /* 3D plans: G_d, 1 entry */
     GF_OUT_MAXWELL6 = 2,  /* Maxwell plans: GG_xx, GG_yy, GG_zz, GG_xy, GG_xz, GG_yz */
-    GF_OUT_MAXWELL7 = 3   /* Maxwell plans: the six entries above, then G_d */
+    GF_OUT_MAXWELL7 = 3,  /* Maxwell plans: the six entries above, then G_d */
+    GF_OUT_LD = 4         /* 3D Helmholtz plans: the interpolated remainder L_dN at the in-cell
+                             point (t1, t2, x3), no singular part, no phase (Alg. 2 step 2d);
+                             targets with |x3| > c give NaN */
 };
 
 /* Method parameters.  Defaults (gf_trunc_default): c = 0.6, c~ = 1 (Sec. 5),
@@ -220,6 +223,65 @@ gf_status gf_batch_get_plan(gf_batch_t batch, int i, gf_plan_t *out);
 
 /* Release the batch, its plans and graphs (synchronises the device).  NULL is accepted. */
 gf_status gf_batch_destroy(gf_batch_t batch);
+
+/* ---------------------------------------------------------------------------
+ * Tensor-core BF16 GEMM (the building block of the surrogate below):
+ *   C[M x N] (fp32, row stride ldc) = A . B^T with A(m,k) = A[m*lda + k]
+ *   (a_trans: A[k*lda + m]) and B(n,k) = B[n*ldb + k] (b_trans: B[k*ldb + n]),
+ *   bf16 operands, fp32 accumulation in tensor memory (tcgen05).  M, N, K
+ *   positive multiples of 16; leading dimensions multiples of 8 elements and
+ *   pointers 16-byte aligned.  ksplit > 1 splits K over CTAs (C is zeroed and
+ *   accumulated atomically).  All pointers are device memory. */
+gf_status gf_gemm_bf16(const void *A, int64_t lda, int a_trans, const void *B, int64_t ldb, int b_trans,
+                       int M, int N, int K, float *C, int64_t ldc, int ksplit, void *cuda_stream);
+
+/* ---------------------------------------------------------------------------
+ * Learned surrogate of the smooth remainder L_d (spec extension; the
+ * paper has no learned part).  A 5-layer MLP 80 -> 256 -> 256 -> 256 -> 256 -> 2
+ * with SiLU activations: bf16 weights and activations, fp32 accumulation on the
+ * tensor cores, fp32 master weights with Adam.  Inputs per sample, float
+ * [n][6]: (t1, t2, x3, alpha1, alpha2, k) with t the in-cell coordinates; the
+ * features are cos/sin of n1 t1 + n2 t2 + m3 pi x3 / c~ for 32 fixed integer
+ * vectors plus 2 alpha1, 2 alpha2, (k - 2.5)/1.5.  Output float [n][2]: the
+ * real and imaginary parts of L_d / scale.
+ * ------------------------------------------------------------------------- */
+typedef struct gf_mlp_s *gf_mlp_t;
+
+/* Create a network with uniform(+-1/sqrt(fan_in)) weights drawn from `seed`
+ * (counter-based, reproducible) and zero biases; c_tilde sets the x3 period. */
+gf_status gf_mlp_create(uint64_t seed, double c_tilde, gf_mlp_t *out);
+/* Number of floats of gf_mlp_params: per layer W [out][in] then b [out]. */
+int64_t gf_mlp_param_count(void);
+/* Copy the fp32 parameters to (to_device = 0) or from (to_device = 1) host
+ * memory (checkpointing; gradient checks).  Synchronises the device. */
+gf_status gf_mlp_params(gf_mlp_t mlp, float *host, int64_t count, int to_device);
+/* Scale of the targets: the network learns L_d / scale. */
+gf_status gf_mlp_set_scale(gf_mlp_t mlp, double scale);
+/* Forward pass of n samples (device pointers), output float [n][2]. */
+gf_status gf_mlp_forward(gf_mlp_t mlp, const float *dev_in, int n, float *dev_out, void *cuda_stream);
+/* One Adam step (lr; beta 0.9/0.999) on the mean-squared loss
+ * sum (Y - T)^2 / (2n) of one batch (targets float [n][2]); the batch loss is
+ * written to dev_loss (device float) when not NULL. */
+gf_status gf_mlp_train_step(gf_mlp_t mlp, const float *dev_in, const float *dev_target, int n, float lr,
+                            float *dev_loss, void *cuda_stream);
+/* Gradients of that loss (no update), copied to host in the layout of
+ * gf_mlp_params; the loss to *host_loss when not NULL.  Synchronises. */
+gf_status gf_mlp_gradients(gf_mlp_t mlp, const float *dev_in, const float *dev_target, int n, float *host_grads,
+                           float *host_loss, void *cuda_stream);
+/* Tensor-core error word (1 after a bounded wait ran out): GF_ERR_TIMEOUT if set. */
+gf_status gf_mlp_error_word(gf_mlp_t mlp, int *out);
+/* G_d at near targets (|x3| <= c) of many (alpha, k) pairs, with the network
+ * standing in for the interpolated remainder: G = e^{i2pi<alpha.m>}(e^{i alpha.t}
+ * scale*MLP + e^{ikr} Y_eps/(4 pi r)).  Pairs whose Wood distance
+ * min_n | |alpha_n| - k | is below wood_delta are evaluated by the FFT path
+ * instead (a 128 x 128 x 64 double-precision plan); their count is written to
+ * *n_fallback_pairs.  k [npairs], alpha [npairs][2], offsets [npairs + 1] are host
+ * memory; dev_xyz [offsets[npairs]][3] doubles and dev_out complex128 are device
+ * memory.  Targets with |x3| > c get NaN (outside the surrogate's domain). */
+gf_status gf_surrogate_eval(gf_mlp_t mlp, int npairs, const double *k, const double *alpha, const int64_t *offsets,
+                            const double *dev_xyz, void *dev_out, double wood_delta, const gf_trunc_t *trunc,
+                            int *n_fallback_pairs, void *cuda_stream);
+gf_status gf_mlp_destroy(gf_mlp_t mlp);
 
 /* Plan facts (host memory).  Returns GF_ERR_ARG on NULL arguments. */
 typedef struct {

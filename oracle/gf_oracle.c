@@ -633,6 +633,7 @@ static void eval_point(const or_params *p, const cplx *g, const double *x, int w
         return;
     }
     /* Algorithms 2 / 3, step 2b: branch on |x3| */
+    if (which == 4 && fabs(x[2]) > p->c) { out[0] = NAN; return; }
     if (fabs(x[2]) > p->c) { series_point(p, x, which, out); return; }
     double t1, m1, t2, m2;
     reduce_period(x[0], &t1, &m1);                            /* step 2c */
@@ -660,6 +661,7 @@ static void eval_point(const or_params *p, const cplx *g, const double *x, int w
         d2Phi = g2 * Y0 + 2.0 * g1 * Y1 + gr * Y2;
         F = back * Phi;
     }
+    if (which == 4) { out[0] = Ld; return; }                  /* the remainder alone (step 2d) */
     cplx Kd = Ld + F;                                         /* step 2e */
     if (which <= 1) { out[0] = lift * Kd; return; }           /* step 2f + lift */
 

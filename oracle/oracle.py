@@ -90,8 +90,8 @@ def _ptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
-OUT_G, OUT_GD, OUT_MAXWELL6, OUT_MAXWELL7 = 0, 1, 2, 3
-N_ENTRIES = {OUT_G: 1, OUT_GD: 1, OUT_MAXWELL6: 6, OUT_MAXWELL7: 7}
+OUT_G, OUT_GD, OUT_MAXWELL6, OUT_MAXWELL7, OUT_LD = 0, 1, 2, 3, 4
+N_ENTRIES = {OUT_G: 1, OUT_GD: 1, OUT_MAXWELL6: 6, OUT_MAXWELL7: 7, OUT_LD: 1}
 
 
 @dataclass

@@ -127,6 +127,12 @@ __device__ void near3d_tiles(const EvalArgs &a, int64_t base0, int64_t stride, i
         }
         bool finite = isfinite(x1) && isfinite(x2) && isfinite(x3);
         bool isfar = valid && finite && fabs(x3) > a.c;
+        const bool only_L = NF == 1 && a.which == GF_OUT_LD;
+        if (only_L && isfar) {
+            out[i] = nan_c<R>();  // the remainder alone is served on the near region only
+            isfar = false;
+            valid = false;
+        }
         push_far(isfar, (int)i, a.far_idx, a.far_count);
         if (isfar) atomicAdd(&hist[far_bucket(fabs(x3), a.c)], 1);
         if (!valid || isfar) continue;
@@ -203,6 +209,10 @@ __device__ void near3d_tiles(const EvalArgs &a, int64_t base0, int64_t stride, i
         }
         if (NF == 1) {
             double2 L = make_double2((double)acc[0][0], (double)acc[0][1]);
+            if (only_L) {
+                store_out(o, L);
+                continue;
+            }
             double2 v = cadd(cmul(lift, L), cmul(lat, PhiY));
             store_out(o, v);
         } else {

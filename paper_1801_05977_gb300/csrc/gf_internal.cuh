@@ -94,6 +94,7 @@ struct SynthArgs {
     int TJ;             // columns per CTA in the first pass (power of two)
     double k, a1, a2;   // wave number, alpha
     double ct;          // c~ (possibly perturbed)
+    double gskip;       // evanescent |beta| above which e^{-|beta| c}/(2 |beta|^2) < 1e-20
     double invV;        // 1 / |D|: 1/(8 pi^2 c~) in 3D, 1/(4 pi c~) in 2D
     const double *tW;   // [Q] w_m hw X'(t_m) on [c, (c+c~)/2]
     const double *tt;   // [Q] t_m

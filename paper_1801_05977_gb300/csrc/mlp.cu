@@ -1,0 +1,724 @@
+// Learned surrogate of the smooth remainder L_d (not in the paper): a 5-layer
+// BF16 MLP with FP32 accumulation on the tensor cores (tcgen05 GEMMs of
+// umma_gemm.cuh), Fourier-feature inputs of (t1, t2, x3) plus (alpha1, alpha2, k),
+// trained by the library's own forward, backward and Adam kernels on samples of
+// the FFT path, and evaluated with the FFT path as fallback near Wood anomalies.
+//
+// Network: 80 -> 256 -> 256 -> 256 -> 256 -> 2 (Re, Im of L_d / scale), SiLU
+// between layers.  Input features: cos and sin of n1 t1 + n2 t2 + m3 pi x3 / c~
+// for 32 fixed integer vectors (n1, n2, m3), then 2 alpha1, 2 alpha2,
+// (k - 2.5)/1.5, zero padding to 80.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "gf_internal.cuh"
+#include "umma_gemm.cuh"
+
+typedef __nv_bfloat16 bf16;
+
+namespace {
+
+constexpr int K0 = 80, HID = 256, NL = 5;
+const int IN_DIM[NL] = {K0, HID, HID, HID, HID};
+const int OUT_DIM[NL] = {HID, HID, HID, HID, 2};
+
+// the 32 frequency vectors (n1, n2, m3) of the Fourier features
+__constant__ int c_freq[32][3];
+
+gf_status err(gf_status s, const char *fmt, ...)
+{
+    char msg[256];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(msg, sizeof(msg), fmt, ap);
+    va_end(ap);
+    return gf_set_error(s, msg);
+}
+
+#define CUM(call)                                                                                  \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return err(e_ == cudaErrorMemoryAllocation ? GF_ERR_NOMEM : GF_ERR_CUDA, "%s: %s", #call, \
+                       cudaGetErrorString(e_));                                                    \
+    } while (0)
+
+// counter-based uniform in [0, 1) (splitmix64 finaliser)
+__host__ __device__ inline double u01(unsigned long long seed, unsigned long long i)
+{
+    unsigned long long z = seed * 0x9E3779B97F4A7C15ull + i * 0xBF58476D1CE4E5B9ull + 0x94D049BB133111EBull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+}
+
+__global__ void features_kernel(const float *in, int n, bf16 *X0, float pi_ct)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float *p = in + 6 * (size_t)i;
+        const float t1 = p[0], t2 = p[1], x3 = p[2];
+        bf16 *o = X0 + (size_t)i * K0;
+#pragma unroll 4
+        for (int f = 0; f < 32; ++f) {
+            float ph = c_freq[f][0] * t1 + c_freq[f][1] * t2 + c_freq[f][2] * pi_ct * x3;
+            float s, c;
+            sincosf(ph, &s, &c);
+            o[2 * f] = __float2bfloat16(c);
+            o[2 * f + 1] = __float2bfloat16(s);
+        }
+        o[64] = __float2bfloat16(2.f * p[3]);
+        o[65] = __float2bfloat16(2.f * p[4]);
+        o[66] = __float2bfloat16((p[5] - 2.5f) / 1.5f);
+        for (int j = 67; j < K0; ++j) o[j] = __float2bfloat16(0.f);
+    }
+}
+
+// Y = H4 W5^T + b5 (one warp per sample); with targets: loss += sum (Y - T)^2 / (2n), dY = (Y - T)/n
+__global__ void head_fwd_kernel(const bf16 *H4, const float *W5, const float *b5, float *Y, int n, const float *T,
+                                float *dY, float *loss, float invn)
+{
+    const int lane = threadIdx.x & 31;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    float lsum = 0.f;
+    for (int i = w; i < n; i += nw) {
+        float a0 = 0.f, a1 = 0.f;
+        for (int j = lane; j < HID; j += 32) {
+            float h = __bfloat162float(H4[(size_t)i * HID + j]);
+            a0 = fmaf(h, W5[j], a0);
+            a1 = fmaf(h, W5[HID + j], a1);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+            a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+        }
+        if (lane == 0) {
+            float y0 = a0 + b5[0], y1 = a1 + b5[1];
+            Y[2 * (size_t)i] = y0;
+            Y[2 * (size_t)i + 1] = y1;
+            if (T) {
+                float d0 = y0 - T[2 * (size_t)i], d1 = y1 - T[2 * (size_t)i + 1];
+                dY[2 * (size_t)i] = d0 * invn;
+                dY[2 * (size_t)i + 1] = d1 * invn;
+                lsum += 0.5f * (d0 * d0 + d1 * d1) * invn;
+            }
+        }
+    }
+    if (T && lane == 0 && lsum != 0.f) atomicAdd(loss, lsum);
+}
+
+// dZ4 = (dY W5) * silu'(Z4)
+__global__ void head_bwd_kernel(const float *dY, const float *W5, const bf16 *Z4, bf16 *dZ4, int n)
+{
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)n * HID;
+         e += (size_t)gridDim.x * blockDim.x) {
+        size_t i = e / HID;
+        int j = (int)(e % HID);
+        float d = dY[2 * i] * W5[j] + dY[2 * i + 1] * W5[HID + j];
+        dZ4[e] = __float2bfloat16(d * umma::dsilu(__bfloat162float(Z4[e])));
+    }
+}
+
+// gW5[o][j] += sum_i dY[i][o] H4[i][j]; gb5[o] += sum_i dY[i][o]   (block: 256 threads = columns j)
+__global__ void head_wgrad_kernel(const float *dY, const bf16 *H4, float *gW5, float *gb5, int n, int rows_per_block)
+{
+    const int j = threadIdx.x;
+    const int i0 = blockIdx.x * rows_per_block, i1 = min(n, i0 + rows_per_block);
+    float s0 = 0.f, s1 = 0.f, t0 = 0.f, t1 = 0.f;
+    for (int i = i0; i < i1; ++i) {
+        float h = __bfloat162float(H4[(size_t)i * HID + j]);
+        float d0 = dY[2 * (size_t)i], d1 = dY[2 * (size_t)i + 1];
+        s0 = fmaf(d0, h, s0);
+        s1 = fmaf(d1, h, s1);
+        if (j == 0) {
+            t0 += d0;
+            t1 += d1;
+        }
+    }
+    atomicAdd(&gW5[j], s0);
+    atomicAdd(&gW5[HID + j], s1);
+    if (j == 0) {
+        atomicAdd(&gb5[0], t0);
+        atomicAdd(&gb5[1], t1);
+    }
+}
+
+// gb[j] += sum_i dZ[i][j]
+__global__ void bias_grad_kernel(const bf16 *dZ, float *gb, int n, int rows_per_block)
+{
+    const int j = threadIdx.x;
+    const int i0 = blockIdx.x * rows_per_block, i1 = min(n, i0 + rows_per_block);
+    float s = 0.f;
+    for (int i = i0; i < i1; ++i) s += __bfloat162float(dZ[(size_t)i * HID + j]);
+    atomicAdd(&gb[j], s);
+}
+
+// Adam (Kingma & Ba) on one flat parameter array
+__global__ void adam_kernel(float *w, const float *g, float *m, float *v, int count, float lr, float b1, float b2,
+                            float eps, float c1, float c2)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        float gi = g[i];
+        float mi = b1 * m[i] + (1.f - b1) * gi;
+        float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// bf16 copies W [out][in] and W^T [in][out]
+__global__ void convert_kernel(const float *W, bf16 *Wb, bf16 *WTb, int out, int in)
+{
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < out * in; e += gridDim.x * blockDim.x) {
+        int o = e / in, i = e % in;
+        bf16 b = __float2bfloat16(W[e]);
+        Wb[e] = b;
+        WTb[(size_t)i * out + o] = b;
+    }
+}
+
+__global__ void init_kernel(float *W, int count, float bound, unsigned long long seed)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+        W[i] = (float)((2.0 * u01(seed, i) - 1.0) * bound);
+}
+
+// Surrogate inputs of near targets: (t1, t2, x3, alpha1, alpha2, k) in float,
+// with the pair of each target from the offsets.
+__global__ void surrogate_inputs_kernel(const double *x, int n, const int *pair_of, const double *pk, float *in)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int p = pair_of[i];
+        double t1 = x[3 * (size_t)i] - 2.0 * GF_PI * floor((x[3 * (size_t)i] + GF_PI) / (2.0 * GF_PI));
+        double t2 = x[3 * (size_t)i + 1] - 2.0 * GF_PI * floor((x[3 * (size_t)i + 1] + GF_PI) / (2.0 * GF_PI));
+        float *o = in + 6 * (size_t)i;
+        o[0] = (float)t1;
+        o[1] = (float)t2;
+        o[2] = (float)x[3 * (size_t)i + 2];
+        o[3] = (float)pk[3 * p];
+        o[4] = (float)pk[3 * p + 1];
+        o[5] = (float)pk[3 * p + 2];
+    }
+}
+
+// G = e^{i2pi<alpha.m>} (e^{i alpha.t} L + e^{ikr} Y_eps(r)/(4 pi r)) for near targets
+// (L = scale * network output); far targets (|x3| > c) are outside the
+// surrogate's domain and get NaN.
+__global__ void surrogate_assemble_kernel(const double *x, int n, const int *pair_of, const double *pk,
+                                          const float *Y, double scale, double c, double eps, double2 *out)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int p = pair_of[i];
+        const double a1 = pk[3 * p], a2 = pk[3 * p + 1], k = pk[3 * p + 2];
+        const double x1 = x[3 * (size_t)i], x2 = x[3 * (size_t)i + 1], x3 = x[3 * (size_t)i + 2];
+        if (!(fabs(x3) <= c)) {
+            out[i] = make_double2(nan(""), nan(""));
+            continue;
+        }
+        const double m1 = floor((x1 + GF_PI) / (2.0 * GF_PI)), m2 = floor((x2 + GF_PI) / (2.0 * GF_PI));
+        const double t1 = x1 - 2.0 * GF_PI * m1, t2 = x2 - 2.0 * GF_PI * m2;
+        double ph = a1 * m1 + a2 * m2;
+        ph -= rint(ph);
+        double sl, cl, sa, ca;
+        sincospi(2.0 * ph, &sl, &cl);
+        sincos(a1 * t1 + a2 * t2, &sa, &ca);
+        const double2 lat = make_double2(cl, sl);
+        const double2 lift = cmul(make_double2(ca, sa), lat);
+        const double2 L = make_double2(scale * Y[2 * (size_t)i], scale * Y[2 * (size_t)i + 1]);
+        double2 v = cmul(lift, L);
+        const double r = sqrt(t1 * t1 + t2 * t2 + x3 * x3);
+        if (r < 2.0 * eps) {
+            double sk, ck;
+            sincos(k * r, &sk, &ck);
+            const double Yc = 1.0 - smooth8((r - eps) / eps);
+            const double f = Yc * 0.25 / (GF_PI * r);
+            v = cadd(v, cmul(lat, make_double2(ck * f, sk * f)));
+        }
+        out[i] = v;
+    }
+}
+
+}  // namespace
+
+struct gf_mlp_s {
+    float *W[NL] = {}, *b[NL] = {}, *mW[NL] = {}, *vW[NL] = {}, *mb[NL] = {}, *vb[NL] = {}, *gW[NL] = {}, *gb[NL] = {};
+    bf16 *Wb[NL] = {}, *WTb[NL] = {};
+    int cap = 0;
+    bf16 *X0 = nullptr, *Z[4] = {}, *H[4] = {}, *dZ[4] = {};
+    float *Y = nullptr, *dY = nullptr, *in = nullptr, *loss = nullptr;
+    int *errw = nullptr;
+    int adam_t = 0;
+    double scale = 1.0;
+    double ct = 1.0;
+    int nsm = 152;
+};
+
+namespace {
+
+gf_status ensure_cap(gf_mlp_t m, int n)
+{
+    if (n <= m->cap) return GF_OK;
+    CUM(cudaDeviceSynchronize());
+    auto fr = [](void *p) {
+        if (p) cudaFree(p);
+    };
+    fr(m->X0);
+    fr(m->Y);
+    fr(m->dY);
+    fr(m->in);
+    for (int l = 0; l < 4; ++l) {
+        fr(m->Z[l]);
+        fr(m->H[l]);
+        fr(m->dZ[l]);
+    }
+    int cap = (n + 127) / 128 * 128;
+    CUM(cudaMalloc(&m->X0, sizeof(bf16) * (size_t)cap * K0));
+    CUM(cudaMalloc(&m->Y, sizeof(float) * 2 * (size_t)cap));
+    CUM(cudaMalloc(&m->dY, sizeof(float) * 2 * (size_t)cap));
+    CUM(cudaMalloc(&m->in, sizeof(float) * 6 * (size_t)cap));
+    for (int l = 0; l < 4; ++l) {
+        CUM(cudaMalloc(&m->Z[l], sizeof(bf16) * (size_t)cap * HID));
+        CUM(cudaMalloc(&m->H[l], sizeof(bf16) * (size_t)cap * HID));
+        CUM(cudaMalloc(&m->dZ[l], sizeof(bf16) * (size_t)cap * HID));
+    }
+    m->cap = cap;
+    return GF_OK;
+}
+
+cudaError_t launch_gemm(const umma::GemmArgs &g0, bool at, bool bt, int ksplit, cudaStream_t s)
+{
+    umma::GemmArgs g = g0;
+    g.kper = ksplit > 1 ? ((g.K + ksplit - 1) / ksplit + umma::KC - 1) / umma::KC * umma::KC : g.K;
+    int zs = (g.K + g.kper - 1) / g.kper;
+    dim3 grid((g.M + umma::BM - 1) / umma::BM, (g.N + g.BN - 1) / g.BN, zs);
+    cudaError_t e;
+    if (!at && !bt) {
+        e = cudaFuncSetAttribute(umma::gemm_bf16<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, umma::SMEM);
+        if (e != cudaSuccess) return e;
+        umma::gemm_bf16<false, false><<<grid, 128, umma::SMEM, s>>>(g);
+    } else if (at && bt) {
+        e = cudaFuncSetAttribute(umma::gemm_bf16<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, umma::SMEM);
+        if (e != cudaSuccess) return e;
+        umma::gemm_bf16<true, true><<<grid, 128, umma::SMEM, s>>>(g);
+    } else if (at) {
+        e = cudaFuncSetAttribute(umma::gemm_bf16<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, umma::SMEM);
+        if (e != cudaSuccess) return e;
+        umma::gemm_bf16<true, false><<<grid, 128, umma::SMEM, s>>>(g);
+    } else {
+        e = cudaFuncSetAttribute(umma::gemm_bf16<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, umma::SMEM);
+        if (e != cudaSuccess) return e;
+        umma::gemm_bf16<false, true><<<grid, 128, umma::SMEM, s>>>(g);
+    }
+    gf_count_launch(1);
+    return cudaGetLastError();
+}
+
+// forward of n samples whose float inputs are in m->in; output m->Y
+gf_status forward(gf_mlp_t m, int n, cudaStream_t s)
+{
+    const int blocks = m->nsm * 8;
+    features_kernel<<<blocks, 256, 0, s>>>(m->in, n, m->X0, (float)(GF_PI / m->ct));
+    gf_count_launch(1);
+    const bf16 *A = m->X0;
+    for (int l = 0; l < 4; ++l) {
+        umma::GemmArgs g{};
+        g.A = A;
+        g.lda = IN_DIM[l];
+        g.B = m->Wb[l];
+        g.ldb = IN_DIM[l];
+        g.M = n;
+        g.N = HID;
+        g.K = IN_DIM[l];
+        g.BN = HID;
+        g.epi = umma::EPI_BIAS_SILU;
+        g.bias = m->b[l];
+        g.Z = m->Z[l];
+        g.H = m->H[l];
+        g.ldz = HID;
+        g.err = m->errw;
+        CUM(launch_gemm(g, false, false, 1, s));
+        A = m->H[l];
+    }
+    return GF_OK;
+}
+
+int64_t nparams(int l) { return (int64_t)OUT_DIM[l] * IN_DIM[l]; }
+
+}  // namespace
+
+extern "C" {
+
+gf_status gf_gemm_bf16(const void *A, int64_t lda, int a_trans, const void *B, int64_t ldb, int b_trans, int M, int N,
+                       int K, float *C, int64_t ldc, int ksplit, void *cuda_stream)
+{
+    if (!A || !B || !C) return err(GF_ERR_ARG, "gf_gemm_bf16: NULL buffer");
+    if (M <= 0 || N <= 0 || K <= 0 || M % 16 || N % 16 || K % 16)
+        return err(GF_ERR_ARG, "gf_gemm_bf16: M, N, K must be positive multiples of 16");
+    if (ksplit < 1) ksplit = 1;
+    umma::GemmArgs g{};
+    g.A = (const bf16 *)A;
+    g.lda = lda;
+    g.B = (const bf16 *)B;
+    g.ldb = ldb;
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.BN = N < umma::BN_MAX ? N : umma::BN_MAX;
+    if (N > umma::BN_MAX && N % umma::BN_MAX) g.BN = 128;
+    g.epi = umma::EPI_F32;
+    g.C = C;
+    g.ldc = ldc;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (ksplit > 1) CUM(cudaMemsetAsync(C, 0, sizeof(float) * (size_t)M * ldc, s));
+    CUM(launch_gemm(g, a_trans != 0, b_trans != 0, ksplit, s));
+    return GF_OK;
+}
+
+gf_status gf_mlp_create(uint64_t seed, double c_tilde, gf_mlp_t *out)
+{
+    if (!out) return err(GF_ERR_ARG, "gf_mlp_create: out is NULL");
+    *out = nullptr;
+    gf_mlp_s *m = new gf_mlp_s();
+    m->ct = c_tilde > 0 ? c_tilde : 1.0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&m->nsm, cudaDevAttrMultiProcessorCount, dev);
+    // frequency vectors: (n1, n2) in {-1,0,1}^2, m3 in {0,1,2} without (0,0,0); then (+-2,0,0), (0,+-2,0), (0,0,3), (0,0,4)
+    int fr[32][3], nf = 0;
+    for (int m3 = 0; m3 <= 2; ++m3)
+        for (int n1 = -1; n1 <= 1; ++n1)
+            for (int n2 = -1; n2 <= 1; ++n2)
+                if (n1 || n2 || m3) {
+                    fr[nf][0] = n1;
+                    fr[nf][1] = n2;
+                    fr[nf][2] = m3;
+                    ++nf;
+                }
+    const int extra[6][3] = {{2, 0, 0}, {-2, 0, 0}, {0, 2, 0}, {0, -2, 0}, {0, 0, 3}, {0, 0, 4}};
+    for (int e = 0; e < 6; ++e, ++nf) memcpy(fr[nf], extra[e], sizeof(int) * 3);
+    gf_status s = GF_OK;
+    do {
+        cudaError_t e;
+        if ((e = cudaMemcpyToSymbol(c_freq, fr, sizeof(fr))) != cudaSuccess) {
+            s = err(GF_ERR_CUDA, "gf_mlp_create: %s", cudaGetErrorString(e));
+            break;
+        }
+        if ((e = cudaMalloc(&m->errw, sizeof(int))) != cudaSuccess || (e = cudaMalloc(&m->loss, sizeof(float))) != cudaSuccess) {
+            s = err(GF_ERR_NOMEM, "gf_mlp_create: cudaMalloc");
+            break;
+        }
+        cudaMemset(m->errw, 0, sizeof(int));
+        for (int l = 0; l < NL && s == GF_OK; ++l) {
+            size_t nw = nparams(l), nb = OUT_DIM[l];
+            float **f[8] = {&m->W[l], &m->mW[l], &m->vW[l], &m->gW[l], &m->b[l], &m->mb[l], &m->vb[l], &m->gb[l]};
+            size_t sz[8] = {nw, nw, nw, nw, nb, nb, nb, nb};
+            for (int q = 0; q < 8; ++q)
+                if (cudaMalloc(f[q], sizeof(float) * sz[q]) != cudaSuccess) s = err(GF_ERR_NOMEM, "gf_mlp_create: cudaMalloc");
+            if (s != GF_OK) break;
+            if (cudaMalloc(&m->Wb[l], sizeof(bf16) * nw) != cudaSuccess ||
+                cudaMalloc(&m->WTb[l], sizeof(bf16) * nw) != cudaSuccess) {
+                s = err(GF_ERR_NOMEM, "gf_mlp_create: cudaMalloc");
+                break;
+            }
+            for (int q = 1; q < 8; ++q)
+                if (q != 4) cudaMemset(*f[q], 0, sizeof(float) * sz[q]);
+            cudaMemset(m->b[l], 0, sizeof(float) * nb);
+            // uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights, zero biases
+            init_kernel<<<64, 256>>>(m->W[l], (int)nw, (float)(1.0 / sqrt((double)IN_DIM[l])), seed * 16 + l);
+            convert_kernel<<<64, 256>>>(m->W[l], m->Wb[l], m->WTb[l], OUT_DIM[l], IN_DIM[l]);
+            gf_count_launch(2);
+        }
+    } while (0);
+    if (s == GF_OK && cudaDeviceSynchronize() != cudaSuccess) s = err(GF_ERR_CUDA, "gf_mlp_create: init failed");
+    if (s != GF_OK) {
+        gf_mlp_destroy(m);
+        return s;
+    }
+    *out = m;
+    return GF_OK;
+}
+
+gf_status gf_mlp_set_scale(gf_mlp_t m, double scale)
+{
+    if (!m || !(scale > 0)) return err(GF_ERR_ARG, "gf_mlp_set_scale: bad argument");
+    m->scale = scale;
+    return GF_OK;
+}
+
+gf_status gf_mlp_params(gf_mlp_t m, float *host, int64_t count, int to_device)
+{
+    if (!m || !host) return err(GF_ERR_ARG, "gf_mlp_params: NULL argument");
+    int64_t need = 0;
+    for (int l = 0; l < NL; ++l) need += nparams(l) + OUT_DIM[l];
+    if (count < need) return err(GF_ERR_ARG, "gf_mlp_params: need %lld floats", (long long)need);
+    CUM(cudaDeviceSynchronize());
+    int64_t off = 0;
+    for (int l = 0; l < NL; ++l) {
+        size_t nw = nparams(l), nb = OUT_DIM[l];
+        if (to_device) {
+            CUM(cudaMemcpy(m->W[l], host + off, sizeof(float) * nw, cudaMemcpyHostToDevice));
+            CUM(cudaMemcpy(m->b[l], host + off + nw, sizeof(float) * nb, cudaMemcpyHostToDevice));
+            convert_kernel<<<64, 256>>>(m->W[l], m->Wb[l], m->WTb[l], OUT_DIM[l], IN_DIM[l]);
+            gf_count_launch(1);
+        } else {
+            CUM(cudaMemcpy(host + off, m->W[l], sizeof(float) * nw, cudaMemcpyDeviceToHost));
+            CUM(cudaMemcpy(host + off + nw, m->b[l], sizeof(float) * nb, cudaMemcpyDeviceToHost));
+        }
+        off += nw + nb;
+    }
+    CUM(cudaDeviceSynchronize());
+    return GF_OK;
+}
+
+int64_t gf_mlp_param_count(void)
+{
+    int64_t need = 0;
+    for (int l = 0; l < NL; ++l) need += nparams(l) + OUT_DIM[l];
+    return need;
+}
+
+gf_status gf_mlp_forward(gf_mlp_t m, const float *dev_in, int n, float *dev_out, void *cuda_stream)
+{
+    if (!m || n < 0 || (n > 0 && (!dev_in || !dev_out))) return err(GF_ERR_ARG, "gf_mlp_forward: bad argument");
+    if (n == 0) return GF_OK;
+    gf_status s = ensure_cap(m, n);
+    if (s != GF_OK) return s;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    CUM(cudaMemcpyAsync(m->in, dev_in, sizeof(float) * 6 * (size_t)n, cudaMemcpyDeviceToDevice, st));
+    if ((s = forward(m, n, st)) != GF_OK) return s;
+    head_fwd_kernel<<<m->nsm * 8, 256, 0, st>>>(m->H[3], m->W[4], m->b[4], dev_out, n, nullptr, nullptr, nullptr, 0.f);
+    gf_count_launch(1);
+    CUM(cudaGetLastError());
+    return GF_OK;
+}
+
+// Gradients of the mean-squared loss over one batch (into the grad buffers);
+// optionally followed by one Adam step.
+static gf_status train_or_grad(gf_mlp_t m, const float *dev_in, const float *dev_target, int n, float lr, int do_step,
+                               float *dev_loss, cudaStream_t st)
+{
+    gf_status s = ensure_cap(m, n);
+    if (s != GF_OK) return s;
+    CUM(cudaMemcpyAsync(m->in, dev_in, sizeof(float) * 6 * (size_t)n, cudaMemcpyDeviceToDevice, st));
+    for (int l = 0; l < NL; ++l) {
+        CUM(cudaMemsetAsync(m->gW[l], 0, sizeof(float) * nparams(l), st));
+        CUM(cudaMemsetAsync(m->gb[l], 0, sizeof(float) * OUT_DIM[l], st));
+    }
+    CUM(cudaMemsetAsync(m->loss, 0, sizeof(float), st));
+    if ((s = forward(m, n, st)) != GF_OK) return s;
+    const int blocks = m->nsm * 8;
+    head_fwd_kernel<<<blocks, 256, 0, st>>>(m->H[3], m->W[4], m->b[4], m->Y, n, dev_target, m->dY, m->loss, 1.f / n);
+    head_bwd_kernel<<<blocks, 256, 0, st>>>(m->dY, m->W[4], m->Z[3], m->dZ[3], n);
+    const int rpb = 64;
+    head_wgrad_kernel<<<(n + rpb - 1) / rpb, HID, 0, st>>>(m->dY, m->H[3], m->gW[4], m->gb[4], n, rpb);
+    gf_count_launch(3);
+    for (int l = 3; l >= 0; --l) {
+        // weight gradient gW_l = dZ_l^T . A_l  (A_0 = X0, A_l = H_{l-1}); reduction over the batch, split-K
+        umma::GemmArgs g{};
+        g.A = m->dZ[l];
+        g.lda = HID;
+        g.B = l == 0 ? m->X0 : m->H[l - 1];
+        g.ldb = IN_DIM[l];
+        g.M = HID;
+        g.N = IN_DIM[l];
+        g.K = n;
+        g.BN = IN_DIM[l];
+        g.epi = umma::EPI_F32;
+        g.C = m->gW[l];
+        g.ldc = IN_DIM[l];
+        g.err = m->errw;
+        int ks = n / 512 > 1 ? n / 512 : 1;
+        if (ks > 64) ks = 64;
+        CUM(launch_gemm(g, true, true, ks, st));
+        bias_grad_kernel<<<(n + rpb - 1) / rpb, HID, 0, st>>>(m->dZ[l], m->gb[l], n, rpb);
+        gf_count_launch(1);
+        if (l > 0) {
+            // dZ_{l-1} = (dZ_l . W_l) * silu'(Z_{l-1})
+            umma::GemmArgs h{};
+            h.A = m->dZ[l];
+            h.lda = HID;
+            h.B = m->WTb[l];
+            h.ldb = HID;
+            h.M = n;
+            h.N = IN_DIM[l];
+            h.K = HID;
+            h.BN = IN_DIM[l];
+            h.epi = umma::EPI_DSILU;
+            h.Zin = m->Z[l - 1];
+            h.dZ = m->dZ[l - 1];
+            h.ldz = HID;
+            h.err = m->errw;
+            CUM(launch_gemm(h, false, false, 1, st));
+        }
+    }
+    if (do_step) {
+        m->adam_t += 1;
+        const float b1 = 0.9f, b2 = 0.999f;
+        const float c1 = 1.f - powf(b1, (float)m->adam_t), c2 = 1.f - powf(b2, (float)m->adam_t);
+        for (int l = 0; l < NL; ++l) {
+            adam_kernel<<<256, 256, 0, st>>>(m->W[l], m->gW[l], m->mW[l], m->vW[l], (int)nparams(l), lr, b1, b2, 1e-8f, c1, c2);
+            adam_kernel<<<4, 256, 0, st>>>(m->b[l], m->gb[l], m->mb[l], m->vb[l], OUT_DIM[l], lr, b1, b2, 1e-8f, c1, c2);
+            convert_kernel<<<128, 256, 0, st>>>(m->W[l], m->Wb[l], m->WTb[l], OUT_DIM[l], IN_DIM[l]);
+            gf_count_launch(3);
+        }
+    }
+    if (dev_loss) CUM(cudaMemcpyAsync(dev_loss, m->loss, sizeof(float), cudaMemcpyDeviceToDevice, st));
+    CUM(cudaGetLastError());
+    return GF_OK;
+}
+
+gf_status gf_mlp_train_step(gf_mlp_t m, const float *dev_in, const float *dev_target, int n, float lr, float *dev_loss,
+                            void *cuda_stream)
+{
+    if (!m || n <= 0 || !dev_in || !dev_target) return err(GF_ERR_ARG, "gf_mlp_train_step: bad argument");
+    return train_or_grad(m, dev_in, dev_target, n, lr, 1, dev_loss, (cudaStream_t)cuda_stream);
+}
+
+gf_status gf_mlp_gradients(gf_mlp_t m, const float *dev_in, const float *dev_target, int n, float *host_grads,
+                           float *host_loss, void *cuda_stream)
+{
+    if (!m || n <= 0 || !dev_in || !dev_target || !host_grads) return err(GF_ERR_ARG, "gf_mlp_gradients: bad argument");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    gf_status s = train_or_grad(m, dev_in, dev_target, n, 0.f, 0, nullptr, st);
+    if (s != GF_OK) return s;
+    CUM(cudaStreamSynchronize(st));
+    int64_t off = 0;
+    for (int l = 0; l < NL; ++l) {
+        size_t nw = nparams(l), nb = OUT_DIM[l];
+        CUM(cudaMemcpy(host_grads + off, m->gW[l], sizeof(float) * nw, cudaMemcpyDeviceToHost));
+        CUM(cudaMemcpy(host_grads + off + nw, m->gb[l], sizeof(float) * nb, cudaMemcpyDeviceToHost));
+        off += nw + nb;
+    }
+    if (host_loss) CUM(cudaMemcpy(host_loss, m->loss, sizeof(float), cudaMemcpyDeviceToHost));
+    return GF_OK;
+}
+
+gf_status gf_mlp_error_word(gf_mlp_t m, int *out)
+{
+    if (!m || !out) return err(GF_ERR_ARG, "gf_mlp_error_word: NULL argument");
+    CUM(cudaMemcpy(out, m->errw, sizeof(int), cudaMemcpyDeviceToHost));
+    return *out ? GF_ERR_TIMEOUT : GF_OK;
+}
+
+gf_status gf_surrogate_eval(gf_mlp_t m, int npairs, const double *k, const double *alpha, const int64_t *offsets,
+                            const double *dev_xyz, void *dev_out, double wood_delta, const gf_trunc_t *trunc,
+                            int *n_fallback_pairs, void *cuda_stream)
+{
+    if (!m || npairs <= 0 || !k || !alpha || !offsets || (offsets[npairs] > 0 && (!dev_xyz || !dev_out)))
+        return err(GF_ERR_ARG, "gf_surrogate_eval: bad argument");
+    if (offsets[0] != 0) return err(GF_ERR_ARG, "gf_surrogate_eval: offsets[0] must be 0");
+    for (int p = 0; p < npairs; ++p)
+        if (offsets[p + 1] < offsets[p]) return err(GF_ERR_ARG, "gf_surrogate_eval: offsets must be non-decreasing");
+    gf_trunc_t tr;
+    gf_trunc_default(&tr);
+    if (trunc) tr = *trunc;
+    tr.precision = GF_FP64;
+    tr.kind = GF_HELMHOLTZ;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int64_t total = offsets[npairs];
+    if (total > 0x7fffffff) return err(GF_ERR_ARG, "gf_surrogate_eval: too many targets");
+    // Wood distance per pair: min_n | |alpha_n| - k |
+    std::vector<int> fallback(npairs, 0);
+    int nfb = 0;
+    for (int p = 0; p < npairs; ++p) {
+        const double a1 = alpha[2 * p], a2 = alpha[2 * p + 1], kk = k[p];
+        const int R = (int)ceil(kk) + 2;
+        double dmin = 1e300;
+        for (int n1 = -R - (int)fabs(a1); n1 <= R + (int)fabs(a1); ++n1)
+            for (int n2 = -R - (int)fabs(a2); n2 <= R + (int)fabs(a2); ++n2) {
+                double d = fabs(sqrt((a1 + n1) * (a1 + n1) + (a2 + n2) * (a2 + n2)) - kk);
+                dmin = d < dmin ? d : dmin;
+            }
+        if (dmin < wood_delta) {
+            fallback[p] = 1;
+            ++nfb;
+        }
+    }
+    if (n_fallback_pairs) *n_fallback_pairs = nfb;
+    // network pairs: per-target pair index and pair parameters
+    std::vector<int> pair_of((size_t)total);
+    std::vector<double> pk(3 * (size_t)npairs);
+    for (int p = 0; p < npairs; ++p) {
+        pk[3 * p] = alpha[2 * p];
+        pk[3 * p + 1] = alpha[2 * p + 1];
+        pk[3 * p + 2] = k[p];
+        for (int64_t i = offsets[p]; i < offsets[p + 1]; ++i) pair_of[i] = p;
+    }
+    if (total > 0) {
+        gf_status s = ensure_cap(m, (int)total);
+        if (s != GF_OK) return s;
+        int *d_pair = nullptr;
+        double *d_pk = nullptr;
+        CUM(cudaMalloc(&d_pair, sizeof(int) * total));
+        CUM(cudaMalloc(&d_pk, sizeof(double) * pk.size()));
+        CUM(cudaMemcpyAsync(d_pair, pair_of.data(), sizeof(int) * total, cudaMemcpyHostToDevice, st));
+        CUM(cudaMemcpyAsync(d_pk, pk.data(), sizeof(double) * pk.size(), cudaMemcpyHostToDevice, st));
+        const int blocks = m->nsm * 8;
+        surrogate_inputs_kernel<<<blocks, 256, 0, st>>>(dev_xyz, (int)total, d_pair, d_pk, m->in);
+        gf_count_launch(1);
+        if ((s = forward(m, (int)total, st)) != GF_OK) return s;
+        head_fwd_kernel<<<blocks, 256, 0, st>>>(m->H[3], m->W[4], m->b[4], m->Y, (int)total, nullptr, nullptr, nullptr,
+                                                 0.f);
+        surrogate_assemble_kernel<<<blocks, 256, 0, st>>>(dev_xyz, (int)total, d_pair, d_pk, m->Y, m->scale, tr.c,
+                                                          tr.eps, (double2 *)dev_out);
+        gf_count_launch(2);
+        CUM(cudaStreamSynchronize(st));
+        cudaFree(d_pair);
+        cudaFree(d_pk);
+    }
+    // FFT-path fallback near Wood anomalies: overwrite those pairs' rows
+    for (int p = 0; p < npairs; ++p) {
+        if (!fallback[p] || offsets[p + 1] == offsets[p]) continue;
+        const int M[3] = {128, 128, 64};
+        gf_plan_t pl = nullptr;
+        gf_status s = gf_plan(3, k[p], alpha + 2 * p, M, &tr, cuda_stream, &pl);
+        if (s != GF_OK) return s;
+        s = gf_eval_points(pl, dev_xyz + 3 * offsets[p], offsets[p + 1] - offsets[p], GF_OUT_GD,
+                           (double2 *)dev_out + offsets[p], cuda_stream);
+        CUM(cudaStreamSynchronize(st));
+        gf_destroy(pl);
+        if (s != GF_OK) return s;
+    }
+    return GF_OK;
+}
+
+gf_status gf_mlp_destroy(gf_mlp_t m)
+{
+    if (!m) return GF_OK;
+    cudaDeviceSynchronize();
+    auto fr = [](void *p) {
+        if (p) cudaFree(p);
+    };
+    for (int l = 0; l < NL; ++l) {
+        fr(m->W[l]);
+        fr(m->b[l]);
+        fr(m->mW[l]);
+        fr(m->vW[l]);
+        fr(m->mb[l]);
+        fr(m->vb[l]);
+        fr(m->gW[l]);
+        fr(m->gb[l]);
+        fr(m->Wb[l]);
+        fr(m->WTb[l]);
+    }
+    fr(m->X0);
+    fr(m->Y);
+    fr(m->dY);
+    fr(m->in);
+    fr(m->loss);
+    fr(m->errw);
+    for (int l = 0; l < 4; ++l) {
+        fr(m->Z[l]);
+        fr(m->H[l]);
+        fr(m->dZ[l]);
+    }
+    delete m;
+    return GF_OK;
+}
+
+}  // extern "C"

@@ -371,6 +371,12 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
         sa.a1 = a1;
         sa.a2 = a2;
         sa.ct = ct;
+        // smallest g with e^{-g c}/(2 g^2) < 1e-20 (the function decreases in g)
+        {
+            double g = 1.0;
+            while (exp(-g * c) / (2.0 * g * g) >= 1e-20) g += 0.25;
+            sa.gskip = g;
+        }
         sa.invV = dim == 3 ? 1.0 / (8.0 * GF_PI * GF_PI * ct) : 1.0 / (4.0 * GF_PI * ct);
         sa.tW = d_tW;
         sa.tt = d_tt;
@@ -511,7 +517,7 @@ gf_status gf_eval_points(gf_plan_t p, const double *dev_xyz, int64_t n, int whic
     if (n < 0 || n > (int64_t)0x7fffffff) return fail(GF_ERR_ARG, "gf_eval_points: n = %lld out of range", (long long)n);
     if (n == 0) return GF_OK;
     if (!dev_xyz || !dev_out) return fail(GF_ERR_ARG, "gf_eval_points: NULL buffer");
-    bool ok = (p->dim == 2 && which == GF_OUT_G) || (p->dim == 3 && p->kind == GF_HELMHOLTZ && which == GF_OUT_GD) ||
+    bool ok = (p->dim == 2 && which == GF_OUT_G) || (p->dim == 3 && p->kind == GF_HELMHOLTZ && (which == GF_OUT_GD || which == GF_OUT_LD)) ||
               (p->kind == GF_MAXWELL && (which == GF_OUT_MAXWELL6 || which == GF_OUT_MAXWELL7));
     if (!ok) return fail(GF_ERR_ARG, "gf_eval_points: output kind %d does not match the plan", which);
     std::lock_guard<std::mutex> lk(p->mu);
@@ -574,7 +580,7 @@ gf_status gf_plan_eval_args(gf_plan_t p, const double *dev_xyz, int64_t n, int w
     if (!p || !a_out) return fail(GF_ERR_ARG, "gf_eval_points_noalloc: NULL plan");
     if (n < 0) return fail(GF_ERR_ARG, "gf_eval_points_noalloc: n < 0");
     if (n > 0 && (!dev_xyz || !dev_out)) return fail(GF_ERR_ARG, "gf_eval_points_noalloc: NULL buffer");
-    bool ok = (p->dim == 2 && which == GF_OUT_G) || (p->dim == 3 && p->kind == GF_HELMHOLTZ && which == GF_OUT_GD) ||
+    bool ok = (p->dim == 2 && which == GF_OUT_G) || (p->dim == 3 && p->kind == GF_HELMHOLTZ && (which == GF_OUT_GD || which == GF_OUT_LD)) ||
               (p->kind == GF_MAXWELL && (which == GF_OUT_MAXWELL6 || which == GF_OUT_MAXWELL7));
     if (!ok) return fail(GF_ERR_ARG, "gf_eval_points_noalloc: output kind %d does not match the plan", which);
     EvalArgs a{};

@@ -98,6 +98,7 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
     for (int i = threadIdx.x; i < TJ * Q; i += blockDim.x) {
         int t = i / Q, m = i - t * Q;
         double2 b = betas[t];
+        if (b.y > a.gskip) continue;  // this column's X'-integrals are not used
         double tm = a.tt[m];
         double2 e;
         if (b.y == 0.0) {
@@ -121,20 +122,37 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
         double A2 = A2s[t];
         const double2 *Am = Av + t * Q;
         const double2 *Em = a.E + (size_t)b * Q;
-        // I1 = sum A conj(E), I2 = sum A E, from four real sums
-        double s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0;
-        for (int m = 0; m < Q; ++m) {
-            double2 A = Am[m], E = Em[m];
-            s1 = fma(A.x, E.x, s1);
-            s2 = fma(A.y, E.y, s2);
-            s3 = fma(A.x, E.y, s3);
-            s4 = fma(A.y, E.x, s4);
+        // T1 - T2 = I1/(2 beta (q - beta)) - I2/(2 beta (q + beta)), with
+        // I1 = sum A conj(E), I2 = sum A E (four real sums).  For evanescent
+        // beta = i g: |I1|, |I2| <= e^{-g c} (X' has total variation 1) and
+        // |2 beta (q -+ beta)| >= 2 g^2, so when e^{-g c}/(2 g^2) < 1e-20 (g > gskip)
+        // the two terms are below double rounding of C and are not formed; else
+        // T1 - T2 = [I1 (g - i q) + I2 (g + i q)] / (2 g (g^2 + q^2)).
+        double2 T12 = make_double2(0.0, 0.0);
+        if (beta.y <= a.gskip) {
+            double s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0;
+            for (int m = 0; m < Q; ++m) {
+                double2 A = Am[m], E = Em[m];
+                s1 = fma(A.x, E.x, s1);
+                s2 = fma(A.y, E.y, s2);
+                s3 = fma(A.x, E.y, s3);
+                s4 = fma(A.y, E.x, s4);
+            }
+            double2 I1 = make_double2(s1 + s2, s4 - s3);
+            double2 I2 = make_double2(s1 - s2, s3 + s4);
+            if (beta.y > 0.0) {
+                const double g = beta.y;
+                const double den = 1.0 / (2.0 * g * (g * g + q * q));
+                // I1 (g - i q) + I2 (g + i q)
+                T12.x = (g * (I1.x + I2.x) + q * (I1.y - I2.y)) * den;
+                T12.y = (g * (I1.y + I2.y) - q * (I1.x - I2.x)) * den;
+            } else {
+                double2 tb = cscale(beta, 2.0);
+                double2 T1 = cdiv(I1, cmul(tb, make_double2(q - beta.x, -beta.y)));
+                double2 T2 = cdiv(I2, cmul(tb, make_double2(q + beta.x, beta.y)));
+                T12 = csub(T1, T2);
+            }
         }
-        double2 I1 = make_double2(s1 + s2, s4 - s3);
-        double2 I2 = make_double2(s1 - s2, s3 + s4);
-        double2 tb = cscale(beta, 2.0);
-        double2 T1 = cdiv(I1, cmul(tb, make_double2(q - beta.x, -beta.y)));
-        double2 T2 = cdiv(I2, cmul(tb, make_double2(q + beta.x, beta.y)));
         double D = A2 + q * q - k2;
         double2 Cj;
         if (a.dim == 3) {
@@ -157,10 +175,11 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
             }
             double hr = fma(x, b1r, cc[0].x - b2r);
             double hi = fma(x, b1i, cc[0].y - b2i);
-            Cj = make_double2(hr / D + T1.x - T2.x, hi / D + T1.y - T2.y);
+            const double iD = 1.0 / D;
+            Cj = make_double2(fma(hr, iD, T12.x), fma(hi, iD, T12.y));
         } else {
             int jx = freq_of(col, a.M1);
-            double2 K = make_double2(1.0 / D + T1.x - T2.x, T1.y - T2.y);
+            double2 K = make_double2(1.0 / D + T12.x, T12.y);
             double eta2 = (double)jx * jx + q * q;
             double2 F1, F2;
             if (eta2 == 0.0) {

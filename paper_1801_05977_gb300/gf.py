@@ -17,8 +17,8 @@ GF_OK, GF_ERR_ARG, GF_ERR_WOOD, GF_ERR_RESONANCE, GF_ERR_NOMEM, GF_ERR_CUDA, GF_
 GF_FP64, GF_FP32_SPLIT = 0, 1
 GF_HELMHOLTZ, GF_MAXWELL = 0, 1
 GF_PERTURB_CTILDE, GF_FAIL = 0, 1
-GF_OUT_G, GF_OUT_GD, GF_OUT_MAXWELL6, GF_OUT_MAXWELL7 = 0, 1, 2, 3
-N_ENTRIES = {GF_OUT_G: 1, GF_OUT_GD: 1, GF_OUT_MAXWELL6: 6, GF_OUT_MAXWELL7: 7}
+GF_OUT_G, GF_OUT_GD, GF_OUT_MAXWELL6, GF_OUT_MAXWELL7, GF_OUT_LD = 0, 1, 2, 3, 4
+N_ENTRIES = {GF_OUT_G: 1, GF_OUT_GD: 1, GF_OUT_MAXWELL6: 6, GF_OUT_MAXWELL7: 7, GF_OUT_LD: 1}
 
 
 class GfError(RuntimeError):
@@ -46,7 +46,10 @@ EXPORTS = ["gf_trunc_default", "gf_plan", "gf_eval_grid", "gf_grid_bytes", "gf_e
            "gf_eval_points_host", "gf_plan_get_info", "gf_destroy", "gf_status_string", "gf_last_error",
            "gf_launch_count", "gf_set_phase_timing", "gf_plan_phase_ms", "gf_eval_points_noalloc",
            "gf_plan_batch", "gf_batch_synthesize", "gf_batch_eval_points", "gf_batch_autotune",
-           "gf_batch_get_tuning", "gf_batch_run_graph", "gf_batch_get_plan", "gf_batch_destroy"]
+           "gf_batch_get_tuning", "gf_batch_run_graph", "gf_batch_get_plan", "gf_batch_destroy",
+           "gf_gemm_bf16", "gf_mlp_create", "gf_mlp_param_count", "gf_mlp_params", "gf_mlp_set_scale",
+           "gf_mlp_forward", "gf_mlp_train_step", "gf_mlp_gradients", "gf_mlp_error_word", "gf_surrogate_eval",
+           "gf_mlp_destroy"]
 
 NOALLOC_MAX_TARGETS = 1 << 18
 
@@ -85,6 +88,17 @@ def lib(build_if_missing: bool = True):
     L.gf_batch_get_tuning.argtypes = [vp, P(ctypes.c_int)]
     L.gf_batch_get_plan.argtypes = [vp, i32, P(vp)]
     L.gf_batch_destroy.argtypes = [vp]
+    L.gf_gemm_bf16.argtypes = [vp, i64, i32, vp, i64, i32, i32, i32, i32, vp, i64, i32, vp]
+    L.gf_mlp_create.argtypes = [ctypes.c_uint64, d, P(vp)]
+    L.gf_mlp_param_count.restype = i64
+    L.gf_mlp_params.argtypes = [vp, vp, i64, i32]
+    L.gf_mlp_set_scale.argtypes = [vp, d]
+    L.gf_mlp_forward.argtypes = [vp, vp, i32, vp, vp]
+    L.gf_mlp_train_step.argtypes = [vp, vp, vp, i32, ctypes.c_float, vp, vp]
+    L.gf_mlp_gradients.argtypes = [vp, vp, vp, i32, vp, vp, vp]
+    L.gf_mlp_error_word.argtypes = [vp, P(ctypes.c_int)]
+    L.gf_surrogate_eval.argtypes = [vp, i32, P(d), P(d), P(ctypes.c_int64), vp, vp, d, P(Trunc), P(ctypes.c_int), vp]
+    L.gf_mlp_destroy.argtypes = [vp]
     L.gf_plan_get_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
     L.gf_destroy.argtypes = [vp]
     L.gf_status_string.argtypes = [i32]
@@ -96,7 +110,9 @@ def lib(build_if_missing: bool = True):
     for name in ("gf_trunc_default", "gf_plan", "gf_eval_grid", "gf_eval_points", "gf_eval_points_host",
                  "gf_eval_points_noalloc", "gf_plan_batch", "gf_batch_synthesize", "gf_batch_eval_points",
                  "gf_batch_autotune", "gf_batch_get_tuning", "gf_batch_run_graph", "gf_batch_get_plan",
-                 "gf_batch_destroy",
+                 "gf_batch_destroy", "gf_gemm_bf16", "gf_mlp_create", "gf_mlp_params", "gf_mlp_set_scale",
+                 "gf_mlp_forward", "gf_mlp_train_step", "gf_mlp_gradients", "gf_mlp_error_word",
+                 "gf_surrogate_eval", "gf_mlp_destroy",
                  "gf_plan_get_info", "gf_destroy", "gf_set_phase_timing", "gf_plan_phase_ms"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
@@ -277,6 +293,99 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             lib().gf_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gemm_bf16(A, B, a_trans=False, b_trans=False, ksplit=1, stream=None):
+    """C = A . B^T on the tensor cores: A (M, K) or its transpose (K, M), B (N, K)
+    or its transpose (K, N), bf16 CUDA tensors; returns fp32 (M, N)."""
+    import torch
+    M = A.shape[1] if a_trans else A.shape[0]
+    K = A.shape[0] if a_trans else A.shape[1]
+    N = B.shape[1] if b_trans else B.shape[0]
+    C = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    _check(lib().gf_gemm_bf16(ctypes.c_void_p(A.data_ptr()), A.stride(0), int(a_trans), ctypes.c_void_p(B.data_ptr()),
+                              B.stride(0), int(b_trans), M, N, K, ctypes.c_void_p(C.data_ptr()), C.stride(0),
+                              int(ksplit), _stream_ptr(stream)))
+    return C
+
+
+class MLP:
+    """The surrogate network (gf_mlp_*)."""
+
+    def __init__(self, seed: int = 0, c_tilde: float = 1.0):
+        h = ctypes.c_void_p()
+        _check(lib().gf_mlp_create(ctypes.c_uint64(seed), float(c_tilde), ctypes.byref(h)))
+        self._h = h
+        self.scale = 1.0
+
+    @staticmethod
+    def param_count() -> int:
+        return int(lib().gf_mlp_param_count())
+
+    def get_params(self) -> np.ndarray:
+        p = np.zeros(self.param_count(), dtype=np.float32)
+        _check(lib().gf_mlp_params(self._h, p.ctypes.data, p.size, 0))
+        return p
+
+    def set_params(self, p: np.ndarray):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(lib().gf_mlp_params(self._h, p.ctypes.data, p.size, 1))
+
+    def set_scale(self, s: float):
+        _check(lib().gf_mlp_set_scale(self._h, float(s)))
+        self.scale = s
+
+    def forward(self, inp, stream=None):
+        import torch
+        out = torch.empty((inp.shape[0], 2), dtype=torch.float32, device=inp.device)
+        _check(lib().gf_mlp_forward(self._h, ctypes.c_void_p(inp.data_ptr()), inp.shape[0],
+                                    ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        return out
+
+    def train_step(self, inp, target, lr: float, loss=None, stream=None):
+        _check(lib().gf_mlp_train_step(self._h, ctypes.c_void_p(inp.data_ptr()), ctypes.c_void_p(target.data_ptr()),
+                                       inp.shape[0], ctypes.c_float(lr),
+                                       ctypes.c_void_p(loss.data_ptr()) if loss is not None else None,
+                                       _stream_ptr(stream)))
+
+    def gradients(self, inp, target, stream=None):
+        g = np.zeros(self.param_count(), dtype=np.float32)
+        loss = ctypes.c_float()
+        _check(lib().gf_mlp_gradients(self._h, ctypes.c_void_p(inp.data_ptr()), ctypes.c_void_p(target.data_ptr()),
+                                      inp.shape[0], g.ctypes.data, ctypes.byref(loss), _stream_ptr(stream)))
+        return g, loss.value
+
+    def error_word(self) -> int:
+        v = ctypes.c_int()
+        lib().gf_mlp_error_word(self._h, ctypes.byref(v))
+        return v.value
+
+    def surrogate_eval(self, k, alpha, offsets, x, wood_delta=1e-2, trunc=None, stream=None):
+        import torch
+        k = np.ascontiguousarray(k, dtype=np.float64)
+        alpha = np.ascontiguousarray(alpha, dtype=np.float64).reshape(-1, 2)
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        out = torch.empty((x.shape[0],), dtype=torch.complex128, device=x.device)
+        nfb = ctypes.c_int()
+        if trunc is None:
+            trunc = trunc_default()
+        _check(lib().gf_surrogate_eval(self._h, k.shape[0], k.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                       alpha.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                       off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                       ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                       float(wood_delta), ctypes.byref(trunc), ctypes.byref(nfb), _stream_ptr(stream)))
+        return out, nfb.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().gf_mlp_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -1,0 +1,118 @@
+"""Tensor-core GEMM and the surrogate network's kernels.
+
+The GEMM is checked against torch's fp32 matmul of the same bf16 operands; the
+network's gradients against the FP64 NumPy reference (oracle/mlp.py) with the
+same bf16-rounded weights; training must reduce the loss; the surrogate must
+reproduce the FFT path on unseen (alpha, k) within its stated error, and its
+Wood-anomaly fallback must be the FFT path itself."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import mlp as R
+from paper_1801_05977_gb300 import gf
+from paper_1801_05977_gb300 import surrogate as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("M,N,K,at,bt,ks", [(128, 256, 64, False, False, 1), (256, 80, 80, False, False, 1),
+                                            (384, 256, 256, False, False, 1), (256, 256, 1024, True, True, 8),
+                                            (256, 80, 512, True, True, 4), (512, 256, 256, False, True, 1),
+                                            (128, 96, 48, True, False, 1)])
+def test_gemm_matches_torch(M, N, K, at, bt, ks):
+    g = torch.Generator(device="cuda").manual_seed(M + N + K)
+    A = torch.randn((K, M) if at else (M, K), device="cuda", generator=g).to(torch.bfloat16)
+    B = torch.randn((K, N) if bt else (N, K), device="cuda", generator=g).to(torch.bfloat16)
+    C = gf.gemm_bf16(A, B, a_trans=at, b_trans=bt, ksplit=ks)
+    Af = A.float().T if at else A.float()
+    Bf = B.float() if bt else B.float().T
+    ref = Af @ Bf
+    torch.cuda.synchronize()
+    err = (C - ref).abs().max().item() / ref.abs().max().item()
+    assert err < 1e-5, err
+
+
+def rand_inputs(n, seed):
+    rng = np.random.default_rng(seed)
+    inp = np.column_stack([rng.uniform(-np.pi, np.pi, (n, 2)), rng.uniform(-0.6, 0.6, n),
+                           rng.uniform(-0.5, 0.5, (n, 2)), rng.uniform(1, 4, n)]).astype(np.float32)
+    tgt = rng.standard_normal((n, 2)).astype(np.float32)
+    return inp, tgt
+
+
+def bf16_round(a):
+    return torch.from_numpy(np.asarray(a, np.float32)).to(torch.bfloat16).float().numpy()
+
+
+def test_gradients_match_fp64_reference():
+    mlp = gf.MLP(seed=3)
+    p = mlp.get_params()
+    # the network multiplies with bf16 copies of W1..W4 (W5 stays fp32): give the reference the same weights
+    Ws, bs = R.unpack(p)
+    pr = R.pack([bf16_round(W) for W in Ws[:4]] + [Ws[4]], bs)
+    inp, tgt = rand_inputs(512, 1)
+    g, loss = mlp.gradients(torch.from_numpy(inp).cuda(), torch.from_numpy(tgt).cuda())
+    lref, gref = R.loss_and_grad(pr, inp.astype(np.float64), tgt.astype(np.float64))
+    assert abs(loss - lref) < 2e-2 * lref
+    off = 0
+    for l in range(5):
+        n = R.DIMS[l + 1] * R.DIMS[l] + R.DIMS[l + 1]
+        a, b = g[off:off + n], gref[off:off + n]
+        e = np.abs(a - b).max() / np.abs(b).max()
+        assert e < 6e-2, (l, e)
+        off += n
+    assert mlp.error_word() == 0
+    mlp.close()
+
+
+def test_training_reduces_loss():
+    mlp = gf.MLP(seed=5)
+    inp, _ = rand_inputs(16384, 7)
+    # a smooth function of the inputs to learn
+    tg = np.column_stack([np.cos(inp[:, 0] + inp[:, 3]) * np.exp(-inp[:, 2] ** 2),
+                          np.sin(inp[:, 1]) * inp[:, 5] / 4]).astype(np.float32)
+    x, t = torch.from_numpy(inp).cuda(), torch.from_numpy(tg).cuda()
+    loss = torch.zeros(1, device="cuda")
+    first = None
+    for it in range(300):
+        b = (it % 8) * 2048
+        mlp.train_step(x[b:b + 2048], t[b:b + 2048], 2e-3, loss)
+        if it == 0:
+            torch.cuda.synchronize()
+            first = loss.item()
+    torch.cuda.synchronize()
+    assert loss.item() < 0.05 * first, (first, loss.item())
+    assert mlp.error_word() == 0
+    mlp.close()
+
+
+def test_surrogate_vs_fft_path_and_fallback():
+    inp, L, pairs = S.make_dataset(40, 4000, seed=1)
+    mlp = gf.MLP(seed=0)
+    hist = S.train(mlp, inp, L, epochs=6, batch=4096, lr=2e-3)
+    assert hist[-1] < hist[0]
+    # unseen pairs: surrogate G vs FFT-path G (double precision plans) at near points
+    test_pairs = np.array([[0.13, -0.27, 1.9], [-0.41, 0.08, 3.3]])
+    xs = [S.near_points(3000, seed=99 + i) for i in range(2)]
+    off = np.array([0, 3000, 6000], dtype=np.int64)
+    x = torch.from_numpy(np.concatenate(xs)).cuda()
+    G, nfb = mlp.surrogate_eval(test_pairs[:, 2], test_pairs[:, :2], off, x, wood_delta=1e-2)
+    torch.cuda.synchronize()
+    assert nfb == 0
+    for i in range(2):
+        p = gf.Plan(3, test_pairs[i, 2], tuple(test_pairs[i, :2]), S.grid_for(test_pairs[i, 2]))
+        ref = p.eval_points(x[off[i]:off[i + 1]], gf.GF_OUT_GD)[:, 0].cpu().numpy()
+        got = G[off[i]:off[i + 1]].cpu().numpy()
+        err = np.abs(got - ref).max() / np.abs(ref).max()
+        print(f"surrogate pair {i}: normwise error vs FFT path {err:.3e}")
+        assert err < 0.25
+    # Wood-near pair: routed to the FFT path, identical to it
+    k_w = np.hypot(0.1 + 1, 0.2) + 3e-3
+    G2, nfb2 = mlp.surrogate_eval([k_w], [[0.1, 0.2]], [0, 3000], x[:3000], wood_delta=1e-2)
+    assert nfb2 == 1
+    p = gf.Plan(3, k_w, (0.1, 0.2), (128, 128, 64))
+    ref = p.eval_points(x[:3000], gf.GF_OUT_GD)[:, 0].cpu().numpy()
+    assert np.abs(G2.cpu().numpy() - ref).max() / np.abs(ref).max() < 1e-11
+    mlp.close()
