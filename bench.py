@@ -288,6 +288,7 @@ def run_gpu(args):
     split_err = float(d.max() / out64.abs().max())
 
     batched = None if args.no_batch else run_batched(args, dev, flush)
+    surrogate = None if args.no_surrogate else run_surrogate(args, dev)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -319,6 +320,7 @@ def run_gpu(args):
         "e2e": {"value": world * n_targets / e2e_s, "unit": "evals/s",
                 "h2d_bytes_per_step": int(x_np.nbytes), "d2h_bytes_per_step": int(n_targets * 16)},
         "batched": batched,
+        "surrogate": surrogate,
         "gpu_launches": launches,
         "clocks": clocks,
         "cpu_baseline": cpu,
@@ -394,6 +396,94 @@ def run_batched(args, dev, flush):
             "setup_s": t_setup, "max_err_vs_sequential_normwise": d}
 
 
+def run_surrogate(args, dev):
+    """Learned surrogate: 5-layer BF16 MLP (tensor cores) trained on FFT-path
+    samples of the remainder for (alpha, k) in [-1/2, 1/2]^2 x [1, 4]; then
+    inference at near targets of many pairs with FFT-path fallback near Wood
+    anomalies, against the FFT path (batched sweep) on the same targets."""
+    import torch
+
+    from paper_1801_05977_gb300 import gf
+    from paper_1801_05977_gb300 import surrogate as S
+
+    t0 = time.perf_counter()
+    inp, L, _ = S.make_dataset(args.sur_train_pairs, args.sur_train_per_pair, seed=0)
+    t_data = time.perf_counter() - t0
+    mlp = gf.MLP(seed=0)
+    t0 = time.perf_counter()
+    hist = S.train(mlp, inp, L, epochs=args.sur_epochs, batch=8192, lr=2e-3, min_steps=args.sur_min_steps)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del inp, L
+    # inference workload: unseen pairs (another seed), near targets
+    npairs, per = args.sur_pairs, args.sur_per_pair
+    # unseen pairs clear of Wood anomalies by the fallback threshold: the network serves all of them
+    pr = W.sweep_pairs(npairs, seed=12345, kmin=1.0, kmax=4.0, wood_gap=1e-2)
+    k, al = pr[:, 2].copy(), pr[:, :2].copy()
+    x_np = np.concatenate([S.near_points(per, seed=777 + i) for i in range(npairs)])
+    off = np.arange(npairs + 1, dtype=np.int64) * per
+    x = torch.from_numpy(x_np).to(dev)
+    times = []
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        G, nfb = mlp.surrogate_eval(k, al, off, x, wood_delta=1e-2)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    t_sur = float(np.mean(times))
+    # the FFT path on the same targets: batched sweep (plans built, then one graph: synthesis + evaluation)
+    M = np.array([S.grid_for(v) for v in k], dtype=np.int32)
+    t0 = time.perf_counter()
+    batch = gf.Batch(k, al, M, precision=gf.GF_FP64)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    ref = torch.empty((x.shape[0], 1), dtype=torch.complex128, device=dev)
+    s = torch.cuda.Stream(device=dev)
+    ft = []
+    with torch.cuda.stream(s):
+        for i in range(args.warmup + args.steps):
+            s.synchronize()
+            t0 = time.perf_counter()
+            batch.run_graph(x, off, ref, gf.GF_OUT_GD, stream=s)
+            s.synchronize()
+            if i >= args.warmup:
+                ft.append(time.perf_counter() - t0)
+    t_fft = float(np.mean(ft))
+    g, r = G.cpu().numpy(), ref[:, 0].cpu().numpy()
+    errs = np.array([np.abs(g[off[i]:off[i + 1]] - r[off[i]:off[i + 1]]).max() / np.abs(r[off[i]:off[i + 1]]).max()
+                     for i in range(npairs)])
+    batch.close()
+    mlp.close()
+    # tensor-core GEMM of one hidden layer at inference size: (2^20 x 256) . (256 x 256)^T
+    A = torch.randn((1 << 20, 256), device=dev).to(torch.bfloat16)
+    Bm = torch.randn((256, 256), device=dev).to(torch.bfloat16)
+    gt = []
+    for i in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        gf.gemm_bf16(A, Bm)
+        e1.record()
+        torch.cuda.synchronize()
+        if i >= 2:
+            gt.append(e0.elapsed_time(e1))
+    gemm_ms = float(np.mean(gt))
+    gemm_tf = 2.0 * (1 << 20) * 256 * 256 / (gemm_ms * 1e-3) / 1e12
+    total = npairs * per
+    return {"value": total / t_sur, "unit": "evals/s", "s_per_call": t_sur, "pairs": npairs,
+            "gemm_bf16": {"shape": "M=2^20, N=256, K=256", "ms": gemm_ms, "tflops": gemm_tf},
+            "targets_per_pair": per, "targets": "near region |x3| <= c", "dtype": "bf16 weights, fp32 accumulation",
+            "fallback_pairs": nfb, "wood_delta": 1e-2,
+            "fft_path": {"value": total / t_fft, "s_per_call": t_fft, "setup_s": t_setup,
+                         "how": "batched sweep (graph) of FP64 plans on the same targets; setup excluded"},
+            "speedup_vs_fft_path": t_fft / t_sur,
+            "speedup_vs_fft_path_with_setup": (t_fft + t_setup) / t_sur,
+            "err_vs_fft_path_normwise": {"median": float(np.median(errs)), "p90": float(np.percentile(errs, 90)),
+                                         "max": float(errs.max())},
+            "training": {"samples": args.sur_train_pairs * args.sur_train_per_pair, "epochs": len(hist),
+                         "batch": 8192, "final_loss": hist[-1], "train_s": t_train, "data_s": t_data}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -411,6 +501,13 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-sweep leg")
     ap.add_argument("--batch-pairs", type=int, default=256)
     ap.add_argument("--batch-targets", type=int, default=100_000)
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate leg")
+    ap.add_argument("--sur-train-pairs", type=int, default=1000)
+    ap.add_argument("--sur-train-per-pair", type=int, default=10_000)
+    ap.add_argument("--sur-epochs", type=int, default=2)
+    ap.add_argument("--sur-min-steps", type=int, default=8000)
+    ap.add_argument("--sur-pairs", type=int, default=1000)
+    ap.add_argument("--sur-per-pair", type=int, default=10_000)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -2,8 +2,8 @@
 
 Plain double-precision forward and backward passes of the 5-layer MLP the
 library trains on the tensor cores: features cos/sin(n1 t1 + n2 t2 + m3 pi x3/c~)
-for 32 integer vectors (n1, n2, m3), 2 alpha1, 2 alpha2, (k - 2.5)/1.5, zero
-padding to 80; layers 80 -> 256 -> 256 -> 256 -> 256 -> 2 with SiLU between
+for 32 integer vectors (n1, n2, m3), 2 alpha1, 2 alpha2, (k - 2.5)/1.5, the
+in-cell distance r and 12 Gaussian shells exp(-((r - 0.15 j)/0.15)^2/2); layers 80 -> 256 -> 256 -> 256 -> 256 -> 2 with SiLU between
 them; loss sum (Y - T)^2 / (2n).  Parameters are flattened layer by layer as
 W [out][in] then b [out].  Written from the layer equations; shares no code
 with the CUDA library.  Its gradients are pinned against finite differences.
@@ -16,13 +16,16 @@ DIMS = [80, 256, 256, 256, 256, 2]
 
 
 def frequencies():
+    """The 32 feature vectors (n1, n2, m3): the 17 non-zero ones with n1, n2 in
+    {-1, 0, 1} and m3 in {0, 1} (m3 slowest, then n1, then n2), then 15 higher ones."""
     fr = []
-    for m3 in range(3):
+    for m3 in range(2):
         for n1 in (-1, 0, 1):
             for n2 in (-1, 0, 1):
                 if n1 or n2 or m3:
                     fr.append((n1, n2, m3))
-    fr += [(2, 0, 0), (-2, 0, 0), (0, 2, 0), (0, -2, 0), (0, 0, 3), (0, 0, 4)]
+    fr += [(0, 0, 2), (0, 0, 3), (2, 0, 0), (-2, 0, 0), (0, 2, 0), (0, -2, 0), (2, 0, 1), (0, 2, 1),
+           (3, 0, 0), (0, 3, 0), (-3, 0, 0), (0, -3, 0), (1, 1, 2), (-1, 1, 2), (2, 2, 0)]
     return np.array(fr, dtype=np.float64)
 
 
@@ -37,6 +40,10 @@ def features(inp: np.ndarray, c_tilde: float = 1.0) -> np.ndarray:
     X[:, 64] = 2 * a1
     X[:, 65] = 2 * a2
     X[:, 66] = (k - 2.5) / 1.5
+    r = np.sqrt(t1 * t1 + t2 * t2 + x3 * x3)
+    X[:, 67] = r
+    for j in range(12):
+        X[:, 68 + j] = np.exp(-0.5 * ((r - 0.15 * j) / 0.15) ** 2)
     return X
 
 

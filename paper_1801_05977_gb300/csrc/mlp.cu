@@ -6,8 +6,10 @@
 //
 // Network: 80 -> 256 -> 256 -> 256 -> 256 -> 2 (Re, Im of L_d / scale), SiLU
 // between layers.  Input features: cos and sin of n1 t1 + n2 t2 + m3 pi x3 / c~
-// for 32 fixed integer vectors (n1, n2, m3), then 2 alpha1, 2 alpha2,
-// (k - 2.5)/1.5, zero padding to 80.
+// for 32 fixed integer vectors (n1, n2, m3) (|n_i| <= 3, m3 <= 3), then
+// 2 alpha1, 2 alpha2, (k - 2.5)/1.5, then the in-cell distance r = |(t, x3)| and
+// 12 Gaussian shells of r (the remainder's main structure is radial: the
+// transition of the singular cutoff around the lattice point).
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -74,7 +76,14 @@ __global__ void features_kernel(const float *in, int n, bf16 *X0, float pi_ct)
         o[64] = __float2bfloat16(2.f * p[3]);
         o[65] = __float2bfloat16(2.f * p[4]);
         o[66] = __float2bfloat16((p[5] - 2.5f) / 1.5f);
-        for (int j = 67; j < K0; ++j) o[j] = __float2bfloat16(0.f);
+        // radial features of the in-cell distance to the lattice point: r and
+        // Gaussian shells exp(-((r - 0.15 j)/0.15)^2 / 2), j = 0..11
+        const float r = sqrtf(t1 * t1 + t2 * t2 + x3 * x3);
+        o[67] = __float2bfloat16(r);
+        for (int j = 0; j < 12; ++j) {
+            const float d = (r - 0.15f * j) * (1.f / 0.15f);
+            o[68 + j] = __float2bfloat16(__expf(-0.5f * d * d));
+        }
     }
 }
 
@@ -188,12 +197,27 @@ __global__ void init_kernel(float *W, int count, float bound, unsigned long long
         W[i] = (float)((2.0 * u01(seed, i) - 1.0) * bound);
 }
 
+// pair of target i from the offsets (largest p with off[p] <= i)
+__device__ __forceinline__ int pair_of_target(const int64_t *off, int np, int64_t i)
+{
+    int lo = 0, hi = np - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= i)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
 // Surrogate inputs of near targets: (t1, t2, x3, alpha1, alpha2, k) in float,
 // with the pair of each target from the offsets.
-__global__ void surrogate_inputs_kernel(const double *x, int n, const int *pair_of, const double *pk, float *in)
+__global__ void surrogate_inputs_kernel(const double *x, int n, int64_t base, const int64_t *off, int np,
+                                        const double *pk, float *in)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int p = pair_of[i];
+        const int p = pair_of_target(off, np, base + i);
         double t1 = x[3 * (size_t)i] - 2.0 * GF_PI * floor((x[3 * (size_t)i] + GF_PI) / (2.0 * GF_PI));
         double t2 = x[3 * (size_t)i + 1] - 2.0 * GF_PI * floor((x[3 * (size_t)i + 1] + GF_PI) / (2.0 * GF_PI));
         float *o = in + 6 * (size_t)i;
@@ -209,11 +233,12 @@ __global__ void surrogate_inputs_kernel(const double *x, int n, const int *pair_
 // G = e^{i2pi<alpha.m>} (e^{i alpha.t} L + e^{ikr} Y_eps(r)/(4 pi r)) for near targets
 // (L = scale * network output); far targets (|x3| > c) are outside the
 // surrogate's domain and get NaN.
-__global__ void surrogate_assemble_kernel(const double *x, int n, const int *pair_of, const double *pk,
-                                          const float *Y, double scale, double c, double eps, double2 *out)
+__global__ void surrogate_assemble_kernel(const double *x, int n, int64_t base, const int64_t *off, int np,
+                                          const double *pk, const float *Y, double scale, double c, double eps,
+                                          double2 *out)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int p = pair_of[i];
+        const int p = pair_of_target(off, np, base + i);
         const double a1 = pk[3 * p], a2 = pk[3 * p + 1], k = pk[3 * p + 2];
         const double x1 = x[3 * (size_t)i], x2 = x[3 * (size_t)i + 1], x3 = x[3 * (size_t)i + 2];
         if (!(fabs(x3) <= c)) {
@@ -388,9 +413,9 @@ gf_status gf_mlp_create(uint64_t seed, double c_tilde, gf_mlp_t *out)
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&m->nsm, cudaDevAttrMultiProcessorCount, dev);
-    // frequency vectors: (n1, n2) in {-1,0,1}^2, m3 in {0,1,2} without (0,0,0); then (+-2,0,0), (0,+-2,0), (0,0,3), (0,0,4)
+    // frequency vectors: (n1, n2) in {-1,0,1}^2, m3 in {0,1} without (0,0,0) (17 vectors), then 15 higher ones
     int fr[32][3], nf = 0;
-    for (int m3 = 0; m3 <= 2; ++m3)
+    for (int m3 = 0; m3 <= 1; ++m3)
         for (int n1 = -1; n1 <= 1; ++n1)
             for (int n2 = -1; n2 <= 1; ++n2)
                 if (n1 || n2 || m3) {
@@ -399,8 +424,9 @@ gf_status gf_mlp_create(uint64_t seed, double c_tilde, gf_mlp_t *out)
                     fr[nf][2] = m3;
                     ++nf;
                 }
-    const int extra[6][3] = {{2, 0, 0}, {-2, 0, 0}, {0, 2, 0}, {0, -2, 0}, {0, 0, 3}, {0, 0, 4}};
-    for (int e = 0; e < 6; ++e, ++nf) memcpy(fr[nf], extra[e], sizeof(int) * 3);
+    const int extra[15][3] = {{0, 0, 2}, {0, 0, 3}, {2, 0, 0}, {-2, 0, 0}, {0, 2, 0}, {0, -2, 0}, {2, 0, 1}, {0, 2, 1},
+                              {3, 0, 0}, {0, 3, 0}, {-3, 0, 0}, {0, -3, 0}, {1, 1, 2}, {-1, 1, 2}, {2, 2, 0}};
+    for (int e = 0; e < 15; ++e, ++nf) memcpy(fr[nf], extra[e], sizeof(int) * 3);
     gf_status s = GF_OK;
     do {
         cudaError_t e;
@@ -640,35 +666,37 @@ gf_status gf_surrogate_eval(gf_mlp_t m, int npairs, const double *k, const doubl
         }
     }
     if (n_fallback_pairs) *n_fallback_pairs = nfb;
-    // network pairs: per-target pair index and pair parameters
-    std::vector<int> pair_of((size_t)total);
+    // network pairs: pair parameters and offsets on the device
     std::vector<double> pk(3 * (size_t)npairs);
     for (int p = 0; p < npairs; ++p) {
         pk[3 * p] = alpha[2 * p];
         pk[3 * p + 1] = alpha[2 * p + 1];
         pk[3 * p + 2] = k[p];
-        for (int64_t i = offsets[p]; i < offsets[p + 1]; ++i) pair_of[i] = p;
     }
     if (total > 0) {
-        gf_status s = ensure_cap(m, (int)total);
+        // network activations are held for at most kChunk targets at a time
+        const int64_t kChunk = 1 << 20;
+        gf_status s = ensure_cap(m, (int)(total < kChunk ? total : kChunk));
         if (s != GF_OK) return s;
-        int *d_pair = nullptr;
+        int64_t *d_off = nullptr;
         double *d_pk = nullptr;
-        CUM(cudaMalloc(&d_pair, sizeof(int) * total));
+        CUM(cudaMalloc(&d_off, sizeof(int64_t) * (npairs + 1)));
         CUM(cudaMalloc(&d_pk, sizeof(double) * pk.size()));
-        CUM(cudaMemcpyAsync(d_pair, pair_of.data(), sizeof(int) * total, cudaMemcpyHostToDevice, st));
+        CUM(cudaMemcpyAsync(d_off, offsets, sizeof(int64_t) * (npairs + 1), cudaMemcpyHostToDevice, st));
         CUM(cudaMemcpyAsync(d_pk, pk.data(), sizeof(double) * pk.size(), cudaMemcpyHostToDevice, st));
         const int blocks = m->nsm * 8;
-        surrogate_inputs_kernel<<<blocks, 256, 0, st>>>(dev_xyz, (int)total, d_pair, d_pk, m->in);
-        gf_count_launch(1);
-        if ((s = forward(m, (int)total, st)) != GF_OK) return s;
-        head_fwd_kernel<<<blocks, 256, 0, st>>>(m->H[3], m->W[4], m->b[4], m->Y, (int)total, nullptr, nullptr, nullptr,
-                                                 0.f);
-        surrogate_assemble_kernel<<<blocks, 256, 0, st>>>(dev_xyz, (int)total, d_pair, d_pk, m->Y, m->scale, tr.c,
-                                                          tr.eps, (double2 *)dev_out);
-        gf_count_launch(2);
+        for (int64_t base = 0; base < total; base += kChunk) {
+            const int n = (int)(total - base < kChunk ? total - base : kChunk);
+            surrogate_inputs_kernel<<<blocks, 256, 0, st>>>(dev_xyz + 3 * base, n, base, d_off, npairs, d_pk, m->in);
+            gf_count_launch(1);
+            if ((s = forward(m, n, st)) != GF_OK) return s;
+            head_fwd_kernel<<<blocks, 256, 0, st>>>(m->H[3], m->W[4], m->b[4], m->Y, n, nullptr, nullptr, nullptr, 0.f);
+            surrogate_assemble_kernel<<<blocks, 256, 0, st>>>(dev_xyz + 3 * base, n, base, d_off, npairs, d_pk, m->Y,
+                                                              m->scale, tr.c, tr.eps, (double2 *)dev_out + base);
+            gf_count_launch(2);
+        }
         CUM(cudaStreamSynchronize(st));
-        cudaFree(d_pair);
+        cudaFree(d_off);
         cudaFree(d_pk);
     }
     // FFT-path fallback near Wood anomalies: overwrite those pairs' rows

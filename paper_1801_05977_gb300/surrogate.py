@@ -59,8 +59,9 @@ def make_dataset(n_pairs: int, per_pair: int, seed: int = 0, wood_gap: float = 1
 
 
 def train(mlp: "gf.MLP", inp: np.ndarray, L: np.ndarray, epochs: int = 8, batch: int = 8192, lr: float = 2e-3,
-          seed: int = 0, log=None):
-    """Adam on mean-squared error of L / scale; cosine learning-rate decay."""
+          seed: int = 0, log=None, min_steps: int = 0):
+    """Adam on mean-squared error of L / scale; cosine learning-rate decay.
+    At least `min_steps` optimizer steps are taken (epochs are extended)."""
     import torch
 
     scale = float(np.sqrt(np.mean(np.abs(L) ** 2)))
@@ -74,6 +75,7 @@ def train(mlp: "gf.MLP", inp: np.ndarray, L: np.ndarray, epochs: int = 8, batch:
     tgt = torch.from_numpy(tg[perm]).cuda()
     loss = torch.zeros(1, dtype=torch.float32, device="cuda")
     nb = inp.shape[0] // batch
+    epochs = max(epochs, -(-min_steps // nb))
     total = epochs * nb
     it = 0
     hist = []

@@ -89,9 +89,9 @@ def test_training_reduces_loss():
 
 
 def test_surrogate_vs_fft_path_and_fallback():
-    inp, L, pairs = S.make_dataset(40, 4000, seed=1)
+    inp, L, pairs = S.make_dataset(160, 8000, seed=1)
     mlp = gf.MLP(seed=0)
-    hist = S.train(mlp, inp, L, epochs=6, batch=4096, lr=2e-3)
+    hist = S.train(mlp, inp, L, epochs=1, batch=4096, lr=2e-3, min_steps=5000)
     assert hist[-1] < hist[0]
     # unseen pairs: surrogate G vs FFT-path G (double precision plans) at near points
     test_pairs = np.array([[0.13, -0.27, 1.9], [-0.41, 0.08, 3.3]])

@@ -19,7 +19,9 @@ def test_features_layout():
     assert fr.shape == (32, 3) and len({tuple(f) for f in fr}) == 32 and not (fr == 0).all(1).any()
     ph = fr[5, 0] * 0.3 + fr[5, 1] * -1.2 + fr[5, 2] * np.pi * 0.4
     assert abs(X[0, 10] - np.cos(ph)) < 1e-15 and abs(X[0, 11] - np.sin(ph)) < 1e-15
-    assert X[0, 64] == 0.2 and X[0, 65] == -0.4 and abs(X[0, 66] - 1 / 3) < 1e-15 and (X[0, 67:] == 0).all()
+    assert X[0, 64] == 0.2 and X[0, 65] == -0.4 and abs(X[0, 66] - 1 / 3) < 1e-15
+    r = np.sqrt(0.3**2 + 1.2**2 + 0.4**2)
+    assert abs(X[0, 67] - r) < 1e-15 and abs(X[0, 68 + 8] - np.exp(-0.5 * ((r - 1.2) / 0.15) ** 2)) < 1e-15
 
 
 def test_gradients_match_finite_differences():
