@@ -289,6 +289,7 @@ def run_gpu(args):
 
     batched = None if args.no_batch else run_batched(args, dev, flush)
     surrogate = None if args.no_surrogate else run_surrogate(args, dev)
+    configs = None if args.no_configs else run_configs(args, dev, flush)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -321,6 +322,7 @@ def run_gpu(args):
                 "h2d_bytes_per_step": int(x_np.nbytes), "d2h_bytes_per_step": int(n_targets * 16)},
         "batched": batched,
         "surrogate": surrogate,
+        "other_configs": configs,
         "gpu_launches": launches,
         "clocks": clocks,
         "cpu_baseline": cpu,
@@ -484,6 +486,62 @@ def run_surrogate(args, dev):
                          "batch": 8192, "final_loss": hist[-1], "train_s": t_train, "data_s": t_data}}
 
 
+def run_configs(args, dev, flush):
+    """The other configurations, one plan + evaluation per step (device time):
+    2D G (k = 1.3, alpha = 0.2, 64 x 64, 1e4 targets, complex128) and the Maxwell
+    tensor (k = 2.5, alpha = (0.1, 0.3), 256 x 256 x 64, six entries, float bulk
+    with double singular part; 1e6 targets, 10% clustered within 0.05 of lattice
+    points; its error stated against the double-precision path on the GPU)."""
+    import torch
+
+    from paper_1801_05977_gb300 import gf
+
+    def timed(mk, x, which, steps, warm, out):
+        ts, ph = [], []
+        for i in range(warm + steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            p = mk()
+            p.eval_points_into(x, out, which)
+            e1.record()
+            torch.cuda.synchronize()
+            if i >= warm:
+                ts.append(e0.elapsed_time(e1))
+                ph.append(p.phase_ms())
+            p.close()
+        return float(np.mean(ts)), ph
+
+    res = {}
+    x2 = torch.from_numpy(W.targets_2d(10_000, seed=0)).to(dev)
+    o2 = torch.empty((10_000, 1), dtype=torch.complex128, device=dev)
+    ms, ph = timed(lambda: gf.Plan(2, 1.3, (0.2,), (64, 64)), x2, gf.GF_OUT_G, args.steps, args.warmup, o2)
+    res["2d_G"] = {"workload": "2D quasi-periodic G, k=1.3, alpha=0.2, grid 64x64, 1e4 uniform targets",
+                   "value": 1e4 / (ms * 1e-3), "unit": "evals/s", "ms_per_step": ms, "dtype": "f64",
+                   "phases_ms": {"synthesis": float(np.mean([p[0] for p in ph])), "near": float(np.mean([p[2] for p in ph])),
+                                 "far": float(np.mean([p[3] for p in ph]))}}
+    x3 = torch.from_numpy(W.targets_3d_clustered(1_000_000, seed=0)).to(dev)
+    o32 = torch.empty((1_000_000, 6), dtype=torch.complex64, device=dev)
+    ms32, ph32 = timed(lambda: gf.Plan(3, 2.5, (0.1, 0.3), (256, 256, 64), precision=gf.GF_FP32_SPLIT,
+                                       kind=gf.GF_MAXWELL), x3, gf.GF_OUT_MAXWELL6, args.steps, args.warmup, o32)
+    o64 = torch.empty((1_000_000, 6), dtype=torch.complex128, device=dev)
+    ms64, ph64 = timed(lambda: gf.Plan(3, 2.5, (0.1, 0.3), (256, 256, 64), kind=gf.GF_MAXWELL), x3,
+                       gf.GF_OUT_MAXWELL6, 1, 1, o64)
+    d = (o32.to(torch.complex128) - o64).abs()
+    err = float((d.max(dim=0).values / o64.abs().max(dim=0).values).max())
+    res["maxwell"] = {"workload": "Maxwell tensor (6 entries), k=2.5, alpha=(0.1,0.3), grid 256x256x64, 1e6 targets, "
+                                  "10% clustered within 0.05 of lattice points",
+                      "value": 1e6 / (ms32 * 1e-3), "unit": "evals/s (tensor = 6 entries)", "ms_per_step": ms32,
+                      "dtype": "f32/f64 split", "max_entry_err_vs_fp64_normwise": err,
+                      "phases_ms": {"synthesis": float(np.mean([p[0] for p in ph32])),
+                                    "near": float(np.mean([p[2] for p in ph32])),
+                                    "far": float(np.mean([p[3] for p in ph32]))},
+                      "fp64": {"value": 1e6 / (ms64 * 1e-3), "ms_per_step": ms64,
+                               "phases_ms": {"synthesis": ph64[0][0], "near": ph64[0][2], "far": ph64[0][3]}}}
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -502,6 +560,7 @@ def main():
     ap.add_argument("--batch-pairs", type=int, default=256)
     ap.add_argument("--batch-targets", type=int, default=100_000)
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate leg")
+    ap.add_argument("--no-configs", action="store_true", help="skip the 2D and Maxwell configurations")
     ap.add_argument("--sur-train-pairs", type=int, default=1000)
     ap.add_argument("--sur-train-per-pair", type=int, default=10_000)
     ap.add_argument("--sur-epochs", type=int, default=2)
