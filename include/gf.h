@@ -257,7 +257,8 @@ int64_t gf_mlp_param_count(void);
 gf_status gf_mlp_params(gf_mlp_t mlp, float *host, int64_t count, int to_device);
 /* Scale of the targets: the network learns L_d / scale. */
 gf_status gf_mlp_set_scale(gf_mlp_t mlp, double scale);
-/* Forward pass of n samples (device pointers), output float [n][2]. */
+/* Forward pass of n samples (device pointers), output float [n][2]: one fused
+ * persistent tensor-core kernel (activations stay on chip). */
 gf_status gf_mlp_forward(gf_mlp_t mlp, const float *dev_in, int n, float *dev_out, void *cuda_stream);
 /* One Adam step (lr; beta 0.9/0.999) on the mean-squared loss
  * sum (Y - T)^2 / (2n) of one batch (targets float [n][2]); the batch loss is

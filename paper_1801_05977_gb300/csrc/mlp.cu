@@ -268,6 +268,212 @@ __global__ void surrogate_assemble_kernel(const double *x, int n, int64_t base, 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Fused inference: all five layers of the network for 2 x 128 rows per
+// iteration of a persistent CTA (one per SM).  The two 128 x 256 bf16
+// activation tiles stay in shared memory (canonical K-major layout), the two
+// 128 x 256 fp32 accumulators in tensor memory (all 512 columns); each
+// layer's weights stream through two 256 x 64 stages; the epilogue applies
+// bias + SiLU and writes the next layer's input back into shared memory; the
+// 256 -> 2 head is folded into the last epilogue.  HBM traffic per sample:
+// 6 input floats and 2 output floats.
+// ---------------------------------------------------------------------------
+namespace fused {
+constexpr int ROWS = 128, NT = 2;
+constexpr int ACT_BYTES = ROWS * HID * 2;                // 64 KiB per tile
+constexpr int WST_BYTES = HID * umma::KC * 2;           // 32 KiB per weight stage
+constexpr int SMEM = NT * ACT_BYTES + 2 * WST_BYTES + 64 + NT * ROWS * 2 * 4;
+constexpr int TMEM_COLS = 512;
+
+// act tile: [r/8][k/8] core matrices, 32 K-blocks per row group (LBO 128 B, SBO 4096 B)
+__device__ __forceinline__ uint32_t act_off(int r, int k) { return ((r >> 3) * (HID / 8) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2; }
+
+struct Args {
+    const float *in;
+    int n;
+    float pi_ct;
+    const bf16 *W[4];
+    const float *b[4];
+    const float *W5, *b5;
+    float *Y;
+    int *err;
+};
+}  // namespace fused
+
+__global__ void __launch_bounds__(256, 1) mlp_infer_fused(fused::Args A)
+{
+    using namespace fused;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t *act[NT] = {smem, smem + ACT_BYTES};
+    uint8_t *wst[2] = {smem + NT * ACT_BYTES, smem + NT * ACT_BYTES + WST_BYTES};
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + NT * ACT_BYTES + 2 * WST_BYTES);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
+    float *yhalf = reinterpret_cast<float *>(tslot + 2);  // [NT][ROWS][2] head partial sums of the second column half
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // 8 warps: warp w reads TMEM lanes 32 (w % 4) .. +31 (its rows) and the column half w / 4
+    const int quarter = warp & 3, half = warp >> 2;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(umma::smem_u32(tslot)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(umma::smem_u32(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(umma::smem_u32(&mbar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *tslot;
+    const uint32_t idesc = umma::make_idesc(ROWS, HID);
+    int g = 0;  // weight stages used so far (stage g & 1, use g >> 1)
+    bool ok = true;
+    for (int tp = blockIdx.x; tp * (NT * ROWS) < A.n && ok; tp += gridDim.x) {
+        const int row0 = tp * NT * ROWS;
+        // features of 256 rows into the first 80 columns of the activation tiles
+        for (int q = threadIdx.x; q < NT * ROWS; q += blockDim.x) {
+            const int t = q / ROWS, r = q % ROWS, i = row0 + q;
+            const bool live = i < A.n;
+            float t1 = 0.f, t2 = 0.f, x3 = 0.f, p3 = 0.f, p4 = 0.f, p5 = 2.5f;
+            if (live) {
+                const float *p = A.in + 6 * (size_t)i;
+                t1 = p[0];
+                t2 = p[1];
+                x3 = p[2];
+                p3 = p[3];
+                p4 = p[4];
+                p5 = p[5];
+            }
+            const float rr = sqrtf(t1 * t1 + t2 * t2 + x3 * x3);
+            // ten blocks of 8 features: blocks 0..7 hold cos/sin of 4 frequencies each
+            for (int kb = 0; kb < K0 / 8; ++kb) {
+                float v[8];
+                if (kb < 8) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int j = kb * 4 + u;
+                        // |phase| < 30: the fast sine/cosine error (~1e-5 there) is far below bf16 rounding
+                        const float ph = c_freq[j][0] * t1 + c_freq[j][1] * t2 + c_freq[j][2] * A.pi_ct * x3;
+                        __sincosf(ph, &v[2 * u + 1], &v[2 * u]);
+                    }
+                } else if (kb == 8) {
+                    v[0] = 2.f * p3;
+                    v[1] = 2.f * p4;
+                    v[2] = (p5 - 2.5f) / 1.5f;
+                    v[3] = rr;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const float d = (rr - 0.15f * u) * (1.f / 0.15f);
+                        v[4 + u] = __expf(-0.5f * d * d);
+                    }
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const float d = (rr - 0.15f * (4 + u)) * (1.f / 0.15f);
+                        v[u] = __expf(-0.5f * d * d);
+                    }
+                }
+                __align__(16) bf16 hv[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) hv[e] = __float2bfloat16(live ? v[e] : 0.f);
+                *reinterpret_cast<uint4 *>(act[t] + act_off(r, kb * 8)) = *reinterpret_cast<const uint4 *>(hv);
+            }
+        }
+        for (int l = 0; l < 4 && ok; ++l) {
+            const int K = l == 0 ? K0 : HID;
+            const int nch = (K + umma::KC - 1) / umma::KC;
+            for (int c = 0; c < nch; ++c, ++g) {
+                const int buf = g & 1;
+                if (g >= 2) ok = __syncthreads_and(umma::mbar_wait(umma::smem_u32(&mbar[buf]), ((g - 2) >> 1) & 1)) != 0;
+                if (!ok) break;
+                umma::load_stage<false>(wst[buf], A.W[l], K, 0, HID, HID, c * umma::KC, K);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const int ksteps = (min(umma::KC, K - c * umma::KC) + 15) / 16;
+                    const uint32_t b0 = umma::smem_u32(wst[buf]);
+                    for (int t = 0; t < NT; ++t) {
+                        const uint32_t a0 = umma::smem_u32(act[t]);
+                        for (int kk = 0; kk < ksteps; ++kk) {
+                            const uint64_t ad = umma::make_desc(a0 + (c * 8 + kk * 2) * 128, 128, (HID / 8) * 128);
+                            const uint64_t bd = umma::make_desc(b0 + kk * 256, 128, (umma::KC / 8) * 128);
+                            const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
+                            asm volatile(
+                                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + t * HID),
+                                "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                        }
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        umma::smem_u32(&mbar[buf])));
+                }
+            }
+            if (!ok) break;
+            // the layer's last commit covers all its MMAs
+            const int gl = g - 1;
+            ok = __syncthreads_and(umma::mbar_wait(umma::smem_u32(&mbar[gl & 1]), (gl >> 1) & 1)) != 0;
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const float *bias = A.b[l];
+            for (int t = 0; t < NT; ++t) {
+                const int r = quarter * 32 + lane;
+                float y0 = 0.f, y1 = 0.f;
+                for (int j = half * (HID / 2); j < (half + 1) * (HID / 2); j += 16) {
+                    uint32_t v[16];
+                    const uint32_t taddr = tmem + t * HID + ((uint32_t)(quarter * 32) << 16) + (uint32_t)j;
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                          "=r"(v[15])
+                        : "r"(taddr));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    __align__(16) bf16 h[16];
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        const float z = __bfloat162float(__float2bfloat16(__uint_as_float(v[e]) + bias[j + e]));
+                        h[e] = __float2bfloat16(__fdividef(z, 1.f + __expf(-z)));
+                        if (l == 3) {
+                            const float hf = __bfloat162float(h[e]);
+                            y0 = fmaf(hf, A.W5[j + e], y0);
+                            y1 = fmaf(hf, A.W5[HID + j + e], y1);
+                        }
+                    }
+                    if (l < 3) {
+                        *reinterpret_cast<uint4 *>(act[t] + act_off(r, j)) = *reinterpret_cast<const uint4 *>(h);
+                        *reinterpret_cast<uint4 *>(act[t] + act_off(r, j + 8)) = *reinterpret_cast<const uint4 *>(h + 8);
+                    }
+                }
+                if (l == 3 && half == 1) {
+                    yhalf[(t * ROWS + r) * 2] = y0;
+                    yhalf[(t * ROWS + r) * 2 + 1] = y1;
+                }
+                if (l == 3) __syncwarp();
+                if (l == 3) {
+                    // combine the two column halves (second half parked in shared memory)
+                    __syncthreads();
+                    const int i = row0 + t * ROWS + r;
+                    if (half == 0 && i < A.n) {
+                        A.Y[2 * (size_t)i] = y0 + yhalf[(t * ROWS + r) * 2] + A.b5[0];
+                        A.Y[2 * (size_t)i + 1] = y1 + yhalf[(t * ROWS + r) * 2 + 1] + A.b5[1];
+                    }
+                    __syncthreads();
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            // the next layer's MMAs read the tiles written above and overwrite the accumulators
+        }
+    }
+    if (!ok && threadIdx.x == 0 && A.err) atomicExch(A.err, 1);
+    // bounded wait for anything still in flight before freeing tensor memory
+    if (g > 0) __syncthreads_and(umma::mbar_wait(umma::smem_u32(&mbar[(g - 1) & 1]), ((g - 1) >> 1) & 1));
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+}
+
 }  // namespace
 
 struct gf_mlp_s {
@@ -373,6 +579,30 @@ gf_status forward(gf_mlp_t m, int n, cudaStream_t s)
 }
 
 int64_t nparams(int l) { return (int64_t)OUT_DIM[l] * IN_DIM[l]; }
+
+// inference of n samples whose float inputs are in m->in, output float [n][2]
+gf_status infer(gf_mlp_t m, int n, float *Y, cudaStream_t s)
+{
+    fused::Args A{};
+    A.in = m->in;
+    A.n = n;
+    A.pi_ct = (float)(GF_PI / m->ct);
+    for (int l = 0; l < 4; ++l) {
+        A.W[l] = m->Wb[l];
+        A.b[l] = m->b[l];
+    }
+    A.W5 = m->W[4];
+    A.b5 = m->b[4];
+    A.Y = Y;
+    A.err = m->errw;
+    CUM(cudaFuncSetAttribute(mlp_infer_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, fused::SMEM));
+    int tiles = (n + fused::NT * fused::ROWS - 1) / (fused::NT * fused::ROWS);
+    int grid = tiles < m->nsm ? tiles : m->nsm;
+    mlp_infer_fused<<<grid, 256, fused::SMEM, s>>>(A);
+    gf_count_launch(1);
+    CUM(cudaGetLastError());
+    return GF_OK;
+}
 
 }  // namespace
 
@@ -516,11 +746,7 @@ gf_status gf_mlp_forward(gf_mlp_t m, const float *dev_in, int n, float *dev_out,
     if (s != GF_OK) return s;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     CUM(cudaMemcpyAsync(m->in, dev_in, sizeof(float) * 6 * (size_t)n, cudaMemcpyDeviceToDevice, st));
-    if ((s = forward(m, n, st)) != GF_OK) return s;
-    head_fwd_kernel<<<m->nsm * 8, 256, 0, st>>>(m->H[3], m->W[4], m->b[4], dev_out, n, nullptr, nullptr, nullptr, 0.f);
-    gf_count_launch(1);
-    CUM(cudaGetLastError());
-    return GF_OK;
+    return infer(m, n, dev_out, st);
 }
 
 // Gradients of the mean-squared loss over one batch (into the grad buffers);
@@ -689,11 +915,10 @@ gf_status gf_surrogate_eval(gf_mlp_t m, int npairs, const double *k, const doubl
             const int n = (int)(total - base < kChunk ? total - base : kChunk);
             surrogate_inputs_kernel<<<blocks, 256, 0, st>>>(dev_xyz + 3 * base, n, base, d_off, npairs, d_pk, m->in);
             gf_count_launch(1);
-            if ((s = forward(m, n, st)) != GF_OK) return s;
-            head_fwd_kernel<<<blocks, 256, 0, st>>>(m->H[3], m->W[4], m->b[4], m->Y, n, nullptr, nullptr, nullptr, 0.f);
+            if ((s = infer(m, n, m->Y, st)) != GF_OK) return s;
             surrogate_assemble_kernel<<<blocks, 256, 0, st>>>(dev_xyz + 3 * base, n, base, d_off, npairs, d_pk, m->Y,
                                                               m->scale, tr.c, tr.eps, (double2 *)dev_out + base);
-            gf_count_launch(2);
+            gf_count_launch(1);
         }
         CUM(cudaStreamSynchronize(st));
         cudaFree(d_off);
