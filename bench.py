@@ -561,6 +561,22 @@ def run_configs(args, dev, flush):
     return res
 
 
+def run_mlp_forward(args):
+    """Profiling helper: two fused forward passes of the surrogate network on
+    `mlp_forward_only` random samples."""
+    import torch
+
+    from paper_1801_05977_gb300 import gf
+
+    mlp = gf.MLP(seed=1)
+    x = torch.rand((args.mlp_forward_only, 6), device="cuda")
+    for _ in range(2):
+        mlp.forward(x)
+    torch.cuda.synchronize()
+    mlp.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -580,6 +596,7 @@ def main():
     ap.add_argument("--batch-targets", type=int, default=100_000)
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate leg")
     ap.add_argument("--no-configs", action="store_true", help="skip the 2D and Maxwell configurations")
+    ap.add_argument("--mlp-forward-only", type=int, default=0, help="profiling: only run the fused network forward")
     ap.add_argument("--sur-train-pairs", type=int, default=1000)
     ap.add_argument("--sur-train-per-pair", type=int, default=10_000)
     ap.add_argument("--sur-epochs", type=int, default=2)
@@ -589,6 +606,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mlp_forward_only:
+        return run_mlp_forward(args)
     return run_gpu(args)
 
 

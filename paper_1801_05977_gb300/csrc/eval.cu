@@ -617,7 +617,6 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count)
         FarLane L = far_lane(a, w * 32 + lane, count);
         const double R2m = warp_max(L.R2);
         const float R2f = (float)L.R2;
-        const double Rm = sqrt(R2m);
         // core disk of the warp: b z_min <= Y0
         const double iz = L.valid ? 1.0 / L.z : 0.0;
         const double izmax = warp_max(iz);
@@ -650,24 +649,30 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count)
                 }
             }
         }
-        const int n1a = max(a.n1lo, (int)floor(-a.a1 - Rm) - 1), n1b = min(a.n1hi, (int)ceil(-a.a1 + Rm) + 1);
+        // Row bounds and the core segment are index ranges: they are formed in
+        // float with a one-index margin (every lane still keeps exactly its own
+        // truncation set; the core/tail split only moves terms of size ~e^-18
+        // between double and float).
+        const float R2mf = (float)R2m, Rc2f = (float)Rc2, a1f = (float)a.a1;
+        const float Rmf = sqrtf(R2mf);
+        const int n1a = max(a.n1lo, (int)floorf(-a1f - Rmf) - 1), n1b = min(a.n1hi, (int)ceilf(-a1f + Rmf) + 1);
         for (int n1 = n1a; n1 <= n1b; ++n1) {
-            const double c1 = a.a1 + n1;
-            const double rem = R2m - c1 * c1;
-            if (rem < 0.0) continue;
-            const double sr = sqrt(rem);
-            const int n2a = max(a.n2lo, (int)floor(-a.a2 - sr)), n2b = min(a.n2hi, (int)ceil(-a.a2 + sr));
-            if (n2a > n2b) continue;
-            const BetaEntry *row = tab + (size_t)(n1 - a.n1lo) * W2 - a.n2lo;
-            const float c1f = (float)c1;
+            const float c1f = a1f + (float)n1;
             const float c1sq = c1f * c1f;
+            const float remf = R2mf - c1sq;
+            if (remf < -1.0f) continue;
+            const float srf = sqrtf(fmaxf(remf, 0.f));
+            const int n2a = max(a.n2lo, (int)floorf(-a2f - srf) - 1), n2b = min(a.n2hi, (int)ceilf(-a2f + srf) + 1);
+            if (n2a > n2b) continue;
+            const double c1 = a.a1 + n1;
+            const BetaEntry *row = tab + (size_t)(n1 - a.n1lo) * W2 - a.n2lo;
             // core segment [ca, cb] of this row (empty when ca > cb)
             int ca = n2b + 1, cb = n2b;
-            const double remc = Rc2 - c1 * c1;
-            if (remc >= 0.0) {
-                const double src = sqrt(remc);
-                ca = max(n2a, (int)ceil(-a.a2 - src));
-                cb = min(n2b, (int)floor(-a.a2 + src));
+            const float remc = Rc2f - c1sq;
+            if (remc >= 0.f) {
+                const float src = sqrtf(remc);
+                ca = max(n2a, (int)ceilf(-a2f - src));
+                cb = min(n2b, (int)floorf(-a2f + src));
                 if (ca > cb) {
                     ca = n2b + 1;
                     cb = n2b;
@@ -786,7 +791,6 @@ __device__ void far3d_f32_chunk(const EvalArgs &a, int w, int count)
         FarLane L = far_lane(a, w * 32 + lane, count);
         const double R2m = warp_max(L.R2);
         const float R2f = (float)L.R2;
-        const double Rm = sqrt(R2m);
         const float z = (float)L.z, t1 = (float)L.t1, t2 = (float)L.t2, sg = (float)L.sg;
         float sv, cv;
         sincosf(t2, &sv, &cv);
@@ -816,17 +820,19 @@ __device__ void far3d_f32_chunk(const EvalArgs &a, int w, int count)
                 }
             }
         }
-        const int n1a = max(a.n1lo, (int)floor(-a.a1 - Rm) - 1), n1b = min(a.n1hi, (int)ceil(-a.a1 + Rm) + 1);
+        // row bounds in float with a one-index margin (lanes mask their own sets)
+        const float R2mf = (float)R2m, a1f = (float)a.a1;
+        const float Rmf = sqrtf(R2mf);
+        const int n1a = max(a.n1lo, (int)floorf(-a1f - Rmf) - 1), n1b = min(a.n1hi, (int)ceilf(-a1f + Rmf) + 1);
         for (int n1 = n1a; n1 <= n1b; ++n1) {
-            const double c1d = a.a1 + n1;
-            const double rem = R2m - c1d * c1d;
-            if (rem < 0.0) continue;
-            const double sr = sqrt(rem);
-            const int n2a = max(a.n2lo, (int)floor(-a.a2 - sr)), n2b = min(a.n2hi, (int)ceil(-a.a2 + sr));
+            const float c1 = a1f + (float)n1;
+            const float c1sq = c1 * c1;
+            const float remf = R2mf - c1sq;
+            if (remf < -1.0f) continue;
+            const float srf = sqrtf(fmaxf(remf, 0.f));
+            const int n2a = max(a.n2lo, (int)floorf(-a2f - srf) - 1), n2b = min(a.n2hi, (int)ceilf(-a2f + srf) + 1);
             if (n2a > n2b) continue;
             const BetaEntryF *row = tab + (size_t)(n1 - a.n1lo) * W2 - a.n2lo;
-            const float c1 = (float)c1d;
-            const float c1sq = c1 * c1;
             float c2 = a2f + (float)n2b;
             float h[NF == 1 ? 1 : 6][2];
 #pragma unroll

@@ -180,6 +180,8 @@ struct EvalBatch {
 cudaError_t gf_launch_synth(const SynthArgs &a, int precision, cudaStream_t s);
 cudaError_t gf_launch_extract(const SynthArgs &a, int precision, void *dev_out, cudaStream_t s);
 void gf_synth_config(SynthArgs &a, int precision, int tj_max, size_t smem[3]);
+cudaError_t gf_launch_cheb_table(const double *rr, const double2 *B, int Q, int npan, int deg, double w, double2 *out,
+                                 cudaStream_t s);
 cudaError_t gf_launch_synth_batch(const SynthBatch &b, int precision, cudaStream_t s);
 cudaError_t gf_launch_eval_batch(const EvalBatch &b, int precision, cudaStream_t s);
 cudaError_t gf_launch_beta_table(const EvalArgs &a, int precision, cudaStream_t s);

@@ -280,37 +280,13 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
     const int hdeg = 14;
     const double hpan = 2.0;
     int hnpan = 1;
-    std::vector<double2> hcheb;
+    // (computed on the device from the quadrature tables, see gf_launch_cheb_table)
+    size_t hcheb_n = 0;
     if (dim == 3) {
         double m1 = fabs(a1) + M[0] / 2 + 1, m2 = fabs(a2) + M[1] / 2 + 1, m3 = (M[2] / 2 + 1) * GF_PI / ct;
         double smax = sqrt(m1 * m1 + m2 * m2 + m3 * m3) + hpan;
         hnpan = (int)ceil(smax / hpan) + 1;
-        hcheb.assign((size_t)hnpan * (hdeg + 1), make_double2(0, 0));
-        const int nn = hdeg + 1;
-        std::vector<double2> fv(nn);
-        for (int pn = 0; pn < hnpan; ++pn) {
-            double cen = (pn + 0.5) * hpan, hh = 0.5 * hpan;
-            for (int kk = 0; kk < nn; ++kk) {
-                double s = cen + hh * cos(GF_PI * (kk + 0.5) / nn);
-                double hr = 0.0, hi = 0.0;
-                for (int m = 0; m < Q; ++m) {
-                    double ker = (s == 0.0) ? rr[m] : sin(s * rr[m]) / s;
-                    hr += B[m].x * ker;
-                    hi += B[m].y * ker;
-                }
-                fv[kk] = make_double2(hr, hi);
-            }
-            for (int jj = 0; jj < nn; ++jj) {
-                double cr = 0.0, ci = 0.0;
-                for (int kk = 0; kk < nn; ++kk) {
-                    double w = cos(GF_PI * jj * (kk + 0.5) / nn);
-                    cr += fv[kk].x * w;
-                    ci += fv[kk].y * w;
-                }
-                double sc = (jj == 0 ? 1.0 : 2.0) / nn;
-                hcheb[(size_t)pn * nn + jj] = make_double2(cr * sc, ci * sc);
-            }
-        }
+        hcheb_n = (size_t)hnpan * (hdeg + 1);
     }
     double F10 = 0.0;
     if (dim == 2) {
@@ -327,7 +303,7 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
     // ---- device memory
     const size_t nodes_padded = (size_t)p->P1 * p->P2 * p->P3;
     p->grid_bytes = nodes_padded * p->nf * p->elem;
-    const size_t tab_bytes = sizeof(double) * 5 * Q + sizeof(double2) * (Q + E.size() + hcheb.size());
+    const size_t tab_bytes = sizeof(double) * 5 * Q + sizeof(double2) * (Q + E.size() + hcheb_n);
     const size_t ncells = (size_t)p->M[0] * p->M[1] * p->M[2];
     const size_t work_bytes = ncells * p->nf * p->elem;
     void *work = nullptr;
@@ -344,16 +320,21 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
         char *tb = (char *)p->tables;
         double *d_tt = (double *)tb, *d_tW = d_tt + Q, *d_rr = d_tW + Q, *d_P0 = d_rr + Q, *d_P1 = d_P0 + Q;
         double2 *d_B = (double2 *)(d_P1 + Q), *d_E = d_B + Q, *d_H = d_E + E.size();
-        if ((e = cudaMemcpy(d_tt, tt.data(), sizeof(double) * Q, cudaMemcpyHostToDevice)) != cudaSuccess ||
-            (e = cudaMemcpy(d_tW, tW.data(), sizeof(double) * Q, cudaMemcpyHostToDevice)) != cudaSuccess ||
-            (e = cudaMemcpy(d_rr, rr.data(), sizeof(double) * Q, cudaMemcpyHostToDevice)) != cudaSuccess ||
-            (e = cudaMemcpy(d_P0, P0.data(), sizeof(double) * Q, cudaMemcpyHostToDevice)) != cudaSuccess ||
-            (e = cudaMemcpy(d_P1, P1.data(), sizeof(double) * Q, cudaMemcpyHostToDevice)) != cudaSuccess ||
-            (e = cudaMemcpy(d_B, B.data(), sizeof(double2) * Q, cudaMemcpyHostToDevice)) != cudaSuccess ||
-            (e = cudaMemcpy(d_E, E.data(), sizeof(double2) * E.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
-            (!hcheb.empty() &&
-             (e = cudaMemcpy(d_H, hcheb.data(), sizeof(double2) * hcheb.size(), cudaMemcpyHostToDevice)) !=
-                 cudaSuccess)) {
+        // one upload of the packed host tables (same layout as on the device)
+        std::vector<char> pack((char *)d_H - tb);
+        {
+            char *hb = pack.data();
+            memcpy(hb + ((char *)d_tt - tb), tt.data(), sizeof(double) * Q);
+            memcpy(hb + ((char *)d_tW - tb), tW.data(), sizeof(double) * Q);
+            memcpy(hb + ((char *)d_rr - tb), rr.data(), sizeof(double) * Q);
+            memcpy(hb + ((char *)d_P0 - tb), P0.data(), sizeof(double) * Q);
+            memcpy(hb + ((char *)d_P1 - tb), P1.data(), sizeof(double) * Q);
+            memcpy(hb + ((char *)d_B - tb), B.data(), sizeof(double2) * Q);
+            memcpy(hb + ((char *)d_E - tb), E.data(), sizeof(double2) * E.size());
+        }
+        if ((e = cudaMemcpyAsync(tb, pack.data(), pack.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+            (hcheb_n && (e = gf_launch_cheb_table(d_rr, d_B, Q, hnpan, hdeg, hpan, d_H, st)) != cudaSuccess) ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess) {
             st_err = fail(GF_ERR_CUDA, "gf_plan: table upload: %s", cudaGetErrorString(e));
             break;
         }

@@ -505,6 +505,47 @@ cudaError_t gf_launch_synth(const SynthArgs &a, int precision, cudaStream_t s)
     return precision == GF_FP64 ? launch_synth_t<double>(a, s) : launch_synth_t<float>(a, s);
 }
 
+namespace {
+// Piecewise Chebyshev interpolant of h(s) = sum_m B_m sin(s r_m)/s: one CTA per
+// panel [p w, (p+1) w]; values at the nn Chebyshev points, then the discrete
+// cosine transform to coefficients.
+__global__ void cheb_table_kernel(const double *rr, const double2 *B, int Q, int nn, double w, double2 *out)
+{
+    __shared__ double2 fv[64];
+    const int p = blockIdx.x, k = threadIdx.x;
+    const double cen = (p + 0.5) * w, hh = 0.5 * w;
+    if (k < nn) {
+        const double s = cen + hh * cospi((k + 0.5) / nn);
+        double hr = 0.0, hi = 0.0;
+        for (int m = 0; m < Q; ++m) {
+            const double ker = (s == 0.0) ? rr[m] : sin(s * rr[m]) / s;
+            hr = fma(B[m].x, ker, hr);
+            hi = fma(B[m].y, ker, hi);
+        }
+        fv[k] = make_double2(hr, hi);
+    }
+    __syncthreads();
+    if (k < nn) {
+        double cr = 0.0, ci = 0.0;
+        for (int q = 0; q < nn; ++q) {
+            const double c = cospi((double)k * (q + 0.5) / nn);
+            cr = fma(fv[q].x, c, cr);
+            ci = fma(fv[q].y, c, ci);
+        }
+        const double sc = (k == 0 ? 1.0 : 2.0) / nn;
+        out[(size_t)p * nn + k] = make_double2(cr * sc, ci * sc);
+    }
+}
+}  // namespace
+
+cudaError_t gf_launch_cheb_table(const double *rr, const double2 *B, int Q, int npan, int deg, double w, double2 *out,
+                                 cudaStream_t s)
+{
+    cheb_table_kernel<<<npan, 64, 0, s>>>(rr, B, Q, deg + 1, w, out);
+    gf_count_launch(1);
+    return cudaGetLastError();
+}
+
 void gf_synth_config(SynthArgs &a, int precision, int tj_max, size_t smem[3])
 {
     if (precision == GF_FP64)
