@@ -295,9 +295,17 @@ typedef struct {
 } gf_plan_info_t;
 gf_status gf_plan_get_info(gf_plan_t plan, gf_plan_info_t *info);
 
-/* Release the plan and its device memory (synchronises the device first).
- * NULL is accepted. */
+/* Release the plan (synchronises the device first).  NULL is accepted.  Its
+ * device buffers go back to the library's memory pool, which keeps freed
+ * memory reserved so that the next plan's allocations do not reach the driver
+ * (plans and their evaluation scratch are allocated stream-ordered from this
+ * pool on the stream passed to gf_plan / gf_eval_points). */
 gf_status gf_destroy(gf_plan_t plan);
+
+/* Return the memory the library's pool holds for the current device and no
+ * live plan uses to the driver (synchronises the device).  GF_ERR_CUDA on a
+ * driver error. */
+gf_status gf_release_memory(void);
 
 /* Static description of a status code. */
 const char *gf_status_string(gf_status s);

@@ -69,6 +69,19 @@ __device__ __forceinline__ double2 lattice_phase(double a1, double m1, double a2
 
 __device__ __forceinline__ void store_out(double2 *o, double2 v) { *o = v; }
 __device__ __forceinline__ void store_out(float2 *o, double2 v) { *o = make_float2((float)v.x, (float)v.y); }
+__device__ __forceinline__ void add_out(double2 *o, double2 v)
+{
+    atomicAdd(&o->x, v.x);
+    atomicAdd(&o->y, v.y);
+}
+__device__ __forceinline__ void add_out(float2 *o, double2 v)
+{
+    atomicAdd(&o->x, (float)v.x);
+    atomicAdd(&o->y, (float)v.y);
+}
+template <typename R> __device__ __forceinline__ typename cplx_t<R>::T zero_c();
+template <> __device__ __forceinline__ double2 zero_c<double>() { return make_double2(0.0, 0.0); }
+template <> __device__ __forceinline__ float2 zero_c<float>() { return make_float2(0.f, 0.f); }
 
 template <typename R> __device__ __forceinline__ typename cplx_t<R>::T nan_c();
 template <> __device__ __forceinline__ double2 nan_c<double>() { return make_double2(CUDART_NAN, CUDART_NAN); }
@@ -134,9 +147,14 @@ __device__ void near3d_tiles(const EvalArgs &a, int64_t base0, int64_t stride, i
             valid = false;
         }
         push_far(isfar, (int)i, a.far_idx, a.far_count);
-        if (isfar) atomicAdd(&hist[far_bucket(fabs(x3), a.c)], 1);
-        if (!valid || isfar) continue;
         C *o = out + i * ne;
+        if (isfar) {
+            // the far kernel adds its row slabs into these entries
+            atomicAdd(&hist[far_bucket(fabs(x3), a.c)], 1);
+            for (int e = 0; e < ne; ++e) o[e] = zero_c<R>();
+            continue;
+        }
+        if (!valid) continue;
         if (!finite) {
             for (int e = 0; e < ne; ++e) o[e] = nan_c<R>();
             continue;
@@ -400,14 +418,14 @@ __global__ void __launch_bounds__(256) far_scatter_batch(const EvalArgs *args, i
 }
 
 // ---------------------------------------------------------------------------
-// Far-series tables.  beta_table: |beta_n| and 1/|beta_n| for evanescent n
+// Far-series tables: |beta_n|, ln|beta_n| and 1/|beta_n| for evanescent n
 // (beta_n = i |beta_n|); zeros for propagating n, whose terms are summed from
 // the short list PropEntry instead.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void set_entry(BetaEntry &e, double b, double ib)
 {
     e.b = b;
-    e.ib = ib;
+    e.lnb = b > 0.0 ? log(b) : 0.0;
     e.bl2 = (float)(b * 1.4426950408889634);  // b log2(e)
     e.ibf = (float)ib;
     e.bf = (float)b;
@@ -421,8 +439,12 @@ __device__ __forceinline__ void set_entry(BetaEntryF &e, double b, double ib)
     e.pad = 0.f;
 }
 
+// Series tables of a 3D plan, built on the device: the b table over the index
+// box, the exponential table e^{-(j - j0)/128}, and (block 0, warp 0) the list
+// of propagating indices in row-major order of the sub-box pbox = [n1lo, n1hi,
+// n2lo, n2hi] (ballot compaction keeps the order fixed).
 template <typename E>
-__global__ void beta_table(EvalArgs a, E *tab)
+__global__ void series_tables(EvalArgs a, E *tab, double *exptab, PropEntry *prop, int *nprop, int4 pbox)
 {
     const int W2 = a.n2hi - a.n2lo + 1;
     const int tot = (a.n1hi - a.n1lo + 1) * W2;
@@ -439,6 +461,31 @@ __global__ void beta_table(EvalArgs a, E *tab)
         }
         tab[i] = e;
     }
+    if (exptab)
+        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.exptab_n; j += gridDim.x * blockDim.x)
+            exptab[j] = exp(-(double)(j - a.exptab_j0) * 0.0078125);
+    if (blockIdx.x == 0 && threadIdx.x < 32) {
+        const int pw = pbox.w - pbox.z + 1, ptot = (pbox.y - pbox.x + 1) * pw;
+        int cnt = 0;
+        for (int base = 0; base < ptot; base += 32) {
+            const int i = base + (int)threadIdx.x;
+            bool in = false;
+            double c1 = 0, c2 = 0, aa = 0;
+            if (i < ptot) {
+                c1 = a.a1 + (pbox.x + i / pw);
+                c2 = a.a2 + (pbox.z + i % pw);
+                aa = sqrt(c1 * c1 + c2 * c2);
+                in = aa <= a.k;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, in);
+            if (in) {
+                const double br = sqrt((a.k - aa) * (a.k + aa));
+                prop[cnt + __popc(bal & ((1u << threadIdx.x) - 1u))] = PropEntry{c1, c2, br, 1.0 / br};
+            }
+            cnt += __popc(bal);
+        }
+        if (threadIdx.x == 0) *nprop = cnt;
+    }
 }
 
 __device__ __forceinline__ double warp_max(double v)
@@ -447,24 +494,28 @@ __device__ __forceinline__ double warp_max(double v)
     return v;
 }
 
-// e^{-y} for y >= 0 by Tang's table-driven method (ACM TOMS 15, 1989):
-// y = j/64 + r with j = rint(64 y) and |r| <= 1/128; e^{-y} = T[j] e^{-r}, with
-// T[j] = e^{-j/64} a plan table and e^{-r} its Taylor polynomial of degree 6
-// (truncation below 2.5e-19 relative).  j is clamped to the table; callers
-// discard terms whose y lies beyond it.
-__device__ __forceinline__ double exp_neg_tab(double y, const double *__restrict__ T, int jmax)
+// e^{-y} by Tang's table-driven method (ACM TOMS 15, 1989): y = j/128 + r with
+// j = rint(128 y) and |r| <= 1/256; e^{-y} = T[j + j0] e^{-r}, T[i] = e^{-(i - j0)/128}
+// a plan table.  Returns e^{-r} (its Taylor polynomial of degree 5, truncation
+// below 5e-18 relative) and the table index, clamped to the table; callers
+// discard the terms whose y lies beyond it.
+__device__ __forceinline__ double exp_neg_split(double y, int j0, int jmax, int &idx)
 {
     const double MAGIC = 6755399441055744.0;  // 1.5 * 2^52: rint by addition
-    double t = fma(y, 64.0, MAGIC);
-    int j = __double2loint(t);
-    double r = fma(t - MAGIC, -0.015625, y);
-    double p = fma(r, 1.0 / 720.0, -1.0 / 120.0);
-    p = fma(p, r, 1.0 / 24.0);
+    const double t = fma(y, 128.0, MAGIC);
+    idx = min(max(__double2loint(t) + j0, 0), jmax);
+    const double r = fma(t - MAGIC, -0.0078125, y);
+    double p = fma(r, -1.0 / 120.0, 1.0 / 24.0);
     p = fma(p, r, -1.0 / 6.0);
     p = fma(p, r, 0.5);
     p = fma(p, r, -1.0);
-    p = fma(p, r, 1.0);
-    return __ldg(T + min(j, jmax)) * p;
+    return fma(p, r, 1.0);
+}
+
+// x with its sign bit flipped where m = 0x80000000 (an integer operation).
+__device__ __forceinline__ double flip_sign(double x, int m)
+{
+    return __hiloint2double(__double2hiint(x) ^ m, __double2loint(x));
 }
 
 __device__ __forceinline__ float ex2_approx(float x)
@@ -501,41 +552,79 @@ __device__ __forceinline__ FarLane far_lane(const EvalArgs &a, int slot, int cou
     return L;
 }
 
-// Horner sums of one row segment n2 = hi, hi-1, ..., lo (double precision):
-// acc[e] = sum_{n2} w_e(n2) v^{n2-lo}; NH = 1 (G_d) or 6 (Maxwell partial sums
-// A = sum ib e, B = sum c2 ib e, C = sum c2^2 ib e, D = sum b e, E = sum e,
-// F = sum c2 e, with e = e^{-b z} on the lane's own truncation set).
-template <int NH>
-__device__ __forceinline__ void seg_horner_f64(const BetaEntry *__restrict__ row, int lo, int hi, double a2,
-                                               float c1sq, float a2f, float R2f, double z, double cv, double sv,
-                                               const double *__restrict__ T, int jmax, double acc[NH][2])
+// Per-lane constants of Reinsch's form of the Clenshaw recurrence for the row
+// sums sum_{k>=0} w_k e^{ik theta}, theta = t2, real weights w_k:
+//   s = sign(cos theta), lambda = 2 cos theta - 2 s (-4 sin^2(theta/2) or 4 cos^2(theta/2)),
+//   d_k = w_k + lambda b_{k+1} + s d_{k+1},  b_k = d_k + s b_{k+1},
+//   sum = d_0 - (lambda/2) b_1 + i b_1 sin theta,  b_1 = s (b_0 - d_0).
+// Unlike the plain three-term recurrence it keeps its accuracy for theta near
+// 0 and pi (C. Reinsch, 1967; error analysis by Gentleman, Comput. J. 12, 1969).
+struct Reinsch {
+    double lam, hlam, sv;
+    int m;  // sign bit of s
+};
+
+__device__ __forceinline__ Reinsch reinsch_lane(double theta, double sv, double cv)
 {
+    Reinsch R;
+    double sh, ch;
+    sincos(0.5 * theta, &sh, &ch);
+    R.m = cv >= 0.0 ? 0 : (int)0x80000000;
+    R.lam = cv >= 0.0 ? -4.0 * sh * sh : 4.0 * ch * ch;
+    R.hlam = 0.5 * R.lam;
+    R.sv = sv;
+    return R;
+}
+
+// Row segment n2 = hi, hi-1, ..., lo in double precision, anchored at lo:
+// acc[e] = sum_{n2} w_e(n2) e^{i (n2 - lo) theta}, weights on the lane's own
+// truncation set.  NH = 1 (G_d): w = e^{-bz}/b.  NH = 6 (Maxwell partial sums):
+// A = sum w, B = sum c2 w, C = sum c2^2 w, D = sum b^2 w, E = sum b w, F = sum c2 b w.
+// Per term and sum the recurrence costs three FP64 operations; for NH = 1 the
+// product T[j] e^{-r} is folded into the first of them.
+template <int NH>
+__device__ __forceinline__ void seg_sum_f64(const BetaEntry *__restrict__ row, int lo, int hi, double a2,
+                                            float c1sq, float a2f, float R2f, double z, const Reinsch &RS,
+                                            const double *__restrict__ T, int j0, int jmax, double acc[NH][2])
+{
+    double d[NH], bb[NH];
 #pragma unroll
-    for (int e = 0; e < NH; ++e) acc[e][0] = acc[e][1] = 0.0;
+    for (int e = 0; e < NH; ++e) d[e] = bb[e] = 0.0;
     float c2f = a2f + (float)hi;
     double c2 = a2 + hi;
-    for (int n2 = hi; n2 >= lo; --n2, c2f -= 1.0f, c2 -= 1.0) {
+    for (int n2 = hi; n2 >= lo; --n2, c2f -= 1.0f) {
         const BetaEntry be = row[n2];
-        const bool ok = fmaf(c2f, c2f, c1sq) <= R2f && be.ib != 0.0;
-        const double e = exp_neg_tab(be.b * z, T, jmax);
-        double wv[NH];
-        const double ibe = ok ? e * be.ib : 0.0;
-        wv[0] = ibe;
-        if (NH > 1) {
-            const double ee = ok ? e : 0.0;
-            wv[1] = c2 * ibe;
+        const bool ok = fmaf(c2f, c2f, c1sq) <= R2f && be.ibf != 0.f;
+        int j;
+        double p = exp_neg_split(fma(be.b, z, be.lnb), j0, jmax, j);
+        p = ok ? p : 0.0;
+        const double Tj = __ldg(T + j);
+        if (NH == 1) {
+            const double dn = fma(RS.lam, bb[0], fma(Tj, p, flip_sign(d[0], RS.m)));
+            bb[0] = dn + flip_sign(bb[0], RS.m);
+            d[0] = dn;
+        } else {
+            double wv[NH];
+            wv[0] = Tj * p;
+            wv[1] = c2 * wv[0];
             wv[2] = c2 * wv[1];
-            wv[3] = be.b * ee;
-            wv[4] = ee;
-            wv[5] = c2 * ee;
-        }
+            wv[4] = be.b * wv[0];
+            wv[3] = be.b * wv[4];
+            wv[5] = c2 * wv[4];
+            c2 -= 1.0;
 #pragma unroll
-        for (int k = 0; k < NH; ++k) {
-            const double nx = fma(acc[k][0], cv, fma(-acc[k][1], sv, wv[k]));
-            const double ny = fma(acc[k][0], sv, acc[k][1] * cv);
-            acc[k][0] = nx;
-            acc[k][1] = ny;
+            for (int e = 0; e < NH; ++e) {
+                const double dn = fma(RS.lam, bb[e], wv[e] + flip_sign(d[e], RS.m));
+                bb[e] = dn + flip_sign(bb[e], RS.m);
+                d[e] = dn;
+            }
         }
+    }
+#pragma unroll
+    for (int e = 0; e < NH; ++e) {
+        const double b1 = flip_sign(bb[e] - d[e], RS.m);
+        acc[e][0] = fma(-RS.hlam, b1, d[e]);
+        acc[e][1] = b1 * RS.sv;
     }
 }
 
@@ -586,8 +675,9 @@ __device__ __forceinline__ void phase_f32_reduced(double arg, float &s, float &c
 //   S = sum_n beta_n^{-1} e^{i beta_n |x3|} e^{i alpha_n . t},  G_d = e^{i2pi<alpha.m>} (i/8pi^2) S.
 // Propagating n (|alpha_n| < k, a handful) are summed from a list.  For the
 // evanescent n, beta = i b and 1/beta = -i/b; with w = e^{-bz}/b (real) the row
-// n1 contributes -i sum_{n2} w e^{i(c1 t1 + c2 t2)}, summed by Horner's rule
-// in v = e^{i t2} from an anchor phase.  Each lane keeps only its own
+// n1 contributes -i sum_{n2} w e^{i(c1 t1 + c2 t2)}, summed along n2 from an
+// anchor phase: by Reinsch's recurrence in the double core, by Horner's rule
+// in v = e^{i t2} in the float tails.  Each lane keeps only its own
 // truncation set |alpha_n|^2 <= k^2 + (T/z)^2.
 //
 // Precision: the terms of the warp's core disk |alpha_n|^2 <= k^2 + (Y0/z_min)^2
@@ -599,9 +689,27 @@ __device__ __forceinline__ void phase_f32_reduced(double arg, float &s, float &c
 // ---------------------------------------------------------------------------
 constexpr double FAR_CORE_Y0 = 18.0;
 
-// One warp, one chunk w of 32 consecutive entries of the sorted far list.
+// Row slab `slab` of `nslab` of the rows of a chunk: the warp's core rows
+// (|c1| <= sqrt(Rc2)) split evenly, the tail-only rows below and above the core
+// joined to the first and the last slab.  Every row falls in exactly one slab.
+__device__ __forceinline__ void slab_rows(int n1a, int n1b, float Rc2f, float a1f, int slab, int nslab, int &lo, int &hi)
+{
+    lo = n1a;
+    hi = n1b;
+    if (nslab <= 1) return;
+    const float rcf = sqrtf(fmaxf(Rc2f, 0.f));
+    const int k0 = max(n1a, (int)ceilf(-a1f - rcf)), k1 = min(n1b, (int)floorf(-a1f + rcf));
+    const int Lc = max(k1 - k0 + 1, 0);
+    if (slab > 0) lo = k0 + (slab * Lc) / nslab;
+    if (slab < nslab - 1) hi = k0 + ((slab + 1) * Lc) / nslab - 1;
+}
+
+// One warp, row slab `slab` of `nslab` of chunk w (32 consecutive entries of
+// the sorted far list).  The slab's share of the series is added into the
+// output entries, which the near pass set to zero; the propagating terms go
+// with slab 0.
 template <int NF>
-__device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count)
+__device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, int nslab)
 {
     constexpr int NH = NF == 1 ? 1 : 6;
     const BetaEntry *tab = reinterpret_cast<const BetaEntry *>(a.btab);
@@ -611,7 +719,7 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count)
     const int lane = threadIdx.x & 31;
     const double k2 = a.k * a.k, ik2 = 1.0 / k2;
     const double *T = a.exptab;
-    const int jmax = a.exptab_n - 1;
+    const int jmax = a.exptab_n - 1, j0 = a.exptab_j0;
     const float a2f = (float)a.a2;
     {
         FarLane L = far_lane(a, w * 32 + lane, count);
@@ -623,6 +731,7 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count)
         const double Rc2 = fmin(k2 + FAR_CORE_Y0 * FAR_CORE_Y0 * izmax * izmax, R2m);
         double sv, cv;
         sincos(L.t2, &sv, &cv);
+        const Reinsch RS = reinsch_lane(L.t2, sv, cv);
         const float svf = (float)sv, cvf = (float)cv, zf = (float)L.z;
         double P[NF][2];
         double S[NF == 1 ? 1 : 7][2];
@@ -630,7 +739,7 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count)
         for (int e = 0; e < NF; ++e) P[e][0] = P[e][1] = 0.0;
 #pragma unroll
         for (int e = 0; e < (NF == 1 ? 1 : 7); ++e) S[e][0] = S[e][1] = 0.0;
-        for (int q = 0; q < a.nprop; ++q) {
+        for (int q = 0, nq = slab == 0 ? *a.nprop : 0; q < nq; ++q) {
             const PropEntry pe = a.prop[q];
             double sz, cz, sp, cp;
             sincos(pe.br * L.z, &sz, &cz);
@@ -656,7 +765,9 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count)
         const float R2mf = (float)R2m, Rc2f = (float)Rc2, a1f = (float)a.a1;
         const float Rmf = sqrtf(R2mf);
         const int n1a = max(a.n1lo, (int)floorf(-a1f - Rmf) - 1), n1b = min(a.n1hi, (int)ceilf(-a1f + Rmf) + 1);
-        for (int n1 = n1a; n1 <= n1b; ++n1) {
+        int r_lo, r_hi;
+        slab_rows(n1a, n1b, Rc2f, a1f, slab, nslab, r_lo, r_hi);
+        for (int n1 = r_lo; n1 <= r_hi; ++n1) {
             const float c1f = a1f + (float)n1;
             const float c1sq = c1f * c1f;
             const float remf = R2mf - c1sq;
@@ -684,7 +795,7 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count)
             for (int e = 0; e < NH; ++e) rr[e][0] = rr[e][1] = 0.0;
             if (ca <= cb) {
                 double acc[NH][2];
-                seg_horner_f64<NH>(row, ca, cb, a.a2, c1sq, a2f, R2f, L.z, cv, sv, T, jmax, acc);
+                seg_sum_f64<NH>(row, ca, cb, a.a2, c1sq, a2f, R2f, L.z, RS, T, j0, jmax, acc);
                 double sp, cp;
                 sincos(base + (a.a2 + ca) * L.t2, &sp, &cp);
 #pragma unroll
@@ -748,7 +859,7 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count)
         // evanescent sums carry the factor -i (from 1/beta = -i/b), except the
         // xz, yz entries whose factor (-i)(-i sgn) = -sgn is real
         if (NF == 1) {
-            o[0] = cmul(pre, make_double2(P[0][0] + S[0][1], P[0][1] - S[0][0]));
+            add_out(o, cmul(pre, make_double2(P[0][0] + S[0][1], P[0][1] - S[0][0])));
         } else {
             for (int e = 0; e < 6; ++e) {
                 const double *s = S[1 + e];
@@ -757,20 +868,44 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count)
                     v = make_double2(P[1 + e][0] + s[1], P[1 + e][1] - s[0]);
                 else
                     v = make_double2(P[1 + e][0] + L.sg * s[0], P[1 + e][1] + L.sg * s[1]);
-                o[e] = cmul(pre, v);
+                add_out(o + e, cmul(pre, v));
             }
-            if (a.which == GF_OUT_MAXWELL7) o[6] = cmul(pre, make_double2(P[0][0] + S[0][1], P[0][1] - S[0][0]));
+            if (a.which == GF_OUT_MAXWELL7) add_out(o + 6, cmul(pre, make_double2(P[0][0] + S[0][1], P[0][1] - S[0][0])));
         }
     }
+}
+
+// Far work items (a row slab of a chunk of 32 consecutive entries of the
+// sorted list) are handed out one at a time from a counter, the most expensive
+// chunks first: the list is in ascending bucket order and the bucket 64 c/|x3|
+// grows as the target nears the slab, where the truncation disk (radius ~
+// T/|x3|) is largest, so the t-th item taken is slab t % S of chunk
+// nch-1-t/S.  S (row slabs per chunk) is chosen so that there are about eight
+// items per resident warp, which keeps the end of the launch short.
+__device__ __forceinline__ int far_slabs(int nch, int smax)
+{
+    const int nwarps = (int)(gridDim.x * blockDim.x) >> 5;
+    if (nch <= 0) return 1;
+    const int s = (8 * nwarps + nch - 1) / nch;
+    return s < 1 ? 1 : s > smax ? smax : s;
+}
+
+__device__ __forceinline__ int far_take(int *counter, int nitems)
+{
+    int t = 0;
+    if ((threadIdx.x & 31) == 0) t = atomicAdd(counter, 1);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    return t < nitems ? t : -1;
 }
 
 template <int NF>
 __global__ void __launch_bounds__(128) far3d_f64(EvalArgs a)
 {
     const int count = a.far_count[0];
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int w = gw; w * 32 < count; w += nw) far3d_f64_chunk<NF>(a, w, count);
+    const int nch = (count + 31) >> 5, S = far_slabs(nch, 8);
+    int *ctr = a.far_count + GF_WORK_SLOT;
+    for (int t = far_take(ctr, nch * S); t >= 0; t = far_take(ctr, nch * S))
+        far3d_f64_chunk<NF>(a, nch - 1 - t / S, count, t % S, S);
 }
 
 // ---------------------------------------------------------------------------
@@ -778,7 +913,7 @@ __global__ void __launch_bounds__(128) far3d_f64(EvalArgs a)
 // ex2; per-target reduction, lattice phase and the final scaling in double.
 // ---------------------------------------------------------------------------
 template <int NF>
-__device__ void far3d_f32_chunk(const EvalArgs &a, int w, int count)
+__device__ void far3d_f32_chunk(const EvalArgs &a, int w, int count, int slab, int nslab)
 {
     const BetaEntryF *tab = reinterpret_cast<const BetaEntryF *>(a.btab);
     float2 *out = reinterpret_cast<float2 *>(a.out);
@@ -800,7 +935,7 @@ __device__ void far3d_f32_chunk(const EvalArgs &a, int w, int count)
         for (int e = 0; e < NF; ++e) P[e][0] = P[e][1] = 0.f;
 #pragma unroll
         for (int e = 0; e < (NF == 1 ? 1 : 7); ++e) S[e][0] = S[e][1] = 0.f;
-        for (int q = 0; q < a.nprop; ++q) {
+        for (int q = 0, nq = slab == 0 ? *a.nprop : 0; q < nq; ++q) {
             const PropEntry pe = a.prop[q];
             float br = (float)pe.br, ibr = (float)pe.ibr, c1 = (float)pe.c1, c2 = (float)pe.c2;
             float sz, cz, sp, cp;
@@ -824,7 +959,10 @@ __device__ void far3d_f32_chunk(const EvalArgs &a, int w, int count)
         const float R2mf = (float)R2m, a1f = (float)a.a1;
         const float Rmf = sqrtf(R2mf);
         const int n1a = max(a.n1lo, (int)floorf(-a1f - Rmf) - 1), n1b = min(a.n1hi, (int)ceilf(-a1f + Rmf) + 1);
-        for (int n1 = n1a; n1 <= n1b; ++n1) {
+        // row slab: the rows split evenly
+        const int nr = n1b - n1a + 1;
+        const int r_lo = n1a + (slab * nr) / nslab, r_hi = n1a + ((slab + 1) * nr) / nslab - 1;
+        for (int n1 = r_lo; n1 <= r_hi; ++n1) {
             const float c1 = a1f + (float)n1;
             const float c1sq = c1 * c1;
             const float remf = R2mf - c1sq;
@@ -895,7 +1033,7 @@ __device__ void far3d_f32_chunk(const EvalArgs &a, int w, int count)
         const double2 pre = cmul(lat, make_double2(0.0, 1.0 / (8.0 * GF_PI * GF_PI)));
         float2 *o = out + (size_t)L.idx * ne;
         if (NF == 1) {
-            store_out(o, cmul(pre, make_double2(P[0][0] + S[0][1], P[0][1] - S[0][0])));
+            add_out(o, cmul(pre, make_double2(P[0][0] + S[0][1], P[0][1] - S[0][0])));
         } else {
             for (int e = 0; e < 6; ++e) {
                 const float *s = S[1 + e];
@@ -904,10 +1042,10 @@ __device__ void far3d_f32_chunk(const EvalArgs &a, int w, int count)
                     v = make_double2(P[1 + e][0] + s[1], P[1 + e][1] - s[0]);
                 else
                     v = make_double2(P[1 + e][0] + sg * s[0], P[1 + e][1] + sg * s[1]);
-                store_out(o + e, cmul(pre, v));
+                add_out(o + e, cmul(pre, v));
             }
             if (a.which == GF_OUT_MAXWELL7)
-                store_out(o + 6, cmul(pre, make_double2(P[0][0] + S[0][1], P[0][1] - S[0][0])));
+                add_out(o + 6, cmul(pre, make_double2(P[0][0] + S[0][1], P[0][1] - S[0][0])));
         }
     }
 }
@@ -916,34 +1054,46 @@ template <int NF>
 __global__ void __launch_bounds__(128) far3d_f32(EvalArgs a)
 {
     const int count = a.far_count[0];
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int w = gw; w * 32 < count; w += nw) far3d_f32_chunk<NF>(a, w, count);
+    const int nch = (count + 31) >> 5, S = far_slabs(nch, 4);
+    int *ctr = a.far_count + GF_WORK_SLOT;
+    for (int t = far_take(ctr, nch * S); t >= 0; t = far_take(ctr, nch * S))
+        far3d_f32_chunk<NF>(a, nch - 1 - t / S, count, t % S, S);
 }
 
-// Batched far kernel: one persistent launch for all pairs.  The chunks of all
-// pairs form one global list (pair after pair); warp gw takes the chunks whose
-// global index is congruent to gw modulo the number of warps, so no pair
-// waits for another and the load stays balanced across pair boundaries.
+// Batched far kernel: one persistent launch for all pairs.  The work items of
+// all pairs form one global list (pair after pair, each pair's chunks most
+// expensive first, S row slabs per chunk with S from the total chunk count)
+// handed out from pair 0's work counter, so no pair waits for another and the
+// load stays balanced across pair boundaries.  The taken index only grows, so
+// each warp walks the pair list forward.
 template <typename R, int NF>
 __global__ void far3d_batch(const EvalArgs *args, int np)
 {
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    int g0 = 0;
-    for (int p = 0; p < np; ++p) {
-        const EvalArgs &a = args[p];
-        const int count = a.far_count[0];
-        const int nch = (count + 31) >> 5;
-        int c = (gw - g0) % nw;
-        if (c < 0) c += nw;
-        for (; c < nch; c += nw) {
-            if (sizeof(R) == 8)
-                far3d_f64_chunk<NF>(a, c, count);
-            else
-                far3d_f32_chunk<NF>(a, c, count);
+    if (np <= 0) return;
+    int tot = 0;
+    for (int q = 0; q < np; ++q) tot += (args[q].far_count[0] + 31) >> 5;
+    const int S = far_slabs(tot, sizeof(R) == 8 ? 8 : 4);
+    int *ctr = args[0].far_count + GF_WORK_SLOT;
+    int p = 0, base = 0;
+    int count = args[0].far_count[0];
+    int nit = ((count + 31) >> 5) * S;
+    for (;;) {
+        int t = 0;
+        if ((threadIdx.x & 31) == 0) t = atomicAdd(ctr, 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        while (p < np && t >= base + nit) {
+            base += nit;
+            if (++p < np) {
+                count = args[p].far_count[0];
+                nit = ((count + 31) >> 5) * S;
+            }
         }
-        g0 = (g0 + nch) % nw;
+        if (p >= np) return;
+        const int u = t - base, nch = nit / S;
+        if (sizeof(R) == 8)
+            far3d_f64_chunk<NF>(args[p], nch - 1 - u / S, count, u % S, S);
+        else
+            far3d_f32_chunk<NF>(args[p], nch - 1 - u / S, count, u % S, S);
     }
 }
 
@@ -1001,6 +1151,22 @@ __global__ void __launch_bounds__(128) far2d(EvalArgs a)
     }
 }
 
+// Persistent far grid: as many 128-thread CTAs as are resident at once (a
+// grid beyond that would leave the extra CTAs waiting for a second wave).
+template <void (*K)(EvalArgs)>
+int resident_grid(int nsm)
+{
+    static const int per = [] {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, K, 128, 0) != cudaSuccess || v < 1) {
+            cudaGetLastError();
+            v = 1;
+        }
+        return v;
+    }();
+    return per * nsm;
+}
+
 template <typename R>
 cudaError_t launch_eval_t(const EvalArgs &a, cudaStream_t s, cudaEvent_t ev_mid)
 {
@@ -1010,27 +1176,26 @@ cudaError_t launch_eval_t(const EvalArgs &a, cudaStream_t s, cudaEvent_t ev_mid)
     int64_t blocks = (a.n + 255) / 256;
     if (blocks > (int64_t)nsm * 16) blocks = (int64_t)nsm * 16;
     if (blocks < 1) blocks = 1;
-    const int farblocks = nsm * 8;
     if (a.dim == 2) {
         near2d<R><<<(int)blocks, 256, 0, s>>>(a);
         if (ev_mid) cudaEventRecord(ev_mid, s);
-        far2d<R><<<farblocks, 128, 0, s>>>(a);
+        far2d<R><<<resident_grid<far2d<R>>(nsm), 128, 0, s>>>(a);
     } else if (a.nf == 1) {
         near3d<R, 1><<<(int)blocks, 256, 0, s>>>(a);
         if (ev_mid) cudaEventRecord(ev_mid, s);
         far_scatter<<<nsm * 2, 256, 0, s>>>(a);
         if (sizeof(R) == 8)
-            far3d_f64<1><<<farblocks, 128, 0, s>>>(a);
+            far3d_f64<1><<<resident_grid<far3d_f64<1>>(nsm), 128, 0, s>>>(a);
         else
-            far3d_f32<1><<<farblocks, 128, 0, s>>>(a);
+            far3d_f32<1><<<resident_grid<far3d_f32<1>>(nsm), 128, 0, s>>>(a);
     } else {
         near3d<R, 7><<<(int)blocks, 256, 0, s>>>(a);
         if (ev_mid) cudaEventRecord(ev_mid, s);
         far_scatter<<<nsm * 2, 256, 0, s>>>(a);
         if (sizeof(R) == 8)
-            far3d_f64<7><<<farblocks, 128, 0, s>>>(a);
+            far3d_f64<7><<<resident_grid<far3d_f64<7>>(nsm), 128, 0, s>>>(a);
         else
-            far3d_f32<7><<<farblocks, 128, 0, s>>>(a);
+            far3d_f32<7><<<resident_grid<far3d_f32<7>>(nsm), 128, 0, s>>>(a);
     }
     gf_count_launch(a.dim == 2 ? 2 : 3);
     return cudaGetLastError();
@@ -1059,12 +1224,14 @@ cudaError_t gf_launch_eval_batch(const EvalBatch &b, int precision, cudaStream_t
     return precision == GF_FP64 ? launch_eval_batch_t<double>(b, s) : launch_eval_batch_t<float>(b, s);
 }
 
-cudaError_t gf_launch_beta_table(const EvalArgs &a, int precision, cudaStream_t s)
+cudaError_t gf_launch_series_tables(const EvalArgs &a, int precision, double *exptab, PropEntry *prop, int *nprop,
+                                    const int pbox[4], cudaStream_t s)
 {
+    const int4 pb = make_int4(pbox[0], pbox[1], pbox[2], pbox[3]);
     if (precision == GF_FP64)
-        beta_table<BetaEntry><<<256, 256, 0, s>>>(a, (BetaEntry *)const_cast<void *>(a.btab));
+        series_tables<BetaEntry><<<256, 256, 0, s>>>(a, (BetaEntry *)const_cast<void *>(a.btab), exptab, prop, nprop, pb);
     else
-        beta_table<BetaEntryF><<<256, 256, 0, s>>>(a, (BetaEntryF *)const_cast<void *>(a.btab));
+        series_tables<BetaEntryF><<<256, 256, 0, s>>>(a, (BetaEntryF *)const_cast<void *>(a.btab), exptab, prop, nprop, pb);
     gf_count_launch(1);
     return cudaGetLastError();
 }

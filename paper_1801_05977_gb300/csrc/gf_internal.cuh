@@ -113,10 +113,11 @@ struct SynthArgs {
     int P1, P2, P3;     // padded extents (M + 3 per periodic axis; P3 = 1 in 2D)
 };
 
-// Far-series table entry for one in-plane index n: b = |beta_n| and 1/b for
-// evanescent n (beta_n = i b); zeros for propagating n (|alpha_n| <= k).
+// Far-series table entry for one in-plane index n: b = |beta_n|, ln b and 1/b
+// for evanescent n (beta_n = i b); zeros for propagating n (|alpha_n| <= k).
+// The double-precision core sums the weights e^{-b|x3|}/b = e^{-(b|x3| + ln b)}.
 struct BetaEntry {
-    double b, ib;            // double-precision core terms
+    double b, lnb;           // double-precision core terms
     float bl2, ibf, bf, pad; // b log2(e), 1/b, b in float for the exponentially small tail
 };
 struct BetaEntryF {
@@ -143,19 +144,22 @@ struct EvalArgs {
     int64_t n;
     int *far_idx;       // scratch: far-branch target indices, in append order
     int *far_sorted;    // scratch: the same indices ordered by |x_last| bucket (3D)
-    int *far_count;     // scratch counters: [0] far count, [1..NB] bucket sizes, [NB+1..2NB] cursors
+    int *far_count;     // scratch counters (GF_SCRATCH_COUNTERS ints, zero before each evaluation)
     const void *btab;   // far-series table [n1][n2] (BetaEntry or BetaEntryF)
     int n1lo, n1hi, n2lo, n2hi;
     const PropEntry *prop;  // propagating indices (|alpha_n| <= k)
-    int nprop;
-    const double *exptab;   // e^{-j/64}, j = 0 .. exptab_n - 1
-    int exptab_n;
+    const int *nprop;       // their number (device)
+    const double *exptab;   // e^{-(j - exptab_j0)/128}, j = 0 .. exptab_n - 1
+    int exptab_n, exptab_j0;
 };
 
 // Far targets are bucketed by b = floor(NB c / |x_last|) (clamped to NB-1) so
 // that the lanes of a warp share nearly the same series truncation radius.
 #define GF_FAR_BUCKETS 64
-#define GF_SCRATCH_COUNTERS (1 + 2 * GF_FAR_BUCKETS)
+// scratch counters: [0] far count, [1..NB] bucket sizes, [NB+1..2NB] cursors,
+// [GF_WORK_SLOT] far chunks handed out so far
+#define GF_WORK_SLOT (1 + 2 * GF_FAR_BUCKETS)
+#define GF_SCRATCH_COUNTERS (2 + 2 * GF_FAR_BUCKETS)
 
 // A sweep of plans run as batched persistent launches: per-pass virtual-block
 // prefix sums over the pairs (device arrays of np + 1 ints), the per-pair
@@ -184,7 +188,15 @@ cudaError_t gf_launch_cheb_table(const double *rr, const double2 *B, int Q, int 
                                  cudaStream_t s);
 cudaError_t gf_launch_synth_batch(const SynthBatch &b, int precision, cudaStream_t s);
 cudaError_t gf_launch_eval_batch(const EvalBatch &b, int precision, cudaStream_t s);
-cudaError_t gf_launch_beta_table(const EvalArgs &a, int precision, cudaStream_t s);
+cudaError_t gf_launch_series_tables(const EvalArgs &a, int precision, double *exptab, PropEntry *prop, int *nprop,
+                                    const int pbox[4], cudaStream_t s);
+cudaError_t gf_launch_e_table(const double *tt, int Q, int Mlast, double ct, double2 *E, cudaStream_t s);
+
+// runtime.cu: stream-ordered pool allocations, pinned upload staging
+cudaError_t gf_dev_alloc(void **ptr, size_t bytes, cudaStream_t s);
+void gf_dev_free(void *ptr, cudaStream_t s);
+cudaError_t gf_stage_upload(void *dev_dst, const void *src, size_t bytes, cudaStream_t s);
+cudaError_t gf_trim_pool();
 cudaError_t gf_launch_eval(const EvalArgs &a, int precision, cudaStream_t s, cudaEvent_t ev_mid);
 
 void gf_count_launch(int n);

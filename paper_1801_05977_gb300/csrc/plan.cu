@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <atomic>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -39,15 +40,16 @@ gf_status fail(gf_status s, const char *fmt, ...)
 bool pow2_in(int m, int lo, int hi) { return m >= lo && m <= hi && (m & (m - 1)) == 0; }
 
 // Gauss-Legendre nodes/weights on [-1, 1]: Newton iteration on P_Q from the
-// Chebyshev-like first guess, P_Q and P_Q' by the Bonnet recurrence.
-void gauss_legendre(int Q, std::vector<double> &x, std::vector<double> &w)
+// Chebyshev-like first guess, P_Q and P_Q' by the Bonnet recurrence (two more
+// steps once the update is at rounding level).  Computed once per Q.
+void gauss_legendre_compute(int Q, std::vector<double> &x, std::vector<double> &w)
 {
     x.assign(Q, 0.0);
     w.assign(Q, 0.0);
     for (int i = 0; i < (Q + 1) / 2; ++i) {
         double z = cos(GF_PI * (4.0 * i + 3.0) / (4.0 * Q + 2.0));
         double pd = 1.0;
-        for (int it = 0; it < 64; ++it) {
+        for (int it = 0, extra = 0; it < 100 && extra < 2; ++it) {
             double pm = 1.0, pc = z;
             for (int n = 1; n < Q; ++n) {
                 double pn = ((2 * n + 1) * z * pc - n * pm) / (n + 1);
@@ -57,7 +59,7 @@ void gauss_legendre(int Q, std::vector<double> &x, std::vector<double> &w)
             pd = Q * (pm - z * pc) / (1.0 - z * z);
             double dz = pc / pd;
             z -= dz;
-            if (fabs(dz) <= 1e-17) break;
+            if (fabs(dz) <= 1e-15) ++extra;
         }
         double pm = 1.0, pc = z;
         for (int n = 1; n < Q; ++n) {
@@ -72,6 +74,22 @@ void gauss_legendre(int Q, std::vector<double> &x, std::vector<double> &w)
         w[i] = wt;
         w[Q - 1 - i] = wt;
     }
+}
+
+std::mutex g_gl_mu;
+std::map<int, std::pair<std::vector<double>, std::vector<double>>> g_gl;
+
+void gauss_legendre(int Q, std::vector<double> &x, std::vector<double> &w)
+{
+    std::lock_guard<std::mutex> lk(g_gl_mu);
+    auto it = g_gl.find(Q);
+    if (it == g_gl.end()) {
+        std::vector<double> xx, ww;
+        gauss_legendre_compute(Q, xx, ww);
+        it = g_gl.emplace(Q, std::make_pair(std::move(xx), std::move(ww))).first;
+    }
+    x = it->second.first;
+    w = it->second.second;
 }
 
 double chi_d1(double t, double c, double ct)
@@ -96,10 +114,11 @@ struct gf_plan_s {
     size_t grid_bytes = 0;
     void *tables = nullptr;           // synthesis tables
     void *btab = nullptr;             // far-series beta table
-    PropEntry *prop = nullptr;        // propagating indices
-    int nprop = 0;
-    double *exptab = nullptr;         // e^{-j/64}
-    int exptab_n = 0;
+    PropEntry *prop = nullptr;        // propagating indices, then their count
+    int *nprop_dev = nullptr;
+    cudaStream_t stream = nullptr;    // stream of the plan's creation
+    double *exptab = nullptr;         // e^{-(j - exptab_j0)/128}
+    int exptab_n = 0, exptab_j0 = 0;
     int n1lo = 0, n1hi = -1, n2lo = 0, n2hi = -1;
     SynthArgs sa{};
     // eval scratch (far list + counter) and host-call staging, grown on demand
@@ -181,6 +200,7 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
     const double a1 = alpha[0], a2 = dim == 3 ? alpha[1] : 0.0;
 
     // Wood anomaly (Sec. 1): beta_n = 0 for some n.  Only |alpha_n| ~ k matters.
+    double bmin_ev = 1.0;
     {
         int R = (int)ceil(k) + 2;
         int r2 = dim == 3 ? R : 0;
@@ -191,6 +211,8 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
                 double aa = sqrt(c1 * c1 + c2 * c2);
                 double b = sqrt(fabs((k - aa) * (k + aa)));
                 if (b < bmin) bmin = b;
+                // the smallest evanescent b (attained at the smallest |alpha_n| > k, inside this box)
+                if (aa > k && b < bmin_ev) bmin_ev = b;
             }
         if (bmin < 1e-8 * k) return fail(GF_ERR_WOOD, "gf_plan: |beta_n| = %.3g < 1e-8 k (Wood anomaly)", bmin);
     }
@@ -300,29 +322,34 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
         F10 = -s;
     }
 
-    // ---- device memory
+    // ---- device memory (stream-ordered, from the library pool) and the tables:
+    // the small host tables go up through pinned staging; the last-axis phase
+    // table, the Chebyshev table of h(s) and the series tables are built on
+    // the device.  Nothing here waits for the stream.
     const size_t nodes_padded = (size_t)p->P1 * p->P2 * p->P3;
     p->grid_bytes = nodes_padded * p->nf * p->elem;
-    const size_t tab_bytes = sizeof(double) * 5 * Q + sizeof(double2) * (Q + E.size() + hcheb_n);
+    const size_t E_n = (size_t)Mlast * Q;
+    const size_t host_tab_bytes = sizeof(double) * 5 * Q + sizeof(double2) * Q;
+    const size_t tab_bytes = host_tab_bytes + sizeof(double2) * (E_n + hcheb_n);
     const size_t ncells = (size_t)p->M[0] * p->M[1] * p->M[2];
     const size_t work_bytes = ncells * p->nf * p->elem;
     void *work = nullptr;
     gf_status st_err = GF_OK;
+    p->stream = st;
     do {
         cudaError_t e;
-        if ((e = cudaMalloc(&p->grid, p->grid_bytes)) != cudaSuccess ||
-            (e = cudaMalloc(&p->tables, tab_bytes)) != cudaSuccess ||
-            (e = cudaMallocAsync(&work, work_bytes, st)) != cudaSuccess) {
-            st_err = fail(e == cudaErrorMemoryAllocation ? GF_ERR_NOMEM : GF_ERR_CUDA, "gf_plan: cudaMalloc: %s",
+        if ((e = gf_dev_alloc(&p->grid, p->grid_bytes, st)) != cudaSuccess ||
+            (e = gf_dev_alloc(&p->tables, tab_bytes, st)) != cudaSuccess ||
+            (e = gf_dev_alloc(&work, work_bytes, st)) != cudaSuccess) {
+            st_err = fail(e == cudaErrorMemoryAllocation ? GF_ERR_NOMEM : GF_ERR_CUDA, "gf_plan: device allocation: %s",
                           cudaGetErrorString(e));
             break;
         }
         char *tb = (char *)p->tables;
         double *d_tt = (double *)tb, *d_tW = d_tt + Q, *d_rr = d_tW + Q, *d_P0 = d_rr + Q, *d_P1 = d_P0 + Q;
-        double2 *d_B = (double2 *)(d_P1 + Q), *d_E = d_B + Q, *d_H = d_E + E.size();
-        // one upload of the packed host tables (same layout as on the device)
-        std::vector<char> pack((char *)d_H - tb);
+        double2 *d_B = (double2 *)(d_P1 + Q), *d_E = d_B + Q, *d_H = d_E + E_n;
         {
+            std::vector<char> pack(host_tab_bytes);
             char *hb = pack.data();
             memcpy(hb + ((char *)d_tt - tb), tt.data(), sizeof(double) * Q);
             memcpy(hb + ((char *)d_tW - tb), tW.data(), sizeof(double) * Q);
@@ -330,13 +357,12 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
             memcpy(hb + ((char *)d_P0 - tb), P0.data(), sizeof(double) * Q);
             memcpy(hb + ((char *)d_P1 - tb), P1.data(), sizeof(double) * Q);
             memcpy(hb + ((char *)d_B - tb), B.data(), sizeof(double2) * Q);
-            memcpy(hb + ((char *)d_E - tb), E.data(), sizeof(double2) * E.size());
-        }
-        if ((e = cudaMemcpyAsync(tb, pack.data(), pack.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-            (hcheb_n && (e = gf_launch_cheb_table(d_rr, d_B, Q, hnpan, hdeg, hpan, d_H, st)) != cudaSuccess) ||
-            (e = cudaStreamSynchronize(st)) != cudaSuccess) {
-            st_err = fail(GF_ERR_CUDA, "gf_plan: table upload: %s", cudaGetErrorString(e));
-            break;
+            if ((e = gf_stage_upload(tb, hb, host_tab_bytes, st)) != cudaSuccess ||
+                (e = gf_launch_e_table(d_tt, Q, Mlast, ct, d_E, st)) != cudaSuccess ||
+                (hcheb_n && (e = gf_launch_cheb_table(d_rr, d_B, Q, hnpan, hdeg, hpan, d_H, st)) != cudaSuccess)) {
+                st_err = fail(GF_ERR_CUDA, "gf_plan: tables: %s", cudaGetErrorString(e));
+                break;
+            }
         }
         SynthArgs &sa = p->sa;
         sa.dim = dim;
@@ -381,7 +407,8 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
             st_err = fail(GF_ERR_CUDA, "gf_plan: synthesis launch: %s", cudaGetErrorString(e));
             break;
         }
-        // far-series table: index box covering |alpha_n|^2 <= k^2 + (T/c)^2
+        if (p->timing) cudaEventRecord(p->ev[1], st);
+        // far-series tables: index box covering |alpha_n|^2 <= k^2 + (T/c)^2
         if (dim == 3) {
             double Rc = sqrt(k * k + (p->T / c) * (p->T / c));
             p->n1lo = (int)floor(-a1 - Rc) - 1;
@@ -390,38 +417,24 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
             p->n2hi = (int)ceil(-a2 + Rc) + 1;
             size_t ne = (size_t)(p->n1hi - p->n1lo + 1) * (p->n2hi - p->n2lo + 1);
             size_t eb = p->precision == GF_FP64 ? sizeof(BetaEntry) : sizeof(BetaEntryF);
-            if ((e = cudaMalloc(&p->btab, ne * eb)) != cudaSuccess) {
-                st_err = fail(GF_ERR_NOMEM, "gf_plan: cudaMalloc(beta table): %s", cudaGetErrorString(e));
+            // propagating indices lie in the sub-box |c1|, |c2| <= k
+            const int pbox[4] = {(int)floor(-a1 - k) - 1, (int)ceil(-a1 + k) + 1, (int)floor(-a2 - k) - 1,
+                                 (int)ceil(-a2 + k) + 1};
+            const size_t nprop_max = (size_t)(pbox[1] - pbox[0] + 1) * (pbox[3] - pbox[2] + 1);
+            // T[j] = e^{-(j - j0)/128}: the core weights e^{-y}, y = b|x3| + ln b,
+            // of a lane's truncation set (b|x3| <= T) have ln(bmin) <= y <= T + ln(bmax),
+            // bmax <= sqrt(2) (Rc + 2) over the index box
+            p->exptab_j0 = 128 * ((int)ceil(-log(bmin_ev)) + 1);
+            if (p->exptab_j0 < 128) p->exptab_j0 = 128;
+            p->exptab_n = p->exptab_j0 + 128 * ((int)ceil(p->T + log(1.4143 * (Rc + 2.0))) + 2) + 1;
+            const bool want_exp = p->precision == GF_FP64;
+            if ((e = gf_dev_alloc(&p->btab, ne * eb, st)) != cudaSuccess ||
+                (e = gf_dev_alloc((void **)&p->prop, sizeof(PropEntry) * nprop_max + 16, st)) != cudaSuccess ||
+                (want_exp && (e = gf_dev_alloc((void **)&p->exptab, sizeof(double) * p->exptab_n, st)) != cudaSuccess)) {
+                st_err = fail(GF_ERR_NOMEM, "gf_plan: device allocation (series tables): %s", cudaGetErrorString(e));
                 break;
             }
-            // propagating indices (|alpha_n| <= k) and the exponential table e^{-j/64}
-            std::vector<PropEntry> prop;
-            for (int n1 = p->n1lo; n1 <= p->n1hi; ++n1)
-                for (int n2 = p->n2lo; n2 <= p->n2hi; ++n2) {
-                    double c1 = a1 + n1, c2 = a2 + n2;
-                    double aa = sqrt(c1 * c1 + c2 * c2);
-                    if (aa <= k) {
-                        double br = sqrt((k - aa) * (k + aa));
-                        prop.push_back(PropEntry{c1, c2, br, 1.0 / br});
-                    }
-                }
-            p->nprop = (int)prop.size();
-            p->exptab_n = 64 * ((int)ceil(p->T) + 2) + 1;
-            std::vector<double> et(p->exptab_n);
-            for (int j = 0; j < p->exptab_n; ++j) et[j] = exp(-(double)j / 64.0);
-            if ((e = cudaMalloc(&p->prop, sizeof(PropEntry) * (prop.size() + 1))) != cudaSuccess ||
-                (e = cudaMalloc(&p->exptab, sizeof(double) * et.size())) != cudaSuccess) {
-                st_err = fail(GF_ERR_NOMEM, "gf_plan: cudaMalloc(series tables): %s", cudaGetErrorString(e));
-                break;
-            }
-            if ((!prop.empty() &&
-                 (e = cudaMemcpy(p->prop, prop.data(), sizeof(PropEntry) * prop.size(), cudaMemcpyHostToDevice)) !=
-                     cudaSuccess) ||
-                (e = cudaMemcpy(p->exptab, et.data(), sizeof(double) * et.size(), cudaMemcpyHostToDevice)) !=
-                    cudaSuccess) {
-                st_err = fail(GF_ERR_CUDA, "gf_plan: series table upload: %s", cudaGetErrorString(e));
-                break;
-            }
+            p->nprop_dev = (int *)(p->prop + nprop_max);
             EvalArgs ea{};
             ea.k = k;
             ea.a1 = a1;
@@ -431,27 +444,23 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
             ea.n2lo = p->n2lo;
             ea.n2hi = p->n2hi;
             ea.btab = p->btab;
-            if (p->timing) cudaEventRecord(p->ev[1], st);
-            if ((e = gf_launch_beta_table(ea, p->precision, st)) != cudaSuccess) {
-                st_err = fail(GF_ERR_CUDA, "gf_plan: beta table launch: %s", cudaGetErrorString(e));
+            ea.exptab_n = want_exp ? p->exptab_n : 0;
+            ea.exptab_j0 = p->exptab_j0;
+            if ((e = gf_launch_series_tables(ea, p->precision, want_exp ? p->exptab : nullptr, p->prop, p->nprop_dev,
+                                             pbox, st)) != cudaSuccess) {
+                st_err = fail(GF_ERR_CUDA, "gf_plan: series table launch: %s", cudaGetErrorString(e));
                 break;
             }
-            if (p->timing) cudaEventRecord(p->ev[2], st);
-        } else if (p->timing) {
-            cudaEventRecord(p->ev[1], st);
-            cudaEventRecord(p->ev[2], st);
         }
+        if (p->timing) cudaEventRecord(p->ev[2], st);
         p->ev_plan = p->timing;
-        // the work buffer is released in stream order once the synthesis is done
-        if ((e = cudaFreeAsync(work, st)) != cudaSuccess) {
-            st_err = fail(GF_ERR_CUDA, "gf_plan: cudaFreeAsync: %s", cudaGetErrorString(e));
-            break;
-        }
+        // the work buffer goes back to the pool in stream order once the synthesis is done
+        gf_dev_free(work, st);
         work = nullptr;
         p->sa.work = nullptr;
     } while (0);
     if (st_err != GF_OK) {
-        if (work) cudaFreeAsync(work, st);
+        if (work) gf_dev_free(work, st);
         gf_destroy(p);
         return st_err;
     }
@@ -473,20 +482,21 @@ gf_status gf_eval_grid(gf_plan_t p, void *dev_out, size_t out_bytes, void *cuda_
     return GF_OK;
 }
 
-static gf_status ensure_scratch(gf_plan_t p, int64_t n)
+static gf_status ensure_scratch(gf_plan_t p, int64_t n, cudaStream_t st)
 {
     if (p->far_cap >= n && p->far_count) return GF_OK;
     int64_t cap = p->far_cap;
     if (cap < 1024) cap = 1024;
     while (cap < n) cap *= 2;
     if (p->far_idx) {
+        // the old list may still be in use by an evaluation on another stream
         CU(cudaDeviceSynchronize());
-        cudaFree(p->far_idx);
+        gf_dev_free(p->far_idx, st);
         p->far_idx = nullptr;
         p->far_cap = 0;
     }
-    if (!p->far_count) CU(cudaMalloc(&p->far_count, sizeof(int) * GF_SCRATCH_COUNTERS));
-    CU(cudaMalloc(&p->far_idx, sizeof(int) * 2 * cap));
+    if (!p->far_count) CU(gf_dev_alloc((void **)&p->far_count, sizeof(int) * GF_SCRATCH_COUNTERS, st));
+    CU(gf_dev_alloc((void **)&p->far_idx, sizeof(int) * 2 * cap, st));
     p->far_cap = cap;
     return GF_OK;
 }
@@ -502,9 +512,9 @@ gf_status gf_eval_points(gf_plan_t p, const double *dev_xyz, int64_t n, int whic
               (p->kind == GF_MAXWELL && (which == GF_OUT_MAXWELL6 || which == GF_OUT_MAXWELL7));
     if (!ok) return fail(GF_ERR_ARG, "gf_eval_points: output kind %d does not match the plan", which);
     std::lock_guard<std::mutex> lk(p->mu);
-    gf_status s = ensure_scratch(p, n);
-    if (s != GF_OK) return s;
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    gf_status s = ensure_scratch(p, n, st);
+    if (s != GF_OK) return s;
     CU(cudaMemsetAsync(p->far_count, 0, sizeof(int) * GF_SCRATCH_COUNTERS, st));
     EvalArgs a{};
     a.dim = p->dim;
@@ -539,9 +549,10 @@ gf_status gf_eval_points(gf_plan_t p, const double *dev_xyz, int64_t n, int whic
     a.n2lo = p->n2lo;
     a.n2hi = p->n2hi;
     a.prop = p->prop;
-    a.nprop = p->nprop;
+    a.nprop = p->nprop_dev;
     a.exptab = p->exptab;
     a.exptab_n = p->exptab_n;
+    a.exptab_j0 = p->exptab_j0;
     if (p->timing) cudaEventRecord(p->ev[3], st);
     CU(gf_launch_eval(a, p->precision, st, p->timing ? p->ev[4] : nullptr));
     if (p->timing) {
@@ -594,9 +605,10 @@ gf_status gf_plan_eval_args(gf_plan_t p, const double *dev_xyz, int64_t n, int w
     a.n2lo = p->n2lo;
     a.n2hi = p->n2hi;
     a.prop = p->prop;
-    a.nprop = p->nprop;
+    a.nprop = p->nprop_dev;
     a.exptab = p->exptab;
     a.exptab_n = p->exptab_n;
+    a.exptab_j0 = p->exptab_j0;
     *a_out = a;
     return GF_OK;
 }
@@ -647,17 +659,23 @@ gf_status gf_eval_points_host(gf_plan_t p, const double *host_xyz, int64_t n, in
     {
         std::lock_guard<std::mutex> lk(p->mu);
         if (p->stage_x_cap < xb) {
-            CU(cudaDeviceSynchronize());
-            if (p->stage_x) cudaFree(p->stage_x);
+            if (p->stage_x) {
+                CU(cudaDeviceSynchronize());
+                gf_dev_free(p->stage_x, st);
+            }
             p->stage_x = nullptr;
-            CU(cudaMalloc(&p->stage_x, xb));
+            p->stage_x_cap = 0;
+            CU(gf_dev_alloc(&p->stage_x, xb, st));
             p->stage_x_cap = xb;
         }
         if (p->stage_out_cap < ob) {
-            CU(cudaDeviceSynchronize());
-            if (p->stage_out) cudaFree(p->stage_out);
+            if (p->stage_out) {
+                CU(cudaDeviceSynchronize());
+                gf_dev_free(p->stage_out, st);
+            }
             p->stage_out = nullptr;
-            CU(cudaMalloc(&p->stage_out, ob));
+            p->stage_out_cap = 0;
+            CU(gf_dev_alloc(&p->stage_out, ob, st));
             p->stage_out_cap = ob;
         }
     }
@@ -694,19 +712,20 @@ gf_status gf_plan_get_info(gf_plan_t p, gf_plan_info_t *info)
     return GF_OK;
 }
 
+gf_status gf_release_memory(void)
+{
+    CU(gf_trim_pool());
+    return GF_OK;
+}
+
 gf_status gf_destroy(gf_plan_t p)
 {
     if (!p) return GF_OK;
+    // the plan may have been used on any stream: wait for the device, then hand
+    // the buffers back to the pool
     cudaDeviceSynchronize();
-    if (p->grid) cudaFree(p->grid);
-    if (p->tables) cudaFree(p->tables);
-    if (p->btab) cudaFree(p->btab);
-    if (p->prop) cudaFree(p->prop);
-    if (p->exptab) cudaFree(p->exptab);
-    if (p->far_idx) cudaFree(p->far_idx);
-    if (p->far_count) cudaFree(p->far_count);
-    if (p->stage_x) cudaFree(p->stage_x);
-    if (p->stage_out) cudaFree(p->stage_out);
+    void *bufs[] = {p->grid, p->tables, p->btab, p->prop, p->exptab, p->far_idx, p->far_count, p->stage_x, p->stage_out};
+    for (void *b : bufs) gf_dev_free(b, 0);
     for (int i = 0; i < 6; ++i)
         if (p->ev[i]) cudaEventDestroy(p->ev[i]);
     delete p;

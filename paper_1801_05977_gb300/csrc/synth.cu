@@ -538,6 +538,30 @@ __global__ void cheb_table_kernel(const double *rr, const double2 *B, int Q, int
 }
 }  // namespace
 
+// E[b][m] = e^{i q_b t_m}, q_b = j pi / c~ with j = b for b < Mlast/2, else
+// b - Mlast (the last-axis frequencies of Eq. (fck-coef)), t_m the Gauss nodes
+// of the X' integrals.
+__global__ void e_table_kernel(const double *tt, int Q, int Mlast, double ct, double2 *E)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Mlast * Q; i += gridDim.x * blockDim.x) {
+        const int b = i / Q, m = i - b * Q;
+        const int jl = b < Mlast / 2 ? b : b - Mlast;
+        const double q = (double)jl * GF_PI / ct;
+        double sv, cv;
+        sincos(q * tt[m], &sv, &cv);
+        E[i] = make_double2(cv, sv);
+    }
+}
+
+cudaError_t gf_launch_e_table(const double *tt, int Q, int Mlast, double ct, double2 *E, cudaStream_t s)
+{
+    int blocks = (Mlast * Q + 255) / 256;
+    if (blocks > 1024) blocks = 1024;
+    e_table_kernel<<<blocks, 256, 0, s>>>(tt, Q, Mlast, ct, E);
+    gf_count_launch(1);
+    return cudaGetLastError();
+}
+
 cudaError_t gf_launch_cheb_table(const double *rr, const double2 *B, int Q, int npan, int deg, double w, double2 *out,
                                  cudaStream_t s)
 {

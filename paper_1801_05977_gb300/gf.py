@@ -49,7 +49,7 @@ EXPORTS = ["gf_trunc_default", "gf_plan", "gf_eval_grid", "gf_grid_bytes", "gf_e
            "gf_batch_get_tuning", "gf_batch_run_graph", "gf_batch_get_plan", "gf_batch_destroy",
            "gf_gemm_bf16", "gf_mlp_create", "gf_mlp_param_count", "gf_mlp_params", "gf_mlp_set_scale",
            "gf_mlp_forward", "gf_mlp_train_step", "gf_mlp_gradients", "gf_mlp_error_word", "gf_surrogate_eval",
-           "gf_mlp_destroy"]
+           "gf_mlp_destroy", "gf_release_memory"]
 
 NOALLOC_MAX_TARGETS = 1 << 18
 
@@ -107,13 +107,14 @@ def lib(build_if_missing: bool = True):
     L.gf_launch_count.restype = i64
     L.gf_set_phase_timing.argtypes = [i32]
     L.gf_plan_phase_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+    L.gf_release_memory.argtypes = []
     for name in ("gf_trunc_default", "gf_plan", "gf_eval_grid", "gf_eval_points", "gf_eval_points_host",
                  "gf_eval_points_noalloc", "gf_plan_batch", "gf_batch_synthesize", "gf_batch_eval_points",
                  "gf_batch_autotune", "gf_batch_get_tuning", "gf_batch_run_graph", "gf_batch_get_plan",
                  "gf_batch_destroy", "gf_gemm_bf16", "gf_mlp_create", "gf_mlp_params", "gf_mlp_set_scale",
                  "gf_mlp_forward", "gf_mlp_train_step", "gf_mlp_gradients", "gf_mlp_error_word",
                  "gf_surrogate_eval", "gf_mlp_destroy",
-                 "gf_plan_get_info", "gf_destroy", "gf_set_phase_timing", "gf_plan_phase_ms"):
+                 "gf_plan_get_info", "gf_destroy", "gf_set_phase_timing", "gf_plan_phase_ms", "gf_release_memory"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -146,6 +147,11 @@ def launch_count() -> int:
 
 def set_phase_timing(on: bool):
     _check(lib().gf_set_phase_timing(1 if on else 0))
+
+
+def release_memory():
+    """gf_release_memory: hand the pool's unused device memory back to the driver."""
+    _check(lib().gf_release_memory())
 
 
 class Plan:
