@@ -496,17 +496,27 @@ __device__ __forceinline__ double warp_max(double v)
 
 // e^{-y} by Tang's table-driven method (ACM TOMS 15, 1989): y = j/128 + r with
 // j = rint(128 y) and |r| <= 1/256; e^{-y} = T[j + j0] e^{-r}, T[i] = e^{-(i - j0)/128}
-// a plan table.  Returns e^{-r} (its Taylor polynomial of degree 5, truncation
-// below 5e-18 relative) and the table index, clamped to the table; callers
-// discard the terms whose y lies beyond it.
+// a plan table.  Returns e^{-r} by its Taylor polynomial of degree DEG and the
+// table index, clamped to the table (callers discard the terms whose y lies
+// beyond it).  Truncation relative to e^{-y}: 4.9e-18 (DEG 5), 7.6e-15 (DEG 4),
+// 9.7e-12 (DEG 3); callers take DEG 4 and 3 only for terms at least e^7 and
+// e^14 below the largest term of the series.
+template <int DEG>
 __device__ __forceinline__ double exp_neg_split(double y, int j0, int jmax, int &idx)
 {
     const double MAGIC = 6755399441055744.0;  // 1.5 * 2^52: rint by addition
     const double t = fma(y, 128.0, MAGIC);
     idx = min(max(__double2loint(t) + j0, 0), jmax);
     const double r = fma(t - MAGIC, -0.0078125, y);
-    double p = fma(r, -1.0 / 120.0, 1.0 / 24.0);
-    p = fma(p, r, -1.0 / 6.0);
+    double p;
+    if (DEG >= 5) {
+        p = fma(r, -1.0 / 120.0, 1.0 / 24.0);
+        p = fma(p, r, -1.0 / 6.0);
+    } else if (DEG == 4) {
+        p = fma(r, 1.0 / 24.0, -1.0 / 6.0);
+    } else {
+        p = -1.0 / 6.0;
+    }
     p = fma(p, r, 0.5);
     p = fma(p, r, -1.0);
     return fma(p, r, 1.0);
@@ -576,33 +586,37 @@ __device__ __forceinline__ Reinsch reinsch_lane(double theta, double sv, double 
     return R;
 }
 
-// Row segment n2 = hi, hi-1, ..., lo in double precision, anchored at lo:
-// acc[e] = sum_{n2} w_e(n2) e^{i (n2 - lo) theta}, weights on the lane's own
-// truncation set.  NH = 1 (G_d): w = e^{-bz}/b.  NH = 6 (Maxwell partial sums):
-// A = sum w, B = sum c2 w, C = sum c2^2 w, D = sum b^2 w, E = sum b w, F = sum c2 b w.
-// Per term and sum the recurrence costs three FP64 operations; for NH = 1 the
-// product T[j] e^{-r} is folded into the first of them.
+// Double-precision Reinsch state of NH row sums.  NH = 1 (G_d): w = e^{-bz}/b.
+// NH = 6 (Maxwell partial sums): A = sum w, B = sum c2 w, C = sum c2^2 w,
+// D = sum b^2 w, E = sum b w, F = sum c2 b w.
 template <int NH>
-__device__ __forceinline__ void seg_sum_f64(const BetaEntry *__restrict__ row, int lo, int hi, double a2,
-                                            float c1sq, float a2f, float R2f, double z, const Reinsch &RS,
-                                            const double *__restrict__ T, int j0, int jmax, double acc[NH][2])
+struct RState {
+    double d[NH], b[NH];
+};
+
+// Feed `count` terms n2, n2 + dir, ... into the state (the first has the
+// highest recurrence index), advancing n2 and c2; weights on the lane's own
+// truncation set, exponential of degree DEG.  Per term and sum the recurrence
+// costs three FP64 operations; for NH = 1 the product T[j] e^{-r} is folded
+// into the first.
+template <int NH, int DEG>
+__device__ __forceinline__ void reinsch_seg(RState<NH> &st, const BetaEntry *__restrict__ row, int &n2, int count,
+                                            int dir, float &c2f, double &c2, float c1sq, float R2f, double z,
+                                            const Reinsch &RS, const double *__restrict__ T, int j0, int jmax)
 {
-    double d[NH], bb[NH];
-#pragma unroll
-    for (int e = 0; e < NH; ++e) d[e] = bb[e] = 0.0;
-    float c2f = a2f + (float)hi;
-    double c2 = a2 + hi;
-    for (int n2 = hi; n2 >= lo; --n2, c2f -= 1.0f) {
+    const float df = (float)dir;
+    const double dd = (double)dir;
+    for (int i = 0; i < count; ++i, n2 += dir, c2f += df) {
         const BetaEntry be = row[n2];
         const bool ok = fmaf(c2f, c2f, c1sq) <= R2f && be.ibf != 0.f;
         int j;
-        double p = exp_neg_split(fma(be.b, z, be.lnb), j0, jmax, j);
+        double p = exp_neg_split<DEG>(fma(be.b, z, be.lnb), j0, jmax, j);
         p = ok ? p : 0.0;
         const double Tj = __ldg(T + j);
         if (NH == 1) {
-            const double dn = fma(RS.lam, bb[0], fma(Tj, p, flip_sign(d[0], RS.m)));
-            bb[0] = dn + flip_sign(bb[0], RS.m);
-            d[0] = dn;
+            const double dn = fma(RS.lam, st.b[0], fma(Tj, p, flip_sign(st.d[0], RS.m)));
+            st.b[0] = dn + flip_sign(st.b[0], RS.m);
+            st.d[0] = dn;
         } else {
             double wv[NH];
             wv[0] = Tj * p;
@@ -611,20 +625,94 @@ __device__ __forceinline__ void seg_sum_f64(const BetaEntry *__restrict__ row, i
             wv[4] = be.b * wv[0];
             wv[3] = be.b * wv[4];
             wv[5] = c2 * wv[4];
-            c2 -= 1.0;
+            c2 += dd;
 #pragma unroll
             for (int e = 0; e < NH; ++e) {
-                const double dn = fma(RS.lam, bb[e], wv[e] + flip_sign(d[e], RS.m));
-                bb[e] = dn + flip_sign(bb[e], RS.m);
-                d[e] = dn;
+                const double dn = fma(RS.lam, st.b[e], wv[e] + flip_sign(st.d[e], RS.m));
+                st.b[e] = dn + flip_sign(st.b[e], RS.m);
+                st.d[e] = dn;
             }
         }
     }
+}
+
+// The terms n2 = start, start + dir, ... (n3 + n4 + n5 of them, from the outer
+// end of the row towards the anchor): the first n3 with the degree-3
+// exponential, the next n4 with degree 4, the rest with degree 5.
+template <int NH>
+__device__ __forceinline__ void reinsch_run(RState<NH> &st, const BetaEntry *__restrict__ row, int start, int dir,
+                                            int n3, int n4, int n5, double a2, float c1sq, float a2f, float R2f,
+                                            double z, const Reinsch &RS, const double *__restrict__ T, int j0, int jmax)
+{
+    int n2 = start;
+    float c2f = a2f + (float)start;
+    double c2 = a2 + start;
+    reinsch_seg<NH, 3>(st, row, n2, n3, dir, c2f, c2, c1sq, R2f, z, RS, T, j0, jmax);
+    reinsch_seg<NH, 4>(st, row, n2, n4, dir, c2f, c2, c1sq, R2f, z, RS, T, j0, jmax);
+    reinsch_seg<NH, 5>(st, row, n2, n5, dir, c2f, c2, c1sq, R2f, z, RS, T, j0, jmax);
+}
+
+// One recurrence step with zero weight (recurrence index 0 of a sum whose
+// index-0 term belongs to another sum).
+template <int NH>
+__device__ __forceinline__ void reinsch_zero(RState<NH> &st, const Reinsch &RS)
+{
 #pragma unroll
     for (int e = 0; e < NH; ++e) {
-        const double b1 = flip_sign(bb[e] - d[e], RS.m);
-        acc[e][0] = fma(-RS.hlam, b1, d[e]);
-        acc[e][1] = b1 * RS.sv;
+        const double dn = fma(RS.lam, st.b[e], flip_sign(st.d[e], RS.m));
+        st.b[e] = dn + flip_sign(st.b[e], RS.m);
+        st.d[e] = dn;
+    }
+}
+
+// e^{i m t2} in float for an integer |m| < 2^11, with no double arithmetic:
+// t2 = th + tl with th of 12 significant bits (m th exact in float), the
+// product reduced by 2 pi = C1 + C2 + C3 (C1 of 8 bits, so k C1 is exact).
+struct PhaseF {
+    float th, tl;
+};
+
+__device__ __forceinline__ PhaseF phase_split(double t2)
+{
+    PhaseF P;
+    P.th = __int_as_float(__float_as_int((float)t2) & (int)0xFFFFF800);
+    P.tl = (float)(t2 - (double)P.th);
+    return P;
+}
+
+__device__ __forceinline__ void phase_m(const PhaseF &P, int m, float &s, float &c)
+{
+    const float mf = (float)m;
+    const float x = mf * P.th;
+    const float kq = rintf(x * 0.15915494f);
+    float r = fmaf(-kq, 6.28125f, x);
+    r = fmaf(-kq, 1.9353071693331003e-3f, r);
+    r = fmaf(-kq, 1.0253131677018246e-11f, r);
+    r = fmaf(mf, P.tl, r);
+    sincosf(r, &s, &c);
+}
+
+// Row sums combined into the outputs with the row's real factors (c1 fixed):
+// G: A; xx: (1 - c1^2/k^2) A; yy: A - C/k^2; zz: A + D/k^2; xy: -(c1/k^2) B;
+// xz: -(c1/k^2) E (real factor); yz: -(1/k^2) F (real factor).
+template <int NH, typename F>
+__device__ __forceinline__ void add_row(F S[][2], const F rr[][2], F c1, F ik2)
+{
+    if (NH == 1) {
+        S[0][0] += rr[0][0];
+        S[0][1] += rr[0][1];
+    } else {
+        const F fxx = (F)1 - c1 * c1 * ik2;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            S[0][q] += rr[0][q];
+            S[1][q] += fxx * rr[0][q];
+            S[2][q] += rr[0][q] - ik2 * rr[2][q];
+            S[3][q] += rr[0][q] + ik2 * rr[3][q];
+            S[4][q] += -c1 * ik2 * rr[1][q];
+            S[5][q] += -c1 * ik2 * rr[4][q];
+            S[6][q] += -ik2 * rr[5][q];
+        }
     }
 }
 
@@ -660,14 +748,6 @@ __device__ __forceinline__ void seg_horner_f32(const BetaEntry *__restrict__ row
     }
 }
 
-// e^{i arg} for a float segment: argument reduced modulo 2 pi in double, then
-// evaluated in float.
-__device__ __forceinline__ void phase_f32_reduced(double arg, float &s, float &c)
-{
-    double r = fma(-2.0 * GF_PI, rint(arg * (0.5 / GF_PI)), arg);
-    sincosf((float)r, &s, &c);
-}
-
 // ---------------------------------------------------------------------------
 // 3D far kernel for double-precision plans.  Series (he), and for Maxwell the
 // second derivatives (each term times delta_pq - c^p c^q/k^2, c = (alpha_n,
@@ -675,10 +755,13 @@ __device__ __forceinline__ void phase_f32_reduced(double arg, float &s, float &c
 //   S = sum_n beta_n^{-1} e^{i beta_n |x3|} e^{i alpha_n . t},  G_d = e^{i2pi<alpha.m>} (i/8pi^2) S.
 // Propagating n (|alpha_n| < k, a handful) are summed from a list.  For the
 // evanescent n, beta = i b and 1/beta = -i/b; with w = e^{-bz}/b (real) the row
-// n1 contributes -i sum_{n2} w e^{i(c1 t1 + c2 t2)}, summed along n2 from an
-// anchor phase: by Reinsch's recurrence in the double core, by Horner's rule
-// in v = e^{i t2} in the float tails.  Each lane keeps only its own
-// truncation set |alpha_n|^2 <= k^2 + (T/z)^2.
+// n1 contributes -i sum_{n2} w e^{i(c1 t1 + c2 t2)}.  Every row is summed
+// relative to the fixed anchor n2 = N0: the double core outwards from N0 by
+// two Reinsch recurrences, the float tails by Horner's rule in v = e^{i t2}
+// from their first index, moved to N0 by a float phase.  The row phase
+// e^{i c1 t1} follows a recurrence over the rows and e^{i(alpha_2 + N0) t2} is
+// applied once per target.  Each lane keeps only its own truncation set
+// |alpha_n|^2 <= k^2 + (T/z)^2.
 //
 // Precision: the terms of the warp's core disk |alpha_n|^2 <= k^2 + (Y0/z_min)^2
 // (b z_min <= Y0 = 18, z_min the warp's smallest |x3|) are summed in double
@@ -712,15 +795,20 @@ template <int NF>
 __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, int nslab)
 {
     constexpr int NH = NF == 1 ? 1 : 6;
+    constexpr int NS = NF == 1 ? 1 : 7;
     const BetaEntry *tab = reinterpret_cast<const BetaEntry *>(a.btab);
     double2 *out = reinterpret_cast<double2 *>(a.out);
     const int ne = n_entries(a.which);
     const int W2 = a.n2hi - a.n2lo + 1;
     const int lane = threadIdx.x & 31;
     const double k2 = a.k * a.k, ik2 = 1.0 / k2;
+    const float ik2f = (float)ik2;
     const double *T = a.exptab;
     const int jmax = a.exptab_n - 1, j0 = a.exptab_j0;
     const float a2f = (float)a.a2;
+    // every row is summed from the anchor n2 = N0 outwards (the centre of all
+    // rows' truncation intervals); e^{i(alpha_2 + N0) t2} multiplies the total
+    const int N0 = (int)rint(-a.a2);
     {
         FarLane L = far_lane(a, w * 32 + lane, count);
         const double R2m = warp_max(L.R2);
@@ -729,16 +817,24 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, i
         const double iz = L.valid ? 1.0 / L.z : 0.0;
         const double izmax = warp_max(iz);
         const double Rc2 = fmin(k2 + FAR_CORE_Y0 * FAR_CORE_Y0 * izmax * izmax, R2m);
-        double sv, cv;
+        double sv, cv, s1, c1v;
         sincos(L.t2, &sv, &cv);
+        sincos(L.t1, &s1, &c1v);
+        const double2 E1 = make_double2(c1v, s1);
         const Reinsch RS = reinsch_lane(L.t2, sv, cv);
+        const PhaseF PF = phase_split(L.t2);
+        // every term is at most e^{-(b - bmin) z_min} of the largest one (e^{-bz}/b
+        // decreases in b): degree 4 from b >= bmin + 7/z_min, 3 from bmin + 14/z_min
+        const float b4 = (float)(a.bmin + 7.0 * izmax), b3 = (float)(a.bmin + 14.0 * izmax);
+        const float k2f = (float)k2;
         const float svf = (float)sv, cvf = (float)cv, zf = (float)L.z;
         double P[NF][2];
-        double S[NF == 1 ? 1 : 7][2];
+        double S[NS][2];
+        float Sf[NS][2];
 #pragma unroll
         for (int e = 0; e < NF; ++e) P[e][0] = P[e][1] = 0.0;
 #pragma unroll
-        for (int e = 0; e < (NF == 1 ? 1 : 7); ++e) S[e][0] = S[e][1] = 0.0;
+        for (int e = 0; e < NS; ++e) S[e][0] = S[e][1] = 0.0, Sf[e][0] = Sf[e][1] = 0.f;
         for (int q = 0, nq = slab == 0 ? *a.nprop : 0; q < nq; ++q) {
             const PropEntry pe = a.prop[q];
             double sz, cz, sp, cp;
@@ -767,7 +863,25 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, i
         const int n1a = max(a.n1lo, (int)floorf(-a1f - Rmf) - 1), n1b = min(a.n1hi, (int)ceilf(-a1f + Rmf) + 1);
         int r_lo, r_hi;
         slab_rows(n1a, n1b, Rc2f, a1f, slab, nslab, r_lo, r_hi);
+        double2 A = make_double2(1.0, 0.0);  // e^{i c1 t1}
         for (int n1 = r_lo; n1 <= r_hi; ++n1) {
+            // row phase by recurrence, re-anchored every 16 rows
+            if (((n1 - r_lo) & 15) == 0) {
+                double sa, ca_;
+                sincos((a.a1 + n1) * L.t1, &sa, &ca_);
+                A = make_double2(ca_, sa);
+            } else {
+                A = cmul(A, E1);
+            }
+            // float tails fold into the double sums every 8 rows
+            if (((n1 - r_lo) & 7) == 7) {
+#pragma unroll
+                for (int e = 0; e < NS; ++e) {
+                    S[e][0] += (double)Sf[e][0];
+                    S[e][1] += (double)Sf[e][1];
+                    Sf[e][0] = Sf[e][1] = 0.f;
+                }
+            }
             const float c1f = a1f + (float)n1;
             const float c1sq = c1f * c1f;
             const float remf = R2mf - c1sq;
@@ -775,9 +889,8 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, i
             const float srf = sqrtf(fmaxf(remf, 0.f));
             const int n2a = max(a.n2lo, (int)floorf(-a2f - srf) - 1), n2b = min(a.n2hi, (int)ceilf(-a2f + srf) + 1);
             if (n2a > n2b) continue;
-            const double c1 = a.a1 + n1;
             const BetaEntry *row = tab + (size_t)(n1 - a.n1lo) * W2 - a.n2lo;
-            // core segment [ca, cb] of this row (empty when ca > cb)
+            // core segment [ca, cb] of this row, widened to contain N0 (empty when ca > cb)
             int ca = n2b + 1, cb = n2b;
             const float remc = Rc2f - c1sq;
             if (remc >= 0.f) {
@@ -787,72 +900,104 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, i
                 if (ca > cb) {
                     ca = n2b + 1;
                     cb = n2b;
+                } else {
+                    ca = min(ca, N0);
+                    cb = max(cb, N0);
                 }
             }
-            const double base = c1 * L.t1;
-            double rr[NH][2];
-#pragma unroll
-            for (int e = 0; e < NH; ++e) rr[e][0] = rr[e][1] = 0.0;
             if (ca <= cb) {
-                double acc[NH][2];
-                seg_sum_f64<NH>(row, ca, cb, a.a2, c1sq, a2f, R2f, L.z, RS, T, j0, jmax, acc);
-                double sp, cp;
-                sincos(base + (a.a2 + ca) * L.t2, &sp, &cp);
+                // right: n2 = cb .. N0 (index n2 - N0); left: n2 = ca .. N0-1 (index
+                // N0 - n2, e^{-i theta}) and a zero step for index 0
+                RState<NH> R, Lt;
+#pragma unroll
+                for (int e = 0; e < NH; ++e) R.d[e] = R.b[e] = Lt.d[e] = Lt.b[e] = 0.0;
+                // degree bands: |c2| >= q3 (degree 3), >= q4 (degree 4), one index of margin
+                const float q3 = sqrtf(fmaxf(b3 * b3 + k2f - c1sq, 0.f)), q4 = sqrtf(fmaxf(b4 * b4 + k2f - c1sq, 0.f));
+                {
+                    const int tot = cb - N0 + 1;
+                    const int r3 = (int)ceilf(q3 - a2f) + 1, r4 = (int)ceilf(q4 - a2f) + 1;
+                    const int m3 = max(0, cb - max(r3, N0) + 1);
+                    const int m4 = max(0, min(cb - m3, cb) - max(r4, N0) + 1);
+                    reinsch_run<NH>(R, row, cb, -1, m3, m4, tot - m3 - m4, a.a2, c1sq, a2f, R2f, L.z, RS, T, j0, jmax);
+                }
+                double rr[NH][2];
 #pragma unroll
                 for (int e = 0; e < NH; ++e) {
-                    rr[e][0] += cp * acc[e][0] - sp * acc[e][1];
-                    rr[e][1] += cp * acc[e][1] + sp * acc[e][0];
+                    const double b1 = flip_sign(R.b[e] - R.d[e], RS.m);
+                    rr[e][0] = fma(-RS.hlam, b1, R.d[e]);
+                    rr[e][1] = b1 * RS.sv;
                 }
+                if (ca < N0) {
+                    const int tot = N0 - ca;
+                    const int l3 = (int)floorf(-q3 - a2f) - 1, l4 = (int)floorf(-q4 - a2f) - 1;
+                    const int m3 = max(0, min(l3, N0 - 1) - ca + 1);
+                    const int m4 = max(0, min(l4, N0 - 1) - (ca + m3) + 1);
+                    reinsch_run<NH>(Lt, row, ca, 1, m3, m4, tot - m3 - m4, a.a2, c1sq, a2f, R2f, L.z, RS, T, j0, jmax);
+                    reinsch_zero<NH>(Lt, RS);
+#pragma unroll
+                    for (int e = 0; e < NH; ++e) {
+                        const double b1 = flip_sign(Lt.b[e] - Lt.d[e], RS.m);
+                        rr[e][0] += fma(-RS.hlam, b1, Lt.d[e]);
+                        rr[e][1] -= b1 * RS.sv;
+                    }
+                }
+#pragma unroll
+                for (int e = 0; e < NH; ++e) {
+                    const double x = rr[e][0], y = rr[e][1];
+                    rr[e][0] = A.x * x - A.y * y;
+                    rr[e][1] = A.x * y + A.y * x;
+                }
+                add_row<NH, double>(S, rr, a.a1 + n1, ik2);
             }
-            // float tails: [n2a, ca-1] and [cb+1, n2b] (the whole row when there is no core)
+            // float tails [n2a, ca-1] and [cb+1, n2b] (the whole row when there is
+            // no core), each by Horner's rule from its first index lo, moved to
+            // the anchor by e^{i(lo - N0) t2}
             const int tl_hi = (ca <= cb) ? ca - 1 : n2b;
             const int th_lo = (ca <= cb) ? cb + 1 : n2b + 1;
-            if (n2a <= tl_hi) {
-                float acc[NH][2];
-                seg_horner_f32<NH>(row, n2a, tl_hi, a2f, c1sq, R2f, zf, cvf, svf, acc);
-                float sp, cp;
-                phase_f32_reduced(base + (a.a2 + n2a) * L.t2, sp, cp);
+            if (n2a <= tl_hi || th_lo <= n2b) {
+                float tf[NH][2];
+#pragma unroll
+                for (int e = 0; e < NH; ++e) tf[e][0] = tf[e][1] = 0.f;
+                if (n2a <= tl_hi) {
+                    float acc[NH][2], ps, pc;
+                    seg_horner_f32<NH>(row, n2a, tl_hi, a2f, c1sq, R2f, zf, cvf, svf, acc);
+                    phase_m(PF, n2a - N0, ps, pc);
+#pragma unroll
+                    for (int e = 0; e < NH; ++e) {
+                        tf[e][0] += pc * acc[e][0] - ps * acc[e][1];
+                        tf[e][1] += pc * acc[e][1] + ps * acc[e][0];
+                    }
+                }
+                if (th_lo <= n2b) {
+                    float acc[NH][2], ps, pc;
+                    seg_horner_f32<NH>(row, th_lo, n2b, a2f, c1sq, R2f, zf, cvf, svf, acc);
+                    phase_m(PF, th_lo - N0, ps, pc);
+#pragma unroll
+                    for (int e = 0; e < NH; ++e) {
+                        tf[e][0] += pc * acc[e][0] - ps * acc[e][1];
+                        tf[e][1] += pc * acc[e][1] + ps * acc[e][0];
+                    }
+                }
+                const float Ax = (float)A.x, Ay = (float)A.y;
 #pragma unroll
                 for (int e = 0; e < NH; ++e) {
-                    rr[e][0] += (double)(cp * acc[e][0] - sp * acc[e][1]);
-                    rr[e][1] += (double)(cp * acc[e][1] + sp * acc[e][0]);
+                    const float x = tf[e][0], y = tf[e][1];
+                    tf[e][0] = Ax * x - Ay * y;
+                    tf[e][1] = Ax * y + Ay * x;
                 }
-            }
-            if (th_lo <= n2b) {
-                float acc[NH][2];
-                seg_horner_f32<NH>(row, th_lo, n2b, a2f, c1sq, R2f, zf, cvf, svf, acc);
-                float sp, cp;
-                phase_f32_reduced(base + (a.a2 + th_lo) * L.t2, sp, cp);
-#pragma unroll
-                for (int e = 0; e < NH; ++e) {
-                    rr[e][0] += (double)(cp * acc[e][0] - sp * acc[e][1]);
-                    rr[e][1] += (double)(cp * acc[e][1] + sp * acc[e][0]);
-                }
-            }
-            if (NF == 1) {
-                S[0][0] += rr[0][0];
-                S[0][1] += rr[0][1];
-            } else {
-                // row c1 fixed: G: A; xx: (1 - c1^2/k^2) A; yy: A - C/k^2; zz: A + D/k^2;
-                // xy: -(c1/k^2) B; xz: -(c1/k^2) E (real factor); yz: -(1/k^2) F (real factor)
-                const double fxx = 1.0 - c1 * c1 * ik2;
-                S[0][0] += rr[0][0];
-                S[0][1] += rr[0][1];
-                S[1][0] += fxx * rr[0][0];
-                S[1][1] += fxx * rr[0][1];
-                S[2][0] += rr[0][0] - ik2 * rr[2][0];
-                S[2][1] += rr[0][1] - ik2 * rr[2][1];
-                S[3][0] += rr[0][0] + ik2 * rr[3][0];
-                S[3][1] += rr[0][1] + ik2 * rr[3][1];
-                S[4][0] += -c1 * ik2 * rr[1][0];
-                S[4][1] += -c1 * ik2 * rr[1][1];
-                S[5][0] += -c1 * ik2 * rr[4][0];
-                S[5][1] += -c1 * ik2 * rr[4][1];
-                S[6][0] += -ik2 * rr[5][0];
-                S[6][1] += -ik2 * rr[5][1];
+                add_row<NH, float>(Sf, tf, c1f, ik2f);
             }
         }
         if (!L.valid) return;
+        // back from the anchor: S e^{i(alpha_2 + N0) t2}
+        double sN, cN;
+        sincos((a.a2 + N0) * L.t2, &sN, &cN);
+#pragma unroll
+        for (int e = 0; e < NS; ++e) {
+            const double x = S[e][0] + (double)Sf[e][0], y = S[e][1] + (double)Sf[e][1];
+            S[e][0] = cN * x - sN * y;
+            S[e][1] = cN * y + sN * x;
+        }
         const double2 lat = lattice_phase(a.a1, L.m1, a.a2, L.m2);
         const double2 pre = cmul(lat, make_double2(0.0, 1.0 / (8.0 * GF_PI * GF_PI)));
         double2 *o = out + (size_t)L.idx * ne;

@@ -151,6 +151,7 @@ struct EvalArgs {
     const int *nprop;       // their number (device)
     const double *exptab;   // e^{-(j - exptab_j0)/128}, j = 0 .. exptab_n - 1
     int exptab_n, exptab_j0;
+    double bmin;            // smallest |beta_n| over the evanescent n (this value or a larger one, never smaller)
 };
 
 // Far targets are bucketed by b = floor(NB c / |x_last|) (clamped to NB-1) so

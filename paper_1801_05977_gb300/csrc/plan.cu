@@ -119,6 +119,7 @@ struct gf_plan_s {
     cudaStream_t stream = nullptr;    // stream of the plan's creation
     double *exptab = nullptr;         // e^{-(j - exptab_j0)/128}
     int exptab_n = 0, exptab_j0 = 0;
+    double bmin_ev = 1e300;           // smallest evanescent |beta_n|
     int n1lo = 0, n1hi = -1, n2lo = 0, n2hi = -1;
     SynthArgs sa{};
     // eval scratch (far list + counter) and host-call staging, grown on demand
@@ -200,7 +201,7 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
     const double a1 = alpha[0], a2 = dim == 3 ? alpha[1] : 0.0;
 
     // Wood anomaly (Sec. 1): beta_n = 0 for some n.  Only |alpha_n| ~ k matters.
-    double bmin_ev = 1.0;
+    double bmin_ev = 1e300;
     {
         int R = (int)ceil(k) + 2;
         int r2 = dim == 3 ? R : 0;
@@ -248,6 +249,7 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
     p->alpha[1] = a2;
     for (int i = 0; i < 3; ++i) p->M[i] = i < dim ? M[i] : 1;
     p->tr = tr;
+    p->bmin_ev = bmin_ev;
     p->precision = tr.precision;
     p->kind = tr.kind;
     p->nf = tr.kind == GF_MAXWELL ? 7 : 1;
@@ -424,7 +426,7 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
             // T[j] = e^{-(j - j0)/128}: the core weights e^{-y}, y = b|x3| + ln b,
             // of a lane's truncation set (b|x3| <= T) have ln(bmin) <= y <= T + ln(bmax),
             // bmax <= sqrt(2) (Rc + 2) over the index box
-            p->exptab_j0 = 128 * ((int)ceil(-log(bmin_ev)) + 1);
+            p->exptab_j0 = 128 * ((int)ceil(-log(fmin(bmin_ev, 1.0))) + 1);
             if (p->exptab_j0 < 128) p->exptab_j0 = 128;
             p->exptab_n = p->exptab_j0 + 128 * ((int)ceil(p->T + log(1.4143 * (Rc + 2.0))) + 2) + 1;
             const bool want_exp = p->precision == GF_FP64;
@@ -553,6 +555,7 @@ gf_status gf_eval_points(gf_plan_t p, const double *dev_xyz, int64_t n, int whic
     a.exptab = p->exptab;
     a.exptab_n = p->exptab_n;
     a.exptab_j0 = p->exptab_j0;
+    a.bmin = p->bmin_ev;
     if (p->timing) cudaEventRecord(p->ev[3], st);
     CU(gf_launch_eval(a, p->precision, st, p->timing ? p->ev[4] : nullptr));
     if (p->timing) {
@@ -609,6 +612,7 @@ gf_status gf_plan_eval_args(gf_plan_t p, const double *dev_xyz, int64_t n, int w
     a.exptab = p->exptab;
     a.exptab_n = p->exptab_n;
     a.exptab_j0 = p->exptab_j0;
+    a.bmin = p->bmin_ev;
     *a_out = a;
     return GF_OK;
 }
