@@ -429,7 +429,7 @@ __device__ __forceinline__ void set_entry(BetaEntry &e, double b, double ib)
     e.bl2 = (float)(b * 1.4426950408889634);  // b log2(e)
     e.ibf = (float)ib;
     e.bf = (float)b;
-    e.pad = 0.f;
+    e.lnbf = (float)e.lnb;
 }
 __device__ __forceinline__ void set_entry(BetaEntryF &e, double b, double ib)
 {
@@ -444,7 +444,7 @@ __device__ __forceinline__ void set_entry(BetaEntryF &e, double b, double ib)
 // of propagating indices in row-major order of the sub-box pbox = [n1lo, n1hi,
 // n2lo, n2hi] (ballot compaction keeps the order fixed).
 template <typename E>
-__global__ void series_tables(EvalArgs a, E *tab, double *exptab, PropEntry *prop, int *nprop, int4 pbox)
+__global__ void series_tables(EvalArgs a, E *tab, double2 *exptab, PropEntry *prop, int *nprop, int4 pbox)
 {
     const int W2 = a.n2hi - a.n2lo + 1;
     const int tot = (a.n1hi - a.n1lo + 1) * W2;
@@ -463,7 +463,10 @@ __global__ void series_tables(EvalArgs a, E *tab, double *exptab, PropEntry *pro
     }
     if (exptab)
         for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.exptab_n; j += gridDim.x * blockDim.x)
-            exptab[j] = exp(-(double)(j - a.exptab_j0) * 0.0078125);
+        {
+            const double off = (double)(j - a.exptab_j0) * 0.0078125;
+            exptab[j] = make_double2(exp(-off), off);
+        }
     if (blockIdx.x == 0 && threadIdx.x < 32) {
         const int pw = pbox.w - pbox.z + 1, ptot = (pbox.y - pbox.x + 1) * pw;
         int cnt = 0;
@@ -494,20 +497,24 @@ __device__ __forceinline__ double warp_max(double v)
     return v;
 }
 
-// e^{-y} by Tang's table-driven method (ACM TOMS 15, 1989): y = j/128 + r with
-// j = rint(128 y) and |r| <= 1/256; e^{-y} = T[j + j0] e^{-r}, T[i] = e^{-(i - j0)/128}
-// a plan table.  Returns e^{-r} by its Taylor polynomial of degree DEG and the
-// table index, clamped to the table (callers discard the terms whose y lies
-// beyond it).  Truncation relative to e^{-y}: 4.9e-18 (DEG 5), 7.6e-15 (DEG 4),
-// 9.7e-12 (DEG 3); callers take DEG 4 and 3 only for terms at least e^7 and
+// e^{-y} by Tang's table-driven method (ACM TOMS 15, 1989): y = y_j + r with
+// y_j = (j - j0)/128, |r| <= (1/2 + 3e-3)/128; e^{-y} = T[j] e^{-r}, the plan
+// table holding (e^{-y_j}, y_j).  The index is rint(128 yf) + j0 for a float
+// evaluation yf of y (|128 (yf - y)| < 3e-3 for |y| < 100, rounding by the
+// 1.5 * 2^23 shift), clamped to the table (callers discard the terms whose y
+// lies beyond it).  Returns e^{-r} by its Taylor polynomial of degree DEG and
+// T[j].x.  Truncation relative to e^{-y}: 5e-18 (DEG 5), 7.7e-15 (DEG 4),
+// 9.9e-12 (DEG 3); callers take DEG 4 and 3 only for terms at least e^7 and
 // e^14 below the largest term of the series.
 template <int DEG>
-__device__ __forceinline__ double exp_neg_split(double y, int j0, int jmax, int &idx)
+__device__ __forceinline__ double exp_neg_split(double y, float yf, const double2 *__restrict__ T, int j0, int jmax,
+                                                double &Tj)
 {
-    const double MAGIC = 6755399441055744.0;  // 1.5 * 2^52: rint by addition
-    const double t = fma(y, 128.0, MAGIC);
-    idx = min(max(__double2loint(t) + j0, 0), jmax);
-    const double r = fma(t - MAGIC, -0.0078125, y);
+    const float jm = fmaf(128.0f, yf, 12582912.0f);
+    const int idx = min(max(__float_as_int(jm) - 0x4B400000 + j0, 0), jmax);
+    const double2 t = __ldg(T + idx);
+    const double r = y - t.y;
+    Tj = t.x;
     double p;
     if (DEG >= 5) {
         p = fma(r, -1.0 / 120.0, 1.0 / 24.0);
@@ -574,13 +581,14 @@ struct Reinsch {
     int m;  // sign bit of s
 };
 
-__device__ __forceinline__ Reinsch reinsch_lane(double theta, double sv, double cv)
+__device__ __forceinline__ Reinsch reinsch_lane(double sv, double cv)
 {
+    // 2 - 2 cos = 2 sin^2/(1 + cos) and 2 + 2 cos = 2 sin^2/(1 - cos), free of
+    // cancellation on the side where each is used
     Reinsch R;
-    double sh, ch;
-    sincos(0.5 * theta, &sh, &ch);
+    const double s2 = 2.0 * sv * sv;
     R.m = cv >= 0.0 ? 0 : (int)0x80000000;
-    R.lam = cv >= 0.0 ? -4.0 * sh * sh : 4.0 * ch * ch;
+    R.lam = cv >= 0.0 ? -s2 / (1.0 + cv) : s2 / (1.0 - cv);
     R.hlam = 0.5 * R.lam;
     R.sv = sv;
     return R;
@@ -602,17 +610,17 @@ struct RState {
 template <int NH, int DEG>
 __device__ __forceinline__ void reinsch_seg(RState<NH> &st, const BetaEntry *__restrict__ row, int &n2, int count,
                                             int dir, float &c2f, double &c2, float c1sq, float R2f, double z,
-                                            const Reinsch &RS, const double *__restrict__ T, int j0, int jmax)
+                                            const Reinsch &RS, const double2 *__restrict__ T, int j0, int jmax)
 {
+    const float zf = (float)z;
     const float df = (float)dir;
     const double dd = (double)dir;
     for (int i = 0; i < count; ++i, n2 += dir, c2f += df) {
         const BetaEntry be = row[n2];
         const bool ok = fmaf(c2f, c2f, c1sq) <= R2f && be.ibf != 0.f;
-        int j;
-        double p = exp_neg_split<DEG>(fma(be.b, z, be.lnb), j0, jmax, j);
+        double Tj;
+        double p = exp_neg_split<DEG>(fma(be.b, z, be.lnb), fmaf(be.bf, zf, be.lnbf), T, j0, jmax, Tj);
         p = ok ? p : 0.0;
-        const double Tj = __ldg(T + j);
         if (NH == 1) {
             const double dn = fma(RS.lam, st.b[0], fma(Tj, p, flip_sign(st.d[0], RS.m)));
             st.b[0] = dn + flip_sign(st.b[0], RS.m);
@@ -642,7 +650,7 @@ __device__ __forceinline__ void reinsch_seg(RState<NH> &st, const BetaEntry *__r
 template <int NH>
 __device__ __forceinline__ void reinsch_run(RState<NH> &st, const BetaEntry *__restrict__ row, int start, int dir,
                                             int n3, int n4, int n5, double a2, float c1sq, float a2f, float R2f,
-                                            double z, const Reinsch &RS, const double *__restrict__ T, int j0, int jmax)
+                                            double z, const Reinsch &RS, const double2 *__restrict__ T, int j0, int jmax)
 {
     int n2 = start;
     float c2f = a2f + (float)start;
@@ -803,7 +811,7 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, i
     const int lane = threadIdx.x & 31;
     const double k2 = a.k * a.k, ik2 = 1.0 / k2;
     const float ik2f = (float)ik2;
-    const double *T = a.exptab;
+    const double2 *T = a.exptab;
     const int jmax = a.exptab_n - 1, j0 = a.exptab_j0;
     const float a2f = (float)a.a2;
     // every row is summed from the anchor n2 = N0 outwards (the centre of all
@@ -821,7 +829,7 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, i
         sincos(L.t2, &sv, &cv);
         sincos(L.t1, &s1, &c1v);
         const double2 E1 = make_double2(c1v, s1);
-        const Reinsch RS = reinsch_lane(L.t2, sv, cv);
+        const Reinsch RS = reinsch_lane(sv, cv);
         const PhaseF PF = phase_split(L.t2);
         // every term is at most e^{-(b - bmin) z_min} of the largest one (e^{-bz}/b
         // decreases in b): degree 4 from b >= bmin + 7/z_min, 3 from bmin + 14/z_min
@@ -835,11 +843,24 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, i
         for (int e = 0; e < NF; ++e) P[e][0] = P[e][1] = 0.0;
 #pragma unroll
         for (int e = 0; e < NS; ++e) S[e][0] = S[e][1] = 0.0, Sf[e][0] = Sf[e][1] = 0.f;
+        // propagating terms, in the anchor frame: e^{i(c1 t1 + (c2 - alpha_2 - N0) t2)};
+        // the list is in row-major order, so within a row the phase steps by e^{i t2}
+        double2 ph = make_double2(1.0, 0.0);
+        double pc1 = 0.0, pc2 = 0.0;
         for (int q = 0, nq = slab == 0 ? *a.nprop : 0; q < nq; ++q) {
             const PropEntry pe = a.prop[q];
-            double sz, cz, sp, cp;
+            if (q > 0 && pe.c1 == pc1 && fabs(pe.c2 - pc2 - 1.0) < 0.5) {
+                ph = cmul(ph, make_double2(cv, sv));
+            } else {
+                double sp, cp;
+                sincos(pe.c1 * L.t1 + ((pe.c2 - a.a2) - N0) * L.t2, &sp, &cp);
+                ph = make_double2(cp, sp);
+            }
+            pc1 = pe.c1;
+            pc2 = pe.c2;
+            double sz, cz;
             sincos(pe.br * L.z, &sz, &cz);
-            sincos(pe.c1 * L.t1 + pe.c2 * L.t2, &sp, &cp);
+            const double cp = ph.x, sp = ph.y;
             double tx = pe.ibr * (cz * cp - sz * sp), ty = pe.ibr * (cz * sp + sz * cp);
             P[0][0] += tx;
             P[0][1] += ty;
@@ -989,17 +1010,18 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, i
             }
         }
         if (!L.valid) return;
-        // back from the anchor: S e^{i(alpha_2 + N0) t2}
-        double sN, cN;
-        sincos((a.a2 + N0) * L.t2, &sN, &cN);
 #pragma unroll
         for (int e = 0; e < NS; ++e) {
-            const double x = S[e][0] + (double)Sf[e][0], y = S[e][1] + (double)Sf[e][1];
-            S[e][0] = cN * x - sN * y;
-            S[e][1] = cN * y + sN * x;
+            S[e][0] += (double)Sf[e][0];
+            S[e][1] += (double)Sf[e][1];
         }
-        const double2 lat = lattice_phase(a.a1, L.m1, a.a2, L.m2);
-        const double2 pre = cmul(lat, make_double2(0.0, 1.0 / (8.0 * GF_PI * GF_PI)));
+        // back from the anchor frame with the lattice phase: one factor
+        // e^{i(2 pi <alpha.m> + (alpha_2 + N0) t2)} (i/8pi^2)
+        double ph2 = a.a1 * L.m1 + a.a2 * L.m2;
+        ph2 -= rint(ph2);
+        double sN, cN;
+        sincos(fma(2.0 * GF_PI, ph2, (a.a2 + N0) * L.t2), &sN, &cN);
+        const double2 pre = make_double2(-sN / (8.0 * GF_PI * GF_PI), cN / (8.0 * GF_PI * GF_PI));
         double2 *o = out + (size_t)L.idx * ne;
         // evanescent sums carry the factor -i (from 1/beta = -i/b), except the
         // xz, yz entries whose factor (-i)(-i sgn) = -sgn is real
@@ -1369,7 +1391,7 @@ cudaError_t gf_launch_eval_batch(const EvalBatch &b, int precision, cudaStream_t
     return precision == GF_FP64 ? launch_eval_batch_t<double>(b, s) : launch_eval_batch_t<float>(b, s);
 }
 
-cudaError_t gf_launch_series_tables(const EvalArgs &a, int precision, double *exptab, PropEntry *prop, int *nprop,
+cudaError_t gf_launch_series_tables(const EvalArgs &a, int precision, double2 *exptab, PropEntry *prop, int *nprop,
                                     const int pbox[4], cudaStream_t s)
 {
     const int4 pb = make_int4(pbox[0], pbox[1], pbox[2], pbox[3]);

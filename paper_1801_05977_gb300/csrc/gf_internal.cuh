@@ -117,8 +117,8 @@ struct SynthArgs {
 // for evanescent n (beta_n = i b); zeros for propagating n (|alpha_n| <= k).
 // The double-precision core sums the weights e^{-b|x3|}/b = e^{-(b|x3| + ln b)}.
 struct BetaEntry {
-    double b, lnb;           // double-precision core terms
-    float bl2, ibf, bf, pad; // b log2(e), 1/b, b in float for the exponentially small tail
+    double b, lnb;             // double-precision core terms
+    float bl2, ibf, bf, lnbf;  // b log2(e), 1/b, b for the float tail; ln b for the table index
 };
 struct BetaEntryF {
     float bl2, ib, b, pad;  // b log2(e), 1/b, b
@@ -149,7 +149,7 @@ struct EvalArgs {
     int n1lo, n1hi, n2lo, n2hi;
     const PropEntry *prop;  // propagating indices (|alpha_n| <= k)
     const int *nprop;       // their number (device)
-    const double *exptab;   // e^{-(j - exptab_j0)/128}, j = 0 .. exptab_n - 1
+    const double2 *exptab;  // (e^{-(j - exptab_j0)/128}, (j - exptab_j0)/128), j = 0 .. exptab_n - 1
     int exptab_n, exptab_j0;
     double bmin;            // smallest |beta_n| over the evanescent n (this value or a larger one, never smaller)
 };
@@ -189,7 +189,7 @@ cudaError_t gf_launch_cheb_table(const double *rr, const double2 *B, int Q, int 
                                  cudaStream_t s);
 cudaError_t gf_launch_synth_batch(const SynthBatch &b, int precision, cudaStream_t s);
 cudaError_t gf_launch_eval_batch(const EvalBatch &b, int precision, cudaStream_t s);
-cudaError_t gf_launch_series_tables(const EvalArgs &a, int precision, double *exptab, PropEntry *prop, int *nprop,
+cudaError_t gf_launch_series_tables(const EvalArgs &a, int precision, double2 *exptab, PropEntry *prop, int *nprop,
                                     const int pbox[4], cudaStream_t s);
 cudaError_t gf_launch_e_table(const double *tt, int Q, int Mlast, double ct, double2 *E, cudaStream_t s);
 
