@@ -271,7 +271,7 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
     gauss_legendre(Q, gx, gw);
     const double c = tr.c, ct = tr.c_tilde, eps = tr.eps, cm = 0.5 * (c + ct);
     std::vector<double> tt(Q), tW(Q), rr(Q), P0(Q, 0.0), P1(Q, 0.0);
-    std::vector<double2> B(Q), E((size_t)Mlast * Q);
+    std::vector<double2> B(Q);
     {
         double hw = 0.5 * (cm - c), mid = 0.5 * (cm + c);
         for (int m = 0; m < Q; ++m) {
@@ -293,22 +293,24 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
             P0[m] = wr * ph1 * r;
             P1[m] = wr * ph1 * r * r;
         }
-        for (int b = 0; b < Mlast; ++b) {
-            int jl = b < Mlast / 2 ? b : b - Mlast;
-            double q = (double)jl * GF_PI / ct;
-            for (int m = 0; m < Q; ++m) E[(size_t)b * Q + m] = make_double2(cos(q * tt[m]), sin(q * tt[m]));
-        }
     }
-    // 3D: piecewise Chebyshev interpolant of h(s) = sum_m B_m sin(s r_m)/s on
-    // [0, s_max], s_max >= max_j |xi_j|; degree 14, panels of width 2.
+    // Piecewise Chebyshev interpolants (degree 14, panels of width 2) of the
+    // radial transforms on [0, s_max], s_max >= the largest frequency norm:
+    // 3D h(s) = sum_m B_m sin(s r_m)/s, 2D the Bessel sums of F1-hat, F2-hat.
+    // (computed on the device from the quadrature tables, see gf_launch_cheb_table)
     const int hdeg = 14;
     const double hpan = 2.0;
     int hnpan = 1;
-    // (computed on the device from the quadrature tables, see gf_launch_cheb_table)
     size_t hcheb_n = 0;
-    if (dim == 3) {
-        double m1 = fabs(a1) + M[0] / 2 + 1, m2 = fabs(a2) + M[1] / 2 + 1, m3 = (M[2] / 2 + 1) * GF_PI / ct;
-        double smax = sqrt(m1 * m1 + m2 * m2 + m3 * m3) + hpan;
+    {
+        double smax;
+        if (dim == 3) {
+            double m1 = fabs(a1) + M[0] / 2 + 1, m2 = fabs(a2) + M[1] / 2 + 1, m3 = (M[2] / 2 + 1) * GF_PI / ct;
+            smax = sqrt(m1 * m1 + m2 * m2 + m3 * m3) + hpan;
+        } else {
+            double m1 = M[0] / 2 + 1, m2 = (M[1] / 2 + 1) * GF_PI / ct;
+            smax = sqrt(m1 * m1 + m2 * m2) + hpan;
+        }
         hnpan = (int)ceil(smax / hpan) + 1;
         hcheb_n = (size_t)hnpan * (hdeg + 1);
     }
@@ -360,8 +362,8 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
             memcpy(hb + ((char *)d_P1 - tb), P1.data(), sizeof(double) * Q);
             memcpy(hb + ((char *)d_B - tb), B.data(), sizeof(double2) * Q);
             if ((e = gf_stage_upload(tb, hb, host_tab_bytes, st)) != cudaSuccess ||
-                (e = gf_launch_e_table(d_tt, Q, Mlast, ct, d_E, st)) != cudaSuccess ||
-                (hcheb_n && (e = gf_launch_cheb_table(d_rr, d_B, Q, hnpan, hdeg, hpan, d_H, st)) != cudaSuccess)) {
+                (e = gf_launch_e_table(d_tt, Q, Mlast, GF_PI / ct, d_E, st)) != cudaSuccess ||
+                (e = gf_launch_cheb_table(dim, d_rr, d_B, d_P0, d_P1, Q, hnpan, hdeg, hpan, d_H, st)) != cudaSuccess) {
                 st_err = fail(GF_ERR_CUDA, "gf_plan: tables: %s", cudaGetErrorString(e));
                 break;
             }
@@ -380,6 +382,7 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
         sa.a1 = a1;
         sa.a2 = a2;
         sa.ct = ct;
+        sa.qs = GF_PI / ct;
         // smallest g with e^{-g c}/(2 g^2) < 1e-20 (the function decreases in g)
         {
             double g = 1.0;
@@ -396,6 +399,7 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
         sa.hdeg = hdeg;
         sa.hnpan = hnpan;
         sa.hpan = hpan;
+        sa.ihpan = 1.0 / hpan;
         sa.Pw0 = d_P0;
         sa.Pw1 = d_P1;
         sa.F10 = F10;

@@ -117,7 +117,7 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
         int t = i >> lg, b = i & (n - 1);
         int col = col0 + t;
         int jl = freq_of(b, n);
-        double q = (double)jl * GF_PI / a.ct;
+        double q = (double)jl * a.qs;
         double2 beta = betas[t];
         double A2 = A2s[t];
         const double2 *Am = Av + t * Q;
@@ -129,7 +129,19 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
         // the two terms are below double rounding of C and are not formed; else
         // T1 - T2 = [I1 (g - i q) + I2 (g + i q)] / (2 g (g^2 + q^2)).
         double2 T12 = make_double2(0.0, 0.0);
-        if (beta.y <= a.gskip) {
+        if (beta.y > 0.0 && beta.y <= a.gskip) {
+            // evanescent: A_m is real, I1 = s1 - i s3, I2 = s1 + i s3 (two real sums),
+            // and T1 - T2 = (g s1 - q s3)/(g (g^2 + q^2)) is real
+            double s1 = 0.0, s3 = 0.0;
+            for (int m = 0; m < Q; ++m) {
+                const double A = Am[m].x;
+                const double2 E = Em[m];
+                s1 = fma(A, E.x, s1);
+                s3 = fma(A, E.y, s3);
+            }
+            const double g = beta.y;
+            T12.x = (g * s1 - q * s3) / (g * (g * g + q * q));
+        } else if (beta.y <= a.gskip) {
             double s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0;
             for (int m = 0; m < Q; ++m) {
                 double2 A = Am[m], E = Em[m];
@@ -138,20 +150,13 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
                 s3 = fma(A.x, E.y, s3);
                 s4 = fma(A.y, E.x, s4);
             }
+            // propagating beta (real)
             double2 I1 = make_double2(s1 + s2, s4 - s3);
             double2 I2 = make_double2(s1 - s2, s3 + s4);
-            if (beta.y > 0.0) {
-                const double g = beta.y;
-                const double den = 1.0 / (2.0 * g * (g * g + q * q));
-                // I1 (g - i q) + I2 (g + i q)
-                T12.x = (g * (I1.x + I2.x) + q * (I1.y - I2.y)) * den;
-                T12.y = (g * (I1.y + I2.y) - q * (I1.x - I2.x)) * den;
-            } else {
-                double2 tb = cscale(beta, 2.0);
-                double2 T1 = cdiv(I1, cmul(tb, make_double2(q - beta.x, -beta.y)));
-                double2 T2 = cdiv(I2, cmul(tb, make_double2(q + beta.x, beta.y)));
-                T12 = csub(T1, T2);
-            }
+            double2 tb = cscale(beta, 2.0);
+            double2 T1 = cdiv(I1, cmul(tb, make_double2(q - beta.x, -beta.y)));
+            double2 T2 = cdiv(I2, cmul(tb, make_double2(q + beta.x, beta.y)));
+            T12 = csub(T1, T2);
         }
         double D = A2 + q * q - k2;
         double2 Cj;
@@ -160,7 +165,7 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
             // interpolant (Clenshaw); h has bandwidth 2 eps in s, so degree 14 on
             // panels of width 2 reproduces the quadrature to rounding.
             double s = sqrt(A2 + q * q);
-            int pnl = min((int)(s / a.hpan), a.hnpan - 1);
+            int pnl = min((int)(s * a.ihpan), a.hnpan - 1);
             double x = (s - (pnl + 0.5) * a.hpan) * (2.0 / a.hpan);
             const double2 *cc = a.hcheb + (size_t)pnl * (a.hdeg + 1);
             double b1r = 0.0, b1i = 0.0, b2r = 0.0, b2i = 0.0;
@@ -186,13 +191,24 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
                 F1 = make_double2(a.F10, 0.0);
                 F2 = make_double2(0.0, 0.0);
             } else {
+                // S0 = sum_m P0_m J0(eta r_m), S1 = sum_m P1_m J1(eta r_m) from their
+                // piecewise Chebyshev interpolants (band-limited in eta: r_m <= 2 eps)
                 double eta = sqrt(eta2);
-                double S0 = 0.0, S1 = 0.0;
-                for (int m = 0; m < Q; ++m) {
-                    double z = eta * a.rr[m];
-                    S0 = fma(a.Pw0[m], j0(z), S0);
-                    S1 = fma(a.Pw1[m], j1(z), S1);
+                int pnl = min((int)(eta * a.ihpan), a.hnpan - 1);
+                double x = (eta - (pnl + 0.5) * a.hpan) * (2.0 / a.hpan);
+                const double2 *cc = a.hcheb + (size_t)pnl * (a.hdeg + 1);
+                double b1r = 0.0, b1i = 0.0, b2r = 0.0, b2i = 0.0;
+                for (int kk = a.hdeg; kk >= 1; --kk) {
+                    double2 ck = cc[kk];
+                    double tr = fma(2.0 * x, b1r, ck.x - b2r);
+                    double ti = fma(2.0 * x, b1i, ck.y - b2i);
+                    b2r = b1r;
+                    b2i = b1i;
+                    b1r = tr;
+                    b1i = ti;
                 }
+                const double S0 = fma(x, b1r, cc[0].x - b2r);
+                const double S1 = fma(x, b1i, cc[0].y - b2i);
                 // F1 = (1 + Phi1-hat/(2 pi))/eta^2,  Phi1-hat/(2 pi) = S0
                 F1 = make_double2((1.0 + S0) / eta2, 0.0);
                 // F2 = (-2 i j1 F1 + Phi2-hat/(2 pi))/eta^2,  Phi2-hat/(2 pi) = -i (j1/eta) S1
@@ -506,66 +522,91 @@ cudaError_t gf_launch_synth(const SynthArgs &a, int precision, cudaStream_t s)
 }
 
 namespace {
-// Piecewise Chebyshev interpolant of h(s) = sum_m B_m sin(s r_m)/s: one CTA per
-// panel [p w, (p+1) w]; values at the nn Chebyshev points, then the discrete
+// Piecewise Chebyshev interpolants of the radial transforms, one CTA per panel
+// [p w, (p+1) w]: values at the nn <= 16 Chebyshev points (sixteen threads per
+// point share the quadrature sum, reduced by shuffles), then the discrete
 // cosine transform to coefficients.
-__global__ void cheb_table_kernel(const double *rr, const double2 *B, int Q, int nn, double w, double2 *out)
+//   3D: h(s) = sum_m B_m sin(s r_m)/s (complex).
+//   2D: (S0, S1)(s) = (sum_m P0_m J0(s r_m), sum_m P1_m J1(s r_m)) (two real functions).
+template <int DIM>
+__global__ void __launch_bounds__(256) cheb_table_kernel(const double *rr, const double2 *B, const double *P0,
+                                                         const double *P1, int Q, int nn, double w, double2 *out)
 {
-    __shared__ double2 fv[64];
-    const int p = blockIdx.x, k = threadIdx.x;
+    __shared__ double2 fv[16];
+    const int p = blockIdx.x, t = threadIdx.x, k = t >> 4, g = t & 15;
     const double cen = (p + 0.5) * w, hh = 0.5 * w;
+    double ar = 0.0, ai = 0.0, s = 0.0;
     if (k < nn) {
-        const double s = cen + hh * cospi((k + 0.5) / nn);
-        double hr = 0.0, hi = 0.0;
-        for (int m = 0; m < Q; ++m) {
-            const double ker = (s == 0.0) ? rr[m] : sin(s * rr[m]) / s;
-            hr = fma(B[m].x, ker, hr);
-            hi = fma(B[m].y, ker, hi);
+        s = cen + hh * cospi((k + 0.5) / nn);
+        for (int m = g; m < Q; m += 16) {
+            const double z = s * rr[m];
+            if (DIM == 3) {
+                const double ker = (s == 0.0) ? rr[m] : sin(z);
+                ar = fma(B[m].x, ker, ar);
+                ai = fma(B[m].y, ker, ai);
+            } else {
+                ar = fma(P0[m], j0(z), ar);
+                ai = fma(P1[m], j1(z), ai);
+            }
         }
-        fv[k] = make_double2(hr, hi);
+    }
+    for (int o = 8; o > 0; o >>= 1) {
+        ar += __shfl_xor_sync(0xffffffffu, ar, o);
+        ai += __shfl_xor_sync(0xffffffffu, ai, o);
+    }
+    if (k < nn && g == 0) {
+        if (DIM == 3 && s != 0.0) {
+            ar /= s;
+            ai /= s;
+        }
+        fv[k] = make_double2(ar, ai);
     }
     __syncthreads();
-    if (k < nn) {
+    if (t < nn) {
         double cr = 0.0, ci = 0.0;
         for (int q = 0; q < nn; ++q) {
-            const double c = cospi((double)k * (q + 0.5) / nn);
+            const double c = cospi((double)t * (q + 0.5) / nn);
             cr = fma(fv[q].x, c, cr);
             ci = fma(fv[q].y, c, ci);
         }
-        const double sc = (k == 0 ? 1.0 : 2.0) / nn;
-        out[(size_t)p * nn + k] = make_double2(cr * sc, ci * sc);
+        const double sc = (t == 0 ? 1.0 : 2.0) / nn;
+        out[(size_t)p * nn + t] = make_double2(cr * sc, ci * sc);
     }
 }
 }  // namespace
 
-// E[b][m] = e^{i q_b t_m}, q_b = j pi / c~ with j = b for b < Mlast/2, else
+// E[b][m] = e^{i q_b t_m}, q_b = j qs (qs = pi / c~) with j = b for b < Mlast/2, else
 // b - Mlast (the last-axis frequencies of Eq. (fck-coef)), t_m the Gauss nodes
 // of the X' integrals.
-__global__ void e_table_kernel(const double *tt, int Q, int Mlast, double ct, double2 *E)
+__global__ void e_table_kernel(const double *tt, int Q, int Mlast, double qs, double2 *E)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Mlast * Q; i += gridDim.x * blockDim.x) {
         const int b = i / Q, m = i - b * Q;
         const int jl = b < Mlast / 2 ? b : b - Mlast;
-        const double q = (double)jl * GF_PI / ct;
+        const double q = (double)jl * qs;
         double sv, cv;
         sincos(q * tt[m], &sv, &cv);
         E[i] = make_double2(cv, sv);
     }
 }
 
-cudaError_t gf_launch_e_table(const double *tt, int Q, int Mlast, double ct, double2 *E, cudaStream_t s)
+cudaError_t gf_launch_e_table(const double *tt, int Q, int Mlast, double qs, double2 *E, cudaStream_t s)
 {
     int blocks = (Mlast * Q + 255) / 256;
     if (blocks > 1024) blocks = 1024;
-    e_table_kernel<<<blocks, 256, 0, s>>>(tt, Q, Mlast, ct, E);
+    e_table_kernel<<<blocks, 256, 0, s>>>(tt, Q, Mlast, qs, E);
     gf_count_launch(1);
     return cudaGetLastError();
 }
 
-cudaError_t gf_launch_cheb_table(const double *rr, const double2 *B, int Q, int npan, int deg, double w, double2 *out,
-                                 cudaStream_t s)
+cudaError_t gf_launch_cheb_table(int dim, const double *rr, const double2 *B, const double *P0, const double *P1, int Q,
+                                 int npan, int deg, double w, double2 *out, cudaStream_t s)
 {
-    cheb_table_kernel<<<npan, 64, 0, s>>>(rr, B, Q, deg + 1, w, out);
+    if (deg + 1 > 16 || npan < 1) return cudaErrorInvalidValue;
+    if (dim == 3)
+        cheb_table_kernel<3><<<npan, 256, 0, s>>>(rr, B, P0, P1, Q, deg + 1, w, out);
+    else
+        cheb_table_kernel<2><<<npan, 256, 0, s>>>(rr, B, P0, P1, Q, deg + 1, w, out);
     gf_count_launch(1);
     return cudaGetLastError();
 }
