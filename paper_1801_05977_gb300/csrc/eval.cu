@@ -1266,7 +1266,9 @@ __global__ void far3d_batch(const EvalArgs *args, int np)
 
 // ---------------------------------------------------------------------------
 // 2D far kernel: G = e^{i2pi alpha m} (i/4pi) sum_n beta_n^{-1} e^{i alpha_n t + i beta_n |x2|}
-// (terms and sums in double for both precisions; the 1D series is short).
+// (terms and sums in double for both precisions).  One warp per target: lane l
+// takes n = na + l, na + l + 32, ... (phase e^{i alpha_n t} from a sincos and the
+// step e^{i 32 t}), and the lanes' sums are added by shuffles.
 // ---------------------------------------------------------------------------
 template <typename R>
 __global__ void __launch_bounds__(128) far2d(EvalArgs a)
@@ -1275,46 +1277,51 @@ __global__ void __launch_bounds__(128) far2d(EvalArgs a)
     C *out = reinterpret_cast<C *>(a.out);
     const int count = *a.far_count;
     const double k2 = a.k * a.k;
-    for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < count; slot += gridDim.x * blockDim.x) {
-        int idx = a.far_idx[slot];
-        double x1 = a.x[2 * (size_t)idx], x2 = a.x[2 * (size_t)idx + 1];
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int slot = gw; slot < count; slot += nw) {
+        const int idx = a.far_idx[slot];
+        const double x1 = a.x[2 * (size_t)idx], x2 = a.x[2 * (size_t)idx + 1];
         double t, m;
         reduce_period(x1, t, m);
-        double z = fabs(x2);
-        double Tz = a.T / z;
-        double R2 = k2 + Tz * Tz, Rr = sqrt(R2);
-        int na = (int)floor(-a.a1 - Rr) - 1, nb = (int)ceil(-a.a1 + Rr) + 1;
-        double st, ct;
-        sincos(t, &st, &ct);
-        const double2 step = make_double2(ct, st);
-        double sp, cp;
-        sincos((a.a1 + na) * t, &sp, &cp);
+        const double z = fabs(x2);
+        const double Tz = a.T / z;
+        const double R2 = k2 + Tz * Tz, Rr = sqrt(R2);
+        const int na = (int)floor(-a.a1 - Rr) - 1, nb = (int)ceil(-a.a1 + Rr) + 1;
+        double sp, cp, s32, c32;
+        sincos((a.a1 + (na + lane)) * t, &sp, &cp);
+        sincos(32.0 * t, &s32, &c32);
         double2 p = make_double2(cp, sp);
+        const double2 step = make_double2(c32, s32);
         double sr = 0, si = 0;
-        for (int n = na; n <= nb; ++n) {
-            double c1 = a.a1 + n;
-            double A2 = c1 * c1;
-            if (A2 <= R2) {
-                double aa = fabs(c1);
-                double2 term;
-                if (aa <= a.k) {
-                    double b = sqrt((a.k - aa) * (a.k + aa));
-                    double sz, cz;
-                    sincos(b * z, &sz, &cz);
-                    term = cscale(cmul(make_double2(cz, sz), p), 1.0 / b);
-                } else {
-                    double b = sqrt((aa - a.k) * (aa + a.k));
-                    double e = exp(-b * z) / b;
-                    term = cmul(make_double2(0.0, -e), p);  // (1/(i b)) e^{-b z} p
-                }
-                sr += term.x;
-                si += term.y;
+        for (int n = na + lane; n <= nb; n += 32, p = cmul(p, step)) {
+            const double c1 = a.a1 + n;
+            if (c1 * c1 > R2) continue;
+            const double aa = fabs(c1);
+            double2 term;
+            if (aa <= a.k) {
+                const double b = sqrt((a.k - aa) * (a.k + aa));
+                double sz, cz;
+                sincos(b * z, &sz, &cz);
+                term = cscale(cmul(make_double2(cz, sz), p), 1.0 / b);
+            } else {
+                const double b = sqrt((aa - a.k) * (aa + a.k));
+                const double e = exp(-b * z) / b;
+                term = cmul(make_double2(0.0, -e), p);  // (1/(i b)) e^{-b z} p
             }
-            p = cmul(p, step);
+            sr += term.x;
+            si += term.y;
         }
-        double2 lat = lattice_phase(a.a1, m, 0.0, 0.0);
-        double2 pre = cmul(lat, make_double2(0.0, 0.25 / GF_PI));
-        store_out(out + idx, cmul(pre, make_double2(sr, si)));
+        for (int o = 16; o > 0; o >>= 1) {
+            sr += __shfl_xor_sync(0xffffffffu, sr, o);
+            si += __shfl_xor_sync(0xffffffffu, si, o);
+        }
+        if (lane == 0) {
+            const double2 lat = lattice_phase(a.a1, m, 0.0, 0.0);
+            const double2 pre = cmul(lat, make_double2(0.0, 0.25 / GF_PI));
+            store_out(out + idx, cmul(pre, make_double2(sr, si)));
+        }
     }
 }
 
