@@ -150,6 +150,25 @@ def dist_setup():
     return world, rank, local
 
 
+def max_over_ranks(vals, dev=None):
+    """Entry-wise max over all ranks of a list of floats (identity on one rank).
+    The timing rule of the multi-GPU line: every rank times the same steps and
+    the job's time is the slowest rank's."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in vals]
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def whole_job_rate(units_per_rank: int, world: int, seconds: float) -> float:
+    """Units all ranks processed per second of the slowest rank (weak scaling)."""
+    return world * units_per_rank / seconds
+
+
 def host_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -266,13 +285,8 @@ def run_gpu(args):
         return 0
     out32, t32, ph32, _ = run_path(gf.GF_FP32_SPLIT, args.steps, args.warmup, 1e-8)
 
-    ms64 = float(np.mean(t64))
-    ms32 = float(np.mean(t32))
-    if world > 1:
-        tt = torch.tensor([ms64, ms32], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms64, ms32 = float(tt[0]), float(tt[1])
-    value = world * n_targets / (ms64 * 1e-3)
+    ms64, ms32 = max_over_ranks([np.mean(t64), np.mean(t32)], dev)
+    value = whole_job_rate(n_targets, world, ms64 * 1e-3)
 
     # e2e through the host-buffer entry point (pinned buffers, copies inside the timed region)
     x_pin = torch.from_numpy(x_np).pin_memory()
@@ -289,11 +303,7 @@ def run_gpu(args):
         p.close()
         if i >= args.warmup:
             e2e_t.append(dt)
-    e2e_s = float(np.mean(e2e_t)) if e2e_t else float("nan")
-    if world > 1:
-        tt = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt[0])
+    e2e_s = max_over_ranks([np.mean(e2e_t) if e2e_t else float("nan")], dev)[0]
 
     # roofline of the dominant kernel (the double-precision far-series kernel)
     far_ms = float(np.mean([p[3] for p in ph64]))
@@ -329,7 +339,7 @@ def run_gpu(args):
                    "series_tol": tol64, "parallelism": f"replicas{world}", "l2": "flushed (256 MiB write) between steps"},
         "phases_ms": {"synthesis": synth_ms, "near": near_ms, "far": far_ms,
                       "far_series_terms": terms, "far_core_terms_fp64": core_terms},
-        "split": {"value": world * n_targets / (ms32 * 1e-3), "ms_per_step": ms32, "dtype": "f32/f64 split",
+        "split": {"value": whole_job_rate(n_targets, world, ms32 * 1e-3), "ms_per_step": ms32, "dtype": "f32/f64 split",
                   "series_tol": 1e-8, "max_err_vs_fp64_normwise": split_err,
                   "phases_ms": {"synthesis": float(np.mean([p[0] for p in ph32])),
                                 "near": float(np.mean([p[2] for p in ph32])),
@@ -343,7 +353,7 @@ def run_gpu(args):
                              "exponential degree 5/4/3, FMA = 2 flops) / far-kernel time; the float tail is not "
                              "counted; peak from unit counts and clock (152 SMs x 2 FP64 FMA/clk x 2 flop x "
                              "2.07 GHz; FMA probe 1.21 TFLOP/s)"},
-        "e2e": {"value": world * n_targets / e2e_s, "unit": "evals/s",
+        "e2e": {"value": whole_job_rate(n_targets, world, e2e_s), "unit": "evals/s",
                 "h2d_bytes_per_step": int(x_np.nbytes), "d2h_bytes_per_step": int(n_targets * 16)},
         "batched": batched,
         "surrogate": surrogate,

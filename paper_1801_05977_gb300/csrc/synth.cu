@@ -112,7 +112,7 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
     }
     __syncthreads();
 
-    const double k2 = a.k * a.k;
+    const double k2 = a.k * a.k, ik2 = 1.0 / k2;
     for (int i = threadIdx.x; i < TJ * n; i += blockDim.x) {
         int t = i >> lg, b = i & (n - 1);
         int col = col0 + t;
@@ -225,8 +225,8 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
             // order xx, yy, zz, xy, xz, yz, then the plain field C (for G_d).
             int jx = freq_of(col % a.M1, a.M1), jy = freq_of(col / a.M1, a.M2);
             double cv0 = a.a1 + jx, cv1 = a.a2 + jy, cv2 = q;
-            double f[7] = {1.0 - cv0 * cv0 / k2, 1.0 - cv1 * cv1 / k2, 1.0 - cv2 * cv2 / k2,
-                           -cv0 * cv1 / k2,      -cv0 * cv2 / k2,      -cv1 * cv2 / k2, 1.0};
+            double f[7] = {1.0 - cv0 * cv0 * ik2, 1.0 - cv1 * cv1 * ik2, 1.0 - cv2 * cv2 * ik2,
+                           -cv0 * cv1 * ik2,      -cv0 * cv2 * ik2,      -cv1 * cv2 * ik2, 1.0};
 #pragma unroll
             for (int e = 0; e < 7; ++e) buf0[(e * TJ + t) * n + b] = cmk((R)(f[e] * Cj.x), (R)(f[e] * Cj.y));
         }
