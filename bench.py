@@ -88,7 +88,8 @@ def far_terms(x: np.ndarray, k: float, alpha, c: float, tol: float):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms while the timed
+    regions run (the double-precision, split and host-buffer steps)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -102,10 +103,15 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # the timed region starts once the sampler is producing lines
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 3.0:
+                time.sleep(0.01)
+            self.skip = len(self.lines)
         except Exception:
             self.proc = None
         return self
@@ -125,7 +131,7 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in self.lines[getattr(self, "skip", 0):]:
             p = [s.strip() for s in ln.split(",")]
             if len(p) < 9:
                 continue
@@ -278,10 +284,10 @@ def run_gpu(args):
     if args.paths == "split":
         run_path(gf.GF_FP32_SPLIT, args.steps, args.warmup, 1e-8)
         return 0
-    with ClockSampler(local) as clk:
-        out64, t64, ph64, launches = run_path(gf.GF_FP64, args.steps, args.warmup, tol64)
-    clocks = clk.summary()
+    clk = ClockSampler(local).__enter__()
+    out64, t64, ph64, launches = run_path(gf.GF_FP64, args.steps, args.warmup, tol64)
     if args.paths == "fp64":
+        clk.__exit__()
         return 0
     out32, t32, ph32, _ = run_path(gf.GF_FP32_SPLIT, args.steps, args.warmup, 1e-8)
 
@@ -303,6 +309,8 @@ def run_gpu(args):
         p.close()
         if i >= args.warmup:
             e2e_t.append(dt)
+    clk.__exit__()
+    clocks = clk.summary()
     e2e_s = max_over_ranks([np.mean(e2e_t) if e2e_t else float("nan")], dev)[0]
 
     # roofline of the dominant kernel (the double-precision far-series kernel)

@@ -17,12 +17,31 @@
 namespace {
 
 constexpr double TWO_PI = 2.0 * GF_PI;
+constexpr double INV_TWO_PI = 1.0 / (2.0 * GF_PI);
+
+// floor of the correctly rounded quotient a/b.  The product a * ib (ib = fl(1/b))
+// differs from that quotient by a few ulps, so it decides the floor unless it
+// lies within 1e-14 max(1, |a/b|) of an integer, where the quotient is formed.
+// q receives the value the floor was taken of.
+__device__ __forceinline__ double floor_quot(double a, double b, double ib, double &q)
+{
+    q = __dmul_rn(a, ib);
+    const double fq = floor(q), fr = q - fq;
+    const double g = 1e-14 * fmax(1.0, fabs(q));
+    if (fr < g || fr > 1.0 - g) {
+        q = __ddiv_rn(a, b);
+        return floor(q);
+    }
+    return fq;
+}
 
 // x = 2 pi m + t, t in [-pi, pi), with explicit round-to-nearest operations
-// (no contraction) so that the cell decision is reproducible.
+// (no contraction) so that the cell decision is reproducible: m is the floor of
+// the correctly rounded (x + pi)/(2 pi).
 __device__ __forceinline__ void reduce_period(double x, double &t, double &m)
 {
-    double mm = floor(__ddiv_rn(__dadd_rn(x, GF_PI), TWO_PI));
+    double q;
+    double mm = floor_quot(__dadd_rn(x, GF_PI), TWO_PI, INV_TWO_PI, q);
     double tt = __dsub_rn(x, __dmul_rn(TWO_PI, mm));
     if (tt >= GF_PI) {
         tt = __dsub_rn(tt, TWO_PI);
@@ -38,10 +57,11 @@ __device__ __forceinline__ void reduce_period(double x, double &t, double &m)
 
 // stencil origin on an axis: u = (y - y0)/h, i0 = floor(u) clamped to [0, M-1],
 // f = u - i0; the padded nodes i0 .. i0+3 hold the stencil nodes i0-1 .. i0+2.
-__device__ __forceinline__ int stencil_origin(double y, double y0, double h, int M, double &f)
+// i0 is the floor of the correctly rounded quotient (ih = fl(1/h)).
+__device__ __forceinline__ int stencil_origin(double y, double y0, double h, double ih, int M, double &f)
 {
-    double u = __ddiv_rn(__dsub_rn(y, y0), h);
-    double i0 = floor(u);
+    double u;
+    double i0 = floor_quot(__dsub_rn(y, y0), h, ih, u);
     if (i0 > (double)(M - 1)) i0 = (double)(M - 1);
     if (i0 < 0.0) i0 = 0.0;
     f = u - i0;
@@ -129,6 +149,7 @@ __device__ void near3d_tiles(const EvalArgs &a, int64_t base0, int64_t stride, i
     const C *G = reinterpret_cast<const C *>(a.grid);
     C *out = reinterpret_cast<C *>(a.out);
     const int ne = n_entries(a.which);
+    const double ih1 = 1.0 / a.h1, ih2 = 1.0 / a.h2, ih3 = 1.0 / a.h3;
     for (int64_t base = base0; base < a.n; base += stride) {
         const int64_t i = base + threadIdx.x;
         bool valid = i < a.n;
@@ -163,9 +184,9 @@ __device__ void near3d_tiles(const EvalArgs &a, int64_t base0, int64_t stride, i
         reduce_period(x1, t1, m1);
         reduce_period(x2, t2, m2);
         double f1, f2, f3;
-        int i1 = stencil_origin(t1, -GF_PI, a.h1, a.M1, f1);
-        int i2 = stencil_origin(t2, -GF_PI, a.h2, a.M2, f2);
-        int i3 = stencil_origin(x3, -a.ct, a.h3, a.M3, f3);
+        int i1 = stencil_origin(t1, -GF_PI, a.h1, ih1, a.M1, f1);
+        int i2 = stencil_origin(t2, -GF_PI, a.h2, ih2, a.M2, f2);
+        int i3 = stencil_origin(x3, -a.ct, a.h3, ih3, a.M3, f3);
         double w1d[4], w2d[4], w3d[4];
         lagrange4(f1, w1d);
         lagrange4(f2, w2d);
@@ -317,6 +338,7 @@ __global__ void __launch_bounds__(256) near2d(EvalArgs a)
     typedef typename cplx_t<R>::T C;
     const C *G = reinterpret_cast<const C *>(a.grid);
     C *out = reinterpret_cast<C *>(a.out);
+    const double ih1 = 1.0 / a.h1, ih2 = 1.0 / a.h2;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < a.n; base += stride) {
         const int64_t i = base + threadIdx.x;
@@ -337,8 +359,8 @@ __global__ void __launch_bounds__(256) near2d(EvalArgs a)
         double t, m;
         reduce_period(x1, t, m);
         double f1, f2;
-        int i1 = stencil_origin(t, -GF_PI, a.h1, a.M1, f1);
-        int i2 = stencil_origin(x2, -a.ct, a.h2, a.M2, f2);
+        int i1 = stencil_origin(t, -GF_PI, a.h1, ih1, a.M1, f1);
+        int i2 = stencil_origin(x2, -a.ct, a.h2, ih2, a.M2, f2);
         double w1[4], w2[4];
         lagrange4(f1, w1);
         lagrange4(f2, w2);
@@ -544,7 +566,7 @@ __device__ __forceinline__ float ex2_approx(float x)
 
 // Per-lane set-up of a far target (double): reduced t, lattice index m, z, sign.
 struct FarLane {
-    double t1, m1, t2, m2, z, sg, R2;
+    double t1, m1, t2, m2, z, iz, sg, R2;
     int idx;
     bool valid;
 };
@@ -564,7 +586,8 @@ __device__ __forceinline__ FarLane far_lane(const EvalArgs &a, int slot, int cou
     reduce_period(x2, L.t2, L.m2);
     L.z = fabs(x3);
     L.sg = x3 >= 0.0 ? 1.0 : -1.0;
-    double Tz = a.T / L.z;
+    L.iz = 1.0 / L.z;
+    double Tz = a.T * L.iz;
     L.R2 = L.valid ? a.k * a.k + Tz * Tz : 0.0;
     return L;
 }
@@ -822,7 +845,7 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, i
         const double R2m = warp_max(L.R2);
         const float R2f = (float)L.R2;
         // core disk of the warp: b z_min <= Y0
-        const double iz = L.valid ? 1.0 / L.z : 0.0;
+        const double iz = L.valid ? L.iz : 0.0;
         const double izmax = warp_max(iz);
         const double Rc2 = fmin(k2 + FAR_CORE_Y0 * FAR_CORE_Y0 * izmax * izmax, R2m);
         double sv, cv, s1, c1v;
@@ -1286,7 +1309,7 @@ __global__ void __launch_bounds__(128) far2d(EvalArgs a)
         double t, m;
         reduce_period(x1, t, m);
         const double z = fabs(x2);
-        const double Tz = a.T / z;
+        const double Tz = a.T * (1.0 / z);
         const double R2 = k2 + Tz * Tz, Rr = sqrt(R2);
         const int na = (int)floor(-a.a1 - Rr) - 1, nb = (int)ceil(-a.a1 + Rr) + 1;
         double sp, cp, s32, c32;
