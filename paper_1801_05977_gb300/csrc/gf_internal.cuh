@@ -96,13 +96,16 @@ struct SynthArgs {
     double ct;          // c~ (possibly perturbed)
     double qs;          // pi / c~: last-axis frequency q_b = freq(b) qs
     double gskip;       // evanescent |beta| above which e^{-|beta| c}/(2 |beta|^2) < 1e-20
+    double gfloat;      // split plans (3D): evanescent |beta| from which a column's coefficients are formed in float
     double invV;        // 1 / |D|: 1/(8 pi^2 c~) in 3D, 1/(4 pi c~) in 2D
     const double *tW;   // [Q] w_m hw X'(t_m) on [c, (c+c~)/2]
     const double *tt;   // [Q] t_m
     const double2 *E;   // [Mlast][Q] e^{i q_b t_m}, q_b = freq(b) pi / c~
+    const float2 *Ef;   // the same in float (split plans)
     const double *rr;   // [Q] r_m on [eps, 2 eps]
     const double2 *B;   // [Q] 3D: w_m hw e^{i k r_m}(2 i k Y'(r_m) + Y''(r_m))
     const double2 *hcheb; // Chebyshev coefficients per panel [hnpan][hdeg + 1]: 3D h(s); 2D (S0, S1)(eta)
+    const float2 *hchebf; // the same in float (split plans)
     int hdeg, hnpan;
     double hpan, ihpan; // panel width in s and its inverse
     const double *Pw0;  // [Q] 2D: w_m hw Phi_1(r_m) r_m      (J0 weights)
@@ -187,12 +190,12 @@ cudaError_t gf_launch_synth(const SynthArgs &a, int precision, cudaStream_t s);
 cudaError_t gf_launch_extract(const SynthArgs &a, int precision, void *dev_out, cudaStream_t s);
 void gf_synth_config(SynthArgs &a, int precision, int tj_max, size_t smem[3]);
 cudaError_t gf_launch_cheb_table(int dim, const double *rr, const double2 *B, const double *P0, const double *P1, int Q,
-                                 int npan, int deg, double w, double2 *out, cudaStream_t s);
+                                 int npan, int deg, double w, double2 *out, float2 *outf, cudaStream_t s);
 cudaError_t gf_launch_synth_batch(const SynthBatch &b, int precision, cudaStream_t s);
 cudaError_t gf_launch_eval_batch(const EvalBatch &b, int precision, cudaStream_t s);
 cudaError_t gf_launch_series_tables(const EvalArgs &a, int precision, double2 *exptab, PropEntry *prop, int *nprop,
                                     const int pbox[4], cudaStream_t s);
-cudaError_t gf_launch_e_table(const double *tt, int Q, int Mlast, double qs, double2 *E, cudaStream_t s);
+cudaError_t gf_launch_e_table(const double *tt, int Q, int Mlast, double qs, double2 *E, float2 *Ef, cudaStream_t s);
 
 // runtime.cu: stream-ordered pool allocations, pinned upload staging
 cudaError_t gf_dev_alloc(void **ptr, size_t bytes, cudaStream_t s);

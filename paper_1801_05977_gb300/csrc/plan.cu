@@ -334,7 +334,8 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
     p->grid_bytes = nodes_padded * p->nf * p->elem;
     const size_t E_n = (size_t)Mlast * Q;
     const size_t host_tab_bytes = sizeof(double) * 5 * Q + sizeof(double2) * Q;
-    const size_t tab_bytes = host_tab_bytes + sizeof(double2) * (E_n + hcheb_n);
+    const bool ftabs = tr.precision == GF_FP32_SPLIT;  // float copies for the split plans' coefficients
+    const size_t tab_bytes = host_tab_bytes + sizeof(double2) * (E_n + hcheb_n) + (ftabs ? sizeof(float2) * (E_n + hcheb_n) : 0);
     const size_t ncells = (size_t)p->M[0] * p->M[1] * p->M[2];
     const size_t work_bytes = ncells * p->nf * p->elem;
     void *work = nullptr;
@@ -352,6 +353,7 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
         char *tb = (char *)p->tables;
         double *d_tt = (double *)tb, *d_tW = d_tt + Q, *d_rr = d_tW + Q, *d_P0 = d_rr + Q, *d_P1 = d_P0 + Q;
         double2 *d_B = (double2 *)(d_P1 + Q), *d_E = d_B + Q, *d_H = d_E + E_n;
+        float2 *d_Ef = ftabs ? (float2 *)(d_H + hcheb_n) : nullptr, *d_Hf = ftabs ? d_Ef + E_n : nullptr;
         {
             std::vector<char> pack(host_tab_bytes);
             char *hb = pack.data();
@@ -362,8 +364,8 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
             memcpy(hb + ((char *)d_P1 - tb), P1.data(), sizeof(double) * Q);
             memcpy(hb + ((char *)d_B - tb), B.data(), sizeof(double2) * Q);
             if ((e = gf_stage_upload(tb, hb, host_tab_bytes, st)) != cudaSuccess ||
-                (e = gf_launch_e_table(d_tt, Q, Mlast, GF_PI / ct, d_E, st)) != cudaSuccess ||
-                (e = gf_launch_cheb_table(dim, d_rr, d_B, d_P0, d_P1, Q, hnpan, hdeg, hpan, d_H, st)) != cudaSuccess) {
+                (e = gf_launch_e_table(d_tt, Q, Mlast, GF_PI / ct, d_E, d_Ef, st)) != cudaSuccess ||
+                (e = gf_launch_cheb_table(dim, d_rr, d_B, d_P0, d_P1, Q, hnpan, hdeg, hpan, d_H, d_Hf, st)) != cudaSuccess) {
                 st_err = fail(GF_ERR_CUDA, "gf_plan: tables: %s", cudaGetErrorString(e));
                 break;
             }
@@ -393,6 +395,11 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
         sa.tW = d_tW;
         sa.tt = d_tt;
         sa.E = d_E;
+        sa.Ef = d_Ef;
+        sa.hchebf = d_Hf;
+        // split plans form a column's coefficients in float when its beta is evanescent
+        // and at least 0.05 k (clear of Wood anomalies; propagating columns stay double)
+        sa.gfloat = ftabs ? 0.05 * k : 1e300;
         sa.rr = d_rr;
         sa.B = d_B;
         sa.hcheb = d_H;

@@ -75,8 +75,14 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
     C *buf0 = tw + (n >> 1);                             // [nf][TJ][n]
     C *buf1 = buf0 + nf * TJ * n;
     double *A2s = reinterpret_cast<double *>(buf1 + nf * TJ * n); // [TJ]
+    // split plans, float coefficients: A_m [TJ][Q], |alpha_j|^2 - k^2 and its float [TJ], q_b^2 [n]
+    float *Avf = reinterpret_cast<float *>(A2s + TJ);
+    double *A2mk = reinterpret_cast<double *>(Avf + ((TJ * Q + 1) & ~1));
+    double *qq = A2mk + TJ;
+    float *A2f = reinterpret_cast<float *>(qq + n);
     const int ncols = (a.dim == 3) ? a.M1 * a.M2 : a.M1;
     const int col0 = blk * TJ;
+    const bool fcoef = sizeof(R) == 4 && a.dim == 3;
 
     load_twiddles<R>(tw, n);
     for (int t = threadIdx.x; t < TJ; t += blockDim.x) {
@@ -93,12 +99,25 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
         }
         A2s[t] = A2;
         betas[t] = beta_of(a.k, A2);
+        if (fcoef) {
+            A2mk[t] = A2 - a.k * a.k;
+            A2f[t] = (float)A2;
+        }
     }
+    if (fcoef)
+        for (int b = threadIdx.x; b < n; b += blockDim.x) {
+            const double q = (double)freq_of(b, n) * a.qs;
+            qq[b] = q * q;
+        }
     __syncthreads();
     for (int i = threadIdx.x; i < TJ * Q; i += blockDim.x) {
         int t = i / Q, m = i - t * Q;
         double2 b = betas[t];
         if (b.y > a.gskip) continue;  // this column's X'-integrals are not used
+        if (fcoef && b.y >= a.gfloat) {
+            Avf[i] = (float)a.tW[m] * expf(-(float)b.y * (float)a.tt[m]);
+            continue;
+        }
         double tm = a.tt[m];
         double2 e;
         if (b.y == 0.0) {
@@ -117,8 +136,59 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
         int t = i >> lg, b = i & (n - 1);
         int col = col0 + t;
         int jl = freq_of(b, n);
-        double q = (double)jl * a.qs;
         double2 beta = betas[t];
+        if (fcoef && beta.y >= a.gfloat) {
+            // Split plans, evanescent column clear of Wood anomalies (g >= gfloat):
+            // the coefficient in float.  D = |xi|^2 - k^2 is formed in double (it is
+            // small near the resonance sphere) and then rounded; every other factor is
+            // O(1) in relative terms.
+            const float qf = (float)jl * (float)a.qs;
+            const float g = (float)beta.y;
+            float T12f = 0.f;
+            if (beta.y <= a.gskip) {
+                const float *Am = Avf + t * Q;
+                const float2 *Em = a.Ef + (size_t)b * Q;
+                float s1 = 0.f, s3 = 0.f;
+                for (int m = 0; m < Q; ++m) {
+                    const float A = Am[m];
+                    const float2 E = Em[m];
+                    s1 = fmaf(A, E.x, s1);
+                    s3 = fmaf(A, E.y, s3);
+                }
+                T12f = (g * s1 - qf * s3) / (g * (g * g + qf * qf));
+            }
+            const float iD = 1.0f / (float)(A2mk[t] + qq[b]);
+            const float sf = sqrtf(A2f[t] + qf * qf);
+            const int pnl = min((int)(sf * (float)a.ihpan), a.hnpan - 1);
+            const float x = (sf - ((float)pnl + 0.5f) * (float)a.hpan) * (2.0f / (float)a.hpan);
+            const float2 *cc = a.hchebf + (size_t)pnl * (a.hdeg + 1);
+            float b1r = 0.f, b1i = 0.f, b2r = 0.f, b2i = 0.f;
+            for (int kk = a.hdeg; kk >= 1; --kk) {
+                const float2 ck = cc[kk];
+                const float tr = fmaf(2.0f * x, b1r, ck.x - b2r);
+                const float ti = fmaf(2.0f * x, b1i, ck.y - b2i);
+                b2r = b1r;
+                b2i = b1i;
+                b1r = tr;
+                b1i = ti;
+            }
+            const float hr = fmaf(x, b1r, cc[0].x - b2r), hi = fmaf(x, b1i, cc[0].y - b2i);
+            const float invVf = (float)a.invV;
+            const float cr = fmaf(hr, iD, T12f) * invVf, ci = hi * iD * invVf;
+            if (nf == 1) {
+                buf0[t * n + b] = cmk((R)cr, (R)ci);
+            } else {
+                const int jx = freq_of(col % a.M1, a.M1), jy = freq_of(col / a.M1, a.M2);
+                const float ik2f = (float)ik2;
+                const float cv0 = (float)(a.a1 + jx), cv1 = (float)(a.a2 + jy), cv2 = qf;
+                const float f[7] = {1.f - cv0 * cv0 * ik2f, 1.f - cv1 * cv1 * ik2f, 1.f - cv2 * cv2 * ik2f,
+                                    -cv0 * cv1 * ik2f,      -cv0 * cv2 * ik2f,      -cv1 * cv2 * ik2f, 1.f};
+#pragma unroll
+                for (int e = 0; e < 7; ++e) buf0[(e * TJ + t) * n + b] = cmk((R)(f[e] * cr), (R)(f[e] * ci));
+            }
+            continue;
+        }
+        double q = (double)jl * a.qs;
         double A2 = A2s[t];
         const double2 *Am = Av + t * Q;
         const double2 *Em = a.E + (size_t)b * Q;
@@ -453,15 +523,17 @@ void synth_config_t(SynthArgs &a, int tj_max, size_t sm[3])
 {
     typedef typename cplx_t<R>::T C;
     const int ncols = (a.dim == 3) ? a.M1 * a.M2 : a.M1;
-    size_t fixed = sizeof(C) * (a.Mlast / 2);
+    // per column: A_m (double2 and float), beta, |alpha|^2 (double), |alpha|^2 - k^2, its float;
+    // per b: twiddles and q_b^2; plus the two line buffers
+    auto bytes = [&](int TJ) {
+        return sizeof(C) * (a.Mlast / 2) + sizeof(double) * a.Mlast +
+               TJ * (sizeof(double2) * a.Q + sizeof(double2) + 2 * sizeof(double) + sizeof(float)) +
+               sizeof(float) * ((TJ * a.Q + 1) & ~1) + 2 * sizeof(C) * a.nf * TJ * a.Mlast + 16;
+    };
     int TJ = tj_max;
-    while (TJ > 1 && (TJ > ncols ||
-                      fixed + TJ * (sizeof(double2) * a.Q + sizeof(double2) + sizeof(double)) +
-                              2 * sizeof(C) * a.nf * TJ * a.Mlast >
-                          160 * 1024))
-        TJ >>= 1;
+    while (TJ > 1 && (TJ > ncols || bytes(TJ) > 160 * 1024)) TJ >>= 1;
     a.TJ = TJ;
-    sm[0] = fixed + TJ * (sizeof(double2) * a.Q + sizeof(double2) + sizeof(double)) + 2 * sizeof(C) * a.nf * TJ * a.Mlast;
+    sm[0] = bytes(TJ);
     int TJ2 = 8;
     while (TJ2 > 1 && (TJ2 > a.M1 || sizeof(C) * (a.M2 / 2 + 2 * TJ2 * a.M2) > 160 * 1024)) TJ2 >>= 1;
     a.TJ2 = TJ2;
@@ -530,7 +602,8 @@ namespace {
 //   2D: (S0, S1)(s) = (sum_m P0_m J0(s r_m), sum_m P1_m J1(s r_m)) (two real functions).
 template <int DIM>
 __global__ void __launch_bounds__(256) cheb_table_kernel(const double *rr, const double2 *B, const double *P0,
-                                                         const double *P1, int Q, int nn, double w, double2 *out)
+                                                         const double *P1, int Q, int nn, double w, double2 *out,
+                                                         float2 *outf)
 {
     __shared__ double2 fv[16];
     const int p = blockIdx.x, t = threadIdx.x, k = t >> 4, g = t & 15;
@@ -571,6 +644,7 @@ __global__ void __launch_bounds__(256) cheb_table_kernel(const double *rr, const
         }
         const double sc = (t == 0 ? 1.0 : 2.0) / nn;
         out[(size_t)p * nn + t] = make_double2(cr * sc, ci * sc);
+        if (outf) outf[(size_t)p * nn + t] = make_float2((float)(cr * sc), (float)(ci * sc));
     }
 }
 }  // namespace
@@ -578,7 +652,7 @@ __global__ void __launch_bounds__(256) cheb_table_kernel(const double *rr, const
 // E[b][m] = e^{i q_b t_m}, q_b = j qs (qs = pi / c~) with j = b for b < Mlast/2, else
 // b - Mlast (the last-axis frequencies of Eq. (fck-coef)), t_m the Gauss nodes
 // of the X' integrals.
-__global__ void e_table_kernel(const double *tt, int Q, int Mlast, double qs, double2 *E)
+__global__ void e_table_kernel(const double *tt, int Q, int Mlast, double qs, double2 *E, float2 *Ef)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Mlast * Q; i += gridDim.x * blockDim.x) {
         const int b = i / Q, m = i - b * Q;
@@ -587,26 +661,27 @@ __global__ void e_table_kernel(const double *tt, int Q, int Mlast, double qs, do
         double sv, cv;
         sincos(q * tt[m], &sv, &cv);
         E[i] = make_double2(cv, sv);
+        if (Ef) Ef[i] = make_float2((float)cv, (float)sv);
     }
 }
 
-cudaError_t gf_launch_e_table(const double *tt, int Q, int Mlast, double qs, double2 *E, cudaStream_t s)
+cudaError_t gf_launch_e_table(const double *tt, int Q, int Mlast, double qs, double2 *E, float2 *Ef, cudaStream_t s)
 {
     int blocks = (Mlast * Q + 255) / 256;
     if (blocks > 1024) blocks = 1024;
-    e_table_kernel<<<blocks, 256, 0, s>>>(tt, Q, Mlast, qs, E);
+    e_table_kernel<<<blocks, 256, 0, s>>>(tt, Q, Mlast, qs, E, Ef);
     gf_count_launch(1);
     return cudaGetLastError();
 }
 
 cudaError_t gf_launch_cheb_table(int dim, const double *rr, const double2 *B, const double *P0, const double *P1, int Q,
-                                 int npan, int deg, double w, double2 *out, cudaStream_t s)
+                                 int npan, int deg, double w, double2 *out, float2 *outf, cudaStream_t s)
 {
     if (deg + 1 > 16 || npan < 1) return cudaErrorInvalidValue;
     if (dim == 3)
-        cheb_table_kernel<3><<<npan, 256, 0, s>>>(rr, B, P0, P1, Q, deg + 1, w, out);
+        cheb_table_kernel<3><<<npan, 256, 0, s>>>(rr, B, P0, P1, Q, deg + 1, w, out, outf);
     else
-        cheb_table_kernel<2><<<npan, 256, 0, s>>>(rr, B, P0, P1, Q, deg + 1, w, out);
+        cheb_table_kernel<2><<<npan, 256, 0, s>>>(rr, B, P0, P1, Q, deg + 1, w, out, outf);
     gf_count_launch(1);
     return cudaGetLastError();
 }
