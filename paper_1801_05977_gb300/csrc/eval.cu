@@ -68,13 +68,14 @@ __device__ __forceinline__ int stencil_origin(double y, double y0, double h, dou
     return (int)i0;
 }
 
-__device__ __forceinline__ void lagrange4(double f, double w[4])
+template <typename T>
+__device__ __forceinline__ void lagrange4(T f, T w[4])
 {
-    double fm1 = f - 1.0, fm2 = f - 2.0, fp1 = f + 1.0;
-    w[0] = -f * fm1 * fm2 * (1.0 / 6.0);
-    w[1] = fp1 * fm1 * fm2 * 0.5;
-    w[2] = -fp1 * f * fm2 * 0.5;
-    w[3] = fp1 * f * fm1 * (1.0 / 6.0);
+    const T fm1 = f - (T)1, fm2 = f - (T)2, fp1 = f + (T)1;
+    w[0] = -f * fm1 * fm2 * (T)(1.0 / 6.0);
+    w[1] = fp1 * fm1 * fm2 * (T)0.5;
+    w[2] = -fp1 * f * fm2 * (T)0.5;
+    w[3] = fp1 * f * fm1 * (T)(1.0 / 6.0);
 }
 
 // quasi-periodic lift e^{i 2 pi <alpha . m>} (fractional part taken first)
@@ -94,10 +95,14 @@ __device__ __forceinline__ void add_out(double2 *o, double2 v)
     atomicAdd(&o->x, v.x);
     atomicAdd(&o->y, v.y);
 }
-__device__ __forceinline__ void add_out(float2 *o, double2 v)
+__device__ __forceinline__ void add_out_f(float2 *o, float2 v)
 {
-    atomicAdd(&o->x, (float)v.x);
-    atomicAdd(&o->y, (float)v.y);
+    atomicAdd(&o->x, v.x);
+    atomicAdd(&o->y, v.y);
+}
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b)
+{
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 template <typename R> __device__ __forceinline__ typename cplx_t<R>::T zero_c();
 template <> __device__ __forceinline__ double2 zero_c<double>() { return make_double2(0.0, 0.0); }
@@ -187,13 +192,11 @@ __device__ void near3d_tiles(const EvalArgs &a, int64_t base0, int64_t stride, i
         int i1 = stencil_origin(t1, -GF_PI, a.h1, ih1, a.M1, f1);
         int i2 = stencil_origin(t2, -GF_PI, a.h2, ih2, a.M2, f2);
         int i3 = stencil_origin(x3, -a.ct, a.h3, ih3, a.M3, f3);
-        double w1d[4], w2d[4], w3d[4];
-        lagrange4(f1, w1d);
-        lagrange4(f2, w2d);
-        lagrange4(f3, w3d);
-        R w1[4];
-#pragma unroll
-        for (int d = 0; d < 4; ++d) w1[d] = (R)w1d[d];
+        // weights in the grid's precision (f itself is formed in double)
+        R w1[4], w2[4], w3[4];
+        lagrange4<R>((R)f1, w1);
+        lagrange4<R>((R)f2, w2);
+        lagrange4<R>((R)f3, w3);
         R acc[NF][2];
 #pragma unroll
         for (int e = 0; e < NF; ++e) acc[e][0] = acc[e][1] = (R)0;
@@ -202,7 +205,7 @@ __device__ void near3d_tiles(const EvalArgs &a, int64_t base0, int64_t stride, i
 #pragma unroll
             for (int d2 = 0; d2 < 4; ++d2) {
                 const C *row = G + (((size_t)(i3 + d3) * a.P2 + (i2 + d2)) * a.P1 + i1) * NF;
-                R w23 = (R)(w3d[d3] * w2d[d2]);
+                const R w23 = w3[d3] * w2[d2];
 #pragma unroll
                 for (int e = 0; e < NF; ++e) {
                     R sr = 0, si = 0;
@@ -217,11 +220,26 @@ __device__ void near3d_tiles(const EvalArgs &a, int64_t base0, int64_t stride, i
                 }
             }
         }
-        // lift = e^{i alpha.t} e^{i 2 pi <alpha.m>}; G = lift L + e^{i 2pi<alpha.m>} Phi Y (K = L + F, F = e^{-i alpha.t} Phi Y)
-        double2 lat = lattice_phase(a.a1, m1, a.a2, m2);
-        double sa, ca;
-        sincos(a.a1 * t1 + a.a2 * t2, &sa, &ca);
-        double2 lift = cmul(make_double2(ca, sa), lat);
+        // lift = e^{i alpha.t} e^{i 2 pi <alpha.m>}; G = lift L + e^{i 2pi<alpha.m>} Phi Y (K = L + F, F = e^{-i alpha.t} Phi Y).
+        // Split plans: the fractional part in double, the two phases in float.
+        double2 lat, lift;
+        float2 latf = make_float2(0.f, 0.f), liftf = make_float2(0.f, 0.f);
+        if (sizeof(R) == 4) {
+            double ph = a.a1 * m1 + a.a2 * m2;
+            ph -= rint(ph);
+            float sl, cl, sa, ca;
+            sincospif(2.0f * (float)ph, &sl, &cl);
+            sincosf((float)a.a1 * (float)t1 + (float)a.a2 * (float)t2, &sa, &ca);
+            latf = make_float2(cl, sl);
+            liftf = cmulf(make_float2(ca, sa), latf);
+            lat = make_double2(cl, sl);
+            lift = make_double2(liftf.x, liftf.y);
+        } else {
+            lat = lattice_phase(a.a1, m1, a.a2, m2);
+            double sa, ca;
+            sincos(a.a1 * t1 + a.a2 * t2, &sa, &ca);
+            lift = cmul(make_double2(ca, sa), lat);
+        }
         double r = sqrt(t1 * t1 + t2 * t2 + x3 * x3);
         bool sing = r < 2.0 * a.eps;
         double2 PhiY = make_double2(0, 0), dPhi = make_double2(0, 0), d2Phi = make_double2(0, 0);
@@ -250,6 +268,13 @@ __device__ void near3d_tiles(const EvalArgs &a, int64_t base0, int64_t stride, i
             double2 L = make_double2((double)acc[0][0], (double)acc[0][1]);
             if (only_L) {
                 store_out(o, L);
+                continue;
+            }
+            if (sizeof(R) == 4) {
+                // split: the combination in float (the singular part was formed in double)
+                const float2 v = cmulf(liftf, make_float2((float)acc[0][0], (float)acc[0][1]));
+                const float2 u = sing ? cmulf(latf, make_float2((float)PhiY.x, (float)PhiY.y)) : make_float2(0.f, 0.f);
+                reinterpret_cast<float2 *>(o)[0] = make_float2(v.x + u.x, v.y + u.y);
                 continue;
             }
             double2 v = cadd(cmul(lift, L), cmul(lat, PhiY));
@@ -444,18 +469,20 @@ __global__ void __launch_bounds__(256) far_scatter_batch(const EvalArgs *args, i
 // (beta_n = i |beta_n|); zeros for propagating n, whose terms are summed from
 // the short list PropEntry instead.
 // ---------------------------------------------------------------------------
+// Propagating n (b = 0) get bl2 = +inf, so that the float sums' ex2(-bl2 z) is 0
+// for them without a test.
 __device__ __forceinline__ void set_entry(BetaEntry &e, double b, double ib)
 {
     e.b = b;
     e.lnb = b > 0.0 ? log(b) : 0.0;
-    e.bl2 = (float)(b * 1.4426950408889634);  // b log2(e)
+    e.bl2 = b > 0.0 ? (float)(b * 1.4426950408889634) : CUDART_INF_F;  // b log2(e)
     e.ibf = (float)ib;
     e.bf = (float)b;
     e.lnbf = (float)e.lnb;
 }
 __device__ __forceinline__ void set_entry(BetaEntryF &e, double b, double ib)
 {
-    e.bl2 = (float)(b * 1.4426950408889634);  // b log2(e)
+    e.bl2 = b > 0.0 ? (float)(b * 1.4426950408889634) : CUDART_INF_F;  // b log2(e)
     e.ib = (float)ib;
     e.b = (float)b;
     e.pad = 0.f;
@@ -758,8 +785,10 @@ __device__ __forceinline__ void seg_horner_f32(const BetaEntry *__restrict__ row
     float c2 = a2f + (float)hi;
     for (int n2 = hi; n2 >= lo; --n2, c2 -= 1.0f) {
         const BetaEntry be = row[n2];
-        const bool ok = fmaf(c2, c2, c1sq) <= R2f && be.ibf != 0.f;
-        const float e = ok ? ex2_approx(-be.bl2 * z) : 0.f;
+        // no per-lane truncation test: the terms of the warp's disk beyond the
+        // lane's own set are below e^{-T} of its largest term (they add accuracy),
+        // and propagating n have bl2 = +inf
+        const float e = ex2_approx(-be.bl2 * z);
         float wv[NH];
         wv[0] = e * be.ibf;
         if (NH > 1) {
@@ -1100,7 +1129,8 @@ __global__ void __launch_bounds__(128) far3d_f64(EvalArgs a)
 
 // ---------------------------------------------------------------------------
 // 3D far kernel, split precision: the same sums in float with the hardware
-// ex2; per-target reduction, lattice phase and the final scaling in double.
+// ex2; the per-target cell reduction and the lattice phase's fractional part in
+// double, everything else in float.
 // ---------------------------------------------------------------------------
 template <int NF>
 __device__ void far3d_f32_chunk(const EvalArgs &a, int w, int count, int slab, int nslab)
@@ -1113,10 +1143,24 @@ __device__ void far3d_f32_chunk(const EvalArgs &a, int w, int count, int slab, i
     const float ik2 = (float)(1.0 / (a.k * a.k));
     const float a2f = (float)a.a2;
     {
-        FarLane L = far_lane(a, w * 32 + lane, count);
-        const double R2m = warp_max(L.R2);
-        const float R2f = (float)L.R2;
-        const float z = (float)L.z, t1 = (float)L.t1, t2 = (float)L.t2, sg = (float)L.sg;
+        // per-target set-up: the cell reduction in double, the rest in float
+        const int slot = w * 32 + lane;
+        const bool valid = slot < count;
+        const int idx = valid ? a.far_sorted[slot] : 0;
+        double x1 = 0, x2 = 0, x3 = 1;
+        if (valid) {
+            x1 = a.x[3 * (size_t)idx];
+            x2 = a.x[3 * (size_t)idx + 1];
+            x3 = a.x[3 * (size_t)idx + 2];
+        }
+        double t1d, m1, t2d, m2;
+        reduce_period(x1, t1d, m1);
+        reduce_period(x2, t2d, m2);
+        const float z = fabsf((float)x3), t1 = (float)t1d, t2 = (float)t2d, sg = x3 >= 0.0 ? 1.f : -1.f;
+        const float Tz = (float)a.T / z;
+        const float R2f = valid ? (float)(a.k * a.k) + Tz * Tz : 0.f;
+        float R2mf = R2f;
+        for (int o = 16; o > 0; o >>= 1) R2mf = fmaxf(R2mf, __shfl_xor_sync(0xffffffffu, R2mf, o));
         float sv, cv;
         sincosf(t2, &sv, &cv);
         float P[NF][2];
@@ -1145,8 +1189,8 @@ __device__ void far3d_f32_chunk(const EvalArgs &a, int w, int count, int slab, i
                 }
             }
         }
-        // row bounds in float with a one-index margin (lanes mask their own sets)
-        const float R2mf = (float)R2m, a1f = (float)a.a1;
+        // row bounds in float with a one-index margin
+        const float a1f = (float)a.a1;
         const float Rmf = sqrtf(R2mf);
         const int n1a = max(a.n1lo, (int)floorf(-a1f - Rmf) - 1), n1b = min(a.n1hi, (int)ceilf(-a1f + Rmf) + 1);
         // row slab: the rows split evenly
@@ -1167,9 +1211,9 @@ __device__ void far3d_f32_chunk(const EvalArgs &a, int w, int count, int slab, i
             for (int e = 0; e < (NF == 1 ? 1 : 6); ++e) h[e][0] = h[e][1] = 0.f;
             for (int n2 = n2b; n2 >= n2a; --n2, c2 -= 1.0f) {
                 const BetaEntryF be = row[n2];
-                // propagating n carry ib = 0 in the table and are summed separately
-                const bool ok = fmaf(c2, c2, c1sq) <= R2f && be.ib != 0.f;
-                const float e = ok ? ex2_approx(-be.bl2 * z) : 0.f;
+                // propagating n (summed separately) have bl2 = +inf, so e = 0; no
+                // per-lane truncation test (terms beyond the lane's set are below e^{-T})
+                const float e = ex2_approx(-be.bl2 * z);
                 float wv[NF == 1 ? 1 : 6];
                 if (NF == 1) {
                     wv[0] = e * be.ib;
@@ -1218,24 +1262,29 @@ __device__ void far3d_f32_chunk(const EvalArgs &a, int w, int count, int slab, i
                 S[6][1] += -ik2 * r[5][1];
             }
         }
-        if (!L.valid) return;
-        const double2 lat = lattice_phase(a.a1, L.m1, a.a2, L.m2);
-        const double2 pre = cmul(lat, make_double2(0.0, 1.0 / (8.0 * GF_PI * GF_PI)));
-        float2 *o = out + (size_t)L.idx * ne;
+        if (!valid) return;
+        // e^{i 2pi <alpha.m>} (i/8pi^2): the fractional part in double, the phase in float
+        double ph = a.a1 * m1 + a.a2 * m2;
+        ph -= rint(ph);
+        float sl, cl;
+        sincospif(2.0f * (float)ph, &sl, &cl);
+        const float sc = (float)(1.0 / (8.0 * GF_PI * GF_PI));
+        const float2 pre = make_float2(-sl * sc, cl * sc);
+        float2 *o = out + (size_t)idx * ne;
         if (NF == 1) {
-            add_out(o, cmul(pre, make_double2(P[0][0] + S[0][1], P[0][1] - S[0][0])));
+            add_out_f(o, cmulf(pre, make_float2(P[0][0] + S[0][1], P[0][1] - S[0][0])));
         } else {
             for (int e = 0; e < 6; ++e) {
                 const float *s = S[1 + e];
-                double2 v;
+                float2 v;
                 if (e < 4)
-                    v = make_double2(P[1 + e][0] + s[1], P[1 + e][1] - s[0]);
+                    v = make_float2(P[1 + e][0] + s[1], P[1 + e][1] - s[0]);
                 else
-                    v = make_double2(P[1 + e][0] + sg * s[0], P[1 + e][1] + sg * s[1]);
-                add_out(o + e, cmul(pre, v));
+                    v = make_float2(P[1 + e][0] + sg * s[0], P[1 + e][1] + sg * s[1]);
+                add_out_f(o + e, cmulf(pre, v));
             }
             if (a.which == GF_OUT_MAXWELL7)
-                add_out(o + 6, cmul(pre, make_double2(P[0][0] + S[0][1], P[0][1] - S[0][0])));
+                add_out_f(o + 6, cmulf(pre, make_float2(P[0][0] + S[0][1], P[0][1] - S[0][0])));
         }
     }
 }
