@@ -665,6 +665,7 @@ __device__ __forceinline__ void reinsch_seg(RState<NH> &st, const BetaEntry *__r
     const float zf = (float)z;
     const float df = (float)dir;
     const double dd = (double)dir;
+#pragma unroll 3
     for (int i = 0; i < count; ++i, n2 += dir, c2f += df) {
         const BetaEntry be = row[n2];
         const bool ok = fmaf(c2f, c2f, c1sq) <= R2f && be.ibf != 0.f;
