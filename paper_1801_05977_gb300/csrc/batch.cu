@@ -89,7 +89,7 @@ static gf_status batch_synth_setup(gf_batch_t b)
         const int ncols = a.M1 * a.M2;
         b->h_prefix[0][p + 1] = b->h_prefix[0][p] + ncols / a.TJ;
         b->h_prefix[1][p + 1] = b->h_prefix[1][p] + (a.M1 / a.TJ2) * a.M3 * a.nf;
-        b->h_prefix[2][p + 1] = b->h_prefix[2][p] + a.M3 * a.M2;
+        b->h_prefix[2][p + 1] = b->h_prefix[2][p] + a.M3 * a.M2 / a.RB1;
     }
     for (int i = 0; i < 3; ++i)
         CUB(cudaMemcpy(b->d_prefix + i * (b->np + 1), b->h_prefix[i].data(), sizeof(int) * (b->np + 1),
@@ -259,8 +259,8 @@ gf_status gf_batch_autotune(gf_batch_t b, const double *dev_xyz, const int64_t *
     // synthesis: columns per CTA of the first pass
     float best = 1e30f;
     int best_tj = b->tune.tj_max;
-    const int tjs[3] = {2, 4, 8};
-    for (int i = 0; i < 3; ++i) {
+    const int tjs[4] = {2, 4, 8, 16};
+    for (int i = 0; i < 4; ++i) {
         b->tune.tj_max = tjs[i];
         if ((s = batch_synth_setup(b)) != GF_OK) return s;
         float ms = 0.f;

@@ -112,6 +112,7 @@ struct SynthArgs {
     const double *Pw1;  // [Q] 2D: w_m hw Phi_1(r_m) r_m^2    (J1 weights)
     double F10;         // 2D: sqrt(V) F1-hat_0
     int TJ2, lg1, lg2;  // x2-pass columns per CTA; log2 M1, log2 M2
+    int RB1;            // last-pass rows per CTA
     void *work;         // [nf][Mlast][M2][M1] complex (3D) or [M2][M1] (2D), working precision
     void *grid;         // padded gather grid
     int P1, P2, P3;     // padded extents (M + 3 per periodic axis; P3 = 1 in 2D)

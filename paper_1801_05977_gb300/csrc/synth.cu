@@ -369,54 +369,60 @@ __device__ __forceinline__ int pad_dests(int a_node, int M, int *p)
     return nd;
 }
 
-// Last pass: inverse transform along x1 of one row (all fields), then scatter
-// into the padded, field-interleaved gather grid G[p3][p2][p1][f], where
-// padded index p = a + 1 holds node a = (l + M/2) mod M, i.e. x = -pi + a h
-// (x3: -c~ + a h3), with one halo node before and two after on every
-// periodic axis so that a cubic stencil never wraps.
+// Last pass: inverse transform along x1 of RB1 consecutive rows (all fields),
+// then scatter into the padded, field-interleaved gather grid G[p3][p2][p1][f],
+// where padded index p = a + 1 holds node a = (l + M/2) mod M, i.e. x = -pi + a h
+// (x3: -c~ + a h3), with one halo node before and two after on every periodic
+// axis so that a cubic stencil never wraps.
 template <typename R>
-__device__ void synth_x1_body(const SynthArgs &a, int row, unsigned char *smem)
+__device__ void synth_x1_body(const SynthArgs &a, int blk, unsigned char *smem)
 {
     typedef typename cplx_t<R>::T C;
-    const int n = a.M1, nf = a.nf, lg1 = a.lg1;
+    const int n = a.M1, nf = a.nf, lg1 = a.lg1, RB = a.RB1;
     C *tw = reinterpret_cast<C *>(smem);
     C *buf0 = tw + (n >> 1);
-    C *buf1 = buf0 + nf * n;
+    C *buf1 = buf0 + RB * nf * n;
     // row: 3D: l3 * M2 + l2; 2D: l2
     const size_t fstride = (size_t)a.Mlast * (a.dim == 3 ? a.M2 : 1) * a.M1;
     const C *W = reinterpret_cast<const C *>(a.work);
+    const int row0 = blk * RB;
     load_twiddles<R>(tw, n);
-    for (int i = threadIdx.x; i < nf * n; i += blockDim.x) {
-        int f = i / n, b1 = i - f * n;
-        buf0[i] = W[f * fstride + (size_t)row * n + b1];
+    for (int i = threadIdx.x; i < RB * nf * n; i += blockDim.x) {
+        const int r = i / (nf * n), rem = i - r * nf * n;
+        const int f = rem / n, b1 = rem - f * n;
+        buf0[i] = W[f * fstride + (size_t)(row0 + r) * n + b1];
     }
     __syncthreads();
-    C *res = stockham_inverse(buf0, buf1, n, lg1, nf, tw);
-    int l2, l3;
-    if (a.dim == 3) {
-        l3 = row / a.M2;
-        l2 = row - l3 * a.M2;
-    } else {
-        l3 = 0;
-        l2 = row;
-    }
-    int p2[3], p3[3];
-    int n2 = pad_dests((l2 + (a.M2 >> 1)) % a.M2, a.M2, p2);
-    int n3 = 1;
-    p3[0] = 0;
-    if (a.dim == 3) n3 = pad_dests((l3 + (a.M3 >> 1)) % a.M3, a.M3, p3);
+    C *res = stockham_inverse(buf0, buf1, n, lg1, RB * nf, tw);
     C *G = reinterpret_cast<C *>(a.grid);
     const int rowlen = a.P1 * nf;
-    for (int d3 = 0; d3 < n3; ++d3)
-        for (int d2 = 0; d2 < n2; ++d2) {
-            C *dst = G + ((size_t)p3[d3] * a.P2 + p2[d2]) * rowlen;
-            for (int i = threadIdx.x; i < rowlen; i += blockDim.x) {
-                int p1 = i / nf, f = i - p1 * nf;
-                int a1 = (p1 - 1 + n) % n;
-                int l1 = (a1 + (n >> 1)) % n;
-                dst[i] = res[f * n + l1];
-            }
+    for (int r = 0; r < RB; ++r) {
+        const int row = row0 + r;
+        int l2, l3;
+        if (a.dim == 3) {
+            l3 = row / a.M2;
+            l2 = row - l3 * a.M2;
+        } else {
+            l3 = 0;
+            l2 = row;
         }
+        int p2[3], p3[3];
+        int n2 = pad_dests((l2 + (a.M2 >> 1)) % a.M2, a.M2, p2);
+        int n3 = 1;
+        p3[0] = 0;
+        if (a.dim == 3) n3 = pad_dests((l3 + (a.M3 >> 1)) % a.M3, a.M3, p3);
+        const C *rr = res + (size_t)r * nf * n;
+        for (int d3 = 0; d3 < n3; ++d3)
+            for (int d2 = 0; d2 < n2; ++d2) {
+                C *dst = G + ((size_t)p3[d3] * a.P2 + p2[d2]) * rowlen;
+                for (int i = threadIdx.x; i < rowlen; i += blockDim.x) {
+                    int p1 = i / nf, f = i - p1 * nf;
+                    int a1 = (p1 - 1 + n) % n;
+                    int l1 = (a1 + (n >> 1)) % n;
+                    dst[i] = rr[f * n + l1];
+                }
+            }
+    }
 }
 
 template <typename R>
@@ -561,7 +567,14 @@ void synth_config_t(SynthArgs &a, int tj_max, size_t sm[3])
     a.lg2 = ilog2(a.M2);
     a.lg1 = ilog2(a.M1);
     sm[1] = a.dim == 3 ? sizeof(C) * (a.M2 / 2 + 2 * TJ2 * a.M2) : 0;
-    sm[2] = sizeof(C) * (a.M1 / 2 + 2 * a.nf * a.M1);
+    // last pass: RB1 rows per CTA (up to 2048 values, a power of two dividing the rows)
+    const int nrows = a.dim == 3 ? a.M3 * a.M2 : a.M2;
+    int RB1 = 8;
+    while (RB1 > 1 && (RB1 > nrows || RB1 * a.nf * a.M1 > 2048 ||
+                       sizeof(C) * (a.M1 / 2 + 2 * a.nf * RB1 * a.M1) > 160 * 1024))
+        RB1 >>= 1;
+    a.RB1 = RB1;
+    sm[2] = sizeof(C) * (a.M1 / 2 + 2 * a.nf * RB1 * a.M1);
 }
 
 template <typename R>
@@ -569,7 +582,7 @@ cudaError_t launch_synth_t(const SynthArgs &a0, cudaStream_t s)
 {
     SynthArgs a = a0;
     size_t sm[3];
-    synth_config_t<R>(a, 8, sm);
+    synth_config_t<R>(a, sizeof(R) == 4 ? 16 : 8, sm);
     const int ncols = (a.dim == 3) ? a.M1 * a.M2 : a.M1;
     cudaError_t e = cudaFuncSetAttribute(synth_first_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[0]);
     if (e != cudaSuccess) return e;
@@ -584,7 +597,7 @@ cudaError_t launch_synth_t(const SynthArgs &a0, cudaStream_t s)
     e = cudaFuncSetAttribute(synth_x1_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[2]);
     if (e != cudaSuccess) return e;
     int rows = (a.dim == 3) ? a.M3 * a.M2 : a.M2;
-    synth_x1_pass<R><<<rows, 256, sm[2], s>>>(a);
+    synth_x1_pass<R><<<rows / a.RB1, 256, sm[2], s>>>(a);
     gf_count_launch(1);
     return cudaGetLastError();
 }
