@@ -191,7 +191,9 @@ __device__ void near3d_tiles(const EvalArgs &a, int64_t base0, int64_t stride, i
         double f1, f2, f3;
         int i1 = stencil_origin(t1, -GF_PI, a.h1, ih1, a.M1, f1);
         int i2 = stencil_origin(t2, -GF_PI, a.h2, ih2, a.M2, f2);
-        int i3 = stencil_origin(x3, -a.ct, a.h3, ih3, a.M3, f3);
+        // stored planes from Q3lo: a Helmholtz grid (even in x3) holds x3 >= -h3 only
+        // and is read at |x3|; a Maxwell grid holds the slab |x3| <= c
+        int i3 = stencil_origin(NF == 1 ? fabs(x3) : x3, -a.ct, a.h3, ih3, a.M3, f3) - a.Q3lo;
         // weights in the grid's precision (f itself is formed in double)
         R w1[4], w2[4], w3[4];
         lagrange4<R>((R)f1, w1);
@@ -220,6 +222,7 @@ __device__ void near3d_tiles(const EvalArgs &a, int64_t base0, int64_t stride, i
                 }
             }
         }
+
         // lift = e^{i alpha.t} e^{i 2 pi <alpha.m>}; G = lift L + e^{i 2pi<alpha.m>} Phi Y (K = L + F, F = e^{-i alpha.t} Phi Y).
         // Split plans: the fractional part in double, the two phases in float.
         double2 lat, lift;

@@ -115,7 +115,9 @@ struct SynthArgs {
     int RB1;            // last-pass rows per CTA
     void *work;         // [nf][Mlast][M2][M1] complex (3D) or [M2][M1] (2D), working precision
     void *grid;         // padded gather grid
-    int P1, P2, P3;     // padded extents (M + 3 per periodic axis; P3 = 1 in 2D)
+    int P1, P2, P3;     // padded extents (M + 3 per periodic axis); P3 = stored x3 planes (1 in 2D)
+    int Q3lo;           // padded x3 index of the first stored plane
+    int a3first, L3count; // x3 nodes the last two passes transform: a3first .. a3first + L3count - 1
 };
 
 // Far-series table entry for one in-plane index n: b = |beta_n|, ln b and 1/b
@@ -137,6 +139,7 @@ struct EvalArgs {
     int dim;
     int M1, M2, M3;
     int P1, P2, P3;
+    int Q3lo;           // padded x3 index of the grid's first stored plane
     int nf;             // stored fields per node
     int which;
     double k, a1, a2;

@@ -7,6 +7,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <map>
 #include <mutex>
@@ -109,6 +110,7 @@ struct gf_plan_s {
     gf_trunc_t tr{};
     double T = 0;
     int P1 = 1, P2 = 1, P3 = 1;
+    int Q3lo = 0, a3first = 0, L3count = 1;  // stored x3 planes of the gather grid (3D)
     size_t elem = 16;                 // bytes per complex value
     void *grid = nullptr;             // padded gather grid
     size_t grid_bytes = 0;
@@ -258,6 +260,26 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
     p->P1 = p->M[0] + 3;
     p->P2 = dim == 3 ? p->M[1] + 3 : p->M[1] + 3;
     p->P3 = dim == 3 ? p->M[2] + 3 : 1;
+    p->L3count = dim == 3 ? p->M[2] : 1;
+    if (dim == 3) {
+        // The gather grid keeps only the x3 planes the near branch reads: stencil
+        // origins i0 from the smallest near |x3| or x3 to floor((c + c~)/h3) + 1 (one
+        // index of margin each way), padded planes i0 .. i0 + 3.  The grid of L_d is
+        // even in x3 (node a mirrors node M3 - a, the Nyquist row included), so a
+        // Helmholtz plan interpolates at |x3| and keeps the planes x3 >= -h3 only.  The
+        // Maxwell xz and yz fields are odd except for their Nyquist row (it has no
+        // mirror partner), so a Maxwell plan keeps the whole slab |x3| <= c.
+        const int M3 = p->M[2];
+        const double h3 = 2.0 * tr.c_tilde / M3;
+        const int i0min = p->nf == 1 ? M3 / 2 - 1 : std::max(0, (int)floor((tr.c_tilde - tr.c) / h3) - 1);
+        const int i0max = std::min(M3 - 1, (int)floor((tr.c + tr.c_tilde) / h3) + 1);
+        if (i0max + 3 <= M3 && i0min >= 1) {
+            p->Q3lo = i0min;
+            p->P3 = i0max + 3 - i0min + 1;
+            p->a3first = p->Q3lo - 1;
+            p->L3count = p->P3;
+        }
+    }
     cudaStream_t st = (cudaStream_t)cuda_stream;
     if (g_timing.load()) {
         p->timing = true;
@@ -415,6 +437,9 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
         sa.P1 = p->P1;
         sa.P2 = p->P2;
         sa.P3 = p->P3;
+        sa.Q3lo = p->Q3lo;
+        sa.a3first = p->a3first;
+        sa.L3count = p->L3count;
         if (p->timing) cudaEventRecord(p->ev[0], st);
         if ((e = gf_launch_synth(sa, p->precision, st)) != cudaSuccess) {
             st_err = fail(GF_ERR_CUDA, "gf_plan: synthesis launch: %s", cudaGetErrorString(e));
@@ -491,7 +516,30 @@ gf_status gf_eval_grid(gf_plan_t p, void *dev_out, size_t out_bytes, void *cuda_
 {
     if (!p || !dev_out) return fail(GF_ERR_ARG, "gf_eval_grid: NULL argument");
     if (out_bytes < gf_grid_bytes(p)) return fail(GF_ERR_ARG, "gf_eval_grid: out_bytes %zu < %zu", out_bytes, gf_grid_bytes(p));
-    CU(gf_launch_extract(p->sa, p->precision, dev_out, (cudaStream_t)cuda_stream));
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (p->dim == 3 && (p->Q3lo != 0 || p->L3count != p->M[2])) {
+        // the plan keeps only the near planes: synthesise the whole grid once more
+        // into pool buffers returned in stream order
+        SynthArgs fs = p->sa;
+        fs.Q3lo = 0;
+        fs.P3 = p->M[2] + 3;
+        fs.a3first = 0;
+        fs.L3count = p->M[2];
+        void *work = nullptr, *grid = nullptr;
+        CU(gf_dev_alloc(&work, gf_plan_work_bytes(p), st));
+        cudaError_t e = gf_dev_alloc(&grid, (size_t)fs.P1 * fs.P2 * fs.P3 * p->nf * p->elem, st);
+        if (e == cudaSuccess) {
+            fs.work = work;
+            fs.grid = grid;
+            e = gf_launch_synth(fs, p->precision, st);
+            if (e == cudaSuccess) e = gf_launch_extract(fs, p->precision, dev_out, st);
+        }
+        gf_dev_free(work, st);
+        gf_dev_free(grid, st);
+        CU(e);
+        return GF_OK;
+    }
+    CU(gf_launch_extract(p->sa, p->precision, dev_out, st));
     return GF_OK;
 }
 
@@ -537,6 +585,7 @@ gf_status gf_eval_points(gf_plan_t p, const double *dev_xyz, int64_t n, int whic
     a.P1 = p->P1;
     a.P2 = p->P2;
     a.P3 = p->P3;
+    a.Q3lo = p->Q3lo;
     a.nf = p->nf;
     a.which = which;
     a.k = p->k;
@@ -597,6 +646,7 @@ gf_status gf_plan_eval_args(gf_plan_t p, const double *dev_xyz, int64_t n, int w
     a.P1 = p->P1;
     a.P2 = p->P2;
     a.P3 = p->P3;
+    a.Q3lo = p->Q3lo;
     a.nf = p->nf;
     a.which = which;
     a.k = p->k;

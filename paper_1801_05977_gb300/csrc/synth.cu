@@ -335,12 +335,15 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
     }
 }
 
-// Middle pass (3D only): inverse transform along x2 for fixed (field, l3, b1-tile).
+// Middle pass (3D only): inverse transform along x2 for fixed (field, x3 node, b1-tile);
+// only the x3 nodes of the stored planes are transformed.
 template <typename R>
-__device__ void synth_x2_body(const SynthArgs &a, int bx, int l3, int f, unsigned char *smem)
+__device__ void synth_x2_body(const SynthArgs &a, int bx, int y, int f, unsigned char *smem)
 {
     typedef typename cplx_t<R>::T C;
     const int n = a.M2, TJ = a.TJ2, lg2 = a.lg2;
+    // x3 node a3first + y, stored at plane l3 of the work buffer (node = (l3 + M3/2) mod M3)
+    const int l3 = (a.a3first + y + (a.M3 >> 1)) % a.M3;
     C *tw = reinterpret_cast<C *>(smem);
     C *buf0 = tw + (n >> 1);
     C *buf1 = buf0 + TJ * n;
@@ -387,10 +390,16 @@ __device__ void synth_x1_body(const SynthArgs &a, int blk, unsigned char *smem)
     const C *W = reinterpret_cast<const C *>(a.work);
     const int row0 = blk * RB;
     load_twiddles<R>(tw, n);
+    // row = y * M2 + l2 (3D: x3 node a3first + y, work plane l3 = (node + M3/2) mod M3); 2D: l2
+    auto work_row = [&](int row) -> int {
+        if (a.dim != 3) return row;
+        const int y = row / a.M2, l2 = row - y * a.M2;
+        return ((a.a3first + y + (a.M3 >> 1)) % a.M3) * a.M2 + l2;
+    };
     for (int i = threadIdx.x; i < RB * nf * n; i += blockDim.x) {
         const int r = i / (nf * n), rem = i - r * nf * n;
         const int f = rem / n, b1 = rem - f * n;
-        buf0[i] = W[f * fstride + (size_t)(row0 + r) * n + b1];
+        buf0[i] = W[f * fstride + (size_t)work_row(row0 + r) * n + b1];
     }
     __syncthreads();
     C *res = stockham_inverse(buf0, buf1, n, lg1, RB * nf, tw);
@@ -398,23 +407,26 @@ __device__ void synth_x1_body(const SynthArgs &a, int blk, unsigned char *smem)
     const int rowlen = a.P1 * nf;
     for (int r = 0; r < RB; ++r) {
         const int row = row0 + r;
-        int l2, l3;
+        int l2, a3 = 0;
         if (a.dim == 3) {
-            l3 = row / a.M2;
-            l2 = row - l3 * a.M2;
+            const int y = row / a.M2;
+            l2 = row - y * a.M2;
+            a3 = a.a3first + y;
         } else {
-            l3 = 0;
             l2 = row;
         }
         int p2[3], p3[3];
         int n2 = pad_dests((l2 + (a.M2 >> 1)) % a.M2, a.M2, p2);
         int n3 = 1;
         p3[0] = 0;
-        if (a.dim == 3) n3 = pad_dests((l3 + (a.M3 >> 1)) % a.M3, a.M3, p3);
+        if (a.dim == 3) n3 = pad_dests(a3, a.M3, p3);
         const C *rr = res + (size_t)r * nf * n;
-        for (int d3 = 0; d3 < n3; ++d3)
+        for (int d3 = 0; d3 < n3; ++d3) {
+            // only the stored planes Q3lo .. Q3lo + P3 - 1
+            const int q3 = p3[d3] - a.Q3lo;
+            if (q3 < 0 || q3 >= a.P3) continue;
             for (int d2 = 0; d2 < n2; ++d2) {
-                C *dst = G + ((size_t)p3[d3] * a.P2 + p2[d2]) * rowlen;
+                C *dst = G + ((size_t)q3 * a.P2 + p2[d2]) * rowlen;
                 for (int i = threadIdx.x; i < rowlen; i += blockDim.x) {
                     int p1 = i / nf, f = i - p1 * nf;
                     int a1 = (p1 - 1 + n) % n;
@@ -422,6 +434,7 @@ __device__ void synth_x1_body(const SynthArgs &a, int blk, unsigned char *smem)
                     dst[i] = rr[f * n + l1];
                 }
             }
+        }
     }
 }
 
@@ -492,8 +505,8 @@ __global__ void __launch_bounds__(256) synth_x2_pass_batch(const SynthArgs *args
         const int nbx = sa.M1 / sa.TJ2;
         const int bx = loc % nbx;
         loc /= nbx;
-        const int l3 = loc % sa.M3, f = loc / sa.M3;
-        synth_x2_body<R>(sa, bx, l3, f, smem);
+        const int y = loc % sa.L3count, f = loc / sa.L3count;
+        synth_x2_body<R>(sa, bx, y, f, smem);
         __syncthreads();
     }
 }
@@ -531,7 +544,7 @@ __global__ void extract_grid(SynthArgs a, void *out)
         int l3 = (int)(r2 / a.M2);
         int p1 = (l1 + (a.M1 >> 1)) % a.M1 + 1;
         int p2 = (l2 + (a.M2 >> 1)) % a.M2 + 1;
-        int p3 = a.dim == 3 ? (l3 + (a.M3 >> 1)) % a.M3 + 1 : 0;
+        int p3 = a.dim == 3 ? (l3 + (a.M3 >> 1)) % a.M3 + 1 - a.Q3lo : 0;
         o[i] = G[(((size_t)p3 * a.P2 + p2) * a.P1 + p1) * a.nf + f];
     }
 }
@@ -568,7 +581,7 @@ void synth_config_t(SynthArgs &a, int tj_max, size_t sm[3])
     a.lg1 = ilog2(a.M1);
     sm[1] = a.dim == 3 ? sizeof(C) * (a.M2 / 2 + 2 * TJ2 * a.M2) : 0;
     // last pass: RB1 rows per CTA (up to 2048 values, a power of two dividing the rows)
-    const int nrows = a.dim == 3 ? a.M3 * a.M2 : a.M2;
+    const int nrows = a.dim == 3 ? a.L3count * a.M2 : a.M2;
     int RB1 = 8;
     while (RB1 > 1 && (RB1 > nrows || RB1 * a.nf * a.M1 > 2048 ||
                        sizeof(C) * (a.M1 / 2 + 2 * a.nf * RB1 * a.M1) > 160 * 1024))
@@ -591,12 +604,12 @@ cudaError_t launch_synth_t(const SynthArgs &a0, cudaStream_t s)
     if (a.dim == 3) {
         e = cudaFuncSetAttribute(synth_x2_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[1]);
         if (e != cudaSuccess) return e;
-        synth_x2_pass<R><<<dim3(a.M1 / a.TJ2, a.M3, a.nf), 256, sm[1], s>>>(a);
+        synth_x2_pass<R><<<dim3(a.M1 / a.TJ2, a.L3count, a.nf), 256, sm[1], s>>>(a);
         gf_count_launch(1);
     }
     e = cudaFuncSetAttribute(synth_x1_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[2]);
     if (e != cudaSuccess) return e;
-    int rows = (a.dim == 3) ? a.M3 * a.M2 : a.M2;
+    int rows = (a.dim == 3) ? a.L3count * a.M2 : a.M2;
     synth_x1_pass<R><<<rows / a.RB1, 256, sm[2], s>>>(a);
     gf_count_launch(1);
     return cudaGetLastError();
