@@ -292,11 +292,18 @@ __device__ __forceinline__ float silu_tanh(float z)
 constexpr int ROWS = 128, NT = 2;
 constexpr int ACT_BYTES = ROWS * HID * 2;                // 64 KiB per tile
 constexpr int WST_BYTES = HID * umma::KC * 2;           // 32 KiB per weight stage
-constexpr int SMEM = NT * ACT_BYTES + 2 * WST_BYTES + 64 + NT * ROWS * 2 * 4;
+constexpr int PAR_FLOATS = 4 * HID + 2 * HID;  // biases of layers 1-4, then the head weights
+constexpr int SMEM = NT * ACT_BYTES + 2 * WST_BYTES + 64 + NT * ROWS * 2 * 4 + PAR_FLOATS * 4;
 constexpr int TMEM_COLS = 512;
 
-// act tile: [r/8][k/8] core matrices, 32 K-blocks per row group (LBO 128 B, SBO 4096 B)
-__device__ __forceinline__ uint32_t act_off(int r, int k) { return ((r >> 3) * (HID / 8) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2; }
+// act tile: [k/8][r/8] core matrices, the 16 row groups of a K block adjacent
+// (LBO 2048 B along K, SBO 128 B along M), so that the 32 rows a warp writes for one
+// K block are 512 contiguous bytes (no shared-memory bank conflicts)
+constexpr uint32_t ACT_LBO = (ROWS / 8) * 128, ACT_SBO = 128;
+__device__ __forceinline__ uint32_t act_off(int r, int k)
+{
+    return (k >> 3) * ACT_LBO + (r >> 3) * ACT_SBO + (r & 7) * 16 + (k & 7) * 2;
+}
 
 struct Args {
     const float *in;
@@ -319,6 +326,10 @@ __global__ void __launch_bounds__(256, 1) mlp_infer_fused(fused::Args A)
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + NT * ACT_BYTES + 2 * WST_BYTES);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
     float *yhalf = reinterpret_cast<float *>(tslot + 2);  // [NT][ROWS][2] head partial sums of the second column half
+    float *par = yhalf + NT * ROWS * 2;                  // biases [4][HID], head weights [2][HID]
+    for (int i = threadIdx.x; i < PAR_FLOATS; i += blockDim.x)
+        par[i] = i < 4 * HID ? A.b[i / HID][i % HID] : A.W5[i - 4 * HID];
+    const float *W5s = par + 4 * HID;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // 8 warps: warp w reads TMEM lanes 32 (w % 4) .. +31 (its rows) and the column half w / 4
     const int quarter = warp & 3, half = warp >> 2;
@@ -407,7 +418,7 @@ __global__ void __launch_bounds__(256, 1) mlp_infer_fused(fused::Args A)
                     for (int t = 0; t < NT; ++t) {
                         const uint32_t a0 = umma::smem_u32(act[t]);
                         for (int kk = 0; kk < ksteps; ++kk) {
-                            const uint64_t ad = umma::make_desc(a0 + (c * 8 + kk * 2) * 128, 128, (HID / 8) * 128);
+                            const uint64_t ad = umma::make_desc(a0 + (c * 8 + kk * 2) * ACT_LBO, ACT_LBO, ACT_SBO);
                             const uint64_t bd = umma::make_desc(b0 + kk * 256, 128, (umma::KC / 8) * 128);
                             const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
                             asm volatile(
@@ -426,7 +437,7 @@ __global__ void __launch_bounds__(256, 1) mlp_infer_fused(fused::Args A)
             ok = __syncthreads_and(umma::mbar_wait(umma::smem_u32(&mbar[gl & 1]), (gl >> 1) & 1)) != 0;
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const float *bias = A.b[l];
+            const float *bias = par + l * HID;
             for (int t = 0; t < NT; ++t) {
                 const int r = quarter * 32 + lane;
                 float y0 = 0.f, y1 = 0.f;
@@ -452,8 +463,8 @@ __global__ void __launch_bounds__(256, 1) mlp_infer_fused(fused::Args A)
                         pk[e >> 1] = (uint32_t)__bfloat16_as_ushort(hb.x) | ((uint32_t)__bfloat16_as_ushort(hb.y) << 16);
                         if (l == 3) {
                             const float h0 = __bfloat162float(hb.x), h1 = __bfloat162float(hb.y);
-                            y0 = fmaf(h0, A.W5[j + e], fmaf(h1, A.W5[j + e + 1], y0));
-                            y1 = fmaf(h0, A.W5[HID + j + e], fmaf(h1, A.W5[HID + j + e + 1], y1));
+                            y0 = fmaf(h0, W5s[j + e], fmaf(h1, W5s[j + e + 1], y0));
+                            y1 = fmaf(h0, W5s[HID + j + e], fmaf(h1, W5s[HID + j + e + 1], y1));
                         }
                     }
                     if (l < 3) {
