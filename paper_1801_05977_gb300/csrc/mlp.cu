@@ -191,6 +191,24 @@ __global__ void convert_kernel(const float *W, bf16 *Wb, bf16 *WTb, int out, int
     }
 }
 
+// Shared-memory images of a layer's weight stages for the fused inference kernel:
+// chunk c (32 KiB) holds rows 0..HID-1, K range [c KC, (c + 1) KC) of the bf16
+// weights W [HID][K] in the core-matrix layout of the B operand (zero beyond K), so
+// that one bulk copy puts a stage in place.
+__global__ void stage_images_kernel(const bf16 *W, int K, int nch, bf16 *img)
+{
+    constexpr int CH = HID * (umma::KC / 8);  // 16-byte pieces per stage
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nch * CH; i += gridDim.x * blockDim.x) {
+        const int c = i / CH, rem = i - c * CH;
+        const int r = rem / (umma::KC / 8), kb = rem - r * (umma::KC / 8);
+        const int gk = c * umma::KC + kb * 8;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (gk < K) v = *reinterpret_cast<const uint4 *>(W + (size_t)r * K + gk);
+        *reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(img) + (size_t)c * (HID * umma::KC * 2) +
+                                   umma::core_off(r, kb * 8)) = v;
+    }
+}
+
 __global__ void init_kernel(float *W, int count, float bound, unsigned long long seed)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
@@ -310,6 +328,7 @@ struct Args {
     int n;
     float pi_ct;
     const bf16 *W[4];
+    const bf16 *Wimg[4];  // per layer: its K chunks as ready 32 KiB shared-memory images
     const float *b[4];
     const float *W5, *b5;
     float *Y;
@@ -323,8 +342,9 @@ __global__ void __launch_bounds__(256, 1) mlp_infer_fused(fused::Args A)
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *act[NT] = {smem, smem + ACT_BYTES};
     uint8_t *wst[2] = {smem + NT * ACT_BYTES, smem + NT * ACT_BYTES + WST_BYTES};
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + NT * ACT_BYTES + 2 * WST_BYTES);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + NT * ACT_BYTES + 2 * WST_BYTES);  // MMA commits
+    uint64_t *lbar = mbar + 2;                                                            // weight-stage copies
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 4);
     float *yhalf = reinterpret_cast<float *>(tslot + 2);  // [NT][ROWS][2] head partial sums of the second column half
     float *par = yhalf + NT * ROWS * 2;                  // biases [4][HID], head weights [2][HID]
     for (int i = threadIdx.x; i < PAR_FLOATS; i += blockDim.x)
@@ -339,8 +359,7 @@ __global__ void __launch_bounds__(256, 1) mlp_infer_fused(fused::Args A)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(umma::smem_u32(&mbar[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(umma::smem_u32(&mbar[1])));
+        for (int q = 0; q < 4; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(umma::smem_u32(&mbar[q])));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -350,6 +369,7 @@ __global__ void __launch_bounds__(256, 1) mlp_infer_fused(fused::Args A)
     const uint32_t idesc = umma::make_idesc(ROWS, HID);
     int g = 0;  // weight stages used so far (stage g & 1, use g >> 1)
     bool ok = true;
+    int issued = -1, landed = -1;  // thread 0: last weight stage copy issued / seen complete
     for (int tp = blockIdx.x; tp * (NT * ROWS) < A.n && ok; tp += gridDim.x) {
         const int row0 = tp * NT * ROWS;
         // features of 256 rows into the first 80 columns of the activation tiles
@@ -404,14 +424,31 @@ __global__ void __launch_bounds__(256, 1) mlp_infer_fused(fused::Args A)
         for (int l = 0; l < 4 && ok; ++l) {
             const int K = l == 0 ? K0 : HID;
             const int nch = (K + umma::KC - 1) / umma::KC;
-            for (int c = 0; c < nch; ++c, ++g) {
-                const int buf = g & 1;
-                if (g >= 2) ok = __syncthreads_and(umma::mbar_wait(umma::smem_u32(&mbar[buf]), ((g - 2) >> 1) & 1)) != 0;
-                if (!ok) break;
-                umma::load_stage<false>(wst[buf], A.W[l], K, 0, HID, HID, c * umma::KC, K);
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                __syncthreads();
-                if (threadIdx.x == 0) {
+            // the activation tiles written by every thread (features or the previous
+            // epilogue) become visible to the tensor cores
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            // Thread 0 streams the layer's weight stages (one bulk copy of a ready image
+            // each, completion on lbar) and issues the MMAs of both tiles.  Stage g uses
+            // buffer g & 1: free once the MMAs of stage g - 2 have committed.
+            bool ok0 = true;
+            if (threadIdx.x == 0) {
+                for (int c = 0; c < nch && ok0; ++c) {
+                    const int gg = g + c, buf = gg & 1;
+                    if (gg >= 2) ok0 = umma::mbar_wait(umma::smem_u32(&mbar[buf]), ((gg - 2) >> 1) & 1);
+                    if (!ok0) break;
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(umma::smem_u32(&lbar[buf])),
+                                 "r"(WST_BYTES)
+                                 : "memory");
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                            umma::smem_u32(wst[buf])),
+                        "l"(A.Wimg[l] + (size_t)c * (WST_BYTES / 2)), "r"(WST_BYTES), "r"(umma::smem_u32(&lbar[buf]))
+                        : "memory");
+                    issued = gg;
+                    ok0 = umma::mbar_wait(umma::smem_u32(&lbar[buf]), (gg >> 1) & 1);
+                    if (!ok0) break;
+                    landed = gg;
                     asm volatile("tcgen05.fence::after_thread_sync;");
                     const int ksteps = (min(umma::KC, K - c * umma::KC) + 15) / 16;
                     const uint32_t b0 = umma::smem_u32(wst[buf]);
@@ -431,6 +468,8 @@ __global__ void __launch_bounds__(256, 1) mlp_infer_fused(fused::Args A)
                         umma::smem_u32(&mbar[buf])));
                 }
             }
+            ok = __syncthreads_and(threadIdx.x == 0 ? ok0 : true) != 0;
+            g += nch;
             if (!ok) break;
             // the layer's last commit covers all its MMAs
             const int gl = g - 1;
@@ -495,6 +534,8 @@ __global__ void __launch_bounds__(256, 1) mlp_infer_fused(fused::Args A)
         }
     }
     if (!ok && threadIdx.x == 0 && A.err) atomicExch(A.err, 1);
+    // a weight-stage copy not seen complete (after a timeout) must land before the CTA exits
+    if (threadIdx.x == 0 && issued > landed) umma::mbar_wait(umma::smem_u32(&lbar[issued & 1]), (issued >> 1) & 1);
     // bounded wait for anything still in flight before freeing tensor memory
     if (g > 0) __syncthreads_and(umma::mbar_wait(umma::smem_u32(&mbar[(g - 1) & 1]), ((g - 1) >> 1) & 1));
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -507,6 +548,8 @@ __global__ void __launch_bounds__(256, 1) mlp_infer_fused(fused::Args A)
 struct gf_mlp_s {
     float *W[NL] = {}, *b[NL] = {}, *mW[NL] = {}, *vW[NL] = {}, *mb[NL] = {}, *vb[NL] = {}, *gW[NL] = {}, *gb[NL] = {};
     bf16 *Wb[NL] = {}, *WTb[NL] = {};
+    bf16 *Wimg = nullptr;   // weight-stage images of layers 1-4 (fused inference)
+    int wver = 1, imgver = 0;  // bf16 weights version / version the images were built from
     int cap = 0;
     bf16 *X0 = nullptr, *Z[4] = {}, *H[4] = {}, *dZ[4] = {};
     float *Y = nullptr, *dY = nullptr, *in = nullptr, *loss = nullptr;
@@ -609,9 +652,30 @@ gf_status forward(gf_mlp_t m, int n, cudaStream_t s)
 int64_t nparams(int l) { return (int64_t)OUT_DIM[l] * IN_DIM[l]; }
 
 // inference of n samples whose float inputs are in m->in, output float [n][2]
+constexpr int IMG_CHUNKS[4] = {(K0 + umma::KC - 1) / umma::KC, HID / umma::KC, HID / umma::KC, HID / umma::KC};
+
 gf_status infer(gf_mlp_t m, int n, float *Y, cudaStream_t s)
 {
     fused::Args A{};
+    const size_t stage = (size_t)HID * umma::KC;  // bf16 elements per image
+    if (!m->Wimg) {
+        int tot = 0;
+        for (int l = 0; l < 4; ++l) tot += IMG_CHUNKS[l];
+        CUM(cudaMalloc(&m->Wimg, sizeof(bf16) * stage * tot));
+    }
+    {
+        size_t off = 0;
+        for (int l = 0; l < 4; ++l) {
+            if (m->imgver != m->wver) {
+                stage_images_kernel<<<64, 256, 0, s>>>(m->Wb[l], IN_DIM[l], IMG_CHUNKS[l], m->Wimg + off);
+                gf_count_launch(1);
+            }
+            A.Wimg[l] = m->Wimg + off;
+            off += stage * IMG_CHUNKS[l];
+        }
+        CUM(cudaGetLastError());
+        m->imgver = m->wver;
+    }
     A.in = m->in;
     A.n = n;
     A.pi_ct = (float)(GF_PI / m->ct);
@@ -715,6 +779,7 @@ gf_status gf_mlp_create(uint64_t seed, double c_tilde, gf_mlp_t *out)
             // uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights, zero biases
             init_kernel<<<64, 256>>>(m->W[l], (int)nw, (float)(1.0 / sqrt((double)IN_DIM[l])), seed * 16 + l);
             convert_kernel<<<64, 256>>>(m->W[l], m->Wb[l], m->WTb[l], OUT_DIM[l], IN_DIM[l]);
+            ++m->wver;
             gf_count_launch(2);
         }
     } while (0);
@@ -748,6 +813,7 @@ gf_status gf_mlp_params(gf_mlp_t m, float *host, int64_t count, int to_device)
             CUM(cudaMemcpy(m->W[l], host + off, sizeof(float) * nw, cudaMemcpyHostToDevice));
             CUM(cudaMemcpy(m->b[l], host + off + nw, sizeof(float) * nb, cudaMemcpyHostToDevice));
             convert_kernel<<<64, 256>>>(m->W[l], m->Wb[l], m->WTb[l], OUT_DIM[l], IN_DIM[l]);
+            ++m->wver;
             gf_count_launch(1);
         } else {
             CUM(cudaMemcpy(host + off, m->W[l], sizeof(float) * nw, cudaMemcpyDeviceToHost));
@@ -844,6 +910,7 @@ static gf_status train_or_grad(gf_mlp_t m, const float *dev_in, const float *dev
             adam_kernel<<<256, 256, 0, st>>>(m->W[l], m->gW[l], m->mW[l], m->vW[l], (int)nparams(l), lr, b1, b2, 1e-8f, c1, c2);
             adam_kernel<<<4, 256, 0, st>>>(m->b[l], m->gb[l], m->mb[l], m->vb[l], OUT_DIM[l], lr, b1, b2, 1e-8f, c1, c2);
             convert_kernel<<<128, 256, 0, st>>>(m->W[l], m->Wb[l], m->WTb[l], OUT_DIM[l], IN_DIM[l]);
+            ++m->wver;
             gf_count_launch(3);
         }
     }
@@ -987,6 +1054,7 @@ gf_status gf_mlp_destroy(gf_mlp_t m)
         fr(m->Wb[l]);
         fr(m->WTb[l]);
     }
+    fr(m->Wimg);
     fr(m->X0);
     fr(m->Y);
     fr(m->dY);
