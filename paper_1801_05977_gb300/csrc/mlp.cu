@@ -345,7 +345,8 @@ __global__ void __launch_bounds__(256, 1) mlp_infer_fused(fused::Args A)
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + NT * ACT_BYTES + 2 * WST_BYTES);  // MMA commits
     uint64_t *lbar = mbar + 2;                                                            // weight-stage copies
     uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 4);
-    float *yhalf = reinterpret_cast<float *>(tslot + 2);  // [NT][ROWS][2] head partial sums of the second column half
+    // [NT][ROWS][2] head partial sums of the second column half (16-byte aligned, as is par)
+    float *yhalf = reinterpret_cast<float *>(smem + NT * ACT_BYTES + 2 * WST_BYTES + 64);
     float *par = yhalf + NT * ROWS * 2;                  // biases [4][HID], head weights [2][HID]
     for (int i = threadIdx.x; i < PAR_FLOATS; i += blockDim.x)
         par[i] = i < 4 * HID ? A.b[i / HID][i % HID] : A.W5[i - 4 * HID];
@@ -495,15 +496,22 @@ __global__ void __launch_bounds__(256, 1) mlp_infer_fused(fused::Args A)
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                     uint32_t pk[16];  // bf16 pairs, kept in registers
 #pragma unroll
-                    for (int e = 0; e < 32; e += 2) {
-                        const float z0 = __bfloat162float(__float2bfloat16(__uint_as_float(v[e]) + bias[j + e]));
-                        const float z1 = __bfloat162float(__float2bfloat16(__uint_as_float(v[e + 1]) + bias[j + e + 1]));
-                        const __nv_bfloat162 hb = __floats2bfloat162_rn(silu_tanh(z0), silu_tanh(z1));
-                        pk[e >> 1] = (uint32_t)__bfloat16_as_ushort(hb.x) | ((uint32_t)__bfloat16_as_ushort(hb.y) << 16);
+                    for (int e = 0; e < 32; e += 4) {
+                        const float4 bb = *reinterpret_cast<const float4 *>(bias + j + e);  // shared, broadcast
+                        const float z[4] = {__uint_as_float(v[e]) + bb.x, __uint_as_float(v[e + 1]) + bb.y,
+                                            __uint_as_float(v[e + 2]) + bb.z, __uint_as_float(v[e + 3]) + bb.w};
+                        const __nv_bfloat162 h01 = __floats2bfloat162_rn(silu_tanh(z[0]), silu_tanh(z[1]));
+                        const __nv_bfloat162 h23 = __floats2bfloat162_rn(silu_tanh(z[2]), silu_tanh(z[3]));
+                        pk[e >> 1] = (uint32_t)__bfloat16_as_ushort(h01.x) | ((uint32_t)__bfloat16_as_ushort(h01.y) << 16);
+                        pk[(e >> 1) + 1] =
+                            (uint32_t)__bfloat16_as_ushort(h23.x) | ((uint32_t)__bfloat16_as_ushort(h23.y) << 16);
                         if (l == 3) {
-                            const float h0 = __bfloat162float(hb.x), h1 = __bfloat162float(hb.y);
-                            y0 = fmaf(h0, W5s[j + e], fmaf(h1, W5s[j + e + 1], y0));
-                            y1 = fmaf(h0, W5s[HID + j + e], fmaf(h1, W5s[HID + j + e + 1], y1));
+                            const float4 w0 = *reinterpret_cast<const float4 *>(W5s + j + e);
+                            const float4 w1 = *reinterpret_cast<const float4 *>(W5s + HID + j + e);
+                            const float h[4] = {__bfloat162float(h01.x), __bfloat162float(h01.y), __bfloat162float(h23.x),
+                                                __bfloat162float(h23.y)};
+                            y0 = fmaf(h[0], w0.x, fmaf(h[1], w0.y, fmaf(h[2], w0.z, fmaf(h[3], w0.w, y0))));
+                            y1 = fmaf(h[0], w1.x, fmaf(h[1], w1.y, fmaf(h[2], w1.z, fmaf(h[3], w1.w, y1))));
                         }
                     }
                     if (l < 3) {
