@@ -311,7 +311,9 @@ constexpr int ROWS = 128, NT = 2;
 constexpr int ACT_BYTES = ROWS * HID * 2;                // 64 KiB per tile
 constexpr int WST_BYTES = HID * umma::KC * 2;           // 32 KiB per weight stage
 constexpr int PAR_FLOATS = 4 * HID + 2 * HID;  // biases of layers 1-4, then the head weights
-constexpr int SMEM = NT * ACT_BYTES + 2 * WST_BYTES + 64 + NT * ROWS * 2 * 4 + PAR_FLOATS * 4;
+constexpr int NCW = 2 * NT * 2;                 // consumer warps (4 per tile)
+constexpr int THREADS = (NCW + 1) * 32;         // plus one producer warp
+constexpr int SMEM = NT * ACT_BYTES + 2 * WST_BYTES + 128 + PAR_FLOATS * 4;
 constexpr int TMEM_COLS = 512;
 
 // act tile: [k/8][r/8] core matrices, the 16 row groups of a K block adjacent
@@ -336,31 +338,45 @@ struct Args {
 };
 }  // namespace fused
 
-__global__ void __launch_bounds__(256, 1) mlp_infer_fused(fused::Args A)
+// Producer warp (warp 8, one lane): weight-stage bulk copies and MMA issue, tile
+// after tile.  Consumer warps 0-3 own tile 0, 4-7 own tile 1 (warp w reads TMEM
+// lanes 32 (w % 4) .. +31, i.e. its 32 rows, all 256 columns).  While the
+// consumers of one tile run its epilogue (bias, SiLU, bf16 activations back into
+// shared memory) the tensor cores work on the other tile.
+//   lbar[b]  stage copy landed in buffer b    mbar[b]  MMAs of that stage done
+//   accf[t]  tile t's layer MMAs done         actr[t]  tile t's activations written
+//                                                      and its accumulator read (128 arrivals)
+// Every wait is bounded; a timeout sets *err and makes every warp leave.
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__global__ void __launch_bounds__(fused::THREADS, 1) mlp_infer_fused(fused::Args A)
 {
     using namespace fused;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *act[NT] = {smem, smem + ACT_BYTES};
     uint8_t *wst[2] = {smem + NT * ACT_BYTES, smem + NT * ACT_BYTES + WST_BYTES};
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + NT * ACT_BYTES + 2 * WST_BYTES);  // MMA commits
-    uint64_t *lbar = mbar + 2;                                                            // weight-stage copies
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 4);
-    // [NT][ROWS][2] head partial sums of the second column half (16-byte aligned, as is par)
-    float *yhalf = reinterpret_cast<float *>(smem + NT * ACT_BYTES + 2 * WST_BYTES + 64);
-    float *par = yhalf + NT * ROWS * 2;                  // biases [4][HID], head weights [2][HID]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NT * ACT_BYTES + 2 * WST_BYTES);
+    uint64_t *mbar = bars, *lbar = bars + 2, *accf = bars + 4, *actr = bars + 6;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 8);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
+    float *par = reinterpret_cast<float *>(smem + NT * ACT_BYTES + 2 * WST_BYTES + 128);  // biases [4][HID], head [2][HID]
     for (int i = threadIdx.x; i < PAR_FLOATS; i += blockDim.x)
         par[i] = i < 4 * HID ? A.b[i / HID][i % HID] : A.W5[i - 4 * HID];
     const float *W5s = par + 4 * HID;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // 8 warps: warp w reads TMEM lanes 32 (w % 4) .. +31 (its rows) and the column half w / 4
-    const int quarter = warp & 3, half = warp >> 2;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(umma::smem_u32(tslot)),
                      "r"(TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (threadIdx.x == 0) {
-        for (int q = 0; q < 4; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(umma::smem_u32(&mbar[q])));
+        for (int q = 0; q < 6; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(umma::smem_u32(&bars[q])));
+        for (int q = 6; q < 8; ++q)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(umma::smem_u32(&bars[q])), "r"(ROWS));
+        *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -368,120 +384,143 @@ __global__ void __launch_bounds__(256, 1) mlp_infer_fused(fused::Args A)
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tslot;
     const uint32_t idesc = umma::make_idesc(ROWS, HID);
-    int g = 0;  // weight stages used so far (stage g & 1, use g >> 1)
-    bool ok = true;
-    int issued = -1, landed = -1;  // thread 0: last weight stage copy issued / seen complete
-    for (int tp = blockIdx.x; tp * (NT * ROWS) < A.n && ok; tp += gridDim.x) {
-        const int row0 = tp * NT * ROWS;
-        // features of 256 rows into the first 80 columns of the activation tiles
-        for (int q = threadIdx.x; q < NT * ROWS; q += blockDim.x) {
-            const int t = q / ROWS, r = q % ROWS, i = row0 + q;
-            const bool live = i < A.n;
-            float t1 = 0.f, t2 = 0.f, x3 = 0.f, p3 = 0.f, p4 = 0.f, p5 = 2.5f;
-            if (live) {
-                const float *p = A.in + 6 * (size_t)i;
-                t1 = p[0];
-                t2 = p[1];
-                x3 = p[2];
-                p3 = p[3];
-                p4 = p[4];
-                p5 = p[5];
-            }
-            const float rr = sqrtf(t1 * t1 + t2 * t2 + x3 * x3);
-            // ten blocks of 8 features: blocks 0..7 hold cos/sin of 4 frequencies each
-            for (int kb = 0; kb < K0 / 8; ++kb) {
-                float v[8];
-                if (kb < 8) {
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int j = kb * 4 + u;
-                        // |phase| < 30: the fast sine/cosine error (~1e-5 there) is far below bf16 rounding
-                        const float ph = c_freq[j][0] * t1 + c_freq[j][1] * t2 + c_freq[j][2] * A.pi_ct * x3;
-                        __sincosf(ph, &v[2 * u + 1], &v[2 * u]);
-                    }
-                } else if (kb == 8) {
-                    v[0] = 2.f * p3;
-                    v[1] = 2.f * p4;
-                    v[2] = (p5 - 2.5f) / 1.5f;
-                    v[3] = rr;
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const float d = (rr - 0.15f * u) * (1.f / 0.15f);
-                        v[4 + u] = __expf(-0.5f * d * d);
-                    }
-                } else {
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const float d = (rr - 0.15f * (4 + u)) * (1.f / 0.15f);
-                        v[u] = __expf(-0.5f * d * d);
+
+    if (warp == NCW) {
+        // ---------------------------------------------------------------- producer
+        if (lane == 0) {
+            int g = 0, issued = -1, landed = -1, committed = 0, ua[NT] = {0, 0};
+            bool ok = true;
+            for (int tp = blockIdx.x; ok && tp * (NT * ROWS) < A.n; tp += gridDim.x)
+                for (int l = 0; ok && l < 4; ++l) {
+                    const int K = l == 0 ? K0 : HID;
+                    const int nch = (K + umma::KC - 1) / umma::KC;
+                    for (int t = 0; ok && t < NT; ++t) {
+                        // tile t's activations for layer l are written and its accumulator is free
+                        ok = umma::mbar_wait(umma::smem_u32(&actr[t]), ua[t] & 1) && !*abort_flag;
+                        ++ua[t];
+                        if (!ok) break;
+                        asm volatile("tcgen05.fence::after_thread_sync;");
+                        for (int c = 0; ok && c < nch; ++c, ++g) {
+                            const int buf = g & 1;
+                            if (g >= 2) ok = umma::mbar_wait(umma::smem_u32(&mbar[buf]), ((g - 2) >> 1) & 1);
+                            if (!ok) break;
+                            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                                             umma::smem_u32(&lbar[buf])),
+                                         "r"(WST_BYTES)
+                                         : "memory");
+                            asm volatile(
+                                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                                    umma::smem_u32(wst[buf])),
+                                "l"(A.Wimg[l] + (size_t)c * (WST_BYTES / 2)), "r"(WST_BYTES),
+                                "r"(umma::smem_u32(&lbar[buf]))
+                                : "memory");
+                            issued = g;
+                            ok = umma::mbar_wait(umma::smem_u32(&lbar[buf]), (g >> 1) & 1);
+                            if (!ok) break;
+                            landed = g;
+                            asm volatile("tcgen05.fence::after_thread_sync;");
+                            const int ksteps = (min(umma::KC, K - c * umma::KC) + 15) / 16;
+                            const uint32_t b0 = umma::smem_u32(wst[buf]), a0 = umma::smem_u32(act[t]);
+                            for (int kk = 0; kk < ksteps; ++kk) {
+                                const uint64_t ad = umma::make_desc(a0 + (c * 8 + kk * 2) * ACT_LBO, ACT_LBO, ACT_SBO);
+                                const uint64_t bd = umma::make_desc(b0 + kk * 256, 128, (umma::KC / 8) * 128);
+                                const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
+                                asm volatile(
+                                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + t * HID),
+                                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                            }
+                            asm volatile(
+                                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                    umma::smem_u32(&mbar[buf])));
+                        }
+                        if (!ok) break;
+                        // tile t's accumulator is complete once its MMAs are
+                        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                            umma::smem_u32(&accf[t])));
+                        ++committed;
                     }
                 }
-                __align__(16) bf16 hv[8];
-#pragma unroll
-                for (int e = 0; e < 8; ++e) hv[e] = __float2bfloat16(live ? v[e] : 0.f);
-                *reinterpret_cast<uint4 *>(act[t] + act_off(r, kb * 8)) = *reinterpret_cast<const uint4 *>(hv);
+            if (!ok) {
+                *abort_flag = 1;
+                if (A.err) atomicExch(A.err, 1);
             }
+            // before the CTA exits: the last copy has landed and every MMA has completed
+            if (issued > landed) umma::mbar_wait(umma::smem_u32(&lbar[issued & 1]), (issued >> 1) & 1);
+            if (g > 0) umma::mbar_wait(umma::smem_u32(&mbar[(g - 1) & 1]), ((g - 1) >> 1) & 1);
+            (void)committed;
         }
-        for (int l = 0; l < 4 && ok; ++l) {
-            const int K = l == 0 ? K0 : HID;
-            const int nch = (K + umma::KC - 1) / umma::KC;
-            // the activation tiles written by every thread (features or the previous
-            // epilogue) become visible to the tensor cores
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
-            // Thread 0 streams the layer's weight stages (one bulk copy of a ready image
-            // each, completion on lbar) and issues the MMAs of both tiles.  Stage g uses
-            // buffer g & 1: free once the MMAs of stage g - 2 have committed.
-            bool ok0 = true;
-            if (threadIdx.x == 0) {
-                for (int c = 0; c < nch && ok0; ++c) {
-                    const int gg = g + c, buf = gg & 1;
-                    if (gg >= 2) ok0 = umma::mbar_wait(umma::smem_u32(&mbar[buf]), ((gg - 2) >> 1) & 1);
-                    if (!ok0) break;
-                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(umma::smem_u32(&lbar[buf])),
-                                 "r"(WST_BYTES)
-                                 : "memory");
-                    asm volatile(
-                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                            umma::smem_u32(wst[buf])),
-                        "l"(A.Wimg[l] + (size_t)c * (WST_BYTES / 2)), "r"(WST_BYTES), "r"(umma::smem_u32(&lbar[buf]))
-                        : "memory");
-                    issued = gg;
-                    ok0 = umma::mbar_wait(umma::smem_u32(&lbar[buf]), (gg >> 1) & 1);
-                    if (!ok0) break;
-                    landed = gg;
-                    asm volatile("tcgen05.fence::after_thread_sync;");
-                    const int ksteps = (min(umma::KC, K - c * umma::KC) + 15) / 16;
-                    const uint32_t b0 = umma::smem_u32(wst[buf]);
-                    for (int t = 0; t < NT; ++t) {
-                        const uint32_t a0 = umma::smem_u32(act[t]);
-                        for (int kk = 0; kk < ksteps; ++kk) {
-                            const uint64_t ad = umma::make_desc(a0 + (c * 8 + kk * 2) * ACT_LBO, ACT_LBO, ACT_SBO);
-                            const uint64_t bd = umma::make_desc(b0 + kk * 256, 128, (umma::KC / 8) * 128);
-                            const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
-                            asm volatile(
-                                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + t * HID),
-                                "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+    } else {
+        // ---------------------------------------------------------------- consumers
+        const int t = warp >> 2, quarter = warp & 3, r = quarter * 32 + lane;
+        uint8_t *at = act[t];
+        const float b50 = A.b5[0], b51 = A.b5[1];
+        int fa = 0;
+        bool ok = true;
+        for (int tp = blockIdx.x; ok && tp * (NT * ROWS) < A.n; tp += gridDim.x) {
+            const int i = tp * NT * ROWS + t * ROWS + r;
+            const bool live = i < A.n;
+            // features of this row into the first 80 columns of the tile
+            {
+                float t1 = 0.f, t2 = 0.f, x3 = 0.f, p3 = 0.f, p4 = 0.f, p5 = 2.5f;
+                if (live) {
+                    const float *p = A.in + 6 * (size_t)i;
+                    t1 = p[0];
+                    t2 = p[1];
+                    x3 = p[2];
+                    p3 = p[3];
+                    p4 = p[4];
+                    p5 = p[5];
+                }
+                const float rr = sqrtf(t1 * t1 + t2 * t2 + x3 * x3);
+                // ten blocks of 8 features: blocks 0..7 hold cos/sin of 4 frequencies each
+                for (int kb = 0; kb < K0 / 8; ++kb) {
+                    float v[8];
+                    if (kb < 8) {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int j = kb * 4 + u;
+                            // |phase| < 30: the fast sine/cosine error (~1e-5 there) is far below bf16 rounding
+                            const float ph = c_freq[j][0] * t1 + c_freq[j][1] * t2 + c_freq[j][2] * A.pi_ct * x3;
+                            __sincosf(ph, &v[2 * u + 1], &v[2 * u]);
+                        }
+                    } else if (kb == 8) {
+                        v[0] = 2.f * p3;
+                        v[1] = 2.f * p4;
+                        v[2] = (p5 - 2.5f) / 1.5f;
+                        v[3] = rr;
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const float d = (rr - 0.15f * u) * (1.f / 0.15f);
+                            v[4 + u] = __expf(-0.5f * d * d);
+                        }
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const float d = (rr - 0.15f * (4 + u)) * (1.f / 0.15f);
+                            v[u] = __expf(-0.5f * d * d);
                         }
                     }
-                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                        umma::smem_u32(&mbar[buf])));
+                    uint32_t pk[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const __nv_bfloat162 hb = __floats2bfloat162_rn(live ? v[2 * e] : 0.f, live ? v[2 * e + 1] : 0.f);
+                        pk[e] = (uint32_t)__bfloat16_as_ushort(hb.x) | ((uint32_t)__bfloat16_as_ushort(hb.y) << 16);
+                    }
+                    *reinterpret_cast<uint4 *>(at + act_off(r, kb * 8)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                 }
             }
-            ok = __syncthreads_and(threadIdx.x == 0 ? ok0 : true) != 0;
-            g += nch;
-            if (!ok) break;
-            // the layer's last commit covers all its MMAs
-            const int gl = g - 1;
-            ok = __syncthreads_and(umma::mbar_wait(umma::smem_u32(&mbar[gl & 1]), (gl >> 1) & 1)) != 0;
-            if (!ok) break;
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            const float *bias = par + l * HID;
-            for (int t = 0; t < NT; ++t) {
-                const int r = quarter * 32 + lane;
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            mbar_arrive(umma::smem_u32(&actr[t]));
+            for (int l = 0; ok && l < 4; ++l) {
+                ok = umma::mbar_wait(umma::smem_u32(&accf[t]), fa & 1) && !*abort_flag;
+                ++fa;
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const float *bias = par + l * HID;
                 float y0 = 0.f, y1 = 0.f;
-                for (int j = half * (HID / 2); j < (half + 1) * (HID / 2); j += 32) {
+                for (int j = 0; j < HID; j += 32) {
                     uint32_t v[32];
                     const uint32_t taddr = tmem + t * HID + ((uint32_t)(quarter * 32) << 16) + (uint32_t)j;
                     asm volatile(
@@ -517,37 +556,32 @@ __global__ void __launch_bounds__(256, 1) mlp_infer_fused(fused::Args A)
                     if (l < 3) {
 #pragma unroll
                         for (int q = 0; q < 4; ++q)
-                            *reinterpret_cast<uint4 *>(act[t] + act_off(r, j + 8 * q)) =
+                            *reinterpret_cast<uint4 *>(at + act_off(r, j + 8 * q)) =
                                 make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
                     }
                 }
-                if (l == 3 && half == 1) {
-                    yhalf[(t * ROWS + r) * 2] = y0;
-                    yhalf[(t * ROWS + r) * 2 + 1] = y1;
-                }
-                if (l == 3) __syncwarp();
-                if (l == 3) {
-                    // combine the two column halves (second half parked in shared memory)
-                    __syncthreads();
-                    const int i = row0 + t * ROWS + r;
-                    if (half == 0 && i < A.n) {
-                        A.Y[2 * (size_t)i] = y0 + yhalf[(t * ROWS + r) * 2] + A.b5[0];
-                        A.Y[2 * (size_t)i + 1] = y1 + yhalf[(t * ROWS + r) * 2 + 1] + A.b5[1];
+                if (l < 3) {
+                    // next layer's input written, accumulator read: hand the tile back
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    asm volatile("tcgen05.fence::before_thread_sync;");
+                    mbar_arrive(umma::smem_u32(&actr[t]));
+                } else {
+                    asm volatile("tcgen05.fence::before_thread_sync;");
+                    if (live) {
+                        A.Y[2 * (size_t)i] = y0 + b50;
+                        A.Y[2 * (size_t)i + 1] = y1 + b51;
                     }
-                    __syncthreads();
                 }
             }
-            asm volatile("tcgen05.fence::before_thread_sync;");
-            // the next layer's MMAs read the tiles written above and overwrite the accumulators
+        }
+        if (!ok) {
+            *abort_flag = 1;
+            if (A.err) atomicExch(A.err, 1);
         }
     }
-    if (!ok && threadIdx.x == 0 && A.err) atomicExch(A.err, 1);
-    // a weight-stage copy not seen complete (after a timeout) must land before the CTA exits
-    if (threadIdx.x == 0 && issued > landed) umma::mbar_wait(umma::smem_u32(&lbar[issued & 1]), (issued >> 1) & 1);
-    // bounded wait for anything still in flight before freeing tensor memory
-    if (g > 0) __syncthreads_and(umma::mbar_wait(umma::smem_u32(&mbar[(g - 1) & 1]), ((g - 1) >> 1) & 1));
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
 }
 
@@ -698,7 +732,7 @@ gf_status infer(gf_mlp_t m, int n, float *Y, cudaStream_t s)
     CUM(cudaFuncSetAttribute(mlp_infer_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, fused::SMEM));
     int tiles = (n + fused::NT * fused::ROWS - 1) / (fused::NT * fused::ROWS);
     int grid = tiles < m->nsm ? tiles : m->nsm;
-    mlp_infer_fused<<<grid, 256, fused::SMEM, s>>>(A);
+    mlp_infer_fused<<<grid, fused::THREADS, fused::SMEM, s>>>(A);
     gf_count_launch(1);
     CUM(cudaGetLastError());
     return GF_OK;
