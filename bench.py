@@ -356,7 +356,7 @@ def run_gpu(args):
                      "unit": "TFLOP/s", "frac": achieved / peak_fp64,
                      "traffic": FAR_TRAFFIC_BYTES if n_targets == 1_000_000 else None,
                      "algorithmic_flops": far_flops, "core_terms_by_degree": bands,
-                     "note": "FP64 pipe bound (ncu: 80% of peak while active); achieved = algorithmic FP64 flops "
+                     "note": "FP64 pipe bound (ncu: 86% of peak while active); achieved = algorithmic FP64 flops "
                              "of the double-precision core terms (b|x3| <= 18; 18/16/14 flops per term for "
                              "exponential degree 5/4/3, FMA = 2 flops) / far-kernel time; the float tail is not "
                              "counted; peak from unit counts and clock (152 SMs x 2 FP64 FMA/clk x 2 flop x "
