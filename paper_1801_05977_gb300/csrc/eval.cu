@@ -516,7 +516,7 @@ __global__ void series_tables(EvalArgs a, E *tab, double2 *exptab, PropEntry *pr
     if (exptab)
         for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.exptab_n; j += gridDim.x * blockDim.x)
         {
-            const double off = (double)(j - a.exptab_j0) * 0.0078125;
+            const double off = (double)(j - a.exptab_j0) * (1.0 / GF_EXPTAB_STEPS);
             exptab[j] = make_double2(exp(-off), off);
         }
     if (blockIdx.x == 0 && threadIdx.x < 32) {
@@ -550,33 +550,56 @@ __device__ __forceinline__ double warp_max(double v)
 }
 
 // e^{-y} by Tang's table-driven method (ACM TOMS 15, 1989): y = y_j + r with
-// y_j = (j - j0)/128, |r| <= (1/2 + 3e-3)/128; e^{-y} = T[j] e^{-r}, the plan
-// table holding (e^{-y_j}, y_j).  The index is rint(128 yf) + j0 for a float
-// evaluation yf of y (|128 (yf - y)| < 3e-3 for |y| < 100, rounding by the
-// 1.5 * 2^23 shift), clamped to the table (callers discard the terms whose y
-// lies beyond it).  Returns e^{-r} by its Taylor polynomial of degree DEG and
-// T[j].x.  Truncation relative to e^{-y}: 5e-18 (DEG 5), 7.7e-15 (DEG 4),
-// 9.9e-12 (DEG 3); callers take DEG 4 and 3 only for terms at least e^7 and
-// e^14 below the largest term of the series.
+// y_j = (j - j0)/S, S = GF_EXPTAB_STEPS, |r| <= (1/2 + 2e-2)/S; e^{-y} = T[j] e^{-r},
+// the plan table holding (e^{-y_j}, y_j).  The index is rint(S yf) + j0 for a
+// float evaluation yf of y (|yf - y| < 6e-8 (2 b|x3| + 2 |ln b| + |y|), so that
+// |S (yf - y)| < 2e-2 for the core terms, b|x3| < 20, and S <= 2048; rounding
+// by the 1.5 * 2^23 shift), clamped to the table (callers discard the
+// terms whose y lies beyond it).  Returns e^{-r} by its Taylor polynomial of
+// degree DEG and T[j].x.  The truncation relative to e^{-y} is at most
+// |r|^{DEG+1}/(DEG+1)! e^{|r|}; the far kernel takes three degrees (EXP_DEG_A >
+// B > C), switching where a term lies e^{EXP_GAP_B} and e^{EXP_GAP_C} below the
+// largest term of its series, so that every term's truncation stays below
+// 1e-17 of that largest term (bounds at |r| = 0.51/S, 0.52/S for S = 2048):
+//   S = 128: degrees 5/4/3 (5.6e-18, 8.4e-15, 1.1e-11), gaps 7 and 14;
+//   S = 256: degrees 5/4/3 (8.7e-20, 2.6e-16, 6.6e-13), gaps 4 and 12;
+//   S = 512: degrees 4/3/2 (8.2e-18, 4.1e-14, 1.7e-10), gaps 9 and 17.5;
+//   S = 1024: degrees 4/3/2 (2.6e-19, 2.6e-15, 2.1e-11), gaps 6.25 and 15.25;
+//   S = 2048: degrees 4/3/2 (8.8e-21, 1.7e-16, 2.7e-12), gaps 3.5 and 13.25.
+constexpr int EXP_DEG_A = GF_EXPTAB_STEPS >= 512 ? 4 : 5;
+constexpr int EXP_DEG_B = EXP_DEG_A - 1, EXP_DEG_C = EXP_DEG_A - 2;
+constexpr double EXP_GAP_B = GF_EXPTAB_STEPS >= 2048 ? 3.5 : GF_EXPTAB_STEPS >= 1024 ? 6.25
+                           : GF_EXPTAB_STEPS >= 512  ? 9.0 : GF_EXPTAB_STEPS >= 256  ? 4.0 : 7.0;
+constexpr double EXP_GAP_C = GF_EXPTAB_STEPS >= 2048 ? 13.25 : GF_EXPTAB_STEPS >= 1024 ? 15.25
+                           : GF_EXPTAB_STEPS >= 512  ? 17.5 : GF_EXPTAB_STEPS >= 256  ? 12.0 : 14.0;
+
+// (-1)^i / i!
+__host__ __device__ constexpr double exp_taylor_coef(int i) { return i == 0 ? 1.0 : -exp_taylor_coef(i - 1) / i; }
+
 template <int DEG>
 __device__ __forceinline__ double exp_neg_split(double y, float yf, const double2 *__restrict__ T, int j0, int jmax,
                                                 double &Tj)
 {
-    const float jm = fmaf(128.0f, yf, 12582912.0f);
+    const float jm = fmaf((float)GF_EXPTAB_STEPS, yf, 12582912.0f);
     const int idx = min(max(__float_as_int(jm) - 0x4B400000 + j0, 0), jmax);
     const double2 t = __ldg(T + idx);
     const double r = y - t.y;
     Tj = t.x;
+    constexpr double c5 = exp_taylor_coef(5), c4 = exp_taylor_coef(4), c3 = exp_taylor_coef(3),
+                     c2 = exp_taylor_coef(2);
     double p;
     if (DEG >= 5) {
-        p = fma(r, -1.0 / 120.0, 1.0 / 24.0);
-        p = fma(p, r, -1.0 / 6.0);
+        p = fma(r, c5, c4);
+        p = fma(p, r, c3);
     } else if (DEG == 4) {
-        p = fma(r, 1.0 / 24.0, -1.0 / 6.0);
+        p = fma(r, c4, c3);
     } else {
-        p = -1.0 / 6.0;
+        p = c3;
     }
-    p = fma(p, r, 0.5);
+    if (DEG >= 3)
+        p = fma(p, r, c2);
+    else
+        p = c2;
     p = fma(p, r, -1.0);
     return fma(p, r, 1.0);
 }
@@ -616,9 +639,11 @@ __device__ __forceinline__ FarLane far_lane(const EvalArgs &a, int slot, int cou
     reduce_period(x2, L.t2, L.m2);
     L.z = fabs(x3);
     L.sg = x3 >= 0.0 ? 1.0 : -1.0;
-    L.iz = 1.0 / L.z;
-    double Tz = a.T * L.iz;
-    L.R2 = L.valid ? a.k * a.k + Tz * Tz : 0.0;
+    // explicitly rounded (no contraction): R2 decides the row split, which the
+    // double-precision and float-tail kernels must reproduce exactly
+    L.iz = __ddiv_rn(1.0, L.z);
+    const double Tz = __dmul_rn(a.T, L.iz);
+    L.R2 = L.valid ? __dadd_rn(__dmul_rn(a.k, a.k), __dmul_rn(Tz, Tz)) : 0.0;
     return L;
 }
 
@@ -698,20 +723,20 @@ __device__ __forceinline__ void reinsch_seg(RState<NH> &st, const BetaEntry *__r
     }
 }
 
-// The terms n2 = start, start + dir, ... (n3 + n4 + n5 of them, from the outer
-// end of the row towards the anchor): the first n3 with the degree-3
-// exponential, the next n4 with degree 4, the rest with degree 5.
+// The terms n2 = start, start + dir, ... (nc + nb + na of them, from the outer
+// end of the row towards the anchor): the first nc with the degree-EXP_DEG_C
+// exponential, the next nb with degree EXP_DEG_B, the rest with EXP_DEG_A.
 template <int NH>
 __device__ __forceinline__ void reinsch_run(RState<NH> &st, const BetaEntry *__restrict__ row, int start, int dir,
-                                            int n3, int n4, int n5, double a2, float c1sq, float a2f, float R2f,
+                                            int nc, int nb, int na, double a2, float c1sq, float a2f, float R2f,
                                             double z, const Reinsch &RS, const double2 *__restrict__ T, int j0, int jmax)
 {
     int n2 = start;
     float c2f = a2f + (float)start;
     double c2 = a2 + start;
-    reinsch_seg<NH, 3>(st, row, n2, n3, dir, c2f, c2, c1sq, R2f, z, RS, T, j0, jmax);
-    reinsch_seg<NH, 4>(st, row, n2, n4, dir, c2f, c2, c1sq, R2f, z, RS, T, j0, jmax);
-    reinsch_seg<NH, 5>(st, row, n2, n5, dir, c2f, c2, c1sq, R2f, z, RS, T, j0, jmax);
+    reinsch_seg<NH, EXP_DEG_C>(st, row, n2, nc, dir, c2f, c2, c1sq, R2f, z, RS, T, j0, jmax);
+    reinsch_seg<NH, EXP_DEG_B>(st, row, n2, nb, dir, c2f, c2, c1sq, R2f, z, RS, T, j0, jmax);
+    reinsch_seg<NH, EXP_DEG_A>(st, row, n2, na, dir, c2f, c2, c1sq, R2f, z, RS, T, j0, jmax);
 }
 
 // One recurrence step with zero weight (recurrence index 0 of a sum whose
@@ -779,37 +804,51 @@ __device__ __forceinline__ void add_row(F S[][2], const F rr[][2], F c1, F ik2)
 }
 
 // The same segment sums in float (hardware ex2), for the exponentially small
-// tail of a double-precision plan.
+// tail of a double-precision plan: sum_{n2=lo}^{hi} w(n2) v^{n2-lo}, v = e^{i t2},
+// by Horner's rule from hi down.  Four entries are loaded ahead of their four
+// Horner steps, so that a warp has four independent loads in flight.
+template <int NH>
+__device__ __forceinline__ void horner_step_f32(const BetaEntry &be, float c2, float z, float cv, float sv,
+                                                float acc[NH][2])
+{
+    // no per-lane truncation test: the terms of the warp's disk beyond the lane's
+    // own set are below e^{-T} of its largest term (they add accuracy), and
+    // propagating n have bl2 = +inf
+    const float e = ex2_approx(-be.bl2 * z);
+    float wv[NH];
+    wv[0] = e * be.ibf;
+    if (NH > 1) {
+        wv[1] = c2 * wv[0];
+        wv[2] = c2 * wv[1];
+        wv[3] = be.bf * e;
+        wv[4] = e;
+        wv[5] = c2 * e;
+    }
+#pragma unroll
+    for (int k = 0; k < NH; ++k) {
+        const float nx = fmaf(acc[k][0], cv, fmaf(-acc[k][1], sv, wv[k]));
+        const float ny = fmaf(acc[k][0], sv, acc[k][1] * cv);
+        acc[k][0] = nx;
+        acc[k][1] = ny;
+    }
+}
+
 template <int NH>
 __device__ __forceinline__ void seg_horner_f32(const BetaEntry *__restrict__ row, int lo, int hi, float a2f,
-                                               float c1sq, float R2f, float z, float cv, float sv, float acc[NH][2])
+                                               float z, float cv, float sv, float acc[NH][2])
 {
 #pragma unroll
     for (int e = 0; e < NH; ++e) acc[e][0] = acc[e][1] = 0.f;
     float c2 = a2f + (float)hi;
-    for (int n2 = hi; n2 >= lo; --n2, c2 -= 1.0f) {
-        const BetaEntry be = row[n2];
-        // no per-lane truncation test: the terms of the warp's disk beyond the
-        // lane's own set are below e^{-T} of its largest term (they add accuracy),
-        // and propagating n have bl2 = +inf
-        const float e = ex2_approx(-be.bl2 * z);
-        float wv[NH];
-        wv[0] = e * be.ibf;
-        if (NH > 1) {
-            wv[1] = c2 * wv[0];
-            wv[2] = c2 * wv[1];
-            wv[3] = be.bf * e;
-            wv[4] = e;
-            wv[5] = c2 * e;
-        }
+    int n2 = hi;
+    for (; n2 - 3 >= lo; n2 -= 4, c2 -= 4.0f) {
+        BetaEntry be[4];
 #pragma unroll
-        for (int k = 0; k < NH; ++k) {
-            const float nx = fmaf(acc[k][0], cv, fmaf(-acc[k][1], sv, wv[k]));
-            const float ny = fmaf(acc[k][0], sv, acc[k][1] * cv);
-            acc[k][0] = nx;
-            acc[k][1] = ny;
-        }
+        for (int u = 0; u < 4; ++u) be[u] = row[n2 - u];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) horner_step_f32<NH>(be[u], c2 - (float)u, z, cv, sv, acc);
     }
+    for (; n2 >= lo; --n2, c2 -= 1.0f) horner_step_f32<NH>(row[n2], c2, z, cv, sv, acc);
 }
 
 // ---------------------------------------------------------------------------
@@ -851,11 +890,119 @@ __device__ __forceinline__ void slab_rows(int n1a, int n1b, float Rc2f, float a1
     if (slab < nslab - 1) hi = k0 + ((slab + 1) * Lc) / nslab - 1;
 }
 
+// The rows of a warp's far sums and their core segments.  The double-precision
+// kernel and the float-tail kernel must split every row identically, so every
+// operation here (and in far_lane) is explicitly rounded: no contraction can
+// make the two kernels disagree on a term.
+struct FarWarp {
+    double izmax;      // 1/z_min over the warp's lanes
+    float R2mf, Rc2f;  // truncation disk |alpha_n|^2 <= R2m (warp maximum) and core disk Rc2
+    float a1f, a2f;
+    int n1a, n1b;      // rows of the truncation disk (one index of margin)
+    int N0;            // anchor n2 = rint(-alpha_2)
+};
+
+__device__ __forceinline__ FarWarp far_warp(const EvalArgs &a, const FarLane &L)
+{
+    FarWarp W;
+    const double R2m = warp_max(L.R2);
+    W.izmax = warp_max(L.valid ? L.iz : 0.0);
+    // core disk of the warp: b z_min <= Y0
+    const double Rc2 = fmin(__dadd_rn(__dmul_rn(a.k, a.k), __dmul_rn(__dmul_rn(FAR_CORE_Y0 * FAR_CORE_Y0, W.izmax), W.izmax)), R2m);
+    W.R2mf = __double2float_rn(R2m);
+    W.Rc2f = __double2float_rn(Rc2);
+    W.a1f = __double2float_rn(a.a1);
+    W.a2f = __double2float_rn(a.a2);
+    const float Rmf = __fsqrt_rn(W.R2mf);
+    W.n1a = max(a.n1lo, (int)floorf(__fsub_rn(-W.a1f, Rmf)) - 1);
+    W.n1b = min(a.n1hi, (int)ceilf(__fadd_rn(-W.a1f, Rmf)) + 1);
+    W.N0 = (int)rint(-a.a2);
+    return W;
+}
+
+// Row n1 of the warp's truncation disk: its index range [n2a, n2b] (false when
+// the row is empty) and core segment [ca, cb] (ca > cb: no core), the core
+// widened to contain N0.  Bounds are formed in float with a one-index margin:
+// every lane still keeps exactly its own truncation set in the double sums, and
+// the core/tail split only moves terms of size ~e^-18 between double and float.
+__device__ __forceinline__ bool far_row(const FarWarp &W, const EvalArgs &a, int n1, float &c1f, float &c1sq, int &n2a,
+                                        int &n2b, int &ca, int &cb)
+{
+    c1f = __fadd_rn(W.a1f, (float)n1);
+    c1sq = __fmul_rn(c1f, c1f);
+    const float remf = __fsub_rn(W.R2mf, c1sq);
+    if (remf < -1.0f) return false;
+    const float srf = __fsqrt_rn(fmaxf(remf, 0.f));
+    n2a = max(a.n2lo, (int)floorf(__fsub_rn(-W.a2f, srf)) - 1);
+    n2b = min(a.n2hi, (int)ceilf(__fadd_rn(-W.a2f, srf)) + 1);
+    if (n2a > n2b) return false;
+    ca = n2b + 1;
+    cb = n2b;
+    const float remc = __fsub_rn(W.Rc2f, c1sq);
+    if (remc >= 0.f) {
+        const float src = __fsqrt_rn(remc);
+        ca = max(n2a, (int)ceilf(__fsub_rn(-W.a2f, src)));
+        cb = min(n2b, (int)floorf(__fadd_rn(-W.a2f, src)));
+        if (ca > cb) {
+            ca = n2b + 1;
+            cb = n2b;
+        } else {
+            ca = min(ca, W.N0);
+            cb = max(cb, W.N0);
+        }
+    }
+    return true;
+}
+
+// The float tails of row n1 (the segments outside its core, or the whole row
+// when it has none), each by Horner's rule from its first index and moved to the
+// anchor N0, rotated by the row phase A = e^{i c1 t1} and added into Sf.
+template <int NH, int NS>
+__device__ __forceinline__ void far_row_tails(const BetaEntry *__restrict__ row, int n2a, int n2b, int ca, int cb,
+                                              int N0, float a2f, float c1f, float c1sq, float zf, float cvf, float svf,
+                                              const PhaseF &PF, float Ax, float Ay, float ik2f, float Sf[NS][2])
+{
+    const int tl_hi = (ca <= cb) ? ca - 1 : n2b;
+    const int th_lo = (ca <= cb) ? cb + 1 : n2b + 1;
+    if (n2a > tl_hi && th_lo > n2b) return;
+    float tf[NH][2];
+#pragma unroll
+    for (int e = 0; e < NH; ++e) tf[e][0] = tf[e][1] = 0.f;
+    if (n2a <= tl_hi) {
+        float acc[NH][2], ps, pc;
+        seg_horner_f32<NH>(row, n2a, tl_hi, a2f, zf, cvf, svf, acc);
+        phase_m(PF, n2a - N0, ps, pc);
+#pragma unroll
+        for (int e = 0; e < NH; ++e) {
+            tf[e][0] += pc * acc[e][0] - ps * acc[e][1];
+            tf[e][1] += pc * acc[e][1] + ps * acc[e][0];
+        }
+    }
+    if (th_lo <= n2b) {
+        float acc[NH][2], ps, pc;
+        seg_horner_f32<NH>(row, th_lo, n2b, a2f, zf, cvf, svf, acc);
+        phase_m(PF, th_lo - N0, ps, pc);
+#pragma unroll
+        for (int e = 0; e < NH; ++e) {
+            tf[e][0] += pc * acc[e][0] - ps * acc[e][1];
+            tf[e][1] += pc * acc[e][1] + ps * acc[e][0];
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < NH; ++e) {
+        const float x = tf[e][0], y = tf[e][1];
+        tf[e][0] = Ax * x - Ay * y;
+        tf[e][1] = Ax * y + Ay * x;
+    }
+    add_row<NH, float>(Sf, tf, c1f, ik2f);
+}
+
 // One warp, row slab `slab` of `nslab` of chunk w (32 consecutive entries of
 // the sorted far list).  The slab's share of the series is added into the
 // output entries, which the near pass set to zero; the propagating terms go
-// with slab 0.
-template <int NF>
+// with slab 0.  TAILS: the float tails are summed here too; otherwise the
+// float-tail kernel (far3d_tail) adds them.
+template <int NF, bool TAILS>
 __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, int nslab)
 {
     constexpr int NH = NF == 1 ? 1 : 6;
@@ -870,17 +1017,14 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, i
     const double2 *T = a.exptab;
     const int jmax = a.exptab_n - 1, j0 = a.exptab_j0;
     const float a2f = (float)a.a2;
-    // every row is summed from the anchor n2 = N0 outwards (the centre of all
-    // rows' truncation intervals); e^{i(alpha_2 + N0) t2} multiplies the total
-    const int N0 = (int)rint(-a.a2);
     {
         FarLane L = far_lane(a, w * 32 + lane, count);
-        const double R2m = warp_max(L.R2);
+        const FarWarp W = far_warp(a, L);
         const float R2f = (float)L.R2;
-        // core disk of the warp: b z_min <= Y0
-        const double iz = L.valid ? L.iz : 0.0;
-        const double izmax = warp_max(iz);
-        const double Rc2 = fmin(k2 + FAR_CORE_Y0 * FAR_CORE_Y0 * izmax * izmax, R2m);
+        const double izmax = W.izmax;
+        // every row is summed from the anchor n2 = N0 outwards (the centre of all
+        // rows' truncation intervals); e^{i(alpha_2 + N0) t2} multiplies the total
+        const int N0 = W.N0;
         double sv, cv, s1, c1v;
         sincos(L.t2, &sv, &cv);
         sincos(L.t1, &s1, &c1v);
@@ -888,8 +1032,9 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, i
         const Reinsch RS = reinsch_lane(sv, cv);
         const PhaseF PF = phase_split(L.t2);
         // every term is at most e^{-(b - bmin) z_min} of the largest one (e^{-bz}/b
-        // decreases in b): degree 4 from b >= bmin + 7/z_min, 3 from bmin + 14/z_min
-        const float b4 = (float)(a.bmin + 7.0 * izmax), b3 = (float)(a.bmin + 14.0 * izmax);
+        // decreases in b): degree B from b >= bmin + EXP_GAP_B/z_min, C from
+        // bmin + EXP_GAP_C/z_min
+        const float b4 = (float)(a.bmin + EXP_GAP_B * izmax), b3 = (float)(a.bmin + EXP_GAP_C * izmax);
         const float k2f = (float)k2;
         const float svf = (float)sv, cvf = (float)cv, zf = (float)L.z;
         double P[NF][2];
@@ -931,15 +1076,14 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, i
                 }
             }
         }
-        // Row bounds and the core segment are index ranges: they are formed in
-        // float with a one-index margin (every lane still keeps exactly its own
-        // truncation set; the core/tail split only moves terms of size ~e^-18
-        // between double and float).
-        const float R2mf = (float)R2m, Rc2f = (float)Rc2, a1f = (float)a.a1;
-        const float Rmf = sqrtf(R2mf);
-        const int n1a = max(a.n1lo, (int)floorf(-a1f - Rmf) - 1), n1b = min(a.n1hi, (int)ceilf(-a1f + Rmf) + 1);
         int r_lo, r_hi;
-        slab_rows(n1a, n1b, Rc2f, a1f, slab, nslab, r_lo, r_hi);
+        slab_rows(W.n1a, W.n1b, W.Rc2f, W.a1f, slab, nslab, r_lo, r_hi);
+        if (!TAILS) {
+            // only rows with a core segment: |c1| <= sqrt(Rc2), one row of margin
+            const float rcf = sqrtf(fmaxf(W.Rc2f, 0.f));
+            r_lo = max(r_lo, (int)ceilf(-W.a1f - rcf) - 1);
+            r_hi = min(r_hi, (int)floorf(-W.a1f + rcf) + 1);
+        }
         double2 A = make_double2(1.0, 0.0);  // e^{i c1 t1}
         for (int n1 = r_lo; n1 <= r_hi; ++n1) {
             // row phase by recurrence, re-anchored every 16 rows
@@ -951,7 +1095,7 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, i
                 A = cmul(A, E1);
             }
             // float tails fold into the double sums every 8 rows
-            if (((n1 - r_lo) & 7) == 7) {
+            if (TAILS && ((n1 - r_lo) & 7) == 7) {
 #pragma unroll
                 for (int e = 0; e < NS; ++e) {
                     S[e][0] += (double)Sf[e][0];
@@ -959,36 +1103,17 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, i
                     Sf[e][0] = Sf[e][1] = 0.f;
                 }
             }
-            const float c1f = a1f + (float)n1;
-            const float c1sq = c1f * c1f;
-            const float remf = R2mf - c1sq;
-            if (remf < -1.0f) continue;
-            const float srf = sqrtf(fmaxf(remf, 0.f));
-            const int n2a = max(a.n2lo, (int)floorf(-a2f - srf) - 1), n2b = min(a.n2hi, (int)ceilf(-a2f + srf) + 1);
-            if (n2a > n2b) continue;
+            float c1f, c1sq;
+            int n2a, n2b, ca, cb;
+            if (!far_row(W, a, n1, c1f, c1sq, n2a, n2b, ca, cb)) continue;
             const BetaEntry *row = tab + (size_t)(n1 - a.n1lo) * W2 - a.n2lo;
-            // core segment [ca, cb] of this row, widened to contain N0 (empty when ca > cb)
-            int ca = n2b + 1, cb = n2b;
-            const float remc = Rc2f - c1sq;
-            if (remc >= 0.f) {
-                const float src = sqrtf(remc);
-                ca = max(n2a, (int)ceilf(-a2f - src));
-                cb = min(n2b, (int)floorf(-a2f + src));
-                if (ca > cb) {
-                    ca = n2b + 1;
-                    cb = n2b;
-                } else {
-                    ca = min(ca, N0);
-                    cb = max(cb, N0);
-                }
-            }
             if (ca <= cb) {
                 // right: n2 = cb .. N0 (index n2 - N0); left: n2 = ca .. N0-1 (index
                 // N0 - n2, e^{-i theta}) and a zero step for index 0
                 RState<NH> R, Lt;
 #pragma unroll
                 for (int e = 0; e < NH; ++e) R.d[e] = R.b[e] = Lt.d[e] = Lt.b[e] = 0.0;
-                // degree bands: |c2| >= q3 (degree 3), >= q4 (degree 4), one index of margin
+                // degree bands: |c2| >= q3 (degree C), >= q4 (degree B), one index of margin
                 const float q3 = sqrtf(fmaxf(b3 * b3 + k2f - c1sq, 0.f)), q4 = sqrtf(fmaxf(b4 * b4 + k2f - c1sq, 0.f));
                 {
                     const int tot = cb - N0 + 1;
@@ -1027,43 +1152,10 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, i
                 add_row<NH, double>(S, rr, a.a1 + n1, ik2);
             }
             // float tails [n2a, ca-1] and [cb+1, n2b] (the whole row when there is
-            // no core), each by Horner's rule from its first index lo, moved to
-            // the anchor by e^{i(lo - N0) t2}
-            const int tl_hi = (ca <= cb) ? ca - 1 : n2b;
-            const int th_lo = (ca <= cb) ? cb + 1 : n2b + 1;
-            if (n2a <= tl_hi || th_lo <= n2b) {
-                float tf[NH][2];
-#pragma unroll
-                for (int e = 0; e < NH; ++e) tf[e][0] = tf[e][1] = 0.f;
-                if (n2a <= tl_hi) {
-                    float acc[NH][2], ps, pc;
-                    seg_horner_f32<NH>(row, n2a, tl_hi, a2f, c1sq, R2f, zf, cvf, svf, acc);
-                    phase_m(PF, n2a - N0, ps, pc);
-#pragma unroll
-                    for (int e = 0; e < NH; ++e) {
-                        tf[e][0] += pc * acc[e][0] - ps * acc[e][1];
-                        tf[e][1] += pc * acc[e][1] + ps * acc[e][0];
-                    }
-                }
-                if (th_lo <= n2b) {
-                    float acc[NH][2], ps, pc;
-                    seg_horner_f32<NH>(row, th_lo, n2b, a2f, c1sq, R2f, zf, cvf, svf, acc);
-                    phase_m(PF, th_lo - N0, ps, pc);
-#pragma unroll
-                    for (int e = 0; e < NH; ++e) {
-                        tf[e][0] += pc * acc[e][0] - ps * acc[e][1];
-                        tf[e][1] += pc * acc[e][1] + ps * acc[e][0];
-                    }
-                }
-                const float Ax = (float)A.x, Ay = (float)A.y;
-#pragma unroll
-                for (int e = 0; e < NH; ++e) {
-                    const float x = tf[e][0], y = tf[e][1];
-                    tf[e][0] = Ax * x - Ay * y;
-                    tf[e][1] = Ax * y + Ay * x;
-                }
-                add_row<NH, float>(Sf, tf, c1f, ik2f);
-            }
+            // no core)
+            if (TAILS)
+                far_row_tails<NH, NS>(row, n2a, n2b, ca, cb, N0, a2f, c1f, c1sq, zf, cvf, svf, PF, (float)A.x, (float)A.y,
+                                      ik2f, Sf);
         }
         if (!L.valid) return;
 #pragma unroll
@@ -1121,14 +1213,105 @@ __device__ __forceinline__ int far_take(int *counter, int nitems)
     return t < nitems ? t : -1;
 }
 
-template <int NF>
+template <int NF, bool TAILS>
 __global__ void __launch_bounds__(128) far3d_f64(EvalArgs a)
 {
     const int count = a.far_count[0];
     const int nch = (count + 31) >> 5, S = far_slabs(nch, 8);
     int *ctr = a.far_count + GF_WORK_SLOT;
     for (int t = far_take(ctr, nch * S); t >= 0; t = far_take(ctr, nch * S))
-        far3d_f64_chunk<NF>(a, nch - 1 - t / S, count, t % S, S);
+        far3d_f64_chunk<NF, TAILS>(a, nch - 1 - t / S, count, t % S, S);
+}
+
+// ---------------------------------------------------------------------------
+// Float tails of a double-precision plan's far series, as a kernel of their
+// own: the terms of each warp's truncation disk outside its core disk (the
+// same chunks of the sorted far list and the same row split as far3d_f64, from
+// far_warp and far_row), summed in float with the hardware ex2 and added into
+// the double outputs.  Kept apart from the double sums so that the FP64 pipe is
+// fed only by warps with double work, while these warps run on the FP32 and
+// transcendental pipes.  The per-target set-up and the lattice phase are in
+// double; the row phase e^{i c1 t1} = e^{i alpha_1 t1} e^{i n1 t1} in float.
+// ---------------------------------------------------------------------------
+template <int NF>
+__device__ void far3d_tail_chunk(const EvalArgs &a, int w, int count, int slab, int nslab)
+{
+    constexpr int NH = NF == 1 ? 1 : 6;
+    constexpr int NS = NF == 1 ? 1 : 7;
+    const BetaEntry *tab = reinterpret_cast<const BetaEntry *>(a.btab);
+    double2 *out = reinterpret_cast<double2 *>(a.out);
+    const int ne = n_entries(a.which);
+    const int W2 = a.n2hi - a.n2lo + 1;
+    const int lane = threadIdx.x & 31;
+    const float ik2f = (float)(1.0 / (a.k * a.k));
+    const FarLane L = far_lane(a, w * 32 + lane, count);
+    const FarWarp W = far_warp(a, L);
+    const int N0 = W.N0;
+    const float zf = (float)L.z;
+    float svf, cvf;
+    sincosf((float)L.t2, &svf, &cvf);
+    const PhaseF P1 = phase_split(L.t1), P2 = phase_split(L.t2);
+    double sa1, ca1;
+    sincos(a.a1 * L.t1, &sa1, &ca1);
+    const float A0x = (float)ca1, A0y = (float)sa1;  // e^{i alpha_1 t1}
+    double S[NS][2];
+    float Sf[NS][2];
+#pragma unroll
+    for (int e = 0; e < NS; ++e) S[e][0] = S[e][1] = 0.0, Sf[e][0] = Sf[e][1] = 0.f;
+    // the rows split evenly over the slabs
+    const int nr = W.n1b - W.n1a + 1;
+    const int r_lo = W.n1a + (slab * nr) / nslab, r_hi = W.n1a + ((slab + 1) * nr) / nslab - 1;
+    for (int n1 = r_lo; n1 <= r_hi; ++n1) {
+        if (((n1 - r_lo) & 7) == 7) {
+#pragma unroll
+            for (int e = 0; e < NS; ++e) {
+                S[e][0] += (double)Sf[e][0];
+                S[e][1] += (double)Sf[e][1];
+                Sf[e][0] = Sf[e][1] = 0.f;
+            }
+        }
+        float c1f, c1sq;
+        int n2a, n2b, ca, cb;
+        if (!far_row(W, a, n1, c1f, c1sq, n2a, n2b, ca, cb)) continue;
+        const BetaEntry *row = tab + (size_t)(n1 - a.n1lo) * W2 - a.n2lo;
+        float sn, cn;
+        phase_m(P1, n1, sn, cn);
+        far_row_tails<NH, NS>(row, n2a, n2b, ca, cb, N0, W.a2f, c1f, c1sq, zf, cvf, svf, P2, A0x * cn - A0y * sn,
+                              A0x * sn + A0y * cn, ik2f, Sf);
+    }
+    if (!L.valid) return;
+#pragma unroll
+    for (int e = 0; e < NS; ++e) {
+        S[e][0] += (double)Sf[e][0];
+        S[e][1] += (double)Sf[e][1];
+    }
+    // the same lattice phase and factors as far3d_f64_chunk (no propagating terms)
+    double ph2 = a.a1 * L.m1 + a.a2 * L.m2;
+    ph2 -= rint(ph2);
+    double sN, cN;
+    sincos(fma(2.0 * GF_PI, ph2, (a.a2 + N0) * L.t2), &sN, &cN);
+    const double2 pre = make_double2(-sN / (8.0 * GF_PI * GF_PI), cN / (8.0 * GF_PI * GF_PI));
+    double2 *o = out + (size_t)L.idx * ne;
+    if (NF == 1) {
+        add_out(o, cmul(pre, make_double2(S[0][1], -S[0][0])));
+    } else {
+        for (int e = 0; e < 6; ++e) {
+            const double *s = S[1 + e];
+            const double2 v = e < 4 ? make_double2(s[1], -s[0]) : make_double2(L.sg * s[0], L.sg * s[1]);
+            add_out(o + e, cmul(pre, v));
+        }
+        if (a.which == GF_OUT_MAXWELL7) add_out(o + 6, cmul(pre, make_double2(S[0][1], -S[0][0])));
+    }
+}
+
+template <int NF>
+__global__ void __launch_bounds__(128) far3d_tail(EvalArgs a)
+{
+    const int count = a.far_count[0];
+    const int nch = (count + 31) >> 5, S = far_slabs(nch, 8);
+    int *ctr = a.far_count + GF_TAIL_SLOT;
+    for (int t = far_take(ctr, nch * S); t >= 0; t = far_take(ctr, nch * S))
+        far3d_tail_chunk<NF>(a, nch - 1 - t / S, count, t % S, S);
 }
 
 // ---------------------------------------------------------------------------
@@ -1334,7 +1517,7 @@ __global__ void far3d_batch(const EvalArgs *args, int np)
         if (p >= np) return;
         const int u = t - base, nch = nit / S;
         if (sizeof(R) == 8)
-            far3d_f64_chunk<NF>(args[p], nch - 1 - u / S, count, u % S, S);
+            far3d_f64_chunk<NF, true>(args[p], nch - 1 - u / S, count, u % S, S);
         else
             far3d_f32_chunk<NF>(args[p], nch - 1 - u / S, count, u % S, S);
     }
@@ -1417,8 +1600,63 @@ int resident_grid(int nsm)
     return per * nsm;
 }
 
+// Concurrent far kernels of a Helmholtz double-precision plan: the double
+// kernel gives up FAR_F64_DROP of its resident CTAs per SM, and the float-tail
+// kernel (64-thread CTAs) fills the registers left free, so that both run at
+// once on every SM.
+constexpr int FAR_F64_DROP = 1;
+
+struct FarShare {
+    int f64, tail;  // resident CTAs per SM of each kernel
+};
+
+FarShare far_share()
+{
+    FarShare sh{1, 1};
+    int dev = 0, regs_sm = 65536, per = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaFuncAttributes fa, ta;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, far3d_f64<1, false>, 128, 0) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, far3d_f64<1, false>) != cudaSuccess ||
+        cudaFuncGetAttributes(&ta, far3d_tail<1>) != cudaSuccess) {
+        cudaGetLastError();
+        return sh;
+    }
+    // registers are allocated per warp in units of 8 per thread
+    auto cta_regs = [](int regs, int threads) { return (regs + 7) / 8 * 8 * 32 * ((threads + 31) / 32); };
+    sh.f64 = per > FAR_F64_DROP ? per - FAR_F64_DROP : 1;
+    sh.tail = (regs_sm - sh.f64 * cta_regs(fa.numRegs, 128)) / cta_regs(ta.numRegs, 64);
+    if (sh.tail < 1) sh.tail = 1;
+    return sh;
+}
+
+// The double sums and float tails of a double-precision plan's far series.
+// With a fork (Helmholtz only), the tails run on the side stream alongside the
+// double kernel, with the resident CTAs split by far_share; otherwise (and for
+// Maxwell plans, whose double kernel leaves too few registers) after it, at full
+// occupancy.
+template <int NF>
+cudaError_t launch_far_f64(const EvalArgs &a, int nsm, cudaStream_t s, const EvalFork *fork)
+{
+    if (NF != 1) fork = nullptr;
+    if (!fork) {
+        far3d_f64<NF, false><<<resident_grid<far3d_f64<NF, false>>(nsm), 128, 0, s>>>(a);
+        far3d_tail<NF><<<resident_grid<far3d_tail<NF>>(nsm), 128, 0, s>>>(a);
+        return cudaSuccess;
+    }
+    static const FarShare sh = far_share();
+    cudaError_t e;
+    if ((e = cudaEventRecord(fork->fork, s)) != cudaSuccess || (e = cudaStreamWaitEvent(fork->aux, fork->fork, 0)) != cudaSuccess)
+        return e;
+    far3d_f64<NF, false><<<sh.f64 * nsm, 128, 0, s>>>(a);
+    far3d_tail<NF><<<sh.tail * nsm, 64, 0, fork->aux>>>(a);
+    if ((e = cudaEventRecord(fork->join, fork->aux)) != cudaSuccess) return e;
+    return cudaStreamWaitEvent(s, fork->join, 0);
+}
+
 template <typename R>
-cudaError_t launch_eval_t(const EvalArgs &a, cudaStream_t s, cudaEvent_t ev_mid)
+cudaError_t launch_eval_t(const EvalArgs &a, cudaStream_t s, cudaEvent_t ev_mid, const EvalFork *fork)
 {
     int dev = 0, nsm = 152;
     cudaGetDevice(&dev);
@@ -1434,20 +1672,22 @@ cudaError_t launch_eval_t(const EvalArgs &a, cudaStream_t s, cudaEvent_t ev_mid)
         near3d<R, 1><<<(int)blocks, 256, 0, s>>>(a);
         if (ev_mid) cudaEventRecord(ev_mid, s);
         far_scatter<<<nsm * 2, 256, 0, s>>>(a);
-        if (sizeof(R) == 8)
-            far3d_f64<1><<<resident_grid<far3d_f64<1>>(nsm), 128, 0, s>>>(a);
-        else
+        if (sizeof(R) == 8) {
+            cudaError_t e = launch_far_f64<1>(a, nsm, s, fork);
+            if (e != cudaSuccess) return e;
+        } else
             far3d_f32<1><<<resident_grid<far3d_f32<1>>(nsm), 128, 0, s>>>(a);
     } else {
         near3d<R, 7><<<(int)blocks, 256, 0, s>>>(a);
         if (ev_mid) cudaEventRecord(ev_mid, s);
         far_scatter<<<nsm * 2, 256, 0, s>>>(a);
-        if (sizeof(R) == 8)
-            far3d_f64<7><<<resident_grid<far3d_f64<7>>(nsm), 128, 0, s>>>(a);
-        else
+        if (sizeof(R) == 8) {
+            cudaError_t e = launch_far_f64<7>(a, nsm, s, fork);
+            if (e != cudaSuccess) return e;
+        } else
             far3d_f32<7><<<resident_grid<far3d_f32<7>>(nsm), 128, 0, s>>>(a);
     }
-    gf_count_launch(a.dim == 2 ? 2 : 3);
+    gf_count_launch(a.dim == 2 ? 2 : sizeof(R) == 8 ? 4 : 3);
     return cudaGetLastError();
 }
 
@@ -1486,7 +1726,7 @@ cudaError_t gf_launch_series_tables(const EvalArgs &a, int precision, double2 *e
     return cudaGetLastError();
 }
 
-cudaError_t gf_launch_eval(const EvalArgs &a, int precision, cudaStream_t s, cudaEvent_t ev_mid)
+cudaError_t gf_launch_eval(const EvalArgs &a, int precision, cudaStream_t s, cudaEvent_t ev_mid, const EvalFork *fork)
 {
-    return precision == GF_FP64 ? launch_eval_t<double>(a, s, ev_mid) : launch_eval_t<float>(a, s, ev_mid);
+    return precision == GF_FP64 ? launch_eval_t<double>(a, s, ev_mid, fork) : launch_eval_t<float>(a, s, ev_mid, fork);
 }

@@ -157,18 +157,26 @@ struct EvalArgs {
     int n1lo, n1hi, n2lo, n2hi;
     const PropEntry *prop;  // propagating indices (|alpha_n| <= k)
     const int *nprop;       // their number (device)
-    const double2 *exptab;  // (e^{-(j - exptab_j0)/128}, (j - exptab_j0)/128), j = 0 .. exptab_n - 1
+    const double2 *exptab;  // (e^{-y_j}, y_j), y_j = (j - exptab_j0)/GF_EXPTAB_STEPS, j = 0 .. exptab_n - 1
     int exptab_n, exptab_j0;
     double bmin;            // smallest |beta_n| over the evanescent n (this value or a larger one, never smaller)
 };
+
+// Entries per unit of y of the far kernel's exponential table e^{-y_j}
+// (a power of two from 128 to 2048).
+#ifndef GF_EXPTAB_STEPS
+#define GF_EXPTAB_STEPS 2048
+#endif
 
 // Far targets are bucketed by b = floor(NB c / |x_last|) (clamped to NB-1) so
 // that the lanes of a warp share nearly the same series truncation radius.
 #define GF_FAR_BUCKETS 64
 // scratch counters: [0] far count, [1..NB] bucket sizes, [NB+1..2NB] cursors,
-// [GF_WORK_SLOT] far chunks handed out so far
+// [GF_WORK_SLOT] far work items handed out so far, [GF_TAIL_SLOT] the same for
+// the float-tail kernel of double-precision plans
 #define GF_WORK_SLOT (1 + 2 * GF_FAR_BUCKETS)
-#define GF_SCRATCH_COUNTERS (2 + 2 * GF_FAR_BUCKETS)
+#define GF_TAIL_SLOT (2 + 2 * GF_FAR_BUCKETS)
+#define GF_SCRATCH_COUNTERS (3 + 2 * GF_FAR_BUCKETS)
 
 // A sweep of plans run as batched persistent launches: per-pass virtual-block
 // prefix sums over the pairs (device arrays of np + 1 ints), the per-pair
@@ -206,7 +214,18 @@ cudaError_t gf_dev_alloc(void **ptr, size_t bytes, cudaStream_t s);
 void gf_dev_free(void *ptr, cudaStream_t s);
 cudaError_t gf_stage_upload(void *dev_dst, const void *src, size_t bytes, cudaStream_t s);
 cudaError_t gf_trim_pool();
-cudaError_t gf_launch_eval(const EvalArgs &a, int precision, cudaStream_t s, cudaEvent_t ev_mid);
+// A side stream and two events: the double-precision far kernel and the
+// float-tail kernel run concurrently, the tails on `aux` between `fork` (recorded
+// on the caller's stream) and `join` (waited for by the caller's stream).
+struct EvalFork {
+    cudaStream_t aux;
+    cudaEvent_t fork, join;
+};
+// fork == nullptr: every kernel on stream s, in order
+cudaError_t gf_launch_eval(const EvalArgs &a, int precision, cudaStream_t s, cudaEvent_t ev_mid,
+                           const EvalFork *fork = nullptr);
+// per-device side stream of the library (non-blocking, lives until the process exits)
+cudaStream_t gf_aux_stream();
 
 void gf_count_launch(int n);
 gf_status gf_plan_eval_args(gf_plan_t p, const double *dev_xyz, int64_t n, int which, void *dev_out, EvalArgs *a);

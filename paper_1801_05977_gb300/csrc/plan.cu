@@ -119,7 +119,7 @@ struct gf_plan_s {
     PropEntry *prop = nullptr;        // propagating indices, then their count
     int *nprop_dev = nullptr;
     cudaStream_t stream = nullptr;    // stream of the plan's creation
-    double2 *exptab = nullptr;        // (e^{-(j - exptab_j0)/128}, (j - exptab_j0)/128)
+    double2 *exptab = nullptr;        // (e^{-y_j}, y_j), y_j = (j - exptab_j0)/GF_EXPTAB_STEPS
     int exptab_n = 0, exptab_j0 = 0;
     double bmin_ev = 1e300;           // smallest evanescent |beta_n|
     int n1lo = 0, n1hi = -1, n2lo = 0, n2hi = -1;
@@ -135,6 +135,8 @@ struct gf_plan_s {
     bool timing = false;
     cudaEvent_t ev[6] = {};
     bool ev_plan = false, ev_eval = false;
+    // fork/join events of the concurrent far kernels (3D double-precision plans)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 void gf_count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
@@ -459,12 +461,13 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
             const int pbox[4] = {(int)floor(-a1 - k) - 1, (int)ceil(-a1 + k) + 1, (int)floor(-a2 - k) - 1,
                                  (int)ceil(-a2 + k) + 1};
             const size_t nprop_max = (size_t)(pbox[1] - pbox[0] + 1) * (pbox[3] - pbox[2] + 1);
-            // T[j] = e^{-(j - j0)/128}: the core weights e^{-y}, y = b|x3| + ln b,
-            // of a lane's truncation set (b|x3| <= T) have ln(bmin) <= y <= T + ln(bmax),
-            // bmax <= sqrt(2) (Rc + 2) over the index box
-            p->exptab_j0 = 128 * ((int)ceil(-log(fmin(bmin_ev, 1.0))) + 1);
-            if (p->exptab_j0 < 128) p->exptab_j0 = 128;
-            p->exptab_n = p->exptab_j0 + 128 * ((int)ceil(p->T + log(1.4143 * (Rc + 2.0))) + 2) + 1;
+            // T[j] = e^{-(j - j0)/S}, S = GF_EXPTAB_STEPS: the core weights e^{-y},
+            // y = b|x3| + ln b, of a lane's truncation set (b|x3| <= T) have
+            // ln(bmin) <= y <= T + ln(bmax), bmax <= sqrt(2) (Rc + 2) over the index box
+            constexpr int S = GF_EXPTAB_STEPS;
+            p->exptab_j0 = S * ((int)ceil(-log(fmin(bmin_ev, 1.0))) + 1);
+            if (p->exptab_j0 < S) p->exptab_j0 = S;
+            p->exptab_n = p->exptab_j0 + S * ((int)ceil(p->T + log(1.4143 * (Rc + 2.0))) + 2) + 1;
             const bool want_exp = p->precision == GF_FP64;
             if ((e = gf_dev_alloc(&p->btab, ne * eb, st)) != cudaSuccess ||
                 (e = gf_dev_alloc((void **)&p->prop, sizeof(PropEntry) * nprop_max + 16, st)) != cudaSuccess ||
@@ -616,8 +619,22 @@ gf_status gf_eval_points(gf_plan_t p, const double *dev_xyz, int64_t n, int whic
     a.exptab_n = p->exptab_n;
     a.exptab_j0 = p->exptab_j0;
     a.bmin = p->bmin_ev;
+    // 3D double-precision plans run the far series' double sums and float tails
+    // as two concurrent kernels (the tails on the library's side stream)
+    EvalFork fk{};
+    const EvalFork *fork = nullptr;
+    if (p->dim == 3 && p->precision == GF_FP64) {
+        if (!p->ev_fork) {
+            CU(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+            CU(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
+        }
+        fk.aux = gf_aux_stream();
+        fk.fork = p->ev_fork;
+        fk.join = p->ev_join;
+        if (fk.aux) fork = &fk;
+    }
     if (p->timing) cudaEventRecord(p->ev[3], st);
-    CU(gf_launch_eval(a, p->precision, st, p->timing ? p->ev[4] : nullptr));
+    CU(gf_launch_eval(a, p->precision, st, p->timing ? p->ev[4] : nullptr, fork));
     if (p->timing) {
         cudaEventRecord(p->ev[5], st);
         p->ev_eval = true;
@@ -793,6 +810,8 @@ gf_status gf_destroy(gf_plan_t p)
     for (void *b : bufs) gf_dev_free(b, 0);
     for (int i = 0; i < 6; ++i)
         if (p->ev[i]) cudaEventDestroy(p->ev[i]);
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    if (p->ev_join) cudaEventDestroy(p->ev_join);
     delete p;
     return GF_OK;
 }

@@ -97,6 +97,24 @@ cudaError_t gf_stage_upload(void *dev_dst, const void *src, size_t bytes, cudaSt
     return cudaSuccess;
 }
 
+cudaStream_t gf_aux_stream()
+{
+    static std::mutex mu;
+    static std::map<int, cudaStream_t> streams;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = streams.find(dev);
+    if (it != streams.end()) return it->second;
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    streams[dev] = s;
+    return s;
+}
+
 cudaError_t gf_trim_pool()
 {
     cudaMemPool_t pool = pool_for_current_device();
