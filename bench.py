@@ -38,12 +38,12 @@ WORKLOAD = "3D doubly quasi-periodic G_d, k=2.5, alpha=(0.1,0.3), grid 128x128x6
 # Algorithmic FP64 work of one double-precision core series term, by the degree
 # of its exponential polynomial: y = b|x3| + ln b (1 FMA), r = y - y_j (1 add),
 # e^{-r} (DEG FMAs), one Reinsch step (2 FMAs + 1 add); an FMA counts 2 flops.
-# The far core is b|x3| <= Y0; the exponential (table step 1/2048) has degree 4,
-# then 3 from b >= bmin + 3.5/|x3| and 2 from b >= bmin + 13.25/|x3|.
-FP64_TERM_FLOPS = {4: 16, 3: 14, 2: 12}
+# The far core is b|x3| <= Y0; the exponential (table step 1/4096) has degree 3,
+# then 2 from b >= bmin + 10.75/|x3| and 1 from b >= bmin + 20.75/|x3|.
+FP64_TERM_FLOPS = {3: 14, 2: 12, 1: 10}
 FAR_CORE_Y0 = 18.0
-FAR_BAND_DEGS = (4, 3, 2)
-FAR_BAND_GAPS = (3.5, 13.25)
+FAR_BAND_DEGS = (3, 2, 1)
+FAR_BAND_GAPS = (10.75, 20.75)
 # DRAM bytes of one far3d_f64 launch on this workload: ncu (dram__bytes_read.sum
 # + dram__bytes_write.sum) of a 2e5-target launch, scaled by the far targets
 FAR_TRAFFIC_BYTES = 8.352768e6 * 5
@@ -360,8 +360,8 @@ def run_gpu(args):
                      "traffic": FAR_TRAFFIC_BYTES if n_targets == 1_000_000 else None,
                      "algorithmic_flops": far_flops, "core_terms_by_degree": bands,
                      "note": "FP64 pipe bound (ncu: 86% of peak while active); achieved = algorithmic FP64 flops "
-                             "of the double-precision core terms (b|x3| <= 18; 16/14/12 flops per term for "
-                             "exponential degree 4/3/2, FMA = 2 flops) / far-kernel time; the float tail is not "
+                             "of the double-precision core terms (b|x3| <= 18; 14/12/10 flops per term for "
+                             "exponential degree 3/2/1, FMA = 2 flops) / far-kernel time; the float tail is not "
                              "counted; peak from unit counts and clock (152 SMs x 2 FP64 FMA/clk x 2 flop x "
                              "2.07 GHz; FMA probe 1.21 TFLOP/s)"},
         "e2e": {"value": whole_job_rate(n_targets, world, e2e_s), "unit": "evals/s",

@@ -429,11 +429,29 @@ __global__ void __launch_bounds__(256) near2d(EvalArgs a)
 // ---------------------------------------------------------------------------
 __device__ void far_scatter_body(const EvalArgs &a, int blk, int nblk, int *off)
 {
-    if (threadIdx.x == 0) {
-        int s = 0;
-        for (int b = GF_FAR_BUCKETS - 1; b >= 0; --b) {
-            off[b] = s;
-            s += a.far_count[1 + b];
+    // exclusive prefix of the bucket sizes in descending bucket order, by one
+    // warp: lane l takes the descending positions l PER .. l PER + PER - 1
+    static_assert(GF_FAR_BUCKETS % 32 == 0, "bucket count: a multiple of 32");
+    if (threadIdx.x < 32) {
+        constexpr int PER = GF_FAR_BUCKETS / 32;
+        const int lane = threadIdx.x;
+        int c[PER], tot = 0;
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            c[i] = a.far_count[1 + (GF_FAR_BUCKETS - 1 - (lane * PER + i))];
+            tot += c[i];
+        }
+        int incl = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        int s = incl - tot;
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            off[GF_FAR_BUCKETS - 1 - (lane * PER + i)] = s;
+            s += c[i];
         }
     }
     __syncthreads();
@@ -550,28 +568,32 @@ __device__ __forceinline__ double warp_max(double v)
 }
 
 // e^{-y} by Tang's table-driven method (ACM TOMS 15, 1989): y = y_j + r with
-// y_j = (j - j0)/S, S = GF_EXPTAB_STEPS, |r| <= (1/2 + 2e-2)/S; e^{-y} = T[j] e^{-r},
+// y_j = (j - j0)/S, S = GF_EXPTAB_STEPS, |r| <= (1/2 + 4e-2)/S; e^{-y} = T[j] e^{-r},
 // the plan table holding (e^{-y_j}, y_j).  The index is rint(S yf) + j0 for a
 // float evaluation yf of y (|yf - y| < 6e-8 (2 b|x3| + 2 |ln b| + |y|), so that
-// |S (yf - y)| < 2e-2 for the core terms, b|x3| < 20, and S <= 2048; rounding
+// |S (yf - y)| < 4e-2 for the core terms, b|x3| < 20, and S <= 4096; rounding
 // by the 1.5 * 2^23 shift), clamped to the table (callers discard the
 // terms whose y lies beyond it).  Returns e^{-r} by its Taylor polynomial of
 // degree DEG and T[j].x.  The truncation relative to e^{-y} is at most
 // |r|^{DEG+1}/(DEG+1)! e^{|r|}; the far kernel takes three degrees (EXP_DEG_A >
 // B > C), switching where a term lies e^{EXP_GAP_B} and e^{EXP_GAP_C} below the
 // largest term of its series, so that every term's truncation stays below
-// 1e-17 of that largest term (bounds at |r| = 0.51/S, 0.52/S for S = 2048):
+// about 1e-17 of that largest term (bounds at |r| = 0.51/S, 0.52/S for S = 2048,
+// 0.54/S for S = 4096):
 //   S = 128: degrees 5/4/3 (5.6e-18, 8.4e-15, 1.1e-11), gaps 7 and 14;
 //   S = 256: degrees 5/4/3 (8.7e-20, 2.6e-16, 6.6e-13), gaps 4 and 12;
 //   S = 512: degrees 4/3/2 (8.2e-18, 4.1e-14, 1.7e-10), gaps 9 and 17.5;
 //   S = 1024: degrees 4/3/2 (2.6e-19, 2.6e-15, 2.1e-11), gaps 6.25 and 15.25;
-//   S = 2048: degrees 4/3/2 (8.8e-21, 1.7e-16, 2.7e-12), gaps 3.5 and 13.25.
-constexpr int EXP_DEG_A = GF_EXPTAB_STEPS >= 512 ? 4 : 5;
+//   S = 2048: degrees 4/3/2 (8.8e-21, 1.7e-16, 2.7e-12), gaps 3.5 and 13.25;
+//   S = 4096: degrees 3/2/1 (1.3e-17, 3.8e-13, 8.7e-9), gaps 10.75 and 20.75.
+constexpr int EXP_DEG_A = GF_EXPTAB_STEPS >= 4096 ? 3 : GF_EXPTAB_STEPS >= 512 ? 4 : 5;
 constexpr int EXP_DEG_B = EXP_DEG_A - 1, EXP_DEG_C = EXP_DEG_A - 2;
-constexpr double EXP_GAP_B = GF_EXPTAB_STEPS >= 2048 ? 3.5 : GF_EXPTAB_STEPS >= 1024 ? 6.25
-                           : GF_EXPTAB_STEPS >= 512  ? 9.0 : GF_EXPTAB_STEPS >= 256  ? 4.0 : 7.0;
-constexpr double EXP_GAP_C = GF_EXPTAB_STEPS >= 2048 ? 13.25 : GF_EXPTAB_STEPS >= 1024 ? 15.25
-                           : GF_EXPTAB_STEPS >= 512  ? 17.5 : GF_EXPTAB_STEPS >= 256  ? 12.0 : 14.0;
+constexpr double EXP_GAP_B = GF_EXPTAB_STEPS >= 4096 ? 10.75 : GF_EXPTAB_STEPS >= 2048 ? 3.5
+                           : GF_EXPTAB_STEPS >= 1024 ? 6.25 : GF_EXPTAB_STEPS >= 512 ? 9.0
+                           : GF_EXPTAB_STEPS >= 256  ? 4.0 : 7.0;
+constexpr double EXP_GAP_C = GF_EXPTAB_STEPS >= 4096 ? 20.75 : GF_EXPTAB_STEPS >= 2048 ? 13.25
+                           : GF_EXPTAB_STEPS >= 1024 ? 15.25 : GF_EXPTAB_STEPS >= 512 ? 17.5
+                           : GF_EXPTAB_STEPS >= 256  ? 12.0 : 14.0;
 
 // (-1)^i / i!
 __host__ __device__ constexpr double exp_taylor_coef(int i) { return i == 0 ? 1.0 : -exp_taylor_coef(i - 1) / i; }
@@ -585,6 +607,7 @@ __device__ __forceinline__ double exp_neg_split(double y, float yf, const double
     const double2 t = __ldg(T + idx);
     const double r = y - t.y;
     Tj = t.x;
+    if (DEG <= 1) return 1.0 - r;
     constexpr double c5 = exp_taylor_coef(5), c4 = exp_taylor_coef(4), c3 = exp_taylor_coef(3),
                      c2 = exp_taylor_coef(2);
     double p;

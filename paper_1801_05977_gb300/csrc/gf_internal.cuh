@@ -163,14 +163,14 @@ struct EvalArgs {
 };
 
 // Entries per unit of y of the far kernel's exponential table e^{-y_j}
-// (a power of two from 128 to 2048).
+// (a power of two from 128 to 4096).
 #ifndef GF_EXPTAB_STEPS
-#define GF_EXPTAB_STEPS 2048
+#define GF_EXPTAB_STEPS 4096
 #endif
 
 // Far targets are bucketed by b = floor(NB c / |x_last|) (clamped to NB-1) so
 // that the lanes of a warp share nearly the same series truncation radius.
-#define GF_FAR_BUCKETS 64
+#define GF_FAR_BUCKETS 256
 // scratch counters: [0] far count, [1..NB] bucket sizes, [NB+1..2NB] cursors,
 // [GF_WORK_SLOT] far work items handed out so far, [GF_TAIL_SLOT] the same for
 // the float-tail kernel of double-precision plans

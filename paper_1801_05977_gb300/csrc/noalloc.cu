@@ -13,9 +13,9 @@
 
 namespace {
 
-// counters first (padded to 256 ints), then the far list in append order and
+// counters first (padded to 1024 ints), then the far list in append order and
 // the bucket-sorted far list, each GF_NOALLOC_MAX_TARGETS long
-constexpr int kCounterSlots = 256;
+constexpr int kCounterSlots = 1024;
 static_assert(GF_SCRATCH_COUNTERS <= kCounterSlots, "counter block too small");
 constexpr size_t kScratchInts = kCounterSlots + 2 * (size_t)GF_NOALLOC_MAX_TARGETS;
 
