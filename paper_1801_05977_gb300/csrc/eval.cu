@@ -496,10 +496,13 @@ __device__ __forceinline__ void set_entry(BetaEntry &e, double b, double ib)
 {
     e.b = b;
     e.lnb = b > 0.0 ? log(b) : 0.0;
+    e.bf = (float)b;
+    e.blo = (float)(b - (double)e.bf);
+    e.lnbf = (float)e.lnb;
+    e.lnblo = (float)(e.lnb - (double)e.lnbf);
     e.bl2 = b > 0.0 ? (float)(b * 1.4426950408889634) : CUDART_INF_F;  // b log2(e)
     e.ibf = (float)ib;
-    e.bf = (float)b;
-    e.lnbf = (float)e.lnb;
+    e.pad0 = e.pad1 = 0.f;
 }
 __device__ __forceinline__ void set_entry(BetaEntryF &e, double b, double ib)
 {
@@ -535,7 +538,11 @@ __global__ void series_tables(EvalArgs a, E *tab, double2 *exptab, PropEntry *pr
         for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.exptab_n; j += gridDim.x * blockDim.x)
         {
             const double off = (double)(j - a.exptab_j0) * (1.0 / GF_EXPTAB_STEPS);
-            exptab[j] = make_double2(exp(-off), off);
+            const double ev = exp(-off);
+            exptab[j] = make_double2(ev, off);
+            // the float-float copy after it: (hi, lo) of e^{-y_j} and y_j (exact in float)
+            const float hi = (float)ev;
+            reinterpret_cast<float4 *>(exptab + a.exptab_n)[j] = make_float4(hi, (float)(ev - (double)hi), (float)off, 0.f);
         }
     if (blockIdx.x == 0 && threadIdx.x < 32) {
         const int pw = pbox.w - pbox.z + 1, ptot = (pbox.y - pbox.x + 1) * pw;
@@ -703,6 +710,94 @@ struct RState {
     double d[NH], b[NH];
 };
 
+// ---------------------------------------------------------------------------
+// Float-float arithmetic: a value is an unevaluated sum h + l of two floats
+// (about 48 significant bits).  Error-free sum by Knuth's TwoSum, product by
+// an fma (Dekker, Numer. Math. 18, 1971).  Every operation is explicitly
+// rounded, so no contraction can break the error-free steps.
+// ---------------------------------------------------------------------------
+struct FF {
+    float h, l;
+};
+
+__device__ __forceinline__ FF two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float v = __fsub_rn(s, a);
+    return FF{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, v)), __fsub_rn(b, v))};
+}
+
+// a double as a float pair
+__device__ __forceinline__ FF ff_split(double x)
+{
+    const float h = (float)x;
+    return FF{h, (float)(x - (double)h)};
+}
+
+// Float-float Reinsch state of one sum (Helmholtz far series).
+struct RStateFF {
+    float dh, dl, bh, bl;
+};
+
+// The terms of the float-float band: n2, n2 + dir, ... (count of them), each
+// at least e^{-FF_GAP} below the largest term of the series.  Float-float
+// rounding perturbs y by about 1.3e-14 max(|y|, 1) (emulated over random b,
+// |x3|), so a term at y = y_max + 8 is off by about 1.4e-13 e^{-8} < 5e-17 of
+// the largest term: below half a double rounding of that term.  Per term: y = b z + ln b and e^{-y} =
+// T[j] e^{-r} (the float-float table of the same step, r = y - y_j, |r| <=
+// 0.54/S, e^{-r} to r^3 with r^2/2 - r^3/6 in float), then one Reinsch step:
+// d' = w + lambda b + s d, b' = d' + s b.
+constexpr float FF_GAP = 8.0f;
+
+__device__ __forceinline__ void reinsch_seg_ff(RStateFF &st, const BetaEntry *__restrict__ row, int &n2, int count,
+                                               int dir, float &c2f, float c1sq, float R2f, FF z, FF lam, float sf,
+                                               const float4 *__restrict__ T, int j0, int jmax)
+{
+    const float df = (float)dir;
+#pragma unroll 2
+    for (int i = 0; i < count; ++i, n2 += dir, c2f += df) {
+        const float4 q = *reinterpret_cast<const float4 *>(&row[n2].bf);  // b hi, lo; ln b hi, lo
+        const bool ok = fmaf(c2f, c2f, c1sq) <= R2f && q.x != 0.f;
+        // y = b z + ln b
+        const float p = __fmul_rn(q.x, z.h);
+        float pe = __fmaf_rn(q.x, z.h, -p);
+        pe = __fmaf_rn(q.x, z.l, __fmaf_rn(q.y, z.h, pe));
+        const FF y0 = two_sum(p, q.z);
+        const FF y = two_sum(y0.h, __fadd_rn(__fadd_rn(y0.l, pe), q.w));
+        // table entry nearest to y
+        const float jm = __fmaf_rn((float)GF_EXPTAB_STEPS, y.h, 12582912.0f);
+        const int idx = min(max(__float_as_int(jm) - 0x4B400000 + j0, 0), jmax);
+        const float4 t = __ldg(T + idx);
+        // r = (y.h - y_j) + y.l (the first difference is exact)
+        const float rh = __fsub_rn(y.h, t.z);
+        const float rs = __fadd_rn(rh, y.l);
+        const float qq = __fmul_rn(__fmul_rn(rs, rs), __fmaf_rn(rs, -1.0f / 6.0f, 0.5f));
+        // e^{-r} = (1 - rh) - y.l + qq, then w = T[j] e^{-r}
+        const FF a = two_sum(1.0f, -rh);
+        const float al = __fadd_rn(__fsub_rn(a.l, y.l), qq);
+        float wh = __fmul_rn(t.x, a.h);
+        float wl = __fmaf_rn(t.x, a.h, -wh);
+        wl = __fmaf_rn(t.x, al, __fmaf_rn(t.y, a.h, wl));
+        wh = ok ? wh : 0.f;
+        wl = ok ? wl : 0.f;
+        // d' = (lambda b + w) + s d
+        const float m = __fmul_rn(lam.h, st.bh);
+        float me = __fmaf_rn(lam.h, st.bh, -m);
+        me = __fmaf_rn(lam.h, st.bl, __fmaf_rn(lam.l, st.bh, me));
+        const FF u = two_sum(m, wh);
+        const FF v = two_sum(u.h, __fmul_rn(sf, st.dh));
+        const float lo = __fadd_rn(__fadd_rn(__fadd_rn(u.l, v.l), __fadd_rn(me, wl)), __fmul_rn(sf, st.dl));
+        const FF dn = two_sum(v.h, lo);
+        // b' = d' + s b
+        const FF x = two_sum(dn.h, __fmul_rn(sf, st.bh));
+        const FF bn = two_sum(x.h, __fadd_rn(__fadd_rn(x.l, dn.l), __fmul_rn(sf, st.bl)));
+        st.dh = dn.h;
+        st.dl = dn.l;
+        st.bh = bn.h;
+        st.bl = bn.l;
+    }
+}
+
 // Feed `count` terms n2, n2 + dir, ... into the state (the first has the
 // highest recurrence index), advancing n2 and c2; weights on the lane's own
 // truncation set, exponential of degree DEG.  Per term and sum the recurrence
@@ -760,6 +855,28 @@ __device__ __forceinline__ void reinsch_run(RState<NH> &st, const BetaEntry *__r
     reinsch_seg<NH, EXP_DEG_C>(st, row, n2, nc, dir, c2f, c2, c1sq, R2f, z, RS, T, j0, jmax);
     reinsch_seg<NH, EXP_DEG_B>(st, row, n2, nb, dir, c2f, c2, c1sq, R2f, z, RS, T, j0, jmax);
     reinsch_seg<NH, EXP_DEG_A>(st, row, n2, na, dir, c2f, c2, c1sq, R2f, z, RS, T, j0, jmax);
+}
+
+// Helmholtz rows: the first nff terms (the outer ones, all in the float-float
+// band) in float-float, the state then carried over to double for the
+// remaining nd terms (all within e^{-FF_GAP} of the largest term, where the
+// degree-EXP_DEG_A exponential is exact to double precision).
+__device__ __forceinline__ void reinsch_run_ff(RState<1> &st, const BetaEntry *__restrict__ row, int start, int dir,
+                                               int nff, int nd, float c1sq, float a2f, float R2f, double z, FF zff,
+                                               const Reinsch &RS, FF lamff, float sf, const double2 *__restrict__ T,
+                                               int j0, int jmax)
+{
+    int n2 = start;
+    float c2f = a2f + (float)start;
+    double c2 = 0.0;  // not used by single sums
+    if (nff > 0) {
+        RStateFF f{0.f, 0.f, 0.f, 0.f};
+        reinsch_seg_ff(f, row, n2, nff, dir, c2f, c1sq, R2f, zff, lamff, sf,
+                       reinterpret_cast<const float4 *>(T + (jmax + 1)), j0, jmax);
+        st.d[0] = (double)f.dh + (double)f.dl;
+        st.b[0] = (double)f.bh + (double)f.bl;
+    }
+    reinsch_seg<1, EXP_DEG_A>(st, row, n2, nd, dir, c2f, c2, c1sq, R2f, z, RS, T, j0, jmax);
 }
 
 // One recurrence step with zero weight (recurrence index 0 of a sum whose
@@ -1058,6 +1175,10 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, i
         // decreases in b): degree B from b >= bmin + EXP_GAP_B/z_min, C from
         // bmin + EXP_GAP_C/z_min
         const float b4 = (float)(a.bmin + EXP_GAP_B * izmax), b3 = (float)(a.bmin + EXP_GAP_C * izmax);
+        // Helmholtz: the float-float band from b >= bmin + FF_GAP/z_min
+        const float bff = (float)(a.bmin + (double)FF_GAP * izmax);
+        const FF zff = ff_split(L.z), lamff = ff_split(RS.lam);
+        const float sgn = RS.m ? -1.0f : 1.0f;
         const float k2f = (float)k2;
         const float svf = (float)sv, cvf = (float)cv, zf = (float)L.z;
         double P[NF][2];
@@ -1136,9 +1257,16 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, i
                 RState<NH> R, Lt;
 #pragma unroll
                 for (int e = 0; e < NH; ++e) R.d[e] = R.b[e] = Lt.d[e] = Lt.b[e] = 0.0;
-                // degree bands: |c2| >= q3 (degree C), >= q4 (degree B), one index of margin
+                // degree bands (Maxwell): |c2| >= q3 (degree C), >= q4 (degree B);
+                // Helmholtz: |c2| >= qff (float-float); one index of margin
                 const float q3 = sqrtf(fmaxf(b3 * b3 + k2f - c1sq, 0.f)), q4 = sqrtf(fmaxf(b4 * b4 + k2f - c1sq, 0.f));
-                {
+                const float qff = sqrtf(fmaxf(bff * bff + k2f - c1sq, 0.f));
+                if (NH == 1) {
+                    const int tot = cb - N0 + 1;
+                    const int mff = max(0, cb - max((int)ceilf(qff - a2f) + 1, N0) + 1);
+                    reinsch_run_ff(*reinterpret_cast<RState<1> *>(&R), row, cb, -1, mff, tot - mff, c1sq, a2f, R2f, L.z,
+                                   zff, RS, lamff, sgn, T, j0, jmax);
+                } else {
                     const int tot = cb - N0 + 1;
                     const int r3 = (int)ceilf(q3 - a2f) + 1, r4 = (int)ceilf(q4 - a2f) + 1;
                     const int m3 = max(0, cb - max(r3, N0) + 1);
@@ -1154,10 +1282,16 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, i
                 }
                 if (ca < N0) {
                     const int tot = N0 - ca;
-                    const int l3 = (int)floorf(-q3 - a2f) - 1, l4 = (int)floorf(-q4 - a2f) - 1;
-                    const int m3 = max(0, min(l3, N0 - 1) - ca + 1);
-                    const int m4 = max(0, min(l4, N0 - 1) - (ca + m3) + 1);
-                    reinsch_run<NH>(Lt, row, ca, 1, m3, m4, tot - m3 - m4, a.a2, c1sq, a2f, R2f, L.z, RS, T, j0, jmax);
+                    if (NH == 1) {
+                        const int mff = max(0, min((int)floorf(-qff - a2f) - 1, N0 - 1) - ca + 1);
+                        reinsch_run_ff(*reinterpret_cast<RState<1> *>(&Lt), row, ca, 1, mff, tot - mff, c1sq, a2f, R2f,
+                                       L.z, zff, RS, lamff, sgn, T, j0, jmax);
+                    } else {
+                        const int l3 = (int)floorf(-q3 - a2f) - 1, l4 = (int)floorf(-q4 - a2f) - 1;
+                        const int m3 = max(0, min(l3, N0 - 1) - ca + 1);
+                        const int m4 = max(0, min(l4, N0 - 1) - (ca + m3) + 1);
+                        reinsch_run<NH>(Lt, row, ca, 1, m3, m4, tot - m3 - m4, a.a2, c1sq, a2f, R2f, L.z, RS, T, j0, jmax);
+                    }
                     reinsch_zero<NH>(Lt, RS);
 #pragma unroll
                     for (int e = 0; e < NH; ++e) {

@@ -123,9 +123,10 @@ struct SynthArgs {
 // Far-series table entry for one in-plane index n: b = |beta_n|, ln b and 1/b
 // for evanescent n (beta_n = i b); zeros for propagating n (|alpha_n| <= k).
 // The double-precision core sums the weights e^{-b|x3|}/b = e^{-(b|x3| + ln b)}.
-struct BetaEntry {
-    double b, lnb;             // double-precision core terms
-    float bl2, ibf, bf, lnbf;  // b log2(e), 1/b, b for the float tail; ln b for the table index
+struct __align__(16) BetaEntry {
+    double b, lnb;                // double-precision core terms
+    float bf, blo, lnbf, lnblo;   // b and ln b as float pairs (hi + lo): the float-float band; hi parts index the table
+    float bl2, ibf, pad0, pad1;   // b log2(e), 1/b for the float tail
 };
 struct BetaEntryF {
     float bl2, ib, b, pad;  // b log2(e), 1/b, b
@@ -157,7 +158,8 @@ struct EvalArgs {
     int n1lo, n1hi, n2lo, n2hi;
     const PropEntry *prop;  // propagating indices (|alpha_n| <= k)
     const int *nprop;       // their number (device)
-    const double2 *exptab;  // (e^{-y_j}, y_j), y_j = (j - exptab_j0)/GF_EXPTAB_STEPS, j = 0 .. exptab_n - 1
+    const double2 *exptab;  // (e^{-y_j}, y_j), y_j = (j - exptab_j0)/GF_EXPTAB_STEPS, j = 0 .. exptab_n - 1,
+                            // followed by exptab_n float4 (hi, lo of e^{-y_j}, y_j, 0)
     int exptab_n, exptab_j0;
     double bmin;            // smallest |beta_n| over the evanescent n (this value or a larger one, never smaller)
 };

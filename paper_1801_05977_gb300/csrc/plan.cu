@@ -119,7 +119,7 @@ struct gf_plan_s {
     PropEntry *prop = nullptr;        // propagating indices, then their count
     int *nprop_dev = nullptr;
     cudaStream_t stream = nullptr;    // stream of the plan's creation
-    double2 *exptab = nullptr;        // (e^{-y_j}, y_j), y_j = (j - exptab_j0)/GF_EXPTAB_STEPS
+    double2 *exptab = nullptr;        // (e^{-y_j}, y_j), y_j = (j - exptab_j0)/GF_EXPTAB_STEPS, then a float4 copy
     int exptab_n = 0, exptab_j0 = 0;
     double bmin_ev = 1e300;           // smallest evanescent |beta_n|
     int n1lo = 0, n1hi = -1, n2lo = 0, n2hi = -1;
@@ -471,7 +471,7 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
             const bool want_exp = p->precision == GF_FP64;
             if ((e = gf_dev_alloc(&p->btab, ne * eb, st)) != cudaSuccess ||
                 (e = gf_dev_alloc((void **)&p->prop, sizeof(PropEntry) * nprop_max + 16, st)) != cudaSuccess ||
-                (want_exp && (e = gf_dev_alloc((void **)&p->exptab, sizeof(double2) * p->exptab_n, st)) != cudaSuccess)) {
+                (want_exp && (e = gf_dev_alloc((void **)&p->exptab, 2 * sizeof(double2) * p->exptab_n, st)) != cudaSuccess)) {
                 st_err = fail(GF_ERR_NOMEM, "gf_plan: device allocation (series tables): %s", cudaGetErrorString(e));
                 break;
             }
