@@ -500,9 +500,6 @@ __device__ __forceinline__ void set_entry(BetaEntry &e, double b, double ib)
     e.blo = (float)(b - (double)e.bf);
     e.lnbf = (float)e.lnb;
     e.lnblo = (float)(e.lnb - (double)e.lnbf);
-    e.bl2 = b > 0.0 ? (float)(b * 1.4426950408889634) : CUDART_INF_F;  // b log2(e)
-    e.ibf = (float)ib;
-    e.pad0 = e.pad1 = 0.f;
 }
 __device__ __forceinline__ void set_entry(BetaEntryF &e, double b, double ib)
 {
@@ -533,6 +530,11 @@ __global__ void series_tables(EvalArgs a, E *tab, double2 *exptab, PropEntry *pr
             set_entry(e, b, 1.0 / b);
         }
         tab[i] = e;
+        if (sizeof(E) == sizeof(BetaEntry)) {
+            const double b = aa <= a.k ? 0.0 : sqrt((aa - a.k) * (aa + a.k));
+            reinterpret_cast<TailEntry *>(tab + tot)[i] =
+                TailEntry{b > 0.0 ? (float)(b * 1.4426950408889634) : CUDART_INF_F, b > 0.0 ? (float)(1.0 / b) : 0.f};
+        }
     }
     if (exptab)
         for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.exptab_n; j += gridDim.x * blockDim.x)
@@ -814,7 +816,7 @@ __device__ __forceinline__ void reinsch_seg(RState<NH> &st, const BetaEntry *__r
 #pragma unroll 3
     for (int i = 0; i < count; ++i, n2 += dir, c2f += df) {
         const BetaEntry be = row[n2];
-        const bool ok = fmaf(c2f, c2f, c1sq) <= R2f && be.ibf != 0.f;
+        const bool ok = fmaf(c2f, c2f, c1sq) <= R2f && be.bf != 0.f;
         double Tj;
         double p = exp_neg_split<DEG>(fma(be.b, z, be.lnb), fmaf(be.bf, zf, be.lnbf), T, j0, jmax, Tj);
         p = ok ? p : 0.0;
@@ -948,19 +950,19 @@ __device__ __forceinline__ void add_row(F S[][2], const F rr[][2], F c1, F ik2)
 // by Horner's rule from hi down.  Four entries are loaded ahead of their four
 // Horner steps, so that a warp has four independent loads in flight.
 template <int NH>
-__device__ __forceinline__ void horner_step_f32(const BetaEntry &be, float c2, float z, float cv, float sv,
+__device__ __forceinline__ void horner_step_f32(const TailEntry &be, float c2, float z, float cv, float sv,
                                                 float acc[NH][2])
 {
     // no per-lane truncation test: the terms of the warp's disk beyond the lane's
     // own set are below e^{-T} of its largest term (they add accuracy), and
-    // propagating n have bl2 = +inf
+    // propagating n have bl2 = +inf (e = 0) and 1/b = 0
     const float e = ex2_approx(-be.bl2 * z);
     float wv[NH];
-    wv[0] = e * be.ibf;
+    wv[0] = e * be.ib;
     if (NH > 1) {
         wv[1] = c2 * wv[0];
         wv[2] = c2 * wv[1];
-        wv[3] = be.bf * e;
+        wv[3] = (be.ib != 0.f ? be.bl2 * 0.69314718f : 0.f) * e;  // b e
         wv[4] = e;
         wv[5] = c2 * e;
     }
@@ -974,7 +976,7 @@ __device__ __forceinline__ void horner_step_f32(const BetaEntry &be, float c2, f
 }
 
 template <int NH>
-__device__ __forceinline__ void seg_horner_f32(const BetaEntry *__restrict__ row, int lo, int hi, float a2f,
+__device__ __forceinline__ void seg_horner_f32(const TailEntry *__restrict__ row, int lo, int hi, float a2f,
                                                float z, float cv, float sv, float acc[NH][2])
 {
 #pragma unroll
@@ -982,7 +984,7 @@ __device__ __forceinline__ void seg_horner_f32(const BetaEntry *__restrict__ row
     float c2 = a2f + (float)hi;
     int n2 = hi;
     for (; n2 - 3 >= lo; n2 -= 4, c2 -= 4.0f) {
-        BetaEntry be[4];
+        TailEntry be[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) be[u] = row[n2 - u];
 #pragma unroll
@@ -1098,7 +1100,7 @@ __device__ __forceinline__ bool far_row(const FarWarp &W, const EvalArgs &a, int
 // when it has none), each by Horner's rule from its first index and moved to the
 // anchor N0, rotated by the row phase A = e^{i c1 t1} and added into Sf.
 template <int NH, int NS>
-__device__ __forceinline__ void far_row_tails(const BetaEntry *__restrict__ row, int n2a, int n2b, int ca, int cb,
+__device__ __forceinline__ void far_row_tails(const TailEntry *__restrict__ row, int n2a, int n2b, int ca, int cb,
                                               int N0, float a2f, float c1f, float c1sq, float zf, float cvf, float svf,
                                               const PhaseF &PF, float Ax, float Ay, float ik2f, float Sf[NS][2])
 {
@@ -1151,6 +1153,7 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, i
     double2 *out = reinterpret_cast<double2 *>(a.out);
     const int ne = n_entries(a.which);
     const int W2 = a.n2hi - a.n2lo + 1;
+    const TailEntry *ttab = reinterpret_cast<const TailEntry *>(tab + (size_t)(a.n1hi - a.n1lo + 1) * W2);
     const int lane = threadIdx.x & 31;
     const double k2 = a.k * a.k, ik2 = 1.0 / k2;
     const float ik2f = (float)ik2;
@@ -1311,7 +1314,8 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, i
             // float tails [n2a, ca-1] and [cb+1, n2b] (the whole row when there is
             // no core)
             if (TAILS)
-                far_row_tails<NH, NS>(row, n2a, n2b, ca, cb, N0, a2f, c1f, c1sq, zf, cvf, svf, PF, (float)A.x, (float)A.y,
+                far_row_tails<NH, NS>(ttab + (size_t)(n1 - a.n1lo) * W2 - a.n2lo, n2a, n2b, ca, cb, N0, a2f, c1f, c1sq, zf,
+                                      cvf, svf, PF, (float)A.x, (float)A.y,
                                       ik2f, Sf);
         }
         if (!L.valid) return;
@@ -1399,6 +1403,7 @@ __device__ void far3d_tail_chunk(const EvalArgs &a, int w, int count, int slab, 
     double2 *out = reinterpret_cast<double2 *>(a.out);
     const int ne = n_entries(a.which);
     const int W2 = a.n2hi - a.n2lo + 1;
+    const TailEntry *ttab = reinterpret_cast<const TailEntry *>(tab + (size_t)(a.n1hi - a.n1lo + 1) * W2);
     const int lane = threadIdx.x & 31;
     const float ik2f = (float)(1.0 / (a.k * a.k));
     const FarLane L = far_lane(a, w * 32 + lane, count);
@@ -1430,10 +1435,10 @@ __device__ void far3d_tail_chunk(const EvalArgs &a, int w, int count, int slab, 
         float c1f, c1sq;
         int n2a, n2b, ca, cb;
         if (!far_row(W, a, n1, c1f, c1sq, n2a, n2b, ca, cb)) continue;
-        const BetaEntry *row = tab + (size_t)(n1 - a.n1lo) * W2 - a.n2lo;
         float sn, cn;
         phase_m(P1, n1, sn, cn);
-        far_row_tails<NH, NS>(row, n2a, n2b, ca, cb, N0, W.a2f, c1f, c1sq, zf, cvf, svf, P2, A0x * cn - A0y * sn,
+        far_row_tails<NH, NS>(ttab + (size_t)(n1 - a.n1lo) * W2 - a.n2lo, n2a, n2b, ca, cb, N0, W.a2f, c1f, c1sq, zf, cvf,
+                              svf, P2, A0x * cn - A0y * sn,
                               A0x * sn + A0y * cn, ik2f, Sf);
     }
     if (!L.valid) return;
