@@ -35,18 +35,19 @@ from paper_1801_05977_gb300 import workloads as W  # noqa: E402
 K_WAVE, ALPHA, GRID, N_TARGETS = 2.5, (0.1, 0.3), (128, 128, 64), 1_000_000
 METRIC = "G_d evals/s on 1 GB300 at stated rel err; batched & surrogate vs plain FFT path"
 WORKLOAD = "3D doubly quasi-periodic G_d, k=2.5, alpha=(0.1,0.3), grid 128x128x64, 1e6 uniform targets"
-# Algorithmic FP64 work of one double-precision core series term, by the degree
-# of its exponential polynomial: y = b|x3| + ln b (1 FMA), r = y - y_j (1 add),
-# e^{-r} (DEG FMAs), one Reinsch step (2 FMAs + 1 add); an FMA counts 2 flops.
-# The far core is b|x3| <= Y0; the exponential (table step 1/4096) has degree 3,
-# then 2 from b >= bmin + 10.75/|x3| and 1 from b >= bmin + 20.75/|x3|.
-FP64_TERM_FLOPS = {3: 14, 2: 12, 1: 10}
+# The far series of a double-precision plan: the core (b|x3| <= Y0 = 18) is
+# summed in double for the terms within e^-8 of the largest (b <= bmin + 8/|x3|,
+# the double band) and in float-float on the FP32 pipe beyond (the float-float
+# band); the rest (up to the truncation) is the float tail.  Algorithmic FP64
+# work of a double-band term: y = b|x3| + ln b (1 FMA), r = y - y_j (1 add),
+# e^{-r} to degree 3 (3 FMAs; table step 1/4096), one Reinsch step (2 FMAs +
+# 1 add) = 14 flops (an FMA counts 2).
+FP64_TERM_FLOPS = 14
 FAR_CORE_Y0 = 18.0
-FAR_BAND_DEGS = (3, 2, 1)
-FAR_BAND_GAPS = (10.75, 20.75)
+FAR_FF_GAP = 8.0
 # DRAM bytes of one far3d_f64 launch on this workload: ncu (dram__bytes_read.sum
 # + dram__bytes_write.sum) of a 2e5-target launch, scaled by the far targets
-FAR_TRAFFIC_BYTES = 8.352768e6 * 5
+FAR_TRAFFIC_BYTES = 9.971968e6 * 5
 # FP64 peak from unit counts and clock: 152 SMs x 2 FP64 lanes/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
@@ -76,18 +77,17 @@ def smallest_evanescent_beta(k: float, alpha) -> float:
 
 
 def far_terms(x: np.ndarray, k: float, alpha, c: float, tol: float):
-    """(all terms, double-precision core terms, core terms by exponential degree) of the far branch."""
+    """(all terms, core terms, {"double": double-band terms, "float-float": float-float-band
+    terms}) of the far branch, each target with its own truncation, core and band radii."""
     z = np.abs(x[:, 2])
     z = z[z > c]
     T = np.log(1.0 / tol) + 3.0
     R2 = k * k + (T / z) ** 2
     Rc2 = np.minimum(k * k + (FAR_CORE_Y0 / z) ** 2, R2)
     bmin = smallest_evanescent_beta(k, alpha)
-    R4 = np.minimum(k * k + (bmin + FAR_BAND_GAPS[0] / z) ** 2, Rc2)
-    R3 = np.minimum(k * k + (bmin + FAR_BAND_GAPS[1] / z) ** 2, Rc2)
-    n_core, na, nab = disk_count(Rc2, alpha), disk_count(R4, alpha), disk_count(R3, alpha)
-    da, db, dc = FAR_BAND_DEGS
-    return disk_count(R2, alpha), n_core, {da: na, db: nab - na, dc: n_core - nab}
+    Rd2 = np.minimum(k * k + (bmin + FAR_FF_GAP / z) ** 2, Rc2)
+    n_core, n_double = disk_count(Rc2, alpha), disk_count(Rd2, alpha)
+    return disk_count(R2, alpha), n_core, {"double": n_double, "float-float": n_core - n_double}
 
 
 class ClockSampler:
@@ -321,7 +321,7 @@ def run_gpu(args):
     near_ms = float(np.mean([p[2] for p in ph64]))
     synth_ms = float(np.mean([p[0] for p in ph64]))
     terms, core_terms, bands = far_terms(x_np, K_WAVE, ALPHA, 0.6, tol64)
-    far_flops = world * sum(FP64_TERM_FLOPS[d] * n for d, n in bands.items())
+    far_flops = world * FP64_TERM_FLOPS * bands["double"]
     achieved = far_flops / (far_ms * 1e-3) / 1e12
     peak_fp64 = FP64_PEAK_TFLOPS
 
@@ -349,7 +349,7 @@ def run_gpu(args):
         "config": {"workload": WORKLOAD, "global_batch": world * n_targets, "precision": "fp64 (complex128)",
                    "series_tol": tol64, "parallelism": f"replicas{world}", "l2": "flushed (256 MiB write) between steps"},
         "phases_ms": {"synthesis": synth_ms, "near": near_ms, "far": far_ms,
-                      "far_series_terms": terms, "far_core_terms_fp64": core_terms},
+                      "far_series_terms": terms, "far_core_terms": core_terms},
         "split": {"value": whole_job_rate(n_targets, world, ms32 * 1e-3), "ms_per_step": ms32, "dtype": "f32/f64 split",
                   "series_tol": 1e-8, "max_err_vs_fp64_normwise": split_err,
                   "phases_ms": {"synthesis": float(np.mean([p[0] for p in ph32])),
@@ -357,13 +357,15 @@ def run_gpu(args):
                                 "far": float(np.mean([p[3] for p in ph32]))}},
         "roofline": {"bound": "alu", "kernel": "far3d_f64", "achieved": achieved, "peak": peak_fp64,
                      "unit": "TFLOP/s", "frac": achieved / peak_fp64,
-                     "traffic": FAR_TRAFFIC_BYTES if n_targets == 1_000_000 else None,
-                     "algorithmic_flops": far_flops, "core_terms_by_degree": bands,
-                     "note": "FP64 pipe bound (ncu: 86% of peak while active); achieved = algorithmic FP64 flops "
-                             "of the double-precision core terms (b|x3| <= 18; 14/12/10 flops per term for "
-                             "exponential degree 3/2/1, FMA = 2 flops) / far-kernel time; the float tail is not "
-                             "counted; peak from unit counts and clock (152 SMs x 2 FP64 FMA/clk x 2 flop x "
-                             "2.07 GHz; FMA probe 1.21 TFLOP/s)"},
+                     "traffic": FAR_TRAFFIC_BYTES if n_targets == 1_000_000 and FAR_TRAFFIC_BYTES else None,
+                     "algorithmic_flops": far_flops, "core_terms_by_band": bands,
+                     "note": "FP64 pipe bound (ncu: 82% of the FP64 peak while active, FP32 pipe 18%); achieved = "
+                             "algorithmic FP64 flops of the double-band core terms (b <= bmin + 8/|x3|, 14 flops "
+                             "per term, FMA = 2 flops) / far-phase time; the float-float band (FP32 pipe) and the "
+                             "float tail (concurrent kernel) are not counted, and the per-row and per-target FP64 "
+                             "work (row sums, propagating terms, set-up) is the rest of the FP64 pipe time; peak "
+                             "from unit counts and clock (152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz; FMA probe "
+                             "1.21 TFLOP/s)"},
         "e2e": {"value": whole_job_rate(n_targets, world, e2e_s), "unit": "evals/s",
                 "h2d_bytes_per_step": int(x_np.nbytes), "d2h_bytes_per_step": int(n_targets * 16)},
         "batched": batched,

@@ -530,11 +530,6 @@ __global__ void series_tables(EvalArgs a, E *tab, double2 *exptab, PropEntry *pr
             set_entry(e, b, 1.0 / b);
         }
         tab[i] = e;
-        if (sizeof(E) == sizeof(BetaEntry)) {
-            const double b = aa <= a.k ? 0.0 : sqrt((aa - a.k) * (aa + a.k));
-            reinterpret_cast<TailEntry *>(tab + tot)[i] =
-                TailEntry{b > 0.0 ? (float)(b * 1.4426950408889634) : CUDART_INF_F, b > 0.0 ? (float)(1.0 / b) : 0.f};
-        }
     }
     if (exptab)
         for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.exptab_n; j += gridDim.x * blockDim.x)
@@ -947,22 +942,27 @@ __device__ __forceinline__ void add_row(F S[][2], const F rr[][2], F c1, F ik2)
 
 // The same segment sums in float (hardware ex2), for the exponentially small
 // tail of a double-precision plan: sum_{n2=lo}^{hi} w(n2) v^{n2-lo}, v = e^{i t2},
-// by Horner's rule from hi down.  Four entries are loaded ahead of their four
-// Horner steps, so that a warp has four independent loads in flight.
+// by Horner's rule from hi down.  b and 1/b come from the lattice index itself
+// (b^2 = c1^2 + c2^2 - k^2, one rsqrt), so the loop loads nothing; in float b
+// is good to ~1e-7 relative, e^{-b|x3|} to ~4e-6 for b|x3| <= 40, well inside
+// the tail's error budget.
 template <int NH>
-__device__ __forceinline__ void horner_step_f32(const TailEntry &be, float c2, float z, float cv, float sv,
-                                                float acc[NH][2])
+__device__ __forceinline__ void horner_step_f32(float c2, float q0, float zl2, float cv, float sv, float acc[NH][2])
 {
-    // no per-lane truncation test: the terms of the warp's disk beyond the lane's
-    // own set are below e^{-T} of its largest term (they add accuracy), and
-    // propagating n have bl2 = +inf (e = 0) and 1/b = 0
-    const float e = ex2_approx(-be.bl2 * z);
+    // q0 = c1^2 - k^2; propagating n (b^2 <= 0) get weight 0.  No per-lane
+    // truncation test: the terms of the warp's disk beyond the lane's own set are
+    // below e^{-T} of its largest term (they add accuracy).
+    const float x = fmaf(c2, c2, q0);
+    const bool ev = x > 0.f;
+    const float ib = rsqrtf(ev ? x : 1.f);
+    const float b = x * ib;
+    const float e = ev ? ex2_approx(-b * zl2) : 0.f;
     float wv[NH];
-    wv[0] = e * be.ib;
+    wv[0] = e * ib;
     if (NH > 1) {
         wv[1] = c2 * wv[0];
         wv[2] = c2 * wv[1];
-        wv[3] = (be.ib != 0.f ? be.bl2 * 0.69314718f : 0.f) * e;  // b e
+        wv[3] = b * e;
         wv[4] = e;
         wv[5] = c2 * e;
     }
@@ -975,22 +975,16 @@ __device__ __forceinline__ void horner_step_f32(const TailEntry &be, float c2, f
     }
 }
 
+// zl2 = |x3| log2(e)
 template <int NH>
-__device__ __forceinline__ void seg_horner_f32(const TailEntry *__restrict__ row, int lo, int hi, float a2f,
-                                               float z, float cv, float sv, float acc[NH][2])
+__device__ __forceinline__ void seg_horner_f32(int lo, int hi, float a2f, float q0, float zl2, float cv, float sv,
+                                               float acc[NH][2])
 {
 #pragma unroll
     for (int e = 0; e < NH; ++e) acc[e][0] = acc[e][1] = 0.f;
     float c2 = a2f + (float)hi;
-    int n2 = hi;
-    for (; n2 - 3 >= lo; n2 -= 4, c2 -= 4.0f) {
-        TailEntry be[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) be[u] = row[n2 - u];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) horner_step_f32<NH>(be[u], c2 - (float)u, z, cv, sv, acc);
-    }
-    for (; n2 >= lo; --n2, c2 -= 1.0f) horner_step_f32<NH>(row[n2], c2, z, cv, sv, acc);
+#pragma unroll 4
+    for (int n2 = hi; n2 >= lo; --n2, c2 -= 1.0f) horner_step_f32<NH>(c2, q0, zl2, cv, sv, acc);
 }
 
 // ---------------------------------------------------------------------------
@@ -1100,10 +1094,11 @@ __device__ __forceinline__ bool far_row(const FarWarp &W, const EvalArgs &a, int
 // when it has none), each by Horner's rule from its first index and moved to the
 // anchor N0, rotated by the row phase A = e^{i c1 t1} and added into Sf.
 template <int NH, int NS>
-__device__ __forceinline__ void far_row_tails(const TailEntry *__restrict__ row, int n2a, int n2b, int ca, int cb,
-                                              int N0, float a2f, float c1f, float c1sq, float zf, float cvf, float svf,
-                                              const PhaseF &PF, float Ax, float Ay, float ik2f, float Sf[NS][2])
+__device__ __forceinline__ void far_row_tails(int n2a, int n2b, int ca, int cb, int N0, float a2f, float c1f,
+                                              float c1sq, float k2f, float zf, float cvf, float svf, const PhaseF &PF,
+                                              float Ax, float Ay, float ik2f, float Sf[NS][2])
 {
+    const float q0 = c1sq - k2f, zl2 = zf * 1.44269504f;
     const int tl_hi = (ca <= cb) ? ca - 1 : n2b;
     const int th_lo = (ca <= cb) ? cb + 1 : n2b + 1;
     if (n2a > tl_hi && th_lo > n2b) return;
@@ -1112,7 +1107,7 @@ __device__ __forceinline__ void far_row_tails(const TailEntry *__restrict__ row,
     for (int e = 0; e < NH; ++e) tf[e][0] = tf[e][1] = 0.f;
     if (n2a <= tl_hi) {
         float acc[NH][2], ps, pc;
-        seg_horner_f32<NH>(row, n2a, tl_hi, a2f, zf, cvf, svf, acc);
+        seg_horner_f32<NH>(n2a, tl_hi, a2f, q0, zl2, cvf, svf, acc);
         phase_m(PF, n2a - N0, ps, pc);
 #pragma unroll
         for (int e = 0; e < NH; ++e) {
@@ -1122,7 +1117,7 @@ __device__ __forceinline__ void far_row_tails(const TailEntry *__restrict__ row,
     }
     if (th_lo <= n2b) {
         float acc[NH][2], ps, pc;
-        seg_horner_f32<NH>(row, th_lo, n2b, a2f, zf, cvf, svf, acc);
+        seg_horner_f32<NH>(th_lo, n2b, a2f, q0, zl2, cvf, svf, acc);
         phase_m(PF, th_lo - N0, ps, pc);
 #pragma unroll
         for (int e = 0; e < NH; ++e) {
@@ -1153,7 +1148,6 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, i
     double2 *out = reinterpret_cast<double2 *>(a.out);
     const int ne = n_entries(a.which);
     const int W2 = a.n2hi - a.n2lo + 1;
-    const TailEntry *ttab = reinterpret_cast<const TailEntry *>(tab + (size_t)(a.n1hi - a.n1lo + 1) * W2);
     const int lane = threadIdx.x & 31;
     const double k2 = a.k * a.k, ik2 = 1.0 / k2;
     const float ik2f = (float)ik2;
@@ -1314,8 +1308,7 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, i
             // float tails [n2a, ca-1] and [cb+1, n2b] (the whole row when there is
             // no core)
             if (TAILS)
-                far_row_tails<NH, NS>(ttab + (size_t)(n1 - a.n1lo) * W2 - a.n2lo, n2a, n2b, ca, cb, N0, a2f, c1f, c1sq, zf,
-                                      cvf, svf, PF, (float)A.x, (float)A.y,
+                far_row_tails<NH, NS>(n2a, n2b, ca, cb, N0, a2f, c1f, c1sq, k2f, zf, cvf, svf, PF, (float)A.x, (float)A.y,
                                       ik2f, Sf);
         }
         if (!L.valid) return;
@@ -1399,13 +1392,10 @@ __device__ void far3d_tail_chunk(const EvalArgs &a, int w, int count, int slab, 
 {
     constexpr int NH = NF == 1 ? 1 : 6;
     constexpr int NS = NF == 1 ? 1 : 7;
-    const BetaEntry *tab = reinterpret_cast<const BetaEntry *>(a.btab);
     double2 *out = reinterpret_cast<double2 *>(a.out);
     const int ne = n_entries(a.which);
-    const int W2 = a.n2hi - a.n2lo + 1;
-    const TailEntry *ttab = reinterpret_cast<const TailEntry *>(tab + (size_t)(a.n1hi - a.n1lo + 1) * W2);
     const int lane = threadIdx.x & 31;
-    const float ik2f = (float)(1.0 / (a.k * a.k));
+    const float ik2f = (float)(1.0 / (a.k * a.k)), k2f = (float)(a.k * a.k);
     const FarLane L = far_lane(a, w * 32 + lane, count);
     const FarWarp W = far_warp(a, L);
     const int N0 = W.N0;
@@ -1437,8 +1427,7 @@ __device__ void far3d_tail_chunk(const EvalArgs &a, int w, int count, int slab, 
         if (!far_row(W, a, n1, c1f, c1sq, n2a, n2b, ca, cb)) continue;
         float sn, cn;
         phase_m(P1, n1, sn, cn);
-        far_row_tails<NH, NS>(ttab + (size_t)(n1 - a.n1lo) * W2 - a.n2lo, n2a, n2b, ca, cb, N0, W.a2f, c1f, c1sq, zf, cvf,
-                              svf, P2, A0x * cn - A0y * sn,
+        far_row_tails<NH, NS>(n2a, n2b, ca, cb, N0, W.a2f, c1f, c1sq, k2f, zf, cvf, svf, P2, A0x * cn - A0y * sn,
                               A0x * sn + A0y * cn, ik2f, Sf);
     }
     if (!L.valid) return;

@@ -127,11 +127,7 @@ struct __align__(16) BetaEntry {
     double b, lnb;                // double-precision core terms
     float bf, blo, lnbf, lnblo;   // b and ln b as float pairs (hi + lo): the float-float band; hi parts index the table
 };
-// The float tail of a double-precision plan reads a compact copy that follows
-// the BetaEntry table (same indexing): b log2(e) (+inf for propagating n) and 1/b.
-struct TailEntry {
-    float bl2, ib;
-};
+
 struct BetaEntryF {
     float bl2, ib, b, pad;  // b log2(e), 1/b, b
 };

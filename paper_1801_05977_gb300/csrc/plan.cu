@@ -456,7 +456,7 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
             p->n2lo = (int)floor(-a2 - Rc) - 1;
             p->n2hi = (int)ceil(-a2 + Rc) + 1;
             size_t ne = (size_t)(p->n1hi - p->n1lo + 1) * (p->n2hi - p->n2lo + 1);
-            size_t eb = p->precision == GF_FP64 ? sizeof(BetaEntry) + sizeof(TailEntry) : sizeof(BetaEntryF);
+            size_t eb = p->precision == GF_FP64 ? sizeof(BetaEntry) : sizeof(BetaEntryF);
             // propagating indices lie in the sub-box |c1|, |c2| <= k
             const int pbox[4] = {(int)floor(-a1 - k) - 1, (int)ceil(-a1 + k) + 1, (int)floor(-a2 - k) - 1,
                                  (int)ceil(-a2 + k) + 1};
