@@ -130,6 +130,28 @@ def test_host_entry_point_matches_device():
     assert rel_err(host, dev) < 1e-11
 
 
+@pytest.mark.parametrize("k,al", [(2.5, (0.1, 0.3)), (1.0, (0.002, 0.0)), (4.7, (-0.45, 0.25))],
+                         ids=["config2", "near-wood", "k4.7"])
+def test_far_series_tiers(k, al):
+    """Far targets only (|x3| from just above c to 2): the series summed in its
+    double, float-float and float tiers against the oracle's plain double sums
+    of the same truncated series.  (1.0, (0.002, 0)) puts |alpha_(1,0)| within
+    2e-3 of k: the smallest evanescent b is 0.063, so ln b and 1/b are far from
+    the other cases."""
+    pb = O.Problem(dim=3, k=k, alpha=al, M=(16, 16, 8))
+    plan = gpu_plan(pb)
+    rng = np.random.default_rng(17)
+    n = 6000
+    z = rng.uniform(pb.c * (1 + 1e-9), 2.0, n) * rng.choice([-1.0, 1.0], n)
+    x = np.column_stack([rng.uniform(-7, 7, n), rng.uniform(-7, 7, n), z])
+    ref = O.series(pb, x, O.OUT_GD)
+    got = gpu_eval(plan, x, gf.GF_OUT_GD)
+    e_nw, e_pt = norm_err(got, ref), rel_err(got, ref)
+    print(f"far series k={k}: normwise {e_nw:.2e}, pointwise {e_pt:.2e} vs the oracle's double sums")
+    assert e_nw < 1e-13  # measured 5e-15 .. 1.4e-14
+    assert e_pt < TOL64
+
+
 # ----------------------------------------------------------------------------- 2D (config: k = 1.3, alpha = 0.2, 64 x 64, 10^4 targets)
 def test_parity_2d_config():
     pb = O.Problem(dim=2, k=1.3, alpha=(0.2,), M=(64, 64))
