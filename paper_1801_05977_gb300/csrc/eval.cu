@@ -147,11 +147,150 @@ __device__ __forceinline__ int far_bucket(double z, double c)
 // (fields 0..5 = (delta_pq - c^p c^q/k^2) L_d, field 6 = L_d).
 // R = storage/accumulation type of the grid (double: GF_FP64, float: split).
 // ---------------------------------------------------------------------------
+// The near branch at one target i (valid, finite, |x_last| <= c): cell
+// reduction, tensor cubic interpolation of the stored grid, phases and the
+// singular part (Algorithm 2, calculation step).
 template <typename R, int NF>
-__device__ void near3d_tiles(const EvalArgs &a, int64_t base0, int64_t stride, int *hist)
+__device__ __forceinline__ void near_point(const EvalArgs &a, int64_t i, double x1, double x2, double x3, double ih1,
+                                           double ih2, double ih3)
 {
     typedef typename cplx_t<R>::T C;
     const C *G = reinterpret_cast<const C *>(a.grid);
+    const int ne = n_entries(a.which);
+    C *o = reinterpret_cast<C *>(a.out) + i * ne;
+    const bool only_L = NF == 1 && a.which == GF_OUT_LD;
+    double t1, m1, t2, m2;
+    reduce_period(x1, t1, m1);
+    reduce_period(x2, t2, m2);
+    double f1, f2, f3;
+    int i1 = stencil_origin(t1, -GF_PI, a.h1, ih1, a.M1, f1);
+    int i2 = stencil_origin(t2, -GF_PI, a.h2, ih2, a.M2, f2);
+    // stored planes from Q3lo: a Helmholtz grid (even in x3) holds x3 >= -h3 only
+    // and is read at |x3|; a Maxwell grid holds the slab |x3| <= c
+    int i3 = stencil_origin(NF == 1 ? fabs(x3) : x3, -a.ct, a.h3, ih3, a.M3, f3) - a.Q3lo;
+    // weights in the grid's precision (f itself is formed in double)
+    R w1[4], w2[4], w3[4];
+    lagrange4<R>((R)f1, w1);
+    lagrange4<R>((R)f2, w2);
+    lagrange4<R>((R)f3, w3);
+    R acc[NF][2];
+#pragma unroll
+    for (int e = 0; e < NF; ++e) acc[e][0] = acc[e][1] = (R)0;
+#pragma unroll
+    for (int d3 = 0; d3 < 4; ++d3) {
+#pragma unroll
+        for (int d2 = 0; d2 < 4; ++d2) {
+            const C *row = G + (((size_t)(i3 + d3) * a.P2 + (i2 + d2)) * a.P1 + i1) * NF;
+            const R w23 = w3[d3] * w2[d2];
+#pragma unroll
+            for (int e = 0; e < NF; ++e) {
+                R sr = 0, si = 0;
+#pragma unroll
+                for (int d1 = 0; d1 < 4; ++d1) {
+                    C g = __ldg(row + d1 * NF + e);
+                    sr = fma(w1[d1], g.x, sr);
+                    si = fma(w1[d1], g.y, si);
+                }
+                acc[e][0] = fma(w23, sr, acc[e][0]);
+                acc[e][1] = fma(w23, si, acc[e][1]);
+            }
+        }
+    }
+
+    // lift = e^{i alpha.t} e^{i 2 pi <alpha.m>}; G = lift L + e^{i 2pi<alpha.m>} Phi Y (K = L + F, F = e^{-i alpha.t} Phi Y).
+    // Split plans: the fractional part in double, the two phases in float.
+    double2 lat, lift;
+    float2 latf = make_float2(0.f, 0.f), liftf = make_float2(0.f, 0.f);
+    if (sizeof(R) == 4) {
+        double ph = a.a1 * m1 + a.a2 * m2;
+        ph -= rint(ph);
+        float sl, cl, sa, ca;
+        sincospif(2.0f * (float)ph, &sl, &cl);
+        sincosf((float)a.a1 * (float)t1 + (float)a.a2 * (float)t2, &sa, &ca);
+        latf = make_float2(cl, sl);
+        liftf = cmulf(make_float2(ca, sa), latf);
+        lat = make_double2(cl, sl);
+        lift = make_double2(liftf.x, liftf.y);
+    } else {
+        lat = lattice_phase(a.a1, m1, a.a2, m2);
+        double sa, ca;
+        sincos(a.a1 * t1 + a.a2 * t2, &sa, &ca);
+        lift = cmul(make_double2(ca, sa), lat);
+    }
+    double r = sqrt(t1 * t1 + t2 * t2 + x3 * x3);
+    bool sing = r < 2.0 * a.eps;
+    double2 PhiY = make_double2(0, 0), dPhi = make_double2(0, 0), d2Phi = make_double2(0, 0);
+    if (sing) {
+        // Phi(r) = e^{ikr}/(4 pi r) Y_eps(r) and its r-derivatives (Sec. 3.2, Sec. 4)
+        double sk, ck;
+        sincos(a.k * r, &sk, &ck);
+        double ir = 1.0 / r;
+        double2 g0 = make_double2(ck * ir * (0.25 / GF_PI), sk * ir * (0.25 / GF_PI));
+        double s = (r - a.eps) / a.eps;
+        double Y0 = 1.0 - smooth8(s);
+        PhiY = cscale(g0, Y0);
+        if (NF > 1) {
+            double Y1 = -smooth8_d1(s) / a.eps;
+            double Y2 = -smooth8_d2(s) / (a.eps * a.eps);
+            double2 L1 = make_double2(-ir, a.k);                  // ik - 1/r
+            double2 g1 = cmul(g0, L1);
+            double2 L2 = cmul(L1, L1);
+            L2.x += ir * ir;
+            double2 g2 = cmul(g0, L2);
+            dPhi = cadd(cscale(g1, Y0), cscale(g0, Y1));
+            d2Phi = cadd(cadd(cscale(g2, Y0), cscale(g1, 2.0 * Y1)), cscale(g0, Y2));
+        }
+    }
+    if (NF == 1) {
+        double2 L = make_double2((double)acc[0][0], (double)acc[0][1]);
+        if (only_L) {
+            store_out(o, L);
+            return;
+        }
+        if (sizeof(R) == 4) {
+            // split: the combination in float (the singular part was formed in double)
+            const float2 v = cmulf(liftf, make_float2((float)acc[0][0], (float)acc[0][1]));
+            const float2 u = sing ? cmulf(latf, make_float2((float)PhiY.x, (float)PhiY.y)) : make_float2(0.f, 0.f);
+            reinterpret_cast<float2 *>(o)[0] = make_float2(v.x + u.x, v.y + u.y);
+            return;
+        }
+        double2 v = cadd(cmul(lift, L), cmul(lat, PhiY));
+        store_out(o, v);
+    } else {
+        const double ik2 = 1.0 / (a.k * a.k);
+        const double xv[3] = {t1, t2, x3};
+        const int PP[6] = {0, 1, 2, 0, 0, 1}, QQ[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+        for (int e = 0; e < 6; ++e) {
+            double2 L = make_double2((double)acc[e][0], (double)acc[e][1]);
+            double2 v = cmul(lift, L);
+            if (sing) {
+                double ir = 1.0 / r;
+                double xp = xv[PP[e]] * ir, xq = xv[QQ[e]] * ir;
+                double dl = PP[e] == QQ[e] ? 1.0 : 0.0;
+                // delta_pq Phi + k^-2 [Phi'' xp xq + (Phi'/r)(delta_pq - xp xq)]
+                double2 s = cadd(cscale(d2Phi, xp * xq), cscale(dPhi, ir * (dl - xp * xq)));
+                s = cscale(s, ik2);
+                if (dl != 0.0) s = cadd(s, PhiY);
+                v = cadd(v, cmul(lat, s));
+            }
+            store_out(o + e, v);
+        }
+        if (a.which == GF_OUT_MAXWELL7) {
+            double2 L = make_double2((double)acc[6][0], (double)acc[6][1]);
+            store_out(o + 6, cadd(cmul(lift, L), cmul(lat, PhiY)));
+        }
+    }
+}
+
+// MODE 0: classify every target (far list, bucket histogram, zeroed far
+// outputs, NaN for non-finite ones) and evaluate the near ones here; MODE 1:
+// classify only, appending the near targets to a.near_idx, so that near3d_list
+// evaluates them in full warps.
+template <typename R, int NF, int MODE>
+__device__ void near3d_tiles(const EvalArgs &a, int64_t base0, int64_t stride, int *hist)
+{
+    typedef typename cplx_t<R>::T C;
     C *out = reinterpret_cast<C *>(a.out);
     const int ne = n_entries(a.which);
     const double ih1 = 1.0 / a.h1, ih2 = 1.0 / a.h2, ih3 = 1.0 / a.h3;
@@ -173,9 +312,11 @@ __device__ void near3d_tiles(const EvalArgs &a, int64_t base0, int64_t stride, i
             valid = false;
         }
         push_far(isfar, (int)i, a.far_idx, a.far_count);
+        // (every lane of the warp reaches both appends: they vote by ballot)
+        if (MODE == 1) push_far(valid && finite && !isfar, (int)i, a.near_idx, a.far_count + GF_NEAR_SLOT);
         C *o = out + i * ne;
         if (isfar) {
-            // the far kernel adds its row slabs into these entries
+            // the far kernels add their row slabs into these entries
             atomicAdd(&hist[far_bucket(fabs(x3), a.c)], 1);
             for (int e = 0; e < ne; ++e) o[e] = zero_c<R>();
             continue;
@@ -185,138 +326,29 @@ __device__ void near3d_tiles(const EvalArgs &a, int64_t base0, int64_t stride, i
             for (int e = 0; e < ne; ++e) o[e] = nan_c<R>();
             continue;
         }
-        double t1, m1, t2, m2;
-        reduce_period(x1, t1, m1);
-        reduce_period(x2, t2, m2);
-        double f1, f2, f3;
-        int i1 = stencil_origin(t1, -GF_PI, a.h1, ih1, a.M1, f1);
-        int i2 = stencil_origin(t2, -GF_PI, a.h2, ih2, a.M2, f2);
-        // stored planes from Q3lo: a Helmholtz grid (even in x3) holds x3 >= -h3 only
-        // and is read at |x3|; a Maxwell grid holds the slab |x3| <= c
-        int i3 = stencil_origin(NF == 1 ? fabs(x3) : x3, -a.ct, a.h3, ih3, a.M3, f3) - a.Q3lo;
-        // weights in the grid's precision (f itself is formed in double)
-        R w1[4], w2[4], w3[4];
-        lagrange4<R>((R)f1, w1);
-        lagrange4<R>((R)f2, w2);
-        lagrange4<R>((R)f3, w3);
-        R acc[NF][2];
-#pragma unroll
-        for (int e = 0; e < NF; ++e) acc[e][0] = acc[e][1] = (R)0;
-#pragma unroll
-        for (int d3 = 0; d3 < 4; ++d3) {
-#pragma unroll
-            for (int d2 = 0; d2 < 4; ++d2) {
-                const C *row = G + (((size_t)(i3 + d3) * a.P2 + (i2 + d2)) * a.P1 + i1) * NF;
-                const R w23 = w3[d3] * w2[d2];
-#pragma unroll
-                for (int e = 0; e < NF; ++e) {
-                    R sr = 0, si = 0;
-#pragma unroll
-                    for (int d1 = 0; d1 < 4; ++d1) {
-                        C g = __ldg(row + d1 * NF + e);
-                        sr = fma(w1[d1], g.x, sr);
-                        si = fma(w1[d1], g.y, si);
-                    }
-                    acc[e][0] = fma(w23, sr, acc[e][0]);
-                    acc[e][1] = fma(w23, si, acc[e][1]);
-                }
-            }
-        }
-
-        // lift = e^{i alpha.t} e^{i 2 pi <alpha.m>}; G = lift L + e^{i 2pi<alpha.m>} Phi Y (K = L + F, F = e^{-i alpha.t} Phi Y).
-        // Split plans: the fractional part in double, the two phases in float.
-        double2 lat, lift;
-        float2 latf = make_float2(0.f, 0.f), liftf = make_float2(0.f, 0.f);
-        if (sizeof(R) == 4) {
-            double ph = a.a1 * m1 + a.a2 * m2;
-            ph -= rint(ph);
-            float sl, cl, sa, ca;
-            sincospif(2.0f * (float)ph, &sl, &cl);
-            sincosf((float)a.a1 * (float)t1 + (float)a.a2 * (float)t2, &sa, &ca);
-            latf = make_float2(cl, sl);
-            liftf = cmulf(make_float2(ca, sa), latf);
-            lat = make_double2(cl, sl);
-            lift = make_double2(liftf.x, liftf.y);
-        } else {
-            lat = lattice_phase(a.a1, m1, a.a2, m2);
-            double sa, ca;
-            sincos(a.a1 * t1 + a.a2 * t2, &sa, &ca);
-            lift = cmul(make_double2(ca, sa), lat);
-        }
-        double r = sqrt(t1 * t1 + t2 * t2 + x3 * x3);
-        bool sing = r < 2.0 * a.eps;
-        double2 PhiY = make_double2(0, 0), dPhi = make_double2(0, 0), d2Phi = make_double2(0, 0);
-        if (sing) {
-            // Phi(r) = e^{ikr}/(4 pi r) Y_eps(r) and its r-derivatives (Sec. 3.2, Sec. 4)
-            double sk, ck;
-            sincos(a.k * r, &sk, &ck);
-            double ir = 1.0 / r;
-            double2 g0 = make_double2(ck * ir * (0.25 / GF_PI), sk * ir * (0.25 / GF_PI));
-            double s = (r - a.eps) / a.eps;
-            double Y0 = 1.0 - smooth8(s);
-            PhiY = cscale(g0, Y0);
-            if (NF > 1) {
-                double Y1 = -smooth8_d1(s) / a.eps;
-                double Y2 = -smooth8_d2(s) / (a.eps * a.eps);
-                double2 L1 = make_double2(-ir, a.k);                  // ik - 1/r
-                double2 g1 = cmul(g0, L1);
-                double2 L2 = cmul(L1, L1);
-                L2.x += ir * ir;
-                double2 g2 = cmul(g0, L2);
-                dPhi = cadd(cscale(g1, Y0), cscale(g0, Y1));
-                d2Phi = cadd(cadd(cscale(g2, Y0), cscale(g1, 2.0 * Y1)), cscale(g0, Y2));
-            }
-        }
-        if (NF == 1) {
-            double2 L = make_double2((double)acc[0][0], (double)acc[0][1]);
-            if (only_L) {
-                store_out(o, L);
-                continue;
-            }
-            if (sizeof(R) == 4) {
-                // split: the combination in float (the singular part was formed in double)
-                const float2 v = cmulf(liftf, make_float2((float)acc[0][0], (float)acc[0][1]));
-                const float2 u = sing ? cmulf(latf, make_float2((float)PhiY.x, (float)PhiY.y)) : make_float2(0.f, 0.f);
-                reinterpret_cast<float2 *>(o)[0] = make_float2(v.x + u.x, v.y + u.y);
-                continue;
-            }
-            double2 v = cadd(cmul(lift, L), cmul(lat, PhiY));
-            store_out(o, v);
-        } else {
-            const double ik2 = 1.0 / (a.k * a.k);
-            const double xv[3] = {t1, t2, x3};
-            const int PP[6] = {0, 1, 2, 0, 0, 1}, QQ[6] = {0, 1, 2, 1, 2, 2};
-#pragma unroll
-            for (int e = 0; e < 6; ++e) {
-                double2 L = make_double2((double)acc[e][0], (double)acc[e][1]);
-                double2 v = cmul(lift, L);
-                if (sing) {
-                    double ir = 1.0 / r;
-                    double xp = xv[PP[e]] * ir, xq = xv[QQ[e]] * ir;
-                    double dl = PP[e] == QQ[e] ? 1.0 : 0.0;
-                    // delta_pq Phi + k^-2 [Phi'' xp xq + (Phi'/r)(delta_pq - xp xq)]
-                    double2 s = cadd(cscale(d2Phi, xp * xq), cscale(dPhi, ir * (dl - xp * xq)));
-                    s = cscale(s, ik2);
-                    if (dl != 0.0) s = cadd(s, PhiY);
-                    v = cadd(v, cmul(lat, s));
-                }
-                store_out(o + e, v);
-            }
-            if (a.which == GF_OUT_MAXWELL7) {
-                double2 L = make_double2((double)acc[6][0], (double)acc[6][1]);
-                store_out(o + 6, cadd(cmul(lift, L), cmul(lat, PhiY)));
-            }
-        }
+        if (MODE == 0) near_point<R, NF>(a, i, x1, x2, x3, ih1, ih2, ih3);
     }
 }
 
+// The near targets listed by a MODE-1 classification pass, one per thread.
 template <typename R, int NF>
+__global__ void __launch_bounds__(256) near3d_list(EvalArgs a)
+{
+    const int count = a.far_count[GF_NEAR_SLOT];
+    const double ih1 = 1.0 / a.h1, ih2 = 1.0 / a.h2, ih3 = 1.0 / a.h3;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < count; j += gridDim.x * blockDim.x) {
+        const int64_t i = a.near_idx[j];
+        near_point<R, NF>(a, i, a.x[3 * i], a.x[3 * i + 1], a.x[3 * i + 2], ih1, ih2, ih3);
+    }
+}
+
+template <typename R, int NF, int MODE = 0>
 __global__ void __launch_bounds__(256) near3d(EvalArgs a)
 {
     __shared__ int hist[GF_FAR_BUCKETS];
     for (int b = threadIdx.x; b < GF_FAR_BUCKETS; b += blockDim.x) hist[b] = 0;
     __syncthreads();
-    near3d_tiles<R, NF>(a, (int64_t)blockIdx.x * blockDim.x, (int64_t)gridDim.x * blockDim.x, hist);
+    near3d_tiles<R, NF, MODE>(a, (int64_t)blockIdx.x * blockDim.x, (int64_t)gridDim.x * blockDim.x, hist);
     __syncthreads();
     for (int b = threadIdx.x; b < GF_FAR_BUCKETS; b += blockDim.x)
         if (hist[b]) atomicAdd(&a.far_count[1 + b], hist[b]);
@@ -348,7 +380,7 @@ __global__ void __launch_bounds__(256) near3d_batch(const EvalArgs *args, const 
         for (int b = threadIdx.x; b < GF_FAR_BUCKETS; b += blockDim.x) hist[b] = 0;
         __syncthreads();
         const int64_t base = (int64_t)(vb - prefix[p]) * blockDim.x;
-        near3d_tiles<R, NF>(sa, base, sa.n + blockDim.x, hist);
+        near3d_tiles<R, NF, 0>(sa, base, sa.n + blockDim.x, hist);
         __syncthreads();
         for (int b = threadIdx.x; b < GF_FAR_BUCKETS; b += blockDim.x)
             if (hist[b]) atomicAdd(&sa.far_count[1 + b], hist[b]);
@@ -1820,7 +1852,13 @@ cudaError_t launch_eval_t(const EvalArgs &a, cudaStream_t s, cudaEvent_t ev_mid,
         if (ev_mid) cudaEventRecord(ev_mid, s);
         far2d<R><<<resident_grid<far2d<R>>(nsm), 128, 0, s>>>(a);
     } else if (a.nf == 1) {
-        near3d<R, 1><<<(int)blocks, 256, 0, s>>>(a);
+        // with a near list: classify, then the near targets in full warps
+        if (a.near_idx) {
+            near3d<R, 1, 1><<<(int)blocks, 256, 0, s>>>(a);
+            near3d_list<R, 1><<<(int)blocks, 256, 0, s>>>(a);
+        } else {
+            near3d<R, 1><<<(int)blocks, 256, 0, s>>>(a);
+        }
         if (ev_mid) cudaEventRecord(ev_mid, s);
         far_scatter<<<nsm * 2, 256, 0, s>>>(a);
         if (sizeof(R) == 8) {
@@ -1829,7 +1867,12 @@ cudaError_t launch_eval_t(const EvalArgs &a, cudaStream_t s, cudaEvent_t ev_mid,
         } else
             far3d_f32<1><<<resident_grid<far3d_f32<1>>(nsm), 128, 0, s>>>(a);
     } else {
-        near3d<R, 7><<<(int)blocks, 256, 0, s>>>(a);
+        if (a.near_idx) {
+            near3d<R, 7, 1><<<(int)blocks, 256, 0, s>>>(a);
+            near3d_list<R, 7><<<(int)blocks, 256, 0, s>>>(a);
+        } else {
+            near3d<R, 7><<<(int)blocks, 256, 0, s>>>(a);
+        }
         if (ev_mid) cudaEventRecord(ev_mid, s);
         far_scatter<<<nsm * 2, 256, 0, s>>>(a);
         if (sizeof(R) == 8) {
@@ -1838,7 +1881,7 @@ cudaError_t launch_eval_t(const EvalArgs &a, cudaStream_t s, cudaEvent_t ev_mid,
         } else
             far3d_f32<7><<<resident_grid<far3d_f32<7>>(nsm), 128, 0, s>>>(a);
     }
-    gf_count_launch(a.dim == 2 ? 2 : sizeof(R) == 8 ? 4 : 3);
+    gf_count_launch(a.dim == 2 ? 2 : (sizeof(R) == 8 ? 4 : 3) + (a.near_idx ? 1 : 0));
     return cudaGetLastError();
 }
 

@@ -154,6 +154,7 @@ struct EvalArgs {
     int *far_idx;       // scratch: far-branch target indices, in append order
     int *far_sorted;    // scratch: the same indices ordered by |x_last| bucket (3D)
     int *far_count;     // scratch counters (GF_SCRATCH_COUNTERS ints, zero before each evaluation)
+    int *near_idx;      // scratch (3D, may be null): near-branch target indices, in append order
     const void *btab;   // far-series table [n1][n2] (BetaEntry or BetaEntryF)
     int n1lo, n1hi, n2lo, n2hi;
     const PropEntry *prop;  // propagating indices (|alpha_n| <= k)
@@ -175,10 +176,12 @@ struct EvalArgs {
 #define GF_FAR_BUCKETS 256
 // scratch counters: [0] far count, [1..NB] bucket sizes, [NB+1..2NB] cursors,
 // [GF_WORK_SLOT] far work items handed out so far, [GF_TAIL_SLOT] the same for
-// the float-tail kernel of double-precision plans
+// the float-tail kernel of double-precision plans, [GF_NEAR_SLOT] length of the
+// near list
 #define GF_WORK_SLOT (1 + 2 * GF_FAR_BUCKETS)
 #define GF_TAIL_SLOT (2 + 2 * GF_FAR_BUCKETS)
-#define GF_SCRATCH_COUNTERS (3 + 2 * GF_FAR_BUCKETS)
+#define GF_NEAR_SLOT (3 + 2 * GF_FAR_BUCKETS)
+#define GF_SCRATCH_COUNTERS (4 + 2 * GF_FAR_BUCKETS)
 
 // A sweep of plans run as batched persistent launches: per-pass virtual-block
 // prefix sums over the pairs (device arrays of np + 1 ints), the per-pair

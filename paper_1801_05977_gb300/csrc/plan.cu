@@ -126,7 +126,7 @@ struct gf_plan_s {
     SynthArgs sa{};
     // eval scratch (far list + counter) and host-call staging, grown on demand
     std::mutex mu;
-    int *far_idx = nullptr;      // [2 * cap]: append-order list, then bucket-sorted list
+    int *far_idx = nullptr;      // [3 * cap]: far list in append order, bucket-sorted far list, near list
     int *far_count = nullptr;    // [GF_SCRATCH_COUNTERS]
     int64_t far_cap = 0;
     void *stage_x = nullptr, *stage_out = nullptr;
@@ -560,7 +560,7 @@ static gf_status ensure_scratch(gf_plan_t p, int64_t n, cudaStream_t st)
         p->far_cap = 0;
     }
     if (!p->far_count) CU(gf_dev_alloc((void **)&p->far_count, sizeof(int) * GF_SCRATCH_COUNTERS, st));
-    CU(gf_dev_alloc((void **)&p->far_idx, sizeof(int) * 2 * cap, st));
+    CU(gf_dev_alloc((void **)&p->far_idx, sizeof(int) * 3 * cap, st));
     p->far_cap = cap;
     return GF_OK;
 }
@@ -607,6 +607,7 @@ gf_status gf_eval_points(gf_plan_t p, const double *dev_xyz, int64_t n, int whic
     a.n = n;
     a.far_idx = p->far_idx;
     a.far_sorted = p->far_idx + p->far_cap;
+    a.near_idx = p->dim == 3 ? p->far_idx + 2 * p->far_cap : nullptr;
     a.far_count = p->far_count;
     a.btab = p->btab;
     a.n1lo = p->n1lo;
