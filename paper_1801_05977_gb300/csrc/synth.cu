@@ -83,8 +83,18 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
     double *A2mk = reinterpret_cast<double *>(Avf + ((TJ * Q + 3) & ~3));
     double *qq = A2mk + TJ;
     float *A2f = reinterpret_cast<float *>(qq + n);
+    // float-column data: |alpha_j|^2 - k^2 and q_b^2 as float pairs (hi, lo), g in
+    // float, and per column bit 0 = X'-integrals skipped, bit 1 = float coefficient
+    float2 *A2mkf = reinterpret_cast<float2 *>((reinterpret_cast<uintptr_t>(A2f + TJ) + 15) & ~(uintptr_t)15);
+    float2 *qqf = A2mkf + TJ;
+    float *gcol = reinterpret_cast<float *>(qqf + n);
+    int *cflag = reinterpret_cast<int *>(gcol + TJ);
     const int ncols = (a.dim == 3) ? a.M1 * a.M2 : a.M1;
-    const int col0 = blk * TJ;
+    // tiles alternately from both ends of the column range: the low frequencies
+    // (whose X'-integrals are formed, the expensive tiles) sit at both ends, so
+    // they are scheduled first and the last wave holds the cheap middle
+    const int ntiles = ncols / TJ;
+    const int col0 = ((blk & 1) ? ntiles - 1 - (blk >> 1) : (blk >> 1)) * TJ;
     const bool fcoef = sizeof(R) == 4 && a.dim == 3;
 
     load_twiddles<R>(tw, n);
@@ -101,16 +111,25 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
             A2 = x1 * x1;
         }
         A2s[t] = A2;
-        betas[t] = beta_of(a.k, A2);
+        const double2 bt = beta_of(a.k, A2);
+        betas[t] = bt;
         if (fcoef) {
-            A2mk[t] = A2 - a.k * a.k;
+            const double d = A2 - a.k * a.k;
+            A2mk[t] = d;
             A2f[t] = (float)A2;
+            const float h = (float)d;
+            A2mkf[t] = make_float2(h, (float)(d - (double)h));
+            gcol[t] = (float)bt.y;
+            cflag[t] = (bt.y > a.gskip ? 1 : 0) | (bt.y >= a.gfloat ? 2 : 0);
         }
     }
     if (fcoef)
         for (int b = threadIdx.x; b < n; b += blockDim.x) {
             const double q = (double)freq_of(b, n) * a.qs;
-            qq[b] = q * q;
+            const double q2 = q * q;
+            qq[b] = q2;
+            const float h = (float)q2;
+            qqf[b] = make_float2(h, (float)(q2 - (double)h));
         }
     __syncthreads();
     for (int i = threadIdx.x; i < TJ * Q; i += blockDim.x) {
@@ -135,20 +154,23 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
     __syncthreads();
 
     const double k2 = a.k * a.k, ik2 = 1.0 / k2;
+    // the float branch's constants, converted once
+    const float qsf = (float)a.qs, ihpanf = (float)a.ihpan, hpanf = (float)a.hpan, invVf = (float)a.invV;
     for (int i = threadIdx.x; i < TJ * n; i += blockDim.x) {
         int t = i >> lg, b = i & (n - 1);
         int col = col0 + t;
         int jl = freq_of(b, n);
-        double2 beta = betas[t];
-        if (fcoef && beta.y >= a.gfloat) {
+        if (fcoef && (cflag[t] & 2)) {
             // Split plans, evanescent column clear of Wood anomalies (g >= gfloat):
-            // the coefficient in float.  D = |xi|^2 - k^2 is formed in double (it is
-            // small near the resonance sphere) and then rounded; every other factor is
-            // O(1) in relative terms.
-            const float qf = (float)jl * (float)a.qs;
-            const float g = (float)beta.y;
+            // the coefficient in float, with no double operation.  D = |xi|^2 - k^2
+            // (small near the resonance sphere) is the sum of two float pairs, exact
+            // to ~2^-46 relative to its terms (Knuth's TwoSum), then rounded: since
+            // |D| >= 1e-6 k^2 (the resonance rule), this is below float rounding of D.
+            // Every other factor is O(1) in relative terms.
+            const float qf = (float)jl * qsf;
+            const float g = gcol[t];
             float T12f = 0.f;
-            if (beta.y <= a.gskip) {
+            if (!(cflag[t] & 1)) {
                 const float *Am = Avf + t * Q;
                 const float2 *Em = a.Ef + (size_t)b * Q;
                 float s1 = 0.f, s3 = 0.f;
@@ -178,10 +200,13 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
                 }
                 T12f = (g * s1 - qf * s3) / (g * (g * g + qf * qf));
             }
-            const float iD = 1.0f / (float)(A2mk[t] + qq[b]);
+            const float2 Ad = A2mkf[t], Qd = qqf[b];
+            const float dh = __fadd_rn(Ad.x, Qd.x), dv = __fsub_rn(dh, Ad.x);
+            const float de = __fadd_rn(__fsub_rn(Ad.x, __fsub_rn(dh, dv)), __fsub_rn(Qd.x, dv));
+            const float iD = 1.0f / __fadd_rn(dh, __fadd_rn(de, __fadd_rn(Ad.y, Qd.y)));
             const float sf = sqrtf(A2f[t] + qf * qf);
-            const int pnl = min((int)(sf * (float)a.ihpan), a.hnpan - 1);
-            const float x = (sf - ((float)pnl + 0.5f) * (float)a.hpan) * (2.0f / (float)a.hpan);
+            const int pnl = min((int)(sf * ihpanf), a.hnpan - 1);
+            const float x = (sf - ((float)pnl + 0.5f) * hpanf) * (2.0f / hpanf);
             const float2 *cc = a.hchebf + (size_t)pnl * (a.hdeg + 1);
             float b1r = 0.f, b1i = 0.f, b2r = 0.f, b2i = 0.f;
             for (int kk = a.hdeg; kk >= 1; --kk) {
@@ -194,7 +219,6 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
                 b1i = ti;
             }
             const float hr = fmaf(x, b1r, cc[0].x - b2r), hi = fmaf(x, b1i, cc[0].y - b2i);
-            const float invVf = (float)a.invV;
             const float cr = fmaf(hr, iD, T12f) * invVf, ci = hi * iD * invVf;
             if (nf == 1) {
                 buf0[t * n + b] = cmk((R)cr, (R)ci);
@@ -209,6 +233,7 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
             }
             continue;
         }
+        const double2 beta = betas[t];
         double q = (double)jl * a.qs;
         double A2 = A2s[t];
         const double2 *Am = Av + t * Q;
@@ -564,11 +589,13 @@ void synth_config_t(SynthArgs &a, int tj_max, size_t sm[3])
     typedef typename cplx_t<R>::T C;
     const int ncols = (a.dim == 3) ? a.M1 * a.M2 : a.M1;
     // per column: A_m (double2 and float), beta, |alpha|^2 (double), |alpha|^2 - k^2, its float;
-    // per b: twiddles and q_b^2; plus the two line buffers
+    // float-column data (|alpha|^2 - k^2 as a float pair, g, flags); per b: twiddles, q_b^2
+    // and its float pair; plus the two line buffers
     auto bytes = [&](int TJ) {
-        return sizeof(C) * (a.Mlast / 2) + sizeof(double) * a.Mlast +
+        return sizeof(C) * (a.Mlast / 2) + sizeof(double) * a.Mlast + sizeof(float2) * a.Mlast +
                TJ * (sizeof(double2) * a.Q + sizeof(double2) + 2 * sizeof(double) + sizeof(float)) +
-               sizeof(float) * ((TJ * a.Q + 3) & ~3) + 2 * sizeof(C) * a.nf * TJ * a.Mlast + 48;
+               TJ * (sizeof(float2) + sizeof(float) + sizeof(int)) +
+               sizeof(float) * ((TJ * a.Q + 3) & ~3) + 2 * sizeof(C) * a.nf * TJ * a.Mlast + 64;
     };
     int TJ = tj_max;
     while (TJ > 1 && (TJ > ncols || bytes(TJ) > 160 * 1024)) TJ >>= 1;
@@ -626,9 +653,25 @@ cudaError_t launch_synth_batch_t(const SynthBatch &b, cudaStream_t s)
         (e = cudaFuncSetAttribute(synth_x1_pass_batch<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)b.smem[2])) != cudaSuccess)
         return e;
-    synth_first_pass_batch<R><<<b.grid[0], 256, b.smem[0], s>>>(b.args, b.prefix[0], b.np);
-    synth_x2_pass_batch<R><<<b.grid[1], 256, b.smem[1], s>>>(b.args, b.prefix[1], b.np);
-    synth_x1_pass_batch<R><<<b.grid[2], 256, b.smem[2], s>>>(b.args, b.prefix[2], b.np);
+    // persistent grids of resident CTAs only: a CTA beyond the resident count
+    // would start its share of the work list only after another CTA had finished
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    auto resident = [&](int per, int want) {
+        if (per < 1) {
+            cudaGetLastError();
+            per = 1;
+        }
+        return want < per * nsm ? want : per * nsm;
+    };
+    int per[3] = {0, 0, 0};
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[0], synth_first_pass_batch<R>, 256, b.smem[0]);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[1], synth_x2_pass_batch<R>, 256, b.smem[1]);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[2], synth_x1_pass_batch<R>, 256, b.smem[2]);
+    synth_first_pass_batch<R><<<resident(per[0], b.grid[0]), 256, b.smem[0], s>>>(b.args, b.prefix[0], b.np);
+    synth_x2_pass_batch<R><<<resident(per[1], b.grid[1]), 256, b.smem[1], s>>>(b.args, b.prefix[1], b.np);
+    synth_x1_pass_batch<R><<<resident(per[2], b.grid[2]), 256, b.smem[2], s>>>(b.args, b.prefix[2], b.np);
     gf_count_launch(3);
     return cudaGetLastError();
 }
