@@ -278,7 +278,10 @@ gf_status gf_mlp_error_word(gf_mlp_t mlp, int *out);
  * instead (a 128 x 128 x 64 double-precision plan); their count is written to
  * *n_fallback_pairs.  k [npairs], alpha [npairs][2], offsets [npairs + 1] are host
  * memory; dev_xyz [offsets[npairs]][3] doubles and dev_out complex128 are device
- * memory.  Targets with |x3| > c get NaN (outside the surrogate's domain). */
+ * memory.  Targets with |x3| > c get NaN (outside the surrogate's domain).
+ * Stream-ordered on cuda_stream: without fallback pairs the call returns once the
+ * work is queued (the host arrays may be reused at once); fallback pairs are
+ * evaluated before it returns. */
 gf_status gf_surrogate_eval(gf_mlp_t mlp, int npairs, const double *k, const double *alpha, const int64_t *offsets,
                             const double *dev_xyz, void *dev_out, double wood_delta, const gf_trunc_t *trunc,
                             int *n_fallback_pairs, void *cuda_stream);

@@ -236,8 +236,11 @@ __global__ void surrogate_inputs_kernel(const double *x, int n, int64_t base, co
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int p = pair_of_target(off, np, base + i);
-        double t1 = x[3 * (size_t)i] - 2.0 * GF_PI * floor((x[3 * (size_t)i] + GF_PI) / (2.0 * GF_PI));
-        double t2 = x[3 * (size_t)i + 1] - 2.0 * GF_PI * floor((x[3 * (size_t)i + 1] + GF_PI) / (2.0 * GF_PI));
+        // cell reduction by a multiply (the network's features are periodic in t,
+        // so a cell choice off by one at a boundary changes nothing)
+        const double x1 = x[3 * (size_t)i], x2 = x[3 * (size_t)i + 1];
+        const double t1 = fma(-2.0 * GF_PI, floor(fma(x1, 0.5 / GF_PI, 0.5)), x1);
+        const double t2 = fma(-2.0 * GF_PI, floor(fma(x2, 0.5 / GF_PI, 0.5)), x2);
         float *o = in + 6 * (size_t)i;
         o[0] = (float)t1;
         o[1] = (float)t2;
@@ -263,24 +266,31 @@ __global__ void surrogate_assemble_kernel(const double *x, int n, int64_t base, 
             out[i] = make_double2(nan(""), nan(""));
             continue;
         }
-        const double m1 = floor((x1 + GF_PI) / (2.0 * GF_PI)), m2 = floor((x2 + GF_PI) / (2.0 * GF_PI));
-        const double t1 = x1 - 2.0 * GF_PI * m1, t2 = x2 - 2.0 * GF_PI * m2;
+        // the reduction and the lattice phase's fractional part in double (a few
+        // operations), the rest in float: the network's error (~1e-1) is far
+        // above float rounding; the singular part (targets within 2 eps of a
+        // lattice point, ~1%) stays in double
+        const double m1 = floor(fma(x1, 0.5 / GF_PI, 0.5)), m2 = floor(fma(x2, 0.5 / GF_PI, 0.5));
+        const double t1 = fma(-2.0 * GF_PI, m1, x1), t2 = fma(-2.0 * GF_PI, m2, x2);
         double ph = a1 * m1 + a2 * m2;
         ph -= rint(ph);
-        double sl, cl, sa, ca;
-        sincospi(2.0 * ph, &sl, &cl);
-        sincos(a1 * t1 + a2 * t2, &sa, &ca);
-        const double2 lat = make_double2(cl, sl);
-        const double2 lift = cmul(make_double2(ca, sa), lat);
-        const double2 L = make_double2(scale * Y[2 * (size_t)i], scale * Y[2 * (size_t)i + 1]);
-        double2 v = cmul(lift, L);
-        const double r = sqrt(t1 * t1 + t2 * t2 + x3 * x3);
-        if (r < 2.0 * eps) {
-            double sk, ck;
-            sincos(k * r, &sk, &ck);
-            const double Yc = 1.0 - smooth8((r - eps) / eps);
-            const double f = Yc * 0.25 / (GF_PI * r);
-            v = cadd(v, cmul(lat, make_double2(ck * f, sk * f)));
+        float sl, cl, sa, ca;
+        sincospif(2.0f * (float)ph, &sl, &cl);
+        const float t1f = (float)t1, t2f = (float)t2, x3f = (float)x3;
+        sincosf((float)a1 * t1f + (float)a2 * t2f, &sa, &ca);
+        const float lx = ca * cl - sa * sl, ly = ca * sl + sa * cl;  // lift
+        const float sc = (float)scale, Lx = sc * Y[2 * (size_t)i], Ly = sc * Y[2 * (size_t)i + 1];
+        double2 v = make_double2((double)(lx * Lx - ly * Ly), (double)(lx * Ly + ly * Lx));
+        const float rf = sqrtf(t1f * t1f + t2f * t2f + x3f * x3f);
+        if (rf < (float)(2.0 * eps)) {
+            const double r = sqrt(t1 * t1 + t2 * t2 + x3 * x3);
+            if (r < 2.0 * eps) {
+                double sk, ck;
+                sincos(k * r, &sk, &ck);
+                const double Yc = 1.0 - smooth8((r - eps) / eps);
+                const double f = Yc * 0.25 / (GF_PI * r);
+                v = cadd(v, cmul(make_double2(cl, sl), make_double2(ck * f, sk * f)));
+            }
         }
         out[i] = v;
     }
@@ -1041,12 +1051,14 @@ gf_status gf_surrogate_eval(gf_mlp_t m, int npairs, const double *k, const doubl
         const int64_t kChunk = 1 << 20;
         gf_status s = ensure_cap(m, (int)(total < kChunk ? total : kChunk));
         if (s != GF_OK) return s;
+        // pair offsets and parameters: stream-ordered pool memory, uploaded through
+        // the pinned staging ring (nothing here waits for the device)
         int64_t *d_off = nullptr;
         double *d_pk = nullptr;
-        CUM(cudaMalloc(&d_off, sizeof(int64_t) * (npairs + 1)));
-        CUM(cudaMalloc(&d_pk, sizeof(double) * pk.size()));
-        CUM(cudaMemcpyAsync(d_off, offsets, sizeof(int64_t) * (npairs + 1), cudaMemcpyHostToDevice, st));
-        CUM(cudaMemcpyAsync(d_pk, pk.data(), sizeof(double) * pk.size(), cudaMemcpyHostToDevice, st));
+        CUM(gf_dev_alloc((void **)&d_off, sizeof(int64_t) * (npairs + 1), st));
+        CUM(gf_dev_alloc((void **)&d_pk, sizeof(double) * pk.size(), st));
+        CUM(gf_stage_upload(d_off, offsets, sizeof(int64_t) * (npairs + 1), st));
+        CUM(gf_stage_upload(d_pk, pk.data(), sizeof(double) * pk.size(), st));
         const int blocks = m->nsm * 8;
         for (int64_t base = 0; base < total; base += kChunk) {
             const int n = (int)(total - base < kChunk ? total - base : kChunk);
@@ -1057,9 +1069,8 @@ gf_status gf_surrogate_eval(gf_mlp_t m, int npairs, const double *k, const doubl
                                                               m->scale, tr.c, tr.eps, (double2 *)dev_out + base);
             gf_count_launch(1);
         }
-        CUM(cudaStreamSynchronize(st));
-        cudaFree(d_off);
-        cudaFree(d_pk);
+        gf_dev_free(d_off, st);
+        gf_dev_free(d_pk, st);
     }
     // FFT-path fallback near Wood anomalies: overwrite those pairs' rows
     for (int p = 0; p < npairs; ++p) {
