@@ -115,7 +115,7 @@ static gf_status batch_eval_setup(gf_batch_t b, const double *x, const int64_t *
         if (b->scratch) cudaFree(b->scratch);
         b->scratch = nullptr;
         b->cap = 0;
-        CUB(cudaMalloc(&b->scratch, sizeof(int) * 2 * (size_t)(total > 0 ? total : 1)));
+        CUB(cudaMalloc(&b->scratch, sizeof(int) * 3 * (size_t)(total > 0 ? total : 1)));
         b->cap = total;
     }
     const size_t elem = b->precision == GF_FP64 ? 16 : 8;
@@ -128,6 +128,7 @@ static gf_status batch_eval_setup(gf_batch_t b, const double *x, const int64_t *
         if (s != GF_OK) return s;
         ea[p].far_idx = b->scratch + off[p];
         ea[p].far_sorted = b->scratch + b->cap + off[p];
+        ea[p].near_idx = b->scratch + 2 * b->cap + off[p];
         ea[p].far_count = b->counters + (size_t)GF_SCRATCH_COUNTERS * p;
         pre[p + 1] = pre[p] + (int)((n + 255) / 256);
     }
@@ -139,6 +140,7 @@ static gf_status batch_eval_setup(gf_batch_t b, const double *x, const int64_t *
     b->eb.nf = b->nf;
     b->eb.grid_near = pre[b->np] < b->nsm * 16 ? (pre[b->np] > 0 ? pre[b->np] : 1) : b->nsm * 16;
     b->eb.scatter_per_pair = 2;
+    b->eb.near_lists = b->nf == 1;
     b->eb.grid_scatter = b->np * 2 < b->nsm * 4 ? b->np * 2 : b->nsm * 4;
     b->eb.block_far = b->tune.far_block;
     b->eb.grid_far = b->nsm * b->tune.far_per_sm * 128 / b->tune.far_block;

@@ -368,7 +368,7 @@ __device__ __forceinline__ int batch_pair_e(const int *prefix, int np, int vb)
     return lo;
 }
 
-template <typename R, int NF>
+template <typename R, int NF, int MODE = 0>
 __global__ void __launch_bounds__(256) near3d_batch(const EvalArgs *args, const int *prefix, int np)
 {
     __shared__ int hist[GF_FAR_BUCKETS];
@@ -380,11 +380,35 @@ __global__ void __launch_bounds__(256) near3d_batch(const EvalArgs *args, const 
         for (int b = threadIdx.x; b < GF_FAR_BUCKETS; b += blockDim.x) hist[b] = 0;
         __syncthreads();
         const int64_t base = (int64_t)(vb - prefix[p]) * blockDim.x;
-        near3d_tiles<R, NF, 0>(sa, base, sa.n + blockDim.x, hist);
+        near3d_tiles<R, NF, MODE>(sa, base, sa.n + blockDim.x, hist);
         __syncthreads();
         for (int b = threadIdx.x; b < GF_FAR_BUCKETS; b += blockDim.x)
             if (hist[b]) atomicAdd(&sa.far_count[1 + b], hist[b]);
         __syncthreads();
+    }
+}
+
+// Batched near targets from the pairs' near lists (filled by a MODE-1
+// near3d_batch pass): every CTA walks the pairs in order, and within a pair the
+// list is spread over the grid starting at a CTA that rotates by the previous
+// pairs' block counts, so that small lists land on different CTAs.
+template <typename R, int NF>
+__global__ void __launch_bounds__(256) near3d_list_batch(const EvalArgs *args, int np)
+{
+    __shared__ EvalArgs sa;
+    int rot = 0;
+    for (int p = 0; p < np; ++p) {
+        __syncthreads();
+        if (threadIdx.x == 0) sa = args[p];
+        __syncthreads();
+        const int count = sa.far_count[GF_NEAR_SLOT];
+        const double ih1 = 1.0 / sa.h1, ih2 = 1.0 / sa.h2, ih3 = 1.0 / sa.h3;
+        const int cta = (int)((blockIdx.x + (unsigned)rot) % gridDim.x);
+        for (int j = cta * blockDim.x + threadIdx.x; j < count; j += gridDim.x * blockDim.x) {
+            const int64_t i = sa.near_idx[j];
+            near_point<R, NF>(sa, i, sa.x[3 * i], sa.x[3 * i + 1], sa.x[3 * i + 2], ih1, ih2, ih3);
+        }
+        rot = (int)((rot + (count + blockDim.x - 1) / blockDim.x) % gridDim.x);
     }
 }
 
@@ -1889,7 +1913,22 @@ template <typename R>
 cudaError_t launch_eval_batch_t(const EvalBatch &b, cudaStream_t s)
 {
     if (b.nf == 1) {
-        near3d_batch<R, 1><<<b.grid_near, 256, 0, s>>>(b.args, b.prefix, b.np);
+        if (b.near_lists) {
+            // classification, then the near targets in full warps
+            int per = 0, dev = 0, nsm = 1;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, near3d_list_batch<R, 1>, 256, 0) != cudaSuccess ||
+                per < 1) {
+                cudaGetLastError();
+                per = 1;
+            }
+            near3d_batch<R, 1, 1><<<b.grid_near, 256, 0, s>>>(b.args, b.prefix, b.np);
+            near3d_list_batch<R, 1><<<per * nsm, 256, 0, s>>>(b.args, b.np);
+            gf_count_launch(1);
+        } else {
+            near3d_batch<R, 1><<<b.grid_near, 256, 0, s>>>(b.args, b.prefix, b.np);
+        }
         far_scatter_batch<<<b.grid_scatter, 256, 0, s>>>(b.args, b.np, b.scatter_per_pair);
         far3d_batch<R, 1><<<b.grid_far, b.block_far, 0, s>>>(b.args, b.np);
     } else {

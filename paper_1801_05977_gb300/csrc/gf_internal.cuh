@@ -200,6 +200,7 @@ struct EvalBatch {
     int nf;
     int grid_near, grid_scatter, grid_far, block_far;
     int scatter_per_pair;
+    bool near_lists;        // per-pair near lists present (EvalArgs::near_idx): classify, then near3d_list_batch
 };
 
 // launch helpers implemented in synth.cu / eval.cu
