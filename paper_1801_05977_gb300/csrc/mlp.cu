@@ -307,14 +307,19 @@ __global__ void surrogate_assemble_kernel(const double *x, int n, int64_t base, 
 // 6 input floats and 2 output floats.
 // ---------------------------------------------------------------------------
 namespace fused {
-// SiLU for inference: z sigmoid(z) = (z/2)(1 + tanh(z/2)) with the hardware tanh
-// (one MUFU operation; absolute error of tanh below 2^-10.7, under bf16 rounding)
-__device__ __forceinline__ float silu_tanh(float z)
+// SiLU of two pre-activations on bf16 pairs: z rounded to bf16, halved
+// (exact), one hardware tanh for both (tanh.approx.bf16x2) and one packed
+// fma, z/2 + (z/2) tanh(z/2) = z sigmoid(z).  Returns the bf16 pair (z0 in the
+// low half), the layout of the next layer's activations; the extra rounding of
+// z to bf16 is of the size of the activation's own bf16 rounding.
+__device__ __forceinline__ uint32_t silu2_bf16(float z0, float z1)
 {
-    const float hz = 0.5f * z;
-    float th;
-    asm("tanh.approx.f32 %0, %1;" : "=f"(th) : "f"(hz));
-    return fmaf(hz, th, hz);
+    uint32_t zb, hz, th, r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(zb) : "f"(z1), "f"(z0));
+    asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(hz) : "r"(zb), "r"(0x3F003F00u));
+    asm("tanh.approx.bf16x2 %0, %1;" : "=r"(th) : "r"(hz));
+    asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(r) : "r"(hz), "r"(th), "r"(hz));
+    return r;
 }
 
 constexpr int ROWS = 128, NT = 2;
@@ -549,16 +554,14 @@ __global__ void __launch_bounds__(fused::THREADS, 1) mlp_infer_fused(fused::Args
                         const float4 bb = *reinterpret_cast<const float4 *>(bias + j + e);  // shared, broadcast
                         const float z[4] = {__uint_as_float(v[e]) + bb.x, __uint_as_float(v[e + 1]) + bb.y,
                                             __uint_as_float(v[e + 2]) + bb.z, __uint_as_float(v[e + 3]) + bb.w};
-                        const __nv_bfloat162 h01 = __floats2bfloat162_rn(silu_tanh(z[0]), silu_tanh(z[1]));
-                        const __nv_bfloat162 h23 = __floats2bfloat162_rn(silu_tanh(z[2]), silu_tanh(z[3]));
-                        pk[e >> 1] = (uint32_t)__bfloat16_as_ushort(h01.x) | ((uint32_t)__bfloat16_as_ushort(h01.y) << 16);
-                        pk[(e >> 1) + 1] =
-                            (uint32_t)__bfloat16_as_ushort(h23.x) | ((uint32_t)__bfloat16_as_ushort(h23.y) << 16);
+                        const uint32_t h01 = silu2_bf16(z[0], z[1]), h23 = silu2_bf16(z[2], z[3]);
+                        pk[e >> 1] = h01;
+                        pk[(e >> 1) + 1] = h23;
                         if (l == 3) {
                             const float4 w0 = *reinterpret_cast<const float4 *>(W5s + j + e);
                             const float4 w1 = *reinterpret_cast<const float4 *>(W5s + HID + j + e);
-                            const float h[4] = {__bfloat162float(h01.x), __bfloat162float(h01.y), __bfloat162float(h23.x),
-                                                __bfloat162float(h23.y)};
+                            const float h[4] = {__uint_as_float(h01 << 16), __uint_as_float(h01 & 0xFFFF0000u),
+                                                __uint_as_float(h23 << 16), __uint_as_float(h23 & 0xFFFF0000u)};
                             y0 = fmaf(h[0], w0.x, fmaf(h[1], w0.y, fmaf(h[2], w0.z, fmaf(h[3], w0.w, y0))));
                             y1 = fmaf(h[0], w1.x, fmaf(h[1], w1.y, fmaf(h[2], w1.z, fmaf(h[3], w1.w, y1))));
                         }
