@@ -437,7 +437,7 @@ def run_batched(args, dev, flush):
     total = npairs * per
     return {"value": total / (ms_b * 1e-3), "unit": "evals/s", "ms_per_step": ms_b, "pairs": npairs,
             "targets_per_pair": per, "grid_points_per_pair": "clamp(nextpow2(ceil(32k)),32,256)^2 x 64",
-            "precision": "f32/f64 split", "launch": "one CUDA graph: 3 synthesis + memset + 3 eval kernels",
+            "precision": "f32/f64 split", "launch": "one CUDA graph: 3 synthesis + memset + 4 eval kernels (classification, near list, far sort, far)",
             "graph_kernels_per_step": graph_launches, "tuning": {"tj_max": tune[0], "far_block": tune[1],
                                                                   "far_ctas_per_sm": tune[2]},
             "sequential_plain": {"value": total / t_seq, "s_per_sweep": t_seq,
@@ -609,6 +609,17 @@ def run_configs(args, dev, flush):
     return res
 
 
+def run_batch_only(args):
+    """Profiling helper: the batched-sweep leg alone (plans, autotune, graph
+    steps and the pair-after-pair comparison), its result line printed."""
+    import torch
+
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    print(json.dumps({"batched": run_batched(args, dev, flush)}))
+    return 0
+
+
 def run_mlp_forward(args):
     """Profiling helper: two fused forward passes of the surrogate network on
     `mlp_forward_only` random samples."""
@@ -645,6 +656,7 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate leg")
     ap.add_argument("--no-configs", action="store_true", help="skip the 2D and Maxwell configurations")
     ap.add_argument("--mlp-forward-only", type=int, default=0, help="profiling: only run the fused network forward")
+    ap.add_argument("--batch-only", action="store_true", help="profiling: only run the batched-sweep leg")
     ap.add_argument("--sur-train-pairs", type=int, default=1000)
     ap.add_argument("--sur-train-per-pair", type=int, default=10_000)
     ap.add_argument("--sur-epochs", type=int, default=2)
@@ -656,6 +668,8 @@ def main():
         return run_reference(args)
     if args.mlp_forward_only:
         return run_mlp_forward(args)
+    if args.batch_only:
+        return run_batch_only(args)
     return run_gpu(args)
 
 
