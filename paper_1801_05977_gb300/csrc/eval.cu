@@ -1,15 +1,19 @@
 // Evaluation at targets (Algorithms 1-3, step 2 "Calculation").
 //
-//  near kernel  (|x_last| <= c): reduce to the unit cell (step 2c), gather the
+//  near branch  (|x_last| <= c): reduce to the unit cell (step 2c), gather the
 //               4^d stencil of the padded grid with separable cubic Lagrange
 //               weights (step 2d), add the singular part back in double
-//               precision (step 2e), apply the quasi-periodic phase (step 2f);
-//               far targets are appended to a scratch list instead.
-//  far kernel   (|x_last| > c, step 2b): the eigen-series (ei)/(he) (and its
+//               precision (step 2e), apply the quasi-periodic phase (step 2f).
+//               3D evaluations first classify the targets (a far list sorted
+//               by |x3| bucket, a near list), then run the near targets from
+//               their list in full warps.
+//  far branch   (|x_last| > c, step 2b): the eigen-series (ei)/(he) (and its
 //               second derivatives for the Maxwell tensor), truncated to
 //               |alpha_n|^2 <= k^2 + (T/|x_last|)^2, one thread per target,
 //               the 32 lanes of a warp walking the same index set so that the
-//               per-index table of beta_n is read by broadcast.
+//               per-index table of beta_n is read by broadcast; for
+//               double-precision plans two kernels, the double and float-float
+//               core sums and the float tails, run side by side.
 #include <math_constants.h>
 
 #include "gf_internal.cuh"
@@ -1051,19 +1055,22 @@ __device__ __forceinline__ void seg_horner_f32(int lo, int hi, float a2f, float 
 // Propagating n (|alpha_n| < k, a handful) are summed from a list.  For the
 // evanescent n, beta = i b and 1/beta = -i/b; with w = e^{-bz}/b (real) the row
 // n1 contributes -i sum_{n2} w e^{i(c1 t1 + c2 t2)}.  Every row is summed
-// relative to the fixed anchor n2 = N0: the double core outwards from N0 by
-// two Reinsch recurrences, the float tails by Horner's rule in v = e^{i t2}
-// from their first index, moved to N0 by a float phase.  The row phase
-// e^{i c1 t1} follows a recurrence over the rows and e^{i(alpha_2 + N0) t2} is
-// applied once per target.  Each lane keeps only its own truncation set
+// relative to the fixed anchor n2 = N0: the core outwards from N0 by two
+// Reinsch recurrences, the float tails by Horner's rule in v = e^{i t2} from
+// their first index, moved to N0 by a float phase.  The row phase e^{i c1 t1}
+// follows a recurrence over the rows and e^{i(alpha_2 + N0) t2} is applied once
+// per target.  Each lane keeps only its own truncation set
 // |alpha_n|^2 <= k^2 + (T/z)^2.
 //
-// Precision: the terms of the warp's core disk |alpha_n|^2 <= k^2 + (Y0/z_min)^2
-// (b z_min <= Y0 = 18, z_min the warp's smallest |x3|) are summed in double
-// with the table-driven exponential; the remaining terms, each below
-// e^{-18} = 1.5e-8 of the leading ones and all together below
-// 2 pi e^{-18}/z of the series scale, are summed in float: their float
-// rounding (< 1e-5 relative) contributes < 2e-12 of the series scale.
+// Precision, by term size (every term is at most e^{-(b - bmin) z} of the
+// largest): the warp's core disk |alpha_n|^2 <= k^2 + (Y0/z_min)^2 (b z_min <=
+// Y0 = 18, z_min the warp's smallest |x3|) is summed by the recurrences, its
+// outer band (b >= bmin + FF_GAP/z_min, Helmholtz) in float-float and its inner
+// terms in double with the table-driven exponential; the remaining terms, each
+// below e^{-18} = 1.5e-8 of the leading ones and all together below
+// 2 pi e^{-18}/z of the series scale, are summed in float (by far3d_tail, or
+// here when TAILS): their float rounding (< 1e-5 relative) contributes < 2e-12
+// of the series scale.
 // ---------------------------------------------------------------------------
 constexpr double FAR_CORE_Y0 = 18.0;
 
