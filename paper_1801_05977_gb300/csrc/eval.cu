@@ -1554,9 +1554,12 @@ __device__ void far3d_f32_chunk(const EvalArgs &a, int w, int count, int slab, i
             x2 = a.x[3 * (size_t)idx + 1];
             x3 = a.x[3 * (size_t)idx + 2];
         }
-        double t1d, m1, t2d, m2;
-        reduce_period(x1, t1d, m1);
-        reduce_period(x2, t2d, m2);
+        // cell reduction by a multiply and a floor: the series is the same for any
+        // decomposition x = 2 pi m + t (e^{i alpha_n . x} = e^{i alpha_n . t}
+        // e^{i 2 pi alpha . m}), so the exact cell decision of the near branch
+        // is not needed here
+        const double m1 = floor(fma(x1, INV_TWO_PI, 0.5)), m2 = floor(fma(x2, INV_TWO_PI, 0.5));
+        const double t1d = fma(-TWO_PI, m1, x1), t2d = fma(-TWO_PI, m2, x2);
         const float z = fabsf((float)x3), t1 = (float)t1d, t2 = (float)t2d, sg = x3 >= 0.0 ? 1.f : -1.f;
         const float Tz = (float)a.T / z;
         const float R2f = valid ? (float)(a.k * a.k) + Tz * Tz : 0.f;
