@@ -722,8 +722,13 @@ __device__ __forceinline__ FarLane far_lane(const EvalArgs &a, int slot, int cou
         x2 = a.x[3 * (size_t)L.idx + 1];
         x3 = a.x[3 * (size_t)L.idx + 2];
     }
-    reduce_period(x1, L.t1, L.m1);
-    reduce_period(x2, L.t2, L.m2);
+    // cell reduction by a multiply and a floor: the series does not depend on
+    // the decomposition x = 2 pi m + t, so the near branch's exact cell decision
+    // is not needed here
+    L.m1 = floor(fma(x1, INV_TWO_PI, 0.5));
+    L.m2 = floor(fma(x2, INV_TWO_PI, 0.5));
+    L.t1 = fma(-TWO_PI, L.m1, x1);
+    L.t2 = fma(-TWO_PI, L.m2, x2);
     L.z = fabs(x3);
     L.sg = x3 >= 0.0 ? 1.0 : -1.0;
     // explicitly rounded (no contraction): R2 decides the row split, which the
