@@ -130,10 +130,14 @@ size_t gf_grid_bytes(gf_plan_t plan);
  *   dev_xyz   n * dim doubles, row-major [n][dim], device memory
  *   which     GF_OUT_G (2D), GF_OUT_GD (3D Helmholtz), GF_OUT_MAXWELL6/7 (Maxwell)
  *   dev_out   n * entries complex values, [n][entries], device memory
- * The plan keeps a per-plan scratch list of far-branch targets (grown on
- * demand, synchronously); calls on the same plan must therefore not overlap
- * in time (issue them on one stream).  Non-finite targets give NaN outputs;
- * targets on a lattice point give non-finite outputs.
+ * The plan keeps per-plan scratch lists of far- and near-branch targets (grown
+ * on demand, synchronously); calls on the same plan must therefore not overlap
+ * in time (issue them on one stream).  For 3D double-precision Helmholtz plans
+ * part of the far series runs on a side stream that the library owns (one per
+ * device): it waits for an event recorded on cuda_stream and cuda_stream waits
+ * for its completion, so the call keeps the ordinary stream semantics (also
+ * under CUDA-graph capture of cuda_stream).  Non-finite targets give NaN
+ * outputs; targets on a lattice point give non-finite outputs.
  * Errors: GF_ERR_ARG (n < 0, NULL pointers with n > 0, `which` not valid for the
  * plan), GF_ERR_NOMEM, GF_ERR_CUDA. */
 gf_status gf_eval_points(gf_plan_t plan, const double *dev_xyz, int64_t n, int which,
