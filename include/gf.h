@@ -135,8 +135,8 @@ size_t gf_grid_bytes(gf_plan_t plan);
  * in time (issue them on one stream).  For 3D double-precision Helmholtz plans
  * part of the far series runs on a side stream that the library owns (one per
  * device): it waits for an event recorded on cuda_stream and cuda_stream waits
- * for its completion, so the call keeps the ordinary stream semantics (also
- * under CUDA-graph capture of cuda_stream).  Non-finite targets give NaN
+ * for its completion, so the call keeps the ordinary stream semantics.
+ * Non-finite targets give NaN
  * outputs; targets on a lattice point give non-finite outputs.
  * Errors: GF_ERR_ARG (n < 0, NULL pointers with n > 0, `which` not valid for the
  * plan), GF_ERR_NOMEM, GF_ERR_CUDA. */
