@@ -54,6 +54,8 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 def disk_count(R2: np.ndarray, alpha) -> int:
     """Number of n in Z^2 with |alpha + n|^2 <= R2, summed over the entries of R2."""
+    if R2.size == 0:
+        return 0
     R = np.sqrt(R2.max())
     total = 0
     for n1 in range(int(np.floor(-alpha[0] - R)) - 1, int(np.ceil(-alpha[0] + R)) + 2):
