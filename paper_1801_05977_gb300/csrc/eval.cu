@@ -873,7 +873,7 @@ __device__ __forceinline__ void reinsch_seg(RState<NH> &st, const BetaEntry *__r
     const float zf = (float)z;
     const float df = (float)dir;
     const double dd = (double)dir;
-#pragma unroll 3
+#pragma unroll 2
     for (int i = 0; i < count; ++i, n2 += dir, c2f += df) {
         const BetaEntry be = row[n2];
         const bool ok = fmaf(c2f, c2f, c1sq) <= R2f && be.bf != 0.f;
@@ -1048,7 +1048,7 @@ __device__ __forceinline__ void seg_horner_f32(int lo, int hi, float a2f, float 
 #pragma unroll
     for (int e = 0; e < NH; ++e) acc[e][0] = acc[e][1] = 0.f;
     float c2 = a2f + (float)hi;
-#pragma unroll 4
+#pragma unroll 2
     for (int n2 = hi; n2 >= lo; --n2, c2 -= 1.0f) horner_step_f32<NH>(c2, q0, zl2, cv, sv, acc);
 }
 
