@@ -47,7 +47,7 @@ FAR_CORE_Y0 = 18.0
 FAR_FF_GAP = 8.0
 # DRAM bytes of one far3d_f64 launch on this workload: ncu (dram__bytes_read.sum
 # + dram__bytes_write.sum) of a 2e5-target launch, scaled by the far targets
-FAR_TRAFFIC_BYTES = 9.977344e6 * 5
+FAR_TRAFFIC_BYTES = 9.978112e6 * 5
 # FP64 peak from unit counts and clock: 152 SMs x 2 FP64 lanes/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
