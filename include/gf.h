@@ -50,7 +50,7 @@ typedef enum {
     GF_ERR_NOMEM = 4,        /* device allocation failed */
     GF_ERR_CUDA = 5,         /* a CUDA runtime call failed */
     GF_ERR_TIMEOUT = 6,      /* a bounded device wait ran out */
-    GF_ERR_UNSUPPORTED = 7   /* valid request this build does not implement */
+    GF_ERR_UNSUPPORTED = 7   /* valid request the library does not implement */
 } gf_status;
 
 enum { GF_FP64 = 0, GF_FP32_SPLIT = 1 };          /* gf_trunc_t.precision */
