@@ -35,21 +35,32 @@ from paper_1801_05977_gb300 import workloads as W  # noqa: E402
 K_WAVE, ALPHA, GRID, N_TARGETS = 2.5, (0.1, 0.3), (128, 128, 64), 1_000_000
 METRIC = "G_d evals/s on 1 GB300 at stated rel err; batched & surrogate vs plain FFT path"
 WORKLOAD = "3D doubly quasi-periodic G_d, k=2.5, alpha=(0.1,0.3), grid 128x128x64, 1e6 uniform targets"
-# The far series of a double-precision plan: the core (b|x3| <= Y0 = 18) is
-# summed in double for the terms within e^-8 of the largest (b <= bmin + 8/|x3|,
-# the double band) and in float-float on the FP32 pipe beyond (the float-float
-# band); the rest (up to the truncation) is the float tail.  Algorithmic FP64
-# work of a double-band term: y = b|x3| + ln b (1 FMA), r = y - y_j (1 add),
-# e^{-r} to degree 3 (3 FMAs; table step 1/4096), one Reinsch step (2 FMAs +
-# 1 add) = 14 flops (an FMA counts 2).
+# The far series of a double-precision plan (three precision tiers by term
+# size): the core (b|x3| <= Y0 = 18) is summed in double for the terms within
+# e^-8 of the largest (b <= bmin + 8/|x3|, the double band) and in float-float
+# on the FP32 pipe beyond (the float-float band); the rest (up to the
+# truncation) is the float tail, summed by a concurrent kernel.  Work per term
+# as the kernels implement it (an FMA counts 2 flops):
+#   double band: y = b|x3| + ln b (1 FMA), r = y - y_j (1 add), e^{-r} to degree
+#     3 (3 FMAs; table step 1/4096), one Reinsch step (2 FMAs + 1 add): 14 FP64 flops;
+#   float-float band: the same steps in float pairs (TwoSum / FMA products):
+#     86 FP32 instructions of which 12 FMAs = 98 FP32 flops;
+#   float tail: one Horner step, b^2 = c1^2 + c2^2 - k^2 (1 FMA), b = b^2 rsqrt(b^2)
+#     (1 mul), -b|x3| log2 e (1 mul), w = e/b (1 mul), complex step (2 FMA +
+#     1 FMA + 1 mul), the test and the index (2): 14 FP32 flops (and 2 MUFU ops,
+#     not counted).
 FP64_TERM_FLOPS = 14
+FF_TERM_FLOPS = 98
+TAIL_TERM_FLOPS = 14
 FAR_CORE_Y0 = 18.0
 FAR_FF_GAP = 8.0
 # DRAM bytes of one far3d_f64 launch on this workload: ncu (dram__bytes_read.sum
 # + dram__bytes_write.sum) of a 2e5-target launch, scaled by the far targets
 FAR_TRAFFIC_BYTES = 9.978112e6 * 5
-# FP64 peak from unit counts and clock: 152 SMs x 2 FP64 lanes/clk x 2 flop x 2.07 GHz
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# unit-count peaks, reported beside the measured ones (152 SMs, 2.07 GHz):
+# FP64 2 FMA/clk/SM, FP32 128 FMA/clk/SM
+FP64_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 def disk_count(R2: np.ndarray, alpha) -> int:
@@ -188,50 +199,119 @@ def host_cores() -> int:
 
 
 # --------------------------------------------------------------------------- CPU oracle leg
-def oracle_sample(n_sample: int, seed: int = 0):
-    """Time the FP64 oracle on this host: full plan (coefficients + naive DFT)
-    and n_sample targets of the workload.  Returns (value evals/s, dict)."""
+def _oracle_problem():
     from oracle import oracle as O
-    pb = O.Problem(dim=3, k=K_WAVE, alpha=ALPHA, M=GRID)
-    O.lib()
+    return O, O.Problem(dim=3, k=K_WAVE, alpha=ALPHA, M=GRID)
+
+
+def oracle_full(x: np.ndarray):
+    """The FP64 oracle as it stands, on all of this host's cores: the full plan
+    (coefficients + naive O(M^2) DFT) and every target of the workload, the near
+    and far branches timed apart; then one thread on a bounded sample (2000 near,
+    200 far targets).  Returns (oracle output (n, 1), timing dict)."""
+    O, pb = _oracle_problem()
+    cores = O.set_threads(host_cores())
     t0 = time.perf_counter()
     g = O.grid(pb)
     t_plan = time.perf_counter() - t0
+    far = np.abs(x[:, 2]) > pb.c
+    ref = np.empty((x.shape[0], 1), dtype=np.complex128)
+    t0 = time.perf_counter()
+    ref[~far] = O.evaluate(pb, g, x[~far], O.OUT_GD)
+    t_near = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ref[far] = O.evaluate(pb, g, x[far], O.OUT_GD)
+    t_far = time.perf_counter() - t0
+    n_near, n_far = int((~far).sum()), int(far.sum())
+    O.set_threads(1)
+    xs_near, xs_far = x[~far][:2000], x[far][:200]
+    t0 = time.perf_counter()
+    O.evaluate(pb, g, xs_near, O.OUT_GD)
+    t1_near = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    O.evaluate(pb, g, xs_far, O.OUT_GD)
+    t1_far = time.perf_counter() - t0
+    O.set_threads(cores)
+    info = {"cores": cores, "t_plan_s": t_plan, "t_near_s": t_near, "t_far_s": t_far, "n_near": n_near,
+            "n_far": n_far, "near_evals_per_s": n_near / t_near, "far_evals_per_s": n_far / t_far,
+            "eval_evals_per_s": x.shape[0] / (t_near + t_far),
+            "one_thread": {"near_evals_per_s": xs_near.shape[0] / t1_near,
+                           "far_evals_per_s": xs_far.shape[0] / t1_far,
+                           "sample": f"{xs_near.shape[0]} near + {xs_far.shape[0]} far targets"}}
+    return ref, info
+
+
+def oracle_sample(n_sample: int, seed: int = 0):
+    """One step of the reference arm: the full plan (coefficients + naive DFT)
+    and a sample of n_sample of the workload's targets on all host cores.
+    Returns (the whole workload's evals/s estimated from the step: plan + the
+    sample's evaluation time scaled to 1e6 targets, measured step seconds, info)."""
+    O, pb = _oracle_problem()
+    cores = O.set_threads(host_cores())
     x = W.targets_3d(N_TARGETS, seed=seed)
     rng = np.random.default_rng(seed)
     xs = x[rng.choice(N_TARGETS, n_sample, replace=False)]
     t0 = time.perf_counter()
+    g = O.grid(pb)
+    t_plan = time.perf_counter() - t0
+    t1 = time.perf_counter()
     O.evaluate(pb, g, xs, O.OUT_GD)
-    t_eval = time.perf_counter() - t0
-    step = t_plan + t_eval * (N_TARGETS / n_sample)
-    cores = int(os.environ.get("OMP_NUM_THREADS", host_cores()))
-    info = {"t_plan_s": t_plan, "t_eval_sample_s": t_eval, "sample_targets": n_sample, "cores": cores}
-    return N_TARGETS / step, info
+    t_eval = time.perf_counter() - t1
+    step_s = time.perf_counter() - t0
+    est = N_TARGETS / (t_plan + t_eval * (N_TARGETS / n_sample))
+    return est, step_s, {"t_plan_s": t_plan, "t_eval_sample_s": t_eval, "sample_targets": n_sample, "cores": cores}
 
 
 def run_reference(args):
     world, rank, _ = dist_setup()
     if rank != 0:
         return 0
-    vals = []
+    vals, steps_s = [], []
     info = {}
     for i in range(args.warmup + args.steps):
-        v, info = oracle_sample(args.ref_sample, seed=0)
+        v, st, info = oracle_sample(args.ref_sample, seed=0)
         if i >= args.warmup:
             vals.append(v)
+            steps_s.append(st)
     value = float(np.mean(vals))
+    sample = (f"per step: the full plan (coefficients + naive O(M^2) DFT) and {args.ref_sample} of the 1e6 "
+              f"targets, all host cores; value = 1e6 / (plan time + the sample's eval time x 1e6/"
+              f"{args.ref_sample}); ms_per_step is the measured time of that step")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * N_TARGETS / value,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(steps_s)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "global_batch": N_TARGETS, "precision": "fp64 CPU oracle"},
+        "config": {"workload": WORKLOAD, "global_batch": N_TARGETS, "targets_per_step": args.ref_sample,
+                   "precision": "fp64 CPU oracle"},
         "cpu_baseline": {"value": value, "unit": "evals/s", "cores": info["cores"], "kind": "oracle",
-                         "sample": f"full plan (coefficients + naive O(M^2) DFT) + {args.ref_sample} of the "
-                                   f"1e6 targets per step, eval time scaled to 1e6"},
+                         "sample": sample},
         "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
     return 0
+
+
+def measure_peaks(dev):
+    """FP64 and FP32 FMA rates of this GPU (gf_peak_probe, CUDA events, best of 3
+    launches of about 40 ms each after one warm-up)."""
+    import torch
+
+    from paper_1801_05977_gb300 import gf
+
+    sink = torch.zeros(2, dtype=torch.float64, device=dev)
+    out = {}
+    for name, pipe, iters in (("fp64", gf.GF_PROBE_FP64, 1500), ("fp32", gf.GF_PROBE_FP32, 80000)):
+        best = 0.0
+        for i in range(4):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fl = gf.peak_probe(pipe, iters, sink)
+            e1.record()
+            torch.cuda.synchronize()
+            if i > 0:
+                best = max(best, fl / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+        out[name] = best
+    return out
 
 
 # --------------------------------------------------------------------------- GPU leg
@@ -318,18 +398,28 @@ def run_gpu(args):
     clocks = clk.summary()
     e2e_s = max_over_ranks([np.mean(e2e_t) if e2e_t else float("nan")], dev)[0]
 
-    # roofline of the dominant kernel (the double-precision far-series kernel)
+    # roofline of the dominant kernels (the far series of the double-precision plan:
+    # far3d_f64 and its concurrent float-tail kernel far3d_tail), two pipes
     far_ms = float(np.mean([p[3] for p in ph64]))
     near_ms = float(np.mean([p[2] for p in ph64]))
     synth_ms = float(np.mean([p[0] for p in ph64]))
     terms, core_terms, bands = far_terms(x_np, K_WAVE, ALPHA, 0.6, tol64)
-    far_flops = world * FP64_TERM_FLOPS * bands["double"]
-    achieved = far_flops / (far_ms * 1e-3) / 1e12
-    peak_fp64 = FP64_PEAK_TFLOPS
+    tail_terms = terms - core_terms
+    peaks = measure_peaks(dev)
+    w64 = world * FP64_TERM_FLOPS * bands["double"]
+    w32 = world * (FF_TERM_FLOPS * bands["float-float"] + TAIL_TERM_FLOPS * tail_terms)
+    t_far = far_ms * 1e-3
+    # FP64-equivalent work: FP32 flops weighted by the measured rate ratio, so that
+    # frac = W64 / (P64 t) + W32 / (P32 t), the share of the far phase the two pipes
+    # would need for the term work at their measured rates
+    w_eq = w64 + w32 * (peaks["fp64"] / peaks["fp32"])
+    achieved = w_eq / t_far / 1e12
+    frac64, frac32 = w64 / t_far / 1e12 / peaks["fp64"], w32 / t_far / 1e12 / peaks["fp32"]
 
     # split-precision error vs the double-precision path on this workload
     d = (out32.to(torch.complex128) - out64).abs()
     split_err = float(d.max() / out64.abs().max())
+    g64, g32 = out64.cpu().numpy(), out32.to(torch.complex128).cpu().numpy()
 
     batched = None if args.no_batch else run_batched(args, dev, flush)
     surrogate = None if args.no_surrogate else run_surrogate(args, dev)
@@ -338,12 +428,24 @@ def run_gpu(args):
         if world > 1:
             dist.destroy_process_group()
         return 0
-    cpu = None
+    cpu, err_oracle = None, None
     if world == 1 and not args.no_cpu_baseline:
-        v, info = oracle_sample(args.cpu_sample, seed=0)
-        cpu = {"value": v, "unit": "evals/s", "cores": info["cores"], "kind": "oracle",
-               "sample": f"full plan (coefficients + naive O(M^2) DFT, {info['t_plan_s']:.1f} s) + "
-                         f"{args.cpu_sample} of the 1e6 targets ({info['t_eval_sample_s']:.1f} s), scaled to 1e6"}
+        ref, info = oracle_full(x_np)
+        t_step = info["t_plan_s"] + info["t_near_s"] + info["t_far_s"]
+        cpu = {"value": n_targets / t_step, "unit": "evals/s", "cores": info["cores"], "kind": "oracle",
+               "sample": f"the whole workload, once: full plan (coefficients + naive O(M^2) DFT, "
+                         f"{info['t_plan_s']:.1f} s) + all {n_targets} targets ({info['n_near']} near in "
+                         f"{info['t_near_s']:.2f} s, {info['n_far']} far in {info['t_far_s']:.1f} s)",
+               "eval_only": info["eval_evals_per_s"], "near_evals_per_s": info["near_evals_per_s"],
+               "far_evals_per_s": info["far_evals_per_s"], "one_thread": info["one_thread"],
+               "plan_s_naive_dft": info["t_plan_s"]}
+        sc = np.maximum(np.abs(ref), 1e-6 * np.abs(ref).max())
+        err_oracle = {"targets": n_targets,
+                      "fp64": {"pointwise_max": float((np.abs(g64 - ref) / sc).max()),
+                               "normwise": float(np.abs(g64 - ref).max() / np.abs(ref).max())},
+                      "split": {"pointwise_max": float((np.abs(g32 - ref) / sc).max()),
+                                "normwise": float(np.abs(g32 - ref).max() / np.abs(ref).max())},
+                      "note": "every target of the step against the FP64 oracle; pointwise floor 1e-6 max|G|"}
     line = {
         "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms64, "higher_is_better": True, "scaling": "weak",
@@ -357,17 +459,23 @@ def run_gpu(args):
                   "phases_ms": {"synthesis": float(np.mean([p[0] for p in ph32])),
                                 "near": float(np.mean([p[2] for p in ph32])),
                                 "far": float(np.mean([p[3] for p in ph32]))}},
-        "roofline": {"bound": "alu", "kernel": "far3d_f64", "achieved": achieved, "peak": peak_fp64,
-                     "unit": "TFLOP/s", "frac": achieved / peak_fp64,
+        "roofline": {"bound": "alu", "kernel": "far3d_f64 + far3d_tail (concurrent)", "achieved": achieved,
+                     "peak": peaks["fp64"], "unit": "TFLOP/s (FP64-equivalent)", "frac": achieved / peaks["fp64"],
                      "traffic": FAR_TRAFFIC_BYTES if n_targets == 1_000_000 and FAR_TRAFFIC_BYTES else None,
-                     "algorithmic_flops": far_flops, "core_terms_by_band": bands,
-                     "note": "FP64 pipe bound (ncu: 82% of the FP64 peak while active, FP32 pipe 18%); achieved = "
-                             "algorithmic FP64 flops of the double-band core terms (b <= bmin + 8/|x3|, 14 flops "
-                             "per term, FMA = 2 flops) / far-phase time; the float-float band (FP32 pipe) and the "
-                             "float tail (concurrent kernel) are not counted, and the per-row and per-target FP64 "
-                             "work (row sums, propagating terms, set-up) is the rest of the FP64 pipe time; peak "
-                             "from unit counts and clock (152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz; FMA probe "
-                             "1.21 TFLOP/s)"},
+                     "peaks_measured": {"fp64_tflops": peaks["fp64"], "fp32_tflops": peaks["fp32"],
+                                        "how": "gf_peak_probe FMA chains, CUDA events, best of 3"},
+                     "peaks_nominal": {"fp64_tflops": FP64_NOMINAL_TFLOPS, "fp32_tflops": FP32_NOMINAL_TFLOPS},
+                     "work": {"fp64_flops": w64, "fp32_flops": w32, "double_band_terms": bands["double"],
+                              "float_float_terms": bands["float-float"], "tail_terms": tail_terms,
+                              "all_terms": terms},
+                     "frac_fp64_pipe": frac64, "frac_fp32_pipe": frac32,
+                     "frac_max_model": max(frac64, frac32),
+                     "note": "two-pipe roofline of the far phase over all series terms: achieved = (FP64 term "
+                             "flops + FP32 term flops x P64/P32) / far-phase time, peak = measured FP64 rate, so "
+                             "frac = W64/(P64 t) + W32/(P32 t); per term 14 FP64 flops (double band), 98 FP32 "
+                             "flops (float-float band), 14 FP32 flops (float tail); frac_max_model takes the "
+                             "busier pipe alone"},
+        "err_vs_oracle": err_oracle,
         "e2e": {"value": whole_job_rate(n_targets, world, e2e_s), "unit": "evals/s",
                 "h2d_bytes_per_step": int(x_np.nbytes), "d2h_bytes_per_step": int(n_targets * 16)},
         "batched": batched,
@@ -644,8 +752,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gf", choices=["gf", "reference"])
-    ap.add_argument("--cpu-sample", type=int, default=20000)
-    ap.add_argument("--ref-sample", type=int, default=5000)
+    ap.add_argument("--ref-sample", type=int, default=50000,
+                    help="targets per step of the reference arm (the oracle), beside the full plan")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--targets", type=int, default=N_TARGETS,
                     help="targets per step (the benchmark workload is 1e6; smaller only for profiling captures)")

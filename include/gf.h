@@ -108,8 +108,10 @@ gf_status gf_trunc_default(gf_trunc_t *t);
  *   trunc      parameters, NULL for the defaults
  *   cuda_stream  stream on which the synthesis kernels run
  *   out        receives the plan handle; the plan owns its device memory
- * Device memory is allocated synchronously; the coefficient and FFT kernels
- * are enqueued on cuda_stream (the plan is usable by later work on that stream).
+ * Device memory comes from the library's stream-ordered memory pool on
+ * cuda_stream; the coefficient and FFT kernels are enqueued on cuda_stream (the
+ * plan is usable by later work on that stream, and by work on other streams
+ * once they are ordered after it).  The plan is immutable afterwards.
  * Errors: GF_ERR_ARG (bad sizes/parameters), GF_ERR_WOOD, GF_ERR_RESONANCE,
  * GF_ERR_NOMEM, GF_ERR_CUDA.  On error *out is set to NULL. */
 gf_status gf_plan(int dim, double k, const double *alpha, const int *M,
@@ -130,9 +132,11 @@ size_t gf_grid_bytes(gf_plan_t plan);
  *   dev_xyz   n * dim doubles, row-major [n][dim], device memory
  *   which     GF_OUT_G (2D), GF_OUT_GD (3D Helmholtz), GF_OUT_MAXWELL6/7 (Maxwell)
  *   dev_out   n * entries complex values, [n][entries], device memory
- * The plan keeps per-plan scratch lists of far- and near-branch targets (grown
- * on demand, synchronously); calls on the same plan must therefore not overlap
- * in time (issue them on one stream).  For 3D double-precision Helmholtz plans
+ * The plan is not modified by an evaluation: each call takes its scratch (the
+ * far- and near-branch target lists, 12 bytes per target plus 4 KiB) from the
+ * library's stream-ordered memory pool on cuda_stream and returns it in stream
+ * order, so calls on one plan may run concurrently on different streams and
+ * threads.  For 3D double-precision Helmholtz plans
  * part of the far series runs on a side stream that the library owns (one per
  * device): it waits for an event recorded on cuda_stream and cuda_stream waits
  * for its completion, so the call keeps the ordinary stream semantics.
@@ -145,7 +149,8 @@ gf_status gf_eval_points(gf_plan_t plan, const double *dev_xyz, int64_t n, int w
 
 /* As gf_eval_points, with HOST input and output buffers: copies the targets to
  * the device, evaluates and copies the results back, all on cuda_stream, then
- * synchronises the stream.  Staging buffers are cached in the plan. */
+ * synchronises the stream.  The device staging buffers are taken from the
+ * library's memory pool per call. */
 gf_status gf_eval_points_host(gf_plan_t plan, const double *host_xyz, int64_t n, int which,
                               void *host_out, void *cuda_stream);
 
@@ -154,8 +159,9 @@ gf_status gf_eval_points_host(gf_plan_t plan, const double *host_xyz, int64_t n,
  * while they evaluate, for example a solver that reserved all free device
  * memory for its own pool at start-up, or a latency-critical loop in which a
  * cudaMalloc/cudaFree (which can synchronise the whole device) is not
- * acceptable.  gf_eval_points grows a per-plan scratch list with cudaMalloc
- * when a call brings more targets than before; this function instead uses one
+ * acceptable.  gf_eval_points takes its scratch lists from the library's
+ * memory pool at every call, which reaches the driver whenever the pool has to
+ * grow; this function instead uses one
  * fixed scratch array compiled into the library (about 2 MiB: room for
  * GF_NOALLOC_MAX_TARGETS targets), which every GPU that loads the library
  * holds until the process exits.  It calls no cudaMalloc, cudaFree or other
@@ -167,8 +173,13 @@ gf_status gf_eval_points_host(gf_plan_t plan, const double *host_xyz, int64_t n,
  *   array (cudaGetSymbolAddress) with that device current; make that first
  *   call before any stream capture.
  *   All calls share the one scratch array: each call resets its counters on
- *   cuda_stream before use, and calls whose work overlaps on the GPU (other
- *   streams, other threads) race on it and give wrong results; serialise them.
+ *   cuda_stream before use, and calls of this function whose work overlaps on
+ *   the GPU (other streams, other threads) race on it and give wrong results;
+ *   serialise them.  Calls of gf_eval_points on the same plan do not touch the
+ *   array and may overlap with it.
+ *   The device address found at the first call is kept for the life of the
+ *   process: the library (this array, its memory pool and its side streams) is
+ *   not usable across a cudaDeviceReset.
  * Errors: GF_ERR_ARG, GF_ERR_CUDA, GF_ERR_UNSUPPORTED (device ordinal >= 64). */
 #define GF_NOALLOC_MAX_TARGETS (1 << 18)
 gf_status gf_eval_points_noalloc(gf_plan_t plan, const double *dev_xyz, int64_t n, int which,
@@ -313,6 +324,18 @@ gf_status gf_destroy(gf_plan_t plan);
  * live plan uses to the driver (synchronises the device).  GF_ERR_CUDA on a
  * driver error. */
 gf_status gf_release_memory(void);
+
+/* Arithmetic peak probe (diagnostic; the paper has no counterpart): one launch
+ * of independent fused multiply-add chains filling every SM, for measuring the
+ * FP64 (pipe = GF_PROBE_FP64) or FP32 (GF_PROBE_FP32) pipe's rate, which the
+ * far-series roofline divides by.  The caller times the launch on cuda_stream
+ * (CUDA events) and divides *flops (host; an FMA counts 2) by the time.
+ *   iters     loop trips per thread (each trip is 64 FMAs per thread), >= 1
+ *   dev_sink  device buffer of at least 8 bytes (written only to keep the
+ *             chains alive; its content is meaningless)
+ * Errors: GF_ERR_ARG, GF_ERR_CUDA. */
+enum { GF_PROBE_FP64 = 0, GF_PROBE_FP32 = 1 };
+gf_status gf_peak_probe(int pipe, int64_t iters, void *dev_sink, int64_t *flops, void *cuda_stream);
 
 /* Static description of a status code. */
 const char *gf_status_string(gf_status s);

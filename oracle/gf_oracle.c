@@ -33,6 +33,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef double complex cplx;
 
@@ -53,6 +56,19 @@ typedef struct {
     double eps;     /* singular cutoff radius: Y_eps = 1 on [0,eps], 0 beyond 2 eps */
     double tau;     /* relative truncation tolerance of the eigen-series */
 } or_params;
+
+/* Threads of the OpenMP loops below (n > 0 sets them); returns the count in
+ * effect.  Only the timing of the CPU baseline uses it (1 thread and all). */
+int or_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------------ */
 /* Cutoff functions.                                                          */

@@ -83,7 +83,14 @@ def lib():
         _lib.or_series.argtypes = [P, p, l, i, p]
         _lib.or_interp.argtypes = [P, p, p, l, p]
         _lib.or_grid_nodes.argtypes = [P, p, i, p, l, p]
+        _lib.or_set_threads.restype = i
+        _lib.or_set_threads.argtypes = [i]
     return _lib
+
+
+def set_threads(n: int = 0) -> int:
+    """OpenMP threads of the oracle's loops (n > 0 sets them); returns the count in effect."""
+    return int(lib().or_set_threads(int(n)))
 
 
 def _ptr(a: np.ndarray):

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgf.so")
-SOURCES = ["plan.cu", "runtime.cu", "synth.cu", "eval.cu", "noalloc.cu", "batch.cu", "mlp.cu"]
+SOURCES = ["plan.cu", "runtime.cu", "synth.cu", "eval.cu", "noalloc.cu", "batch.cu", "mlp.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

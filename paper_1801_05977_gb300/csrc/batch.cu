@@ -124,7 +124,8 @@ static gf_status batch_eval_setup(gf_batch_t b, const double *x, const int64_t *
     std::vector<int> pre(b->np + 1, 0);
     for (int p = 0; p < b->np; ++p) {
         const int64_t n = off[p + 1] - off[p];
-        gf_status s = gf_plan_eval_args(b->plans[p], x + 3 * off[p], n, which, (char *)out + elem * ne * off[p], &ea[p]);
+        gf_status s = gf_plan_eval_args(b->plans[p], x + 3 * off[p], n, which, (char *)out + elem * ne * off[p], &ea[p],
+                                        "gf_batch_eval_points");
         if (s != GF_OK) return s;
         ea[p].far_idx = b->scratch + off[p];
         ea[p].far_sorted = b->scratch + b->cap + off[p];

@@ -234,7 +234,8 @@ cudaError_t gf_launch_eval(const EvalArgs &a, int precision, cudaStream_t s, cud
 cudaStream_t gf_aux_stream();
 
 void gf_count_launch(int n);
-gf_status gf_plan_eval_args(gf_plan_t p, const double *dev_xyz, int64_t n, int which, void *dev_out, EvalArgs *a);
+gf_status gf_plan_eval_args(gf_plan_t p, const double *dev_xyz, int64_t n, int which, void *dev_out, EvalArgs *a,
+                            const char *who);
 gf_status gf_set_error(gf_status s, const char *msg);
 SynthArgs gf_plan_synth_args(gf_plan_t p);
 size_t gf_plan_work_bytes(gf_plan_t p);

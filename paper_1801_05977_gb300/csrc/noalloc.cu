@@ -61,7 +61,7 @@ extern "C" gf_status gf_eval_points_noalloc(gf_plan_t plan, const double *dev_xy
         return gf_set_error(GF_ERR_ARG, msg);
     }
     EvalArgs a;
-    gf_status s = gf_plan_eval_args(plan, dev_xyz, n, which, dev_out, &a);
+    gf_status s = gf_plan_eval_args(plan, dev_xyz, n, which, dev_out, &a, "gf_eval_points_noalloc");
     if (s != GF_OK) return s;
     if (n == 0) return GF_OK;
     int *scratch = nullptr;

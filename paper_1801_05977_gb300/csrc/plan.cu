@@ -124,13 +124,11 @@ struct gf_plan_s {
     double bmin_ev = 1e300;           // smallest evanescent |beta_n|
     int n1lo = 0, n1hi = -1, n2lo = 0, n2hi = -1;
     SynthArgs sa{};
-    // eval scratch (far list + counter) and host-call staging, grown on demand
+    // Launch lock: serialises the host-side enqueue of concurrent calls on this
+    // plan (the fork/join event pair and the phase-timing events are recorded
+    // under it).  Device memory of an evaluation is per call, so the plan itself
+    // is never modified after gf_plan.
     std::mutex mu;
-    int *far_idx = nullptr;      // [3 * cap]: far list in append order, bucket-sorted far list, near list
-    int *far_count = nullptr;    // [GF_SCRATCH_COUNTERS]
-    int64_t far_cap = 0;
-    void *stage_x = nullptr, *stage_out = nullptr;
-    size_t stage_x_cap = 0, stage_out_cap = 0;
     // phase timing: [0] synth start, [1] synth end, [2] table end, [3] near start, [4] near end, [5] far end
     bool timing = false;
     cudaEvent_t ev[6] = {};
@@ -283,6 +281,12 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
         }
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (dim == 3 && tr.precision == GF_FP64 && tr.kind == GF_HELMHOLTZ &&
+        (cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+         cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess)) {
+        gf_destroy(p);
+        return fail(GF_ERR_CUDA, "gf_plan: event creation failed");
+    }
     if (g_timing.load()) {
         p->timing = true;
         for (int i = 0; i < 6; ++i)
@@ -546,116 +550,67 @@ gf_status gf_eval_grid(gf_plan_t p, void *dev_out, size_t out_bytes, void *cuda_
     return GF_OK;
 }
 
-static gf_status ensure_scratch(gf_plan_t p, int64_t n, cudaStream_t st)
-{
-    if (p->far_cap >= n && p->far_count) return GF_OK;
-    int64_t cap = p->far_cap;
-    if (cap < 1024) cap = 1024;
-    while (cap < n) cap *= 2;
-    if (p->far_idx) {
-        // the old list may still be in use by an evaluation on another stream
-        CU(cudaDeviceSynchronize());
-        gf_dev_free(p->far_idx, st);
-        p->far_idx = nullptr;
-        p->far_cap = 0;
-    }
-    if (!p->far_count) CU(gf_dev_alloc((void **)&p->far_count, sizeof(int) * GF_SCRATCH_COUNTERS, st));
-    CU(gf_dev_alloc((void **)&p->far_idx, sizeof(int) * 3 * cap, st));
-    p->far_cap = cap;
-    return GF_OK;
-}
+// Scratch of one evaluation (ints): the counters, padded to GF_COUNTER_PAD, then
+// the far list in append order, the bucket-sorted far list and the near list,
+// n entries each.
+constexpr int64_t GF_COUNTER_PAD = 1024;
+static_assert(GF_SCRATCH_COUNTERS <= GF_COUNTER_PAD, "counter block too small");
 
 gf_status gf_eval_points(gf_plan_t p, const double *dev_xyz, int64_t n, int which, void *dev_out,
                          void *cuda_stream)
 {
-    if (!p) return fail(GF_ERR_ARG, "gf_eval_points: NULL plan");
-    if (n < 0 || n > (int64_t)0x7fffffff) return fail(GF_ERR_ARG, "gf_eval_points: n = %lld out of range", (long long)n);
-    if (n == 0) return GF_OK;
-    if (!dev_xyz || !dev_out) return fail(GF_ERR_ARG, "gf_eval_points: NULL buffer");
-    bool ok = (p->dim == 2 && which == GF_OUT_G) || (p->dim == 3 && p->kind == GF_HELMHOLTZ && (which == GF_OUT_GD || which == GF_OUT_LD)) ||
-              (p->kind == GF_MAXWELL && (which == GF_OUT_MAXWELL6 || which == GF_OUT_MAXWELL7));
-    if (!ok) return fail(GF_ERR_ARG, "gf_eval_points: output kind %d does not match the plan", which);
-    std::lock_guard<std::mutex> lk(p->mu);
+    EvalArgs a;
+    gf_status s = gf_plan_eval_args(p, dev_xyz, n, which, dev_out, &a, "gf_eval_points");
+    if (s != GF_OK || n == 0) return s;
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    gf_status s = ensure_scratch(p, n, st);
-    if (s != GF_OK) return s;
-    CU(cudaMemsetAsync(p->far_count, 0, sizeof(int) * GF_SCRATCH_COUNTERS, st));
-    EvalArgs a{};
-    a.dim = p->dim;
-    a.M1 = p->M[0];
-    a.M2 = p->M[1];
-    a.M3 = p->M[2];
-    a.P1 = p->P1;
-    a.P2 = p->P2;
-    a.P3 = p->P3;
-    a.Q3lo = p->Q3lo;
-    a.nf = p->nf;
-    a.which = which;
-    a.k = p->k;
-    a.a1 = p->alpha[0];
-    a.a2 = p->alpha[1];
-    a.c = p->tr.c;
-    a.ct = p->tr.c_tilde;
-    a.eps = p->tr.eps;
-    a.h1 = 2.0 * GF_PI / p->M[0];
-    a.h2 = p->dim == 3 ? 2.0 * GF_PI / p->M[1] : 2.0 * p->tr.c_tilde / p->M[1];
-    a.h3 = p->dim == 3 ? 2.0 * p->tr.c_tilde / p->M[2] : 1.0;
-    a.T = p->T;
-    a.grid = p->grid;
-    a.x = dev_xyz;
-    a.out = dev_out;
-    a.n = n;
-    a.far_idx = p->far_idx;
-    a.far_sorted = p->far_idx + p->far_cap;
-    a.near_idx = p->dim == 3 ? p->far_idx + 2 * p->far_cap : nullptr;
-    a.far_count = p->far_count;
-    a.btab = p->btab;
-    a.n1lo = p->n1lo;
-    a.n1hi = p->n1hi;
-    a.n2lo = p->n2lo;
-    a.n2hi = p->n2hi;
-    a.prop = p->prop;
-    a.nprop = p->nprop_dev;
-    a.exptab = p->exptab;
-    a.exptab_n = p->exptab_n;
-    a.exptab_j0 = p->exptab_j0;
-    a.bmin = p->bmin_ev;
-    // 3D double-precision plans run the far series' double sums and float tails
-    // as two concurrent kernels (the tails on the library's side stream)
-    EvalFork fk{};
-    const EvalFork *fork = nullptr;
-    if (p->dim == 3 && p->precision == GF_FP64) {
-        if (!p->ev_fork) {
-            CU(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
-            CU(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
+    // per-call scratch from the stream-ordered pool on the caller's stream, returned
+    // to the pool in stream order after the kernels: concurrent calls on other
+    // streams each have their own, and the plan stays unchanged
+    int *scratch = nullptr;
+    CU(gf_dev_alloc((void **)&scratch, sizeof(int) * (GF_COUNTER_PAD + 3 * n), st));
+    a.far_count = scratch;
+    a.far_idx = scratch + GF_COUNTER_PAD;
+    a.far_sorted = a.far_idx + n;
+    a.near_idx = p->dim == 3 ? a.far_idx + 2 * n : nullptr;
+    cudaError_t e = cudaMemsetAsync(a.far_count, 0, sizeof(int) * GF_SCRATCH_COUNTERS, st);
+    if (e == cudaSuccess) {
+        std::lock_guard<std::mutex> lk(p->mu);
+        // 3D double-precision Helmholtz plans run the far series' double sums and
+        // float tails as two concurrent kernels (the tails on the library's side stream)
+        EvalFork fk{};
+        const EvalFork *fork = nullptr;
+        if (p->ev_fork) {
+            fk.aux = gf_aux_stream();
+            fk.fork = p->ev_fork;
+            fk.join = p->ev_join;
+            if (fk.aux) fork = &fk;
         }
-        fk.aux = gf_aux_stream();
-        fk.fork = p->ev_fork;
-        fk.join = p->ev_join;
-        if (fk.aux) fork = &fk;
+        if (p->timing) cudaEventRecord(p->ev[3], st);
+        e = gf_launch_eval(a, p->precision, st, p->timing ? p->ev[4] : nullptr, fork);
+        if (p->timing && e == cudaSuccess) {
+            cudaEventRecord(p->ev[5], st);
+            p->ev_eval = true;
+        }
     }
-    if (p->timing) cudaEventRecord(p->ev[3], st);
-    CU(gf_launch_eval(a, p->precision, st, p->timing ? p->ev[4] : nullptr, fork));
-    if (p->timing) {
-        cudaEventRecord(p->ev[5], st);
-        p->ev_eval = true;
-    }
+    gf_dev_free(scratch, st);
+    CU(e);
     return GF_OK;
 }
 
 }  // extern "C"
 
-// Validation and argument set-up of one evaluation, without scratch pointers:
-// used by the allocation-free entry point (noalloc.cu).
+// Validation and argument set-up of one evaluation (everything but the
+// scratch pointers), shared by gf_eval_points, the allocation-free entry
+// point (noalloc.cu) and the batched sweeps; `who` names the caller in errors.
 gf_status gf_plan_eval_args(gf_plan_t p, const double *dev_xyz, int64_t n, int which, void *dev_out,
-                            EvalArgs *a_out)
+                            EvalArgs *a_out, const char *who)
 {
-    if (!p || !a_out) return fail(GF_ERR_ARG, "gf_eval_points_noalloc: NULL plan");
-    if (n < 0) return fail(GF_ERR_ARG, "gf_eval_points_noalloc: n < 0");
-    if (n > 0 && (!dev_xyz || !dev_out)) return fail(GF_ERR_ARG, "gf_eval_points_noalloc: NULL buffer");
+    if (!p || !a_out) return fail(GF_ERR_ARG, "%s: NULL plan", who);
+    if (n < 0 || n > (int64_t)0x7fffffff) return fail(GF_ERR_ARG, "%s: n = %lld out of range", who, (long long)n);
+    if (n > 0 && (!dev_xyz || !dev_out)) return fail(GF_ERR_ARG, "%s: NULL buffer", who);
     bool ok = (p->dim == 2 && which == GF_OUT_G) || (p->dim == 3 && p->kind == GF_HELMHOLTZ && (which == GF_OUT_GD || which == GF_OUT_LD)) ||
               (p->kind == GF_MAXWELL && (which == GF_OUT_MAXWELL6 || which == GF_OUT_MAXWELL7));
-    if (!ok) return fail(GF_ERR_ARG, "gf_eval_points_noalloc: output kind %d does not match the plan", which);
+    if (!ok) return fail(GF_ERR_ARG, "%s: output kind %d does not match the plan", who, which);
     EvalArgs a{};
     a.dim = p->dim;
     a.M1 = p->M[0];
@@ -739,33 +694,20 @@ gf_status gf_eval_points_host(gf_plan_t p, const double *host_xyz, int64_t n, in
     int ne = which == GF_OUT_MAXWELL6 ? 6 : which == GF_OUT_MAXWELL7 ? 7 : 1;
     size_t xb = sizeof(double) * p->dim * (size_t)n, ob = p->elem * ne * (size_t)n;
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    {
-        std::lock_guard<std::mutex> lk(p->mu);
-        if (p->stage_x_cap < xb) {
-            if (p->stage_x) {
-                CU(cudaDeviceSynchronize());
-                gf_dev_free(p->stage_x, st);
-            }
-            p->stage_x = nullptr;
-            p->stage_x_cap = 0;
-            CU(gf_dev_alloc(&p->stage_x, xb, st));
-            p->stage_x_cap = xb;
-        }
-        if (p->stage_out_cap < ob) {
-            if (p->stage_out) {
-                CU(cudaDeviceSynchronize());
-                gf_dev_free(p->stage_out, st);
-            }
-            p->stage_out = nullptr;
-            p->stage_out_cap = 0;
-            CU(gf_dev_alloc(&p->stage_out, ob, st));
-            p->stage_out_cap = ob;
-        }
+    // device staging per call from the stream-ordered pool (pool hits after the first call)
+    void *dx = nullptr, *dout = nullptr;
+    CU(gf_dev_alloc(&dx, xb, st));
+    cudaError_t e = gf_dev_alloc(&dout, ob, st);
+    gf_status s = GF_OK;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dx, host_xyz, xb, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        s = gf_eval_points(p, (const double *)dx, n, which, dout, cuda_stream);
+        if (s == GF_OK) e = cudaMemcpyAsync(host_out, dout, ob, cudaMemcpyDeviceToHost, st);
     }
-    CU(cudaMemcpyAsync(p->stage_x, host_xyz, xb, cudaMemcpyHostToDevice, st));
-    gf_status s = gf_eval_points(p, (const double *)p->stage_x, n, which, p->stage_out, cuda_stream);
+    gf_dev_free(dout, st);
+    gf_dev_free(dx, st);
     if (s != GF_OK) return s;
-    CU(cudaMemcpyAsync(host_out, p->stage_out, ob, cudaMemcpyDeviceToHost, st));
+    CU(e);
     CU(cudaStreamSynchronize(st));
     return GF_OK;
 }
@@ -807,7 +749,7 @@ gf_status gf_destroy(gf_plan_t p)
     // the plan may have been used on any stream: wait for the device, then hand
     // the buffers back to the pool
     cudaDeviceSynchronize();
-    void *bufs[] = {p->grid, p->tables, p->btab, p->prop, p->exptab, p->far_idx, p->far_count, p->stage_x, p->stage_out};
+    void *bufs[] = {p->grid, p->tables, p->btab, p->prop, p->exptab};
     for (void *b : bufs) gf_dev_free(b, 0);
     for (int i = 0; i < 6; ++i)
         if (p->ev[i]) cudaEventDestroy(p->ev[i]);

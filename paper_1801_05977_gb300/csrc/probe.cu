@@ -1,0 +1,58 @@
+// Arithmetic peak probes (diagnostics; the paper has no counterpart).
+//
+// The far-series kernels are bound by the FP64 and FP32 pipes, whose rates are
+// not in the measured-peak record of the machine (it holds the HBM copy rate
+// and the BF16 tensor rate).  These kernels measure them the plain way: every
+// thread runs ILP independent chains of fused multiply-adds, so the pipe never
+// waits on a result, and the grid fills every SM at full occupancy.
+#include "gf_internal.cuh"
+
+namespace {
+
+constexpr int PROBE_ILP = 8;
+constexpr int PROBE_THREADS = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(PROBE_THREADS) fma_chains(int64_t iters, T never, T *sink)
+{
+    T a[PROBE_ILP];
+#pragma unroll
+    for (int j = 0; j < PROBE_ILP; ++j) a[j] = (T)(threadIdx.x + 1 + j) * (T)1e-3;
+    const T m = (T)0.9999999, c = (T)1e-7;
+    for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int j = 0; j < PROBE_ILP; ++j) a[j] = fma(a[j], m, c);
+    }
+    T s = 0;
+#pragma unroll
+    for (int j = 0; j < PROBE_ILP; ++j) s += a[j];
+    // never true (the chains stay positive); keeps the chains from being removed
+    if (s == never) sink[0] = s;
+}
+
+}  // namespace
+
+extern "C" gf_status gf_peak_probe(int pipe, int64_t iters, void *dev_sink, int64_t *flops, void *cuda_stream)
+{
+    if ((pipe != GF_PROBE_FP64 && pipe != GF_PROBE_FP32) || iters < 1 || !dev_sink || !flops)
+        return gf_set_error(GF_ERR_ARG, "gf_peak_probe: bad argument");
+    int dev = 0, nsm = 1, per = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    cudaError_t e;
+    if (pipe == GF_PROBE_FP64) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fma_chains<double>, PROBE_THREADS, 0);
+        if (e == cudaSuccess) fma_chains<double><<<per * nsm, PROBE_THREADS, 0, st>>>(iters, -1.0, (double *)dev_sink);
+    } else {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fma_chains<float>, PROBE_THREADS, 0);
+        if (e == cudaSuccess) fma_chains<float><<<per * nsm, PROBE_THREADS, 0, st>>>(iters, -1.0f, (float *)dev_sink);
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return gf_set_error(GF_ERR_CUDA, "gf_peak_probe: launch failed");
+    gf_count_launch(1);
+    *flops = (int64_t)2 * PROBE_ILP * 8 * iters * (int64_t)per * nsm * PROBE_THREADS;
+    return GF_OK;
+}

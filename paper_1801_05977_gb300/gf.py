@@ -49,7 +49,7 @@ EXPORTS = ["gf_trunc_default", "gf_plan", "gf_eval_grid", "gf_grid_bytes", "gf_e
            "gf_batch_get_tuning", "gf_batch_run_graph", "gf_batch_get_plan", "gf_batch_destroy",
            "gf_gemm_bf16", "gf_mlp_create", "gf_mlp_param_count", "gf_mlp_params", "gf_mlp_set_scale",
            "gf_mlp_forward", "gf_mlp_train_step", "gf_mlp_gradients", "gf_mlp_error_word", "gf_surrogate_eval",
-           "gf_mlp_destroy", "gf_release_memory"]
+           "gf_mlp_destroy", "gf_release_memory", "gf_peak_probe"]
 
 NOALLOC_MAX_TARGETS = 1 << 18
 
@@ -108,13 +108,15 @@ def lib(build_if_missing: bool = True):
     L.gf_set_phase_timing.argtypes = [i32]
     L.gf_plan_phase_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
     L.gf_release_memory.argtypes = []
+    L.gf_peak_probe.argtypes = [i32, i64, vp, P(ctypes.c_int64), vp]
     for name in ("gf_trunc_default", "gf_plan", "gf_eval_grid", "gf_eval_points", "gf_eval_points_host",
                  "gf_eval_points_noalloc", "gf_plan_batch", "gf_batch_synthesize", "gf_batch_eval_points",
                  "gf_batch_autotune", "gf_batch_get_tuning", "gf_batch_run_graph", "gf_batch_get_plan",
                  "gf_batch_destroy", "gf_gemm_bf16", "gf_mlp_create", "gf_mlp_params", "gf_mlp_set_scale",
                  "gf_mlp_forward", "gf_mlp_train_step", "gf_mlp_gradients", "gf_mlp_error_word",
                  "gf_surrogate_eval", "gf_mlp_destroy",
-                 "gf_plan_get_info", "gf_destroy", "gf_set_phase_timing", "gf_plan_phase_ms", "gf_release_memory"):
+                 "gf_plan_get_info", "gf_destroy", "gf_set_phase_timing", "gf_plan_phase_ms", "gf_release_memory",
+                 "gf_peak_probe"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -147,6 +149,18 @@ def launch_count() -> int:
 
 def set_phase_timing(on: bool):
     _check(lib().gf_set_phase_timing(1 if on else 0))
+
+
+GF_PROBE_FP64, GF_PROBE_FP32 = 0, 1
+
+
+def peak_probe(pipe: int, iters: int, sink, stream=None) -> int:
+    """gf_peak_probe: enqueue one FMA-chain launch on the FP64 or FP32 pipe;
+    returns its flop count (the caller times the launch)."""
+    fl = ctypes.c_int64()
+    _check(lib().gf_peak_probe(int(pipe), int(iters), ctypes.c_void_p(sink.data_ptr()), ctypes.byref(fl),
+                               _stream_ptr(stream)))
+    return int(fl.value)
 
 
 def release_memory():
@@ -193,8 +207,23 @@ class Plan:
         _check(lib().gf_eval_grid(self._h, ctypes.c_void_p(out.data_ptr()), nbytes, _stream_ptr(stream)))
         return out
 
+    def _check_io(self, x, out, which: int):
+        """The kernels write n * entries values of the plan's complex type into out
+        and read n * dim doubles from x: refuse buffers that do not hold them."""
+        import torch
+        if which not in N_ENTRIES:
+            raise GfError(GF_ERR_ARG, f"unknown output kind {which}")
+        if not (x.is_cuda and x.dtype == torch.float64 and x.is_contiguous() and x.dim() == 2
+                and x.shape[1] == self.dim):
+            raise GfError(GF_ERR_ARG, f"x must be a contiguous float64 CUDA tensor of shape (n, {self.dim})")
+        if not (out.is_cuda and out.dtype == self.complex_dtype and out.is_contiguous()
+                and tuple(out.shape) == (x.shape[0], N_ENTRIES[which]) and out.device == x.device):
+            raise GfError(GF_ERR_ARG, f"out must be a contiguous {self.complex_dtype} tensor of shape "
+                                      f"({x.shape[0]}, {N_ENTRIES[which]}) on {x.device}")
+
     def eval_points_into(self, x, out, which: int, stream=None):
         """x: float64 CUDA tensor (n, dim); out: complex CUDA tensor (n, entries)."""
+        self._check_io(x, out, which)
         n = x.shape[0]
         _check(lib().gf_eval_points(self._h, ctypes.c_void_p(x.data_ptr()), n, int(which),
                                     ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
@@ -202,6 +231,7 @@ class Plan:
 
     def eval_points_noalloc_into(self, x, out, which: int, stream=None):
         """gf_eval_points_noalloc: same result, fixed library scratch, no allocation."""
+        self._check_io(x, out, which)
         n = x.shape[0]
         _check(lib().gf_eval_points_noalloc(self._h, ctypes.c_void_p(x.data_ptr()), n, int(which),
                                             ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
@@ -209,12 +239,27 @@ class Plan:
 
     def eval_points(self, x, which: int, stream=None):
         import torch
-        assert x.is_cuda and x.dtype == torch.float64 and x.is_contiguous() and x.shape[1] == self.dim
+        if which not in N_ENTRIES:
+            raise GfError(GF_ERR_ARG, f"unknown output kind {which}")
         out = torch.empty((x.shape[0], N_ENTRIES[which]), dtype=self.complex_dtype, device=x.device)
         return self.eval_points_into(x, out, which, stream)
 
     def eval_points_host(self, x: np.ndarray, out: np.ndarray, which: int, stream=None):
         """Host buffers in and out (numpy or pinned torch CPU tensors)."""
+        if which not in N_ENTRIES:
+            raise GfError(GF_ERR_ARG, f"unknown output kind {which}")
+        item = 16 if self.precision == GF_FP64 else 8
+        if isinstance(x, np.ndarray):
+            ok_x = x.dtype == np.float64 and x.flags.c_contiguous
+        else:
+            import torch
+            ok_x = (not x.is_cuda) and x.dtype == torch.float64 and x.is_contiguous()
+        if not (ok_x and x.ndim == 2 and x.shape[1] == self.dim):
+            raise GfError(GF_ERR_ARG, f"x must be a contiguous float64 host array of shape (n, {self.dim})")
+        obytes = out.nbytes if isinstance(out, np.ndarray) else out.numel() * out.element_size()
+        ocont = out.flags.c_contiguous if isinstance(out, np.ndarray) else (out.is_contiguous() and not out.is_cuda)
+        if not (ocont and obytes >= x.shape[0] * N_ENTRIES[which] * item):
+            raise GfError(GF_ERR_ARG, "out must be a contiguous host buffer of n * entries complex values")
         xp = x.ctypes.data if isinstance(x, np.ndarray) else x.data_ptr()
         op = out.ctypes.data if isinstance(out, np.ndarray) else out.data_ptr()
         n = x.shape[0]

@@ -1,0 +1,237 @@
+"""GPU path vs the FP64 oracle on the remaining configurations and parameters.
+
+- the Maxwell tensor (Algorithm 3, Sec. 4) at its full size, 256 x 256 x 64
+  with 1e6 targets of which 10% are clustered within 0.05 of lattice points,
+  in double precision (1e-10 pointwise) and in the split precision (float
+  bulk, double singular part) at its stated bound;
+- the split precision of the 2D path (Algorithm 1) and of the Maxwell path
+  against the oracle;
+- a plan whose c~ the resonance rule perturbed (Secs. 2.1 and 3.1: the case
+  beta = +-j pi/c~ "is avoided by a perturbation of c~"), against the oracle run
+  at the perturbed c~ read back from the plan;
+- eps = 0.25 in 2D, 3D and Maxwell, where 2 eps < c and the singular add-back
+  covers only part of the near slab;
+- concurrent evaluations of one plan on two streams and from two host threads.
+"""
+import threading
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O
+from paper_1801_05977_gb300 import gf
+from paper_1801_05977_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+# split precision (float grid, gather and series; double coefficients, singular
+# part, reduction and phase), normwise per output entry against the oracle
+TOL_SPLIT = 1e-6
+
+
+def rel_err(got, ref, floor=1e-6):
+    got, ref = np.asarray(got), np.asarray(ref)
+    scale = np.maximum(np.abs(ref), floor * np.abs(ref).max(axis=0, keepdims=True))
+    return float((np.abs(got - ref) / scale).max())
+
+
+def norm_err(got, ref):
+    """max over entries of max|got - ref| / max|ref| (column-wise for tensors)."""
+    got, ref = np.asarray(got), np.asarray(ref)
+    if got.ndim == 1:
+        got, ref = got[:, None], ref[:, None]
+    return float((np.abs(got - ref).max(axis=0) / np.abs(ref).max(axis=0)).max())
+
+
+def gpu_plan(pb: O.Problem, precision=gf.GF_FP64, **kw):
+    args = dict(c=pb.c, c_tilde=pb.ct, eps=pb.eps, quad_nodes=pb.Q, precision=precision,
+                kind=gf.GF_MAXWELL if pb.maxwell else gf.GF_HELMHOLTZ)
+    if precision == gf.GF_FP64:
+        args["series_tol"] = pb.tau
+    args.update(kw)
+    return gf.Plan(pb.dim, pb.k, pb.alpha, pb.M, **args)
+
+
+def gpu_eval(plan, x, which):
+    xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    out = plan.eval_points(xd, which)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def lattice_r(x):
+    d1 = x[:, 0] - 2 * np.pi * np.round(x[:, 0] / (2 * np.pi))
+    d2 = x[:, 1] - 2 * np.pi * np.round(x[:, 1] / (2 * np.pi))
+    return np.sqrt(d1 * d1 + d2 * d2 + x[:, 2] ** 2)
+
+
+# ----------------------------------------------------------------------------- config 3 at full size
+def test_full_size_config3_maxwell_sampled():
+    """256 x 256 x 64 Maxwell: 8 grid nodes per field straight from the truncated
+    series, then 1500 of the 1e6 targets (150 of them clustered) through the
+    oracle's whole path (seven grids, seven interpolations), double precision
+    at 1e-10 pointwise and the split precision at its bound."""
+    pb = O.Problem(dim=3, k=2.5, alpha=(0.1, 0.3), M=(256, 256, 64), maxwell=True)
+    x_all = W.targets_3d_clustered(1_000_000, seed=0)
+    xd = torch.from_numpy(x_all).cuda()
+    plan = gpu_plan(pb)
+    got64 = plan.eval_points(xd, gf.GF_OUT_MAXWELL7)
+    torch.cuda.synchronize()
+    got64 = got64.cpu().numpy()
+    gg = plan.eval_grid().cpu().numpy()
+    plan.close()
+    split = gpu_plan(pb, precision=gf.GF_FP32_SPLIT)
+    got32 = split.eval_points(xd, gf.GF_OUT_MAXWELL7)
+    torch.cuda.synchronize()
+    got32 = got32.cpu().numpy()
+    split.close()
+    del xd
+    assert np.isfinite(got64).all() and np.isfinite(got32).all()
+
+    C = O.coef(pb)
+    rng = np.random.default_rng(3)
+    nodes = np.stack([rng.integers(0, m, 8) for m in pb.M], axis=1).astype(np.int32)
+    pairs = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+    scale = np.abs(gg).max(axis=(1, 2, 3))
+    ref_ld = O.grid_nodes(pb, C, nodes, field=0)
+    for e, (p, q) in enumerate(pairs):
+        ref = (ref_ld if p == q else 0) + O.grid_nodes(pb, C, nodes, field=1 + e) / pb.k**2
+        got = np.array([gg[e, n[2], n[1], n[0]] for n in nodes])
+        assert np.abs(got - ref).max() < 1e-12 * scale[e], f"grid field {e}"
+    got = np.array([gg[6, n[2], n[1], n[0]] for n in nodes])
+    assert np.abs(got - ref_ld).max() < 1e-12 * scale[6]
+
+    g = O.grid(pb, C)
+    del C
+    r = lattice_r(x_all)
+    clustered = np.flatnonzero(r <= 0.05)
+    uniform = np.flatnonzero(r > 0.05)
+    sel = np.concatenate([rng.choice(clustered, 150, replace=False), rng.choice(uniform, 1350, replace=False)])
+    ref = O.evaluate(pb, g, x_all[sel], O.OUT_MAXWELL7)
+    e_pt, e_nw = rel_err(got64[sel], ref), norm_err(got64[sel], ref)
+    e_split = norm_err(got32[sel], ref)
+    print(f"config-3 full size: FP64 pointwise {e_pt:.2e}, normwise {e_nw:.2e}; "
+          f"split normwise per entry {e_split:.2e} vs the FP64 oracle")
+    assert e_pt < TOL64
+    assert e_split < TOL_SPLIT
+
+
+# ----------------------------------------------------------------------------- split precision: 2D and Maxwell
+def test_split_precision_2d_config1():
+    """Algorithm 1 at config 1 (64 x 64, 1e4 targets) in split precision (float
+    grid and gather; the 2D far series stays in double)."""
+    pb = O.Problem(dim=2, k=1.3, alpha=(0.2,), M=(64, 64))
+    g = O.grid(pb)
+    plan = gpu_plan(pb, precision=gf.GF_FP32_SPLIT)
+    # float inverse FFT over 64 x 64 nodes: rounding ~ log2(4096) float ulps (measured 1.8e-7)
+    e_grid = norm_err(plan.eval_grid().cpu().numpy().ravel(), g.ravel())
+    assert e_grid < 1e-6, e_grid
+    x = W.targets_2d(10_000, seed=0)
+    ref = O.evaluate(pb, g, x, O.OUT_G)
+    e = norm_err(gpu_eval(plan, x, gf.GF_OUT_G), ref)
+    print(f"2D split precision: normwise {e:.2e} vs the FP64 oracle")
+    assert e < TOL_SPLIT
+
+
+def test_split_precision_maxwell():
+    pb = O.Problem(dim=3, k=2.5, alpha=(0.1, 0.3), M=(64, 64, 32), maxwell=True)
+    g = O.grid(pb)
+    plan = gpu_plan(pb, precision=gf.GF_FP32_SPLIT)
+    x = np.concatenate([W.targets_3d(3000, seed=31), W.targets_3d_clustered(1000, seed=32, frac=1.0)])
+    ref = O.evaluate(pb, g, x, O.OUT_MAXWELL7)
+    e = norm_err(gpu_eval(plan, x, gf.GF_OUT_MAXWELL7), ref)
+    print(f"Maxwell split precision: normwise per entry {e:.2e} vs the FP64 oracle")
+    assert e < TOL_SPLIT
+
+
+# ----------------------------------------------------------------------------- resonance-perturbed plans
+@pytest.mark.parametrize("dim", [2, 3])
+def test_resonance_perturbed_plan(dim):
+    """k chosen so that beta_0 = pi/c~ exactly at c~ = 1: the plan moves c~ to
+    c~(1 + 1e-3 m); the oracle run at that c~ must agree."""
+    al = (0.1, 0.2) if dim == 3 else (0.15,)
+    k = float(np.sqrt(np.pi**2 + sum(a * a for a in al)))
+    M = (32, 32, 16) if dim == 3 else (64, 64)
+    plan = gf.Plan(dim, k, al, M, series_tol=1e-16)
+    ct = plan.info.c_tilde
+    assert ct != 1.0 and abs(ct / 1.0 - 1.0 - 1e-3 * round((ct - 1.0) / 1e-3)) < 1e-15
+    pb = O.Problem(dim=dim, k=k, alpha=al, M=M, ct=ct)
+    g = O.grid(pb)
+    got_g = plan.eval_grid().cpu().numpy()
+    assert norm_err(got_g.ravel(), g.ravel()) < 1e-12
+    x = W.targets_3d(3000, seed=41) if dim == 3 else W.targets_2d(3000, seed=41)
+    which, owhich = (gf.GF_OUT_GD, O.OUT_GD) if dim == 3 else (gf.GF_OUT_G, O.OUT_G)
+    e = rel_err(gpu_eval(plan, x, which), O.evaluate(pb, g, x, owhich))
+    print(f"resonance-perturbed plan, dim {dim}: c~ = {ct}, pointwise {e:.2e} vs the oracle")
+    assert e < TOL64
+
+
+# ----------------------------------------------------------------------------- eps = 0.25 (2 eps < c)
+@pytest.mark.parametrize("kind", ["2d", "3d", "maxwell"])
+def test_eps_quarter(kind):
+    if kind == "2d":
+        pb = O.Problem(dim=2, k=1.3, alpha=(0.2,), M=(64, 64), eps=0.25)
+        x = W.targets_2d(4000, seed=51)
+        which, owhich = gf.GF_OUT_G, O.OUT_G
+    else:
+        pb = O.Problem(dim=3, k=2.5, alpha=(0.1, 0.3), M=(32, 32, 16), eps=0.25, maxwell=(kind == "maxwell"))
+        x = np.concatenate([W.targets_3d(3000, seed=52), W.targets_3d_clustered(1000, seed=53, frac=1.0, rmax=0.6)])
+        which, owhich = (gf.GF_OUT_MAXWELL7, O.OUT_MAXWELL7) if pb.maxwell else (gf.GF_OUT_GD, O.OUT_GD)
+    g = O.grid(pb)
+    plan = gpu_plan(pb)
+    assert plan.info.eps == 0.25
+    assert norm_err(plan.eval_grid().cpu().numpy().ravel(), g.ravel()) < 1e-12
+    e = rel_err(gpu_eval(plan, x, which), O.evaluate(pb, g, x, owhich))
+    print(f"eps = 0.25, {kind}: pointwise {e:.2e} vs the oracle")
+    assert e < TOL64
+
+
+# ----------------------------------------------------------------------------- concurrent evaluations of one plan
+@pytest.mark.parametrize("precision", [gf.GF_FP64, gf.GF_FP32_SPLIT])
+def test_concurrent_streams_one_plan(precision):
+    """The plan is immutable after gf_plan: evaluations on two streams at once,
+    and from two host threads, equal the serial results (to the far list's
+    atomic-append grouping, which moves the row-sum anchors)."""
+    plan = gf.Plan(3, 2.5, (0.1, 0.3), (32, 32, 16), precision=precision)
+    tol = 1e-11 if precision == gf.GF_FP64 else 1e-6
+    xa = torch.from_numpy(W.targets_3d(60_000, seed=61)).cuda()
+    xb = torch.from_numpy(W.targets_3d(33_001, seed=62)).cuda()
+    ra = plan.eval_points(xa, gf.GF_OUT_GD)
+    rb = plan.eval_points(xb, gf.GF_OUT_GD)
+    torch.cuda.synchronize()
+    ra, rb = ra.cpu().numpy(), rb.cpu().numpy()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    for _ in range(3):
+        oa = torch.empty((xa.shape[0], 1), dtype=plan.complex_dtype, device="cuda")
+        ob = torch.empty((xb.shape[0], 1), dtype=plan.complex_dtype, device="cuda")
+        torch.cuda.synchronize()
+        plan.eval_points_into(xa, oa, gf.GF_OUT_GD, stream=s1)
+        plan.eval_points_into(xb, ob, gf.GF_OUT_GD, stream=s2)
+        torch.cuda.synchronize()
+        assert norm_err(oa.cpu().numpy(), ra) < tol and norm_err(ob.cpu().numpy(), rb) < tol
+
+    results, errors = {}, []
+
+    def worker(name, x, ref):
+        try:
+            s = torch.cuda.Stream()
+            for i in range(4):
+                o = torch.empty((x.shape[0], 1), dtype=plan.complex_dtype, device="cuda")
+                torch.cuda.synchronize()
+                plan.eval_points_into(x, o, gf.GF_OUT_GD, stream=s)
+                s.synchronize()
+                results[(name, i)] = norm_err(o.cpu().numpy(), ref)
+        except Exception as exc:  # reported by the main thread
+            errors.append(exc)
+
+    th = [threading.Thread(target=worker, args=("a", xa, ra)), threading.Thread(target=worker, args=("b", xb, rb))]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert not errors, errors
+    assert len(results) == 8 and max(results.values()) < tol
+    plan.close()

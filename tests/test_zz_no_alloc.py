@@ -36,18 +36,49 @@ def norm_err(got, ref):
 # rounding, not bitwise); split plans:
 # the normwise 2e-5 bound the split-precision parity test states, since float
 # sums depend on that grouping
-@pytest.mark.parametrize("precision,metric,tol", [(gf.GF_FP64, rel_err, 1e-11), (gf.GF_FP32_SPLIT, norm_err, 2e-5)])
-def test_noalloc_matches_eval_points_twice(precision, metric, tol):
-    plan = gf.Plan(3, 2.5, (0.1, 0.3), (32, 32, 16), precision=precision)
-    for call, (n, seed) in enumerate([(20000, 1), (7001, 2)]):
-        x = torch.from_numpy(W.targets_3d(n, seed=seed)).cuda()
-        ref = plan.eval_points(x, gf.GF_OUT_GD)
+CASES = [
+    # id, plan arguments, output kind, metric, tolerance
+    ("3d-fp64", dict(dim=3, k=2.5, alpha=(0.1, 0.3), M=(32, 32, 16), precision=gf.GF_FP64), gf.GF_OUT_GD,
+     rel_err, 1e-11),
+    ("3d-split", dict(dim=3, k=2.5, alpha=(0.1, 0.3), M=(32, 32, 16), precision=gf.GF_FP32_SPLIT), gf.GF_OUT_GD,
+     norm_err, 2e-5),
+    ("2d-fp64", dict(dim=2, k=1.3, alpha=(0.2,), M=(64, 64), precision=gf.GF_FP64), gf.GF_OUT_G, rel_err, 1e-11),
+    ("maxwell-fp64", dict(dim=3, k=2.5, alpha=(0.1, 0.3), M=(32, 32, 16), precision=gf.GF_FP64,
+                          kind=gf.GF_MAXWELL), gf.GF_OUT_MAXWELL7, rel_err, 1e-11),
+]
+
+
+def _targets(dim, n, seed):
+    return W.targets_3d(n, seed=seed) if dim == 3 else W.targets_2d(n, seed=seed)
+
+
+def _compare(plan, dim, which, metric, tol, calls):
+    for call, (n, seed) in enumerate(calls):
+        x = torch.from_numpy(_targets(dim, n, seed)).cuda()
+        ref = plan.eval_points(x, which)
         out = torch.full_like(ref, complex("nan"))
-        plan.eval_points_noalloc_into(x, out, gf.GF_OUT_GD)
+        plan.eval_points_noalloc_into(x, out, which)
         torch.cuda.synchronize()
         r, o = ref.cpu().numpy(), out.cpu().numpy()
         assert np.isfinite(o).all(), f"call {call}: unwritten outputs"
         assert metric(o, r) < tol, f"call {call}"
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_noalloc_matches_eval_points_twice(case):
+    _, kw, which, metric, tol = case
+    kw = dict(kw)
+    dim, k, alpha, M = kw.pop("dim"), kw.pop("k"), kw.pop("alpha"), kw.pop("M")
+    plan = gf.Plan(dim, k, alpha, M, **kw)
+    _compare(plan, dim, which, metric, tol, [(20000, 1), (7001, 2)])
+    plan.close()
+
+
+def test_noalloc_at_the_size_limit():
+    """Exactly GF_NOALLOC_MAX_TARGETS targets (the far lists fill the array to
+    its end), then a smaller call that reuses what the first one left behind."""
+    plan = gf.Plan(3, 2.5, (0.1, 0.3), (32, 32, 16))
+    _compare(plan, 3, gf.GF_OUT_GD, rel_err, 1e-11, [(gf.NOALLOC_MAX_TARGETS, 3), (1001, 4)])
     plan.close()
 
 
