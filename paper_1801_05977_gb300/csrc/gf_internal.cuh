@@ -113,7 +113,7 @@ struct SynthArgs {
     double F10;         // 2D: sqrt(V) F1-hat_0
     int TJ2, lg1, lg2;  // x2-pass columns per CTA; log2 M1, log2 M2
     int RB1;            // last-pass rows per CTA
-    void *work;         // [nf][Mlast][M2][M1] complex (3D) or [M2][M1] (2D), working precision
+    void *work;         // 3D: [nf][L3count][M2][M1] complex (the transformed x3 planes, compact); 2D: [M2][M1]
     void *grid;         // padded gather grid
     int P1, P2, P3;     // padded extents (M + 3 per periodic axis); P3 = stored x3 planes (1 in 2D)
     int Q3lo;           // padded x3 index of the first stored plane

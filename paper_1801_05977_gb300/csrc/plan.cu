@@ -364,8 +364,7 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
     const size_t host_tab_bytes = sizeof(double) * 5 * Q + sizeof(double2) * Q;
     const bool ftabs = tr.precision == GF_FP32_SPLIT;  // float copies for the split plans' coefficients
     const size_t tab_bytes = host_tab_bytes + sizeof(double2) * (E_n + hcheb_n) + (ftabs ? sizeof(float2) * (E_n + hcheb_n) : 0);
-    const size_t ncells = (size_t)p->M[0] * p->M[1] * p->M[2];
-    const size_t work_bytes = ncells * p->nf * p->elem;
+    const size_t work_bytes = gf_plan_work_bytes(p);
     void *work = nullptr;
     gf_status st_err = GF_OK;
     p->stream = st;
@@ -533,7 +532,7 @@ gf_status gf_eval_grid(gf_plan_t p, void *dev_out, size_t out_bytes, void *cuda_
         fs.a3first = 0;
         fs.L3count = p->M[2];
         void *work = nullptr, *grid = nullptr;
-        CU(gf_dev_alloc(&work, gf_plan_work_bytes(p), st));
+        CU(gf_dev_alloc(&work, (size_t)p->M[0] * p->M[1] * p->M[2] * p->nf * p->elem, st));
         cudaError_t e = gf_dev_alloc(&grid, (size_t)fs.P1 * fs.P2 * fs.P3 * p->nf * p->elem, st);
         if (e == cudaSuccess) {
             fs.work = work;
@@ -656,7 +655,11 @@ gf_status gf_set_error(gf_status s, const char *msg) { return fail(s, "%s", msg)
 // Synthesis arguments of a plan (batched sweeps re-run the synthesis of many
 // plans with their own work buffers) and the bytes of its work buffer.
 SynthArgs gf_plan_synth_args(gf_plan_t p) { return p->sa; }
-size_t gf_plan_work_bytes(gf_plan_t p) { return (size_t)p->M[0] * p->M[1] * p->M[2] * p->nf * p->elem; }
+// (3D: only the stored x3 planes, compact; 2D: the whole grid)
+size_t gf_plan_work_bytes(gf_plan_t p)
+{
+    return (size_t)p->M[0] * p->M[1] * (p->dim == 3 ? p->L3count : 1) * p->nf * p->elem;
+}
 int gf_plan_precision(gf_plan_t p) { return p->precision; }
 
 extern "C" {

@@ -156,8 +156,15 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
     const double k2 = a.k * a.k, ik2 = 1.0 / k2;
     // the float branch's constants, converted once
     const float qsf = (float)a.qs, ihpanf = (float)a.ihpan, hpanf = (float)a.hpan, invVf = (float)a.invV;
-    for (int i = threadIdx.x; i < TJ * n; i += blockDim.x) {
-        int t = i >> lg, b = i & (n - 1);
+    // The coefficients are even in the last-axis index j (they depend on q_j
+    // through q_j^2, and the two X' terms of Eqs. (fck-coef)/(kdj1) trade places
+    // under q -> -q), except the Maxwell xz and yz fields, whose factor c^3 = q_j
+    // makes them odd (Sec. 4).  Only b = 0 .. n/2 (j = 0 .. n/2 - 1 and the
+    // Nyquist index j = -n/2) are formed here; b > n/2 (j = b - n) is filled
+    // below from b' = n - b (j' = -j).
+    const int nh = (n >> 1) + 1;
+    for (int i = threadIdx.x; i < TJ * nh; i += blockDim.x) {
+        int t = i / nh, b = i - t * nh;
         int col = col0 + t;
         int jl = freq_of(b, n);
         if (fcoef && (cflag[t] & 2)) {
@@ -348,15 +355,39 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
         }
     }
     __syncthreads();
+    {
+        const int nm = (n >> 1) - 1;  // b = n/2 + 1 .. n - 1
+        for (int i = threadIdx.x; i < nf * TJ * nm; i += blockDim.x) {
+            const int line = i / nm, b = (n >> 1) + 1 + (i - line * nm);
+            const int e = line / TJ;
+            const C v = buf0[line * n + (n - b)];
+            // Maxwell fields 4 (xz) and 5 (yz) are odd in j
+            buf0[line * n + b] = (nf > 1 && (e == 4 || e == 5)) ? cmk(-v.x, -v.y) : v;
+        }
+    }
+    __syncthreads();
     C *res = stockham_inverse(buf0, buf1, n, lg, nf * TJ, tw);
     C *W = reinterpret_cast<C *>(a.work);
-    const int tot = nf * n * TJ;
-    for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-        int t = i % TJ;
-        int rest = i / TJ;
-        int l = rest & (n - 1);
-        int f = rest >> lg;
-        W[((size_t)f * n + l) * ncols + col0 + t] = res[(f * TJ + t) * n + l];
+    if (a.dim == 3) {
+        // only the x3 nodes the last two passes transform (a3first .. a3first +
+        // L3count - 1), compact: work plane y holds node a3first + y, whose output
+        // index is l = (a + n/2) mod n
+        const int tot = nf * a.L3count * TJ;
+        for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+            const int t = i % TJ, rest = i / TJ;
+            const int y = rest % a.L3count, f = rest / a.L3count;
+            const int l = (a.a3first + y + (n >> 1)) & (n - 1);
+            W[((size_t)f * a.L3count + y) * ncols + col0 + t] = res[(f * TJ + t) * n + l];
+        }
+    } else {
+        const int tot = nf * n * TJ;
+        for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+            int t = i % TJ;
+            int rest = i / TJ;
+            int l = rest & (n - 1);
+            int f = rest >> lg;
+            W[((size_t)f * n + l) * ncols + col0 + t] = res[(f * TJ + t) * n + l];
+        }
     }
 }
 
@@ -367,13 +398,12 @@ __device__ void synth_x2_body(const SynthArgs &a, int bx, int y, int f, unsigned
 {
     typedef typename cplx_t<R>::T C;
     const int n = a.M2, TJ = a.TJ2, lg2 = a.lg2;
-    // x3 node a3first + y, stored at plane l3 of the work buffer (node = (l3 + M3/2) mod M3)
-    const int l3 = (a.a3first + y + (a.M3 >> 1)) % a.M3;
+    // x3 node a3first + y, stored at plane y of the (compact) work buffer
     C *tw = reinterpret_cast<C *>(smem);
     C *buf0 = tw + (n >> 1);
     C *buf1 = buf0 + TJ * n;
     const int b10 = bx * TJ;
-    C *W = reinterpret_cast<C *>(a.work) + ((size_t)f * a.M3 + l3) * (size_t)a.M2 * a.M1;
+    C *W = reinterpret_cast<C *>(a.work) + ((size_t)f * a.L3count + y) * (size_t)a.M2 * a.M1;
     load_twiddles<R>(tw, n);
     for (int i = threadIdx.x; i < TJ * n; i += blockDim.x) {
         int t = i % TJ, b2 = i / TJ;
@@ -410,21 +440,15 @@ __device__ void synth_x1_body(const SynthArgs &a, int blk, unsigned char *smem)
     C *tw = reinterpret_cast<C *>(smem);
     C *buf0 = tw + (n >> 1);
     C *buf1 = buf0 + RB * nf * n;
-    // row: 3D: l3 * M2 + l2; 2D: l2
-    const size_t fstride = (size_t)a.Mlast * (a.dim == 3 ? a.M2 : 1) * a.M1;
+    // row = y * M2 + l2 (3D: x3 node a3first + y at compact work plane y); 2D: l2
+    const size_t fstride = (size_t)(a.dim == 3 ? a.L3count * a.M2 : a.Mlast) * a.M1;
     const C *W = reinterpret_cast<const C *>(a.work);
     const int row0 = blk * RB;
     load_twiddles<R>(tw, n);
-    // row = y * M2 + l2 (3D: x3 node a3first + y, work plane l3 = (node + M3/2) mod M3); 2D: l2
-    auto work_row = [&](int row) -> int {
-        if (a.dim != 3) return row;
-        const int y = row / a.M2, l2 = row - y * a.M2;
-        return ((a.a3first + y + (a.M3 >> 1)) % a.M3) * a.M2 + l2;
-    };
     for (int i = threadIdx.x; i < RB * nf * n; i += blockDim.x) {
         const int r = i / (nf * n), rem = i - r * nf * n;
         const int f = rem / n, b1 = rem - f * n;
-        buf0[i] = W[f * fstride + (size_t)work_row(row0 + r) * n + b1];
+        buf0[i] = W[f * fstride + (size_t)(row0 + r) * n + b1];
     }
     __syncthreads();
     C *res = stockham_inverse(buf0, buf1, n, lg1, RB * nf, tw);

@@ -30,12 +30,19 @@ def norm_err(got, ref):
     return float(np.abs(got - ref).max() / np.abs(ref).max())
 
 
+def entry_norm_err(got, ref):
+    return float((np.abs(got - ref).max(axis=0) / np.abs(ref).max(axis=0)).max())
+
+
 # double plans: pointwise 1e-11 (the far targets are grouped into warps in
 # atomic-append order, which moves the row-sum anchors and the warp's
 # double/float split of the exponentially small series tail, so sums agree to
-# rounding, not bitwise); split plans:
-# the normwise 2e-5 bound the split-precision parity test states, since float
-# sums depend on that grouping
+# rounding, not bitwise); the Maxwell entries weight that tail by b^2 and
+# c^p c^q, and some of them pass near zero, so they are compared normwise per
+# entry (1e-13; a pointwise floor of 1e-6 max|G| would magnify a 1e-16
+# difference at such a point 1e6-fold); split plans: the normwise 2e-5 bound
+# the split-precision parity test states, since float sums depend on that
+# grouping
 CASES = [
     # id, plan arguments, output kind, metric, tolerance
     ("3d-fp64", dict(dim=3, k=2.5, alpha=(0.1, 0.3), M=(32, 32, 16), precision=gf.GF_FP64), gf.GF_OUT_GD,
@@ -44,7 +51,7 @@ CASES = [
      norm_err, 2e-5),
     ("2d-fp64", dict(dim=2, k=1.3, alpha=(0.2,), M=(64, 64), precision=gf.GF_FP64), gf.GF_OUT_G, rel_err, 1e-11),
     ("maxwell-fp64", dict(dim=3, k=2.5, alpha=(0.1, 0.3), M=(32, 32, 16), precision=gf.GF_FP64,
-                          kind=gf.GF_MAXWELL), gf.GF_OUT_MAXWELL7, rel_err, 1e-11),
+                          kind=gf.GF_MAXWELL), gf.GF_OUT_MAXWELL7, entry_norm_err, 1e-13),
 ]
 
 
