@@ -88,8 +88,8 @@ static gf_status batch_synth_setup(gf_batch_t b)
         for (int i = 0; i < 3; ++i) smax[i] = sm[i] > smax[i] ? sm[i] : smax[i];
         const int ncols = a.M1 * a.M2;
         b->h_prefix[0][p + 1] = b->h_prefix[0][p] + ncols / a.TJ;
-        b->h_prefix[1][p + 1] = b->h_prefix[1][p] + (a.M1 / a.TJ2) * a.L3count * a.nf;
-        b->h_prefix[2][p + 1] = b->h_prefix[2][p] + a.L3count * a.M2 / a.RB1;
+        b->h_prefix[1][p + 1] = b->h_prefix[1][p] + (a.M1 / a.TJ2) * (a.L3count + a.nyq) * a.nf;
+        b->h_prefix[2][p + 1] = b->h_prefix[2][p] + (a.L3count + a.nyq) * a.M2 / a.RB1;
     }
     for (int i = 0; i < 3; ++i)
         CUB(cudaMemcpy(b->d_prefix + i * (b->np + 1), b->h_prefix[i].data(), sizeof(int) * (b->np + 1),

@@ -170,8 +170,11 @@ __device__ __forceinline__ void near_point(const EvalArgs &a, int64_t i, double 
     int i1 = stencil_origin(t1, -GF_PI, a.h1, ih1, a.M1, f1);
     int i2 = stencil_origin(t2, -GF_PI, a.h2, ih2, a.M2, f2);
     // stored planes from Q3lo: a Helmholtz grid (even in x3) holds x3 >= -h3 only
-    // and is read at |x3|; a Maxwell grid holds the slab |x3| <= c
-    int i3 = stencil_origin(NF == 1 ? fabs(x3) : x3, -a.ct, a.h3, ih3, a.M3, f3) - a.Q3lo;
+    // and is read at |x3|; so is a Maxwell grid that keeps the odd fields' Nyquist
+    // planes (nyqgrid), otherwise it holds the slab |x3| <= c
+    const bool mirror = NF == 1 || a.nyqgrid != nullptr;
+    const int i3n = stencil_origin(mirror ? fabs(x3) : x3, -a.ct, a.h3, ih3, a.M3, f3);
+    const int i3 = i3n - a.Q3lo;
     // weights in the grid's precision (f itself is formed in double)
     R w1[4], w2[4], w3[4];
     lagrange4<R>((R)f1, w1);
@@ -198,6 +201,40 @@ __device__ __forceinline__ void near_point(const EvalArgs &a, int64_t i, double 
                 acc[e][0] = fma(w23, sr, acc[e][0]);
                 acc[e][1] = fma(w23, si, acc[e][1]);
             }
+        }
+    }
+    if (NF > 1 && a.nyqgrid != nullptr && x3 < 0.0) {
+        // The stencil of x3 < 0 is the mirror of the one read at |x3| (nodes
+        // a' = i3n - 1 .. i3n + 2 <-> M3 - a').  Even fields: the same values.  Odd
+        // fields (4: xz, 5: yz): L(M3 - a') = -L(a') + 2 (-1)^(M3/2 + a') P(t), so
+        // the interpolant is -acc + 2 (-1)^(M3/2) (sum_d w3_d (-1)^(a'_d)) P(t),
+        // P interpolated bicubically from the Nyquist planes.
+        R sgn = w3[0] - w3[1] + w3[2] - w3[3];
+        if (((i3n - 1) ^ (a.M3 >> 1)) & 1) sgn = -sgn;
+        const C *NG = reinterpret_cast<const C *>(a.nyqgrid);
+        R pr[2] = {0, 0}, pi[2] = {0, 0};
+#pragma unroll
+        for (int d2 = 0; d2 < 4; ++d2) {
+            const C *row = NG + ((size_t)(i2 + d2) * a.P1 + i1) * 2;
+            R s4r = 0, s4i = 0, s5r = 0, s5i = 0;
+#pragma unroll
+            for (int d1 = 0; d1 < 4; ++d1) {
+                const C g4 = __ldg(row + 2 * d1), g5 = __ldg(row + 2 * d1 + 1);
+                s4r = fma(w1[d1], g4.x, s4r);
+                s4i = fma(w1[d1], g4.y, s4i);
+                s5r = fma(w1[d1], g5.x, s5r);
+                s5i = fma(w1[d1], g5.y, s5i);
+            }
+            pr[0] = fma(w2[d2], s4r, pr[0]);
+            pi[0] = fma(w2[d2], s4i, pi[0]);
+            pr[1] = fma(w2[d2], s5r, pr[1]);
+            pi[1] = fma(w2[d2], s5i, pi[1]);
+        }
+        const R two_s = (R)2 * sgn;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            acc[4 + q][0] = fma(two_s, pr[q], -acc[4 + q][0]);
+            acc[4 + q][1] = fma(two_s, pi[q], -acc[4 + q][1]);
         }
     }
 

@@ -118,6 +118,12 @@ struct SynthArgs {
     int P1, P2, P3;     // padded extents (M + 3 per periodic axis); P3 = stored x3 planes (1 in 2D)
     int Q3lo;           // padded x3 index of the first stored plane
     int a3first, L3count; // x3 nodes the last two passes transform: a3first .. a3first + L3count - 1
+    // Maxwell plans keeping only the x3 >= -h3 planes: 1, and the in-plane
+    // transforms P_e of the odd fields' (e = 4, 5: xz, yz) Nyquist row j3 = -M3/2
+    // go through the last two passes as work plane L3count of those fields into
+    // nyqgrid [P2][P1][2] (padded like the grid)
+    int nyq;
+    void *nyqgrid;
 };
 
 // Far-series table entry for one in-plane index n: b = |beta_n|, ln b and 1/b
@@ -159,6 +165,7 @@ struct EvalArgs {
     int n1lo, n1hi, n2lo, n2hi;
     const PropEntry *prop;  // propagating indices (|alpha_n| <= k)
     const int *nprop;       // their number (device)
+    const void *nyqgrid;    // Maxwell half grids: in-plane Nyquist transforms of the odd fields ([P2][P1][2]), else null
     const double2 *exptab;  // (e^{-y_j}, y_j), y_j = (j - exptab_j0)/GF_EXPTAB_STEPS, j = 0 .. exptab_n - 1,
                             // followed by exptab_n float4 (hi, lo of e^{-y_j}, y_j, 0)
     int exptab_n, exptab_j0;

@@ -111,6 +111,8 @@ struct gf_plan_s {
     double T = 0;
     int P1 = 1, P2 = 1, P3 = 1;
     int Q3lo = 0, a3first = 0, L3count = 1;  // stored x3 planes of the gather grid (3D)
+    int nyq = 0;                      // Maxwell half grid: odd fields' Nyquist planes in nyqgrid
+    void *nyqgrid = nullptr;          // [P2][P1][2] complex
     size_t elem = 16;                 // bytes per complex value
     void *grid = nullptr;             // padded gather grid
     size_t grid_bytes = 0;
@@ -262,22 +264,25 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
     p->P3 = dim == 3 ? p->M[2] + 3 : 1;
     p->L3count = dim == 3 ? p->M[2] : 1;
     if (dim == 3) {
-        // The gather grid keeps only the x3 planes the near branch reads: stencil
-        // origins i0 from the smallest near |x3| or x3 to floor((c + c~)/h3) + 1 (one
-        // index of margin each way), padded planes i0 .. i0 + 3.  The grid of L_d is
-        // even in x3 (node a mirrors node M3 - a, the Nyquist row included), so a
-        // Helmholtz plan interpolates at |x3| and keeps the planes x3 >= -h3 only.  The
-        // Maxwell xz and yz fields are odd except for their Nyquist row (it has no
-        // mirror partner), so a Maxwell plan keeps the whole slab |x3| <= c.
+        // The gather grid keeps only the x3 planes the near branch reads at |x3|:
+        // stencil origins i0 from M3/2 - 1 (x3 >= -h3) to floor((c + c~)/h3) + 1 (one
+        // index of margin each way), padded planes i0 .. i0 + 3.  The grid of L_d and
+        // the even Maxwell fields (xx, yy, zz, xy) are even in x3: node a mirrors node
+        // M3 - a, the Nyquist row included.  The odd fields xz, yz (factor c^3 = q_j)
+        // are odd except for their Nyquist row j3 = -M3/2, which has no mirror
+        // partner and is even at the nodes: L(M3 - a) = -L(a) + 2 (-1)^(M3/2 + a) P(t)
+        // with P the in-plane transform of that row, which a Maxwell plan keeps
+        // beside the grid (nyqgrid) for the targets with x3 < 0.
         const int M3 = p->M[2];
         const double h3 = 2.0 * tr.c_tilde / M3;
-        const int i0min = p->nf == 1 ? M3 / 2 - 1 : std::max(0, (int)floor((tr.c_tilde - tr.c) / h3) - 1);
+        const int i0min = M3 / 2 - 1;
         const int i0max = std::min(M3 - 1, (int)floor((tr.c + tr.c_tilde) / h3) + 1);
         if (i0max + 3 <= M3 && i0min >= 1) {
             p->Q3lo = i0min;
             p->P3 = i0max + 3 - i0min + 1;
             p->a3first = p->Q3lo - 1;
             p->L3count = p->P3;
+            p->nyq = p->nf == 7 ? 1 : 0;
         }
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -370,7 +375,8 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
     p->stream = st;
     do {
         cudaError_t e;
-        if ((e = gf_dev_alloc(&p->grid, p->grid_bytes, st)) != cudaSuccess ||
+        if ((p->nyq && (e = gf_dev_alloc(&p->nyqgrid, (size_t)p->P1 * p->P2 * 2 * p->elem, st)) != cudaSuccess) ||
+            (e = gf_dev_alloc(&p->grid, p->grid_bytes, st)) != cudaSuccess ||
             (e = gf_dev_alloc(&p->tables, tab_bytes, st)) != cudaSuccess ||
             (e = gf_dev_alloc(&work, work_bytes, st)) != cudaSuccess) {
             st_err = fail(e == cudaErrorMemoryAllocation ? GF_ERR_NOMEM : GF_ERR_CUDA, "gf_plan: device allocation: %s",
@@ -445,6 +451,8 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
         sa.Q3lo = p->Q3lo;
         sa.a3first = p->a3first;
         sa.L3count = p->L3count;
+        sa.nyq = p->nyq;
+        sa.nyqgrid = p->nyqgrid;
         if (p->timing) cudaEventRecord(p->ev[0], st);
         if ((e = gf_launch_synth(sa, p->precision, st)) != cudaSuccess) {
             st_err = fail(GF_ERR_CUDA, "gf_plan: synthesis launch: %s", cudaGetErrorString(e));
@@ -531,6 +539,8 @@ gf_status gf_eval_grid(gf_plan_t p, void *dev_out, size_t out_bytes, void *cuda_
         fs.P3 = p->M[2] + 3;
         fs.a3first = 0;
         fs.L3count = p->M[2];
+        fs.nyq = 0;
+        fs.nyqgrid = nullptr;
         void *work = nullptr, *grid = nullptr;
         CU(gf_dev_alloc(&work, (size_t)p->M[0] * p->M[1] * p->M[2] * p->nf * p->elem, st));
         cudaError_t e = gf_dev_alloc(&grid, (size_t)fs.P1 * fs.P2 * fs.P3 * p->nf * p->elem, st);
@@ -646,6 +656,7 @@ gf_status gf_plan_eval_args(gf_plan_t p, const double *dev_xyz, int64_t n, int w
     a.exptab_n = p->exptab_n;
     a.exptab_j0 = p->exptab_j0;
     a.bmin = p->bmin_ev;
+    a.nyqgrid = p->nyqgrid;
     *a_out = a;
     return GF_OK;
 }
@@ -658,7 +669,7 @@ SynthArgs gf_plan_synth_args(gf_plan_t p) { return p->sa; }
 // (3D: only the stored x3 planes, compact; 2D: the whole grid)
 size_t gf_plan_work_bytes(gf_plan_t p)
 {
-    return (size_t)p->M[0] * p->M[1] * (p->dim == 3 ? p->L3count : 1) * p->nf * p->elem;
+    return (size_t)p->M[0] * p->M[1] * (p->dim == 3 ? p->L3count + p->nyq : 1) * p->nf * p->elem;
 }
 int gf_plan_precision(gf_plan_t p) { return p->precision; }
 
@@ -752,7 +763,7 @@ gf_status gf_destroy(gf_plan_t p)
     // the plan may have been used on any stream: wait for the device, then hand
     // the buffers back to the pool
     cudaDeviceSynchronize();
-    void *bufs[] = {p->grid, p->tables, p->btab, p->prop, p->exptab};
+    void *bufs[] = {p->grid, p->nyqgrid, p->tables, p->btab, p->prop, p->exptab};
     for (void *b : bufs) gf_dev_free(b, 0);
     for (int i = 0; i < 6; ++i)
         if (p->ev[i]) cudaEventDestroy(p->ev[i]);

@@ -355,6 +355,15 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
         }
     }
     __syncthreads();
+    C *W = reinterpret_cast<C *>(a.work);
+    const int planes = a.L3count + a.nyq;  // 3D work planes per field
+    if (a.nyq) {
+        // the odd fields' Nyquist coefficients (b = n/2, j3 = -n/2), before the x3 transform
+        for (int i = threadIdx.x; i < 2 * TJ; i += blockDim.x) {
+            const int f = 4 + i / TJ, t = i % TJ;
+            W[((size_t)f * planes + a.L3count) * ncols + col0 + t] = buf0[(f * TJ + t) * n + (n >> 1)];
+        }
+    }
     {
         const int nm = (n >> 1) - 1;  // b = n/2 + 1 .. n - 1
         for (int i = threadIdx.x; i < nf * TJ * nm; i += blockDim.x) {
@@ -367,7 +376,6 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
     }
     __syncthreads();
     C *res = stockham_inverse(buf0, buf1, n, lg, nf * TJ, tw);
-    C *W = reinterpret_cast<C *>(a.work);
     if (a.dim == 3) {
         // only the x3 nodes the last two passes transform (a3first .. a3first +
         // L3count - 1), compact: work plane y holds node a3first + y, whose output
@@ -377,7 +385,7 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
             const int t = i % TJ, rest = i / TJ;
             const int y = rest % a.L3count, f = rest / a.L3count;
             const int l = (a.a3first + y + (n >> 1)) & (n - 1);
-            W[((size_t)f * a.L3count + y) * ncols + col0 + t] = res[(f * TJ + t) * n + l];
+            W[((size_t)f * planes + y) * ncols + col0 + t] = res[(f * TJ + t) * n + l];
         }
     } else {
         const int tot = nf * n * TJ;
@@ -403,7 +411,9 @@ __device__ void synth_x2_body(const SynthArgs &a, int bx, int y, int f, unsigned
     C *buf0 = tw + (n >> 1);
     C *buf1 = buf0 + TJ * n;
     const int b10 = bx * TJ;
-    C *W = reinterpret_cast<C *>(a.work) + ((size_t)f * a.L3count + y) * (size_t)a.M2 * a.M1;
+    // work plane L3count (half-grid Maxwell plans) holds the Nyquist row of the odd fields only
+    if (y == a.L3count && f != 4 && f != 5) return;
+    C *W = reinterpret_cast<C *>(a.work) + ((size_t)f * (a.L3count + a.nyq) + y) * (size_t)a.M2 * a.M1;
     load_twiddles<R>(tw, n);
     for (int i = threadIdx.x; i < TJ * n; i += blockDim.x) {
         int t = i % TJ, b2 = i / TJ;
@@ -441,7 +451,7 @@ __device__ void synth_x1_body(const SynthArgs &a, int blk, unsigned char *smem)
     C *buf0 = tw + (n >> 1);
     C *buf1 = buf0 + RB * nf * n;
     // row = y * M2 + l2 (3D: x3 node a3first + y at compact work plane y); 2D: l2
-    const size_t fstride = (size_t)(a.dim == 3 ? a.L3count * a.M2 : a.Mlast) * a.M1;
+    const size_t fstride = (size_t)(a.dim == 3 ? (a.L3count + a.nyq) * a.M2 : a.Mlast) * a.M1;
     const C *W = reinterpret_cast<const C *>(a.work);
     const int row0 = blk * RB;
     load_twiddles<R>(tw, n);
@@ -466,10 +476,23 @@ __device__ void synth_x1_body(const SynthArgs &a, int blk, unsigned char *smem)
         }
         int p2[3], p3[3];
         int n2 = pad_dests((l2 + (a.M2 >> 1)) % a.M2, a.M2, p2);
+        const C *rr = res + (size_t)r * nf * n;
+        if (a.dim == 3 && a.nyq && row / a.M2 == a.L3count) {
+            // Nyquist row of the odd fields -> nyqgrid [p2][p1][2]
+            C *NG = reinterpret_cast<C *>(a.nyqgrid);
+            for (int d2 = 0; d2 < n2; ++d2) {
+                C *dst = NG + (size_t)p2[d2] * a.P1 * 2;
+                for (int i = threadIdx.x; i < 2 * a.P1; i += blockDim.x) {
+                    const int p1 = i >> 1, f = 4 + (i & 1);
+                    const int a1 = (p1 - 1 + n) % n;
+                    dst[i] = rr[f * n + (a1 + (n >> 1)) % n];
+                }
+            }
+            continue;
+        }
         int n3 = 1;
         p3[0] = 0;
         if (a.dim == 3) n3 = pad_dests(a3, a.M3, p3);
-        const C *rr = res + (size_t)r * nf * n;
         for (int d3 = 0; d3 < n3; ++d3) {
             // only the stored planes Q3lo .. Q3lo + P3 - 1
             const int q3 = p3[d3] - a.Q3lo;
@@ -554,7 +577,8 @@ __global__ void __launch_bounds__(256) synth_x2_pass_batch(const SynthArgs *args
         const int nbx = sa.M1 / sa.TJ2;
         const int bx = loc % nbx;
         loc /= nbx;
-        const int y = loc % sa.L3count, f = loc / sa.L3count;
+        const int pl = sa.L3count + sa.nyq;
+        const int y = loc % pl, f = loc / pl;
         synth_x2_body<R>(sa, bx, y, f, smem);
         __syncthreads();
     }
@@ -632,7 +656,7 @@ void synth_config_t(SynthArgs &a, int tj_max, size_t sm[3])
     a.lg1 = ilog2(a.M1);
     sm[1] = a.dim == 3 ? sizeof(C) * (a.M2 / 2 + 2 * TJ2 * a.M2) : 0;
     // last pass: RB1 rows per CTA (up to 2048 values, a power of two dividing the rows)
-    const int nrows = a.dim == 3 ? a.L3count * a.M2 : a.M2;
+    const int nrows = a.dim == 3 ? (a.L3count + a.nyq) * a.M2 : a.M2;
     int RB1 = 8;
     while (RB1 > 1 && (RB1 > nrows || RB1 * a.nf * a.M1 > 2048 ||
                        sizeof(C) * (a.M1 / 2 + 2 * a.nf * RB1 * a.M1) > 160 * 1024))
@@ -655,12 +679,12 @@ cudaError_t launch_synth_t(const SynthArgs &a0, cudaStream_t s)
     if (a.dim == 3) {
         e = cudaFuncSetAttribute(synth_x2_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[1]);
         if (e != cudaSuccess) return e;
-        synth_x2_pass<R><<<dim3(a.M1 / a.TJ2, a.L3count, a.nf), 256, sm[1], s>>>(a);
+        synth_x2_pass<R><<<dim3(a.M1 / a.TJ2, a.L3count + a.nyq, a.nf), 256, sm[1], s>>>(a);
         gf_count_launch(1);
     }
     e = cudaFuncSetAttribute(synth_x1_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[2]);
     if (e != cudaSuccess) return e;
-    int rows = (a.dim == 3) ? a.L3count * a.M2 : a.M2;
+    int rows = (a.dim == 3) ? (a.L3count + a.nyq) * a.M2 : a.M2;
     synth_x1_pass<R><<<rows / a.RB1, 256, sm[2], s>>>(a);
     gf_count_launch(1);
     return cudaGetLastError();
