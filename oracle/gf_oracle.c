@@ -710,6 +710,103 @@ void or_eval(const or_params *p, const double *grid, const double *x, long n, in
     for (long i = 0; i < n; ++i) eval_point(p, g, x + (size_t)p->dim * i, which, o + (size_t)ne * i);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Far-region grid.  The paper sums the eigen-series (he) for |x3| > c         */
+/* (Algorithm 2 step 2b); the far-region grid replaces it on a slab           */
+/* c < |x3| <= zmax by the same device as the near branch: for z = |x3| > 0   */
+/*   F(t, z) = e^{-i alpha.t} G_d(t, z)                                       */
+/*           = (i/8pi^2) sum_n beta_n^{-1} e^{i beta_n z} e^{i n.t}           */
+/* is smooth and 2pi-periodic in t, its coefficients decaying like            */
+/* e^{-|n| z}.  Planes m = 0 .. Nz + 2 sit at z_m = c + (m - 1) hz,           */
+/* hz = (zmax - c)/Nz; on each, F at the Mf1 x Mf2 in-plane nodes (node l at  */
+/* x = l h, h = 2 pi/Mf, as for the near grid) is the inverse DFT of           */
+/* a_n(z_m) = (i/8pi^2) e^{i beta_n z_m}/beta_n over -Mf/2 <= n_i < Mf/2.      */
+/* Maxwell (Sec. 4): seven fields, the six combined                           */
+/* (delta_pq - c^p c^q/k^2) a_n with c = (alpha_n, beta_n) (z > 0), then a_n. */
+/* Layout [field][m][l2][l1].                                                 */
+/* ------------------------------------------------------------------------ */
+void or_far_grid(const or_params *p, int Mf1, int Mf2, int Nz, double zmax, double *out)
+{
+    const int nz = Nz + 3, nf = nfields(p);
+    const double hz = (zmax - p->c) / Nz;
+    const size_t per = (size_t)Mf1 * Mf2 * nz;
+    cplx *g = (cplx *)out;
+    for (int m = 0; m < nz; ++m) {
+        const double z = p->c + (m - 1) * hz;
+        for (int b2 = 0; b2 < Mf2; ++b2)
+            for (int b1 = 0; b1 < Mf1; ++b1) {
+                const int n1 = freq_of(b1, Mf1), n2 = freq_of(b2, Mf2);
+                const double a1 = p->alpha[0] + n1, a2 = p->alpha[1] + n2;
+                const cplx beta = beta_of(p->k, a1 * a1 + a2 * a2);
+                const cplx an = (I / (8.0 * M_PI * M_PI)) * cexp(I * beta * z) / beta;
+                const size_t idx = ((size_t)m * Mf2 + b2) * Mf1 + b1;
+                if (nf == 1) {
+                    g[idx] = an;
+                } else {
+                    const cplx cv[3] = {a1, a2, beta};
+                    for (int e = 0; e < 6; ++e) {
+                        const cplx d = (PQ[e][0] == PQ[e][1]) ? 1.0 : 0.0;
+                        g[(size_t)e * per + idx] = (d - cv[PQ[e][0]] * cv[PQ[e][1]] / (p->k * p->k)) * an;
+                    }
+                    g[(size_t)6 * per + idx] = an;
+                }
+            }
+    }
+    /* naive inverse DFT along x1, then x2, of every plane of every field */
+    int dims[3] = {Mf1, Mf2, nz};
+    for (int f = 0; f < nf; ++f) {
+        idft_axis(g + (size_t)f * per, dims, 3, 0);
+        idft_axis(g + (size_t)f * per, dims, 3, 1);
+    }
+}
+
+/* Far-grid evaluation of targets with c < |x3| <= zmax (the caller sends only
+ * those): reduce t, interpolate the far grid by tensor cubics (in-plane as the
+ * near grid, periodic; in z from the plane origin c - hz with the stencil
+ * origin clamped to Nz, the last full interval), lift by e^{i alpha.t}
+ * e^{i 2 pi alpha.m}.  which: 1 = G_d, 2 / 3 = six tensor entries (/ + G_d);
+ * the xz and yz entries change sign with x3. */
+void or_eval_far_grid(const or_params *p, int Mf1, int Mf2, int Nz, double zmax, const double *fgrid,
+                      const double *x, long n, int which, double *out)
+{
+    const int nz = Nz + 3, ne = n_entries(which);
+    const double hz = (zmax - p->c) / Nz;
+    const size_t per = (size_t)Mf1 * Mf2 * nz;
+    const cplx *g = (const cplx *)fgrid;
+    cplx *o = (cplx *)out;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (long i = 0; i < n; ++i) {
+        const double *xi = x + 3 * i;
+        double t1, m1, t2, m2;
+        reduce_period(xi[0], &t1, &m1);
+        reduce_period(xi[1], &t2, &m2);
+        const double z = fabs(xi[2]);
+        int i1[4], i2[4];
+        double w1[4], w2[4], w3[4];
+        stencil(t1, -M_PI, 2.0 * M_PI / Mf1, Mf1, i1, w1);
+        stencil(t2, -M_PI, 2.0 * M_PI / Mf2, Mf2, i2, w2);
+        double u3 = (z - (p->c - hz)) / hz;
+        double i03 = floor(u3);
+        if (i03 > (double)Nz) i03 = (double)Nz;
+        lagrange4(u3 - i03, w3);
+        const int m0 = (int)i03 - 1;
+        double ph = p->alpha[0] * m1 + p->alpha[1] * m2;
+        ph -= round(ph);
+        const cplx lift = cexp(I * (p->alpha[0] * t1 + p->alpha[1] * t2)) * cexp(2.0 * M_PI * I * ph);
+        for (int e = 0; e < ne; ++e) {
+            const int f = (which <= 1) ? 0 : (e < 6 ? e : 6);
+            cplx s = 0.0;
+            for (int c3 = 0; c3 < 4; ++c3)
+                for (int b = 0; b < 4; ++b)
+                    for (int a = 0; a < 4; ++a)
+                        s += w3[c3] * w2[b] * w1[a] *
+                             g[(size_t)f * per + ((size_t)(m0 + c3) * Mf2 + i2[b]) * Mf1 + i1[a]];
+            if (which >= 2 && (e == 4 || e == 5) && xi[2] < 0.0) s = -s;
+            o[(size_t)ne * i + e] = lift * s;
+        }
+    }
+}
+
 /* Grid values at selected nodes only, straight from the truncated series
  * (no FFT, no row-column split): L_N(x_l) = V^{-1} sum_j C_j e^{2 pi i sum j_i l_i / M_i}.
  * Used to check single grid values of very large grids. nodes: [n][dim] ints. */

@@ -83,6 +83,8 @@ def lib():
         _lib.or_series.argtypes = [P, p, l, i, p]
         _lib.or_interp.argtypes = [P, p, p, l, p]
         _lib.or_grid_nodes.argtypes = [P, p, i, p, l, p]
+        _lib.or_far_grid.argtypes = [P, i, i, i, d, p]
+        _lib.or_eval_far_grid.argtypes = [P, i, i, i, d, p, p, l, i, p]
         _lib.or_set_threads.restype = i
         _lib.or_set_threads.argtypes = [i]
     return _lib
@@ -242,3 +244,26 @@ def interp(pb: Problem, g: np.ndarray, y: np.ndarray) -> np.ndarray:
 def run(pb: Problem, x: np.ndarray, which: int) -> np.ndarray:
     """Whole path: coefficients, grid, point values."""
     return evaluate(pb, grid(pb), x, which)
+
+
+def far_grid(pb: Problem, Mf, Nz: int, zmax: float) -> np.ndarray:
+    """Far-region grid: F = e^{-i alpha.t} G_d on planes z_m = c + (m - 1) hz,
+    m = 0 .. Nz + 2, by a naive inverse DFT of the series terms over n in S_Mf;
+    shape (nfields, Nz + 3, Mf2, Mf1)."""
+    Mf1, Mf2 = (Mf, Mf) if np.isscalar(Mf) else Mf
+    out = np.zeros((pb.nfields, Nz + 3, Mf2, Mf1), dtype=np.complex128)
+    p = pb.cstruct()
+    lib().or_far_grid(ctypes.byref(p), int(Mf1), int(Mf2), int(Nz), float(zmax), _ptr(out))
+    return out
+
+
+def far_grid_evaluate(pb: Problem, fg: np.ndarray, Nz: int, zmax: float, x: np.ndarray, which: int) -> np.ndarray:
+    """Targets with c < |x3| <= zmax from the far-region grid (tensor cubics + phase)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    fg = np.ascontiguousarray(fg, dtype=np.complex128)
+    ne = N_ENTRIES[which]
+    out = np.zeros((x.shape[0], ne), dtype=np.complex128)
+    p = pb.cstruct()
+    lib().or_eval_far_grid(ctypes.byref(p), int(fg.shape[3]), int(fg.shape[2]), int(Nz), float(zmax), _ptr(fg),
+                           _ptr(x), x.shape[0], int(which), _ptr(out))
+    return out
