@@ -68,7 +68,7 @@ enum {                                            /* gf_eval_points `which` */
 
 /* Method parameters.  Defaults (gf_trunc_default): c = 0.6, c~ = 1 (Sec. 5),
  * eps = 0.45, series_tol = 0 (automatic), quad_nodes = 64, GF_FP64,
- * GF_HELMHOLTZ, GF_PERTURB_CTILDE.
+ * GF_HELMHOLTZ, GF_PERTURB_CTILDE, far_grid_M = 0 (far branch by the series).
  *   c          |x_last| <= c: grid + interpolation; > c: eigen-series (Alg. 1-3, step 2b)
  *   c_tilde    half period of the artificial periodisation in x_last (c < c~); the cutoff
  *              X(t) falls from 1 at t = c to 0 at t = (c + c~)/2 (Sec. 2.1)
@@ -84,6 +84,18 @@ enum {                                            /* gf_eval_points `which` */
  *   kind       GF_MAXWELL (3D only) stores seven fields per node: the six combined
  *              fields (delta_pq - c^p c^q / k^2) L_d (Sec. 4; one interpolation per
  *              tensor entry) and L_d itself (for G_d)
+ *   far_grid_M (3D) 0: far targets (|x3| > c) by the eigen-series (he), as in
+ *              Algorithm 2 step 2b.  > 0: the far-region grid, which the paper does
+ *              not have: F = e^{-i alpha.t} G_d (and its Maxwell fields) synthesised
+ *              on planes z_m = c + (m - 1) hz, m = 0 .. far_grid_nz + 2, hz =
+ *              (far_grid_zmax - c)/far_grid_nz, each by an inverse FFT of the series
+ *              terms (i/8pi^2) e^{i beta_n z_m}/beta_n over far_grid_M x far_grid_M
+ *              in-plane indices (a power of two in [16, 2048]), then far targets with
+ *              |x3| <= far_grid_zmax interpolated by tensor cubics like the near
+ *              branch (the others keep the series).  Interpolation caps its accuracy
+ *              at O(h^4): about 1.4e-5 (M = 128), 7e-7 (256), 5e-8 (512) relative
+ *              to max|G| at c = 0.6; meant for GF_FP32_SPLIT plans.
+ *   far_grid_nz  intervals in z (0: 16); far_grid_zmax  end of the slab (<= 0: c~)
  */
 typedef struct {
     double c, c_tilde, eps;
@@ -92,6 +104,8 @@ typedef struct {
     int precision;
     int kind;
     int resonance_policy;
+    int far_grid_M, far_grid_nz;
+    double far_grid_zmax;
 } gf_trunc_t;
 
 /* Fill *t with the defaults listed above.  Returns GF_ERR_ARG if t is NULL. */
@@ -310,6 +324,9 @@ typedef struct {
     int quad_nodes;
     int series_n1_lo, series_n1_hi, series_n2_lo, series_n2_hi; /* far-series index box */
     size_t grid_device_bytes;            /* padded gather grid held by the plan */
+    int far_grid_M, far_grid_nz;         /* far-region grid (0: none) */
+    double far_grid_zmax;
+    size_t far_grid_device_bytes;
 } gf_plan_info_t;
 gf_status gf_plan_get_info(gf_plan_t plan, gf_plan_info_t *info);
 

@@ -324,10 +324,101 @@ __device__ __forceinline__ void near_point(const EvalArgs &a, int64_t i, double 
     }
 }
 
+// Far-region grid at one target i (valid, finite, c < |x3| <= fzmax): the same
+// cell reduction as the near branch, tensor cubic interpolation of the far
+// planes (in z from fz0 with the stencil origin clamped to the last full
+// interval), and the lift e^{i alpha.t} e^{i 2 pi <alpha.m>}; the Maxwell xz and
+// yz entries change sign with x3.  No singular part: |x3| > c >= 2 eps.
+template <typename R, int NF>
+__device__ __forceinline__ void far_grid_point(const EvalArgs &a, int64_t i, double x1, double x2, double x3)
+{
+    typedef typename cplx_t<R>::T C;
+    const C *G = reinterpret_cast<const C *>(a.fargrid);
+    const int ne = n_entries(a.which);
+    C *o = reinterpret_cast<C *>(a.out) + i * ne;
+    double t1, m1, t2, m2;
+    reduce_period(x1, t1, m1);
+    reduce_period(x2, t2, m2);
+    double f1, f2, f3;
+    const int i1 = stencil_origin(t1, -GF_PI, a.fh1, 1.0 / a.fh1, a.fM1, f1);
+    const int i2 = stencil_origin(t2, -GF_PI, a.fh2, 1.0 / a.fh2, a.fM2, f2);
+    // planes are not padded: the stencil planes are i0 - 1 .. i0 + 2, i0 <= fNZ - 3
+    const int i3 = stencil_origin(fabs(x3), a.fz0, a.fhz, 1.0 / a.fhz, a.fNZ - 2, f3) - 1;
+    R w1[4], w2[4], w3[4];
+    lagrange4<R>((R)f1, w1);
+    lagrange4<R>((R)f2, w2);
+    lagrange4<R>((R)f3, w3);
+    R acc[NF][2];
+#pragma unroll
+    for (int e = 0; e < NF; ++e) acc[e][0] = acc[e][1] = (R)0;
+#pragma unroll
+    for (int d3 = 0; d3 < 4; ++d3) {
+#pragma unroll
+        for (int d2 = 0; d2 < 4; ++d2) {
+            const C *row = G + (((size_t)(i3 + d3) * a.fP2 + (i2 + d2)) * a.fP1 + i1) * NF;
+            const R w23 = w3[d3] * w2[d2];
+#pragma unroll
+            for (int e = 0; e < NF; ++e) {
+                R sr = 0, si = 0;
+#pragma unroll
+                for (int d1 = 0; d1 < 4; ++d1) {
+                    C g = __ldg(row + d1 * NF + e);
+                    sr = fma(w1[d1], g.x, sr);
+                    si = fma(w1[d1], g.y, si);
+                }
+                acc[e][0] = fma(w23, sr, acc[e][0]);
+                acc[e][1] = fma(w23, si, acc[e][1]);
+            }
+        }
+    }
+    if (sizeof(R) == 4) {
+        double ph = a.a1 * m1 + a.a2 * m2;
+        ph -= rint(ph);
+        float sl, cl, sa, ca;
+        sincospif(2.0f * (float)ph, &sl, &cl);
+        sincosf((float)a.a1 * (float)t1 + (float)a.a2 * (float)t2, &sa, &ca);
+        const float2 lift = cmulf(make_float2(ca, sa), make_float2(cl, sl));
+        float2 *of = reinterpret_cast<float2 *>(o);
+        for (int e = 0; e < ne; ++e) {
+            const int f = NF == 1 ? 0 : (e < 6 ? e : 6);
+            float2 v = cmulf(lift, make_float2((float)acc[f][0], (float)acc[f][1]));
+            if (NF > 1 && (e == 4 || e == 5) && x3 < 0.0) v = make_float2(-v.x, -v.y);
+            of[e] = v;
+        }
+    } else {
+        const double2 lat = lattice_phase(a.a1, m1, a.a2, m2);
+        double sa, ca;
+        sincos(a.a1 * t1 + a.a2 * t2, &sa, &ca);
+        const double2 lift = cmul(make_double2(ca, sa), lat);
+        for (int e = 0; e < ne; ++e) {
+            const int f = NF == 1 ? 0 : (e < 6 ? e : 6);
+            double2 v = cmul(lift, make_double2((double)acc[f][0], (double)acc[f][1]));
+            if (NF > 1 && (e == 4 || e == 5) && x3 < 0.0) v = make_double2(-v.x, -v.y);
+            store_out(o + e, v);
+        }
+    }
+}
+
+// Append to the end of the near list, backwards (far-grid targets): the list
+// holds the near targets from its start and these from its end, so that the
+// warps of the list kernel see one kind or the other.
+__device__ __forceinline__ void push_back_end(bool take, int i, int *list, int64_t cap, int *count)
+{
+    unsigned mask = __ballot_sync(0xffffffffu, take);
+    if (mask == 0u) return;
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(mask) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(count, __popc(mask));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (take) list[cap - 1 - (base + __popc(mask & ((1u << lane) - 1u)))] = i;
+}
+
 // MODE 0: classify every target (far list, bucket histogram, zeroed far
-// outputs, NaN for non-finite ones) and evaluate the near ones here; MODE 1:
-// classify only, appending the near targets to a.near_idx, so that near3d_list
-// evaluates them in full warps.
+// outputs, NaN for non-finite ones) and evaluate the near ones (and those of
+// the far-region grid) here; MODE 1: classify only, appending the near targets
+// to the start of a.near_idx and the far-grid targets to its end, so that
+// near3d_list evaluates them in full warps.
 template <typename R, int NF, int MODE>
 __device__ void near3d_tiles(const EvalArgs &a, int64_t base0, int64_t stride, int *hist)
 {
@@ -352,10 +443,20 @@ __device__ void near3d_tiles(const EvalArgs &a, int64_t base0, int64_t stride, i
             isfar = false;
             valid = false;
         }
+        // far targets inside the far-region grid's slab are gathered, not summed
+        const bool fgrid = isfar && a.fargrid != nullptr && fabs(x3) <= a.fzmax;
+        if (fgrid) isfar = false;
         push_far(isfar, (int)i, a.far_idx, a.far_count);
-        // (every lane of the warp reaches both appends: they vote by ballot)
-        if (MODE == 1) push_far(valid && finite && !isfar, (int)i, a.near_idx, a.far_count + GF_NEAR_SLOT);
+        // (every lane of the warp reaches the appends: they vote by ballot)
+        if (MODE == 1) {
+            push_far(valid && finite && !isfar && !fgrid, (int)i, a.near_idx, a.far_count + GF_NEAR_SLOT);
+            push_back_end(fgrid, (int)i, a.near_idx, a.n, a.far_count + GF_FGRID_SLOT);
+        }
         C *o = out + i * ne;
+        if (fgrid) {
+            if (MODE == 0) far_grid_point<R, NF>(a, i, x1, x2, x3);
+            continue;
+        }
         if (isfar) {
             // the far kernels add their row slabs into these entries
             atomicAdd(&hist[far_bucket(fabs(x3), a.c)], 1);
@@ -371,16 +472,30 @@ __device__ void near3d_tiles(const EvalArgs &a, int64_t base0, int64_t stride, i
     }
 }
 
-// The near targets listed by a MODE-1 classification pass, one per thread.
+// Entry j of the targets listed by a MODE-1 classification pass: the near
+// targets (j < nnear) from the start of the list, then the far-grid ones from
+// its end.
+template <typename R, int NF>
+__device__ __forceinline__ void list_point(const EvalArgs &a, int j, int nnear, double ih1, double ih2, double ih3)
+{
+    if (j < nnear) {
+        const int64_t i = a.near_idx[j];
+        near_point<R, NF>(a, i, a.x[3 * i], a.x[3 * i + 1], a.x[3 * i + 2], ih1, ih2, ih3);
+    } else {
+        const int64_t i = a.near_idx[a.n - 1 - (j - nnear)];
+        far_grid_point<R, NF>(a, i, a.x[3 * i], a.x[3 * i + 1], a.x[3 * i + 2]);
+    }
+}
+
+// The targets listed by a MODE-1 classification pass, one per thread.
 template <typename R, int NF>
 __global__ void __launch_bounds__(256) near3d_list(EvalArgs a)
 {
-    const int count = a.far_count[GF_NEAR_SLOT];
+    const int nnear = a.far_count[GF_NEAR_SLOT];
+    const int count = nnear + a.far_count[GF_FGRID_SLOT];
     const double ih1 = 1.0 / a.h1, ih2 = 1.0 / a.h2, ih3 = 1.0 / a.h3;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < count; j += gridDim.x * blockDim.x) {
-        const int64_t i = a.near_idx[j];
-        near_point<R, NF>(a, i, a.x[3 * i], a.x[3 * i + 1], a.x[3 * i + 2], ih1, ih2, ih3);
-    }
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < count; j += gridDim.x * blockDim.x)
+        list_point<R, NF>(a, j, nnear, ih1, ih2, ih3);
 }
 
 template <typename R, int NF, int MODE = 0>
@@ -442,13 +557,12 @@ __global__ void __launch_bounds__(256) near3d_list_batch(const EvalArgs *args, i
         __syncthreads();
         if (threadIdx.x == 0) sa = args[p];
         __syncthreads();
-        const int count = sa.far_count[GF_NEAR_SLOT];
+        const int nnear = sa.far_count[GF_NEAR_SLOT];
+        const int count = nnear + sa.far_count[GF_FGRID_SLOT];
         const double ih1 = 1.0 / sa.h1, ih2 = 1.0 / sa.h2, ih3 = 1.0 / sa.h3;
         const int cta = (int)((blockIdx.x + (unsigned)rot) % gridDim.x);
-        for (int j = cta * blockDim.x + threadIdx.x; j < count; j += gridDim.x * blockDim.x) {
-            const int64_t i = sa.near_idx[j];
-            near_point<R, NF>(sa, i, sa.x[3 * i], sa.x[3 * i + 1], sa.x[3 * i + 2], ih1, ih2, ih3);
-        }
+        for (int j = cta * blockDim.x + threadIdx.x; j < count; j += gridDim.x * blockDim.x)
+            list_point<R, NF>(sa, j, nnear, ih1, ih2, ih3);
         rot = (int)((rot + (count + blockDim.x - 1) / blockDim.x) % gridDim.x);
     }
 }

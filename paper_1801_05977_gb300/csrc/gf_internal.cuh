@@ -124,6 +124,9 @@ struct SynthArgs {
     // nyqgrid [P2][P1][2] (padded like the grid)
     int nyq;
     void *nyqgrid;
+    // far-region grid: the x3 axis is a run of L3count planes, not periodic; the
+    // last pass writes work plane y to grid plane y (no halo, no wrap)
+    int zlinear;
 };
 
 // Far-series table entry for one in-plane index n: b = |beta_n|, ln b and 1/b
@@ -166,6 +169,12 @@ struct EvalArgs {
     const PropEntry *prop;  // propagating indices (|alpha_n| <= k)
     const int *nprop;       // their number (device)
     const void *nyqgrid;    // Maxwell half grids: in-plane Nyquist transforms of the odd fields ([P2][P1][2]), else null
+    // far-region grid (null: far targets by the series): planes [fNZ][fP2][fP1][nf],
+    // plane m at z = fz0 + m fhz, in-plane node spacing fh1, fh2 (padded like the
+    // near grid); targets with c < |x3| <= fzmax read it
+    const void *fargrid;
+    int fM1, fM2, fNZ, fP1, fP2;
+    double fz0, fhz, fzmax, fh1, fh2;
     const double2 *exptab;  // (e^{-y_j}, y_j), y_j = (j - exptab_j0)/GF_EXPTAB_STEPS, j = 0 .. exptab_n - 1,
                             // followed by exptab_n float4 (hi, lo of e^{-y_j}, y_j, 0)
     int exptab_n, exptab_j0;
@@ -188,7 +197,9 @@ struct EvalArgs {
 #define GF_WORK_SLOT (1 + 2 * GF_FAR_BUCKETS)
 #define GF_TAIL_SLOT (2 + 2 * GF_FAR_BUCKETS)
 #define GF_NEAR_SLOT (3 + 2 * GF_FAR_BUCKETS)
-#define GF_SCRATCH_COUNTERS (4 + 2 * GF_FAR_BUCKETS)
+// [GF_FGRID_SLOT] far-grid targets, listed from the end of the near list backwards
+#define GF_FGRID_SLOT (4 + 2 * GF_FAR_BUCKETS)
+#define GF_SCRATCH_COUNTERS (5 + 2 * GF_FAR_BUCKETS)
 
 // A sweep of plans run as batched persistent launches: per-pass virtual-block
 // prefix sums over the pairs (device arrays of np + 1 ints), the per-pair
@@ -221,6 +232,10 @@ cudaError_t gf_launch_eval_batch(const EvalBatch &b, int precision, cudaStream_t
 cudaError_t gf_launch_series_tables(const EvalArgs &a, int precision, double2 *exptab, PropEntry *prop, int *nprop,
                                     const int pbox[4], cudaStream_t s);
 cudaError_t gf_launch_e_table(const double *tt, int Q, int Mlast, double qs, double2 *E, float2 *Ef, cudaStream_t s);
+// far-region grid: the planes' coefficients into a.work ([nf][L3count][M2][M1], FFT
+// order), then the x2 and x1 passes into a.grid (a.zlinear set)
+cudaError_t gf_launch_far_grid(const SynthArgs &a, int precision, double k, double a1, double a2, double z0,
+                               double hz, cudaStream_t s);
 
 // runtime.cu: stream-ordered pool allocations, pinned upload staging
 cudaError_t gf_dev_alloc(void **ptr, size_t bytes, cudaStream_t s);

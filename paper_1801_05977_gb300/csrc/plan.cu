@@ -113,6 +113,11 @@ struct gf_plan_s {
     int Q3lo = 0, a3first = 0, L3count = 1;  // stored x3 planes of the gather grid (3D)
     int nyq = 0;                      // Maxwell half grid: odd fields' Nyquist planes in nyqgrid
     void *nyqgrid = nullptr;          // [P2][P1][2] complex
+    // far-region grid (far_grid_M > 0): [fNZ][fM + 3][fM + 3][nf], plane m at z = fz0 + m fhz
+    void *fargrid = nullptr;
+    size_t far_bytes = 0;
+    int fM = 0, fNZ = 0;
+    double fz0 = 0, fhz = 0, fzmax = 0;
     size_t elem = 16;                 // bytes per complex value
     void *grid = nullptr;             // padded gather grid
     size_t grid_bytes = 0;
@@ -173,6 +178,9 @@ gf_status gf_trunc_default(gf_trunc_t *t)
     t->precision = GF_FP64;
     t->kind = GF_HELMHOLTZ;
     t->resonance_policy = GF_PERTURB_CTILDE;
+    t->far_grid_M = 0;
+    t->far_grid_nz = 0;
+    t->far_grid_zmax = 0.0;
     return GF_OK;
 }
 
@@ -200,6 +208,16 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
     if (tr.precision != GF_FP64 && tr.precision != GF_FP32_SPLIT) return fail(GF_ERR_ARG, "gf_plan: bad precision");
     if (tr.kind != GF_HELMHOLTZ && tr.kind != GF_MAXWELL) return fail(GF_ERR_ARG, "gf_plan: bad kind");
     if (tr.kind == GF_MAXWELL && dim != 3) return fail(GF_ERR_ARG, "gf_plan: the Maxwell tensor needs dim = 3");
+    if (tr.far_grid_M != 0) {
+        if (dim != 3) return fail(GF_ERR_ARG, "gf_plan: the far-region grid is for 3D plans");
+        if (!pow2_in(tr.far_grid_M, 16, 2048))
+            return fail(GF_ERR_ARG, "gf_plan: far_grid_M = %d is not a power of two in [16, 2048]", tr.far_grid_M);
+        if (tr.far_grid_nz == 0) tr.far_grid_nz = 16;
+        if (tr.far_grid_nz < 1 || tr.far_grid_nz > 4096) return fail(GF_ERR_ARG, "gf_plan: far_grid_nz out of [1, 4096]");
+        if (!(tr.far_grid_zmax > 0.0)) tr.far_grid_zmax = tr.c_tilde;
+        if (!(tr.far_grid_zmax > tr.c) || !isfinite(tr.far_grid_zmax))
+            return fail(GF_ERR_ARG, "gf_plan: need far_grid_zmax > c");
+    }
     if (!(tr.series_tol > 0.0)) tr.series_tol = tr.precision == GF_FP64 ? 1e-16 : 1e-8;
     if (!(tr.series_tol < 1.0)) return fail(GF_ERR_ARG, "gf_plan: series_tol must be < 1");
     const double a1 = alpha[0], a2 = dim == 3 ? alpha[1] : 0.0;
@@ -458,6 +476,43 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
             st_err = fail(GF_ERR_CUDA, "gf_plan: synthesis launch: %s", cudaGetErrorString(e));
             break;
         }
+        if (tr.far_grid_M > 0) {
+            // far-region grid: planes z_m = c + (m - 1) hz, m = 0 .. nz + 2
+            p->fM = tr.far_grid_M;
+            p->fNZ = tr.far_grid_nz + 3;
+            p->fhz = (tr.far_grid_zmax - c) / tr.far_grid_nz;
+            p->fz0 = c - p->fhz;
+            p->fzmax = tr.far_grid_zmax;
+            const int fP = p->fM + 3;
+            p->far_bytes = (size_t)fP * fP * p->fNZ * p->nf * p->elem;
+            void *fwork = nullptr;
+            if ((e = gf_dev_alloc(&p->fargrid, p->far_bytes, st)) != cudaSuccess ||
+                (e = gf_dev_alloc(&fwork, (size_t)p->fM * p->fM * p->fNZ * p->nf * p->elem, st)) != cudaSuccess) {
+                st_err = fail(e == cudaErrorMemoryAllocation ? GF_ERR_NOMEM : GF_ERR_CUDA,
+                              "gf_plan: device allocation (far-region grid): %s", cudaGetErrorString(e));
+                if (fwork) gf_dev_free(fwork, st);
+                break;
+            }
+            SynthArgs fa = sa;
+            fa.M1 = fa.M2 = p->fM;
+            fa.M3 = p->fNZ;
+            fa.P1 = fa.P2 = fP;
+            fa.P3 = p->fNZ;
+            fa.Q3lo = 0;
+            fa.a3first = 0;
+            fa.L3count = p->fNZ;
+            fa.nyq = 0;
+            fa.nyqgrid = nullptr;
+            fa.zlinear = 1;
+            fa.work = fwork;
+            fa.grid = p->fargrid;
+            e = gf_launch_far_grid(fa, p->precision, k, a1, a2, p->fz0, p->fhz, st);
+            gf_dev_free(fwork, st);
+            if (e != cudaSuccess) {
+                st_err = fail(GF_ERR_CUDA, "gf_plan: far-region grid launch: %s", cudaGetErrorString(e));
+                break;
+            }
+        }
         if (p->timing) cudaEventRecord(p->ev[1], st);
         // far-series tables: index box covering |alpha_n|^2 <= k^2 + (T/c)^2
         if (dim == 3) {
@@ -657,6 +712,16 @@ gf_status gf_plan_eval_args(gf_plan_t p, const double *dev_xyz, int64_t n, int w
     a.exptab_j0 = p->exptab_j0;
     a.bmin = p->bmin_ev;
     a.nyqgrid = p->nyqgrid;
+    a.fargrid = p->fargrid;
+    if (p->fargrid) {
+        a.fM1 = a.fM2 = p->fM;
+        a.fP1 = a.fP2 = p->fM + 3;
+        a.fNZ = p->fNZ;
+        a.fz0 = p->fz0;
+        a.fhz = p->fhz;
+        a.fzmax = p->fzmax;
+        a.fh1 = a.fh2 = 2.0 * GF_PI / p->fM;
+    }
     *a_out = a;
     return GF_OK;
 }
@@ -748,6 +813,10 @@ gf_status gf_plan_get_info(gf_plan_t p, gf_plan_info_t *info)
     info->series_n2_lo = p->n2lo;
     info->series_n2_hi = p->n2hi;
     info->grid_device_bytes = p->grid_bytes;
+    info->far_grid_M = p->fM;
+    info->far_grid_nz = p->fNZ ? p->fNZ - 3 : 0;
+    info->far_grid_zmax = p->fzmax;
+    info->far_grid_device_bytes = p->far_bytes;
     return GF_OK;
 }
 
@@ -763,7 +832,7 @@ gf_status gf_destroy(gf_plan_t p)
     // the plan may have been used on any stream: wait for the device, then hand
     // the buffers back to the pool
     cudaDeviceSynchronize();
-    void *bufs[] = {p->grid, p->nyqgrid, p->tables, p->btab, p->prop, p->exptab};
+    void *bufs[] = {p->grid, p->nyqgrid, p->fargrid, p->tables, p->btab, p->prop, p->exptab};
     for (void *b : bufs) gf_dev_free(b, 0);
     for (int i = 0; i < 6; ++i)
         if (p->ev[i]) cudaEventDestroy(p->ev[i]);

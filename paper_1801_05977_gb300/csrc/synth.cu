@@ -492,7 +492,12 @@ __device__ void synth_x1_body(const SynthArgs &a, int blk, unsigned char *smem)
         }
         int n3 = 1;
         p3[0] = 0;
-        if (a.dim == 3) n3 = pad_dests(a3, a.M3, p3);
+        if (a.dim == 3) {
+            if (a.zlinear)
+                p3[0] = a3;  // far-region planes: node = plane, no halo
+            else
+                n3 = pad_dests(a3, a.M3, p3);
+        }
         for (int d3 = 0; d3 < n3; ++d3) {
             // only the stored planes Q3lo .. Q3lo + P3 - 1
             const int q3 = p3[d3] - a.Q3lo;
@@ -801,6 +806,85 @@ __global__ void e_table_kernel(const double *tt, int Q, int Mlast, double qs, do
         E[i] = make_double2(cv, sv);
         if (Ef) Ef[i] = make_float2((float)cv, (float)sv);
     }
+}
+
+namespace {
+// Far-region grid coefficients (the far branch's series (he) on planes): for
+// in-plane index n (FFT order b) and plane m at z = z0 + m hz,
+//   a_n(z) = (i/8pi^2) e^{i beta_n z}/beta_n
+// = e^{-b z}/(8pi^2 b) for evanescent beta_n = i b, and (-sin + i cos)(beta z)/(8pi^2 beta)
+// for propagating ones; Maxwell fields (delta_pq - c^p c^q/k^2) a_n with
+// c = (alpha_n, beta_n), then a_n.  Work layout [f][m][b2][b1], working precision.
+template <typename R>
+__global__ void __launch_bounds__(256) fargrid_coef(SynthArgs a, double k, double a1, double a2, double z0, double hz)
+{
+    typedef typename cplx_t<R>::T C;
+    C *W = reinterpret_cast<C *>(a.work);
+    const size_t plane = (size_t)a.M1 * a.M2, per = plane * a.L3count;
+    const double k2 = k * k, ik2 = 1.0 / k2, s8 = 1.0 / (8.0 * GF_PI * GF_PI);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < per; i += (size_t)gridDim.x * blockDim.x) {
+        const int b1 = (int)(i % a.M1), b2 = (int)((i / a.M1) % a.M2), m = (int)(i / plane);
+        const double c1 = a1 + freq_of(b1, a.M1), c2 = a2 + freq_of(b2, a.M2);
+        const double A2 = c1 * c1 + c2 * c2;
+        const double2 beta = beta_of(k, A2);
+        const double z = z0 + m * hz;
+        double2 an;
+        if (beta.y > 0.0) {
+            if (sizeof(R) == 4) {
+                const float bf = (float)beta.y;
+                an = make_double2((double)(exp2f(-bf * (float)z * 1.44269504f) / (bf * (float)(8.0 * GF_PI * GF_PI))), 0.0);
+            } else {
+                an = make_double2(exp(-beta.y * z) * s8 / beta.y, 0.0);
+            }
+        } else {
+            double sz, cz;
+            sincos(beta.x * z, &sz, &cz);
+            an = make_double2(-sz * s8 / beta.x, cz * s8 / beta.x);
+        }
+        if (a.nf == 1) {
+            W[i] = cmk((R)an.x, (R)an.y);
+        } else {
+            // c = (c1, c2, beta); products with beta complex for evanescent n
+            const double2 cv[3] = {make_double2(c1, 0.0), make_double2(c2, 0.0), beta};
+            const int P[6] = {0, 1, 2, 0, 0, 1}, Q[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+            for (int e = 0; e < 6; ++e) {
+                const double2 cc = cmul(cv[P[e]], cv[Q[e]]);
+                const double2 f = make_double2((P[e] == Q[e] ? 1.0 : 0.0) - cc.x * ik2, -cc.y * ik2);
+                const double2 v = cmul(f, an);
+                W[(size_t)e * per + i] = cmk((R)v.x, (R)v.y);
+            }
+            W[(size_t)6 * per + i] = cmk((R)an.x, (R)an.y);
+        }
+    }
+}
+
+template <typename R>
+cudaError_t launch_far_grid_t(const SynthArgs &a0, double k, double a1, double a2, double z0, double hz, cudaStream_t s)
+{
+    SynthArgs a = a0;
+    size_t sm[3];
+    synth_config_t<R>(a, 8, sm);
+    const size_t per = (size_t)a.M1 * a.M2 * a.L3count;
+    int blocks = (int)((per + 255) / 256);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    fargrid_coef<R><<<blocks, 256, 0, s>>>(a, k, a1, a2, z0, hz);
+    cudaError_t e = cudaFuncSetAttribute(synth_x2_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[1]);
+    if (e != cudaSuccess) return e;
+    synth_x2_pass<R><<<dim3(a.M1 / a.TJ2, a.L3count, a.nf), 256, sm[1], s>>>(a);
+    e = cudaFuncSetAttribute(synth_x1_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[2]);
+    if (e != cudaSuccess) return e;
+    synth_x1_pass<R><<<a.L3count * a.M2 / a.RB1, 256, sm[2], s>>>(a);
+    gf_count_launch(3);
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t gf_launch_far_grid(const SynthArgs &a, int precision, double k, double a1, double a2, double z0,
+                               double hz, cudaStream_t s)
+{
+    return precision == GF_FP64 ? launch_far_grid_t<double>(a, k, a1, a2, z0, hz, s)
+                                : launch_far_grid_t<float>(a, k, a1, a2, z0, hz, s);
 }
 
 cudaError_t gf_launch_e_table(const double *tt, int Q, int Mlast, double qs, double2 *E, float2 *Ef, cudaStream_t s)

@@ -30,7 +30,8 @@ class GfError(RuntimeError):
 class Trunc(ctypes.Structure):
     _fields_ = [("c", ctypes.c_double), ("c_tilde", ctypes.c_double), ("eps", ctypes.c_double),
                 ("series_tol", ctypes.c_double), ("quad_nodes", ctypes.c_int), ("precision", ctypes.c_int),
-                ("kind", ctypes.c_int), ("resonance_policy", ctypes.c_int)]
+                ("kind", ctypes.c_int), ("resonance_policy", ctypes.c_int), ("far_grid_M", ctypes.c_int),
+                ("far_grid_nz", ctypes.c_int), ("far_grid_zmax", ctypes.c_double)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -39,7 +40,9 @@ class PlanInfo(ctypes.Structure):
                 ("alpha", ctypes.c_double * 2), ("c", ctypes.c_double), ("c_tilde", ctypes.c_double),
                 ("eps", ctypes.c_double), ("series_tol", ctypes.c_double), ("quad_nodes", ctypes.c_int),
                 ("series_n1_lo", ctypes.c_int), ("series_n1_hi", ctypes.c_int), ("series_n2_lo", ctypes.c_int),
-                ("series_n2_hi", ctypes.c_int), ("grid_device_bytes", ctypes.c_size_t)]
+                ("series_n2_hi", ctypes.c_int), ("grid_device_bytes", ctypes.c_size_t),
+                ("far_grid_M", ctypes.c_int), ("far_grid_nz", ctypes.c_int), ("far_grid_zmax", ctypes.c_double),
+                ("far_grid_device_bytes", ctypes.c_size_t)]
 
 
 EXPORTS = ["gf_trunc_default", "gf_plan", "gf_eval_grid", "gf_grid_bytes", "gf_eval_points",
