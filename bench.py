@@ -59,6 +59,8 @@ FAR_FF_GAP = 8.0
 FAR_TRAFFIC_BYTES = 9.978112e6 * 5
 # unit-count peaks, reported beside the measured ones (152 SMs, 2.07 GHz):
 # FP64 2 FMA/clk/SM, FP32 128 FMA/clk/SM
+# in-plane points of the far-region grid of the split leg that uses it
+FAR_GRID_M = 512
 FP64_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
@@ -339,10 +341,10 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def run_path(precision: int, steps: int, warmup: int, tol: float):
+    def run_path(precision: int, steps: int, warmup: int, tol: float, **extra):
         cdt = torch.complex128 if precision == gf.GF_FP64 else torch.complex64
         out = torch.empty((n_targets, 1), dtype=cdt, device=dev)
-        kw = dict(precision=precision, series_tol=tol)
+        kw = dict(precision=precision, series_tol=tol, **extra)
         for _ in range(warmup):
             p = gf.Plan(3, K_WAVE, ALPHA, GRID, **kw)
             p.eval_points_into(x, out, gf.GF_OUT_GD)
@@ -375,8 +377,10 @@ def run_gpu(args):
         clk.__exit__()
         return 0
     out32, t32, ph32, _ = run_path(gf.GF_FP32_SPLIT, args.steps, args.warmup, 1e-8)
+    # split precision with the far-region grid (512 x 512 planes over c < |x3| <= c~)
+    outfg, tfg, phfg, _ = run_path(gf.GF_FP32_SPLIT, args.steps, args.warmup, 1e-8, far_grid_M=FAR_GRID_M)
 
-    ms64, ms32 = max_over_ranks([np.mean(t64), np.mean(t32)], dev)
+    ms64, ms32, msfg = max_over_ranks([np.mean(t64), np.mean(t32), np.mean(tfg)], dev)
     value = whole_job_rate(n_targets, world, ms64 * 1e-3)
 
     # e2e through the host-buffer entry point (pinned buffers, copies inside the timed region)
@@ -419,6 +423,10 @@ def run_gpu(args):
     # split-precision error vs the double-precision path on this workload
     d = (out32.to(torch.complex128) - out64).abs()
     split_err = float(d.max() / out64.abs().max())
+    far_mask = x[:, 2].abs() > 0.6
+    dfg = (outfg.to(torch.complex128) - out64).abs()
+    fg_err, fg_err_far = float(dfg.max() / out64.abs().max()), float(dfg[far_mask].max() / out64.abs().max())
+    del dfg, d
     g64, g32 = out64.cpu().numpy(), out32.to(torch.complex128).cpu().numpy()
 
     batched = None if args.no_batch else run_batched(args, dev, flush)
@@ -459,6 +467,13 @@ def run_gpu(args):
                   "phases_ms": {"synthesis": float(np.mean([p[0] for p in ph32])),
                                 "near": float(np.mean([p[2] for p in ph32])),
                                 "far": float(np.mean([p[3] for p in ph32]))}},
+        "split_far_grid": {"value": whole_job_rate(n_targets, world, msfg * 1e-3), "ms_per_step": msfg,
+                           "dtype": "f32/f64 split", "far_grid": f"{FAR_GRID_M}x{FAR_GRID_M} in-plane x 16 "
+                                                                 f"intervals over 0.6 < |x3| <= 1",
+                           "max_err_vs_fp64_normwise": fg_err, "far_targets_err_vs_fp64_normwise": fg_err_far,
+                           "phases_ms": {"synthesis": float(np.mean([p[0] for p in phfg])),
+                                         "near_and_far_grid": float(np.mean([p[2] for p in phfg])),
+                                         "far_series": float(np.mean([p[3] for p in phfg]))}},
         "roofline": {"bound": "alu", "kernel": "far3d_f64 + far3d_tail (concurrent)", "achieved": achieved,
                      "peak": peaks["fp64"], "unit": "TFLOP/s (FP64-equivalent)", "frac": achieved / peaks["fp64"],
                      "traffic": FAR_TRAFFIC_BYTES if n_targets == 1_000_000 and FAR_TRAFFIC_BYTES else None,

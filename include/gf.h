@@ -118,7 +118,7 @@ gf_status gf_trunc_default(gf_trunc_t *t);
  *   k          wave number, > 0
  *   alpha      dim-1 doubles (host memory)
  *   M          dim ints (host memory): grid points per axis (x1, x2[, x3]) = the
- *              paper's 2N; each a power of two in [8, 1024]
+ *              paper's 2N; each a power of two in [8, 1024] (3D) or [8, 2048] (2D)
  *   trunc      parameters, NULL for the defaults
  *   cuda_stream  stream on which the synthesis kernels run
  *   out        receives the plan handle; the plan owns its device memory
@@ -127,7 +127,9 @@ gf_status gf_trunc_default(gf_trunc_t *t);
  * plan is usable by later work on that stream, and by work on other streams
  * once they are ordered after it).  The plan is immutable afterwards.
  * Errors: GF_ERR_ARG (bad sizes/parameters), GF_ERR_WOOD, GF_ERR_RESONANCE,
- * GF_ERR_NOMEM, GF_ERR_CUDA.  On error *out is set to NULL. */
+ * GF_ERR_NOMEM, GF_ERR_CUDA, GF_ERR_UNSUPPORTED (a synthesis pass would need
+ * more shared memory than one CTA has: double-precision Maxwell plans with
+ * 1024 points on an axis).  On error *out is set to NULL. */
 gf_status gf_plan(int dim, double k, const double *alpha, const int *M,
                   const gf_trunc_t *trunc, void *cuda_stream, gf_plan_t *out);
 

@@ -225,6 +225,7 @@ struct EvalBatch {
 cudaError_t gf_launch_synth(const SynthArgs &a, int precision, cudaStream_t s);
 cudaError_t gf_launch_extract(const SynthArgs &a, int precision, void *dev_out, cudaStream_t s);
 void gf_synth_config(SynthArgs &a, int precision, int tj_max, size_t smem[3]);
+size_t gf_synth_smem_need(const SynthArgs &a, int precision);
 cudaError_t gf_launch_cheb_table(int dim, const double *rr, const double2 *B, const double *P0, const double *P1, int Q,
                                  int npan, int deg, double w, double2 *out, float2 *outf, cudaStream_t s);
 cudaError_t gf_launch_synth_batch(const SynthBatch &b, int precision, cudaStream_t s);

@@ -195,8 +195,12 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
     if (!(k > 0.0) || !isfinite(k)) return fail(GF_ERR_ARG, "gf_plan: k must be finite and > 0");
     for (int i = 0; i < dim - 1; ++i)
         if (!isfinite(alpha[i])) return fail(GF_ERR_ARG, "gf_plan: alpha must be finite");
+    // 3D grids up to 1024 points per axis, 2D up to 2048 (the paper's 2D examples
+    // reach N = 1024, i.e. 2048 points per axis, Sec. 5.1)
+    const int Mmax = dim == 2 ? 2048 : 1024;
     for (int i = 0; i < dim; ++i)
-        if (!pow2_in(M[i], 8, 1024)) return fail(GF_ERR_ARG, "gf_plan: M[%d] = %d is not a power of two in [8, 1024]", i, M[i]);
+        if (!pow2_in(M[i], 8, Mmax))
+            return fail(GF_ERR_ARG, "gf_plan: M[%d] = %d is not a power of two in [8, %d]", i, M[i], Mmax);
     gf_trunc_t tr;
     gf_trunc_default(&tr);
     if (trunc) tr = *trunc;
@@ -471,6 +475,23 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
         sa.L3count = p->L3count;
         sa.nyq = p->nyq;
         sa.nyqgrid = p->nyqgrid;
+        {
+            // one CTA holds whole lines of every stored field in shared memory
+            int dev = 0, optin = 232448;
+            if (cudaGetDevice(&dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+                cudaGetLastError();
+                optin = 232448;
+            }
+            const size_t need = gf_synth_smem_need(sa, p->precision);
+            if (need > (size_t)optin) {
+                st_err = fail(GF_ERR_UNSUPPORTED,
+                              "gf_plan: the synthesis of this grid needs %zu bytes of shared memory per CTA (limit %d): "
+                              "fewer points per axis, fewer fields or the split precision",
+                              need, optin);
+                break;
+            }
+        }
         if (p->timing) cudaEventRecord(p->ev[0], st);
         if ((e = gf_launch_synth(sa, p->precision, st)) != cudaSuccess) {
             st_err = fail(GF_ERR_CUDA, "gf_plan: synthesis launch: %s", cudaGetErrorString(e));

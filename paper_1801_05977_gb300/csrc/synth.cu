@@ -908,6 +908,20 @@ cudaError_t gf_launch_cheb_table(int dim, const double *rr, const double2 *B, co
     return cudaGetLastError();
 }
 
+// Largest dynamic shared memory the plan's own synthesis launches ask for.
+size_t gf_synth_smem_need(const SynthArgs &a0, int precision)
+{
+    SynthArgs a = a0;
+    size_t sm[3];
+    if (precision == GF_FP64)
+        synth_config_t<double>(a, 8, sm);
+    else
+        synth_config_t<float>(a, 16, sm);
+    size_t m = sm[0];
+    if (a.dim == 3 && sm[1] > m) m = sm[1];
+    return sm[2] > m ? sm[2] : m;
+}
+
 void gf_synth_config(SynthArgs &a, int precision, int tj_max, size_t smem[3])
 {
     if (precision == GF_FP64)

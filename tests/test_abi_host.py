@@ -50,7 +50,8 @@ def _plan_status(dim, k, alpha, M, **kw):
     ((3, float("nan"), (0.1, 0.2), (16, 16, 16)), {}),
     ((3, 1.0, (0.1, float("inf")), (16, 16, 16)), {}),
     ((3, 1.0, (0.1, 0.2), (12, 16, 16)), {}),          # not a power of two
-    ((3, 1.0, (0.1, 0.2), (16, 16, 2048)), {}),        # too large
+    ((3, 1.0, (0.1, 0.2), (16, 16, 2048)), {}),        # too large (3D)
+    ((2, 1.0, (0.1,), (16, 4096)), {}),                # too large (2D)
     ((3, 1.0, (0.1, 0.2), (4, 16, 16)), {}),           # too small
     ((3, 1.0, (0.1, 0.2), (16, 16, 16)), {"c": 1.2}),  # c >= c~
     ((3, 1.0, (0.1, 0.2), (16, 16, 16)), {"eps": 0.6}),  # 2 eps >= c~
