@@ -56,6 +56,23 @@ __device__ C *stockham_inverse(C *x, C *y, int n, int lg, int nlines, const C *t
     return x;
 }
 
+// The same transform of nlines lines held in x, `group` lines at a time, with a
+// scratch y of only `group` lines; the result is left in x.  Lets a pass hold
+// every field of its lines plus one field's worth of scratch instead of two full
+// copies.  All threads of the CTA must call it.
+template <typename C>
+__device__ void stockham_inverse_grouped(C *x, C *y, int n, int lg, int nlines, int group, const C *tw)
+{
+    for (int g0 = 0; g0 < nlines; g0 += group) {
+        C *xg = x + (size_t)g0 * n;
+        const C *res = stockham_inverse(xg, y, n, lg, group, tw);
+        if (res != xg) {
+            for (int i = threadIdx.x; i < group * n; i += blockDim.x) xg[i] = res[i];
+            __syncthreads();
+        }
+    }
+}
+
 template <typename R>
 __device__ void load_twiddles(typename cplx_t<R>::T *tw, int n)
 {
@@ -75,8 +92,8 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
     double2 *betas = Av + TJ * Q;                        // [TJ]
     C *tw = reinterpret_cast<C *>(betas + TJ);           // [n/2]
     C *buf0 = tw + (n >> 1);                             // [nf][TJ][n]
-    C *buf1 = buf0 + nf * TJ * n;
-    double *A2s = reinterpret_cast<double *>(buf1 + nf * TJ * n); // [TJ]
+    C *buf1 = buf0 + nf * TJ * n;                      // [TJ][n] scratch of the transforms
+    double *A2s = reinterpret_cast<double *>(buf1 + TJ * n); // [TJ]
     // split plans, float coefficients: A_m [TJ][Q], |alpha_j|^2 - k^2 and its float [TJ], q_b^2 [n]
     // (16-byte aligned so that the X'-integral loop reads it four nodes at a time)
     float *Avf = reinterpret_cast<float *>(reinterpret_cast<uintptr_t>(A2s + TJ + 1) & ~(uintptr_t)15);
@@ -375,7 +392,8 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
         }
     }
     __syncthreads();
-    C *res = stockham_inverse(buf0, buf1, n, lg, nf * TJ, tw);
+    stockham_inverse_grouped(buf0, buf1, n, lg, nf * TJ, TJ, tw);
+    const C *res = buf0;
     if (a.dim == 3) {
         // only the x3 nodes the last two passes transform (a3first .. a3first +
         // L3count - 1), compact: work plane y holds node a3first + y, whose output
@@ -449,7 +467,7 @@ __device__ void synth_x1_body(const SynthArgs &a, int blk, unsigned char *smem)
     const int n = a.M1, nf = a.nf, lg1 = a.lg1, RB = a.RB1;
     C *tw = reinterpret_cast<C *>(smem);
     C *buf0 = tw + (n >> 1);
-    C *buf1 = buf0 + RB * nf * n;
+    C *buf1 = buf0 + RB * nf * n;  // [RB][n] scratch of the transforms
     // row = y * M2 + l2 (3D: x3 node a3first + y at compact work plane y); 2D: l2
     const size_t fstride = (size_t)(a.dim == 3 ? (a.L3count + a.nyq) * a.M2 : a.Mlast) * a.M1;
     const C *W = reinterpret_cast<const C *>(a.work);
@@ -461,7 +479,8 @@ __device__ void synth_x1_body(const SynthArgs &a, int blk, unsigned char *smem)
         buf0[i] = W[f * fstride + (size_t)(row0 + r) * n + b1];
     }
     __syncthreads();
-    C *res = stockham_inverse(buf0, buf1, n, lg1, RB * nf, tw);
+    stockham_inverse_grouped(buf0, buf1, n, lg1, RB * nf, RB, tw);
+    const C *res = buf0;
     C *G = reinterpret_cast<C *>(a.grid);
     const int rowlen = a.P1 * nf;
     for (int r = 0; r < RB; ++r) {
@@ -648,7 +667,7 @@ void synth_config_t(SynthArgs &a, int tj_max, size_t sm[3])
         return sizeof(C) * (a.Mlast / 2) + sizeof(double) * a.Mlast + sizeof(float2) * a.Mlast +
                TJ * (sizeof(double2) * a.Q + sizeof(double2) + 2 * sizeof(double) + sizeof(float)) +
                TJ * (sizeof(float2) + sizeof(float) + sizeof(int)) +
-               sizeof(float) * ((TJ * a.Q + 3) & ~3) + 2 * sizeof(C) * a.nf * TJ * a.Mlast + 64;
+               sizeof(float) * ((TJ * a.Q + 3) & ~3) + sizeof(C) * (a.nf + 1) * TJ * a.Mlast + 64;
     };
     int TJ = tj_max;
     while (TJ > 1 && (TJ > ncols || bytes(TJ) > 160 * 1024)) TJ >>= 1;
@@ -664,10 +683,10 @@ void synth_config_t(SynthArgs &a, int tj_max, size_t sm[3])
     const int nrows = a.dim == 3 ? (a.L3count + a.nyq) * a.M2 : a.M2;
     int RB1 = 8;
     while (RB1 > 1 && (RB1 > nrows || RB1 * a.nf * a.M1 > 2048 ||
-                       sizeof(C) * (a.M1 / 2 + 2 * a.nf * RB1 * a.M1) > 160 * 1024))
+                       sizeof(C) * (a.M1 / 2 + (a.nf + 1) * RB1 * a.M1) > 160 * 1024))
         RB1 >>= 1;
     a.RB1 = RB1;
-    sm[2] = sizeof(C) * (a.M1 / 2 + 2 * a.nf * RB1 * a.M1);
+    sm[2] = sizeof(C) * (a.M1 / 2 + (a.nf + 1) * RB1 * a.M1);
 }
 
 template <typename R>
@@ -815,46 +834,62 @@ namespace {
 // = e^{-b z}/(8pi^2 b) for evanescent beta_n = i b, and (-sin + i cos)(beta z)/(8pi^2 beta)
 // for propagating ones; Maxwell fields (delta_pq - c^p c^q/k^2) a_n with
 // c = (alpha_n, beta_n), then a_n.  Work layout [f][m][b2][b1], working precision.
+// One thread per in-plane index walks the planes: |alpha_n|^2 - k^2 is formed once
+// in double; split plans take b and the exponentials in float (a relative error
+// of about 1e-7 per coefficient) except within 0.05 k of a Wood anomaly, where b
+// comes from the double difference as in the near grid's coefficients.
 template <typename R>
 __global__ void __launch_bounds__(256) fargrid_coef(SynthArgs a, double k, double a1, double a2, double z0, double hz)
 {
     typedef typename cplx_t<R>::T C;
     C *W = reinterpret_cast<C *>(a.work);
-    const size_t plane = (size_t)a.M1 * a.M2, per = plane * a.L3count;
+    const int plane = a.M1 * a.M2;
+    const size_t per = (size_t)plane * a.L3count;
     const double k2 = k * k, ik2 = 1.0 / k2, s8 = 1.0 / (8.0 * GF_PI * GF_PI);
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < per; i += (size_t)gridDim.x * blockDim.x) {
-        const int b1 = (int)(i % a.M1), b2 = (int)((i / a.M1) % a.M2), m = (int)(i / plane);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < plane; i += gridDim.x * blockDim.x) {
+        const int b1 = i % a.M1, b2 = i / a.M1;
         const double c1 = a1 + freq_of(b1, a.M1), c2 = a2 + freq_of(b2, a.M2);
-        const double A2 = c1 * c1 + c2 * c2;
-        const double2 beta = beta_of(k, A2);
-        const double z = z0 + m * hz;
-        double2 an;
-        if (beta.y > 0.0) {
-            if (sizeof(R) == 4) {
-                const float bf = (float)beta.y;
-                an = make_double2((double)(exp2f(-bf * (float)z * 1.44269504f) / (bf * (float)(8.0 * GF_PI * GF_PI))), 0.0);
+        const double d = fma(c1, c1, fma(c2, c2, -k2));  // |alpha_n|^2 - k^2
+        const bool ev = d > 0.0;
+        // b = |beta_n|: float where it is not small against k (split plans)
+        const bool fast = sizeof(R) == 4 && d > 0.0025 * k2;
+        double bd = 0.0;
+        float bf = 0.f;
+        if (fast)
+            bf = sqrtf((float)d);
+        else
+            bd = sqrt(fabs(d));
+        const double bb = fast ? (double)bf : bd;
+        for (int m = 0; m < a.L3count; ++m) {
+            const double z = z0 + m * hz;
+            double2 an;
+            if (ev) {
+                if (fast)
+                    an = make_double2((double)(exp2f(-bf * (float)z * 1.44269504f) * ((float)s8 / bf)), 0.0);
+                else
+                    an = make_double2(exp(-bd * z) * s8 / bd, 0.0);
             } else {
-                an = make_double2(exp(-beta.y * z) * s8 / beta.y, 0.0);
+                double sz, cz;
+                sincos(bd * z, &sz, &cz);
+                an = make_double2(-sz * s8 / bd, cz * s8 / bd);
             }
-        } else {
-            double sz, cz;
-            sincos(beta.x * z, &sz, &cz);
-            an = make_double2(-sz * s8 / beta.x, cz * s8 / beta.x);
-        }
-        if (a.nf == 1) {
-            W[i] = cmk((R)an.x, (R)an.y);
-        } else {
-            // c = (c1, c2, beta); products with beta complex for evanescent n
-            const double2 cv[3] = {make_double2(c1, 0.0), make_double2(c2, 0.0), beta};
-            const int P[6] = {0, 1, 2, 0, 0, 1}, Q[6] = {0, 1, 2, 1, 2, 2};
+            const size_t o = (size_t)m * plane + i;
+            if (a.nf == 1) {
+                W[o] = cmk((R)an.x, (R)an.y);
+            } else {
+                // c = (c1, c2, beta): beta = i b (evanescent) or b (propagating)
+                const double2 beta = ev ? make_double2(0.0, bb) : make_double2(bb, 0.0);
+                const double2 cv[3] = {make_double2(c1, 0.0), make_double2(c2, 0.0), beta};
+                const int P[6] = {0, 1, 2, 0, 0, 1}, Q[6] = {0, 1, 2, 1, 2, 2};
 #pragma unroll
-            for (int e = 0; e < 6; ++e) {
-                const double2 cc = cmul(cv[P[e]], cv[Q[e]]);
-                const double2 f = make_double2((P[e] == Q[e] ? 1.0 : 0.0) - cc.x * ik2, -cc.y * ik2);
-                const double2 v = cmul(f, an);
-                W[(size_t)e * per + i] = cmk((R)v.x, (R)v.y);
+                for (int e = 0; e < 6; ++e) {
+                    const double2 cc = cmul(cv[P[e]], cv[Q[e]]);
+                    const double2 f = make_double2((P[e] == Q[e] ? 1.0 : 0.0) - cc.x * ik2, -cc.y * ik2);
+                    const double2 v = cmul(f, an);
+                    W[(size_t)e * per + o] = cmk((R)v.x, (R)v.y);
+                }
+                W[(size_t)6 * per + o] = cmk((R)an.x, (R)an.y);
             }
-            W[(size_t)6 * per + i] = cmk((R)an.x, (R)an.y);
         }
     }
 }
@@ -865,8 +900,8 @@ cudaError_t launch_far_grid_t(const SynthArgs &a0, double k, double a1, double a
     SynthArgs a = a0;
     size_t sm[3];
     synth_config_t<R>(a, 8, sm);
-    const size_t per = (size_t)a.M1 * a.M2 * a.L3count;
-    int blocks = (int)((per + 255) / 256);
+    const int plane = a.M1 * a.M2;
+    int blocks = (plane + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     fargrid_coef<R><<<blocks, 256, 0, s>>>(a, k, a1, a2, z0, hz);
     cudaError_t e = cudaFuncSetAttribute(synth_x2_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[1]);
