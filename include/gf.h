@@ -67,7 +67,7 @@ enum {                                            /* gf_eval_points `which` */
 };
 
 /* Method parameters.  Defaults (gf_trunc_default): c = 0.6, c~ = 1 (Sec. 5),
- * eps = 0.45, series_tol = 0 (automatic), quad_nodes = 64, GF_FP64,
+ * eps = 0.45, series_tol = 0 (automatic), quad_nodes = 0 (automatic), GF_FP64,
  * GF_HELMHOLTZ, GF_PERTURB_CTILDE, far_grid_M = 0 (far branch by the series).
  *   c          |x_last| <= c: grid + interpolation; > c: eigen-series (Alg. 1-3, step 2b)
  *   c_tilde    half period of the artificial periodisation in x_last (c < c~); the cutoff
@@ -77,7 +77,12 @@ enum {                                            /* gf_eval_points `which` */
  *   series_tol far-series truncation: terms with |alpha_n|^2 <= k^2 + (T/|x_last|)^2,
  *              T = ln(1/series_tol) + 3, are summed; <= 0 selects 1e-16 for GF_FP64
  *              and 1e-8 for GF_FP32_SPLIT
- *   quad_nodes Gauss-Legendre nodes for the 1D integrals in the coefficients
+ *   quad_nodes Gauss-Legendre nodes Q for the 1D integrals in the coefficients, in
+ *              [8, 1024]; <= 0 picks Q from the grid's highest frequencies (the
+ *              integrands oscillate like sin(s r) on [eps, 2 eps] with s up to
+ *              |xi|_max, and like e^{i(beta -+ q)t} on [c, (c + c~)/2]): Q = max(64,
+ *              max(s_max eps/2, (q_max + k)(c~ - c)/4) + 24), rounded up to a
+ *              multiple of 8 (64 for the grids of up to about 128 points per axis)
  *   precision  GF_FP64: everything in double.  GF_FP32_SPLIT: grid synthesis,
  *              interpolation and series in float; coefficients, singular part,
  *              reduction and phase in double.

@@ -174,7 +174,7 @@ gf_status gf_trunc_default(gf_trunc_t *t)
     t->c_tilde = 1.0;
     t->eps = 0.45;
     t->series_tol = 0.0;
-    t->quad_nodes = 64;
+    t->quad_nodes = 0;
     t->precision = GF_FP64;
     t->kind = GF_HELMHOLTZ;
     t->resonance_policy = GF_PERTURB_CTILDE;
@@ -208,7 +208,27 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
         return fail(GF_ERR_ARG, "gf_plan: need 0 < c < c_tilde");
     if (!(tr.eps > 0.0) || !(2.0 * tr.eps < tr.c_tilde) || !(2.0 * tr.eps < GF_PI))
         return fail(GF_ERR_ARG, "gf_plan: need 0 < 2 eps < min(c_tilde, pi)");
-    if (tr.quad_nodes < 8 || tr.quad_nodes > 512) return fail(GF_ERR_ARG, "gf_plan: quad_nodes must be in [8, 512]");
+    if (tr.quad_nodes <= 0) {
+        // Automatic: the 1D integrals of the coefficients oscillate at the grid's
+        // frequencies -- h(s) over [eps, 2 eps] at s up to |xi|_max, the X' integrals
+        // over [c, (c + c~)/2] at up to q_max + k -- and Gauss-Legendre resolves
+        // e^{i w t} on a half-width a once Q exceeds w a by a margin (24 nodes more
+        // reach rounding level).  64 nodes at least, a multiple of 8, at most 1024.
+        const double qmax = (M[dim - 1] / 2 + 1) * GF_PI / tr.c_tilde;
+        double smax;
+        if (dim == 3) {
+            const double m1 = fabs(alpha[0]) + M[0] / 2 + 1, m2 = fabs(alpha[1]) + M[1] / 2 + 1;
+            smax = sqrt(m1 * m1 + m2 * m2 + qmax * qmax);
+        } else {
+            const double m1 = M[0] / 2 + 1;
+            smax = sqrt(m1 * m1 + qmax * qmax);
+        }
+        const double need = fmax(smax * 0.5 * tr.eps, (qmax + k) * 0.25 * (tr.c_tilde - tr.c)) + 24.0;
+        int Qa = (int)ceil(need);
+        Qa = (Qa + 7) / 8 * 8;
+        tr.quad_nodes = Qa < 64 ? 64 : Qa > 1024 ? 1024 : Qa;
+    }
+    if (tr.quad_nodes < 8 || tr.quad_nodes > 1024) return fail(GF_ERR_ARG, "gf_plan: quad_nodes must be in [8, 1024]");
     if (tr.precision != GF_FP64 && tr.precision != GF_FP32_SPLIT) return fail(GF_ERR_ARG, "gf_plan: bad precision");
     if (tr.kind != GF_HELMHOLTZ && tr.kind != GF_MAXWELL) return fail(GF_ERR_ARG, "gf_plan: bad kind");
     if (tr.kind == GF_MAXWELL && dim != 3) return fail(GF_ERR_ARG, "gf_plan: the Maxwell tensor needs dim = 3");

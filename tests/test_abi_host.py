@@ -29,7 +29,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_trunc_defaults():
     t = gf.trunc_default()
-    assert (t.c, t.c_tilde, t.eps, t.quad_nodes) == (0.6, 1.0, 0.45, 64)
+    assert (t.c, t.c_tilde, t.eps, t.quad_nodes) == (0.6, 1.0, 0.45, 0)
     assert (t.far_grid_M, t.far_grid_nz, t.far_grid_zmax) == (0, 0, 0.0)
     assert t.precision == gf.GF_FP64 and t.kind == gf.GF_HELMHOLTZ
 
@@ -56,6 +56,7 @@ def _plan_status(dim, k, alpha, M, **kw):
     ((3, 1.0, (0.1, 0.2), (16, 16, 16)), {"c": 1.2}),  # c >= c~
     ((3, 1.0, (0.1, 0.2), (16, 16, 16)), {"eps": 0.6}),  # 2 eps >= c~
     ((3, 1.0, (0.1, 0.2), (16, 16, 16)), {"quad_nodes": 4}),
+    ((3, 1.0, (0.1, 0.2), (16, 16, 16)), {"quad_nodes": 2000}),
     ((3, 1.0, (0.1, 0.2), (16, 16, 16)), {"precision": 7}),
     ((2, 1.0, (0.1,), (16, 16)), {"kind": gf.GF_MAXWELL}),  # Maxwell is 3D only
     ((3, 1.0, (0.1, 0.2), (16, 16, 16)), {"far_grid_M": 100}),  # far grid: not a power of two

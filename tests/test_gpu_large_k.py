@@ -97,7 +97,7 @@ def test_large_k_matches_oracle(kind):
         pb = O.Problem(dim=3, k=k, alpha=(3 ** 0.5, 0.5), M=(64, 64, 32), maxwell=(kind == "maxwell"))
         x = np.concatenate([W.targets_3d(1500, seed=82), W.targets_3d_clustered(300, seed=83, frac=1.0)])
         which, owhich = (gf.GF_OUT_MAXWELL7, O.OUT_MAXWELL7) if pb.maxwell else (gf.GF_OUT_GD, O.OUT_GD)
-    plan = gf.Plan(pb.dim, k, pb.alpha, pb.M, series_tol=pb.tau,
+    plan = gf.Plan(pb.dim, k, pb.alpha, pb.M, series_tol=pb.tau, quad_nodes=pb.Q,
                    kind=gf.GF_MAXWELL if pb.maxwell else gf.GF_HELMHOLTZ)
     pb.ct = plan.info.c_tilde  # (a resonance perturbation would show here)
     ref = O.evaluate(pb, O.grid(pb), x, owhich)
