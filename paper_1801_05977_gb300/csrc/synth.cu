@@ -73,13 +73,21 @@ __device__ void stockham_inverse_grouped(C *x, C *y, int n, int lg, int nlines, 
     }
 }
 
+// tw[i] = e^{2 pi i i/n}, i < n/2, in the pass's precision (float passes take
+// the float sincospi: within an ulp, and no double arithmetic in a float pass)
 template <typename R>
 __device__ void load_twiddles(typename cplx_t<R>::T *tw, int n)
 {
     for (int i = threadIdx.x; i < (n >> 1); i += blockDim.x) {
-        double s, c;
-        sincospi(2.0 * (double)i / (double)n, &s, &c);
-        tw[i] = cmk((R)c, (R)s);
+        if (sizeof(R) == 4) {
+            float s, c;
+            sincospif(2.0f * (float)i / (float)n, &s, &c);
+            tw[i] = cmk((R)c, (R)s);
+        } else {
+            double s, c;
+            sincospi(2.0 * (double)i / (double)n, &s, &c);
+            tw[i] = cmk((R)c, (R)s);
+        }
     }
 }
 
