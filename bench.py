@@ -368,13 +368,27 @@ def run_gpu(args):
         return out, times, phases, launches
 
     tol64 = 1e-16
+
+    def path_line(name, t, ph):
+        # profiling modes: one line with the device time per step and its phases
+        print(json.dumps({"path": name, "targets": n_targets, "ms_per_step": float(np.mean(t)),
+                          "phases_ms": {"synthesis": float(np.mean([p[0] for p in ph])),
+                                        "near": float(np.mean([p[2] for p in ph])),
+                                        "far": float(np.mean([p[3] for p in ph]))}}))
+
     if args.paths == "split":
-        run_path(gf.GF_FP32_SPLIT, args.steps, args.warmup, 1e-8)
+        _, t, ph, _ = run_path(gf.GF_FP32_SPLIT, args.steps, args.warmup, 1e-8)
+        path_line("split", t, ph)
+        return 0
+    if args.paths == "split_far_grid":
+        _, t, ph, _ = run_path(gf.GF_FP32_SPLIT, args.steps, args.warmup, 1e-8, far_grid_M=FAR_GRID_M)
+        path_line("split_far_grid", t, ph)
         return 0
     clk = ClockSampler(local).__enter__()
     out64, t64, ph64, launches = run_path(gf.GF_FP64, args.steps, args.warmup, tol64)
     if args.paths == "fp64":
         clk.__exit__()
+        path_line("fp64", t64, ph64)
         return 0
     out32, t32, ph32, _ = run_path(gf.GF_FP32_SPLIT, args.steps, args.warmup, 1e-8)
     # split precision with the far-region grid (512 x 512 planes over c < |x3| <= c~)
@@ -626,10 +640,76 @@ def run_surrogate(args, dev):
                 ft.append(time.perf_counter() - t0)
     t_fft = float(np.mean(ft))
     g, r = G.cpu().numpy(), ref[:, 0].cpu().numpy()
-    errs = np.array([np.abs(g[off[i]:off[i + 1]] - r[off[i]:off[i + 1]]).max() / np.abs(r[off[i]:off[i + 1]]).max()
-                     for i in range(npairs)])
+
+    def pair_errs(vals):
+        return np.array([np.abs(vals[off[i]:off[i + 1]] - r[off[i]:off[i + 1]]).max() /
+                         np.abs(r[off[i]:off[i + 1]]).max() for i in range(npairs)])
+
+    errs = pair_errs(g)
     batch.close()
     mlp.close()
+    del G
+
+    # residual form: the network learns L_d minus a coarse plan's L_d (surrogate.COARSE
+    # points per axis); at inference a coarse batched sweep of the same pairs supplies
+    # that value (its plans built once: the preparation) and gf_surrogate_eval_residual
+    # adds it back
+    t0 = time.perf_counter()
+    inp_r, L_r, _ = S.make_dataset(args.sur_train_pairs, args.sur_train_per_pair, seed=0, residual=True)
+    t_data_r = time.perf_counter() - t0
+    mlp_r = gf.MLP(seed=0)
+    t0 = time.perf_counter()
+    hist_r = S.train(mlp_r, inp_r, L_r, epochs=args.sur_epochs, batch=8192, lr=2e-3, min_steps=args.sur_min_steps)
+    torch.cuda.synchronize()
+    t_train_r = time.perf_counter() - t0
+    del inp_r, L_r
+    Mc = np.tile(np.array(S.COARSE, dtype=np.int32), (npairs, 1))
+    t0 = time.perf_counter()
+    cbatch = gf.Batch(k, al, Mc, precision=gf.GF_FP32_SPLIT)
+    torch.cuda.synchronize()
+    t_cprep = time.perf_counter() - t0
+    cbase = torch.empty((x.shape[0], 1), dtype=torch.complex64, device=dev)
+    rt = []
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cbatch.eval_points_into(x, off, cbase, gf.GF_OUT_LD)
+        Gr, _ = mlp_r.surrogate_eval(k, al, off, x, wood_delta=1e-2, base=cbase[:, 0].to(torch.complex128))
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            rt.append(time.perf_counter() - t0)
+    t_res = float(np.mean(rt))
+    errs_r = pair_errs(Gr.cpu().numpy())
+    cbatch.close()
+    mlp_r.close()
+    del Gr, cbase
+    # the split-precision batched FFT path (each pair's full grid) on the same targets
+    sbatch = gf.Batch(k, al, M, precision=gf.GF_FP32_SPLIT)
+    sref = torch.empty((x.shape[0], 1), dtype=torch.complex64, device=dev)
+    st_ = []
+    with torch.cuda.stream(s):
+        for i in range(args.warmup + args.steps):
+            s.synchronize()
+            t0 = time.perf_counter()
+            sbatch.run_graph(x, off, sref, gf.GF_OUT_GD, stream=s)
+            s.synchronize()
+            if i >= args.warmup:
+                st_.append(time.perf_counter() - t0)
+    t_split = float(np.mean(st_))
+    errs_s = pair_errs(sref[:, 0].to(torch.complex128).cpu().numpy())
+    sbatch.close()
+    del sref
+    residual = {"value": npairs * per / t_res, "unit": "evals/s", "s_per_call": t_res,
+                "coarse_grid": "x".join(map(str, S.COARSE)), "coarse_plans_setup_s": t_cprep,
+                "value_with_setup": npairs * per / (t_res + t_cprep),
+                "err_vs_fft_path_normwise": {"median": float(np.median(errs_r)),
+                                             "p90": float(np.percentile(errs_r, 90)), "max": float(errs_r.max())},
+                "training": {"samples": args.sur_train_pairs * args.sur_train_per_pair, "epochs": len(hist_r),
+                             "final_loss": hist_r[-1], "train_s": t_train_r, "data_s": t_data_r},
+                "how": "per call: coarse batched sweep (split) GF_OUT_LD at the targets + gf_surrogate_eval_residual"}
+    split_path = {"value": npairs * per / t_split, "unit": "evals/s", "s_per_call": t_split,
+                  "err_vs_fft_path_normwise": {"median": float(np.median(errs_s)), "max": float(errs_s.max())},
+                  "how": "split-precision batched sweep (graph: synthesis + evaluation) of each pair's full grid"}
     # tensor-core GEMM of one hidden layer at inference size: (2^20 x 256) . (256 x 256)^T
     A = torch.randn((1 << 20, 256), device=dev).to(torch.bfloat16)
     Bm = torch.randn((256, 256), device=dev).to(torch.bfloat16)
@@ -675,7 +755,8 @@ def run_surrogate(args, dev):
             "err_vs_fft_path_normwise": {"median": float(np.median(errs)), "p90": float(np.percentile(errs, 90)),
                                          "max": float(errs.max())},
             "training": {"samples": args.sur_train_pairs * args.sur_train_per_pair, "epochs": len(hist),
-                         "batch": 8192, "final_loss": hist[-1], "train_s": t_train, "data_s": t_data}}
+                         "batch": 8192, "final_loss": hist[-1], "train_s": t_train, "data_s": t_data},
+            "residual": residual, "split_fft_path": split_path}
 
 
 def run_configs(args, dev, flush):
@@ -772,7 +853,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--targets", type=int, default=N_TARGETS,
                     help="targets per step (the benchmark workload is 1e6; smaller only for profiling captures)")
-    ap.add_argument("--paths", default="both", choices=["both", "fp64", "split"],
+    ap.add_argument("--paths", default="both", choices=["both", "fp64", "split", "split_far_grid"],
                     help="which precision paths to run (profiling captures run one)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling captures)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-sweep leg")

@@ -321,6 +321,20 @@ gf_status gf_mlp_error_word(gf_mlp_t mlp, int *out);
 gf_status gf_surrogate_eval(gf_mlp_t mlp, int npairs, const double *k, const double *alpha, const int64_t *offsets,
                             const double *dev_xyz, void *dev_out, double wood_delta, const gf_trunc_t *trunc,
                             int *n_fallback_pairs, void *cuda_stream);
+/* Residual form of gf_surrogate_eval (the surrogate's fallback design when the
+ * network alone cannot reach the FFT path's accuracy; the paper has no learned
+ * part): the network was trained on L_d minus a coarse FFT-path value of it, and
+ * the caller passes that coarse value at every target,
+ *   dev_base  complex128 [offsets[npairs]] device memory: the remainder L_d of a
+ *             coarse plan per pair at the same targets (for example gf_plan_batch
+ *             with 32^3 points and gf_batch_eval_points(..., GF_OUT_LD, ...)),
+ * so that G = e^{i2pi<alpha.m>}(e^{i alpha.t}(L_base + scale*MLP) + e^{ikr} Y_eps/(4 pi r)).
+ * Everything else as gf_surrogate_eval.  Errors: as gf_surrogate_eval;
+ * GF_ERR_ARG for a NULL dev_base with targets. */
+gf_status gf_surrogate_eval_residual(gf_mlp_t mlp, int npairs, const double *k, const double *alpha,
+                                     const int64_t *offsets, const double *dev_xyz, const void *dev_base,
+                                     void *dev_out, double wood_delta, const gf_trunc_t *trunc,
+                                     int *n_fallback_pairs, void *cuda_stream);
 gf_status gf_mlp_destroy(gf_mlp_t mlp);
 
 /* Plan facts (host memory).  Returns GF_ERR_ARG on NULL arguments. */

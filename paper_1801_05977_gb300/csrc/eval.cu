@@ -1405,10 +1405,25 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, i
 #pragma unroll
         for (int e = 0; e < NS; ++e) S[e][0] = S[e][1] = 0.0, Sf[e][0] = Sf[e][1] = 0.f;
         // propagating terms, in the anchor frame: e^{i(c1 t1 + (c2 - alpha_2 - N0) t2)};
-        // the list is in row-major order, so within a row the phase steps by e^{i t2}
+        // the list is in row-major order, so within a row the phase steps by e^{i t2}.
+        // e^{i beta z} = e^{i beta z_w} e^{i beta (z - z_w)}, z_w the warp's smallest
+        // |x3|: the lanes share a narrow |x3| bucket, so the first factor is one sincos
+        // per entry per warp (lane q mod 32 forms it, shuffles hand it out) and the
+        // second a Taylor polynomial while |beta (z - z_w)| <= 0.02 (cos to theta^6,
+        // sin to theta^7: truncation below 1e-17); a warp whose spread is wider takes
+        // a sincos per lane.
         double2 ph = make_double2(1.0, 0.0);
         double pc1 = 0.0, pc2 = 0.0;
-        for (int q = 0, nq = slab == 0 ? *a.nprop : 0; q < nq; ++q) {
+        const int nq = slab == 0 ? *a.nprop : 0;
+        double zw = L.valid ? L.z : 1e300;
+        for (int o = 16; o > 0; o >>= 1) zw = fmin(zw, __shfl_xor_sync(0xffffffffu, zw, o));
+        const double dz = L.z - zw;
+        const bool taylor = nq > 0 && warp_max(L.valid ? dz : 0.0) * a.k <= 0.02;
+        double ewx = 1.0, ewy = 0.0;  // e^{i beta_{q0 + lane} z_w}
+        for (int q = 0; q < nq; ++q) {
+            if (taylor && (q & 31) == 0) {
+                if (q + lane < nq) sincos(a.prop[q + lane].br * zw, &ewy, &ewx);
+            }
             const PropEntry pe = a.prop[q];
             if (q > 0 && pe.c1 == pc1 && fabs(pe.c2 - pc2 - 1.0) < 0.5) {
                 ph = cmul(ph, make_double2(cv, sv));
@@ -1420,7 +1435,16 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, i
             pc1 = pe.c1;
             pc2 = pe.c2;
             double sz, cz;
-            sincos(pe.br * L.z, &sz, &cz);
+            if (taylor) {
+                const double Ex = __shfl_sync(0xffffffffu, ewx, q & 31), Ey = __shfl_sync(0xffffffffu, ewy, q & 31);
+                const double th = pe.br * dz, th2 = th * th;
+                const double ct = fma(fma(fma(th2, -1.0 / 720.0, 1.0 / 24.0), th2, -0.5), th2, 1.0);
+                const double st = th * fma(fma(fma(th2, -1.0 / 5040.0, 1.0 / 120.0), th2, -1.0 / 6.0), th2, 1.0);
+                cz = Ex * ct - Ey * st;
+                sz = Ex * st + Ey * ct;
+            } else {
+                sincos(pe.br * L.z, &sz, &cz);
+            }
             const double cp = ph.x, sp = ph.y;
             double tx = pe.ibr * (cz * cp - sz * sp), ty = pe.ibr * (cz * sp + sz * cp);
             P[0][0] += tx;

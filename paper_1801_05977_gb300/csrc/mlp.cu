@@ -252,11 +252,12 @@ __global__ void surrogate_inputs_kernel(const double *x, int n, int64_t base, co
 }
 
 // G = e^{i2pi<alpha.m>} (e^{i alpha.t} L + e^{ikr} Y_eps(r)/(4 pi r)) for near targets
-// (L = scale * network output); far targets (|x3| > c) are outside the
-// surrogate's domain and get NaN.
+// (L = scale * network output, plus the caller's base value of the remainder
+// when Lb is not null: the residual form); far targets (|x3| > c) are outside
+// the surrogate's domain and get NaN.
 __global__ void surrogate_assemble_kernel(const double *x, int n, int64_t base, const int64_t *off, int np,
                                           const double *pk, const float *Y, double scale, double c, double eps,
-                                          double2 *out)
+                                          const double2 *Lb, double2 *out)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int p = pair_of_target(off, np, base + i);
@@ -279,7 +280,13 @@ __global__ void surrogate_assemble_kernel(const double *x, int n, int64_t base, 
         const float t1f = (float)t1, t2f = (float)t2, x3f = (float)x3;
         sincosf((float)a1 * t1f + (float)a2 * t2f, &sa, &ca);
         const float lx = ca * cl - sa * sl, ly = ca * sl + sa * cl;  // lift
-        const float sc = (float)scale, Lx = sc * Y[2 * (size_t)i], Ly = sc * Y[2 * (size_t)i + 1];
+        const float sc = (float)scale;
+        float Lx = sc * Y[2 * (size_t)i], Ly = sc * Y[2 * (size_t)i + 1];
+        if (Lb) {
+            const double2 b = Lb[i];
+            Lx += (float)b.x;
+            Ly += (float)b.y;
+        }
         double2 v = make_double2((double)(lx * Lx - ly * Ly), (double)(lx * Ly + ly * Lx));
         const float rf = sqrtf(t1f * t1f + t2f * t2f + x3f * x3f);
         if (rf < (float)(2.0 * eps)) {
@@ -1007,9 +1014,13 @@ gf_status gf_mlp_error_word(gf_mlp_t m, int *out)
     return *out ? GF_ERR_TIMEOUT : GF_OK;
 }
 
-gf_status gf_surrogate_eval(gf_mlp_t m, int npairs, const double *k, const double *alpha, const int64_t *offsets,
-                            const double *dev_xyz, void *dev_out, double wood_delta, const gf_trunc_t *trunc,
-                            int *n_fallback_pairs, void *cuda_stream)
+}  // extern "C"
+
+// Shared body of gf_surrogate_eval (dev_base null) and gf_surrogate_eval_residual.
+static gf_status surrogate_eval_impl(gf_mlp_t m, int npairs, const double *k, const double *alpha,
+                                     const int64_t *offsets, const double *dev_xyz, const double2 *dev_base,
+                                     void *dev_out, double wood_delta, const gf_trunc_t *trunc, int *n_fallback_pairs,
+                                     void *cuda_stream)
 {
     if (!m || npairs <= 0 || !k || !alpha || !offsets || (offsets[npairs] > 0 && (!dev_xyz || !dev_out)))
         return err(GF_ERR_ARG, "gf_surrogate_eval: bad argument");
@@ -1069,7 +1080,8 @@ gf_status gf_surrogate_eval(gf_mlp_t m, int npairs, const double *k, const doubl
             gf_count_launch(1);
             if ((s = infer(m, n, m->Y, st)) != GF_OK) return s;
             surrogate_assemble_kernel<<<blocks, 256, 0, st>>>(dev_xyz + 3 * base, n, base, d_off, npairs, d_pk, m->Y,
-                                                              m->scale, tr.c, tr.eps, (double2 *)dev_out + base);
+                                                              m->scale, tr.c, tr.eps, dev_base ? dev_base + base : nullptr,
+                                                              (double2 *)dev_out + base);
             gf_count_launch(1);
         }
         gf_dev_free(d_off, st);
@@ -1089,6 +1101,27 @@ gf_status gf_surrogate_eval(gf_mlp_t m, int npairs, const double *k, const doubl
         if (s != GF_OK) return s;
     }
     return GF_OK;
+}
+
+extern "C" {
+
+gf_status gf_surrogate_eval(gf_mlp_t m, int npairs, const double *k, const double *alpha, const int64_t *offsets,
+                            const double *dev_xyz, void *dev_out, double wood_delta, const gf_trunc_t *trunc,
+                            int *n_fallback_pairs, void *cuda_stream)
+{
+    return surrogate_eval_impl(m, npairs, k, alpha, offsets, dev_xyz, nullptr, dev_out, wood_delta, trunc,
+                               n_fallback_pairs, cuda_stream);
+}
+
+gf_status gf_surrogate_eval_residual(gf_mlp_t m, int npairs, const double *k, const double *alpha,
+                                     const int64_t *offsets, const double *dev_xyz, const void *dev_base,
+                                     void *dev_out, double wood_delta, const gf_trunc_t *trunc,
+                                     int *n_fallback_pairs, void *cuda_stream)
+{
+    if (!dev_base && offsets && npairs > 0 && offsets[npairs] > 0)
+        return err(GF_ERR_ARG, "gf_surrogate_eval_residual: dev_base is NULL");
+    return surrogate_eval_impl(m, npairs, k, alpha, offsets, dev_xyz, (const double2 *)dev_base, dev_out, wood_delta,
+                               trunc, n_fallback_pairs, cuda_stream);
 }
 
 gf_status gf_mlp_destroy(gf_mlp_t m)

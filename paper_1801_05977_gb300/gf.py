@@ -52,7 +52,7 @@ EXPORTS = ["gf_trunc_default", "gf_plan", "gf_eval_grid", "gf_grid_bytes", "gf_e
            "gf_batch_get_tuning", "gf_batch_run_graph", "gf_batch_get_plan", "gf_batch_destroy",
            "gf_gemm_bf16", "gf_mlp_create", "gf_mlp_param_count", "gf_mlp_params", "gf_mlp_set_scale",
            "gf_mlp_forward", "gf_mlp_train_step", "gf_mlp_gradients", "gf_mlp_error_word", "gf_surrogate_eval",
-           "gf_mlp_destroy", "gf_release_memory", "gf_peak_probe"]
+           "gf_mlp_destroy", "gf_release_memory", "gf_peak_probe", "gf_surrogate_eval_residual"]
 
 NOALLOC_MAX_TARGETS = 1 << 18
 
@@ -101,6 +101,8 @@ def lib(build_if_missing: bool = True):
     L.gf_mlp_gradients.argtypes = [vp, vp, vp, i32, vp, vp, vp]
     L.gf_mlp_error_word.argtypes = [vp, P(ctypes.c_int)]
     L.gf_surrogate_eval.argtypes = [vp, i32, P(d), P(d), P(ctypes.c_int64), vp, vp, d, P(Trunc), P(ctypes.c_int), vp]
+    L.gf_surrogate_eval_residual.argtypes = [vp, i32, P(d), P(d), P(ctypes.c_int64), vp, vp, vp, d, P(Trunc),
+                                             P(ctypes.c_int), vp]
     L.gf_mlp_destroy.argtypes = [vp]
     L.gf_plan_get_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
     L.gf_destroy.argtypes = [vp]
@@ -119,7 +121,7 @@ def lib(build_if_missing: bool = True):
                  "gf_mlp_forward", "gf_mlp_train_step", "gf_mlp_gradients", "gf_mlp_error_word",
                  "gf_surrogate_eval", "gf_mlp_destroy",
                  "gf_plan_get_info", "gf_destroy", "gf_set_phase_timing", "gf_plan_phase_ms", "gf_release_memory",
-                 "gf_peak_probe"):
+                 "gf_peak_probe", "gf_surrogate_eval_residual"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -421,20 +423,31 @@ class MLP:
         lib().gf_mlp_error_word(self._h, ctypes.byref(v))
         return v.value
 
-    def surrogate_eval(self, k, alpha, offsets, x, wood_delta=1e-2, trunc=None, stream=None):
+    def surrogate_eval(self, k, alpha, offsets, x, wood_delta=1e-2, trunc=None, stream=None, base=None):
+        """gf_surrogate_eval, or gf_surrogate_eval_residual when `base` (complex128 CUDA
+        tensor of the coarse remainder at the targets) is given."""
         import torch
         k = np.ascontiguousarray(k, dtype=np.float64)
         alpha = np.ascontiguousarray(alpha, dtype=np.float64).reshape(-1, 2)
         off = np.ascontiguousarray(offsets, dtype=np.int64)
+        if off.shape[0] != k.shape[0] + 1 or alpha.shape[0] != k.shape[0] or off[-1] != x.shape[0]:
+            raise GfError(GF_ERR_ARG, "k, alpha and offsets must describe the rows of x")
         out = torch.empty((x.shape[0],), dtype=torch.complex128, device=x.device)
         nfb = ctypes.c_int()
         if trunc is None:
             trunc = trunc_default()
-        _check(lib().gf_surrogate_eval(self._h, k.shape[0], k.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                                       alpha.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                                       off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
-                                       ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
-                                       float(wood_delta), ctypes.byref(trunc), ctypes.byref(nfb), _stream_ptr(stream)))
+        args = (self._h, k.shape[0], k.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                alpha.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), ctypes.c_void_p(x.data_ptr()))
+        tail = (ctypes.c_void_p(out.data_ptr()), float(wood_delta), ctypes.byref(trunc), ctypes.byref(nfb),
+                _stream_ptr(stream))
+        if base is None:
+            _check(lib().gf_surrogate_eval(*args, *tail))
+        else:
+            if not (base.is_cuda and base.dtype == torch.complex128 and base.is_contiguous()
+                    and base.numel() == x.shape[0]):
+                raise GfError(GF_ERR_ARG, "base must be a contiguous complex128 CUDA tensor with one value per target")
+            _check(lib().gf_surrogate_eval_residual(*args, ctypes.c_void_p(base.data_ptr()), *tail))
         return out, nfb.value
 
     def close(self):

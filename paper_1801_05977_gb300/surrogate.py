@@ -7,6 +7,11 @@ L_dN (GF_OUT_LD) at `per_pair` near-region points (x1, x2 ~ U[-pi, pi),
 x3 ~ U[-c, c]).  Samples are (t1, t2, x3, alpha1, alpha2, k) -> L_d / scale,
 shuffled once on the host.  Training runs the library's own tensor-core
 forward/backward kernels and Adam (gf_mlp_train_step) over mini-batches.
+
+Residual form: the network learns L_d minus the remainder of a coarse plan
+(COARSE points per axis), which a coarse batched sweep supplies again at
+inference (gf_surrogate_eval_residual adds it back); the network then only
+has to carry the difference between the two grids.
 """
 from __future__ import annotations
 
@@ -16,6 +21,10 @@ import numpy as np
 
 from . import gf
 from . import workloads as W
+
+
+# grid of the coarse plans of the residual form (points per axis)
+COARSE = (32, 32, 32)
 
 
 def grid_for(k: float) -> tuple:
@@ -32,24 +41,39 @@ def near_points(n: int, seed: int, c: float = 0.6) -> np.ndarray:
     return x
 
 
-def make_dataset(n_pairs: int, per_pair: int, seed: int = 0, wood_gap: float = 1e-2, kmin=1.0, kmax=4.0):
-    """Returns (inputs float32 [N][6], targets complex64 [N], pairs [P][3] (a1, a2, k))."""
+def remainder_values(pairs, xd, off, M=None, precision=gf.GF_FP32_SPLIT):
+    """L_d of one plan per pair (grid grid_for(k), or M for every pair) at the
+    rows of xd (pair p owns rows off[p] .. off[p+1]-1): complex CUDA tensor [N]."""
+    import torch
+
+    k = np.ascontiguousarray(pairs[:, 2])
+    al = np.ascontiguousarray(pairs[:, :2])
+    Mm = np.array([M if M is not None else grid_for(v) for v in k], dtype=np.int32)
+    batch = gf.Batch(k, al, Mm, precision=precision)
+    out = torch.empty((xd.shape[0], 1), dtype=batch.complex_dtype, device=xd.device)
+    batch.eval_points_into(xd, off, out, gf.GF_OUT_LD)
+    torch.cuda.synchronize()
+    batch.close()
+    return out[:, 0]
+
+
+def make_dataset(n_pairs: int, per_pair: int, seed: int = 0, wood_gap: float = 1e-2, kmin=1.0, kmax=4.0,
+                 residual: bool = False):
+    """Returns (inputs float32 [N][6], targets complex64 [N], pairs [P][3] (a1, a2, k)).
+    residual: the targets are L_d minus the coarse plans' L_d (COARSE points per axis)."""
     import torch
 
     pairs = W.sweep_pairs(n_pairs, seed=seed, kmin=kmin, kmax=kmax, wood_gap=wood_gap)
     k = pairs[:, 2].copy()
     al = pairs[:, :2].copy()
-    M = np.array([grid_for(v) for v in k], dtype=np.int32)
     xs = [near_points(per_pair, seed=10_000 * (seed + 1) + i) for i in range(n_pairs)]
     x = np.concatenate(xs)
     off = np.arange(n_pairs + 1, dtype=np.int64) * per_pair
-    batch = gf.Batch(k, al, M, precision=gf.GF_FP32_SPLIT)
     xd = torch.from_numpy(x).cuda()
-    out = torch.empty((x.shape[0], 1), dtype=torch.complex64, device="cuda")
-    batch.eval_points_into(xd, off, out, gf.GF_OUT_LD)
-    torch.cuda.synchronize()
-    L = out.cpu().numpy()[:, 0]
-    batch.close()
+    Lt = remainder_values(pairs, xd, off)
+    if residual:
+        Lt = Lt - remainder_values(pairs, xd, off, M=COARSE)
+    L = Lt.cpu().numpy()
     inp = np.empty((x.shape[0], 6), dtype=np.float32)
     inp[:, :3] = x
     rep = np.repeat(np.arange(n_pairs), per_pair)
