@@ -375,6 +375,16 @@ gf_status gf_release_memory(void);
 enum { GF_PROBE_FP64 = 0, GF_PROBE_FP32 = 1 };
 gf_status gf_peak_probe(int pipe, int64_t iters, void *dev_sink, int64_t *flops, void *cuda_stream);
 
+/* Self-test of the bounded device waits (diagnostic; the paper has no
+ * counterpart).  The tensor-core kernels wait on mbarriers with a poll limit and
+ * report GF_ERR_TIMEOUT instead of hanging; this launches one warp that waits
+ * the same way on a barrier that only it could arrive on, with `polls` polls,
+ * arriving first when `arrive` is non-zero.  Synchronises cuda_stream.
+ * Returns GF_ERR_TIMEOUT when the wait ran out (arrive = 0), GF_OK when it
+ * completed (arrive != 0); the context stays usable either way.
+ * Errors: GF_ERR_ARG (polls outside [1, 2^40]), GF_ERR_NOMEM, GF_ERR_CUDA. */
+gf_status gf_wait_selftest(int64_t polls, int arrive, void *cuda_stream);
+
 /* Static description of a status code. */
 const char *gf_status_string(gf_status s);
 

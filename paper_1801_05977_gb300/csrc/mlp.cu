@@ -333,7 +333,7 @@ constexpr int ROWS = 128, NT = 2;
 constexpr int ACT_BYTES = ROWS * HID * 2;                // 64 KiB per tile
 constexpr int WST_BYTES = HID * umma::KC * 2;           // 32 KiB per weight stage
 constexpr int PAR_FLOATS = 4 * HID + 2 * HID;  // biases of layers 1-4, then the head weights
-constexpr int NCW = 2 * NT * 2;                 // consumer warps (4 per tile)
+constexpr int NCW = 8 * NT;                     // consumer warps (8 per tile: 4 row quarters x 2 column halves)
 constexpr int THREADS = (NCW + 1) * 32;         // plus one producer warp
 constexpr int SMEM = NT * ACT_BYTES + 2 * WST_BYTES + 128 + PAR_FLOATS * 4;
 constexpr int TMEM_COLS = 512;
@@ -360,11 +360,14 @@ struct Args {
 };
 }  // namespace fused
 
-// Producer warp (warp 8, one lane): weight-stage bulk copies and MMA issue, tile
-// after tile.  Consumer warps 0-3 own tile 0, 4-7 own tile 1 (warp w reads TMEM
-// lanes 32 (w % 4) .. +31, i.e. its 32 rows, all 256 columns).  While the
-// consumers of one tile run its epilogue (bias, SiLU, bf16 activations back into
-// shared memory) the tensor cores work on the other tile.
+// Producer warp (warp 16, one lane): weight-stage bulk copies and MMA issue, tile
+// after tile.  Consumer warps 0-7 own tile 0, 8-15 own tile 1; warp w reads TMEM
+// lanes 32 (w % 4) .. +31, i.e. its 32 rows, and the column half (w / 4) % 2 of
+// the 256 columns, so two warps share each row's epilogue (and features).  While
+// the consumers of one tile run its epilogue (bias, SiLU, bf16 activations back
+// into shared memory) the tensor cores work on the other tile.  The 256 -> 2
+// head's two column halves are added into the output, which is zeroed before the
+// launch (two float terms added to zero: the same result in either order).
 //   lbar[b]  stage copy landed in buffer b    mbar[b]  MMAs of that stage done
 //   accf[t]  tile t's layer MMAs done         actr[t]  tile t's activations written
 //                                                      and its accumulator read (128 arrivals)
@@ -397,7 +400,7 @@ __global__ void __launch_bounds__(fused::THREADS, 1) mlp_infer_fused(fused::Args
     if (threadIdx.x == 0) {
         for (int q = 0; q < 6; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(umma::smem_u32(&bars[q])));
         for (int q = 6; q < 8; ++q)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(umma::smem_u32(&bars[q])), "r"(ROWS));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(umma::smem_u32(&bars[q])), "r"(2 * ROWS));
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
@@ -474,7 +477,7 @@ __global__ void __launch_bounds__(fused::THREADS, 1) mlp_infer_fused(fused::Args
         }
     } else {
         // ---------------------------------------------------------------- consumers
-        const int t = warp >> 2, quarter = warp & 3, r = quarter * 32 + lane;
+        const int t = warp >> 3, quarter = warp & 3, half = (warp >> 2) & 1, r = quarter * 32 + lane;
         uint8_t *at = act[t];
         const float b50 = A.b5[0], b51 = A.b5[1];
         int fa = 0;
@@ -495,8 +498,9 @@ __global__ void __launch_bounds__(fused::THREADS, 1) mlp_infer_fused(fused::Args
                     p5 = p[5];
                 }
                 const float rr = sqrtf(t1 * t1 + t2 * t2 + x3 * x3);
-                // ten blocks of 8 features: blocks 0..7 hold cos/sin of 4 frequencies each
-                for (int kb = 0; kb < K0 / 8; ++kb) {
+                // ten blocks of 8 features: blocks 0..7 hold cos/sin of 4 frequencies each;
+                // the two column halves of a row write blocks 0..4 and 5..9
+                for (int kb = half * (K0 / 16); kb < (half + 1) * (K0 / 16); ++kb) {
                     float v[8];
                     if (kb < 8) {
 #pragma unroll
@@ -542,7 +546,7 @@ __global__ void __launch_bounds__(fused::THREADS, 1) mlp_infer_fused(fused::Args
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const float *bias = par + l * HID;
                 float y0 = 0.f, y1 = 0.f;
-                for (int j = 0; j < HID; j += 32) {
+                for (int j = half * (HID / 2); j < (half + 1) * (HID / 2); j += 32) {
                     uint32_t v[32];
                     const uint32_t taddr = tmem + t * HID + ((uint32_t)(quarter * 32) << 16) + (uint32_t)j;
                     asm volatile(
@@ -588,8 +592,8 @@ __global__ void __launch_bounds__(fused::THREADS, 1) mlp_infer_fused(fused::Args
                 } else {
                     asm volatile("tcgen05.fence::before_thread_sync;");
                     if (live) {
-                        A.Y[2 * (size_t)i] = y0 + b50;
-                        A.Y[2 * (size_t)i + 1] = y1 + b51;
+                        atomicAdd(&A.Y[2 * (size_t)i], half ? y0 : y0 + b50);
+                        atomicAdd(&A.Y[2 * (size_t)i + 1], half ? y1 : y1 + b51);
                     }
                 }
             }
@@ -752,6 +756,8 @@ gf_status infer(gf_mlp_t m, int n, float *Y, cudaStream_t s)
     CUM(cudaFuncSetAttribute(mlp_infer_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, fused::SMEM));
     int tiles = (n + fused::NT * fused::ROWS - 1) / (fused::NT * fused::ROWS);
     int grid = tiles < m->nsm ? tiles : m->nsm;
+    // the head's two column halves are added into Y
+    CUM(cudaMemsetAsync(Y, 0, sizeof(float) * 2 * (size_t)n, s));
     mlp_infer_fused<<<grid, fused::THREADS, fused::SMEM, s>>>(A);
     gf_count_launch(1);
     CUM(cudaGetLastError());

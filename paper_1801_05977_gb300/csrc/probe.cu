@@ -6,6 +6,7 @@
 // thread runs ILP independent chains of fused multiply-adds, so the pipe never
 // waits on a result, and the grid fills every SM at full occupancy.
 #include "gf_internal.cuh"
+#include "umma_gemm.cuh"
 
 namespace {
 
@@ -54,5 +55,55 @@ extern "C" gf_status gf_peak_probe(int pipe, int64_t iters, void *dev_sink, int6
     if (e != cudaSuccess) return gf_set_error(GF_ERR_CUDA, "gf_peak_probe: launch failed");
     gf_count_launch(1);
     *flops = (int64_t)2 * PROBE_ILP * 8 * iters * (int64_t)per * nsm * PROBE_THREADS;
+    return GF_OK;
+}
+
+namespace {
+
+// One warp: lane 0 initialises an mbarrier expecting one arrival, arrives on it
+// only when `arrive` is set, then waits for its phase 0 with the same bounded
+// wait the tensor-core kernels use; the outcome goes to *flag (1: the wait ran
+// out).  Nothing else touches the barrier, so without the arrival the wait can
+// only end by its limit.
+__global__ void wait_selftest_kernel(long long polls, int arrive, int *flag)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(umma::smem_u32(&bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    __syncwarp();
+    if (threadIdx.x == 0) {
+        if (arrive) {
+            uint64_t state;
+            asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(umma::smem_u32(&bar)) : "memory");
+            (void)state;
+        }
+        *flag = umma::mbar_wait_n(umma::smem_u32(&bar), 0u, polls) ? 0 : 1;
+    }
+}
+
+}  // namespace
+
+extern "C" gf_status gf_wait_selftest(int64_t polls, int arrive, void *cuda_stream)
+{
+    if (polls < 1 || polls > ((int64_t)1 << 40)) return gf_set_error(GF_ERR_ARG, "gf_wait_selftest: polls out of range");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int *flag = nullptr;
+    cudaError_t e = gf_dev_alloc((void **)&flag, sizeof(int), st);
+    if (e != cudaSuccess) return gf_set_error(GF_ERR_NOMEM, "gf_wait_selftest: allocation failed");
+    int host = -1;
+    e = cudaMemsetAsync(flag, 0xff, sizeof(int), st);
+    if (e == cudaSuccess) {
+        wait_selftest_kernel<<<1, 32, 0, st>>>((long long)polls, arrive ? 1 : 0, flag);
+        gf_count_launch(1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&host, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    gf_dev_free(flag, st);
+    if (e != cudaSuccess) return gf_set_error(GF_ERR_CUDA, "gf_wait_selftest: CUDA error");
+    if (host == 1) return gf_set_error(GF_ERR_TIMEOUT, "gf_wait_selftest: the bounded wait ran out");
+    if (host != 0) return gf_set_error(GF_ERR_CUDA, "gf_wait_selftest: no result");
     return GF_OK;
 }

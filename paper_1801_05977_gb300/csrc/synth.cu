@@ -868,6 +868,14 @@ __global__ void __launch_bounds__(256) fargrid_coef(SynthArgs a, double k, doubl
         else
             bd = sqrt(fabs(d));
         const double bb = fast ? (double)bf : bd;
+        if (fast && a.nf == 1) {
+            // split plans, evanescent and clear of Wood anomalies: all in float (z to
+            // an ulp, e^{-b z} to a few ulps where it is not negligible)
+            const float zf0 = (float)z0, hzf = (float)hz, blog = -bf * 1.44269504f, w = (float)s8 / bf;
+            C *Wc = W + i;
+            for (int m = 0; m < a.L3count; ++m) Wc[(size_t)m * plane] = cmk((R)(exp2f(blog * fmaf((float)m, hzf, zf0)) * w), (R)0);
+            continue;
+        }
         for (int m = 0; m < a.L3count; ++m) {
             const double z = z0 + m * hz;
             double2 an;

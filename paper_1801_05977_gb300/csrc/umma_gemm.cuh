@@ -80,6 +80,23 @@ __device__ __forceinline__ float dsilu(float z)
     return s * (1.f + z * (1.f - s));
 }
 
+// Wait for the phase of `parity` of the mbarrier to complete, polling at most
+// `limit` times; false when the limit ran out (the caller records an error and
+// unwinds instead of hanging).
+__device__ __forceinline__ bool mbar_wait_n(uint32_t mbar, uint32_t parity, long long limit)
+{
+    for (long long it = 0; it < limit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
 {
     for (long long it = 0; it < WAIT_LIMIT; ++it) {

@@ -52,7 +52,8 @@ EXPORTS = ["gf_trunc_default", "gf_plan", "gf_eval_grid", "gf_grid_bytes", "gf_e
            "gf_batch_get_tuning", "gf_batch_run_graph", "gf_batch_get_plan", "gf_batch_destroy",
            "gf_gemm_bf16", "gf_mlp_create", "gf_mlp_param_count", "gf_mlp_params", "gf_mlp_set_scale",
            "gf_mlp_forward", "gf_mlp_train_step", "gf_mlp_gradients", "gf_mlp_error_word", "gf_surrogate_eval",
-           "gf_mlp_destroy", "gf_release_memory", "gf_peak_probe", "gf_surrogate_eval_residual"]
+           "gf_mlp_destroy", "gf_release_memory", "gf_peak_probe", "gf_surrogate_eval_residual",
+           "gf_wait_selftest"]
 
 NOALLOC_MAX_TARGETS = 1 << 18
 
@@ -114,6 +115,7 @@ def lib(build_if_missing: bool = True):
     L.gf_plan_phase_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
     L.gf_release_memory.argtypes = []
     L.gf_peak_probe.argtypes = [i32, i64, vp, P(ctypes.c_int64), vp]
+    L.gf_wait_selftest.argtypes = [i64, i32, vp]
     for name in ("gf_trunc_default", "gf_plan", "gf_eval_grid", "gf_eval_points", "gf_eval_points_host",
                  "gf_eval_points_noalloc", "gf_plan_batch", "gf_batch_synthesize", "gf_batch_eval_points",
                  "gf_batch_autotune", "gf_batch_get_tuning", "gf_batch_run_graph", "gf_batch_get_plan",
@@ -121,7 +123,7 @@ def lib(build_if_missing: bool = True):
                  "gf_mlp_forward", "gf_mlp_train_step", "gf_mlp_gradients", "gf_mlp_error_word",
                  "gf_surrogate_eval", "gf_mlp_destroy",
                  "gf_plan_get_info", "gf_destroy", "gf_set_phase_timing", "gf_plan_phase_ms", "gf_release_memory",
-                 "gf_peak_probe", "gf_surrogate_eval_residual"):
+                 "gf_peak_probe", "gf_surrogate_eval_residual", "gf_wait_selftest"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -166,6 +168,12 @@ def peak_probe(pipe: int, iters: int, sink, stream=None) -> int:
     _check(lib().gf_peak_probe(int(pipe), int(iters), ctypes.c_void_p(sink.data_ptr()), ctypes.byref(fl),
                                _stream_ptr(stream)))
     return int(fl.value)
+
+
+def wait_selftest(polls: int, arrive: bool, stream=None) -> int:
+    """gf_wait_selftest: the status of one bounded mbarrier wait (GF_ERR_TIMEOUT when
+    nothing arrives and the poll limit runs out, GF_OK when it completes)."""
+    return int(lib().gf_wait_selftest(int(polls), 1 if arrive else 0, _stream_ptr(stream)))
 
 
 def release_memory():
