@@ -277,9 +277,10 @@ gf_status gf_gemm_bf16(const void *A, int64_t lda, int a_trans, const void *B, i
  * with SiLU activations: bf16 weights and activations, fp32 accumulation on the
  * tensor cores, fp32 master weights with Adam.  Inputs per sample, float
  * [n][6]: (t1, t2, x3, alpha1, alpha2, k) with t the in-cell coordinates; the
- * features are cos/sin of n1 t1 + n2 t2 + m3 pi x3 / c~ for 32 fixed integer
- * vectors plus 2 alpha1, 2 alpha2, (k - 2.5)/1.5.  Output float [n][2]: the
- * real and imaginary parts of L_d / scale.
+ * 80 features are cos/sin of n1 t1 + n2 t2 + m3 pi x3 / c~ for 32 fixed integer
+ * vectors, then 2 alpha1, 2 alpha2, (k - 2.5)/1.5, the in-cell radius r and 12
+ * Gaussian radial bumps exp(-((r - 0.15 j)/0.15)^2 / 2), j = 0..11.  Output
+ * float [n][2]: the real and imaginary parts of L_d / scale.
  * ------------------------------------------------------------------------- */
 typedef struct gf_mlp_s *gf_mlp_t;
 

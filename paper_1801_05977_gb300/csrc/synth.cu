@@ -26,27 +26,63 @@ __device__ __forceinline__ double2 beta_of(double k, double a2)
     return make_double2(0.0, sqrt((a - k) * (a + k)));
 }
 
-// Radix-2 Stockham autosort inverse transform (+ sign, unnormalised) of
-// `nlines` contiguous lines of length n = 2^lg held in shared memory x; y is
-// scratch of the same size.  tw[m] = exp(2 pi i m / n), m < n/2.  Returns the
+// e^{2 pi i m/n} for 0 <= m < n from the table of the first half (tw[m] =
+// e^{2 pi i m/n}, m < n/2): the second half is its negative.
+template <typename C>
+__device__ __forceinline__ C twiddle(const C *tw, int m, int half)
+{
+    if (m < half) return tw[m];
+    const C v = tw[m - half];
+    return cmk(-v.x, -v.y);
+}
+
+// Stockham autosort inverse transform (+ sign, unnormalised) of `nlines`
+// contiguous lines of length n = 2^lg held in shared memory x; y is scratch of
+// the same size.  Radix-4 stages, preceded by one radix-2 stage when lg is odd:
+// a stage that combines sub-transforms of length Ns takes, for j < n/4 and
+// k = j mod Ns, v_r = x[j + r n/4] e^{2 pi i r k/(4 Ns)} and writes the 4-point
+// inverse DFT of (v_0..v_3) to y[4(j - k) + k + m Ns], m = 0..3.  Returns the
 // buffer holding the result.  All threads of the CTA must call it.
 template <typename C>
 __device__ C *stockham_inverse(C *x, C *y, int n, int lg, int nlines, const C *tw)
 {
     const int half = n >> 1;
-    const int total = nlines * half;
-    for (int Ns = 1, s = 0; Ns < n; Ns <<= 1, ++s) {
+    int Ns = 1, lns = 0;
+    if (lg & 1) {
+        // radix 2, Ns = 1: no twiddles
+        const int total = nlines * half;
         for (int it = threadIdx.x; it < total; it += blockDim.x) {
-            int L = it >> (lg - 1);
-            int j = it & (half - 1);
-            int k = j & (Ns - 1);
-            C *xl = x + L * n;
+            const int L = it >> (lg - 1), j = it & (half - 1);
+            const C *xl = x + L * n;
             C *yl = y + L * n;
-            C v0 = xl[j];
-            C v1 = cmul(xl[j + half], tw[k << (lg - 1 - s)]);
-            int d = ((j - k) << 1) + k;
-            yl[d] = cadd(v0, v1);
-            yl[d + Ns] = csub(v0, v1);
+            const C v0 = xl[j], v1 = xl[j + half];
+            yl[2 * j] = cadd(v0, v1);
+            yl[2 * j + 1] = csub(v0, v1);
+        }
+        __syncthreads();
+        C *t = x;
+        x = y;
+        y = t;
+        Ns = 2;
+        lns = 1;
+    }
+    const int q = n >> 2;
+    for (; Ns < n; Ns <<= 2, lns += 2) {
+        const int total = nlines * q, sh = lg - 2 - lns;  // e^{2 pi i r k/(4 Ns)} = tw[(r k) << sh]
+        for (int it = threadIdx.x; it < total; it += blockDim.x) {
+            const int L = it >> (lg - 2), j = it & (q - 1), k = j & (Ns - 1);
+            const C *xl = x + L * n;
+            C *yl = y + L * n;
+            const C a = xl[j];
+            const C b = cmul(xl[j + q], twiddle(tw, k << sh, half));
+            const C c = cmul(xl[j + 2 * q], twiddle(tw, (2 * k) << sh, half));
+            const C d = cmul(xl[j + 3 * q], twiddle(tw, (3 * k) << sh, half));
+            const C apc = cadd(a, c), amc = csub(a, c), bpd = cadd(b, d), bmd = csub(b, d);
+            const int o = ((j - k) << 2) + k;
+            yl[o] = cadd(apc, bpd);
+            yl[o + Ns] = cmk(amc.x - bmd.y, amc.y + bmd.x);       // amc + i bmd
+            yl[o + 2 * Ns] = csub(apc, bpd);
+            yl[o + 3 * Ns] = cmk(amc.x + bmd.y, amc.y - bmd.x);   // amc - i bmd
         }
         __syncthreads();
         C *t = x;
