@@ -338,6 +338,13 @@ gf_status gf_surrogate_eval_residual(gf_mlp_t mlp, int npairs, const double *k, 
                                      int *n_fallback_pairs, void *cuda_stream);
 gf_status gf_mlp_destroy(gf_mlp_t mlp);
 
+/* Device status of a plan's synthesis: the inverse-FFT passes stage their tiles
+ * with TMA copies completed on mbarriers, and every such wait has a poll limit;
+ * a wait that ran out sets the plan's device error word instead of hanging.
+ * Synchronises cuda_stream, then returns GF_ERR_TIMEOUT if the word is set,
+ * GF_OK otherwise.  Errors: GF_ERR_ARG, GF_ERR_CUDA. */
+gf_status gf_plan_status(gf_plan_t plan, void *cuda_stream);
+
 /* Plan facts (host memory).  Returns GF_ERR_ARG on NULL arguments. */
 typedef struct {
     int dim, M[3], nfields, precision, kind;

@@ -127,6 +127,9 @@ struct SynthArgs {
     // far-region grid: the x3 axis is a run of L3count planes, not periodic; the
     // last pass writes work plane y to grid plane y (no halo, no wrap)
     int zlinear;
+    // device error word of the plan: set to 1 when a bounded wait for staged
+    // copies ran out (gf_plan_status reports it)
+    int *err;
 };
 
 // Far-series table entry for one in-plane index n: b = |beta_n|, ln b and 1/b

@@ -116,6 +116,7 @@ struct gf_plan_s {
     // far-region grid (far_grid_M > 0): [fNZ][fM + 3][fM + 3][nf], plane m at z = fz0 + m fhz
     void *fargrid = nullptr;
     size_t far_bytes = 0;
+    int *errw = nullptr;              // device error word of the synthesis (bounded waits)
     int fM = 0, fNZ = 0;
     double fz0 = 0, fhz = 0, fzmax = 0;
     size_t elem = 16;                 // bytes per complex value
@@ -417,7 +418,9 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
     p->stream = st;
     do {
         cudaError_t e;
-        if ((p->nyq && (e = gf_dev_alloc(&p->nyqgrid, (size_t)p->P1 * p->P2 * 2 * p->elem, st)) != cudaSuccess) ||
+        if ((e = gf_dev_alloc((void **)&p->errw, sizeof(int), st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(p->errw, 0, sizeof(int), st)) != cudaSuccess ||
+            (p->nyq && (e = gf_dev_alloc(&p->nyqgrid, (size_t)p->P1 * p->P2 * 2 * p->elem, st)) != cudaSuccess) ||
             (e = gf_dev_alloc(&p->grid, p->grid_bytes, st)) != cudaSuccess ||
             (e = gf_dev_alloc(&p->tables, tab_bytes, st)) != cudaSuccess ||
             (e = gf_dev_alloc(&work, work_bytes, st)) != cudaSuccess) {
@@ -495,6 +498,7 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
         sa.L3count = p->L3count;
         sa.nyq = p->nyq;
         sa.nyqgrid = p->nyqgrid;
+        sa.err = p->errw;
         {
             // one CTA holds whole lines of every stored field in shared memory
             int dev = 0, optin = 232448;
@@ -861,6 +865,18 @@ gf_status gf_plan_get_info(gf_plan_t p, gf_plan_info_t *info)
     return GF_OK;
 }
 
+gf_status gf_plan_status(gf_plan_t p, void *cuda_stream)
+{
+    if (!p) return fail(GF_ERR_ARG, "gf_plan_status: NULL plan");
+    if (!p->errw) return GF_OK;
+    int host = 0;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    CU(cudaMemcpyAsync(&host, p->errw, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (host) return fail(GF_ERR_TIMEOUT, "gf_plan_status: a bounded wait for staged copies ran out in the synthesis");
+    return GF_OK;
+}
+
 gf_status gf_release_memory(void)
 {
     CU(gf_trim_pool());
@@ -873,7 +889,7 @@ gf_status gf_destroy(gf_plan_t p)
     // the plan may have been used on any stream: wait for the device, then hand
     // the buffers back to the pool
     cudaDeviceSynchronize();
-    void *bufs[] = {p->grid, p->nyqgrid, p->fargrid, p->tables, p->btab, p->prop, p->exptab};
+    void *bufs[] = {p->grid, p->nyqgrid, p->fargrid, p->tables, p->btab, p->prop, p->exptab, p->errw};
     for (void *b : bufs) gf_dev_free(b, 0);
     for (int i = 0; i < 6; ++i)
         if (p->ev[i]) cudaEventDestroy(p->ev[i]);

@@ -9,9 +9,14 @@
 // node index l standing for x = l h (mod period).  Each pass is a radix-2
 // Stockham autosort transform held in shared memory (one CTA owns a batch of
 // whole lines, so every pass reads and writes global memory exactly once).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "gf_internal.cuh"
+#include "umma_gemm.cuh"
 
 namespace {
 
@@ -111,6 +116,54 @@ __device__ void stockham_inverse_grouped(C *x, C *y, int n, int lg, int nlines, 
 
 // tw[i] = e^{2 pi i i/n}, i < n/2, in the pass's precision (float passes take
 // the float sincospi: within an ulp, and no double arithmetic in a float pass)
+// The same transform on an interleaved tile: element j of line L at x[j NL + L]
+// (NL = 2^lgNL lines), the layout a 2D tensor copy of NL adjacent columns gives.
+// Consecutive threads take consecutive lines, so shared-memory accesses stay
+// contiguous.  Returns the buffer holding the result.
+template <typename C>
+__device__ C *stockham_inverse_il(C *x, C *y, int n, int lg, int lgNL, const C *tw)
+{
+    const int half = n >> 1, NL = 1 << lgNL;
+    int Ns = 1, lns = 0;
+    if (lg & 1) {
+        const int total = NL * half;
+        for (int it = threadIdx.x; it < total; it += blockDim.x) {
+            const int L = it & (NL - 1), j = it >> lgNL;
+            const C v0 = x[j * NL + L], v1 = x[(j + half) * NL + L];
+            y[(2 * j) * NL + L] = cadd(v0, v1);
+            y[(2 * j + 1) * NL + L] = csub(v0, v1);
+        }
+        __syncthreads();
+        C *t = x;
+        x = y;
+        y = t;
+        Ns = 2;
+        lns = 1;
+    }
+    const int q = n >> 2;
+    for (; Ns < n; Ns <<= 2, lns += 2) {
+        const int total = NL * q, sh = lg - 2 - lns;
+        for (int it = threadIdx.x; it < total; it += blockDim.x) {
+            const int L = it & (NL - 1), j = it >> lgNL, k = j & (Ns - 1);
+            const C a = x[j * NL + L];
+            const C b = cmul(x[(j + q) * NL + L], twiddle(tw, k << sh, half));
+            const C c = cmul(x[(j + 2 * q) * NL + L], twiddle(tw, (2 * k) << sh, half));
+            const C d = cmul(x[(j + 3 * q) * NL + L], twiddle(tw, (3 * k) << sh, half));
+            const C apc = cadd(a, c), amc = csub(a, c), bpd = cadd(b, d), bmd = csub(b, d);
+            const int o = ((j - k) << 2) + k;
+            y[o * NL + L] = cadd(apc, bpd);
+            y[(o + Ns) * NL + L] = cmk(amc.x - bmd.y, amc.y + bmd.x);
+            y[(o + 2 * Ns) * NL + L] = csub(apc, bpd);
+            y[(o + 3 * Ns) * NL + L] = cmk(amc.x + bmd.y, amc.y - bmd.x);
+        }
+        __syncthreads();
+        C *t = x;
+        x = y;
+        y = t;
+    }
+    return x;
+}
+
 template <typename R>
 __device__ void load_twiddles(typename cplx_t<R>::T *tw, int n)
 {
@@ -505,22 +558,37 @@ __device__ __forceinline__ int pad_dests(int a_node, int M, int *p)
 // (x3: -c~ + a h3), with one halo node before and two after on every periodic
 // axis so that a cubic stencil never wraps.
 template <typename R>
-__device__ void synth_x1_body(const SynthArgs &a, int blk, unsigned char *smem)
+__device__ void synth_x1_body(const SynthArgs &a, int blk, unsigned char *smem, uint64_t *bar, uint32_t parity)
 {
     typedef typename cplx_t<R>::T C;
     const int n = a.M1, nf = a.nf, lg1 = a.lg1, RB = a.RB1;
     C *tw = reinterpret_cast<C *>(smem);
-    C *buf0 = tw + (n >> 1);
+    C *buf0 = tw + (n >> 1);       // [nf][RB][n]: each field's RB rows, as stored in the work buffer
     C *buf1 = buf0 + RB * nf * n;  // [RB][n] scratch of the transforms
     // row = y * M2 + l2 (3D: x3 node a3first + y at compact work plane y); 2D: l2
     const size_t fstride = (size_t)(a.dim == 3 ? (a.L3count + a.nyq) * a.M2 : a.Mlast) * a.M1;
     const C *W = reinterpret_cast<const C *>(a.work);
     const int row0 = blk * RB;
+    // Each field's RB rows are one contiguous run of the work buffer: one bulk
+    // copy per field (TMA; 16-byte aligned, a multiple of 16 bytes) into shared
+    // memory, completed on the mbarrier by transaction count.
+    if (threadIdx.x == 0) {
+        const uint32_t row_bytes = (uint32_t)(RB * n * sizeof(C));
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(umma::smem_u32(bar)),
+                     "r"(row_bytes * (uint32_t)nf)
+                     : "memory");
+        for (int f = 0; f < nf; ++f)
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                             umma::smem_u32(buf0 + (size_t)f * RB * n)),
+                         "l"(W + f * fstride + (size_t)row0 * n), "r"(row_bytes), "r"(umma::smem_u32(bar))
+                         : "memory");
+    }
     load_twiddles<R>(tw, n);
-    for (int i = threadIdx.x; i < RB * nf * n; i += blockDim.x) {
-        const int r = i / (nf * n), rem = i - r * nf * n;
-        const int f = rem / n, b1 = rem - f * n;
-        buf0[i] = W[f * fstride + (size_t)(row0 + r) * n + b1];
+    if (!umma::mbar_wait_n(umma::smem_u32(bar), parity, umma::WAIT_LIMIT)) {
+        // the copies did not land: record it, give them a second bounded wait, go on
+        if (a.err) atomicExch(a.err, 1);
+        umma::mbar_wait_n(umma::smem_u32(bar), parity, umma::WAIT_LIMIT);
     }
     __syncthreads();
     stockham_inverse_grouped(buf0, buf1, n, lg1, RB * nf, RB, tw);
@@ -539,7 +607,9 @@ __device__ void synth_x1_body(const SynthArgs &a, int blk, unsigned char *smem)
         }
         int p2[3], p3[3];
         int n2 = pad_dests((l2 + (a.M2 >> 1)) % a.M2, a.M2, p2);
-        const C *rr = res + (size_t)r * nf * n;
+        // field f of this row: res[(f RB + r) n + l1]
+        const C *rr = res + (size_t)r * n;
+        const size_t fs = (size_t)RB * n;
         if (a.dim == 3 && a.nyq && row / a.M2 == a.L3count) {
             // Nyquist row of the odd fields -> nyqgrid [p2][p1][2]
             C *NG = reinterpret_cast<C *>(a.nyqgrid);
@@ -548,7 +618,7 @@ __device__ void synth_x1_body(const SynthArgs &a, int blk, unsigned char *smem)
                 for (int i = threadIdx.x; i < 2 * a.P1; i += blockDim.x) {
                     const int p1 = i >> 1, f = 4 + (i & 1);
                     const int a1 = (p1 - 1 + n) % n;
-                    dst[i] = rr[f * n + (a1 + (n >> 1)) % n];
+                    dst[i] = rr[f * fs + (a1 + (n >> 1)) % n];
                 }
             }
             continue;
@@ -571,7 +641,7 @@ __device__ void synth_x1_body(const SynthArgs &a, int blk, unsigned char *smem)
                     int p1 = i / nf, f = i - p1 * nf;
                     int a1 = (p1 - 1 + n) % n;
                     int l1 = (a1 + (n >> 1)) % n;
-                    dst[i] = rr[f * n + l1];
+                    dst[i] = rr[f * fs + l1];
                 }
             }
         }
@@ -581,22 +651,94 @@ __device__ void synth_x1_body(const SynthArgs &a, int blk, unsigned char *smem)
 template <typename R>
 __global__ void __launch_bounds__(256) synth_first_pass(SynthArgs a)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     synth_first_pass_body<R>(a, blockIdx.x, smem);
 }
 
 template <typename R>
 __global__ void __launch_bounds__(256) synth_x2_pass(SynthArgs a)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     synth_x2_body<R>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem);
+}
+
+// mbarrier of the last pass's bulk copies: one arrival (the issuing thread's
+// expect_tx) per phase
+__device__ __forceinline__ void init_copy_barrier(uint64_t *bar)
+{
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(umma::smem_u32(bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    __syncthreads();
+}
+
+// Middle pass with tensor-map copies (single plans): the TJ columns b10 .. b10+TJ-1
+// of the M2 rows of plane (f, y) are one 2D box of the work buffer seen as a
+// [rows][M1] matrix of 8-byte units (a complex is U = sizeof(C)/8 units), loaded
+// by cp.async.bulk.tensor in boxes of at most 256 rows into an interleaved tile
+// [b2][t], transformed there, and written back the same way by a TMA store.
+// The box's first unit x = b10 U is even (TJ >= 2), so x * 8 bytes is a multiple
+// of 16 as the tensor copy requires.
+constexpr int X2_BOX_ROWS = 256;
+
+template <typename R>
+__global__ void __launch_bounds__(256) synth_x2_pass_tma(SynthArgs a, const __grid_constant__ CUtensorMap tm)
+{
+    typedef typename cplx_t<R>::T C;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar;
+    const int n = a.M2, TJ = a.TJ2, lg2 = a.lg2;
+    const int bx = blockIdx.x, y = blockIdx.y, f = blockIdx.z;
+    if (y == a.L3count && f != 4 && f != 5) return;  // the Nyquist plane is only for xz, yz
+    int lgTJ = 0;
+    while ((1 << lgTJ) < TJ) ++lgTJ;
+    C *tw = reinterpret_cast<C *>(smem);
+    C *buf0 = reinterpret_cast<C *>(smem + ((sizeof(C) * (n >> 1) + 127) & ~(size_t)127));
+    C *buf1 = buf0 + TJ * n;
+    const int U = (int)(sizeof(C) / 8);
+    const int x0 = bx * TJ * U, row0 = (f * (a.L3count + a.nyq) + y) * n;
+    const int boxr = n < X2_BOX_ROWS ? n : X2_BOX_ROWS;
+    const uint64_t tmap = reinterpret_cast<uint64_t>(&tm);
+    init_copy_barrier(&bar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(umma::smem_u32(&bar)),
+                     "r"((uint32_t)(n * TJ * sizeof(C)))
+                     : "memory");
+        for (int r = 0; r < n; r += boxr)
+            asm volatile(
+                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+                    umma::smem_u32(buf0 + (size_t)r * TJ)),
+                "l"(tmap), "r"(x0), "r"(row0 + r), "r"(umma::smem_u32(&bar))
+                : "memory");
+    }
+    load_twiddles<R>(tw, n);
+    if (!umma::mbar_wait_n(umma::smem_u32(&bar), 0u, umma::WAIT_LIMIT)) {
+        if (a.err) atomicExch(a.err, 1);
+        umma::mbar_wait_n(umma::smem_u32(&bar), 0u, umma::WAIT_LIMIT);
+    }
+    __syncthreads();
+    C *res = stockham_inverse_il(buf0, buf1, n, lg2, lgTJ, tw);
+    // the transformed tile is read by the async proxy: order the generic writes first
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int r = 0; r < n; r += boxr)
+            asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(tmap),
+                         "r"(x0), "r"(row0 + r), "r"(umma::smem_u32(res + (size_t)r * TJ))
+                         : "memory");
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    }
 }
 
 template <typename R>
 __global__ void __launch_bounds__(256) synth_x1_pass(SynthArgs a)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    synth_x1_body<R>(a, blockIdx.x, smem);
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar;
+    init_copy_barrier(&bar);
+    synth_x1_body<R>(a, blockIdx.x, smem, &bar, 0u);
 }
 
 // pair of virtual block vb: largest p with prefix[p] <= vb
@@ -619,7 +761,7 @@ __device__ __forceinline__ int batch_pair(const int *prefix, int np, int vb)
 template <typename R>
 __global__ void __launch_bounds__(256) synth_first_pass_batch(const SynthArgs *args, const int *prefix, int np)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     __shared__ SynthArgs sa;
     const int total = prefix[np];
     for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
@@ -634,7 +776,7 @@ __global__ void __launch_bounds__(256) synth_first_pass_batch(const SynthArgs *a
 template <typename R>
 __global__ void __launch_bounds__(256) synth_x2_pass_batch(const SynthArgs *args, const int *prefix, int np)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     __shared__ SynthArgs sa;
     const int total = prefix[np];
     for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
@@ -655,14 +797,17 @@ __global__ void __launch_bounds__(256) synth_x2_pass_batch(const SynthArgs *args
 template <typename R>
 __global__ void __launch_bounds__(256) synth_x1_pass_batch(const SynthArgs *args, const int *prefix, int np)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     __shared__ SynthArgs sa;
+    __shared__ __align__(8) uint64_t bar;
+    init_copy_barrier(&bar);
     const int total = prefix[np];
-    for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
+    uint32_t phase = 0;
+    for (int vb = blockIdx.x; vb < total; vb += gridDim.x, phase ^= 1u) {
         const int p = batch_pair(prefix, np, vb);
         if (threadIdx.x == 0) sa = args[p];
         __syncthreads();
-        synth_x1_body<R>(sa, vb - prefix[p], smem);
+        synth_x1_body<R>(sa, vb - prefix[p], smem, &bar, phase);
         __syncthreads();
     }
 }
@@ -733,6 +878,57 @@ void synth_config_t(SynthArgs &a, int tj_max, size_t sm[3])
     sm[2] = sizeof(C) * (a.M1 / 2 + (a.nf + 1) * RB1 * a.M1);
 }
 
+// cuTensorMapEncodeTiled from the driver (through the runtime's entry-point
+// query, so the library needs no link to libcuda); null when unavailable.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// Middle pass of a single plan: tensor-map copies when the tile allows them
+// (TJ >= 2 columns, a map the driver accepts), the plain staged loop otherwise.
+template <typename R>
+cudaError_t launch_x2(const SynthArgs &a, size_t smem_plain, cudaStream_t s)
+{
+    typedef typename cplx_t<R>::T C;
+    const dim3 grid(a.M1 / a.TJ2, a.L3count + a.nyq, a.nf);
+    PFN_cuTensorMapEncodeTiled_v12000 enc = a.TJ2 >= 2 ? tensor_map_encoder() : nullptr;
+    if (enc) {
+        const int U = (int)(sizeof(C) / 8);
+        const cuuint64_t dims[2] = {(cuuint64_t)a.M1 * U, (cuuint64_t)a.M2 * (a.L3count + a.nyq) * a.nf};
+        const cuuint64_t strides[1] = {(cuuint64_t)a.M1 * sizeof(C)};
+        const cuuint32_t box[2] = {(cuuint32_t)(a.TJ2 * U), (cuuint32_t)(a.M2 < X2_BOX_ROWS ? a.M2 : X2_BOX_ROWS)};
+        const cuuint32_t estr[2] = {1, 1};
+        CUtensorMap tm;
+        if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, a.work, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS) {
+            const size_t sm = ((sizeof(C) * (a.M2 >> 1) + 127) & ~(size_t)127) + 2 * sizeof(C) * a.TJ2 * a.M2;
+            cudaError_t e = cudaFuncSetAttribute(synth_x2_pass_tma<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return e;
+            synth_x2_pass_tma<R><<<grid, 256, sm, s>>>(a, tm);
+            gf_count_launch(1);
+            return cudaGetLastError();
+        }
+    }
+    cudaError_t e = cudaFuncSetAttribute(synth_x2_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_plain);
+    if (e != cudaSuccess) return e;
+    synth_x2_pass<R><<<grid, 256, smem_plain, s>>>(a);
+    gf_count_launch(1);
+    return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t launch_synth_t(const SynthArgs &a0, cudaStream_t s)
 {
@@ -745,10 +941,8 @@ cudaError_t launch_synth_t(const SynthArgs &a0, cudaStream_t s)
     synth_first_pass<R><<<ncols / a.TJ, 256, sm[0], s>>>(a);
     gf_count_launch(1);
     if (a.dim == 3) {
-        e = cudaFuncSetAttribute(synth_x2_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[1]);
+        e = launch_x2<R>(a, sm[1], s);
         if (e != cudaSuccess) return e;
-        synth_x2_pass<R><<<dim3(a.M1 / a.TJ2, a.L3count + a.nyq, a.nf), 256, sm[1], s>>>(a);
-        gf_count_launch(1);
     }
     e = cudaFuncSetAttribute(synth_x1_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[2]);
     if (e != cudaSuccess) return e;
@@ -956,13 +1150,12 @@ cudaError_t launch_far_grid_t(const SynthArgs &a0, double k, double a1, double a
     int blocks = (plane + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     fargrid_coef<R><<<blocks, 256, 0, s>>>(a, k, a1, a2, z0, hz);
-    cudaError_t e = cudaFuncSetAttribute(synth_x2_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[1]);
+    cudaError_t e = launch_x2<R>(a, sm[1], s);
     if (e != cudaSuccess) return e;
-    synth_x2_pass<R><<<dim3(a.M1 / a.TJ2, a.L3count, a.nf), 256, sm[1], s>>>(a);
     e = cudaFuncSetAttribute(synth_x1_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[2]);
     if (e != cudaSuccess) return e;
     synth_x1_pass<R><<<a.L3count * a.M2 / a.RB1, 256, sm[2], s>>>(a);
-    gf_count_launch(3);
+    gf_count_launch(2);
     return cudaGetLastError();
 }
 }  // namespace

@@ -53,7 +53,7 @@ EXPORTS = ["gf_trunc_default", "gf_plan", "gf_eval_grid", "gf_grid_bytes", "gf_e
            "gf_gemm_bf16", "gf_mlp_create", "gf_mlp_param_count", "gf_mlp_params", "gf_mlp_set_scale",
            "gf_mlp_forward", "gf_mlp_train_step", "gf_mlp_gradients", "gf_mlp_error_word", "gf_surrogate_eval",
            "gf_mlp_destroy", "gf_release_memory", "gf_peak_probe", "gf_surrogate_eval_residual",
-           "gf_wait_selftest"]
+           "gf_wait_selftest", "gf_plan_status"]
 
 NOALLOC_MAX_TARGETS = 1 << 18
 
@@ -116,6 +116,7 @@ def lib(build_if_missing: bool = True):
     L.gf_release_memory.argtypes = []
     L.gf_peak_probe.argtypes = [i32, i64, vp, P(ctypes.c_int64), vp]
     L.gf_wait_selftest.argtypes = [i64, i32, vp]
+    L.gf_plan_status.argtypes = [vp, vp]
     for name in ("gf_trunc_default", "gf_plan", "gf_eval_grid", "gf_eval_points", "gf_eval_points_host",
                  "gf_eval_points_noalloc", "gf_plan_batch", "gf_batch_synthesize", "gf_batch_eval_points",
                  "gf_batch_autotune", "gf_batch_get_tuning", "gf_batch_run_graph", "gf_batch_get_plan",
@@ -123,7 +124,7 @@ def lib(build_if_missing: bool = True):
                  "gf_mlp_forward", "gf_mlp_train_step", "gf_mlp_gradients", "gf_mlp_error_word",
                  "gf_surrogate_eval", "gf_mlp_destroy",
                  "gf_plan_get_info", "gf_destroy", "gf_set_phase_timing", "gf_plan_phase_ms", "gf_release_memory",
-                 "gf_peak_probe", "gf_surrogate_eval_residual", "gf_wait_selftest"):
+                 "gf_peak_probe", "gf_surrogate_eval_residual", "gf_wait_selftest", "gf_plan_status"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -279,6 +280,10 @@ class Plan:
         _check(lib().gf_eval_points_host(self._h, ctypes.c_void_p(xp), n, int(which), ctypes.c_void_p(op),
                                          _stream_ptr(stream)))
         return out
+
+    def status(self, stream=None) -> int:
+        """gf_plan_status: GF_OK, or GF_ERR_TIMEOUT if a bounded wait of the synthesis ran out."""
+        return int(lib().gf_plan_status(self._h, _stream_ptr(stream)))
 
     def phase_ms(self):
         """(synthesis, far table, near kernel, far kernel) device ms of the latest run."""

@@ -84,6 +84,8 @@ def test_grid_parity_3d(case3):
     torch.cuda.synchronize()
     assert got.shape == g.shape
     assert norm_err(got, g) < 1e-12
+    # the synthesis passes' staged copies (TMA) all completed within their bounded waits
+    assert plan.status() == gf.GF_OK
 
 
 @pytest.mark.parametrize("n", [1, 31, 33, 1017, 3000])
@@ -227,6 +229,7 @@ def test_full_size_config2_sampled():
     rng = np.random.default_rng(0)
     nodes = np.stack([rng.integers(0, m, 6) for m in pb.M], axis=1)
     gg = plan.eval_grid().cpu().numpy()[0]
+    assert plan.status() == gf.GF_OK
     ref_nodes = O.grid_nodes(pb, C, nodes)
     got_nodes = np.array([gg[n[2], n[1], n[0]] for n in nodes])
     assert np.abs(got_nodes - ref_nodes).max() < 1e-12 * np.abs(gg).max()
