@@ -754,6 +754,7 @@ __global__ void series_tables(EvalArgs a, E *tab, double2 *exptab, PropEntry *pr
         }
     if (blockIdx.x == 0 && threadIdx.x < 32) {
         const int pw = pbox.w - pbox.z + 1, ptot = (pbox.y - pbox.x + 1) * pw;
+        const int N0 = (int)rint(-a.a2);
         int cnt = 0;
         for (int base = 0; base < ptot; base += 32) {
             const int i = base + (int)threadIdx.x;
@@ -768,18 +769,47 @@ __global__ void series_tables(EvalArgs a, E *tab, double2 *exptab, PropEntry *pr
             const unsigned bal = __ballot_sync(0xffffffffu, in);
             if (in) {
                 const double br = sqrt((a.k - aa) * (a.k + aa));
-                prop[cnt + __popc(bal & ((1u << threadIdx.x) - 1u))] = PropEntry{c1, c2, br, 1.0 / br};
+                prop[cnt + __popc(bal & ((1u << threadIdx.x) - 1u))] =
+                    PropEntry{c1, c2, br, 1.0 / br, (double)(pbox.z + i % pw - N0), 1, pbox.x + i / pw,
+                              (float)c1, (float)c2, (float)br, (float)(1.0 / br)};
             }
             cnt += __popc(bal);
         }
+        __syncwarp();
+        // row starts: first = 0 where the previous entry is (n1, n2 - 1) (reads n1
+        // and m2, writes only first)
+        for (int q = (int)threadIdx.x; q < cnt; q += 32)
+            prop[q].first = (q > 0 && prop[q - 1].n1 == prop[q].n1 && prop[q - 1].m2 + 1.0 == prop[q].m2) ? 0 : 1;
         if (threadIdx.x == 0) *nprop = cnt;
     }
 }
 
+// Warp maximum / minimum of non-negative doubles, compared as 64-bit integers
+// (for x >= 0 the IEEE bit pattern orders like the value), which keeps the
+// comparisons off the FP64 pipe; the result is one of the lanes' values.
 __device__ __forceinline__ double warp_max(double v)
 {
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
+    long long b = __double_as_longlong(v);
+    for (int o = 16; o > 0; o >>= 1) b = max(b, __shfl_xor_sync(0xffffffffu, b, o));
+    return __longlong_as_double(b);
+}
+
+__device__ __forceinline__ double warp_min(double v)
+{
+    long long b = __double_as_longlong(v);
+    for (int o = 16; o > 0; o >>= 1) b = min(b, __shfl_xor_sync(0xffffffffu, b, o));
+    return __longlong_as_double(b);
+}
+
+// A float as a double by integer operations (no conversion instruction, which
+// would occupy the FP64 pipe): exact for zero and normal floats; denormal floats
+// (below 1.2e-38) read as zero.  Not for infinities or NaN.
+__device__ __forceinline__ double f2d_exact(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const bool nz = (u & 0x7F800000u) != 0u;
+    const unsigned hi = (u & 0x80000000u) | (nz ? ((u & 0x7FFFFFFFu) >> 3) + 0x38000000u : 0u);
+    return __hiloint2double((int)hi, nz ? (int)(u << 29) : 0);
 }
 
 // e^{-y} by Tang's table-driven method (ACM TOMS 15, 1989): y = y_j + r with
@@ -962,53 +992,60 @@ struct RStateFF {
 // d' = w + lambda b + s d, b' = d' + s b.
 constexpr float FF_GAP = 8.0f;
 
+// One float-float Reinsch step with the term n2 (weight 0 outside the lane's
+// truncation set).
+__device__ __forceinline__ void ff_step(RStateFF &st, const BetaEntry *__restrict__ row, int n2, float c2f,
+                                        float c1sq, float R2f, FF z, FF lam, float sf, const float4 *__restrict__ T,
+                                        int j0, int jmax)
+{
+    const float4 q = *reinterpret_cast<const float4 *>(&row[n2].bf);  // b hi, lo; ln b hi, lo
+    const bool ok = fmaf(c2f, c2f, c1sq) <= R2f && q.x != 0.f;
+    // y = b z + ln b
+    const float p = __fmul_rn(q.x, z.h);
+    float pe = __fmaf_rn(q.x, z.h, -p);
+    pe = __fmaf_rn(q.x, z.l, __fmaf_rn(q.y, z.h, pe));
+    const FF y0 = two_sum(p, q.z);
+    const FF y = two_sum(y0.h, __fadd_rn(__fadd_rn(y0.l, pe), q.w));
+    // table entry nearest to y
+    const float jm = __fmaf_rn((float)GF_EXPTAB_STEPS, y.h, 12582912.0f);
+    const int idx = min(max(__float_as_int(jm) - 0x4B400000 + j0, 0), jmax);
+    const float4 t = __ldg(T + idx);
+    // r = (y.h - y_j) + y.l (the first difference is exact)
+    const float rh = __fsub_rn(y.h, t.z);
+    const float rs = __fadd_rn(rh, y.l);
+    const float qq = __fmul_rn(__fmul_rn(rs, rs), __fmaf_rn(rs, -1.0f / 6.0f, 0.5f));
+    // e^{-r} = (1 - rh) - y.l + qq, then w = T[j] e^{-r}
+    const FF a = two_sum(1.0f, -rh);
+    const float al = __fadd_rn(__fsub_rn(a.l, y.l), qq);
+    float wh = __fmul_rn(t.x, a.h);
+    float wl = __fmaf_rn(t.x, a.h, -wh);
+    wl = __fmaf_rn(t.x, al, __fmaf_rn(t.y, a.h, wl));
+    wh = ok ? wh : 0.f;
+    wl = ok ? wl : 0.f;
+    // d' = (lambda b + w) + s d
+    const float m = __fmul_rn(lam.h, st.bh);
+    float me = __fmaf_rn(lam.h, st.bh, -m);
+    me = __fmaf_rn(lam.h, st.bl, __fmaf_rn(lam.l, st.bh, me));
+    const FF u = two_sum(m, wh);
+    const FF v = two_sum(u.h, __fmul_rn(sf, st.dh));
+    const float lo = __fadd_rn(__fadd_rn(__fadd_rn(u.l, v.l), __fadd_rn(me, wl)), __fmul_rn(sf, st.dl));
+    const FF dn = two_sum(v.h, lo);
+    // b' = d' + s b
+    const FF x = two_sum(dn.h, __fmul_rn(sf, st.bh));
+    const FF bn = two_sum(x.h, __fadd_rn(__fadd_rn(x.l, dn.l), __fmul_rn(sf, st.bl)));
+    st.dh = dn.h;
+    st.dl = dn.l;
+    st.bh = bn.h;
+    st.bl = bn.l;
+}
+
 __device__ __forceinline__ void reinsch_seg_ff(RStateFF &st, const BetaEntry *__restrict__ row, int &n2, int count,
                                                int dir, float &c2f, float c1sq, float R2f, FF z, FF lam, float sf,
                                                const float4 *__restrict__ T, int j0, int jmax)
 {
     const float df = (float)dir;
 #pragma unroll 2
-    for (int i = 0; i < count; ++i, n2 += dir, c2f += df) {
-        const float4 q = *reinterpret_cast<const float4 *>(&row[n2].bf);  // b hi, lo; ln b hi, lo
-        const bool ok = fmaf(c2f, c2f, c1sq) <= R2f && q.x != 0.f;
-        // y = b z + ln b
-        const float p = __fmul_rn(q.x, z.h);
-        float pe = __fmaf_rn(q.x, z.h, -p);
-        pe = __fmaf_rn(q.x, z.l, __fmaf_rn(q.y, z.h, pe));
-        const FF y0 = two_sum(p, q.z);
-        const FF y = two_sum(y0.h, __fadd_rn(__fadd_rn(y0.l, pe), q.w));
-        // table entry nearest to y
-        const float jm = __fmaf_rn((float)GF_EXPTAB_STEPS, y.h, 12582912.0f);
-        const int idx = min(max(__float_as_int(jm) - 0x4B400000 + j0, 0), jmax);
-        const float4 t = __ldg(T + idx);
-        // r = (y.h - y_j) + y.l (the first difference is exact)
-        const float rh = __fsub_rn(y.h, t.z);
-        const float rs = __fadd_rn(rh, y.l);
-        const float qq = __fmul_rn(__fmul_rn(rs, rs), __fmaf_rn(rs, -1.0f / 6.0f, 0.5f));
-        // e^{-r} = (1 - rh) - y.l + qq, then w = T[j] e^{-r}
-        const FF a = two_sum(1.0f, -rh);
-        const float al = __fadd_rn(__fsub_rn(a.l, y.l), qq);
-        float wh = __fmul_rn(t.x, a.h);
-        float wl = __fmaf_rn(t.x, a.h, -wh);
-        wl = __fmaf_rn(t.x, al, __fmaf_rn(t.y, a.h, wl));
-        wh = ok ? wh : 0.f;
-        wl = ok ? wl : 0.f;
-        // d' = (lambda b + w) + s d
-        const float m = __fmul_rn(lam.h, st.bh);
-        float me = __fmaf_rn(lam.h, st.bh, -m);
-        me = __fmaf_rn(lam.h, st.bl, __fmaf_rn(lam.l, st.bh, me));
-        const FF u = two_sum(m, wh);
-        const FF v = two_sum(u.h, __fmul_rn(sf, st.dh));
-        const float lo = __fadd_rn(__fadd_rn(__fadd_rn(u.l, v.l), __fadd_rn(me, wl)), __fmul_rn(sf, st.dl));
-        const FF dn = two_sum(v.h, lo);
-        // b' = d' + s b
-        const FF x = two_sum(dn.h, __fmul_rn(sf, st.bh));
-        const FF bn = two_sum(x.h, __fadd_rn(__fadd_rn(x.l, dn.l), __fmul_rn(sf, st.bl)));
-        st.dh = dn.h;
-        st.dl = dn.l;
-        st.bh = bn.h;
-        st.bl = bn.l;
-    }
+    for (int i = 0; i < count; ++i, n2 += dir, c2f += df) ff_step(st, row, n2, c2f, c1sq, R2f, z, lam, sf, T, j0, jmax);
 }
 
 // Feed `count` terms n2, n2 + dir, ... into the state (the first has the
@@ -1086,8 +1123,8 @@ __device__ __forceinline__ void reinsch_run_ff(RState<1> &st, const BetaEntry *_
         RStateFF f{0.f, 0.f, 0.f, 0.f};
         reinsch_seg_ff(f, row, n2, nff, dir, c2f, c1sq, R2f, zff, lamff, sf,
                        reinterpret_cast<const float4 *>(T + (jmax + 1)), j0, jmax);
-        st.d[0] = (double)f.dh + (double)f.dl;
-        st.b[0] = (double)f.bh + (double)f.bl;
+        st.d[0] = f2d_exact(f.dh) + f2d_exact(f.dl);
+        st.b[0] = f2d_exact(f.bh) + f2d_exact(f.bl);
     }
     reinsch_seg<1, EXP_DEG_A>(st, row, n2, nd, dir, c2f, c2, c1sq, R2f, z, RS, T, j0, jmax);
 }
@@ -1103,6 +1140,37 @@ __device__ __forceinline__ void reinsch_zero(RState<NH> &st, const Reinsch &RS)
         st.b[e] = dn + flip_sign(st.b[e], RS.m);
         st.d[e] = dn;
     }
+}
+
+// sin x and cos x in float for |x| < 6000, by Cody and Waite's reduction
+// (Software Manual for the Elementary Functions, 1980): r = x - q pi/2 with
+// pi/2 in three parts (the first two of 12 significant bits, so q times each
+// is exact for |q| <= 4096), |r| <= pi/4, then the Taylor polynomials of sin
+// (to r^9, truncation < 2e-9) and cos (to r^10, < 2e-10) at 0 and the quadrant
+// q mod 4.  Error about 1.5 ulp; float arithmetic only (no FP64-pipe
+// conversion, no MUFU).
+__device__ __forceinline__ void sincos_cw(float x, float &s, float &c)
+{
+    const float qm = fmaf(x, 0.636619772f, 12582912.0f);  // rint(2x/pi) + 1.5 * 2^23
+    const int q = __float_as_int(qm) - 0x4B400000;
+    const float qf = qm - 12582912.0f;
+    float r = fmaf(-qf, 1.5703125f, x);
+    r = fmaf(-qf, 4.837512969970703e-4f, r);
+    r = fmaf(-qf, 7.549790126404332e-8f, r);
+    const float r2 = r * r;
+    float ps = fmaf(r2, 1.0f / 362880.0f, -1.0f / 5040.0f);
+    ps = fmaf(ps, r2, 1.0f / 120.0f);
+    ps = fmaf(ps, r2, -1.0f / 6.0f);
+    const float sr = fmaf(ps * r2, r, r);
+    float pc = fmaf(r2, -1.0f / 3628800.0f, 1.0f / 40320.0f);
+    pc = fmaf(pc, r2, -1.0f / 720.0f);
+    pc = fmaf(pc, r2, 1.0f / 24.0f);
+    pc = fmaf(pc, r2, -0.5f);
+    const float cr = fmaf(pc, r2, 1.0f);
+    const bool odd = (q & 1) != 0;
+    const float ss = odd ? cr : sr, cc = odd ? sr : cr;
+    s = (q & 2) ? -ss : ss;
+    c = ((q + 1) & 2) ? -cc : cc;
 }
 
 // e^{i m t2} in float for an integer |m| < 2^11, with no double arithmetic:
@@ -1129,7 +1197,7 @@ __device__ __forceinline__ void phase_m(const PhaseF &P, int m, float &s, float 
     r = fmaf(-kq, 1.9353071693331003e-3f, r);
     r = fmaf(-kq, 1.0253131677018246e-11f, r);
     r = fmaf(mf, P.tl, r);
-    sincosf(r, &s, &c);
+    sincos_cw(r, s, c);
 }
 
 // Row sums combined into the outputs with the row's real factors (c1 fixed):
@@ -1156,24 +1224,35 @@ __device__ __forceinline__ void add_row(F S[][2], const F rr[][2], F c1, F ik2)
     }
 }
 
-// The same segment sums in float (hardware ex2), for the exponentially small
-// tail of a double-precision plan: sum_{n2=lo}^{hi} w(n2) v^{n2-lo}, v = e^{i t2},
-// by Horner's rule from hi down.  b and 1/b come from the lattice index itself
-// (b^2 = c1^2 + c2^2 - k^2, one rsqrt), so the loop loads nothing; in float b
-// is good to ~1e-7 relative, e^{-b|x3|} to ~4e-6 for b|x3| <= 40, well inside
-// the tail's error budget.
-template <int NH>
-__device__ __forceinline__ void horner_step_f32(float c2, float q0, float zl2, float cv, float sv, float acc[NH][2])
+// The same segment sums in float (hardware ex2 and rsqrt), for the
+// exponentially small tail of a double-precision plan:
+// sum_{n2=lo}^{hi} w(n2) v^{n2-lo}, v = e^{i t2}.  b and 1/b come from the
+// lattice index itself (b^2 = c1^2 + c2^2 - k^2, one rsqrt), so the loop loads
+// nothing; in float b is good to ~1e-7 relative, e^{-b|x3|} to ~4e-6 for
+// b|x3| <= 40, well inside the tail's error budget.  The terms go in groups of
+// four aligned at lo, by Horner's rule in v^4 from the top group down: each
+// group adds w0 + w1 v + w2 v^2 + w3 v^3 (powers formed once per target), so
+// the dependent chain is one complex multiply-add per four terms and the four
+// weights are independent work.
+__device__ __forceinline__ float rsqrt_approx(float x)
 {
-    // q0 = c1^2 - k^2; propagating n (b^2 <= 0) get weight 0.  No per-lane
-    // truncation test: the terms of the warp's disk beyond the lane's own set are
-    // below e^{-T} of its largest term (they add accuracy).
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// weights of one index: q0 = c1^2 - k^2, zl2 = |x3| log2(e); propagating n
+// (b^2 <= 0) get weight 0.  No per-lane truncation test: the terms of the
+// warp's disk beyond the lane's own set are below e^{-T} of its largest term
+// (they add accuracy).
+template <int NH>
+__device__ __forceinline__ void tail_weights(float c2, float q0, float zl2, float wv[NH])
+{
     const float x = fmaf(c2, c2, q0);
     const bool ev = x > 0.f;
-    const float ib = rsqrtf(ev ? x : 1.f);
+    const float ib = rsqrt_approx(ev ? x : 1.f);
     const float b = x * ib;
     const float e = ev ? ex2_approx(-b * zl2) : 0.f;
-    float wv[NH];
     wv[0] = e * ib;
     if (NH > 1) {
         wv[1] = c2 * wv[0];
@@ -1182,25 +1261,63 @@ __device__ __forceinline__ void horner_step_f32(float c2, float q0, float zl2, f
         wv[4] = e;
         wv[5] = c2 * e;
     }
+}
+
+// Powers v, v^2, v^3, v^4 of v = (cv, sv).
+struct VPow {
+    float x[4], y[4];
+};
+
+__device__ __forceinline__ VPow vpowers(float cv, float sv)
+{
+    VPow P;
+    P.x[0] = cv;
+    P.y[0] = sv;
 #pragma unroll
-    for (int k = 0; k < NH; ++k) {
-        const float nx = fmaf(acc[k][0], cv, fmaf(-acc[k][1], sv, wv[k]));
-        const float ny = fmaf(acc[k][0], sv, acc[k][1] * cv);
-        acc[k][0] = nx;
-        acc[k][1] = ny;
+    for (int k = 1; k < 4; ++k) {
+        P.x[k] = P.x[k - 1] * cv - P.y[k - 1] * sv;
+        P.y[k] = P.x[k - 1] * sv + P.y[k - 1] * cv;
+    }
+    return P;
+}
+
+// One group n0 .. n0+3 (GUARD: indices above hi weigh zero): acc = acc v^4 +
+// sum_t w(n0 + t) v^t.
+template <int NH, bool GUARD>
+__device__ __forceinline__ void horner_group_f32(int n0, int hi, float a2f, float q0, float zl2, const VPow &V,
+                                                 float acc[NH][2])
+{
+    float w[4][NH];
+    const float cb = a2f + (float)n0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        tail_weights<NH>(cb + (float)t, q0, zl2, w[t]);
+        if (GUARD && n0 + t > hi) {
+#pragma unroll
+            for (int e = 0; e < NH; ++e) w[t][e] = 0.f;
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < NH; ++e) {
+        const float cx = fmaf(w[3][e], V.x[2], fmaf(w[2][e], V.x[1], fmaf(w[1][e], V.x[0], w[0][e])));
+        const float cy = fmaf(w[3][e], V.y[2], fmaf(w[2][e], V.y[1], w[1][e] * V.y[0]));
+        const float nx = fmaf(acc[e][0], V.x[3], fmaf(-acc[e][1], V.y[3], cx));
+        const float ny = fmaf(acc[e][0], V.y[3], fmaf(acc[e][1], V.x[3], cy));
+        acc[e][0] = nx;
+        acc[e][1] = ny;
     }
 }
 
-// zl2 = |x3| log2(e)
 template <int NH>
-__device__ __forceinline__ void seg_horner_f32(int lo, int hi, float a2f, float q0, float zl2, float cv, float sv,
+__device__ __forceinline__ void seg_horner_f32(int lo, int hi, float a2f, float q0, float zl2, const VPow &V,
                                                float acc[NH][2])
 {
 #pragma unroll
     for (int e = 0; e < NH; ++e) acc[e][0] = acc[e][1] = 0.f;
-    float c2 = a2f + (float)hi;
-#pragma unroll 2
-    for (int n2 = hi; n2 >= lo; --n2, c2 -= 1.0f) horner_step_f32<NH>(c2, q0, zl2, cv, sv, acc);
+    const int g = (hi - lo + 4) >> 2;  // groups; the top one may pass hi
+    if (g <= 0) return;
+    horner_group_f32<NH, true>(lo + 4 * (g - 1), hi, a2f, q0, zl2, V, acc);
+    for (int j = g - 2; j >= 0; --j) horner_group_f32<NH, false>(lo + 4 * j, hi, a2f, q0, zl2, V, acc);
 }
 
 // ---------------------------------------------------------------------------
@@ -1314,7 +1431,7 @@ __device__ __forceinline__ bool far_row(const FarWarp &W, const EvalArgs &a, int
 // anchor N0, rotated by the row phase A = e^{i c1 t1} and added into Sf.
 template <int NH, int NS>
 __device__ __forceinline__ void far_row_tails(int n2a, int n2b, int ca, int cb, int N0, float a2f, float c1f,
-                                              float c1sq, float k2f, float zf, float cvf, float svf, const PhaseF &PF,
+                                              float c1sq, float k2f, float zf, const VPow &V, const PhaseF &PF,
                                               float Ax, float Ay, float ik2f, float Sf[NS][2])
 {
     const float q0 = c1sq - k2f, zl2 = zf * 1.44269504f;
@@ -1326,7 +1443,7 @@ __device__ __forceinline__ void far_row_tails(int n2a, int n2b, int ca, int cb, 
     for (int e = 0; e < NH; ++e) tf[e][0] = tf[e][1] = 0.f;
     if (n2a <= tl_hi) {
         float acc[NH][2], ps, pc;
-        seg_horner_f32<NH>(n2a, tl_hi, a2f, q0, zl2, cvf, svf, acc);
+        seg_horner_f32<NH>(n2a, tl_hi, a2f, q0, zl2, V, acc);
         phase_m(PF, n2a - N0, ps, pc);
 #pragma unroll
         for (int e = 0; e < NH; ++e) {
@@ -1336,7 +1453,7 @@ __device__ __forceinline__ void far_row_tails(int n2a, int n2b, int ca, int cb, 
     }
     if (th_lo <= n2b) {
         float acc[NH][2], ps, pc;
-        seg_horner_f32<NH>(th_lo, n2b, a2f, q0, zl2, cvf, svf, acc);
+        seg_horner_f32<NH>(th_lo, n2b, a2f, q0, zl2, V, acc);
         phase_m(PF, th_lo - N0, ps, pc);
 #pragma unroll
         for (int e = 0; e < NH; ++e) {
@@ -1397,6 +1514,7 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, i
         const float sgn = RS.m ? -1.0f : 1.0f;
         const float k2f = (float)k2;
         const float svf = (float)sv, cvf = (float)cv, zf = (float)L.z;
+        const VPow VP = vpowers(cvf, svf);
         double P[NF][2];
         double S[NS][2];
         float Sf[NS][2];
@@ -1413,43 +1531,52 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, i
         // sin to theta^7: truncation below 1e-17); a warp whose spread is wider takes
         // a sincos per lane.
         double2 ph = make_double2(1.0, 0.0);
-        double pc1 = 0.0, pc2 = 0.0;
         const int nq = slab == 0 ? *a.nprop : 0;
-        double zw = L.valid ? L.z : 1e300;
-        for (int o = 16; o > 0; o >>= 1) zw = fmin(zw, __shfl_xor_sync(0xffffffffu, zw, o));
+        const double zw = warp_min(L.valid ? L.z : 1e300);
         const double dz = L.z - zw;
         const bool taylor = nq > 0 && warp_max(L.valid ? dz : 0.0) * a.k <= 0.02;
-        double ewx = 1.0, ewy = 0.0;  // e^{i beta_{q0 + lane} z_w}
+        double ewx = 1.0, ewy = 0.0;  // e^{i beta_{q0 + lane} z_w} / beta_{q0 + lane}
         for (int q = 0; q < nq; ++q) {
             if (taylor && (q & 31) == 0) {
-                if (q + lane < nq) sincos(a.prop[q + lane].br * zw, &ewy, &ewx);
+                if (q + lane < nq) {
+                    const PropEntry pl = a.prop[q + lane];
+                    sincos(pl.br * zw, &ewy, &ewx);
+                    ewx *= pl.ibr;
+                    ewy *= pl.ibr;
+                }
             }
             const PropEntry pe = a.prop[q];
-            if (q > 0 && pe.c1 == pc1 && fabs(pe.c2 - pc2 - 1.0) < 0.5) {
-                ph = cmul(ph, make_double2(cv, sv));
-            } else {
+            if (pe.first) {
                 double sp, cp;
-                sincos(pe.c1 * L.t1 + ((pe.c2 - a.a2) - N0) * L.t2, &sp, &cp);
+                sincos(fma(pe.c1, L.t1, pe.m2 * L.t2), &sp, &cp);
                 ph = make_double2(cp, sp);
+            } else {
+                ph = cmul(ph, make_double2(cv, sv));
             }
-            pc1 = pe.c1;
-            pc2 = pe.c2;
-            double sz, cz;
+            // u = e^{i beta z} / beta
+            double ux, uy;
             if (taylor) {
                 const double Ex = __shfl_sync(0xffffffffu, ewx, q & 31), Ey = __shfl_sync(0xffffffffu, ewy, q & 31);
                 const double th = pe.br * dz, th2 = th * th;
                 const double ct = fma(fma(fma(th2, -1.0 / 720.0, 1.0 / 24.0), th2, -0.5), th2, 1.0);
                 const double st = th * fma(fma(fma(th2, -1.0 / 5040.0, 1.0 / 120.0), th2, -1.0 / 6.0), th2, 1.0);
-                cz = Ex * ct - Ey * st;
-                sz = Ex * st + Ey * ct;
+                ux = Ex * ct - Ey * st;
+                uy = Ex * st + Ey * ct;
             } else {
+                double sz, cz;
                 sincos(pe.br * L.z, &sz, &cz);
+                ux = pe.ibr * cz;
+                uy = pe.ibr * sz;
             }
             const double cp = ph.x, sp = ph.y;
-            double tx = pe.ibr * (cz * cp - sz * sp), ty = pe.ibr * (cz * sp + sz * cp);
-            P[0][0] += tx;
-            P[0][1] += ty;
+            if (NF == 1) {
+                P[0][0] = fma(ux, cp, fma(-uy, sp, P[0][0]));
+                P[0][1] = fma(ux, sp, fma(uy, cp, P[0][1]));
+            }
             if (NF > 1) {
+                const double tx = ux * cp - uy * sp, ty = ux * sp + uy * cp;
+                P[0][0] += tx;
+                P[0][1] += ty;
                 double b3 = pe.br * L.sg;
                 double f[6] = {1.0 - pe.c1 * pe.c1 * ik2, 1.0 - pe.c2 * pe.c2 * ik2, 1.0 - b3 * b3 * ik2,
                                -pe.c1 * pe.c2 * ik2, -pe.c1 * b3 * ik2, -pe.c2 * b3 * ik2};
@@ -1469,6 +1596,11 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, i
             r_hi = min(r_hi, (int)floorf(-W.a1f + rcf) + 1);
         }
         double2 A = make_double2(1.0, 0.0);  // e^{i c1 t1}
+        // Helmholtz: Reinsch's closing step is linear in the state (d, b), so the
+        // rows' final states, times the row phase A, are summed first and closed
+        // once: DR, BR from the right sums (index n2 - N0 >= 0), DL, BL from the
+        // left ones (index N0 - n2 >= 1, before their zero step)
+        double2 DR = make_double2(0.0, 0.0), BR = DR, DL = DR, BL = DR;
         for (int n1 = r_lo; n1 <= r_hi; ++n1) {
             // row phase by recurrence, re-anchored every 16 rows
             if (((n1 - r_lo) & 15) == 0) {
@@ -1482,8 +1614,8 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, i
             if (TAILS && ((n1 - r_lo) & 7) == 7) {
 #pragma unroll
                 for (int e = 0; e < NS; ++e) {
-                    S[e][0] += (double)Sf[e][0];
-                    S[e][1] += (double)Sf[e][1];
+                    S[e][0] += f2d_exact(Sf[e][0]);
+                    S[e][1] += f2d_exact(Sf[e][1]);
                     Sf[e][0] = Sf[e][1] = 0.f;
                 }
             }
@@ -1506,59 +1638,79 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, i
                     const int mff = max(0, cb - max((int)ceilf(qff - a2f) + 1, N0) + 1);
                     reinsch_run_ff(*reinterpret_cast<RState<1> *>(&R), row, cb, -1, mff, tot - mff, c1sq, a2f, R2f, L.z,
                                    zff, RS, lamff, sgn, T, j0, jmax);
+                    DR.x = fma(A.x, R.d[0], DR.x);
+                    DR.y = fma(A.y, R.d[0], DR.y);
+                    BR.x = fma(A.x, R.b[0], BR.x);
+                    BR.y = fma(A.y, R.b[0], BR.y);
+                    if (ca < N0) {
+                        const int mffl = max(0, min((int)floorf(-qff - a2f) - 1, N0 - 1) - ca + 1);
+                        reinsch_run_ff(*reinterpret_cast<RState<1> *>(&Lt), row, ca, 1, mffl, N0 - ca - mffl, c1sq, a2f,
+                                       R2f, L.z, zff, RS, lamff, sgn, T, j0, jmax);
+                        DL.x = fma(A.x, Lt.d[0], DL.x);
+                        DL.y = fma(A.y, Lt.d[0], DL.y);
+                        BL.x = fma(A.x, Lt.b[0], BL.x);
+                        BL.y = fma(A.y, Lt.b[0], BL.y);
+                    }
                 } else {
                     const int tot = cb - N0 + 1;
                     const int r3 = (int)ceilf(q3 - a2f) + 1, r4 = (int)ceilf(q4 - a2f) + 1;
                     const int m3 = max(0, cb - max(r3, N0) + 1);
                     const int m4 = max(0, min(cb - m3, cb) - max(r4, N0) + 1);
                     reinsch_run<NH>(R, row, cb, -1, m3, m4, tot - m3 - m4, a.a2, c1sq, a2f, R2f, L.z, RS, T, j0, jmax);
-                }
-                double rr[NH][2];
-#pragma unroll
-                for (int e = 0; e < NH; ++e) {
-                    const double b1 = flip_sign(R.b[e] - R.d[e], RS.m);
-                    rr[e][0] = fma(-RS.hlam, b1, R.d[e]);
-                    rr[e][1] = b1 * RS.sv;
-                }
-                if (ca < N0) {
-                    const int tot = N0 - ca;
-                    if (NH == 1) {
-                        const int mff = max(0, min((int)floorf(-qff - a2f) - 1, N0 - 1) - ca + 1);
-                        reinsch_run_ff(*reinterpret_cast<RState<1> *>(&Lt), row, ca, 1, mff, tot - mff, c1sq, a2f, R2f,
-                                       L.z, zff, RS, lamff, sgn, T, j0, jmax);
-                    } else {
-                        const int l3 = (int)floorf(-q3 - a2f) - 1, l4 = (int)floorf(-q4 - a2f) - 1;
-                        const int m3 = max(0, min(l3, N0 - 1) - ca + 1);
-                        const int m4 = max(0, min(l4, N0 - 1) - (ca + m3) + 1);
-                        reinsch_run<NH>(Lt, row, ca, 1, m3, m4, tot - m3 - m4, a.a2, c1sq, a2f, R2f, L.z, RS, T, j0, jmax);
-                    }
-                    reinsch_zero<NH>(Lt, RS);
+                    // Maxwell: each row closed and combined with its own factors in c1
+                    double rr[NH][2];
 #pragma unroll
                     for (int e = 0; e < NH; ++e) {
-                        const double b1 = flip_sign(Lt.b[e] - Lt.d[e], RS.m);
-                        rr[e][0] += fma(-RS.hlam, b1, Lt.d[e]);
-                        rr[e][1] -= b1 * RS.sv;
+                        const double b1 = flip_sign(R.b[e] - R.d[e], RS.m);
+                        rr[e][0] = fma(-RS.hlam, b1, R.d[e]);
+                        rr[e][1] = b1 * RS.sv;
                     }
-                }
+                    if (ca < N0) {
+                        const int totl = N0 - ca;
+                        const int l3 = (int)floorf(-q3 - a2f) - 1, l4 = (int)floorf(-q4 - a2f) - 1;
+                        const int m3l = max(0, min(l3, N0 - 1) - ca + 1);
+                        const int m4l = max(0, min(l4, N0 - 1) - (ca + m3l) + 1);
+                        reinsch_run<NH>(Lt, row, ca, 1, m3l, m4l, totl - m3l - m4l, a.a2, c1sq, a2f, R2f, L.z, RS, T, j0,
+                                        jmax);
+                        reinsch_zero<NH>(Lt, RS);
 #pragma unroll
-                for (int e = 0; e < NH; ++e) {
-                    const double x = rr[e][0], y = rr[e][1];
-                    rr[e][0] = A.x * x - A.y * y;
-                    rr[e][1] = A.x * y + A.y * x;
+                        for (int e = 0; e < NH; ++e) {
+                            const double b1 = flip_sign(Lt.b[e] - Lt.d[e], RS.m);
+                            rr[e][0] += fma(-RS.hlam, b1, Lt.d[e]);
+                            rr[e][1] -= b1 * RS.sv;
+                        }
+                    }
+#pragma unroll
+                    for (int e = 0; e < NH; ++e) {
+                        const double x = rr[e][0], y = rr[e][1];
+                        rr[e][0] = A.x * x - A.y * y;
+                        rr[e][1] = A.x * y + A.y * x;
+                    }
+                    add_row<NH, double>(S, rr, a.a1 + n1, ik2);
                 }
-                add_row<NH, double>(S, rr, a.a1 + n1, ik2);
             }
             // float tails [n2a, ca-1] and [cb+1, n2b] (the whole row when there is
             // no core)
             if (TAILS)
-                far_row_tails<NH, NS>(n2a, n2b, ca, cb, N0, a2f, c1f, c1sq, k2f, zf, cvf, svf, PF, (float)A.x, (float)A.y,
+                far_row_tails<NH, NS>(n2a, n2b, ca, cb, N0, a2f, c1f, c1sq, k2f, zf, VP, PF, (float)A.x, (float)A.y,
                                       ik2f, Sf);
         }
         if (!L.valid) return;
+        if (NH == 1) {
+            // right: sum = D + U (-lambda/2 + i sin theta), U = s (B - D);
+            // left, after the zero step: sum = s D + B (lambda/2 - i sin theta)
+            const double ux = flip_sign(BR.x - DR.x, RS.m), uy = flip_sign(BR.y - DR.y, RS.m);
+            S[0][0] += fma(-RS.hlam, ux, fma(-RS.sv, uy, DR.x));
+            S[0][1] += fma(-RS.hlam, uy, fma(RS.sv, ux, DR.y));
+            S[0][0] += fma(RS.hlam, BL.x, fma(RS.sv, BL.y, flip_sign(DL.x, RS.m)));
+            S[0][1] += fma(RS.hlam, BL.y, fma(-RS.sv, BL.x, flip_sign(DL.y, RS.m)));
+        }
+        if (TAILS) {
 #pragma unroll
-        for (int e = 0; e < NS; ++e) {
-            S[e][0] += (double)Sf[e][0];
-            S[e][1] += (double)Sf[e][1];
+            for (int e = 0; e < NS; ++e) {
+                S[e][0] += f2d_exact(Sf[e][0]);
+                S[e][1] += f2d_exact(Sf[e][1]);
+            }
         }
         // back from the anchor frame with the lattice phase: one factor
         // e^{i(2 pi <alpha.m> + (alpha_2 + N0) t2)} (i/8pi^2)
@@ -1589,16 +1741,18 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, i
 
 // Far work items (a row slab of a chunk of 32 consecutive entries of the
 // sorted list) are handed out one at a time from a counter, the most expensive
-// chunks first: the list is in ascending bucket order and the bucket 64 c/|x3|
-// grows as the target nears the slab, where the truncation disk (radius ~
-// T/|x3|) is largest, so the t-th item taken is slab t % S of chunk
-// nch-1-t/S.  S (row slabs per chunk) is chosen so that there are about eight
-// items per resident warp, which keeps the end of the launch short.
-__device__ __forceinline__ int far_slabs(int nch, int smax)
+// chunks first: the list is in ascending bucket order and the bucket
+// GF_FAR_BUCKETS c/|x3| grows as the target nears the slab, where the truncation
+// disk (radius ~ T/|x3|) is largest, so the t-th item taken is slab t % S of
+// chunk nch-1-t/S.  S (row slabs per chunk) is chosen so that there are about
+// per_warp items per resident warp, which keeps the end of the launch short; the
+// double-precision kernel asks for four, so that long lists keep one slab per
+// chunk and its per-target set-up (double sines, divisions) is not repeated.
+__device__ __forceinline__ int far_slabs(int nch, int smax, int per_warp = 8)
 {
     const int nwarps = (int)(gridDim.x * blockDim.x) >> 5;
     if (nch <= 0) return 1;
-    const int s = (8 * nwarps + nch - 1) / nch;
+    const int s = (per_warp * nwarps + nch - 1) / nch;
     return s < 1 ? 1 : s > smax ? smax : s;
 }
 
@@ -1644,11 +1798,13 @@ __device__ void far3d_tail_chunk(const EvalArgs &a, int w, int count, int slab, 
     const int N0 = W.N0;
     const float zf = (float)L.z;
     float svf, cvf;
-    sincosf((float)L.t2, &svf, &cvf);
+    sincos_cw((float)L.t2, svf, cvf);
+    const VPow VP = vpowers(cvf, svf);
     const PhaseF P1 = phase_split(L.t1), P2 = phase_split(L.t2);
-    double sa1, ca1;
-    sincos(a.a1 * L.t1, &sa1, &ca1);
-    const float A0x = (float)ca1, A0y = (float)sa1;  // e^{i alpha_1 t1}
+    // e^{i alpha_1 t1} in float (the tails are summed in float; this kernel
+    // leaves the FP64 pipe to the double sums running beside it)
+    float A0x, A0y;
+    sincos_cw(W.a1f * (float)L.t1, A0y, A0x);
     double S[NS][2];
     float Sf[NS][2];
 #pragma unroll
@@ -1660,8 +1816,8 @@ __device__ void far3d_tail_chunk(const EvalArgs &a, int w, int count, int slab, 
         if (((n1 - r_lo) & 7) == 7) {
 #pragma unroll
             for (int e = 0; e < NS; ++e) {
-                S[e][0] += (double)Sf[e][0];
-                S[e][1] += (double)Sf[e][1];
+                S[e][0] += f2d_exact(Sf[e][0]);
+                S[e][1] += f2d_exact(Sf[e][1]);
                 Sf[e][0] = Sf[e][1] = 0.f;
             }
         }
@@ -1670,21 +1826,24 @@ __device__ void far3d_tail_chunk(const EvalArgs &a, int w, int count, int slab, 
         if (!far_row(W, a, n1, c1f, c1sq, n2a, n2b, ca, cb)) continue;
         float sn, cn;
         phase_m(P1, n1, sn, cn);
-        far_row_tails<NH, NS>(n2a, n2b, ca, cb, N0, W.a2f, c1f, c1sq, k2f, zf, cvf, svf, P2, A0x * cn - A0y * sn,
+        far_row_tails<NH, NS>(n2a, n2b, ca, cb, N0, W.a2f, c1f, c1sq, k2f, zf, VP, P2, A0x * cn - A0y * sn,
                               A0x * sn + A0y * cn, ik2f, Sf);
     }
     if (!L.valid) return;
 #pragma unroll
     for (int e = 0; e < NS; ++e) {
-        S[e][0] += (double)Sf[e][0];
-        S[e][1] += (double)Sf[e][1];
+        S[e][0] += f2d_exact(Sf[e][0]);
+        S[e][1] += f2d_exact(Sf[e][1]);
     }
-    // the same lattice phase and factors as far3d_f64_chunk (no propagating terms)
+    // the same lattice phase and factors as far3d_f64_chunk (no propagating
+    // terms); the fractional part of <alpha.m> in double, its sine and cosine in
+    // float
     double ph2 = a.a1 * L.m1 + a.a2 * L.m2;
     ph2 -= rint(ph2);
-    double sN, cN;
-    sincos(fma(2.0 * GF_PI, ph2, (a.a2 + N0) * L.t2), &sN, &cN);
-    const double2 pre = make_double2(-sN / (8.0 * GF_PI * GF_PI), cN / (8.0 * GF_PI * GF_PI));
+    float sNf, cNf;
+    sincos_cw((float)fma(2.0 * GF_PI, ph2, (a.a2 + N0) * L.t2), sNf, cNf);
+    constexpr double i8pi2 = 1.0 / (8.0 * GF_PI * GF_PI);
+    const double2 pre = make_double2(-f2d_exact(sNf) * i8pi2, f2d_exact(cNf) * i8pi2);
     double2 *o = out + (size_t)L.idx * ne;
     if (NF == 1) {
         add_out(o, cmul(pre, make_double2(S[0][1], -S[0][0])));
@@ -1746,7 +1905,7 @@ __device__ void far3d_f32_chunk(const EvalArgs &a, int w, int count, int slab, i
         float R2mf = R2f;
         for (int o = 16; o > 0; o >>= 1) R2mf = fmaxf(R2mf, __shfl_xor_sync(0xffffffffu, R2mf, o));
         float sv, cv;
-        sincosf(t2, &sv, &cv);
+        sincos_cw(t2, sv, cv);
         float P[NF][2];
         float S[NF == 1 ? 1 : 7][2];
 #pragma unroll
@@ -1755,10 +1914,10 @@ __device__ void far3d_f32_chunk(const EvalArgs &a, int w, int count, int slab, i
         for (int e = 0; e < (NF == 1 ? 1 : 7); ++e) S[e][0] = S[e][1] = 0.f;
         for (int q = 0, nq = slab == 0 ? *a.nprop : 0; q < nq; ++q) {
             const PropEntry pe = a.prop[q];
-            float br = (float)pe.br, ibr = (float)pe.ibr, c1 = (float)pe.c1, c2 = (float)pe.c2;
+            const float br = pe.brf, ibr = pe.ibrf, c1 = pe.c1f, c2 = pe.c2f;
             float sz, cz, sp, cp;
-            sincosf(br * z, &sz, &cz);
-            sincosf(c1 * t1 + c2 * t2, &sp, &cp);
+            sincos_cw(br * z, sz, cz);
+            sincos_cw(c1 * t1 + c2 * t2, sp, cp);
             float tx = ibr * (cz * cp - sz * sp), ty = ibr * (cz * sp + sz * cp);
             P[0][0] += tx;
             P[0][1] += ty;
@@ -1818,7 +1977,7 @@ __device__ void far3d_f32_chunk(const EvalArgs &a, int w, int count, int slab, i
                 }
             }
             float sp, cp;
-            sincosf(c1 * t1 + (a2f + (float)n2a) * t2, &sp, &cp);
+            sincos_cw(c1 * t1 + (a2f + (float)n2a) * t2, sp, cp);
             float r[NF == 1 ? 1 : 6][2];
 #pragma unroll
             for (int e2 = 0; e2 < (NF == 1 ? 1 : 6); ++e2) {

@@ -143,9 +143,14 @@ struct __align__(16) BetaEntry {
 struct BetaEntryF {
     float bl2, ib, b, pad;  // b log2(e), 1/b, b
 };
-// Propagating index n: in-plane wave vector alpha_n, real beta_n and 1/beta_n.
+// Propagating index n: in-plane wave vector alpha_n, real beta_n and 1/beta_n;
+// m2 = n2 - N0 (N0 = rint(-alpha_2), exact), first = 0 when the entry before
+// it in the list is (n1, n2 - 1), 1 otherwise, the row index n1, and float
+// copies of c1, c2, beta_n, 1/beta_n for the float kernels.
 struct PropEntry {
-    double c1, c2, br, ibr;
+    double c1, c2, br, ibr, m2;
+    int first, n1;
+    float c1f, c2f, brf, ibrf;
 };
 
 struct EvalArgs {
