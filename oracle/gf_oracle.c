@@ -22,7 +22,11 @@
  *   - point evaluation: Algorithms 1, 2 and 3 (branch, reduction, cubic
  *     interpolation on the 4^d nearest nodes, singular add-back, phase);
  *   - far branch / exact reference: eigenfunction expansions (ei), (he) and
- *     their second derivatives.
+ *     their second derivatives;
+ *   - 2D derivatives (Sec. 2.4): the gradient fields K_1 - h_1, K_2 - h_2 and
+ *     the second-derivative differences T_pq - h_pq for two wave numbers, their
+ *     singular parts' coefficients by the plane Fourier transform reduced to
+ *     Hankel transforms, and the term-by-term derivatives of (ei).
  * The integrals that the paper evaluates "by FFT" (the X' integrals in
  * (fck-coef)/(kdj1), the singular-part transform in (fj) and Phi_1-hat,
  * Phi_2-hat in (fcf1-coef)/(fcf2-coef)) are evaluated by Gauss-Legendre
@@ -834,5 +838,309 @@ void or_grid_nodes(const or_params *p, const double *C, int field, const int *no
             s += s3;
         }
         o[i] = s / V;
+    }
+}
+
+/* ======================================================================== */
+/* 2D derivatives (Sec. 2.4).                                                 */
+/*   Sec. 2.4.1: K_1 = e^{-i alpha x1} dG/dx1, K_2 = e^{-i alpha x1} dG/dx2,     */
+/*     with Fourier coefficients i(alpha + j1) K-hat_j and i (j2 pi/c~) K-hat_j; */
+/*     singular parts h_1, h_2 removed, K_i - h_i synthesised by inverse DFT,   */
+/*     interpolated, h_i added back.                                          */
+/*   Sec. 2.4.2: T_pq = K^{(k)}_pq - K^{(k2)}_pq, the differences of            */
+/*     e^{-i alpha x1} d_p d_q G for two wave numbers, coefficients            */
+/*     -(alpha+j1)^2 dK-hat, -(alpha+j1)(j2 pi/c~) dK-hat, -(j2 pi/c~)^2 dK-hat  */
+/*     (dK-hat = K-hat^{(k)} - K-hat^{(k2)}), singular parts h_11, h_12, h_22.  */
+/* The singular parts, with two readings of the printed text (derived from  */
+/* (i/4) H_0(kr) = -(1/2pi) ln r + (k^2/8pi) r^2 ln r + smooth, times         */
+/* e^{-i alpha x1} = 1 - i alpha x1 - alpha^2 x1^2/2 + ...):                   */
+/*   h_1  = -(1/2pi) [ -(k^2/2) x1 ln r + x1/r^2 - i alpha x1^2/r^2             */
+/*                     - (alpha^2/2) x1^3/r^2 ] Y                               */
+/*   h_2  = -(1/2pi) [ -(k^2/2) x2 ln r + x2/r^2 - i alpha x1 x2/r^2            */
+/*                     - (alpha^2/2) x1^2 x2/r^2 ] Y      (x2 ln r, not x1 ln r) */
+/*   h_11 = +(dk2/2pi) [ ln r/2 - (i alpha/2) x1 ln r + x1^2/(2 r^2)           */
+/*                       - i alpha x1^3/(2 r^2) ] Y                             */
+/*   h_12 = +(dk2/2pi) [ x1 x2/(2 r^2) - (i alpha/2) x1^2 x2/r^2 ] Y            */
+/*   h_22 = +(dk2/2pi) [ ln r/2 - (i alpha/2) x1 ln r + x2^2/(2 r^2)           */
+/*                       - (i alpha/2) x1 x2^2/r^2 ] Y                          */
+/* with dk2 = k^2 - k2^2 (the + sign: d_11 of (k^2/8pi) r^2 ln r is            */
+/* (k^2/2pi)(ln r/2 + x1^2/(2r^2)) + const), Y = Y_eps(r).                     */
+/* ======================================================================== */
+
+/* J_0 .. J_3 at z together, by the trapezoidal rule on Bessel's integral with
+ * P >= |z| + 16 (|z|/2 + 1)^{1/3} + 40 points: the rule's error is made of the
+ * aliases J_{P -+ n}(z), which decay faster than e^{-30} once the order
+ * passes |z| by that margin (Airy-type decay beyond the turning point). */
+static void bessel_j0123(double z, double J[4])
+{
+    int P = (int)(fabs(z) + 16.0 * cbrt(0.5 * fabs(z) + 1.0)) + 40;
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int m = 0; m < P; ++m) {
+        double th = 2.0 * M_PI * m / P, zs = z * sin(th);
+        for (int n = 0; n < 4; ++n) s[n] += cos(n * th - zs);
+    }
+    for (int n = 0; n < 4; ++n) J[n] = s[n] / P;
+}
+
+void or_bessel_j0123(double z, double *J) { bessel_j0123(z, J); }
+
+/* The five Hankel integrals of the cutoff int_0^{2 eps} Y(r) J_n(rho r) r^pw dr
+ * used below, (n, pw) = (1,0), (0,1), (2,1), (1,2), (3,2), into out[0..4].
+ * The integrand is analytic on [0, eps] (Y = 1) and on [eps, 2 eps] (Y a
+ * polynomial); each piece is cut into 1 + rho eps / 16 panels (at most about
+ * three oscillations of J_n(rho r) per panel) of Gauss-Legendre with the
+ * plan's Q nodes. */
+static void hankel_Y5(const or_params *p, const double *gx, const double *gw, double rho, double out[5])
+{
+    double e = p->eps;
+    int np = 1 + (int)(rho * e / 16.0);
+    for (int i = 0; i < 5; ++i) out[i] = 0.0;
+    for (int piece = 0; piece < 2; ++piece) {
+        double a0 = piece * e, w = e / np;
+        for (int s = 0; s < np; ++s) {
+            double a = a0 + s * w, hw = 0.5 * w, mid = a + hw;
+            for (int m = 0; m < p->Q; ++m) {
+                double r = mid + hw * gx[m], J[4];
+                bessel_j0123(rho * r, J);
+                double y = (piece == 0 ? 1.0 : or_yps(r, e, 0)) * gw[m] * hw;
+                out[0] += y * J[1];
+                out[1] += y * J[0] * r;
+                out[2] += y * J[2] * r;
+                out[3] += y * J[1] * r * r;
+                out[4] += y * J[3] * r * r;
+            }
+        }
+    }
+}
+
+/* sqrt(V) times the coefficients of x2 ln r Y scaled like f_2: the x2 analogue
+ * of (fcf2-coef), F2'-hat = (-2 i eta2 F1-hat + Phi2'-hat/(2 pi))/|eta|^2 with
+ * Phi2' = x2 Phi_1 (the same derivation: Delta(x2 g) = x2 Delta g + 2 d2 g). */
+static cplx sqrtV_F2y(const or_params *p, const double *gx, const double *gw, int j1, double q, cplx F1)
+{
+    double eta2 = (double)j1 * j1 + q * q;
+    if (eta2 == 0.0) return 0.0;
+    double eta = sqrt(eta2), a = p->eps, b = 2.0 * p->eps;
+    double hw = 0.5 * (b - a), mid = 0.5 * (a + b), s1 = 0.0;
+    for (int m = 0; m < p->Q; ++m) {
+        double r = mid + hw * gx[m];
+        double J0, J1;
+        or_bessel_j01(eta * r, &J0, &J1);
+        s1 += gw[m] * hw * Phi1(r, p->eps) * J1 * r * r;
+    }
+    cplx Phi2y = -2.0 * M_PI * I * (q / eta) * s1;
+    return (-2.0 * I * q * F1 + Phi2y / (2.0 * M_PI)) / eta2;
+}
+
+/* The plane Fourier transforms int int g(x) e^{-i eta.x} dx (= sqrt(V) times
+ * the coefficient) of the singular functions g, eta = (j1, q), by the
+ * angular reduction  FT[g(r) cos(m th)] = 2 pi (-i)^m cos(m phi) int g J_m(rho r) r dr
+ * (and sin for sin), rho = |eta|, eta = rho (cos phi, sin phi):
+ *   out[0] P0  = FT[ln r Y]        = -2 pi sqrt(V) F1-hat
+ *   out[1] P1c = FT[x1 ln r Y]     = -2 pi sqrt(V) F2-hat
+ *   out[2] P1s = FT[x2 ln r Y]     = -2 pi sqrt(V) F2'-hat
+ *   out[3] Q1c = FT[x1/r^2 Y],  out[4] Q1s = FT[x2/r^2 Y]       (m = 1 of Y/r)
+ *   out[5] R0  = FT[Y]                                           (m = 0)
+ *   out[6] R2c = FT[cos 2th Y], out[7] R2s = FT[sin 2th Y]       (m = 2)
+ *   out[8] S1c = FT[x1 Y],      out[9] S1s = FT[x2 Y]             (m = 1 of r Y)
+ *   out[10] S3c = FT[r cos 3th Y], out[11] S3s = FT[r sin 3th Y]  (m = 3 of r Y) */
+static void singular_transforms(const or_params *p, const double *gx, const double *gw, int j1, double q, cplx *out)
+{
+    cplx F1, F2;
+    sqrtV_F12hat(p, gx, gw, j1, q, &F1, &F2);
+    out[0] = -2.0 * M_PI * F1;
+    out[1] = -2.0 * M_PI * F2;
+    out[2] = -2.0 * M_PI * sqrtV_F2y(p, gx, gw, j1, q, F1);
+    double rho = sqrt((double)j1 * j1 + q * q), hk[5];
+    hankel_Y5(p, gx, gw, rho, hk);
+    out[5] = 2.0 * M_PI * hk[1];
+    if (rho == 0.0) {
+        for (int i = 3; i < 12; ++i)
+            if (i != 5) out[i] = 0.0;
+        return;
+    }
+    double cp = j1 / rho, sp = q / rho;
+    double c2 = cp * cp - sp * sp, s2 = 2.0 * cp * sp;
+    double c3 = cp * (4.0 * cp * cp - 3.0), s3 = sp * (3.0 - 4.0 * sp * sp);
+    double q1 = hk[0], r2 = hk[2], s1 = hk[3], s3v = hk[4];
+    out[3] = -2.0 * M_PI * I * cp * q1;
+    out[4] = -2.0 * M_PI * I * sp * q1;
+    out[6] = -2.0 * M_PI * c2 * r2;
+    out[7] = -2.0 * M_PI * s2 * r2;
+    out[8] = -2.0 * M_PI * I * cp * s1;
+    out[9] = -2.0 * M_PI * I * sp * s1;
+    out[10] = 2.0 * M_PI * I * c3 * s3v;
+    out[11] = 2.0 * M_PI * I * s3 * s3v;
+}
+
+/* sqrt(V) times the coefficients of h_1, h_2, h_11, h_12, h_22 (in that order)
+ * from the transforms above (x1^2/r^2 = (1 + cos 2th)/2, x2^2/r^2 = (1 - cos 2th)/2,
+ * x1 x2/r^2 = sin 2th/2, x1^3/r^2 = r (3 cos th + cos 3th)/4,
+ * x1^2 x2/r^2 = r (sin th + sin 3th)/4, x1 x2^2/r^2 = r (cos th - cos 3th)/4). */
+static void sqrtV_Hhat(const or_params *p, const double *gx, const double *gw, double k2, int j1, double q,
+                       cplx *H)
+{
+    cplx T[12];
+    singular_transforms(p, gx, gw, j1, q, T);
+    double al = p->alpha[0], kk = p->k * p->k, dk2 = p->k * p->k - k2 * k2;
+    cplx x1sq = 0.5 * (T[5] + T[6]), x2sq = 0.5 * (T[5] - T[6]), x1x2 = 0.5 * T[7];
+    cplx x1cub = 0.25 * (3.0 * T[8] + T[10]), x1sqx2 = 0.25 * (T[9] + T[11]), x1x2sq = 0.25 * (T[8] - T[10]);
+    H[0] = -(1.0 / (2.0 * M_PI)) * (-0.5 * kk * T[1] + T[3] - I * al * x1sq - 0.5 * al * al * x1cub);
+    H[1] = -(1.0 / (2.0 * M_PI)) * (-0.5 * kk * T[2] + T[4] - I * al * x1x2 - 0.5 * al * al * x1sqx2);
+    H[2] = (dk2 / (2.0 * M_PI)) * (0.5 * T[0] - 0.5 * I * al * T[1] + 0.5 * x1sq - I * al * 0.5 * x1cub);
+    H[3] = (dk2 / (2.0 * M_PI)) * (0.5 * x1x2 - 0.5 * I * al * x1sqx2);
+    H[4] = (dk2 / (2.0 * M_PI)) * (0.5 * T[0] - 0.5 * I * al * T[1] + 0.5 * x2sq - 0.5 * I * al * x1x2sq);
+}
+
+/* Diagnostic: the twelve transforms and the five sqrt(V) H-hat of one index. */
+void or_deriv2_parts(const or_params *p, double k2, int j1, int j2, double *out)
+{
+    double *gx = malloc(sizeof(double) * p->Q), *gw = malloc(sizeof(double) * p->Q);
+    or_gauss_legendre(p->Q, gx, gw);
+    double q = j2 * M_PI / p->ct;
+    singular_transforms(p, gx, gw, j1, q, (cplx *)out);
+    sqrtV_Hhat(p, gx, gw, k2, j1, q, (cplx *)out + 12);
+    free(gx);
+    free(gw);
+}
+
+/* Remainder coefficients of the five derivative fields, sqrt(V)-scaled, FFT
+ * order, layout [field][b2][b1], fields K_1 - h_1, K_2 - h_2, T_11 - h_11,
+ * T_12 - h_12, T_22 - h_22 (the last three only when k2 > 0).  Returns 0, or
+ * -1 on a Wood anomaly or resonance for k or k2. */
+int or_coef_deriv2(const or_params *p, double k2, double *out)
+{
+    double *gx = malloc(sizeof(double) * p->Q), *gw = malloc(sizeof(double) * p->Q);
+    or_gauss_legendre(p->Q, gx, gw);
+    or_params p2 = *p;
+    p2.k = k2;
+    int M1 = p->M[0], M2 = p->M[1], nf = k2 > 0.0 ? 5 : 2, bad = 0;
+    size_t NN = (size_t)M1 * M2;
+    cplx *C = (cplx *)out;
+#pragma omp parallel for collapse(2) schedule(dynamic, 16) reduction(| : bad)
+    for (int b2 = 0; b2 < M2; ++b2)
+        for (int b1 = 0; b1 < M1; ++b1) {
+            int j1 = freq_of(b1, M1), j2 = freq_of(b2, M2);
+            double a = p->alpha[0] + j1, q = j2 * M_PI / p->ct;
+            cplx beta = beta_of(p->k, a * a);
+            if (cabs(beta) == 0.0 || cabs(beta - q) == 0.0 || cabs(beta + q) == 0.0) bad = 1;
+            cplx K = sqrtV_Khat(p, gx, gw, a * a, q), H[5];
+            sqrtV_Hhat(p, gx, gw, k2 > 0.0 ? k2 : p->k, j1, q, H);
+            size_t i = (size_t)b2 * M1 + b1;
+            C[i] = I * a * K - H[0];
+            C[NN + i] = I * q * K - H[1];
+            if (nf == 5) {
+                cplx beta2 = beta_of(k2, a * a);
+                if (cabs(beta2) == 0.0 || cabs(beta2 - q) == 0.0 || cabs(beta2 + q) == 0.0) bad = 1;
+                cplx dK = K - sqrtV_Khat(&p2, gx, gw, a * a, q);
+                C[2 * NN + i] = -a * a * dK - H[2];
+                C[3 * NN + i] = -a * q * dK - H[3];
+                C[4 * NN + i] = -q * q * dK - H[4];
+            }
+        }
+    free(gx);
+    free(gw);
+    return bad ? -1 : 0;
+}
+
+/* The singular parts at (x1, x2) = (t, x2) in the cell, r < 2 eps (zero beyond):
+ * out = {h_1, h_2, h_11, h_12, h_22}. */
+static void deriv2_singular(const or_params *p, double k2, double x1, double x2, cplx *h)
+{
+    double r2 = x1 * x1 + x2 * x2, r = sqrt(r2);
+    for (int e = 0; e < 5; ++e) h[e] = 0.0;
+    if (r >= 2.0 * p->eps) return;
+    double Y = or_yps(r, p->eps, 0), lr = log(r), al = p->alpha[0];
+    double kk = p->k * p->k, dk2 = kk - k2 * k2;
+    h[0] = -(1.0 / (2.0 * M_PI)) * (-0.5 * kk * x1 * lr + x1 / r2 - I * al * x1 * x1 / r2 - 0.5 * al * al * x1 * x1 * x1 / r2) * Y;
+    h[1] = -(1.0 / (2.0 * M_PI)) * (-0.5 * kk * x2 * lr + x2 / r2 - I * al * x1 * x2 / r2 - 0.5 * al * al * x1 * x1 * x2 / r2) * Y;
+    h[2] = (dk2 / (2.0 * M_PI)) * (0.5 * lr - 0.5 * I * al * x1 * lr + x1 * x1 / (2.0 * r2) - I * al * x1 * x1 * x1 / (2.0 * r2)) * Y;
+    h[3] = (dk2 / (2.0 * M_PI)) * (x1 * x2 / (2.0 * r2) - 0.5 * I * al * x1 * x1 * x2 / r2) * Y;
+    h[4] = (dk2 / (2.0 * M_PI)) * (0.5 * lr - 0.5 * I * al * x1 * lr + x2 * x2 / (2.0 * r2) - 0.5 * I * al * x1 * x2 * x2 / r2) * Y;
+}
+
+/* The singular parts at n points (x1, x2) of the cell, out = n x {h_1, h_2,
+ * h_11, h_12, h_22} (test hook). */
+void or_deriv2_singular_at(const or_params *p, double k2, const double *x, long n, double *out)
+{
+    cplx *o = (cplx *)out;
+    for (long i = 0; i < n; ++i) deriv2_singular(p, k2, x[2 * i], x[2 * i + 1], o + 5 * i);
+}
+
+/* Term-by-term derivatives of (ei) (exact reference and far branch):
+ *   dG/dx1 = (i/4pi) sum (i alpha_n/beta_n) E_n,  dG/dx2 = (i/4pi) sum i sgn(x2) E_n,
+ *   d11 G = (i/4pi) sum (-alpha_n^2/beta_n) E_n, d12 G = (i/4pi) sum (-alpha_n sgn) E_n,
+ *   d22 G = (i/4pi) sum (-beta_n) E_n,   E_n = e^{i alpha_n x1 + i beta_n |x2|};
+ * which 0: {dG/dx1, dG/dx2};  which 1: {T_11, T_12, T_22} (k minus k2).
+ * Truncated at |alpha_n|^2 <= max(k, k2)^2 + (T/|x2|)^2. */
+static void series_deriv2_point(const or_params *p, double k2, const double *x, int which, cplx *out)
+{
+    double t, m;
+    reduce_period(x[0], &t, &m);
+    double z = fabs(x[1]), sg = x[1] >= 0.0 ? 1.0 : -1.0;
+    double kmax = (which == 1 && k2 > p->k) ? k2 : p->k;
+    double T = log(1.0 / p->tau) + 3.0, R2 = kmax * kmax + (T / z) * (T / z), R = sqrt(R2);
+    long nlo = (long)floor(-p->alpha[0] - R) - 1, nhi = (long)ceil(-p->alpha[0] + R) + 1;
+    cplx s[3] = {0.0, 0.0, 0.0};
+    for (long n = nlo; n <= nhi; ++n) {
+        double a = p->alpha[0] + n;
+        if (a * a > R2) continue;
+        cplx b1 = beta_of(p->k, a * a), E1 = cexp(I * a * t + I * b1 * z);
+        if (which == 0) {
+            s[0] += I * a / b1 * E1;
+            s[1] += I * sg * E1;
+        } else {
+            cplx b2 = beta_of(k2, a * a), E2 = cexp(I * a * t + I * b2 * z);
+            s[0] += -a * a * (E1 / b1 - E2 / b2);
+            s[1] += -a * sg * (E1 - E2);
+            s[2] += -(b1 * E1 - b2 * E2);
+        }
+    }
+    double ph = p->alpha[0] * m;
+    ph -= round(ph);
+    cplx pre = cexp(2.0 * M_PI * I * ph) * (I / (4.0 * M_PI));
+    for (int e = 0; e < (which == 0 ? 2 : 3); ++e) out[e] = pre * s[e];
+}
+
+void or_series_deriv2(const or_params *p, double k2, const double *x, long n, int which, double *out)
+{
+    int ne = which == 0 ? 2 : 3;
+    cplx *o = (cplx *)out;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (long i = 0; i < n; ++i) series_deriv2_point(p, k2, x + 2 * i, which, o + (size_t)ne * i);
+}
+
+/* Algorithm 1's calculation step for the derivative fields: |x2| > c by the
+ * differentiated series; otherwise x1 = 2 pi m + t, the remainder grids
+ * (grid: the five (or two) fields of or_coef_deriv2 after or_grid, layout
+ * [field][l2][l1]) interpolated at (t, x2), the singular parts added back and
+ * the result lifted by e^{i alpha t} e^{i 2 pi alpha m}.
+ * which 0: {dG/dx1, dG/dx2};  which 1: {T_11, T_12, T_22}. */
+void or_eval_deriv2(const or_params *p, double k2, const double *grid, const double *x, long n, int which,
+                    double *out)
+{
+    int ne = which == 0 ? 2 : 3, f0 = which == 0 ? 0 : 2;
+    size_t NN = (size_t)p->M[0] * p->M[1];
+    const cplx *g = (const cplx *)grid;
+    cplx *o = (cplx *)out;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long i = 0; i < n; ++i) {
+        const double *xi = x + 2 * i;
+        cplx *oi = o + (size_t)ne * i;
+        if (fabs(xi[1]) > p->c) {
+            series_deriv2_point(p, k2, xi, which, oi);
+            continue;
+        }
+        double t, m;
+        reduce_period(xi[0], &t, &m);
+        double h[2] = {2.0 * M_PI / p->M[0], 2.0 * p->ct / p->M[1]};
+        double y0[2] = {-M_PI, -p->ct};
+        double u[2] = {t, xi[1]};
+        cplx hs[5];
+        deriv2_singular(p, k2, t, xi[1], hs);
+        double ph = p->alpha[0] * m;
+        ph -= round(ph);
+        cplx lift = cexp(I * p->alpha[0] * t) * cexp(2.0 * M_PI * I * ph);
+        for (int e = 0; e < ne; ++e) oi[e] = lift * (interp2(g + (size_t)(f0 + e) * NN, p->M, u, y0, h) + hs[f0 + e]);
     }
 }

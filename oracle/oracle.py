@@ -87,6 +87,13 @@ def lib():
         _lib.or_eval_far_grid.argtypes = [P, i, i, i, d, p, p, l, i, p]
         _lib.or_set_threads.restype = i
         _lib.or_set_threads.argtypes = [i]
+        _lib.or_bessel_j0123.argtypes = [d, p]
+        _lib.or_deriv2_singular_at.argtypes = [P, d, p, l, p]
+        _lib.or_deriv2_parts.argtypes = [P, d, i, i, p]
+        _lib.or_coef_deriv2.restype = i
+        _lib.or_coef_deriv2.argtypes = [P, d, p]
+        _lib.or_series_deriv2.argtypes = [P, d, p, l, i, p]
+        _lib.or_eval_deriv2.argtypes = [P, d, p, p, l, i, p]
     return _lib
 
 
@@ -266,4 +273,74 @@ def far_grid_evaluate(pb: Problem, fg: np.ndarray, Nz: int, zmax: float, x: np.n
     p = pb.cstruct()
     lib().or_eval_far_grid(ctypes.byref(p), int(fg.shape[3]), int(fg.shape[2]), int(Nz), float(zmax), _ptr(fg),
                            _ptr(x), x.shape[0], int(which), _ptr(out))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# 2D derivatives (Sec. 2.4): gradient (Sec. 2.4.1) and the differences of
+# second derivatives for two wave numbers (Sec. 2.4.2).
+# ---------------------------------------------------------------------------
+DERIV_GRAD, DERIV_HYPER = 0, 1
+DERIV_FIELDS = ("K1-h1", "K2-h2", "T11-h11", "T12-h12", "T22-h22")
+
+
+def bessel_j0123(z: float) -> np.ndarray:
+    """J_0 .. J_3 at z from one trapezoidal sum of Bessel's integral (the transforms' routine)."""
+    out = np.zeros(4)
+    lib().or_bessel_j0123(float(z), _ptr(out))
+    return out
+
+
+def deriv2_parts(pb: Problem, k2: float, j1: int, j2: int) -> tuple[np.ndarray, np.ndarray]:
+    """(twelve plane transforms of the singular functions, the five sqrt(V) H-hat) of index j."""
+    out = np.zeros(17, dtype=np.complex128)
+    p = pb.cstruct()
+    lib().or_deriv2_parts(ctypes.byref(p), float(k2), int(j1), int(j2), _ptr(out))
+    return out[:12], out[12:]
+
+
+def deriv2_singular_at(pb: Problem, k2: float, x: np.ndarray) -> np.ndarray:
+    """The singular parts h_1, h_2, h_11, h_12, h_22 at in-cell points x (n, 2)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros((x.shape[0], 5), dtype=np.complex128)
+    p = pb.cstruct()
+    lib().or_deriv2_singular_at(ctypes.byref(p), float(k2), _ptr(x), x.shape[0], _ptr(out))
+    return out
+
+
+def coef_deriv2(pb: Problem, k2: float = 0.0) -> np.ndarray:
+    """sqrt(V) coefficients of K1-h1, K2-h2 (and T11-h11, T12-h12, T22-h22 when k2 > 0),
+    FFT order, shape (nf, M2, M1)."""
+    nf = 5 if k2 > 0 else 2
+    out = np.zeros((nf,) + pb.shape, dtype=np.complex128)
+    p = pb.cstruct()
+    if lib().or_coef_deriv2(ctypes.byref(p), float(k2), _ptr(out)) != 0:
+        raise ValueError("Wood anomaly or resonance in the coefficient set")
+    return out
+
+
+def grid_deriv2(pb: Problem, k2: float = 0.0) -> np.ndarray:
+    """The derivative remainder fields at the nodes (naive inverse DFT per field)."""
+    C = coef_deriv2(pb, k2)
+    return np.stack([grid(pb, C[f:f + 1])[0] for f in range(C.shape[0])])
+
+
+def series_deriv2(pb: Problem, k2: float, x: np.ndarray, which: int) -> np.ndarray:
+    """Term-by-term derivatives of (ei): which 0 -> (dG/dx1, dG/dx2), 1 -> (T11, T12, T22)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros((x.shape[0], 2 if which == 0 else 3), dtype=np.complex128)
+    p = pb.cstruct()
+    lib().or_series_deriv2(ctypes.byref(p), float(k2), _ptr(x), x.shape[0], int(which), _ptr(out))
+    return out
+
+
+def evaluate_deriv2(pb: Problem, k2: float, g: np.ndarray, x: np.ndarray, which: int) -> np.ndarray:
+    """Algorithm 1's calculation step for the derivative fields at the points x (n, 2)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.complex128)
+    if which == 1 and g.shape[0] < 5:
+        raise ValueError("T fields need k2 > 0")
+    out = np.zeros((x.shape[0], 2 if which == 0 else 3), dtype=np.complex128)
+    p = pb.cstruct()
+    lib().or_eval_deriv2(ctypes.byref(p), float(k2), _ptr(g), _ptr(x), x.shape[0], int(which), _ptr(out))
     return out
