@@ -17,6 +17,7 @@ it.  L2 is flushed (256 MiB write) between timed steps.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -293,6 +294,16 @@ def run_reference(args):
     return 0
 
 
+def measured_peak(key: str, fallback: float) -> tuple[float, str]:
+    """A peak from MEASURED_PEAKS.json beside this file (the machine's measured HBM copy
+    rate and cuBLAS bf16 rates), else the stated fallback; returns (value, which)."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)[key]), "measured"
+    except (OSError, KeyError, ValueError):
+        return fallback, "fallback"
+
+
 def measure_peaks(dev):
     """FP64 and FP32 FMA rates of this GPU (gf_peak_probe, CUDA events, best of 3
     launches of about 40 ms each after one warm-up)."""
@@ -561,6 +572,30 @@ def run_batched(args, dev, flush):
                 times.append(e0.elapsed_time(e1))
     graph_launches = (gf.launch_count() - l0) / (args.warmup + args.steps)
     ms_b = float(np.mean(times))
+    # the synthesis alone (the three batched passes), against its algorithmic bytes:
+    # per pair the first pass writes the work planes W, the x2 pass reads and writes
+    # them, the x1 pass reads them and writes the padded gather grid G (W = G times
+    # M1 M2 / ((M1 + 3)(M2 + 3)), the planes being those G keeps)
+    syn = []
+    with torch.cuda.stream(s):
+        for i in range(args.warmup + args.steps):
+            flush.zero_()
+            s.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            batch.synthesize(stream=s)
+            e1.record(s)
+            s.synchronize()
+            if i >= args.warmup:
+                syn.append(e0.elapsed_time(e1))
+    ms_syn = float(np.mean(syn))
+    syn_bytes = 0.0
+    for i in range(npairs):
+        info = gf.PlanInfo()
+        gf.lib().gf_plan_get_info(batch.plan_handle(i), ctypes.byref(info))
+        G = float(info.grid_device_bytes)
+        syn_bytes += 4.0 * G * info.M[0] * info.M[1] / ((info.M[0] + 3) * (info.M[1] + 3)) + G
+    hbm, hbm_how = measured_peak("hbm_gbs", 6800.0)
     # plain path, pair after pair (one pass)
     ref = torch.empty_like(out)
     torch.cuda.synchronize()
@@ -582,7 +617,13 @@ def run_batched(args, dev, flush):
             "sequential_plain": {"value": total / t_seq, "s_per_sweep": t_seq,
                                  "how": "gf_plan + gf_eval_points pair after pair, wall clock"},
             "speedup_vs_sequential": (total / (ms_b * 1e-3)) / (total / t_seq),
-            "setup_s": t_setup, "max_err_vs_sequential_normwise": d}
+            "setup_s": t_setup, "max_err_vs_sequential_normwise": d,
+            "synthesis": {"ms": ms_syn, "bytes": syn_bytes, "achieved_gbs": syn_bytes / (ms_syn * 1e-3) / 1e9,
+                          "peak_gbs": hbm, "frac": syn_bytes / (ms_syn * 1e-3) / 1e9 / hbm,
+                          "note": f"the three batched synthesis passes timed alone (CUDA events, L2 flushed); bytes = "
+                                  f"4 W + G per pair (work planes written, read and written, read; gather grid "
+                                  f"written); peak = {hbm_how} HBM copy rate.  The first pass forms the "
+                                  f"coefficients (Gauss-Legendre sums): it is bound by arithmetic, not bytes"}}
 
 
 def run_surrogate(args, dev):
@@ -739,13 +780,14 @@ def run_surrogate(args, dev):
     mlp2.close()
     fwd_ms = float(np.mean(ft2))
     fwd_flops = 2.0 * (80 * 256 + 3 * 256 * 256 + 256 * 2) * (1 << 20)
+    bf16_peak, bf16_how = measured_peak("bf16_tflops", 1900.0)
     total = npairs * per
     return {"value": total / t_sur, "unit": "evals/s", "s_per_call": t_sur, "pairs": npairs,
             "gemm_bf16": {"shape": "M=2^20, N=256, K=256 (per-layer kernel, fp32 out)", "ms": gemm_ms,
                           "tflops": gemm_tf},
             "fused_forward": {"samples": 1 << 20, "ms": fwd_ms, "tflops": fwd_flops / (fwd_ms * 1e-3) / 1e12,
-                              "frac_of_bf16_peak": fwd_flops / (fwd_ms * 1e-3) / 1e12 / 1887.8,
-                              "peak": "1887.8 TFLOP/s bf16 (measured, burst)"},
+                              "frac_of_bf16_peak": fwd_flops / (fwd_ms * 1e-3) / 1e12 / bf16_peak,
+                              "peak": f"{bf16_peak} TFLOP/s bf16 ({bf16_how}, burst)"},
             "targets_per_pair": per, "targets": "near region |x3| <= c", "dtype": "bf16 weights, fp32 accumulation",
             "fallback_pairs": nfb, "wood_delta": 1e-2,
             "fft_path": {"value": total / t_fft, "s_per_call": t_fft, "setup_s": t_setup,
@@ -761,7 +803,9 @@ def run_surrogate(args, dev):
 
 def run_configs(args, dev, flush):
     """The other configurations, one plan + evaluation per step (device time):
-    2D G (k = 1.3, alpha = 0.2, 64 x 64, 1e4 targets, complex128) and the Maxwell
+    2D G (k = 1.3, alpha = 0.2, 64 x 64, 1e4 targets, complex128), the 2D
+    derivatives of Sec. 2.4 (gradient and second-derivative differences, 256 x 256)
+    and the Maxwell
     tensor (k = 2.5, alpha = (0.1, 0.3), 256 x 256 x 64, six entries, float bulk
     with double singular part; 1e6 targets, 10% clustered within 0.05 of lattice
     points; its error stated against the double-precision path on the GPU)."""
@@ -794,6 +838,32 @@ def run_configs(args, dev, flush):
                    "value": 1e4 / (ms * 1e-3), "unit": "evals/s", "ms_per_step": ms, "dtype": "f64",
                    "phases_ms": {"synthesis": float(np.mean([p[0] for p in ph])), "near": float(np.mean([p[2] for p in ph])),
                                  "far": float(np.mean([p[3] for p in ph]))}}
+    # 2D derivatives (Sec. 2.4): one derivative plan (L, K_1 - h_1, K_2 - h_2 and the
+    # three T_pq - h_pq fields for k2) and both outputs per step
+    nd = 100_000
+    xd = torch.from_numpy(W.targets_2d(nd, seed=1)).to(dev)
+    og, oh = (torch.empty((nd, 3), dtype=torch.complex128, device=dev) for _ in range(2))
+    ts, ph = [], []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        p = gf.Plan(2, 1.3, (0.2,), (256, 256), kind=gf.GF_DERIV2D, k2=2.1, c_tilde=1.4)
+        p.eval_points_into(xd, og, gf.GF_OUT_GRAD)
+        p.eval_points_into(xd, oh, gf.GF_OUT_HESSDIFF)
+        e1.record()
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            ts.append(e0.elapsed_time(e1))
+            ph.append(p.phase_ms())
+        p.close()
+    msd = float(np.mean(ts))
+    res["2d_deriv"] = {"workload": "2D derivatives (Sec. 2.4): G, dG/dx1, dG/dx2 and T11, T12, T22 for k=1.3, "
+                                   "k2=2.1, alpha=0.2, c~=1.4, grid 256x256 (6 fields), 1e5 uniform targets",
+                       "value": nd / (msd * 1e-3), "unit": "targets/s (6 entries each: both outputs)",
+                       "ms_per_step": msd, "dtype": "f64",
+                       "synthesis_ms": float(np.mean([q[0] for q in ph]))}
     x3 = torch.from_numpy(W.targets_3d_clustered(1_000_000, seed=0)).to(dev)
     o32 = torch.empty((1_000_000, 6), dtype=torch.complex64, device=dev)
     ms32, ph32 = timed(lambda: gf.Plan(3, 2.5, (0.1, 0.3), (256, 256, 64), precision=gf.GF_FP32_SPLIT,

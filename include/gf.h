@@ -54,16 +54,19 @@ typedef enum {
 } gf_status;
 
 enum { GF_FP64 = 0, GF_FP32_SPLIT = 1 };          /* gf_trunc_t.precision */
-enum { GF_HELMHOLTZ = 0, GF_MAXWELL = 1 };        /* gf_trunc_t.kind */
+enum { GF_HELMHOLTZ = 0, GF_MAXWELL = 1, GF_DERIV2D = 2 };  /* gf_trunc_t.kind */
 enum { GF_PERTURB_CTILDE = 0, GF_FAIL = 1 };      /* gf_trunc_t.resonance_policy */
 enum {                                            /* gf_eval_points `which` */
     GF_OUT_G = 0,         /* 2D plans: G, 1 entry */
     GF_OUT_GD = 1,        /* 3D plans: G_d, 1 entry */
     GF_OUT_MAXWELL6 = 2,  /* Maxwell plans: GG_xx, GG_yy, GG_zz, GG_xy, GG_xz, GG_yz */
     GF_OUT_MAXWELL7 = 3,  /* Maxwell plans: the six entries above, then G_d */
-    GF_OUT_LD = 4         /* 3D Helmholtz plans: the interpolated remainder L_dN at the in-cell
+    GF_OUT_LD = 4,        /* 3D Helmholtz plans: the interpolated remainder L_dN at the in-cell
                              point (t1, t2, x3), no singular part, no phase (Alg. 2 step 2d);
                              targets with |x3| > c give NaN */
+    GF_OUT_GRAD = 5,      /* GF_DERIV2D plans: G, dG/dx1, dG/dx2 (Sec. 2.4.1), 3 entries */
+    GF_OUT_HESSDIFF = 6   /* GF_DERIV2D plans with k2 > 0: T_11, T_12, T_22, the differences
+                             d_p d_q G_k - d_p d_q G_k2 (Sec. 2.4.2), 3 entries */
 };
 
 /* Method parameters.  Defaults (gf_trunc_default): c = 0.6, c~ = 1 (Sec. 5),
@@ -101,6 +104,23 @@ enum {                                            /* gf_eval_points `which` */
  *              at O(h^4): about 1.4e-5 (M = 128), 7e-7 (256), 5e-8 (512) relative
  *              to max|G| at c = 0.6; meant for GF_FP32_SPLIT plans.
  *   far_grid_nz  intervals in z (0: 16); far_grid_zmax  end of the slab (<= 0: c~)
+ *   kind = GF_DERIV2D (2D only): the plan also serves the derivatives of Sec. 2.4.
+ *              It stores, beside L of Eq. (fcl-coef), the remainder fields K_1 - h_1
+ *              and K_2 - h_2 (Sec. 2.4.1: K_1 = e^{-i alpha x1} dG/dx1, K_2 =
+ *              e^{-i alpha x1} dG/dx2, coefficients i (alpha + j1) K-hat and
+ *              i (j2 pi/c~) K-hat less those of the singular parts h_1, h_2), and
+ *              with k2 > 0 the fields T_pq - h_pq of the differences of second
+ *              derivatives for wave numbers k and k2 (Sec. 2.4.2, coefficients
+ *              -(alpha+j1)^2, -(alpha+j1)(j2 pi/c~), -(j2 pi/c~)^2 times K-hat(k) -
+ *              K-hat(k2), less h_11, h_12, h_22's).  The singular parts are the
+ *              paper's with two readings: x2 ln|x| (not x1 ln|x|) in h_2, and the sign
+ *              +(k^2 - k2^2)/2pi of h_11, h_12, h_22.  The x2-derivative fields carry
+ *              the cutoff X's transition multiplied by j2 or j2^2 and converge once
+ *              the grid resolves it: a wider window c~ - c (c~ = 1.4 at c = 0.6, say)
+ *              or more points along x2 (errors against the exact series, c~ = 1.4,
+ *              M = 128^2: dG/dx1 2.7e-4, dG/dx2 6.4e-5, T 3.5e-4 .. 4.3e-3 of max)
+ *   k2         second wave number of GF_DERIV2D plans (0: the gradient only); must
+ *              be 0 for the other kinds
  */
 typedef struct {
     double c, c_tilde, eps;
@@ -111,6 +131,7 @@ typedef struct {
     int resonance_policy;
     int far_grid_M, far_grid_nz;
     double far_grid_zmax;
+    double k2;
 } gf_trunc_t;
 
 /* Fill *t with the defaults listed above.  Returns GF_ERR_ARG if t is NULL. */
@@ -142,7 +163,9 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M,
  * node order [field][l3][l2][l1] (l_i = 0..M_i-1 is the node x_i = l_i h_i
  * modulo the period, h = 2 pi / M in-plane and 2 c~ / M_last in x_last).  One
  * field for Helmholtz plans; for Maxwell plans seven: the six combined fields
- * (delta_pq - c^p c^q / k^2) L_d in the order xx, yy, zz, xy, xz, yz, then L_d.
+ * (delta_pq - c^p c^q / k^2) L_d in the order xx, yy, zz, xy, xz, yz, then L_d;
+ * for GF_DERIV2D plans three (L, K_1 - h_1, K_2 - h_2) or, with k2 > 0, six
+ * (then T_11 - h_11, T_12 - h_12, T_22 - h_22).
  * out_bytes must be >= gf_grid_bytes(plan).  Errors: GF_ERR_ARG, GF_ERR_CUDA. */
 gf_status gf_eval_grid(gf_plan_t plan, void *dev_out, size_t out_bytes, void *cuda_stream);
 
@@ -151,7 +174,8 @@ size_t gf_grid_bytes(gf_plan_t plan);
 
 /* Evaluate at n targets (Algorithms 1-3, step 2 "Calculation").
  *   dev_xyz   n * dim doubles, row-major [n][dim], device memory
- *   which     GF_OUT_G (2D), GF_OUT_GD (3D Helmholtz), GF_OUT_MAXWELL6/7 (Maxwell)
+ *   which     GF_OUT_G (2D), GF_OUT_GD (3D Helmholtz), GF_OUT_MAXWELL6/7 (Maxwell),
+ *             GF_OUT_GRAD and GF_OUT_HESSDIFF (GF_DERIV2D plans; the latter with k2 > 0)
  *   dev_out   n * entries complex values, [n][entries], device memory
  * The plan is not modified by an evaluation: each call takes its scratch (the
  * far- and near-branch target lists, 12 bytes per target plus 4 KiB) from the
@@ -220,7 +244,8 @@ typedef struct gf_batch_s *gf_batch_t;
  *   npairs  number of pairs, >= 1
  *   k       [npairs] wave numbers;  alpha [npairs][2];  M [npairs][3]  (host memory)
  *   trunc   shared parameters (precision, kind, ...), NULL for the defaults
- * Errors: as gf_plan for any pair (the message names the pair), GF_ERR_NOMEM. */
+ * Errors: as gf_plan for any pair (the message names the pair), GF_ERR_NOMEM,
+ * GF_ERR_UNSUPPORTED for kind GF_DERIV2D (derivative plans are single plans). */
 gf_status gf_plan_batch(int npairs, const double *k, const double *alpha, const int *M,
                         const gf_trunc_t *trunc, void *cuda_stream, gf_batch_t *out);
 
@@ -356,6 +381,7 @@ typedef struct {
     int far_grid_M, far_grid_nz;         /* far-region grid (0: none) */
     double far_grid_zmax;
     size_t far_grid_device_bytes;
+    double k2;                           /* second wave number of GF_DERIV2D plans (0: none) */
 } gf_plan_info_t;
 gf_status gf_plan_get_info(gf_plan_t plan, gf_plan_info_t *info);
 

@@ -119,7 +119,7 @@ static gf_status batch_eval_setup(gf_batch_t b, const double *x, const int64_t *
         b->cap = total;
     }
     const size_t elem = b->precision == GF_FP64 ? 16 : 8;
-    const int ne = which == GF_OUT_MAXWELL6 ? 6 : which == GF_OUT_MAXWELL7 ? 7 : 1;
+    const int ne = gf_out_entries(which);
     std::vector<EvalArgs> ea(b->np);
     std::vector<int> pre(b->np + 1, 0);
     for (int p = 0; p < b->np; ++p) {
@@ -182,6 +182,8 @@ gf_status gf_plan_batch(int npairs, const double *k, const double *alpha, const 
     gf_trunc_t tr;
     gf_trunc_default(&tr);
     if (trunc) tr = *trunc;
+    if (tr.kind == GF_DERIV2D)
+        return err(GF_ERR_UNSUPPORTED, "gf_plan_batch: derivative plans (GF_DERIV2D) are not batched; use gf_plan");
     gf_batch_s *b = new gf_batch_s();
     b->np = npairs;
     b->precision = tr.precision;

@@ -124,7 +124,7 @@ __device__ __forceinline__ double2 ld_grid(const float2 *p)
 }
 
 // entries written per target
-__host__ __device__ __forceinline__ int n_entries(int which) { return which == GF_OUT_MAXWELL6 ? 6 : which == GF_OUT_MAXWELL7 ? 7 : 1; }
+__host__ __device__ __forceinline__ int n_entries(int which) { return gf_out_entries(which); }
 
 // Warp-aggregated append of far targets to the scratch list.
 __device__ __forceinline__ void push_far(bool isfar, int i, int *list, int *count)
@@ -570,14 +570,27 @@ __global__ void __launch_bounds__(256) near3d_list_batch(const EvalArgs *args, i
 // ---------------------------------------------------------------------------
 // 2D near kernel (Algorithm 1): K = L + f1 - i alpha f2, G = e^{i alpha x1} K,
 // f1 = -(1/2pi) ln r Y_eps(r), f2 = t f1 at the reduced point (t, x2).
+// NF fields per node: 1 (L), 3 (derivative plans: L, K_1 - h_1, K_2 - h_2) or
+// 6 (and T_11 - h_11, T_12 - h_12, T_22 - h_22).  Outputs: G; GF_OUT_GRAD = G,
+// dG/dx1, dG/dx2 (Sec. 2.4.1: K_i = (K_i - h_i)_N + h_i, dG/dx_i = e^{i alpha x1}
+// K_i); GF_OUT_HESSDIFF = T_11, T_12, T_22 (Sec. 2.4.2, the same with h_pq), the
+// singular parts
+//   h_1  = -(1/2pi)[-(k^2/2) x1 ln r + x1/r^2 - i alpha x1^2/r^2 - (alpha^2/2) x1^3/r^2] Y
+//   h_2  = -(1/2pi)[-(k^2/2) x2 ln r + x2/r^2 - i alpha x1 x2/r^2 - (alpha^2/2) x1^2 x2/r^2] Y
+//   h_11 = (dk2/2pi)[ln r/2 - (i alpha/2) x1 ln r + x1^2/(2r^2) - i alpha x1^3/(2r^2)] Y
+//   h_12 = (dk2/2pi)[x1 x2/(2r^2) - (i alpha/2) x1^2 x2/r^2] Y
+//   h_22 = (dk2/2pi)[ln r/2 - (i alpha/2) x1 ln r + x2^2/(2r^2) - (i alpha/2) x1 x2^2/r^2] Y
+// (dk2 = k^2 - k2^2) at (x1, x2) = (t, x2), in double.
 // ---------------------------------------------------------------------------
-template <typename R>
+template <typename R, int NF>
 __global__ void __launch_bounds__(256) near2d(EvalArgs a)
 {
     typedef typename cplx_t<R>::T C;
     const C *G = reinterpret_cast<const C *>(a.grid);
     C *out = reinterpret_cast<C *>(a.out);
     const double ih1 = 1.0 / a.h1, ih2 = 1.0 / a.h2;
+    const int ne = n_entries(a.which);
+    const int f0 = a.which == GF_OUT_HESSDIFF ? 3 : 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < a.n; base += stride) {
         const int64_t i = base + threadIdx.x;
@@ -592,7 +605,7 @@ __global__ void __launch_bounds__(256) near2d(EvalArgs a)
         push_far(isfar, (int)i, a.far_idx, a.far_count);
         if (!valid || isfar) continue;
         if (!finite) {
-            out[i] = nan_c<R>();
+            for (int e = 0; e < ne; ++e) out[i * ne + e] = nan_c<R>();
             continue;
         }
         double t, m;
@@ -603,33 +616,55 @@ __global__ void __launch_bounds__(256) near2d(EvalArgs a)
         double w1[4], w2[4];
         lagrange4(f1, w1);
         lagrange4(f2, w2);
-        double Lr = 0, Li = 0;
+        double acc[3][2] = {{0, 0}, {0, 0}, {0, 0}};
 #pragma unroll
         for (int d2 = 0; d2 < 4; ++d2) {
-            const C *row = G + (size_t)(i2 + d2) * a.P1 + i1;
-            double sr = 0, si = 0;
+            const C *row = G + ((size_t)(i2 + d2) * a.P1 + i1) * NF + f0;
 #pragma unroll
-            for (int d1 = 0; d1 < 4; ++d1) {
-                double2 g = ld_grid(row + d1);
-                sr = fma(w1[d1], g.x, sr);
-                si = fma(w1[d1], g.y, si);
+            for (int e = 0; e < (NF == 1 ? 1 : 3); ++e) {
+                if (e >= ne) break;
+                double sr = 0, si = 0;
+#pragma unroll
+                for (int d1 = 0; d1 < 4; ++d1) {
+                    double2 g = ld_grid(row + d1 * NF + e);
+                    sr = fma(w1[d1], g.x, sr);
+                    si = fma(w1[d1], g.y, si);
+                }
+                acc[e][0] = fma(w2[d2], sr, acc[e][0]);
+                acc[e][1] = fma(w2[d2], si, acc[e][1]);
             }
-            Lr = fma(w2[d2], sr, Lr);
-            Li = fma(w2[d2], si, Li);
         }
-        double2 K = make_double2(Lr, Li);
         double r = sqrt(t * t + x2 * x2);
         if (r < 2.0 * a.eps) {
-            double Y = 1.0 - smooth8((r - a.eps) / a.eps);
-            double fa = -log(r) * Y * (0.5 / GF_PI);
-            double fb = t * fa;
-            K.x += fa;                 // + f1
-            K.y -= a.a1 * fb;          // - i alpha f2
+            const double Y = 1.0 - smooth8((r - a.eps) / a.eps), lr = log(r), ir2 = 1.0 / (r * r);
+            const double al = a.a1, kk = a.k * a.k, i2p = 0.5 / GF_PI;
+            if (a.which != GF_OUT_HESSDIFF) {
+                // K = L + f1 - i alpha f2
+                const double fa = -lr * Y * i2p;
+                acc[0][0] += fa;
+                acc[0][1] -= al * t * fa;
+            }
+            if (a.which == GF_OUT_GRAD) {
+                acc[1][0] += -i2p * (-0.5 * kk * t * lr + t * ir2 - 0.5 * al * al * t * t * t * ir2) * Y;
+                acc[1][1] += i2p * al * t * t * ir2 * Y;
+                acc[2][0] += -i2p * (-0.5 * kk * x2 * lr + x2 * ir2 - 0.5 * al * al * t * t * x2 * ir2) * Y;
+                acc[2][1] += i2p * al * t * x2 * ir2 * Y;
+            } else if (a.which == GF_OUT_HESSDIFF) {
+                const double s = (kk - a.k2 * a.k2) * i2p * Y;
+                acc[0][0] += s * (0.5 * lr + 0.5 * t * t * ir2);
+                acc[0][1] += s * (-0.5 * al * t * lr - 0.5 * al * t * t * t * ir2);
+                acc[1][0] += s * (0.5 * t * x2 * ir2);
+                acc[1][1] += s * (-0.5 * al * t * t * x2 * ir2);
+                acc[2][0] += s * (0.5 * lr + 0.5 * x2 * x2 * ir2);
+                acc[2][1] += s * (-0.5 * al * t * lr - 0.5 * al * t * x2 * x2 * ir2);
+            }
         }
-        double2 lat = lattice_phase(a.a1, m, 0.0, 0.0);
         double sa, ca;
         sincos(a.a1 * t, &sa, &ca);
-        store_out(out + i, cmul(cmul(make_double2(ca, sa), lat), K));
+        const double2 lift = cmul(make_double2(ca, sa), lattice_phase(a.a1, m, 0.0, 0.0));
+#pragma unroll
+        for (int e = 0; e < 3; ++e)
+            if (e < ne) store_out(out + i * ne + e, cmul(lift, make_double2(acc[e][0], acc[e][1])));
     }
 }
 
@@ -2085,13 +2120,37 @@ __global__ void far3d_batch(const EvalArgs *args, int np)
 // takes n = na + l, na + l + 32, ... (phase e^{i alpha_n t} from a sincos and the
 // step e^{i 32 t}), and the lanes' sums are added by shuffles.
 // ---------------------------------------------------------------------------
+// Term n of (ei) without its factor i/(4pi): beta_n and E_n / beta_n,
+// E_n = e^{i alpha_n t + i beta_n |x2|} (p = e^{i alpha_n t} given).
+__device__ __forceinline__ void ei_term(double kk, double aa, double z, double2 p, double2 &beta, double2 &E)
+{
+    if (aa <= kk) {
+        const double b = sqrt((kk - aa) * (kk + aa));
+        double sz, cz;
+        sincos(b * z, &sz, &cz);
+        beta = make_double2(b, 0.0);
+        E = cmul(make_double2(cz, sz), p);
+    } else {
+        const double b = sqrt((aa - kk) * (aa + kk));
+        beta = make_double2(0.0, b);
+        E = cscale(p, exp(-b * z));
+    }
+}
+
+// 2D far branch (|x2| > c): (ei) summed by one warp per target, lanes over n.
+// GF_OUT_GRAD adds the term-by-term derivatives (i alpha_n/beta_n) E_n and
+// i sgn(x2) E_n; GF_OUT_HESSDIFF sums, over the indices of both wave numbers'
+// truncation sets, -alpha_n^2 (E_n/beta_n - E'_n/beta'_n), -alpha_n sgn (E_n - E'_n)
+// and -(beta_n E_n - beta'_n E'_n) (primes: k2).
 template <typename R>
 __global__ void __launch_bounds__(128) far2d(EvalArgs a)
 {
     typedef typename cplx_t<R>::T C;
     C *out = reinterpret_cast<C *>(a.out);
     const int count = *a.far_count;
-    const double k2 = a.k * a.k;
+    const int ne = n_entries(a.which);
+    const bool hess = a.which == GF_OUT_HESSDIFF, grad = a.which == GF_OUT_GRAD;
+    const double kmax = (hess && a.k2 > a.k) ? a.k2 : a.k;
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -2100,42 +2159,55 @@ __global__ void __launch_bounds__(128) far2d(EvalArgs a)
         const double x1 = a.x[2 * (size_t)idx], x2 = a.x[2 * (size_t)idx + 1];
         double t, m;
         reduce_period(x1, t, m);
-        const double z = fabs(x2);
+        const double z = fabs(x2), sg = x2 >= 0.0 ? 1.0 : -1.0;
         const double Tz = a.T * (1.0 / z);
-        const double R2 = k2 + Tz * Tz, Rr = sqrt(R2);
+        const double R2 = kmax * kmax + Tz * Tz, Rr = sqrt(R2);
         const int na = (int)floor(-a.a1 - Rr) - 1, nb = (int)ceil(-a.a1 + Rr) + 1;
         double sp, cp, s32, c32;
         sincos((a.a1 + (na + lane)) * t, &sp, &cp);
         sincos(32.0 * t, &s32, &c32);
         double2 p = make_double2(cp, sp);
         const double2 step = make_double2(c32, s32);
-        double sr = 0, si = 0;
+        double acc[3][2] = {{0, 0}, {0, 0}, {0, 0}};
         for (int n = na + lane; n <= nb; n += 32, p = cmul(p, step)) {
             const double c1 = a.a1 + n;
             if (c1 * c1 > R2) continue;
             const double aa = fabs(c1);
-            double2 term;
-            if (aa <= a.k) {
-                const double b = sqrt((a.k - aa) * (a.k + aa));
-                double sz, cz;
-                sincos(b * z, &sz, &cz);
-                term = cscale(cmul(make_double2(cz, sz), p), 1.0 / b);
+            double2 beta, E;
+            ei_term(a.k, aa, z, p, beta, E);
+            const double2 term = cdiv(E, beta);
+            if (!hess) {
+                acc[0][0] += term.x;
+                acc[0][1] += term.y;
+                if (grad) {
+                    acc[1][0] -= c1 * term.y;  // i c1 term
+                    acc[1][1] += c1 * term.x;
+                    acc[2][0] -= sg * E.y;     // i sgn E
+                    acc[2][1] += sg * E.x;
+                }
             } else {
-                const double b = sqrt((aa - a.k) * (aa + a.k));
-                const double e = exp(-b * z) / b;
-                term = cmul(make_double2(0.0, -e), p);  // (1/(i b)) e^{-b z} p
+                double2 beta2, E2;
+                ei_term(a.k2, aa, z, p, beta2, E2);
+                const double2 d0 = csub(term, cdiv(E2, beta2)), d1 = csub(E, E2);
+                const double2 d2 = csub(cmul(beta, E), cmul(beta2, E2));
+                acc[0][0] -= c1 * c1 * d0.x;
+                acc[0][1] -= c1 * c1 * d0.y;
+                acc[1][0] -= c1 * sg * d1.x;
+                acc[1][1] -= c1 * sg * d1.y;
+                acc[2][0] -= d2.x;
+                acc[2][1] -= d2.y;
             }
-            sr += term.x;
-            si += term.y;
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            sr += __shfl_xor_sync(0xffffffffu, sr, o);
-            si += __shfl_xor_sync(0xffffffffu, si, o);
-        }
+        for (int e = 0; e < 3; ++e)
+            for (int o = 16; o > 0; o >>= 1) {
+                acc[e][0] += __shfl_xor_sync(0xffffffffu, acc[e][0], o);
+                acc[e][1] += __shfl_xor_sync(0xffffffffu, acc[e][1], o);
+            }
         if (lane == 0) {
             const double2 lat = lattice_phase(a.a1, m, 0.0, 0.0);
             const double2 pre = cmul(lat, make_double2(0.0, 0.25 / GF_PI));
-            store_out(out + idx, cmul(pre, make_double2(sr, si)));
+            for (int e = 0; e < ne; ++e)
+                store_out(out + (size_t)idx * ne + e, cmul(pre, make_double2(acc[e][0], acc[e][1])));
         }
     }
 }
@@ -2221,7 +2293,12 @@ cudaError_t launch_eval_t(const EvalArgs &a, cudaStream_t s, cudaEvent_t ev_mid,
     if (blocks > (int64_t)nsm * 16) blocks = (int64_t)nsm * 16;
     if (blocks < 1) blocks = 1;
     if (a.dim == 2) {
-        near2d<R><<<(int)blocks, 256, 0, s>>>(a);
+        if (a.nf == 1)
+            near2d<R, 1><<<(int)blocks, 256, 0, s>>>(a);
+        else if (a.nf == 3)
+            near2d<R, 3><<<(int)blocks, 256, 0, s>>>(a);
+        else
+            near2d<R, 6><<<(int)blocks, 256, 0, s>>>(a);
         if (ev_mid) cudaEventRecord(ev_mid, s);
         far2d<R><<<resident_grid<far2d<R>>(nsm), 128, 0, s>>>(a);
     } else if (a.nf == 1) {

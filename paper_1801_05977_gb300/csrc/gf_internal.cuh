@@ -130,7 +130,23 @@ struct SynthArgs {
     // device error word of the plan: set to 1 when a bounded wait for staged
     // copies ran out (gf_plan_status reports it)
     int *err;
+    // fields odd in the last-axis index (bit e: field e; their coefficients are
+    // mirrored with a sign): the Maxwell xz, yz fields, the 2D K_2 and T_12 fields
+    int oddmask;
+    // 2D derivative plans (Sec. 2.4): deriv = 1; fields L, K_1 - h_1, K_2 - h_2,
+    // and with k2 > 0 T_11 - h_11, T_12 - h_12, T_22 - h_22.  dcheb: three more
+    // Chebyshev tables [3][hnpan][hdeg + 1] on the panels of hcheb, of the Hankel
+    // transforms of the cutoff (Q1, R0), (R2, S1), (S3, 0) (see synth.cu)
+    int deriv;
+    double k2;
+    const double2 *dcheb;
 };
+
+// Complex entries per target of an output selection (gf_eval_points `which`).
+__host__ __device__ inline int gf_out_entries(int which)
+{
+    return which == GF_OUT_MAXWELL6 ? 6 : which == GF_OUT_MAXWELL7 ? 7 : (which == GF_OUT_GRAD || which == GF_OUT_HESSDIFF) ? 3 : 1;
+}
 
 // Far-series table entry for one in-plane index n: b = |beta_n|, ln b and 1/b
 // for evanescent n (beta_n = i b); zeros for propagating n (|alpha_n| <= k).
@@ -161,6 +177,7 @@ struct EvalArgs {
     int nf;             // stored fields per node
     int which;
     double k, a1, a2;
+    double k2;          // 2D derivative plans: the second wave number of the T fields (0: none)
     double c, ct, eps;
     double h1, h2, h3;  // node spacings
     double T;           // ln(1/series_tol) + 3
@@ -236,6 +253,9 @@ void gf_synth_config(SynthArgs &a, int precision, int tj_max, size_t smem[3]);
 size_t gf_synth_smem_need(const SynthArgs &a, int precision);
 cudaError_t gf_launch_cheb_table(int dim, const double *rr, const double2 *B, const double *P0, const double *P1, int Q,
                                  int npan, int deg, double w, double2 *out, float2 *outf, cudaStream_t s);
+// 2D derivative plans: the cutoff's Hankel transform tables (see SynthArgs::dcheb)
+cudaError_t gf_launch_cheb_deriv(const double *rr, const double *wy, int Q2, int npan, int deg, double w, double2 *out,
+                                 cudaStream_t s);
 cudaError_t gf_launch_synth_batch(const SynthBatch &b, int precision, cudaStream_t s);
 cudaError_t gf_launch_eval_batch(const EvalBatch &b, int precision, cudaStream_t s);
 cudaError_t gf_launch_series_tables(const EvalArgs &a, int precision, double2 *exptab, PropEntry *prop, int *nprop,

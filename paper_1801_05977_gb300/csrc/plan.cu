@@ -182,6 +182,7 @@ gf_status gf_trunc_default(gf_trunc_t *t)
     t->far_grid_M = 0;
     t->far_grid_nz = 0;
     t->far_grid_zmax = 0.0;
+    t->k2 = 0.0;
     return GF_OK;
 }
 
@@ -209,6 +210,18 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
         return fail(GF_ERR_ARG, "gf_plan: need 0 < c < c_tilde");
     if (!(tr.eps > 0.0) || !(2.0 * tr.eps < tr.c_tilde) || !(2.0 * tr.eps < GF_PI))
         return fail(GF_ERR_ARG, "gf_plan: need 0 < 2 eps < min(c_tilde, pi)");
+    if (tr.kind != GF_HELMHOLTZ && tr.kind != GF_MAXWELL && tr.kind != GF_DERIV2D) return fail(GF_ERR_ARG, "gf_plan: bad kind");
+    if (tr.kind == GF_MAXWELL && dim != 3) return fail(GF_ERR_ARG, "gf_plan: the Maxwell tensor needs dim = 3");
+    if (tr.kind == GF_DERIV2D && dim != 2)
+        return fail(GF_ERR_ARG, "gf_plan: the derivative fields (GF_DERIV2D) are for 2D plans");
+    if (tr.kind == GF_DERIV2D) {
+        if (!(tr.k2 >= 0.0) || !isfinite(tr.k2) || tr.k2 == k)
+            return fail(GF_ERR_ARG, "gf_plan: k2 must be 0 (gradient only) or finite, > 0 and different from k");
+    } else if (tr.k2 != 0.0) {
+        return fail(GF_ERR_ARG, "gf_plan: k2 is for GF_DERIV2D plans");
+    }
+    // the wave numbers whose coefficients the plan forms
+    const double kmax = tr.k2 > k ? tr.k2 : k;
     if (tr.quad_nodes <= 0) {
         // Automatic: the 1D integrals of the coefficients oscillate at the grid's
         // frequencies -- h(s) over [eps, 2 eps] at s up to |xi|_max, the X' integrals
@@ -224,15 +237,13 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
             const double m1 = M[0] / 2 + 1;
             smax = sqrt(m1 * m1 + qmax * qmax);
         }
-        const double need = fmax(smax * 0.5 * tr.eps, (qmax + k) * 0.25 * (tr.c_tilde - tr.c)) + 24.0;
+        const double need = fmax(smax * 0.5 * tr.eps, (qmax + kmax) * 0.25 * (tr.c_tilde - tr.c)) + 24.0;
         int Qa = (int)ceil(need);
         Qa = (Qa + 7) / 8 * 8;
         tr.quad_nodes = Qa < 64 ? 64 : Qa > 1024 ? 1024 : Qa;
     }
     if (tr.quad_nodes < 8 || tr.quad_nodes > 1024) return fail(GF_ERR_ARG, "gf_plan: quad_nodes must be in [8, 1024]");
     if (tr.precision != GF_FP64 && tr.precision != GF_FP32_SPLIT) return fail(GF_ERR_ARG, "gf_plan: bad precision");
-    if (tr.kind != GF_HELMHOLTZ && tr.kind != GF_MAXWELL) return fail(GF_ERR_ARG, "gf_plan: bad kind");
-    if (tr.kind == GF_MAXWELL && dim != 3) return fail(GF_ERR_ARG, "gf_plan: the Maxwell tensor needs dim = 3");
     if (tr.far_grid_M != 0) {
         if (dim != 3) return fail(GF_ERR_ARG, "gf_plan: the far-region grid is for 3D plans");
         if (!pow2_in(tr.far_grid_M, 16, 2048))
@@ -249,20 +260,22 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
 
     // Wood anomaly (Sec. 1): beta_n = 0 for some n.  Only |alpha_n| ~ k matters.
     double bmin_ev = 1e300;
-    {
-        int R = (int)ceil(k) + 2;
+    for (int kw = 0; kw < (tr.k2 > 0.0 ? 2 : 1); ++kw) {
+        // the second pass (derivative plans with k2) checks only for a Wood anomaly
+        const double kc = kw == 0 ? k : tr.k2;
+        int R = (int)ceil(kc) + 2;
         int r2 = dim == 3 ? R : 0;
         double bmin = 1e300;
         for (int n1 = -R - (int)fabs(a1); n1 <= R + (int)fabs(a1); ++n1)
             for (int n2 = -r2 - (int)fabs(a2); n2 <= r2 + (int)fabs(a2); ++n2) {
                 double c1 = a1 + n1, c2 = a2 + n2;
                 double aa = sqrt(c1 * c1 + c2 * c2);
-                double b = sqrt(fabs((k - aa) * (k + aa)));
+                double b = sqrt(fabs((kc - aa) * (kc + aa)));
                 if (b < bmin) bmin = b;
                 // the smallest evanescent b (attained at the smallest |alpha_n| > k, inside this box)
-                if (aa > k && b < bmin_ev) bmin_ev = b;
+                if (kw == 0 && aa > k && b < bmin_ev) bmin_ev = b;
             }
-        if (bmin < 1e-8 * k) return fail(GF_ERR_WOOD, "gf_plan: |beta_n| = %.3g < 1e-8 k (Wood anomaly)", bmin);
+        if (bmin < 1e-8 * kc) return fail(GF_ERR_WOOD, "gf_plan: |beta_n| = %.3g < 1e-8 k (Wood anomaly)", bmin);
     }
     // Resonance beta_{j'} = +-q_{j_last} (Secs. 2.1, 3.1): perturb c~ or fail.
     const int Mlast = M[dim - 1];
@@ -270,14 +283,16 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
     for (int attempt = 0;; ++attempt) {
         double worst = 1e300;
         int N1 = M[0] / 2, N2 = dim == 3 ? M[1] / 2 : 1;
+        for (int kw = 0; kw < (tr.k2 > 0.0 ? 2 : 1); ++kw)
         for (int j1 = -N1; j1 < N1; ++j1)
             for (int j2 = (dim == 3 ? -N2 : 0); j2 < (dim == 3 ? N2 : 1); ++j2) {
                 double c1 = a1 + j1, c2 = a2 + j2;
                 double A2 = c1 * c1 + c2 * c2;
-                if (A2 >= k * k) continue;  // evanescent beta cannot equal a real q
+                const double kc = kw == 0 ? k : tr.k2;
+                if (A2 >= kc * kc) continue;  // evanescent beta cannot equal a real q
                 for (int j3 = 0; j3 <= Mlast / 2; ++j3) {
                     double q = j3 * GF_PI / tr.c_tilde;
-                    double d = fabs(k * k - A2 - q * q);
+                    double d = fabs(kc * kc - A2 - q * q) / (kc * kc) * (k * k);
                     if (d < worst) worst = d;
                 }
             }
@@ -299,7 +314,7 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
     p->bmin_ev = bmin_ev;
     p->precision = tr.precision;
     p->kind = tr.kind;
-    p->nf = tr.kind == GF_MAXWELL ? 7 : 1;
+    p->nf = tr.kind == GF_MAXWELL ? 7 : tr.kind == GF_DERIV2D ? (tr.k2 > 0.0 ? 6 : 3) : 1;
     p->elem = tr.precision == GF_FP64 ? 16 : 8;
     p->T = log(1.0 / tr.series_tol) + 3.0;
     p->P1 = p->M[0] + 3;
@@ -370,6 +385,19 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
             P1[m] = wr * ph1 * r * r;
         }
     }
+    // derivative plans: Gauss-Legendre nodes on [0, eps] and [eps, 2 eps] with
+    // weights w Y(r) for the Hankel transforms of the cutoff
+    const bool deriv = tr.kind == GF_DERIV2D;
+    std::vector<double> rrd(deriv ? 2 * Q : 0), wyd(deriv ? 2 * Q : 0);
+    if (deriv) {
+        const double hr = 0.5 * eps;
+        for (int piece = 0; piece < 2; ++piece)
+            for (int m = 0; m < Q; ++m) {
+                const double r = (piece + 0.5) * eps + hr * gx[m];
+                rrd[piece * Q + m] = r;
+                wyd[piece * Q + m] = gw[m] * hr * (piece == 0 ? 1.0 : yps0(r, eps));
+            }
+    }
     // Piecewise Chebyshev interpolants (degree 14, panels of width 2) of the
     // radial transforms on [0, s_max], s_max >= the largest frequency norm:
     // 3D h(s) = sum_m B_m sin(s r_m)/s, 2D the Bessel sums of F1-hat, F2-hat.
@@ -409,9 +437,11 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
     const size_t nodes_padded = (size_t)p->P1 * p->P2 * p->P3;
     p->grid_bytes = nodes_padded * p->nf * p->elem;
     const size_t E_n = (size_t)Mlast * Q;
-    const size_t host_tab_bytes = sizeof(double) * 5 * Q + sizeof(double2) * Q;
+    const size_t host_tab_bytes = sizeof(double) * 5 * Q + sizeof(double2) * Q + (deriv ? sizeof(double) * 4 * Q : 0);
     const bool ftabs = tr.precision == GF_FP32_SPLIT;  // float copies for the split plans' coefficients
-    const size_t tab_bytes = host_tab_bytes + sizeof(double2) * (E_n + hcheb_n) + (ftabs ? sizeof(float2) * (E_n + hcheb_n) : 0);
+    const size_t dcheb_n = deriv ? 3 * hcheb_n : 0;
+    const size_t tab_bytes = host_tab_bytes + sizeof(double2) * (E_n + hcheb_n + dcheb_n) +
+                             (ftabs ? sizeof(float2) * (E_n + hcheb_n) : 0);
     const size_t work_bytes = gf_plan_work_bytes(p);
     void *work = nullptr;
     gf_status st_err = GF_OK;
@@ -430,8 +460,10 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
         }
         char *tb = (char *)p->tables;
         double *d_tt = (double *)tb, *d_tW = d_tt + Q, *d_rr = d_tW + Q, *d_P0 = d_rr + Q, *d_P1 = d_P0 + Q;
-        double2 *d_B = (double2 *)(d_P1 + Q), *d_E = d_B + Q, *d_H = d_E + E_n;
-        float2 *d_Ef = ftabs ? (float2 *)(d_H + hcheb_n) : nullptr, *d_Hf = ftabs ? d_Ef + E_n : nullptr;
+        double2 *d_B = (double2 *)(d_P1 + Q);
+        double *d_rrd = (double *)(d_B + Q), *d_wyd = d_rrd + (deriv ? 2 * Q : 0);
+        double2 *d_E = (double2 *)(d_wyd + (deriv ? 2 * Q : 0)), *d_H = d_E + E_n, *d_D = d_H + hcheb_n;
+        float2 *d_Ef = ftabs ? (float2 *)(d_D + dcheb_n) : nullptr, *d_Hf = ftabs ? d_Ef + E_n : nullptr;
         {
             std::vector<char> pack(host_tab_bytes);
             char *hb = pack.data();
@@ -441,9 +473,14 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
             memcpy(hb + ((char *)d_P0 - tb), P0.data(), sizeof(double) * Q);
             memcpy(hb + ((char *)d_P1 - tb), P1.data(), sizeof(double) * Q);
             memcpy(hb + ((char *)d_B - tb), B.data(), sizeof(double2) * Q);
+            if (deriv) {
+                memcpy(hb + ((char *)d_rrd - tb), rrd.data(), sizeof(double) * 2 * Q);
+                memcpy(hb + ((char *)d_wyd - tb), wyd.data(), sizeof(double) * 2 * Q);
+            }
             if ((e = gf_stage_upload(tb, hb, host_tab_bytes, st)) != cudaSuccess ||
                 (e = gf_launch_e_table(d_tt, Q, Mlast, GF_PI / ct, d_E, d_Ef, st)) != cudaSuccess ||
-                (e = gf_launch_cheb_table(dim, d_rr, d_B, d_P0, d_P1, Q, hnpan, hdeg, hpan, d_H, d_Hf, st)) != cudaSuccess) {
+                (e = gf_launch_cheb_table(dim, d_rr, d_B, d_P0, d_P1, Q, hnpan, hdeg, hpan, d_H, d_Hf, st)) != cudaSuccess ||
+                (deriv && (e = gf_launch_cheb_deriv(d_rrd, d_wyd, 2 * Q, hnpan, hdeg, hpan, d_D, st)) != cudaSuccess)) {
                 st_err = fail(GF_ERR_CUDA, "gf_plan: tables: %s", cudaGetErrorString(e));
                 break;
             }
@@ -499,6 +536,10 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
         sa.nyq = p->nyq;
         sa.nyqgrid = p->nyqgrid;
         sa.err = p->errw;
+        sa.oddmask = tr.kind == GF_MAXWELL ? (1 << 4) | (1 << 5) : deriv ? (1 << 2) | (1 << 4) : 0;
+        sa.deriv = deriv ? 1 : 0;
+        sa.k2 = tr.k2;
+        sa.dcheb = deriv ? d_D : nullptr;
         {
             // one CTA holds whole lines of every stored field in shared memory
             int dev = 0, optin = 232448;
@@ -718,7 +759,8 @@ gf_status gf_plan_eval_args(gf_plan_t p, const double *dev_xyz, int64_t n, int w
     if (n < 0 || n > (int64_t)0x7fffffff) return fail(GF_ERR_ARG, "%s: n = %lld out of range", who, (long long)n);
     if (n > 0 && (!dev_xyz || !dev_out)) return fail(GF_ERR_ARG, "%s: NULL buffer", who);
     bool ok = (p->dim == 2 && which == GF_OUT_G) || (p->dim == 3 && p->kind == GF_HELMHOLTZ && (which == GF_OUT_GD || which == GF_OUT_LD)) ||
-              (p->kind == GF_MAXWELL && (which == GF_OUT_MAXWELL6 || which == GF_OUT_MAXWELL7));
+              (p->kind == GF_MAXWELL && (which == GF_OUT_MAXWELL6 || which == GF_OUT_MAXWELL7)) ||
+              (p->kind == GF_DERIV2D && (which == GF_OUT_GRAD || (which == GF_OUT_HESSDIFF && p->nf == 6)));
     if (!ok) return fail(GF_ERR_ARG, "%s: output kind %d does not match the plan", who, which);
     EvalArgs a{};
     a.dim = p->dim;
@@ -732,6 +774,7 @@ gf_status gf_plan_eval_args(gf_plan_t p, const double *dev_xyz, int64_t n, int w
     a.nf = p->nf;
     a.which = which;
     a.k = p->k;
+    a.k2 = p->tr.k2;
     a.a1 = p->alpha[0];
     a.a2 = p->alpha[1];
     a.c = p->tr.c;
@@ -815,7 +858,7 @@ gf_status gf_eval_points_host(gf_plan_t p, const double *host_xyz, int64_t n, in
     if (n < 0) return fail(GF_ERR_ARG, "gf_eval_points_host: n < 0");
     if (n == 0) return GF_OK;
     if (!host_xyz || !host_out) return fail(GF_ERR_ARG, "gf_eval_points_host: NULL buffer");
-    int ne = which == GF_OUT_MAXWELL6 ? 6 : which == GF_OUT_MAXWELL7 ? 7 : 1;
+    int ne = gf_out_entries(which);
     size_t xb = sizeof(double) * p->dim * (size_t)n, ob = p->elem * ne * (size_t)n;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     // device staging per call from the stream-ordered pool (pool hits after the first call)
@@ -862,6 +905,7 @@ gf_status gf_plan_get_info(gf_plan_t p, gf_plan_info_t *info)
     info->far_grid_nz = p->fNZ ? p->fNZ - 3 : 0;
     info->far_grid_zmax = p->fzmax;
     info->far_grid_device_bytes = p->far_bytes;
+    info->k2 = p->tr.k2;
     return GF_OK;
 }
 

@@ -31,6 +31,64 @@ __device__ __forceinline__ double2 beta_of(double k, double a2)
     return make_double2(0.0, sqrt((a - k) * (a + k)));
 }
 
+// The X'-integral terms of Eq. (fck-coef)/(kdj1) for one coefficient:
+//   T1 - T2 = I1/(2 beta (q - beta)) - I2/(2 beta (q + beta)),
+// I1 = sum A conj(E), I2 = sum A E over the Gauss nodes (A_m = w_m X'(t_m)
+// e^{i beta t_m}, E_m = e^{i q t_m}).  Evanescent beta = i g: A_m is real, I1 =
+// s1 - i s3, I2 = s1 + i s3 and T1 - T2 = (g s1 - q s3)/(g (g^2 + q^2)); for g >
+// gskip both terms are below double rounding of the coefficient (|I| <= e^{-g c},
+// |2 beta (q -+ beta)| >= 2 g^2) and are not formed.
+__device__ __forceinline__ double2 xprime_terms(double2 beta, double q, const double2 *Am, const double2 *Em, int Q,
+                                                double gskip)
+{
+    double2 T12 = make_double2(0.0, 0.0);
+    if (beta.y > 0.0 && beta.y <= gskip) {
+        double s1 = 0.0, s3 = 0.0;
+        for (int m = 0; m < Q; ++m) {
+            const double A = Am[m].x;
+            const double2 E = Em[m];
+            s1 = fma(A, E.x, s1);
+            s3 = fma(A, E.y, s3);
+        }
+        const double g = beta.y;
+        T12.x = (g * s1 - q * s3) / (g * (g * g + q * q));
+    } else if (beta.y <= gskip) {
+        double s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0;
+        for (int m = 0; m < Q; ++m) {
+            const double2 A = Am[m], E = Em[m];
+            s1 = fma(A.x, E.x, s1);
+            s2 = fma(A.y, E.y, s2);
+            s3 = fma(A.x, E.y, s3);
+            s4 = fma(A.y, E.x, s4);
+        }
+        // propagating beta (real)
+        const double2 I1 = make_double2(s1 + s2, s4 - s3);
+        const double2 I2 = make_double2(s1 - s2, s3 + s4);
+        const double2 tb = cscale(beta, 2.0);
+        const double2 T1 = cdiv(I1, cmul(tb, make_double2(q - beta.x, -beta.y)));
+        const double2 T2 = cdiv(I2, cmul(tb, make_double2(q + beta.x, beta.y)));
+        T12 = csub(T1, T2);
+    }
+    return T12;
+}
+
+// Clenshaw sum of one panel's Chebyshev coefficients (two real functions packed
+// in a double2) at x in [-1, 1].
+__device__ __forceinline__ double2 cheb_eval(const double2 *cc, int deg, double x)
+{
+    double b1r = 0.0, b1i = 0.0, b2r = 0.0, b2i = 0.0;
+    for (int kk = deg; kk >= 1; --kk) {
+        const double2 ck = cc[kk];
+        const double tr = fma(2.0 * x, b1r, ck.x - b2r);
+        const double ti = fma(2.0 * x, b1i, ck.y - b2i);
+        b2r = b1r;
+        b2i = b1i;
+        b1r = tr;
+        b1i = ti;
+    }
+    return make_double2(fma(x, b1r, cc[0].x - b2r), fma(x, b1i, cc[0].y - b2i));
+}
+
 // e^{2 pi i m/n} for 0 <= m < n from the table of the first half (tw[m] =
 // e^{2 pi i m/n}, m < n/2): the second half is its negative.
 template <typename C>
@@ -180,6 +238,77 @@ __device__ void load_twiddles(typename cplx_t<R>::T *tw, int n)
     }
 }
 
+// The derivative fields of one 2D coefficient (Sec. 2.4), sqrt(V)-scaled before
+// the 1/V of the synthesis: fields 1 .. nf-1 of buf0 (field 0, L, is the
+// caller's).  K = sqrt(V) K-hat(k); eta = |(j1, q)| (0 at j = 0); F1 = sqrt(V)
+// F1-hat; S1 = int Phi_1 J1(eta r) r^2 dr; (pnl, x) the Chebyshev panel and
+// position of eta; Am2, beta2: the second wave number's X' weights and beta.
+// The singular parts' coefficients come from plane transforms reduced by the
+// angle, FT[g(r) cos(m th)] = 2 pi (-i)^m cos(m phi) int g J_m(eta r) r dr:
+//   ln r Y -> -2 pi F1, x1 ln r Y -> -2 pi F2, x2 ln r Y -> -2 pi F2' (F2 with q
+//   for j1), x_i/r^2 Y (m = 1 of Y/r: Q1), Y (R0), cos 2th Y, sin 2th Y (R2),
+//   x_i Y (m = 1 of r Y: S1), r cos 3th Y, r sin 3th Y (S3),
+// read from the dcheb tables (Q1, R0), (R2, S1), (S3, -); the even-angle
+// transforms are real, the odd-angle ones imaginary, so H_1, H_2 are imaginary
+// and H_11, H_12, H_22 real:
+//   h_1  = -(1/2pi)[-(k^2/2) x1 ln r + x1/r^2 - i alpha x1^2/r^2 - (alpha^2/2) x1^3/r^2] Y
+//   h_2  = -(1/2pi)[-(k^2/2) x2 ln r + x2/r^2 - i alpha x1 x2/r^2 - (alpha^2/2) x1^2 x2/r^2] Y
+//   h_11 = (dk2/2pi)[ln r/2 - (i alpha/2) x1 ln r + x1^2/(2r^2) - i alpha x1^3/(2r^2)] Y
+//   h_12 = (dk2/2pi)[x1 x2/(2r^2) - (i alpha/2) x1^2 x2/r^2] Y
+//   h_22 = (dk2/2pi)[ln r/2 - (i alpha/2) x1 ln r + x2^2/(2r^2) - (i alpha/2) x1 x2^2/r^2] Y
+// (dk2 = k^2 - k2^2), with x1^2/r^2 = (1 + cos 2th)/2, x2^2/r^2 = (1 - cos 2th)/2,
+// x1 x2/r^2 = sin 2th/2, x1^3/r^2 = r (3 cos th + cos 3th)/4, x1^2 x2/r^2 =
+// r (sin th + sin 3th)/4, x1 x2^2/r^2 = r (cos th - cos 3th)/4.  Then
+//   K_1 - h_1: i (alpha + j1) K - H_1,   K_2 - h_2: i q K - H_2,
+//   T_pq - h_pq: -c_p c_q (K - K(k2)) - H_pq,  c = (alpha + j1, q).
+template <typename C>
+__device__ void deriv_fields_2d(const SynthArgs &a, C *buf0, int TJ, int t, int n, int b, int jx, double q,
+                                double eta, double F1, double S1, double2 K, double A2, const double2 *Am2,
+                                const double2 *Em, double2 beta2, int pnl, double x)
+{
+    typedef decltype(C().x) R;
+    const double ip = 2.0 * GF_PI, al = a.a1, kk = a.k * a.k, c1 = al + jx;
+    const int nd = a.hdeg + 1;
+    const size_t tab = (size_t)a.hnpan * nd;
+    const double2 d0 = cheb_eval(a.dcheb + (size_t)pnl * nd, a.hdeg, x);            // (Q1, R0)
+    const double2 d1 = cheb_eval(a.dcheb + tab + (size_t)pnl * nd, a.hdeg, x);      // (R2, S1)
+    const double S3 = cheb_eval(a.dcheb + 2 * tab + (size_t)pnl * nd, a.hdeg, x).x;  // S3
+    double cp = 0.0, sp = 0.0, f2i = 0.0, f2yi = 0.0;
+    if (eta > 0.0) {
+        cp = jx / eta;
+        sp = q / eta;
+        const double ie2 = 1.0 / (eta * eta);
+        f2i = (-2.0 * jx * F1 - cp * S1) * ie2;   // sqrt(V) F2-hat = i f2i
+        f2yi = (-2.0 * q * F1 - sp * S1) * ie2;   // its x2 analogue
+    }
+    const double c2 = cp * cp - sp * sp, s2 = 2.0 * cp * sp;
+    const double c3 = cp * (4.0 * cp * cp - 3.0), s3 = sp * (3.0 - 4.0 * sp * sp);
+    const double Q1 = d0.x, R0 = d0.y, R2 = d1.x, S1Y = d1.y;
+    // real parts of the even-angle transforms, imaginary parts of the odd-angle ones
+    const double x1sq = 0.5 * ip * (R0 - c2 * R2), x2sq = 0.5 * ip * (R0 + c2 * R2), x1x2 = -0.5 * ip * s2 * R2;
+    const double x1cub = 0.25 * ip * (-3.0 * cp * S1Y + c3 * S3);
+    const double x1sqx2 = 0.25 * ip * (-sp * S1Y + s3 * S3);
+    const double x1x2sq = 0.25 * ip * (-cp * S1Y - c3 * S3);
+    const double H1i = -((0.5 * kk) * ip * f2i - ip * cp * Q1 - al * x1sq - 0.5 * al * al * x1cub) / ip;
+    const double H2i = -((0.5 * kk) * ip * f2yi - ip * sp * Q1 - al * x1x2 - 0.5 * al * al * x1sqx2) / ip;
+    const double sc = a.invV;
+    buf0[(1 * TJ + t) * n + b] = cmk((R)(-c1 * K.y * sc), (R)((c1 * K.x - H1i) * sc));
+    buf0[(2 * TJ + t) * n + b] = cmk((R)(-q * K.y * sc), (R)((q * K.x - H2i) * sc));
+    if (a.nf < 6) return;
+    const double dk2 = kk - a.k2 * a.k2;
+    const double2 T12 = xprime_terms(beta2, q, Am2, Em, a.Q, a.gskip);
+    const double iD2 = 1.0 / (A2 + q * q - a.k2 * a.k2);
+    const double2 dK = make_double2(K.x - (iD2 + T12.x), K.y - T12.y);
+    const double base = -0.5 * ip * F1 - 0.5 * al * ip * f2i;  // P0/2 - (i alpha/2) P1c
+    const double H11 = dk2 / ip * (base + 0.5 * x1sq + 0.5 * al * x1cub);
+    const double H12 = dk2 / ip * (0.5 * x1x2 + 0.5 * al * x1sqx2);
+    const double H22 = dk2 / ip * (base + 0.5 * x2sq + 0.5 * al * x1x2sq);
+    const double f[3] = {-c1 * c1, -c1 * q, -q * q}, H[3] = {H11, H12, H22};
+#pragma unroll
+    for (int e = 0; e < 3; ++e)
+        buf0[((3 + e) * TJ + t) * n + b] = cmk((R)((f[e] * dK.x - H[e]) * sc), (R)(f[e] * dK.y * sc));
+}
+
 template <typename R>
 __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char *smem)
 {
@@ -203,6 +332,10 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
     float2 *qqf = A2mkf + TJ;
     float *gcol = reinterpret_cast<float *>(qqf + n);
     int *cflag = reinterpret_cast<int *>(gcol + TJ);
+    // 2D derivative plans with a second wave number: its A_m [TJ][Q] and beta [TJ]
+    const bool need_k2 = a.deriv && a.k2 > 0.0;
+    double2 *Av2 = reinterpret_cast<double2 *>((reinterpret_cast<uintptr_t>(cflag + TJ) + 15) & ~(uintptr_t)15);
+    double2 *betas2 = Av2 + TJ * Q;
     const int ncols = (a.dim == 3) ? a.M1 * a.M2 : a.M1;
     // tiles alternately from both ends of the column range: the low frequencies
     // (whose X'-integrals are formed, the expensive tiles) sit at both ends, so
@@ -227,6 +360,7 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
         A2s[t] = A2;
         const double2 bt = beta_of(a.k, A2);
         betas[t] = bt;
+        if (need_k2) betas2[t] = beta_of(a.k2, A2);
         if (fcoef) {
             const double d = A2 - a.k * a.k;
             A2mk[t] = d;
@@ -265,6 +399,22 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
         }
         Av[i] = cscale(e, a.tW[m]);
     }
+    if (need_k2)
+        for (int i = threadIdx.x; i < TJ * Q; i += blockDim.x) {
+            const int t = i / Q, m = i - t * Q;
+            const double2 b = betas2[t];
+            if (b.y > a.gskip) continue;
+            const double tm = a.tt[m];
+            double2 e;
+            if (b.y == 0.0) {
+                double sn, cs;
+                sincos(b.x * tm, &sn, &cs);
+                e = make_double2(cs, sn);
+            } else {
+                e = make_double2(exp(-b.y * tm), 0.0);
+            }
+            Av2[i] = cscale(e, a.tW[m]);
+        }
     __syncthreads();
 
     const double k2 = a.k * a.k, ik2 = 1.0 / k2;
@@ -359,42 +509,7 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
         double A2 = A2s[t];
         const double2 *Am = Av + t * Q;
         const double2 *Em = a.E + (size_t)b * Q;
-        // T1 - T2 = I1/(2 beta (q - beta)) - I2/(2 beta (q + beta)), with
-        // I1 = sum A conj(E), I2 = sum A E (four real sums).  For evanescent
-        // beta = i g: |I1|, |I2| <= e^{-g c} (X' has total variation 1) and
-        // |2 beta (q -+ beta)| >= 2 g^2, so when e^{-g c}/(2 g^2) < 1e-20 (g > gskip)
-        // the two terms are below double rounding of C and are not formed; else
-        // T1 - T2 = [I1 (g - i q) + I2 (g + i q)] / (2 g (g^2 + q^2)).
-        double2 T12 = make_double2(0.0, 0.0);
-        if (beta.y > 0.0 && beta.y <= a.gskip) {
-            // evanescent: A_m is real, I1 = s1 - i s3, I2 = s1 + i s3 (two real sums),
-            // and T1 - T2 = (g s1 - q s3)/(g (g^2 + q^2)) is real
-            double s1 = 0.0, s3 = 0.0;
-            for (int m = 0; m < Q; ++m) {
-                const double A = Am[m].x;
-                const double2 E = Em[m];
-                s1 = fma(A, E.x, s1);
-                s3 = fma(A, E.y, s3);
-            }
-            const double g = beta.y;
-            T12.x = (g * s1 - q * s3) / (g * (g * g + q * q));
-        } else if (beta.y <= a.gskip) {
-            double s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0;
-            for (int m = 0; m < Q; ++m) {
-                double2 A = Am[m], E = Em[m];
-                s1 = fma(A.x, E.x, s1);
-                s2 = fma(A.y, E.y, s2);
-                s3 = fma(A.x, E.y, s3);
-                s4 = fma(A.y, E.x, s4);
-            }
-            // propagating beta (real)
-            double2 I1 = make_double2(s1 + s2, s4 - s3);
-            double2 I2 = make_double2(s1 - s2, s3 + s4);
-            double2 tb = cscale(beta, 2.0);
-            double2 T1 = cdiv(I1, cmul(tb, make_double2(q - beta.x, -beta.y)));
-            double2 T2 = cdiv(I2, cmul(tb, make_double2(q + beta.x, beta.y)));
-            T12 = csub(T1, T2);
-        }
+        const double2 T12 = xprime_terms(beta, q, Am, Em, Q, a.gskip);
         double D = A2 + q * q - k2;
         double2 Cj;
         if (a.dim == 3) {
@@ -450,9 +565,18 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
                 F1 = make_double2((1.0 + S0) / eta2, 0.0);
                 // F2 = (-2 i j1 F1 + Phi2-hat/(2 pi))/eta^2,  Phi2-hat/(2 pi) = -i (j1/eta) S1
                 F2 = make_double2(0.0, (-2.0 * jx * F1.x - ((double)jx / eta) * S1) / eta2);
+                if (a.deriv) deriv_fields_2d(a, buf0, TJ, t, n, b, jx, q, eta, F1.x, S1, K, A2, Av2 + t * Q, Em,
+                                             need_k2 ? betas2[t] : make_double2(0.0, 0.0), pnl, x);
             }
+            if (a.deriv && eta2 == 0.0) deriv_fields_2d(a, buf0, TJ, t, n, b, jx, q, 0.0, F1.x, 0.0, K, A2, Av2 + t * Q,
+                                                        Em, need_k2 ? betas2[t] : make_double2(0.0, 0.0), 0, -1.0);
             // C = K - F1 + i alpha F2
             Cj = make_double2(K.x - F1.x - a.a1 * F2.y, K.y - F1.y + a.a1 * F2.x);
+            if (a.deriv) {
+                Cj = cscale(Cj, a.invV);
+                buf0[t * n + b] = cmk((R)Cj.x, (R)Cj.y);
+                continue;
+            }
         }
         Cj = cscale(Cj, a.invV);
         if (nf == 1) {
@@ -484,8 +608,8 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
             const int line = i / nm, b = (n >> 1) + 1 + (i - line * nm);
             const int e = line / TJ;
             const C v = buf0[line * n + (n - b)];
-            // Maxwell fields 4 (xz) and 5 (yz) are odd in j
-            buf0[line * n + b] = (nf > 1 && (e == 4 || e == 5)) ? cmk(-v.x, -v.y) : v;
+            // the odd fields (Maxwell xz, yz; 2D K_2, T_12) change sign with j
+            buf0[line * n + b] = ((a.oddmask >> e) & 1) ? cmk(-v.x, -v.y) : v;
         }
     }
     __syncthreads();
@@ -856,7 +980,8 @@ void synth_config_t(SynthArgs &a, int tj_max, size_t sm[3])
         return sizeof(C) * (a.Mlast / 2) + sizeof(double) * a.Mlast + sizeof(float2) * a.Mlast +
                TJ * (sizeof(double2) * a.Q + sizeof(double2) + 2 * sizeof(double) + sizeof(float)) +
                TJ * (sizeof(float2) + sizeof(float) + sizeof(int)) +
-               sizeof(float) * ((TJ * a.Q + 3) & ~3) + sizeof(C) * (a.nf + 1) * TJ * a.Mlast + 64;
+               sizeof(float) * ((TJ * a.Q + 3) & ~3) + sizeof(C) * (a.nf + 1) * TJ * a.Mlast + 64 +
+               (a.deriv && a.k2 > 0.0 ? TJ * sizeof(double2) * (a.Q + 1) + 16 : 0);
     };
     int TJ = tj_max;
     while (TJ > 1 && (TJ > ncols || bytes(TJ) > 160 * 1024)) TJ >>= 1;
@@ -1047,7 +1172,62 @@ __global__ void __launch_bounds__(256) cheb_table_kernel(const double *rr, const
         if (outf) outf[(size_t)p * nn + t] = make_float2((float)(cr * sc), (float)(ci * sc));
     }
 }
+// The 2D derivative plans' Hankel transforms of the cutoff Y on the same panels:
+// at each Chebyshev point s, sums over the nodes r_m of [0, eps] and [eps, 2 eps]
+// with weights wy_m = w_m Y(r_m):
+//   table 0: (Q1, R0) = (sum wy J1(s r), sum wy J0(s r) r)
+//   table 1: (R2, S1) = (sum wy J2(s r) r, sum wy J1(s r) r^2)
+//   table 2: (S3, 0)  = (sum wy J3(s r) r^2, 0)
+// out: [3][npan][nn].
+__global__ void __launch_bounds__(256) cheb_deriv_kernel(const double *rr, const double *wy, int Q2, int nn, double w,
+                                                         int npan, double2 *out)
+{
+    __shared__ double fv[16][5];
+    const int p = blockIdx.x, t = threadIdx.x, k = t >> 4, g = t & 15;
+    const double cen = (p + 0.5) * w, hh = 0.5 * w;
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    if (k < nn) {
+        const double s = cen + hh * cospi((k + 0.5) / nn);
+        for (int m = g; m < Q2; m += 16) {
+            const double r = rr[m], z = s * r, wm = wy[m];
+            const double J0 = j0(z), J1 = j1(z), J2 = jn(2, z), J3 = jn(3, z);
+            acc[0] = fma(wm, J1, acc[0]);
+            acc[1] = fma(wm * r, J0, acc[1]);
+            acc[2] = fma(wm * r, J2, acc[2]);
+            acc[3] = fma(wm * r * r, J1, acc[3]);
+            acc[4] = fma(wm * r * r, J3, acc[4]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+        for (int o = 8; o > 0; o >>= 1) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
+    if (k < nn && g == 0)
+#pragma unroll
+        for (int i = 0; i < 5; ++i) fv[k][i] = acc[i];
+    __syncthreads();
+    if (t < nn) {
+        double c[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int q = 0; q < nn; ++q) {
+            const double cq = cospi((double)t * (q + 0.5) / nn);
+#pragma unroll
+            for (int i = 0; i < 5; ++i) c[i] = fma(fv[q][i], cq, c[i]);
+        }
+        const double sc = (t == 0 ? 1.0 : 2.0) / nn;
+        const size_t tab = (size_t)npan * nn, o = (size_t)p * nn + t;
+        out[o] = make_double2(c[0] * sc, c[1] * sc);
+        out[tab + o] = make_double2(c[2] * sc, c[3] * sc);
+        out[2 * tab + o] = make_double2(c[4] * sc, 0.0);
+    }
+}
 }  // namespace
+
+cudaError_t gf_launch_cheb_deriv(const double *rr, const double *wy, int Q2, int npan, int deg, double w, double2 *out,
+                                 cudaStream_t s)
+{
+    cheb_deriv_kernel<<<npan, 256, 0, s>>>(rr, wy, Q2, deg + 1, w, npan, out);
+    gf_count_launch(1);
+    return cudaGetLastError();
+}
 
 // E[b][m] = e^{i q_b t_m}, q_b = j qs (qs = pi / c~) with j = b for b < Mlast/2, else
 // b - Mlast (the last-axis frequencies of Eq. (fck-coef)), t_m the Gauss nodes

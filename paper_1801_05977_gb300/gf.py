@@ -15,10 +15,11 @@ from . import build as _build
 
 GF_OK, GF_ERR_ARG, GF_ERR_WOOD, GF_ERR_RESONANCE, GF_ERR_NOMEM, GF_ERR_CUDA, GF_ERR_TIMEOUT, GF_ERR_UNSUPPORTED = range(8)
 GF_FP64, GF_FP32_SPLIT = 0, 1
-GF_HELMHOLTZ, GF_MAXWELL = 0, 1
+GF_HELMHOLTZ, GF_MAXWELL, GF_DERIV2D = 0, 1, 2
 GF_PERTURB_CTILDE, GF_FAIL = 0, 1
-GF_OUT_G, GF_OUT_GD, GF_OUT_MAXWELL6, GF_OUT_MAXWELL7, GF_OUT_LD = 0, 1, 2, 3, 4
-N_ENTRIES = {GF_OUT_G: 1, GF_OUT_GD: 1, GF_OUT_MAXWELL6: 6, GF_OUT_MAXWELL7: 7, GF_OUT_LD: 1}
+GF_OUT_G, GF_OUT_GD, GF_OUT_MAXWELL6, GF_OUT_MAXWELL7, GF_OUT_LD, GF_OUT_GRAD, GF_OUT_HESSDIFF = 0, 1, 2, 3, 4, 5, 6
+N_ENTRIES = {GF_OUT_G: 1, GF_OUT_GD: 1, GF_OUT_MAXWELL6: 6, GF_OUT_MAXWELL7: 7, GF_OUT_LD: 1, GF_OUT_GRAD: 3,
+             GF_OUT_HESSDIFF: 3}
 
 
 class GfError(RuntimeError):
@@ -31,7 +32,7 @@ class Trunc(ctypes.Structure):
     _fields_ = [("c", ctypes.c_double), ("c_tilde", ctypes.c_double), ("eps", ctypes.c_double),
                 ("series_tol", ctypes.c_double), ("quad_nodes", ctypes.c_int), ("precision", ctypes.c_int),
                 ("kind", ctypes.c_int), ("resonance_policy", ctypes.c_int), ("far_grid_M", ctypes.c_int),
-                ("far_grid_nz", ctypes.c_int), ("far_grid_zmax", ctypes.c_double)]
+                ("far_grid_nz", ctypes.c_int), ("far_grid_zmax", ctypes.c_double), ("k2", ctypes.c_double)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -42,7 +43,7 @@ class PlanInfo(ctypes.Structure):
                 ("series_n1_lo", ctypes.c_int), ("series_n1_hi", ctypes.c_int), ("series_n2_lo", ctypes.c_int),
                 ("series_n2_hi", ctypes.c_int), ("grid_device_bytes", ctypes.c_size_t),
                 ("far_grid_M", ctypes.c_int), ("far_grid_nz", ctypes.c_int), ("far_grid_zmax", ctypes.c_double),
-                ("far_grid_device_bytes", ctypes.c_size_t)]
+                ("far_grid_device_bytes", ctypes.c_size_t), ("k2", ctypes.c_double)]
 
 
 EXPORTS = ["gf_trunc_default", "gf_plan", "gf_eval_grid", "gf_grid_bytes", "gf_eval_points",

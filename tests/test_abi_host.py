@@ -31,7 +31,7 @@ def test_trunc_defaults():
     t = gf.trunc_default()
     assert (t.c, t.c_tilde, t.eps, t.quad_nodes) == (0.6, 1.0, 0.45, 0)
     assert (t.far_grid_M, t.far_grid_nz, t.far_grid_zmax) == (0, 0, 0.0)
-    assert t.precision == gf.GF_FP64 and t.kind == gf.GF_HELMHOLTZ
+    assert t.precision == gf.GF_FP64 and t.kind == gf.GF_HELMHOLTZ and t.k2 == 0.0
 
 
 def _plan_status(dim, k, alpha, M, **kw):
@@ -64,6 +64,12 @@ def _plan_status(dim, k, alpha, M, **kw):
     ((2, 1.0, (0.1,), (16, 16)), {"far_grid_M": 64}),     # far grid is 3D only
     ((3, 1.0, (0.1, 0.2), (16, 16, 16)), {"far_grid_M": 64, "far_grid_zmax": 0.5}),  # zmax <= c
     ((3, 1.0, (0.1, 0.2), (16, 16, 16)), {"far_grid_M": 64, "far_grid_nz": -1}),
+    ((3, 1.0, (0.1, 0.2), (16, 16, 16)), {"kind": gf.GF_DERIV2D}),  # derivative fields are 2D only
+    ((2, 1.0, (0.1,), (16, 16)), {"kind": 3}),                      # no such kind
+    ((2, 1.0, (0.1,), (16, 16)), {"kind": gf.GF_DERIV2D, "k2": 1.0}),  # k2 = k: no difference
+    ((2, 1.0, (0.1,), (16, 16)), {"kind": gf.GF_DERIV2D, "k2": -2.0}),
+    ((2, 1.0, (0.1,), (16, 16)), {"kind": gf.GF_DERIV2D, "k2": float("inf")}),
+    ((2, 1.0, (0.1,), (16, 16)), {"k2": 2.0}),                      # k2 without derivative fields
 ])
 def test_plan_rejects_bad_arguments(args, kw):
     st, h, msg = _plan_status(*args, **kw)
@@ -76,6 +82,9 @@ def test_plan_detects_wood_anomaly():
     assert st == gf.GF_ERR_WOOD and "Wood" in msg
     st, h, msg = _plan_status(2, 1.3, (0.3,), (16, 16))
     assert st == gf.GF_ERR_WOOD
+    # the second wave number of a derivative plan is checked too
+    st, h, msg = _plan_status(2, 2.1, (0.3,), (16, 16), kind=gf.GF_DERIV2D, k2=1.3)
+    assert st == gf.GF_ERR_WOOD and "Wood" in msg
 
 
 def test_plan_resonance_policy_fail():
@@ -110,5 +119,7 @@ def test_batch_rejects_bad_arguments():
     al2 = (ctypes.c_double * 4)(0.1, 0.0, 0.1, 0.3)
     st = L.gf_plan_batch(2, k2, al2, M, ctypes.byref(t), None, ctypes.byref(h))
     assert st == gf.GF_ERR_WOOD and "pair 0" in L.gf_last_error().decode()
+    td = gf.trunc_default(kind=gf.GF_DERIV2D)
+    assert L.gf_plan_batch(2, k, al, M, ctypes.byref(td), None, ctypes.byref(h)) == gf.GF_ERR_UNSUPPORTED
     assert L.gf_batch_destroy(None) == gf.GF_OK
     assert L.gf_batch_eval_points(None, None, None, 1, None, None) == gf.GF_ERR_ARG
