@@ -432,6 +432,9 @@ def run_gpu(args):
     far_ms = float(np.mean([p[3] for p in ph64]))
     near_ms = float(np.mean([p[2] for p in ph64]))
     synth_ms = float(np.mean([p[0] for p in ph64]))
+    table_ms = float(np.mean([p[1] for p in ph64]))
+    n_far_t = int((np.abs(x_np[:, 2]) > 0.6).sum())
+    n_near_t = n_targets - n_far_t
     terms, core_terms, bands = far_terms(x_np, K_WAVE, ALPHA, 0.6, tol64)
     tail_terms = terms - core_terms
     peaks = measure_peaks(dev)
@@ -487,6 +490,12 @@ def run_gpu(args):
                    "series_tol": tol64, "parallelism": f"replicas{world}", "l2": "flushed (256 MiB write) between steps"},
         "phases_ms": {"synthesis": synth_ms, "near": near_ms, "far": far_ms,
                       "far_series_terms": terms, "far_core_terms": core_terms},
+        "rates": {"plan_ms": synth_ms + table_ms,
+                  "eval_only_evals_per_s": n_targets / ((near_ms + far_ms) * 1e-3),
+                  "near_evals_per_s": n_near_t / (near_ms * 1e-3), "far_evals_per_s": n_far_t / (far_ms * 1e-3),
+                  "note": "from the step's phase events (CUDA events on the plan's stream): plan = coefficients, "
+                          "inverse FFTs and the far-series tables; eval = near pass (classification and gather) + "
+                          "far pass; near and far rates over the targets of each branch"},
         "split": {"value": whole_job_rate(n_targets, world, ms32 * 1e-3), "ms_per_step": ms32, "dtype": "f32/f64 split",
                   "series_tol": 1e-8, "max_err_vs_fp64_normwise": split_err,
                   "phases_ms": {"synthesis": float(np.mean([p[0] for p in ph32])),

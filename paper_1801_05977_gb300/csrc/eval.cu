@@ -1574,13 +1574,13 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, i
         for (int q = 0; q < nq; ++q) {
             if (taylor && (q & 31) == 0) {
                 if (q + lane < nq) {
-                    const PropEntry pl = a.prop[q + lane];
+                    const PropEntry &pl = a.prop[q + lane];
                     sincos(pl.br * zw, &ewy, &ewx);
                     ewx *= pl.ibr;
                     ewy *= pl.ibr;
                 }
             }
-            const PropEntry pe = a.prop[q];
+            const PropEntry &pe = a.prop[q];
             if (pe.first) {
                 double sp, cp;
                 sincos(fma(pe.c1, L.t1, pe.m2 * L.t2), &sp, &cp);
@@ -1800,7 +1800,7 @@ __device__ __forceinline__ int far_take(int *counter, int nitems)
 }
 
 template <int NF, bool TAILS>
-__global__ void __launch_bounds__(128) far3d_f64(EvalArgs a)
+__global__ void __launch_bounds__(128, NF == 1 ? 5 : 1) far3d_f64(EvalArgs a)
 {
     const int count = a.far_count[0];
     const int nch = (count + 31) >> 5, S = far_slabs(nch, 8);
@@ -1948,7 +1948,7 @@ __device__ void far3d_f32_chunk(const EvalArgs &a, int w, int count, int slab, i
 #pragma unroll
         for (int e = 0; e < (NF == 1 ? 1 : 7); ++e) S[e][0] = S[e][1] = 0.f;
         for (int q = 0, nq = slab == 0 ? *a.nprop : 0; q < nq; ++q) {
-            const PropEntry pe = a.prop[q];
+            const PropEntry &pe = a.prop[q];
             const float br = pe.brf, ibr = pe.ibrf, c1 = pe.c1f, c2 = pe.c2f;
             float sz, cz, sp, cp;
             sincos_cw(br * z, sz, cz);
@@ -2120,20 +2120,24 @@ __global__ void far3d_batch(const EvalArgs *args, int np)
 // takes n = na + l, na + l + 32, ... (phase e^{i alpha_n t} from a sincos and the
 // step e^{i 32 t}), and the lanes' sums are added by shuffles.
 // ---------------------------------------------------------------------------
-// Term n of (ei) without its factor i/(4pi): beta_n and E_n / beta_n,
-// E_n = e^{i alpha_n t + i beta_n |x2|} (p = e^{i alpha_n t} given).
-__device__ __forceinline__ void ei_term(double kk, double aa, double z, double2 p, double2 &beta, double2 &E)
+// Term n of (ei) without its factor i/(4pi): beta_n, E_n = e^{i alpha_n t + i beta_n
+// |x2|} (p = e^{i alpha_n t} given) and E_n / beta_n (beta_n = b or i b, so the
+// quotient is E/b or -i E/b).
+__device__ __forceinline__ void ei_term(double kk, double aa, double z, double2 p, double2 &beta, double2 &E,
+                                        double2 &term)
 {
     if (aa <= kk) {
-        const double b = sqrt((kk - aa) * (kk + aa));
+        const double b = sqrt((kk - aa) * (kk + aa)), ib = 1.0 / b;
         double sz, cz;
         sincos(b * z, &sz, &cz);
         beta = make_double2(b, 0.0);
         E = cmul(make_double2(cz, sz), p);
+        term = make_double2(E.x * ib, E.y * ib);
     } else {
-        const double b = sqrt((aa - kk) * (aa + kk));
+        const double b = sqrt((aa - kk) * (aa + kk)), ib = 1.0 / b;
         beta = make_double2(0.0, b);
         E = cscale(p, exp(-b * z));
+        term = make_double2(E.y * ib, -E.x * ib);
     }
 }
 
@@ -2142,14 +2146,16 @@ __device__ __forceinline__ void ei_term(double kk, double aa, double z, double2 
 // i sgn(x2) E_n; GF_OUT_HESSDIFF sums, over the indices of both wave numbers'
 // truncation sets, -alpha_n^2 (E_n/beta_n - E'_n/beta'_n), -alpha_n sgn (E_n - E'_n)
 // and -(beta_n E_n - beta'_n E'_n) (primes: k2).
-template <typename R>
+// OUT: the output kind (GF_OUT_G, GF_OUT_GRAD or GF_OUT_HESSDIFF), one kernel
+// instance each so that the plain G sum carries none of the others' registers.
+template <typename R, int OUT>
 __global__ void __launch_bounds__(128) far2d(EvalArgs a)
 {
     typedef typename cplx_t<R>::T C;
     C *out = reinterpret_cast<C *>(a.out);
     const int count = *a.far_count;
-    const int ne = n_entries(a.which);
-    const bool hess = a.which == GF_OUT_HESSDIFF, grad = a.which == GF_OUT_GRAD;
+    constexpr int ne = OUT == GF_OUT_G ? 1 : 3;
+    constexpr bool hess = OUT == GF_OUT_HESSDIFF, grad = OUT == GF_OUT_GRAD;
     const double kmax = (hess && a.k2 > a.k) ? a.k2 : a.k;
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -2168,27 +2174,28 @@ __global__ void __launch_bounds__(128) far2d(EvalArgs a)
         sincos(32.0 * t, &s32, &c32);
         double2 p = make_double2(cp, sp);
         const double2 step = make_double2(c32, s32);
-        double acc[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+        double acc[ne][2];
+#pragma unroll
+        for (int e = 0; e < ne; ++e) acc[e][0] = acc[e][1] = 0.0;
         for (int n = na + lane; n <= nb; n += 32, p = cmul(p, step)) {
             const double c1 = a.a1 + n;
             if (c1 * c1 > R2) continue;
             const double aa = fabs(c1);
-            double2 beta, E;
-            ei_term(a.k, aa, z, p, beta, E);
-            const double2 term = cdiv(E, beta);
-            if (!hess) {
+            double2 beta, E, term;
+            ei_term(a.k, aa, z, p, beta, E, term);
+            if constexpr (!hess) {
                 acc[0][0] += term.x;
                 acc[0][1] += term.y;
-                if (grad) {
+                if constexpr (grad) {
                     acc[1][0] -= c1 * term.y;  // i c1 term
                     acc[1][1] += c1 * term.x;
                     acc[2][0] -= sg * E.y;     // i sgn E
                     acc[2][1] += sg * E.x;
                 }
             } else {
-                double2 beta2, E2;
-                ei_term(a.k2, aa, z, p, beta2, E2);
-                const double2 d0 = csub(term, cdiv(E2, beta2)), d1 = csub(E, E2);
+                double2 beta2, E2, term2;
+                ei_term(a.k2, aa, z, p, beta2, E2, term2);
+                const double2 d0 = csub(term, term2), d1 = csub(E, E2);
                 const double2 d2 = csub(cmul(beta, E), cmul(beta2, E2));
                 acc[0][0] -= c1 * c1 * d0.x;
                 acc[0][1] -= c1 * c1 * d0.y;
@@ -2198,7 +2205,8 @@ __global__ void __launch_bounds__(128) far2d(EvalArgs a)
                 acc[2][1] -= d2.y;
             }
         }
-        for (int e = 0; e < 3; ++e)
+#pragma unroll
+        for (int e = 0; e < ne; ++e)
             for (int o = 16; o > 0; o >>= 1) {
                 acc[e][0] += __shfl_xor_sync(0xffffffffu, acc[e][0], o);
                 acc[e][1] += __shfl_xor_sync(0xffffffffu, acc[e][1], o);
@@ -2300,7 +2308,12 @@ cudaError_t launch_eval_t(const EvalArgs &a, cudaStream_t s, cudaEvent_t ev_mid,
         else
             near2d<R, 6><<<(int)blocks, 256, 0, s>>>(a);
         if (ev_mid) cudaEventRecord(ev_mid, s);
-        far2d<R><<<resident_grid<far2d<R>>(nsm), 128, 0, s>>>(a);
+        if (a.which == GF_OUT_GRAD)
+            far2d<R, GF_OUT_GRAD><<<resident_grid<far2d<R, GF_OUT_GRAD>>(nsm), 128, 0, s>>>(a);
+        else if (a.which == GF_OUT_HESSDIFF)
+            far2d<R, GF_OUT_HESSDIFF><<<resident_grid<far2d<R, GF_OUT_HESSDIFF>>(nsm), 128, 0, s>>>(a);
+        else
+            far2d<R, GF_OUT_G><<<resident_grid<far2d<R, GF_OUT_G>>(nsm), 128, 0, s>>>(a);
     } else if (a.nf == 1) {
         // with a near list: classify, then the near targets in full warps
         if (a.near_idx) {

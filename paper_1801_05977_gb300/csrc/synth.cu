@@ -309,7 +309,9 @@ __device__ void deriv_fields_2d(const SynthArgs &a, C *buf0, int TJ, int t, int 
         buf0[((3 + e) * TJ + t) * n + b] = cmk((R)((f[e] * dK.x - H[e]) * sc), (R)(f[e] * dK.y * sc));
 }
 
-template <typename R>
+// DERIV: the 2D derivative plans' instance (their extra fields, a second X'
+// table); a separate instance so that the other plans' kernel keeps its registers.
+template <typename R, bool DERIV>
 __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char *smem)
 {
     typedef typename cplx_t<R>::T C;
@@ -333,7 +335,7 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
     float *gcol = reinterpret_cast<float *>(qqf + n);
     int *cflag = reinterpret_cast<int *>(gcol + TJ);
     // 2D derivative plans with a second wave number: its A_m [TJ][Q] and beta [TJ]
-    const bool need_k2 = a.deriv && a.k2 > 0.0;
+    const bool need_k2 = DERIV && a.k2 > 0.0;
     double2 *Av2 = reinterpret_cast<double2 *>((reinterpret_cast<uintptr_t>(cflag + TJ) + 15) & ~(uintptr_t)15);
     double2 *betas2 = Av2 + TJ * Q;
     const int ncols = (a.dim == 3) ? a.M1 * a.M2 : a.M1;
@@ -565,14 +567,14 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
                 F1 = make_double2((1.0 + S0) / eta2, 0.0);
                 // F2 = (-2 i j1 F1 + Phi2-hat/(2 pi))/eta^2,  Phi2-hat/(2 pi) = -i (j1/eta) S1
                 F2 = make_double2(0.0, (-2.0 * jx * F1.x - ((double)jx / eta) * S1) / eta2);
-                if (a.deriv) deriv_fields_2d(a, buf0, TJ, t, n, b, jx, q, eta, F1.x, S1, K, A2, Av2 + t * Q, Em,
+                if (DERIV) deriv_fields_2d(a, buf0, TJ, t, n, b, jx, q, eta, F1.x, S1, K, A2, Av2 + t * Q, Em,
                                              need_k2 ? betas2[t] : make_double2(0.0, 0.0), pnl, x);
             }
-            if (a.deriv && eta2 == 0.0) deriv_fields_2d(a, buf0, TJ, t, n, b, jx, q, 0.0, F1.x, 0.0, K, A2, Av2 + t * Q,
+            if (DERIV && eta2 == 0.0) deriv_fields_2d(a, buf0, TJ, t, n, b, jx, q, 0.0, F1.x, 0.0, K, A2, Av2 + t * Q,
                                                         Em, need_k2 ? betas2[t] : make_double2(0.0, 0.0), 0, -1.0);
             // C = K - F1 + i alpha F2
             Cj = make_double2(K.x - F1.x - a.a1 * F2.y, K.y - F1.y + a.a1 * F2.x);
-            if (a.deriv) {
+            if (DERIV) {
                 Cj = cscale(Cj, a.invV);
                 buf0[t * n + b] = cmk((R)Cj.x, (R)Cj.y);
                 continue;
@@ -772,11 +774,11 @@ __device__ void synth_x1_body(const SynthArgs &a, int blk, unsigned char *smem, 
     }
 }
 
-template <typename R>
+template <typename R, bool DERIV>
 __global__ void __launch_bounds__(256) synth_first_pass(SynthArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    synth_first_pass_body<R>(a, blockIdx.x, smem);
+    synth_first_pass_body<R, DERIV>(a, blockIdx.x, smem);
 }
 
 template <typename R>
@@ -892,7 +894,7 @@ __global__ void __launch_bounds__(256) synth_first_pass_batch(const SynthArgs *a
         const int p = batch_pair(prefix, np, vb);
         if (threadIdx.x == 0) sa = args[p];
         __syncthreads();
-        synth_first_pass_body<R>(sa, vb - prefix[p], smem);
+        synth_first_pass_body<R, false>(sa, vb - prefix[p], smem);
         __syncthreads();
     }
 }
@@ -1061,9 +1063,16 @@ cudaError_t launch_synth_t(const SynthArgs &a0, cudaStream_t s)
     size_t sm[3];
     synth_config_t<R>(a, sizeof(R) == 4 ? 16 : 8, sm);
     const int ncols = (a.dim == 3) ? a.M1 * a.M2 : a.M1;
-    cudaError_t e = cudaFuncSetAttribute(synth_first_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[0]);
-    if (e != cudaSuccess) return e;
-    synth_first_pass<R><<<ncols / a.TJ, 256, sm[0], s>>>(a);
+    cudaError_t e;
+    if (a.deriv) {
+        e = cudaFuncSetAttribute(synth_first_pass<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[0]);
+        if (e != cudaSuccess) return e;
+        synth_first_pass<R, true><<<ncols / a.TJ, 256, sm[0], s>>>(a);
+    } else {
+        e = cudaFuncSetAttribute(synth_first_pass<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[0]);
+        if (e != cudaSuccess) return e;
+        synth_first_pass<R, false><<<ncols / a.TJ, 256, sm[0], s>>>(a);
+    }
     gf_count_launch(1);
     if (a.dim == 3) {
         e = launch_x2<R>(a, sm[1], s);
