@@ -221,7 +221,10 @@ gf_status gf_eval_points_host(gf_plan_t plan, const double *host_xyz, int64_t n,
  *   cuda_stream before use, and calls of this function whose work overlaps on
  *   the GPU (other streams, other threads) race on it and give wrong results;
  *   serialise them.  Calls of gf_eval_points on the same plan do not touch the
- *   array and may overlap with it.
+ *   array and may overlap with it.  The plan is only read (no per-plan state,
+ *   no fork/join events, so no lock is taken): calls of gf_eval_points and
+ *   gf_eval_grid on the same plan may run alongside; gf_destroy may not, as for
+ *   every other call on the plan.
  *   The device address found at the first call is kept for the life of the
  *   process: the library (this array, its memory pool and its side streams) is
  *   not usable across a cudaDeviceReset.
