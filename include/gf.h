@@ -178,10 +178,15 @@ size_t gf_grid_bytes(gf_plan_t plan);
  *             GF_OUT_GRAD and GF_OUT_HESSDIFF (GF_DERIV2D plans; the latter with k2 > 0)
  *   dev_out   n * entries complex values, [n][entries], device memory
  * The plan is not modified by an evaluation: each call takes its scratch (the
- * far- and near-branch target lists, 12 bytes per target plus 4 KiB) from the
- * library's stream-ordered memory pool on cuda_stream and returns it in stream
- * order, so calls on one plan may run concurrently on different streams and
- * threads.  For 3D double-precision Helmholtz plans
+ * far- and near-branch target lists, 12 bytes per target plus 4 KiB; for 3D
+ * plans also about 2.3 bytes per target of far-list counts and tickets and the
+ * far sums' slab partials, 4 * entries * (8 or 16) bytes per target for float or
+ * double plans) from the library's stream-ordered memory pool on cuda_stream
+ * and returns it in stream order, so calls on one plan may run concurrently on
+ * different streams and threads.  Results are reproducible: the same plan and
+ * targets give the same bits at every call (the far targets are grouped by a
+ * stable sort, and each far sum adds its row-slab partials in slab order).
+ * For 3D double-precision Helmholtz plans
  * part of the far series runs on a side stream that the library owns (one per
  * device): it waits for an event recorded on cuda_stream and cuda_stream waits
  * for its completion, so the call keeps the ordinary stream semantics.
@@ -225,6 +230,9 @@ gf_status gf_eval_points_host(gf_plan_t plan, const double *host_xyz, int64_t n,
  *   no fork/join events, so no lock is taken): calls of gf_eval_points and
  *   gf_eval_grid on the same plan may run alongside; gf_destroy may not, as for
  *   every other call on the plan.
+ *   The far sums' row slabs are added into the outputs atomically here (there
+ *   is no room for their partials), so results agree with gf_eval_points' to
+ *   rounding (about 1e-16 of max|G| for double plans), not bit for bit.
  *   The device address found at the first call is kept for the life of the
  *   process: the library (this array, its memory pool and its side streams) is
  *   not usable across a cudaDeviceReset.

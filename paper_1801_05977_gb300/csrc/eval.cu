@@ -104,6 +104,61 @@ __device__ __forceinline__ void add_out_f(float2 *o, float2 v)
     atomicAdd(&o->x, v.x);
     atomicAdd(&o->y, v.y);
 }
+__device__ __forceinline__ void add_c(double2 *o, double2 v) { add_out(o, v); }
+__device__ __forceinline__ void add_c(float2 *o, float2 v) { add_out_f(o, v); }
+
+// A far kernel's share (entries v[0 .. ne-1]) of target idx, from row slab `slab`
+// of `nslab` of chunk w.  With one slab per chunk, or no slab scratch, it is
+// added into the output at once.  Otherwise each slab stores its partials; the
+// chunk's last slab to finish (the one that draws the last ticket; nobody waits)
+// adds them up in slab order and deposits the total.  The output, zeroed by the
+// near pass, then receives one addend per far kernel (two at most), and a sum of
+// two terms onto zero is the same in either order: the result does not depend on
+// which slab or kernel finishes first.
+template <typename C, int NE>
+__device__ __forceinline__ void far_deposit(const EvalArgs &a, int kind, int w, int slab, int nslab, int nslot,
+                                            bool valid, int idx, int ne, const C (&v)[NE])
+{
+    C *o = reinterpret_cast<C *>(a.out) + (size_t)idx * ne;
+    C *buf = reinterpret_cast<C *>(a.slabbuf[kind]);
+    if (nslab <= 1 || buf == nullptr) {
+        if (valid)
+#pragma unroll
+            for (int e = 0; e < NE; ++e)
+                if (e < ne) add_c(o + e, v[e]);
+        return;
+    }
+    const int lane = threadIdx.x & 31;
+    const size_t slot = (size_t)w * 32 + lane;
+    if (valid)
+#pragma unroll
+        for (int e = 0; e < NE; ++e)
+            if (e < ne) buf[((size_t)slab * nslot + slot) * ne + e] = v[e];
+    __threadfence();
+    __syncwarp();
+    int last = 0;
+    if (lane == 0) last = atomicAdd(a.slabtick[kind] + w, 1) == nslab - 1;
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (!last || !valid) return;
+    __threadfence();
+#pragma unroll
+    for (int e = 0; e < NE; ++e) {
+        if (e >= ne) break;
+        C sum = __ldcg(buf + slot * ne + e);
+        for (int s = 1; s < nslab; ++s) sum = cadd(sum, __ldcg(buf + ((size_t)s * nslot + slot) * ne + e));
+        add_c(o + e, sum);
+    }
+}
+
+// Row slabs per chunk of a far launch, capped by the slab scratch (kind 0: the
+// main far kernel, 1: the float tails).
+__device__ __forceinline__ int far_slabs_capped(const EvalArgs &a, int kind, int nch, int S)
+{
+    if (a.slabbuf[kind] == nullptr || nch <= 0) return S;
+    const int64_t fit = a.slabcap / ((int64_t)nch * 32);
+    return (int)(fit < 1 ? 1 : (fit < S ? fit : S));
+}
+
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b)
 {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -139,6 +194,12 @@ __device__ __forceinline__ void push_far(bool isfar, int i, int *list, int *coun
     if (isfar) list[base + __popc(mask & ((1u << lane) - 1u))] = i;
 }
 
+// Adds the number of lanes that vote `take` to *count (one atomic per warp).
+__device__ __forceinline__ void count_votes(bool take, int *count)
+{
+    unsigned mask = __ballot_sync(0xffffffffu, take);
+    if (mask != 0u && (threadIdx.x & 31) == __ffs(mask) - 1) atomicAdd(count, __popc(mask));
+}
 __device__ __forceinline__ int far_bucket(double z, double c)
 {
     double r = (double)GF_FAR_BUCKETS * c / z;
@@ -446,7 +507,13 @@ __device__ void near3d_tiles(const EvalArgs &a, int64_t base0, int64_t stride, i
         // far targets inside the far-region grid's slab are gathered, not summed
         const bool fgrid = isfar && a.fargrid != nullptr && fabs(x3) <= a.fzmax;
         if (fgrid) isfar = false;
-        push_far(isfar, (int)i, a.far_idx, a.far_count);
+        if (a.seghist) {
+            // stable far list: the bucket code here, the list laid out afterwards
+            count_votes(isfar, a.far_count);
+            if (i < a.n) a.far_idx[i] = isfar ? far_bucket(fabs(x3), a.c) : -1;
+        } else {
+            push_far(isfar, (int)i, a.far_idx, a.far_count);
+        }
         // (every lane of the warp reaches the appends: they vote by ballot)
         if (MODE == 1) {
             push_far(valid && finite && !isfar && !fgrid, (int)i, a.near_idx, a.far_count + GF_NEAR_SLOT);
@@ -673,10 +740,12 @@ __global__ void __launch_bounds__(256) near2d(EvalArgs a)
 // radius first (bucket NB-1 first), so that warps see homogeneous lanes and
 // the heaviest targets are scheduled first.
 // ---------------------------------------------------------------------------
-__device__ void far_scatter_body(const EvalArgs &a, int blk, int nblk, int *off)
+// Start of each bucket's run in the far list, the buckets in descending order
+// (nearest the slab first), from the counts a.far_count[1 + b]; called by all
+// threads of the block, by one warp: lane l takes the descending positions
+// l PER .. l PER + PER - 1.
+__device__ void far_bucket_starts(const EvalArgs &a, int *off)
 {
-    // exclusive prefix of the bucket sizes in descending bucket order, by one
-    // warp: lane l takes the descending positions l PER .. l PER + PER - 1
     static_assert(GF_FAR_BUCKETS % 32 == 0, "bucket count: a multiple of 32");
     if (threadIdx.x < 32) {
         constexpr int PER = GF_FAR_BUCKETS / 32;
@@ -701,6 +770,13 @@ __device__ void far_scatter_body(const EvalArgs &a, int blk, int nblk, int *off)
         }
     }
     __syncthreads();
+}
+
+// Bucket sort of the appended far list (the batched sweeps): positions within a
+// bucket in the order of the cursor atomics.
+__device__ void far_scatter_body(const EvalArgs &a, int blk, int nblk, int *off)
+{
+    far_bucket_starts(a, off);
     const int count = a.far_count[0];
     int *cursor = a.far_count + 1 + GF_FAR_BUCKETS;
     for (int i = blk * blockDim.x + threadIdx.x; i < count; i += nblk * blockDim.x) {
@@ -709,6 +785,85 @@ __device__ void far_scatter_body(const EvalArgs &a, int blk, int nblk, int *off)
         int b = far_bucket(z, a.c);
         int pos = off[b] + atomicAdd(&cursor[b], 1);
         a.far_sorted[pos] = idx;
+    }
+}
+
+// Stable counting sort of the far targets (single-plan evaluations), from the
+// bucket codes the classification pass left in a.far_idx: the far kernels' warps
+// take 32 consecutive list entries and set their truncation and precision bands
+// from them, so a list that is the same from call to call makes the sums the same
+// bit for bit.  Three passes over segments of a.segsize targets, one warp each:
+// counts per segment and bucket, their exclusive scan over the segments (per
+// bucket, from the bucket's start), and the scatter in index order.
+__global__ void __launch_bounds__(256) far_seg_count(EvalArgs a)
+{
+    __shared__ int h[8][GF_FAR_BUCKETS];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int seg = blockIdx.x * 8 + w;
+    if (seg >= a.nseg) return;
+    for (int b = lane; b < GF_FAR_BUCKETS; b += 32) h[w][b] = 0;
+    __syncwarp();
+    const int64_t i0 = (int64_t)seg * a.segsize, i1 = min(i0 + (int64_t)a.segsize, a.n);
+    for (int64_t i = i0 + lane; i < i1; i += 32) {
+        const int c = a.far_idx[i];
+        if (c >= 0) atomicAdd(&h[w][c], 1);
+    }
+    __syncwarp();
+    int *dst = a.seghist + (size_t)seg * GF_FAR_BUCKETS;
+    for (int b = lane; b < GF_FAR_BUCKETS; b += 32) dst[b] = h[w][b];
+}
+
+// One block per 32 buckets (a lane each), 32 warps over contiguous ranges of
+// segments: each warp's sum, the warps' exclusive prefix, then the running
+// position written back over the counts.
+__global__ void __launch_bounds__(1024) far_seg_scan(EvalArgs a)
+{
+    __shared__ int start[GF_FAR_BUCKETS];
+    __shared__ int part[32][32];
+    far_bucket_starts(a, start);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.x * 32 + lane;
+    const int per = (a.nseg + 31) / 32;
+    const int s0 = min(w * per, a.nseg), s1 = min(s0 + per, a.nseg);
+    int *col = a.seghist + b;
+    int sum = 0;
+    for (int sg = s0; sg < s1; ++sg) sum += col[(size_t)sg * GF_FAR_BUCKETS];
+    part[w][lane] = sum;
+    __syncthreads();
+    int run = start[b];
+    for (int v = 0; v < w; ++v) run += part[v][lane];
+    for (int sg = s0; sg < s1; ++sg) {
+        const int c = col[(size_t)sg * GF_FAR_BUCKETS];
+        col[(size_t)sg * GF_FAR_BUCKETS] = run;
+        run += c;
+    }
+}
+
+// Each warp walks its segment in index order, 32 targets a step: the lanes with
+// the same bucket take consecutive positions from the segment's running start.
+__global__ void __launch_bounds__(256) far_seg_scatter(EvalArgs a)
+{
+    __shared__ int pos0[8][GF_FAR_BUCKETS];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int seg = blockIdx.x * 8 + w;
+    if (seg >= a.nseg) return;
+    const int *src = a.seghist + (size_t)seg * GF_FAR_BUCKETS;
+    for (int b = lane; b < GF_FAR_BUCKETS; b += 32) pos0[w][b] = src[b];
+    __syncwarp();
+    const unsigned below = (1u << lane) - 1u;
+    const int64_t i0 = (int64_t)seg * a.segsize, i1 = min(i0 + (int64_t)a.segsize, a.n);
+    for (int64_t j = i0; j < i1; j += 32) {
+        const int64_t i = j + lane;
+        const int c = i < i1 ? a.far_idx[i] : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, c);
+        const int before = __popc(peers & below);
+        const int pos = c >= 0 ? pos0[w][c] + before : 0;
+        __syncwarp();
+        if (c >= 0) {
+            a.far_sorted[pos] = (int)i;
+            if (before == 0) pos0[w][c] += __popc(peers);
+        }
+        __syncwarp();
     }
 }
 
@@ -1730,7 +1885,6 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, i
                 far_row_tails<NH, NS>(n2a, n2b, ca, cb, N0, a2f, c1f, c1sq, k2f, zf, VP, PF, (float)A.x, (float)A.y,
                                       ik2f, Sf);
         }
-        if (!L.valid) return;
         if (NH == 1) {
             // right: sum = D + U (-lambda/2 + i sin theta), U = s (B - D);
             // left, after the zero step: sum = s D + B (lambda/2 - i sin theta)
@@ -1754,12 +1908,14 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, i
         double sN, cN;
         sincos(fma(2.0 * GF_PI, ph2, (a.a2 + N0) * L.t2), &sN, &cN);
         const double2 pre = make_double2(-sN / (8.0 * GF_PI * GF_PI), cN / (8.0 * GF_PI * GF_PI));
-        double2 *o = out + (size_t)L.idx * ne;
         // evanescent sums carry the factor -i (from 1/beta = -i/b), except the
         // xz, yz entries whose factor (-i)(-i sgn) = -sgn is real
+        constexpr int NE = NF == 1 ? 1 : 7;
+        double2 vals[NE];
         if (NF == 1) {
-            add_out(o, cmul(pre, make_double2(P[0][0] + S[0][1], P[0][1] - S[0][0])));
+            vals[0] = cmul(pre, make_double2(P[0][0] + S[0][1], P[0][1] - S[0][0]));
         } else {
+#pragma unroll
             for (int e = 0; e < 6; ++e) {
                 const double *s = S[1 + e];
                 double2 v;
@@ -1767,10 +1923,12 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, i
                     v = make_double2(P[1 + e][0] + s[1], P[1 + e][1] - s[0]);
                 else
                     v = make_double2(P[1 + e][0] + L.sg * s[0], P[1 + e][1] + L.sg * s[1]);
-                add_out(o + e, cmul(pre, v));
+                vals[e] = cmul(pre, v);
             }
-            if (a.which == GF_OUT_MAXWELL7) add_out(o + 6, cmul(pre, make_double2(P[0][0] + S[0][1], P[0][1] - S[0][0])));
+            vals[NE - 1] = cmul(pre, make_double2(P[0][0] + S[0][1], P[0][1] - S[0][0]));
         }
+        far_deposit(a, 0, w, slab, nslab, ((count + 31) >> 5) * 32, L.valid, L.idx, ne, vals);
+        (void)out;
     }
 }
 
@@ -1803,7 +1961,7 @@ template <int NF, bool TAILS>
 __global__ void __launch_bounds__(128, NF == 1 ? 5 : 1) far3d_f64(EvalArgs a)
 {
     const int count = a.far_count[0];
-    const int nch = (count + 31) >> 5, S = far_slabs(nch, 8);
+    const int nch = (count + 31) >> 5, S = far_slabs_capped(a, 0, nch, far_slabs(nch, 8));
     int *ctr = a.far_count + GF_WORK_SLOT;
     for (int t = far_take(ctr, nch * S); t >= 0; t = far_take(ctr, nch * S))
         far3d_f64_chunk<NF, TAILS>(a, nch - 1 - t / S, count, t % S, S);
@@ -1864,7 +2022,6 @@ __device__ void far3d_tail_chunk(const EvalArgs &a, int w, int count, int slab, 
         far_row_tails<NH, NS>(n2a, n2b, ca, cb, N0, W.a2f, c1f, c1sq, k2f, zf, VP, P2, A0x * cn - A0y * sn,
                               A0x * sn + A0y * cn, ik2f, Sf);
     }
-    if (!L.valid) return;
 #pragma unroll
     for (int e = 0; e < NS; ++e) {
         S[e][0] += f2d_exact(Sf[e][0]);
@@ -1879,24 +2036,28 @@ __device__ void far3d_tail_chunk(const EvalArgs &a, int w, int count, int slab, 
     sincos_cw((float)fma(2.0 * GF_PI, ph2, (a.a2 + N0) * L.t2), sNf, cNf);
     constexpr double i8pi2 = 1.0 / (8.0 * GF_PI * GF_PI);
     const double2 pre = make_double2(-f2d_exact(sNf) * i8pi2, f2d_exact(cNf) * i8pi2);
-    double2 *o = out + (size_t)L.idx * ne;
+    constexpr int NE = NF == 1 ? 1 : 7;
+    double2 vals[NE];
     if (NF == 1) {
-        add_out(o, cmul(pre, make_double2(S[0][1], -S[0][0])));
+        vals[0] = cmul(pre, make_double2(S[0][1], -S[0][0]));
     } else {
+#pragma unroll
         for (int e = 0; e < 6; ++e) {
             const double *s = S[1 + e];
             const double2 v = e < 4 ? make_double2(s[1], -s[0]) : make_double2(L.sg * s[0], L.sg * s[1]);
-            add_out(o + e, cmul(pre, v));
+            vals[e] = cmul(pre, v);
         }
-        if (a.which == GF_OUT_MAXWELL7) add_out(o + 6, cmul(pre, make_double2(S[0][1], -S[0][0])));
+        vals[NE - 1] = cmul(pre, make_double2(S[0][1], -S[0][0]));
     }
+    far_deposit(a, 1, w, slab, nslab, ((count + 31) >> 5) * 32, L.valid, L.idx, ne, vals);
+    (void)out;
 }
 
 template <int NF>
 __global__ void __launch_bounds__(128) far3d_tail(EvalArgs a)
 {
     const int count = a.far_count[0];
-    const int nch = (count + 31) >> 5, S = far_slabs(nch, 8);
+    const int nch = (count + 31) >> 5, S = far_slabs_capped(a, 1, nch, far_slabs(nch, 8));
     int *ctr = a.far_count + GF_TAIL_SLOT;
     for (int t = far_take(ctr, nch * S); t >= 0; t = far_take(ctr, nch * S))
         far3d_tail_chunk<NF>(a, nch - 1 - t / S, count, t % S, S);
@@ -2040,7 +2201,6 @@ __device__ void far3d_f32_chunk(const EvalArgs &a, int w, int count, int slab, i
                 S[6][1] += -ik2 * r[5][1];
             }
         }
-        if (!valid) return;
         // e^{i 2pi <alpha.m>} (i/8pi^2): the fractional part in double, the phase in float
         double ph = a.a1 * m1 + a.a2 * m2;
         ph -= rint(ph);
@@ -2048,10 +2208,12 @@ __device__ void far3d_f32_chunk(const EvalArgs &a, int w, int count, int slab, i
         sincospif(2.0f * (float)ph, &sl, &cl);
         const float sc = (float)(1.0 / (8.0 * GF_PI * GF_PI));
         const float2 pre = make_float2(-sl * sc, cl * sc);
-        float2 *o = out + (size_t)idx * ne;
+        constexpr int NE = NF == 1 ? 1 : 7;
+        float2 vals[NE];
         if (NF == 1) {
-            add_out_f(o, cmulf(pre, make_float2(P[0][0] + S[0][1], P[0][1] - S[0][0])));
+            vals[0] = cmulf(pre, make_float2(P[0][0] + S[0][1], P[0][1] - S[0][0]));
         } else {
+#pragma unroll
             for (int e = 0; e < 6; ++e) {
                 const float *s = S[1 + e];
                 float2 v;
@@ -2059,11 +2221,12 @@ __device__ void far3d_f32_chunk(const EvalArgs &a, int w, int count, int slab, i
                     v = make_float2(P[1 + e][0] + s[1], P[1 + e][1] - s[0]);
                 else
                     v = make_float2(P[1 + e][0] + sg * s[0], P[1 + e][1] + sg * s[1]);
-                add_out_f(o + e, cmulf(pre, v));
+                vals[e] = cmulf(pre, v);
             }
-            if (a.which == GF_OUT_MAXWELL7)
-                add_out_f(o + 6, cmulf(pre, make_float2(P[0][0] + S[0][1], P[0][1] - S[0][0])));
+            vals[NE - 1] = cmulf(pre, make_float2(P[0][0] + S[0][1], P[0][1] - S[0][0]));
         }
+        far_deposit(a, 0, w, slab, nslab, ((count + 31) >> 5) * 32, valid, idx, ne, vals);
+        (void)out;
     }
 }
 
@@ -2071,7 +2234,7 @@ template <int NF>
 __global__ void __launch_bounds__(128) far3d_f32(EvalArgs a)
 {
     const int count = a.far_count[0];
-    const int nch = (count + 31) >> 5, S = far_slabs(nch, 4);
+    const int nch = (count + 31) >> 5, S = far_slabs_capped(a, 0, nch, far_slabs(nch, 4));
     int *ctr = a.far_count + GF_WORK_SLOT;
     for (int t = far_take(ctr, nch * S); t >= 0; t = far_take(ctr, nch * S))
         far3d_f32_chunk<NF>(a, nch - 1 - t / S, count, t % S, S);
@@ -2291,6 +2454,20 @@ cudaError_t launch_far_f64(const EvalArgs &a, int nsm, cudaStream_t s, const Eva
     return cudaStreamWaitEvent(s, fork->join, 0);
 }
 
+// The far list, bucket-sorted: stable when the evaluation brought segment
+// scratch, else from the appended list.
+void launch_far_list(const EvalArgs &a, int nsm, cudaStream_t s)
+{
+    if (a.seghist) {
+        const int blocks = (a.nseg + 7) / 8;
+        far_seg_count<<<blocks, 256, 0, s>>>(a);
+        far_seg_scan<<<GF_FAR_BUCKETS / 32, 1024, 0, s>>>(a);
+        far_seg_scatter<<<blocks, 256, 0, s>>>(a);
+    } else {
+        far_scatter<<<nsm * 2, 256, 0, s>>>(a);
+    }
+}
+
 template <typename R>
 cudaError_t launch_eval_t(const EvalArgs &a, cudaStream_t s, cudaEvent_t ev_mid, const EvalFork *fork)
 {
@@ -2323,7 +2500,7 @@ cudaError_t launch_eval_t(const EvalArgs &a, cudaStream_t s, cudaEvent_t ev_mid,
             near3d<R, 1><<<(int)blocks, 256, 0, s>>>(a);
         }
         if (ev_mid) cudaEventRecord(ev_mid, s);
-        far_scatter<<<nsm * 2, 256, 0, s>>>(a);
+        launch_far_list(a, nsm, s);
         if (sizeof(R) == 8) {
             cudaError_t e = launch_far_f64<1>(a, nsm, s, fork);
             if (e != cudaSuccess) return e;
@@ -2337,14 +2514,14 @@ cudaError_t launch_eval_t(const EvalArgs &a, cudaStream_t s, cudaEvent_t ev_mid,
             near3d<R, 7><<<(int)blocks, 256, 0, s>>>(a);
         }
         if (ev_mid) cudaEventRecord(ev_mid, s);
-        far_scatter<<<nsm * 2, 256, 0, s>>>(a);
+        launch_far_list(a, nsm, s);
         if (sizeof(R) == 8) {
             cudaError_t e = launch_far_f64<7>(a, nsm, s, fork);
             if (e != cudaSuccess) return e;
         } else
             far3d_f32<7><<<resident_grid<far3d_f32<7>>(nsm), 128, 0, s>>>(a);
     }
-    gf_count_launch(a.dim == 2 ? 2 : (sizeof(R) == 8 ? 4 : 3) + (a.near_idx ? 1 : 0));
+    gf_count_launch(a.dim == 2 ? 2 : (sizeof(R) == 8 ? 4 : 3) + (a.near_idx ? 1 : 0) + (a.seghist ? 2 : 0));
     return cudaGetLastError();
 }
 

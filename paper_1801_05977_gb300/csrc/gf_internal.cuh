@@ -185,10 +185,26 @@ struct EvalArgs {
     const double *x;    // [n][dim]
     void *out;          // [n][entries]
     int64_t n;
-    int *far_idx;       // scratch: far-branch target indices, in append order
+    int *far_idx;       // scratch: far-branch target indices, in append order; with
+                        // seghist, each target's far bucket instead (-1: not summed)
     int *far_sorted;    // scratch: the same indices ordered by |x_last| bucket (3D)
     int *far_count;     // scratch counters (GF_SCRATCH_COUNTERS ints, zero before each evaluation)
     int *near_idx;      // scratch (3D, may be null): near-branch target indices, in append order
+    // far-series slab partials (3D, may be null): [0] for the main far kernel, [1] for
+    // the float-tail kernel, each [slab][slot][entries] with slabcap slots per slab set
+    // in all (a launch uses at most slabcap / slots-per-slab slabs), and one ticket
+    // per 32-target chunk, zero before the evaluation.  Null: slab results are added
+    // into the output atomically (in a run-dependent order)
+    void *slabbuf[2];
+    int *slabtick[2];
+    int64_t slabcap;
+    // stable far list (3D, may be null): per segment of segsize consecutive targets
+    // its far-bucket counts, then the segment's first position in far_sorted for each
+    // bucket ([nseg][GF_FAR_BUCKETS]); far_sorted then lists the far targets by
+    // descending bucket and ascending index.  Null: the list comes out in the order
+    // of the appends (run-dependent)
+    int *seghist;
+    int segsize, nseg;
     const void *btab;   // far-series table [n1][n2] (BetaEntry or BetaEntryF)
     int n1lo, n1hi, n2lo, n2hi;
     const PropEntry *prop;  // propagating indices (|alpha_n| <= k)

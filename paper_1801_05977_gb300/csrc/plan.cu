@@ -701,10 +701,23 @@ gf_status gf_eval_grid(gf_plan_t p, void *dev_out, size_t out_bytes, void *cuda_
 }
 
 // Scratch of one evaluation (ints): the counters, padded to GF_COUNTER_PAD, then
-// the far list in append order, the bucket-sorted far list and the near list,
-// n entries each.
+// the far list in append order (3D: the targets' bucket codes), the bucket-sorted
+// far list and the near list, n entries each; for 3D plans then one ticket per
+// 32-target chunk for each of the two far kernels, the segment counts of the
+// stable far list and, 256-byte aligned, the far kernels' slab partials (2 n_pad
+// target slots of the output's entries each).  With these the far sums are the
+// same bit for bit from call to call: the same list, and slab partials added in
+// slab order.
 constexpr int64_t GF_COUNTER_PAD = 1024;
 static_assert(GF_SCRATCH_COUNTERS <= GF_COUNTER_PAD, "counter block too small");
+
+// Segments of the stable far list: 512 targets, more when that would make over
+// 8192 segments (the scan's work per bucket stays bounded).
+static int64_t far_segment_size(int64_t n)
+{
+    const int64_t segs = (n + 511) / 512;
+    return segs <= 8192 ? 512 : ((n + 8191) / 8192 + 31) / 32 * 32;
+}
 
 gf_status gf_eval_points(gf_plan_t p, const double *dev_xyz, int64_t n, int which, void *dev_out,
                          void *cuda_stream)
@@ -716,13 +729,30 @@ gf_status gf_eval_points(gf_plan_t p, const double *dev_xyz, int64_t n, int whic
     // per-call scratch from the stream-ordered pool on the caller's stream, returned
     // to the pool in stream order after the kernels: concurrent calls on other
     // streams each have their own, and the plan stays unchanged
+    const bool slabs = p->dim == 3;
+    const int64_t npad = (n + 31) / 32 * 32, nchmax = npad / 32, slabcap = 2 * npad;
+    const int64_t segsize = far_segment_size(n), nseg = (n + segsize - 1) / segsize;
+    const size_t ints = (size_t)(GF_COUNTER_PAD + 3 * n + (slabs ? 2 * nchmax + nseg * GF_FAR_BUCKETS : 0));
+    const size_t off_buf = (sizeof(int) * ints + 255) / 256 * 256;
+    const size_t buf_bytes = slabs ? (size_t)slabcap * gf_out_entries(which) * p->elem : 0;
     int *scratch = nullptr;
-    CU(gf_dev_alloc((void **)&scratch, sizeof(int) * (GF_COUNTER_PAD + 3 * n), st));
+    CU(gf_dev_alloc((void **)&scratch, off_buf + 2 * buf_bytes, st));
     a.far_count = scratch;
     a.far_idx = scratch + GF_COUNTER_PAD;
     a.far_sorted = a.far_idx + n;
     a.near_idx = p->dim == 3 ? a.far_idx + 2 * n : nullptr;
     cudaError_t e = cudaMemsetAsync(a.far_count, 0, sizeof(int) * GF_SCRATCH_COUNTERS, st);
+    if (slabs && e == cudaSuccess) {
+        a.slabtick[0] = a.far_idx + 3 * n;
+        a.slabtick[1] = a.slabtick[0] + nchmax;
+        a.slabbuf[0] = (char *)scratch + off_buf;
+        a.slabbuf[1] = (char *)scratch + off_buf + buf_bytes;
+        a.slabcap = slabcap;
+        a.seghist = a.slabtick[1] + nchmax;
+        a.segsize = (int)segsize;
+        a.nseg = (int)nseg;
+        e = cudaMemsetAsync(a.slabtick[0], 0, sizeof(int) * 2 * nchmax, st);
+    }
     if (e == cudaSuccess) {
         std::lock_guard<std::mutex> lk(p->mu);
         // 3D double-precision Helmholtz plans run the far series' double sums and
