@@ -1560,6 +1560,7 @@ struct FarWarp {
     double izmax;      // 1/z_min over the warp's lanes
     float R2mf, Rc2f;  // truncation disk |alpha_n|^2 <= R2m (warp maximum) and core disk Rc2
     float a1f, a2f;
+    float k2f, bff;    // k^2; the float-float band edge b >= bff = bmin + FF_GAP/z_min (Helmholtz)
     int n1a, n1b;      // rows of the truncation disk (one index of margin)
     int N0;            // anchor n2 = rint(-alpha_2)
 };
@@ -1579,7 +1580,19 @@ __device__ __forceinline__ FarWarp far_warp(const EvalArgs &a, const FarLane &L)
     W.n1a = max(a.n1lo, (int)floorf(__fsub_rn(-W.a1f, Rmf)) - 1);
     W.n1b = min(a.n1hi, (int)ceilf(__fadd_rn(-W.a1f, Rmf)) + 1);
     W.N0 = (int)rint(-a.a2);
+    W.k2f = __double2float_rn(__dmul_rn(a.k, a.k));
+    W.bff = __double2float_rn(__fma_rn((double)FF_GAP, W.izmax, a.bmin));
     return W;
+}
+
+// Row n1 of the float-float band edge (Helmholtz): q^2 = bff^2 + k^2 - c1^2 raised
+// by more than the float roundings of its parts (1e-5 of their sizes, and 1e-3),
+// so that every term with |c2| >= sqrt(q^2) has b >= bff (below zero: the whole
+// row lies in the band).
+__device__ __forceinline__ float far_ff_q2(const FarWarp &W, float c1sq)
+{
+    const float qq = __fmaf_rn(W.bff, W.bff, W.k2f);
+    return __fadd_rn(__fmaf_rn(1e-5f, __fadd_rn(qq, c1sq), 1e-3f), __fsub_rn(qq, c1sq));
 }
 
 // Row n1 of the warp's truncation disk: its index range [n2a, n2b] (false when
@@ -1698,8 +1711,7 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, i
         // decreases in b): degree B from b >= bmin + EXP_GAP_B/z_min, C from
         // bmin + EXP_GAP_C/z_min
         const float b4 = (float)(a.bmin + EXP_GAP_B * izmax), b3 = (float)(a.bmin + EXP_GAP_C * izmax);
-        // Helmholtz: the float-float band from b >= bmin + FF_GAP/z_min
-        const float bff = (float)(a.bmin + (double)FF_GAP * izmax);
+        // Helmholtz: the float-float band from b >= W.bff = bmin + FF_GAP/z_min
         const FF zff = ff_split(L.z), lamff = ff_split(RS.lam);
         const float sgn = RS.m ? -1.0f : 1.0f;
         const float k2f = (float)k2;
@@ -1819,13 +1831,14 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, i
                 RState<NH> R, Lt;
 #pragma unroll
                 for (int e = 0; e < NH; ++e) R.d[e] = R.b[e] = Lt.d[e] = Lt.b[e] = 0.0;
-                // degree bands (Maxwell): |c2| >= q3 (degree C), >= q4 (degree B);
-                // Helmholtz: |c2| >= qff (float-float); one index of margin
+                // degree bands (Maxwell): |c2| >= q3 (degree C), >= q4 (degree B),
+                // one index of margin; Helmholtz: |c2| >= qff (float-float, from
+                // far_ff_q2: no term with b < bff leaves the double band, no margin)
                 const float q3 = sqrtf(fmaxf(b3 * b3 + k2f - c1sq, 0.f)), q4 = sqrtf(fmaxf(b4 * b4 + k2f - c1sq, 0.f));
-                const float qff = sqrtf(fmaxf(bff * bff + k2f - c1sq, 0.f));
+                const float qff = sqrtf(fmaxf(far_ff_q2(W, c1sq), 0.f));
                 if (NH == 1) {
                     const int tot = cb - N0 + 1;
-                    const int mff = max(0, cb - max((int)ceilf(qff - a2f) + 1, N0) + 1);
+                    const int mff = max(0, cb - max((int)ceilf(qff - a2f), N0) + 1);
                     reinsch_run_ff(*reinterpret_cast<RState<1> *>(&R), row, cb, -1, mff, tot - mff, c1sq, a2f, R2f, L.z,
                                    zff, RS, lamff, sgn, T, j0, jmax);
                     DR.x = fma(A.x, R.d[0], DR.x);
@@ -1833,7 +1846,7 @@ __device__ void far3d_f64_chunk(const EvalArgs &a, int w, int count, int slab, i
                     BR.x = fma(A.x, R.b[0], BR.x);
                     BR.y = fma(A.y, R.b[0], BR.y);
                     if (ca < N0) {
-                        const int mffl = max(0, min((int)floorf(-qff - a2f) - 1, N0 - 1) - ca + 1);
+                        const int mffl = max(0, min((int)floorf(-qff - a2f), N0 - 1) - ca + 1);
                         reinsch_run_ff(*reinterpret_cast<RState<1> *>(&Lt), row, ca, 1, mffl, N0 - ca - mffl, c1sq, a2f,
                                        R2f, L.z, zff, RS, lamff, sgn, T, j0, jmax);
                         DL.x = fma(A.x, Lt.d[0], DL.x);
@@ -1977,6 +1990,7 @@ __global__ void __launch_bounds__(128, NF == 1 ? 5 : 1) far3d_f64(EvalArgs a)
 // transcendental pipes.  The per-target set-up and the lattice phase are in
 // double; the row phase e^{i c1 t1} = e^{i alpha_1 t1} e^{i n1 t1} in float.
 // ---------------------------------------------------------------------------
+
 template <int NF>
 __device__ void far3d_tail_chunk(const EvalArgs &a, int w, int count, int slab, int nslab)
 {
