@@ -413,11 +413,18 @@ gf_status gf_release_memory(void);
  * FP64 (pipe = GF_PROBE_FP64) or FP32 (GF_PROBE_FP32) pipe's rate, which the
  * far-series roofline divides by.  The caller times the launch on cuda_stream
  * (CUDA events) and divides *flops (host; an FMA counts 2) by the time.
- *   iters     loop trips per thread (each trip is 64 FMAs per thread), >= 1
+ * The overlap modes run FP64 chains on the even warps and FP32 chains
+ * (GF_PROBE_FP32_PER_FP64 times as many trips) on the odd ones: only the FP64
+ * half (GF_PROBE_FP64_HALF), only the FP32 half (GF_PROBE_FP32_HALF) or both
+ * (GF_PROBE_BOTH_HALVES); both taking the longer of the halves' times means
+ * the two pipes overlap, their sum that they do not.
+ *   iters     loop trips per thread (each trip is 64 FMAs per thread),
+ *             1 <= iters <= 2^20
  *   dev_sink  device buffer of at least 8 bytes (written only to keep the
  *             chains alive; its content is meaningless)
  * Errors: GF_ERR_ARG, GF_ERR_CUDA. */
-enum { GF_PROBE_FP64 = 0, GF_PROBE_FP32 = 1 };
+enum { GF_PROBE_FP64 = 0, GF_PROBE_FP32 = 1, GF_PROBE_FP64_HALF = 2, GF_PROBE_FP32_HALF = 3, GF_PROBE_BOTH_HALVES = 4 };
+#define GF_PROBE_FP32_PER_FP64 64
 gf_status gf_peak_probe(int pipe, int64_t iters, void *dev_sink, int64_t *flops, void *cuda_stream);
 
 /* Self-test of the bounded device waits (diagnostic; the paper has no

@@ -827,11 +827,13 @@ __global__ void __launch_bounds__(1024) far_seg_scan(EvalArgs a)
     const int s0 = min(w * per, a.nseg), s1 = min(s0 + per, a.nseg);
     int *col = a.seghist + b;
     int sum = 0;
+#pragma unroll 8
     for (int sg = s0; sg < s1; ++sg) sum += col[(size_t)sg * GF_FAR_BUCKETS];
     part[w][lane] = sum;
     __syncthreads();
     int run = start[b];
     for (int v = 0; v < w; ++v) run += part[v][lane];
+#pragma unroll 8
     for (int sg = s0; sg < s1; ++sg) {
         const int c = col[(size_t)sg * GF_FAR_BUCKETS];
         col[(size_t)sg * GF_FAR_BUCKETS] = run;
@@ -1183,28 +1185,30 @@ struct RStateFF {
 constexpr float FF_GAP = 8.0f;
 
 // One float-float Reinsch step with the term n2 (weight 0 outside the lane's
-// truncation set).
+// truncation set).  Lazy form: the high words follow the recurrence in plain
+// float, d' = (lambda b + w) + s d, b' = d' + s b; their rounding errors, exact
+// by TwoProd and TwoSum, go into the low words, which follow the same
+// recurrence.  The caller renormalizes the pairs every second step, so a low
+// word stays within a few units of the high word's last place, while the high
+// words' dependency chain is four float operations per term (a normalized
+// float-float step chains about a dozen).
 __device__ __forceinline__ void ff_step(RStateFF &st, const BetaEntry *__restrict__ row, int n2, float c2f,
                                         float c1sq, float R2f, FF z, FF lam, float sf, const float4 *__restrict__ T,
                                         int j0, int jmax)
 {
     const float4 q = *reinterpret_cast<const float4 *>(&row[n2].bf);  // b hi, lo; ln b hi, lo
     const bool ok = fmaf(c2f, c2f, c1sq) <= R2f && q.x != 0.f;
-    // y = b z + ln b
     const float p = __fmul_rn(q.x, z.h);
     float pe = __fmaf_rn(q.x, z.h, -p);
     pe = __fmaf_rn(q.x, z.l, __fmaf_rn(q.y, z.h, pe));
     const FF y0 = two_sum(p, q.z);
     const FF y = two_sum(y0.h, __fadd_rn(__fadd_rn(y0.l, pe), q.w));
-    // table entry nearest to y
     const float jm = __fmaf_rn((float)GF_EXPTAB_STEPS, y.h, 12582912.0f);
     const int idx = min(max(__float_as_int(jm) - 0x4B400000 + j0, 0), jmax);
     const float4 t = __ldg(T + idx);
-    // r = (y.h - y_j) + y.l (the first difference is exact)
     const float rh = __fsub_rn(y.h, t.z);
     const float rs = __fadd_rn(rh, y.l);
     const float qq = __fmul_rn(__fmul_rn(rs, rs), __fmaf_rn(rs, -1.0f / 6.0f, 0.5f));
-    // e^{-r} = (1 - rh) - y.l + qq, then w = T[j] e^{-r}
     const FF a = two_sum(1.0f, -rh);
     const float al = __fadd_rn(__fsub_rn(a.l, y.l), qq);
     float wh = __fmul_rn(t.x, a.h);
@@ -1212,21 +1216,27 @@ __device__ __forceinline__ void ff_step(RStateFF &st, const BetaEntry *__restric
     wl = __fmaf_rn(t.x, al, __fmaf_rn(t.y, a.h, wl));
     wh = ok ? wh : 0.f;
     wl = ok ? wl : 0.f;
-    // d' = (lambda b + w) + s d
+    // high words
     const float m = __fmul_rn(lam.h, st.bh);
-    float me = __fmaf_rn(lam.h, st.bh, -m);
-    me = __fmaf_rn(lam.h, st.bl, __fmaf_rn(lam.l, st.bh, me));
+    const float me = __fmaf_rn(lam.h, st.bh, -m);
     const FF u = two_sum(m, wh);
-    const FF v = two_sum(u.h, __fmul_rn(sf, st.dh));
-    const float lo = __fadd_rn(__fadd_rn(__fadd_rn(u.l, v.l), __fadd_rn(me, wl)), __fmul_rn(sf, st.dl));
-    const FF dn = two_sum(v.h, lo);
-    // b' = d' + s b
-    const FF x = two_sum(dn.h, __fmul_rn(sf, st.bh));
-    const FF bn = two_sum(x.h, __fadd_rn(__fadd_rn(x.l, dn.l), __fmul_rn(sf, st.bl)));
+    const FF dn = two_sum(u.h, __fmul_rn(sf, st.dh));
+    // low words: the errors, then lambda b and s d on the low parts
+    const float dl = __fadd_rn(__fadd_rn(__fadd_rn(me, u.l), __fadd_rn(dn.l, wl)),
+                               __fmaf_rn(lam.h, st.bl, __fmaf_rn(lam.l, st.bh, __fmul_rn(sf, st.dl))));
+    const FF bn = two_sum(dn.h, __fmul_rn(sf, st.bh));
+    st.bl = __fadd_rn(__fadd_rn(bn.l, dl), __fmul_rn(sf, st.bl));
     st.dh = dn.h;
-    st.dl = dn.l;
+    st.dl = dl;
     st.bh = bn.h;
-    st.bl = bn.l;
+}
+
+// Renormalized pair (Fast2Sum of the high and the low word).
+__device__ __forceinline__ void ff_renorm(float &h, float &l)
+{
+    const float s = __fadd_rn(h, l);
+    l = __fsub_rn(l, __fsub_rn(s, h));
+    h = s;
 }
 
 __device__ __forceinline__ void reinsch_seg_ff(RStateFF &st, const BetaEntry *__restrict__ row, int &n2, int count,
@@ -1234,8 +1244,20 @@ __device__ __forceinline__ void reinsch_seg_ff(RStateFF &st, const BetaEntry *__
                                                const float4 *__restrict__ T, int j0, int jmax)
 {
     const float df = (float)dir;
-#pragma unroll 2
-    for (int i = 0; i < count; ++i, n2 += dir, c2f += df) ff_step(st, row, n2, c2f, c1sq, R2f, z, lam, sf, T, j0, jmax);
+    int i = 0;
+    for (; i + 1 < count; i += 2, n2 += 2 * dir, c2f += 2.0f * df) {
+        ff_step(st, row, n2, c2f, c1sq, R2f, z, lam, sf, T, j0, jmax);
+        ff_step(st, row, n2 + dir, c2f + df, c1sq, R2f, z, lam, sf, T, j0, jmax);
+        ff_renorm(st.dh, st.dl);
+        ff_renorm(st.bh, st.bl);
+    }
+    if (i < count) {
+        ff_step(st, row, n2, c2f, c1sq, R2f, z, lam, sf, T, j0, jmax);
+        ff_renorm(st.dh, st.dl);
+        ff_renorm(st.bh, st.bl);
+        n2 += dir;
+        c2f += df;
+    }
 }
 
 // Feed `count` terms n2, n2 + dir, ... into the state (the first has the

@@ -33,17 +33,60 @@ __global__ void __launch_bounds__(PROBE_THREADS) fma_chains(int64_t iters, T nev
     if (s == never) sink[0] = s;
 }
 
+// The overlap probe: even warps run FP64 chains (iters trips), odd warps FP32
+// chains (GF_PROBE_FP32_PER_FP64 * iters trips, about as long at the two pipes'
+// rates); `halves` selects which of them run (bit 0: FP64, bit 1: FP32).
+template <typename T>
+__device__ __forceinline__ T chains(int64_t iters, T never)
+{
+    T a[PROBE_ILP];
+#pragma unroll
+    for (int j = 0; j < PROBE_ILP; ++j) a[j] = (T)(threadIdx.x + 1 + j) * (T)1e-3;
+    const T m = (T)0.9999999, c = (T)1e-7;
+    for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int j = 0; j < PROBE_ILP; ++j) a[j] = fma(a[j], m, c);
+    }
+    T s = 0;
+#pragma unroll
+    for (int j = 0; j < PROBE_ILP; ++j) s += a[j];
+    return s == never ? s : (T)0;
+}
+
+__global__ void __launch_bounds__(PROBE_THREADS) split_chains(int halves, int64_t iters, double *sink)
+{
+    const bool odd = ((threadIdx.x >> 5) & 1) != 0;
+    double s = 0;
+    if (!odd && (halves & 1)) s = chains<double>(iters, -1.0);
+    if (odd && (halves & 2)) s = (double)chains<float>(iters * GF_PROBE_FP32_PER_FP64, -1.0f);
+    if (s != 0) sink[0] = s;  // never (the chains stay positive)
+}
+
 }  // namespace
 
 extern "C" gf_status gf_peak_probe(int pipe, int64_t iters, void *dev_sink, int64_t *flops, void *cuda_stream)
 {
-    if ((pipe != GF_PROBE_FP64 && pipe != GF_PROBE_FP32) || iters < 1 || !dev_sink || !flops)
+    if (pipe < GF_PROBE_FP64 || pipe > GF_PROBE_BOTH_HALVES || iters < 1 || iters > ((int64_t)1 << 20) ||
+        !dev_sink || !flops)
         return gf_set_error(GF_ERR_ARG, "gf_peak_probe: bad argument");
     int dev = 0, nsm = 1, per = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaStream_t st = (cudaStream_t)cuda_stream;
     cudaError_t e;
+    if (pipe >= GF_PROBE_FP64_HALF) {
+        const int halves = pipe == GF_PROBE_FP64_HALF ? 1 : pipe == GF_PROBE_FP32_HALF ? 2 : 3;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, split_chains, PROBE_THREADS, 0);
+        if (e == cudaSuccess) split_chains<<<per * nsm, PROBE_THREADS, 0, st>>>(halves, iters, (double *)dev_sink);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess) return gf_set_error(GF_ERR_CUDA, "gf_peak_probe: launch failed");
+        gf_count_launch(1);
+        const int64_t per_half = (int64_t)2 * PROBE_ILP * 8 * iters * (int64_t)per * nsm * (PROBE_THREADS / 2);
+        *flops = ((halves & 1) ? per_half : 0) + ((halves & 2) ? per_half * GF_PROBE_FP32_PER_FP64 : 0);
+        return GF_OK;
+    }
     if (pipe == GF_PROBE_FP64) {
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fma_chains<double>, PROBE_THREADS, 0);
         if (e == cudaSuccess) fma_chains<double><<<per * nsm, PROBE_THREADS, 0, st>>>(iters, -1.0, (double *)dev_sink);

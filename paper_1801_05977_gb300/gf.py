@@ -160,7 +160,8 @@ def set_phase_timing(on: bool):
     _check(lib().gf_set_phase_timing(1 if on else 0))
 
 
-GF_PROBE_FP64, GF_PROBE_FP32 = 0, 1
+GF_PROBE_FP64, GF_PROBE_FP32, GF_PROBE_FP64_HALF, GF_PROBE_FP32_HALF, GF_PROBE_BOTH_HALVES = 0, 1, 2, 3, 4
+GF_PROBE_FP32_PER_FP64 = 64  # FP32 trips per FP64 trip in the overlap modes (gf.h)
 
 
 def peak_probe(pipe: int, iters: int, sink, stream=None) -> int:

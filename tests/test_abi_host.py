@@ -123,3 +123,14 @@ def test_batch_rejects_bad_arguments():
     assert L.gf_plan_batch(2, k, al, M, ctypes.byref(td), None, ctypes.byref(h)) == gf.GF_ERR_UNSUPPORTED
     assert L.gf_batch_destroy(None) == gf.GF_OK
     assert L.gf_batch_eval_points(None, None, None, 1, None, None) == gf.GF_ERR_ARG
+
+
+@pytest.mark.parametrize("pipe,iters,sink", [(-1, 10, 8), (5, 10, 8), (gf.GF_PROBE_BOTH_HALVES, 0, 8),
+                                             (gf.GF_PROBE_FP64_HALF, (1 << 20) + 1, 8), (gf.GF_PROBE_FP32, 10, 0)])
+def test_peak_probe_rejects_bad_arguments(pipe, iters, sink):
+    """The probe checks its arguments before any device work (no GPU needed)."""
+    L = gf.lib()
+    buf = (ctypes.c_double * 1)()
+    ptr = ctypes.cast(buf, ctypes.c_void_p) if sink else None
+    fl = ctypes.c_int64()
+    assert L.gf_peak_probe(pipe, iters, ptr, ctypes.byref(fl), None) == gf.GF_ERR_ARG
