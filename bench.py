@@ -927,8 +927,9 @@ def run_batch_only(args):
 
 
 def run_mlp_forward(args):
-    """Profiling helper: two fused forward passes of the surrogate network on
-    `mlp_forward_only` random samples."""
+    """Profiling helper: fused forward passes of the surrogate network on
+    `mlp_forward_only` random samples (two, then `steps` timed by CUDA events);
+    prints their mean time and rate."""
     import torch
 
     from paper_1801_05977_gb300 import gf
@@ -938,7 +939,19 @@ def run_mlp_forward(args):
     for _ in range(2):
         mlp.forward(x)
     torch.cuda.synchronize()
+    ts = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        mlp.forward(x)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
     mlp.close()
+    ms = float(np.mean(ts))
+    flops = 2.0 * (80 * 256 + 3 * 256 * 256 + 256 * 2) * args.mlp_forward_only
+    print(json.dumps({"mlp_forward": {"samples": args.mlp_forward_only, "ms": ms, "tflops": flops / (ms * 1e-3) / 1e12,
+                                      "note": "per call of gf.MLP.forward (features, fused network, output)"}}))
     return 0
 
 

@@ -308,7 +308,9 @@ __global__ void surrogate_assemble_kernel(const double *x, int n, int64_t base, 
 // iteration of a persistent CTA (one per SM).  The two 128 x 256 bf16
 // activation tiles stay in shared memory (canonical K-major layout), the two
 // 128 x 256 fp32 accumulators in tensor memory (all 512 columns); each
-// layer's weights stream through two 256 x 64 stages; the epilogue applies
+// layer's weights stream through three 256 x 64 stages, their copies issued up
+// to three chunks ahead of the MMAs (the biases and head weights are read
+// through L1 to leave the shared memory to them); the epilogue applies
 // bias + SiLU and writes the next layer's input back into shared memory; the
 // 256 -> 2 head is folded into the last epilogue.  HBM traffic per sample:
 // 6 input floats and 2 output floats.
@@ -332,10 +334,11 @@ __device__ __forceinline__ uint32_t silu2_bf16(float z0, float z1)
 constexpr int ROWS = 128, NT = 2;
 constexpr int ACT_BYTES = ROWS * HID * 2;                // 64 KiB per tile
 constexpr int WST_BYTES = HID * umma::KC * 2;           // 32 KiB per weight stage
-constexpr int PAR_FLOATS = 4 * HID + 2 * HID;  // biases of layers 1-4, then the head weights
+constexpr int NS = 3;                           // weight stages in flight
 constexpr int NCW = 8 * NT;                     // consumer warps (8 per tile: 4 row quarters x 2 column halves)
 constexpr int THREADS = (NCW + 1) * 32;         // plus one producer warp
-constexpr int SMEM = NT * ACT_BYTES + 2 * WST_BYTES + 128 + PAR_FLOATS * 4;
+constexpr int SMEM = NT * ACT_BYTES + NS * WST_BYTES + 128;
+static_assert(SMEM <= 232448, "shared memory of one CTA");
 constexpr int TMEM_COLS = 512;
 
 // act tile: [k/8][r/8] core matrices, the 16 row groups of a K block adjacent
@@ -360,17 +363,20 @@ struct Args {
 };
 }  // namespace fused
 
-// Producer warp (warp 16, one lane): weight-stage bulk copies and MMA issue, tile
-// after tile.  Consumer warps 0-7 own tile 0, 8-15 own tile 1; warp w reads TMEM
-// lanes 32 (w % 4) .. +31, i.e. its 32 rows, and the column half (w / 4) % 2 of
-// the 256 columns, so two warps share each row's epilogue (and features).  While
-// the consumers of one tile run its epilogue (bias, SiLU, bf16 activations back
-// into shared memory) the tensor cores work on the other tile.  The 256 -> 2
-// head's two column halves are added into the output, which is zeroed before the
-// launch (two float terms added to zero: the same result in either order).
+// Producer warp (warp 16, one lane): weight-stage bulk copies and MMA issue,
+// layer by layer, tile 0 then tile 1.  The sixteen consumer warps take every
+// tile's epilogue in turn: warp w reads TMEM lanes 32 (w % 4) .. +31, i.e. its 32
+// rows, and the column quarter w / 4 of the 256 columns, so four warps share each
+// row's epilogue (and features).  While the consumers run one tile's epilogue
+// (bias, SiLU, bf16 activations back into shared memory) the tensor cores work
+// on the other tile.  The 256 -> 2 head's four column quarters meet in shared
+// memory and are added in quarter order by the row quarter's first warp, which
+// writes the output (the same result at every call).
 //   lbar[b]  stage copy landed in buffer b    mbar[b]  MMAs of that stage done
 //   accf[t]  tile t's layer MMAs done         actr[t]  tile t's activations written
-//                                                      and its accumulator read (128 arrivals)
+//                                                      and its accumulator read (one arrival
+//                                                      per consumer warp, after __syncwarp)
+//   hbar[q]  the head partial sums of row quarter q written (one arrival per warp)
 // Every wait is bounded; a timeout sets *err and makes every warp leave.
 __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 {
@@ -382,15 +388,11 @@ __global__ void __launch_bounds__(fused::THREADS, 1) mlp_infer_fused(fused::Args
     using namespace fused;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *act[NT] = {smem, smem + ACT_BYTES};
-    uint8_t *wst[2] = {smem + NT * ACT_BYTES, smem + NT * ACT_BYTES + WST_BYTES};
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NT * ACT_BYTES + 2 * WST_BYTES);
-    uint64_t *mbar = bars, *lbar = bars + 2, *accf = bars + 4, *actr = bars + 6;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 8);
+    uint8_t *wst0 = smem + NT * ACT_BYTES;  // NS weight stages of WST_BYTES
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NT * ACT_BYTES + NS * WST_BYTES);
+    uint64_t *mbar = bars, *lbar = bars + NS, *accf = bars + 2 * NS, *actr = bars + 2 * NS + 2, *hbar = bars + 2 * NS + 4;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * NS + 8);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
-    float *par = reinterpret_cast<float *>(smem + NT * ACT_BYTES + 2 * WST_BYTES + 128);  // biases [4][HID], head [2][HID]
-    for (int i = threadIdx.x; i < PAR_FLOATS; i += blockDim.x)
-        par[i] = i < 4 * HID ? A.b[i / HID][i % HID] : A.W5[i - 4 * HID];
-    const float *W5s = par + 4 * HID;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(umma::smem_u32(tslot)),
@@ -398,9 +400,12 @@ __global__ void __launch_bounds__(fused::THREADS, 1) mlp_infer_fused(fused::Args
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (threadIdx.x == 0) {
-        for (int q = 0; q < 6; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(umma::smem_u32(&bars[q])));
-        for (int q = 6; q < 8; ++q)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(umma::smem_u32(&bars[q])), "r"(2 * ROWS));
+        for (int q = 0; q < 2 * NS + 2; ++q)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(umma::smem_u32(&bars[q])));
+        for (int q = 2 * NS + 2; q < 2 * NS + 4; ++q)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(umma::smem_u32(&bars[q])), "r"(NCW));
+        for (int q = 2 * NS + 4; q < 2 * NS + 8; ++q)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(umma::smem_u32(&bars[q])), "r"(NCW / 4));
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
@@ -413,7 +418,37 @@ __global__ void __launch_bounds__(fused::THREADS, 1) mlp_infer_fused(fused::Args
     if (warp == NCW) {
         // ---------------------------------------------------------------- producer
         if (lane == 0) {
-            int g = 0, issued = -1, landed = -1, committed = 0, ua[NT] = {0, 0};
+            // The weight chunks follow one fixed order per tile pair (layer, tile,
+            // K chunk), so their copies run up to NS chunks ahead of the MMAs:
+            // chunks 0 .. NS-1 at the start, chunk g - 1 + NS into the buffer of
+            // chunk g - 1 once the MMAs of chunk g are issued and those of chunk
+            // g - 1 are done.  Chunk g uses buffer g % NS, whose k-th use is phase k & 1.
+            constexpr int NCH0 = (K0 + umma::KC - 1) / umma::KC, NCHH = HID / umma::KC;
+            constexpr int PER_PAIR = NT * (NCH0 + 3 * NCHH);
+            int npairs = 0;
+            for (int tp = blockIdx.x; tp * (NT * ROWS) < A.n; tp += gridDim.x) ++npairs;
+            const int total = npairs * PER_PAIR;
+            auto issue = [&](int gg) {
+                int q = gg % PER_PAIR, l = 0;
+                if (q < NT * NCH0) {
+                    q %= NCH0;
+                } else {
+                    q -= NT * NCH0;
+                    l = 1 + q / (NT * NCHH);
+                    q %= NCHH;
+                }
+                const int buf = gg % NS;
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(umma::smem_u32(&lbar[buf])),
+                             "r"(WST_BYTES)
+                             : "memory");
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        umma::smem_u32(wst0 + buf * WST_BYTES)),
+                    "l"(A.Wimg[l] + (size_t)q * (WST_BYTES / 2)), "r"(WST_BYTES), "r"(umma::smem_u32(&lbar[buf]))
+                    : "memory");
+            };
+            int g = 0, issued = min(NS, total) - 1, landed = -1, committed = -1, ua[NT] = {0, 0};
+            for (int gg = 0; gg <= issued; ++gg) issue(gg);
             bool ok = true;
             for (int tp = blockIdx.x; ok && tp * (NT * ROWS) < A.n; tp += gridDim.x)
                 for (int l = 0; ok && l < 4; ++l) {
@@ -421,31 +456,18 @@ __global__ void __launch_bounds__(fused::THREADS, 1) mlp_infer_fused(fused::Args
                     const int nch = (K + umma::KC - 1) / umma::KC;
                     for (int t = 0; ok && t < NT; ++t) {
                         // tile t's activations for layer l are written and its accumulator is free
-                        ok = umma::mbar_wait(umma::smem_u32(&actr[t]), ua[t] & 1) && !*abort_flag;
+                        ok = umma::mbar_wait_sleep(umma::smem_u32(&actr[t]), ua[t] & 1) && !*abort_flag;
                         ++ua[t];
                         if (!ok) break;
                         asm volatile("tcgen05.fence::after_thread_sync;");
                         for (int c = 0; ok && c < nch; ++c, ++g) {
-                            const int buf = g & 1;
-                            if (g >= 2) ok = umma::mbar_wait(umma::smem_u32(&mbar[buf]), ((g - 2) >> 1) & 1);
-                            if (!ok) break;
-                            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
-                                             umma::smem_u32(&lbar[buf])),
-                                         "r"(WST_BYTES)
-                                         : "memory");
-                            asm volatile(
-                                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                                    umma::smem_u32(wst[buf])),
-                                "l"(A.Wimg[l] + (size_t)c * (WST_BYTES / 2)), "r"(WST_BYTES),
-                                "r"(umma::smem_u32(&lbar[buf]))
-                                : "memory");
-                            issued = g;
-                            ok = umma::mbar_wait(umma::smem_u32(&lbar[buf]), (g >> 1) & 1);
+                            const int buf = g % NS;
+                            ok = umma::mbar_wait_sleep(umma::smem_u32(&lbar[buf]), (g / NS) & 1);
                             if (!ok) break;
                             landed = g;
                             asm volatile("tcgen05.fence::after_thread_sync;");
                             const int ksteps = (min(umma::KC, K - c * umma::KC) + 15) / 16;
-                            const uint32_t b0 = umma::smem_u32(wst[buf]), a0 = umma::smem_u32(act[t]);
+                            const uint32_t b0 = umma::smem_u32(wst0 + buf * WST_BYTES), a0 = umma::smem_u32(act[t]);
                             for (int kk = 0; kk < ksteps; ++kk) {
                                 const uint64_t ad = umma::make_desc(a0 + (c * 8 + kk * 2) * ACT_LBO, ACT_LBO, ACT_SBO);
                                 const uint64_t bd = umma::make_desc(b0 + kk * 256, 128, (umma::KC / 8) * 128);
@@ -458,31 +480,38 @@ __global__ void __launch_bounds__(fused::THREADS, 1) mlp_infer_fused(fused::Args
                             asm volatile(
                                 "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                                     umma::smem_u32(&mbar[buf])));
+                            committed = g;
+                            // refill the buffer of chunk g - 1 with chunk g - 1 + NS
+                            if (g >= 1 && g - 1 + NS < total) {
+                                ok = umma::mbar_wait_sleep(umma::smem_u32(&mbar[(g - 1) % NS]), ((g - 1) / NS) & 1);
+                                if (!ok) break;
+                                issue(g - 1 + NS);
+                                issued = g - 1 + NS;
+                            }
                         }
                         if (!ok) break;
                         // tile t's accumulator is complete once its MMAs are
                         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                             umma::smem_u32(&accf[t])));
-                        ++committed;
                     }
                 }
             if (!ok) {
                 *abort_flag = 1;
                 if (A.err) atomicExch(A.err, 1);
             }
-            // before the CTA exits: the last copy has landed and every MMA has completed
-            if (issued > landed) umma::mbar_wait(umma::smem_u32(&lbar[issued & 1]), (issued >> 1) & 1);
-            if (g > 0) umma::mbar_wait(umma::smem_u32(&mbar[(g - 1) & 1]), ((g - 1) >> 1) & 1);
-            (void)committed;
+            // before the CTA exits: every issued copy has landed and every MMA has completed
+            for (int gg = landed + 1; gg <= issued; ++gg) umma::mbar_wait_sleep(umma::smem_u32(&lbar[gg % NS]), (gg / NS) & 1);
+            if (committed >= 0) umma::mbar_wait_sleep(umma::smem_u32(&mbar[committed % NS]), (committed / NS) & 1);
         }
     } else {
         // ---------------------------------------------------------------- consumers
-        const int t = warp >> 3, quarter = warp & 3, half = (warp >> 2) & 1, r = quarter * 32 + lane;
-        uint8_t *at = act[t];
+        const int quarter = warp & 3, cq = warp >> 2, r = quarter * 32 + lane;
         const float b50 = A.b5[0], b51 = A.b5[1];
-        int fa = 0;
+        int fa[NT] = {0, 0}, hp = 0;
         bool ok = true;
         for (int tp = blockIdx.x; ok && tp * (NT * ROWS) < A.n; tp += gridDim.x) {
+          for (int t = 0; t < NT; ++t) {
+            uint8_t *at = act[t];
             const int i = tp * NT * ROWS + t * ROWS + r;
             const bool live = i < A.n;
             // features of this row into the first 80 columns of the tile
@@ -499,8 +528,8 @@ __global__ void __launch_bounds__(fused::THREADS, 1) mlp_infer_fused(fused::Args
                 }
                 const float rr = sqrtf(t1 * t1 + t2 * t2 + x3 * x3);
                 // ten blocks of 8 features: blocks 0..7 hold cos/sin of 4 frequencies each;
-                // the two column halves of a row write blocks 0..4 and 5..9
-                for (int kb = half * (K0 / 16); kb < (half + 1) * (K0 / 16); ++kb) {
+                // the four column quarters of a row write blocks 0..1, 2..4, 5..6 and 7..9
+                for (int kb = (cq * (K0 / 8)) / 4; kb < ((cq + 1) * (K0 / 8)) / 4; ++kb) {
                     float v[8];
                     if (kb < 8) {
 #pragma unroll
@@ -538,15 +567,21 @@ __global__ void __launch_bounds__(fused::THREADS, 1) mlp_infer_fused(fused::Args
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;");
-            mbar_arrive(umma::smem_u32(&actr[t]));
-            for (int l = 0; ok && l < 4; ++l) {
-                ok = umma::mbar_wait(umma::smem_u32(&accf[t]), fa & 1) && !*abort_flag;
-                ++fa;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(umma::smem_u32(&actr[t]));
+          }
+            for (int l = 0; ok && l < 4; ++l)
+              for (int t = 0; ok && t < NT; ++t) {
+                uint8_t *at = act[t];
+                const int i = tp * NT * ROWS + t * ROWS + r;
+                const bool live = i < A.n;
+                ok = __all_sync(0xffffffffu, umma::mbar_wait_sleep(umma::smem_u32(&accf[t]), fa[t] & 1) && !*abort_flag);
+                ++fa[t];
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const float *bias = par + l * HID;
+                const float *bias = A.b[l];
                 float y0 = 0.f, y1 = 0.f;
-                for (int j = half * (HID / 2); j < (half + 1) * (HID / 2); j += 32) {
+                for (int j = cq * (HID / 4); j < (cq + 1) * (HID / 4); j += 32) {
                     uint32_t v[32];
                     const uint32_t taddr = tmem + t * HID + ((uint32_t)(quarter * 32) << 16) + (uint32_t)j;
                     asm volatile(
@@ -562,15 +597,15 @@ __global__ void __launch_bounds__(fused::THREADS, 1) mlp_infer_fused(fused::Args
                     uint32_t pk[16];  // bf16 pairs, kept in registers
 #pragma unroll
                     for (int e = 0; e < 32; e += 4) {
-                        const float4 bb = *reinterpret_cast<const float4 *>(bias + j + e);  // shared, broadcast
+                        const float4 bb = __ldg(reinterpret_cast<const float4 *>(bias + j + e));  // broadcast, L1
                         const float z[4] = {__uint_as_float(v[e]) + bb.x, __uint_as_float(v[e + 1]) + bb.y,
                                             __uint_as_float(v[e + 2]) + bb.z, __uint_as_float(v[e + 3]) + bb.w};
                         const uint32_t h01 = silu2_bf16(z[0], z[1]), h23 = silu2_bf16(z[2], z[3]);
                         pk[e >> 1] = h01;
                         pk[(e >> 1) + 1] = h23;
                         if (l == 3) {
-                            const float4 w0 = *reinterpret_cast<const float4 *>(W5s + j + e);
-                            const float4 w1 = *reinterpret_cast<const float4 *>(W5s + HID + j + e);
+                            const float4 w0 = __ldg(reinterpret_cast<const float4 *>(A.W5 + j + e));
+                            const float4 w1 = __ldg(reinterpret_cast<const float4 *>(A.W5 + HID + j + e));
                             const float h[4] = {__uint_as_float(h01 << 16), __uint_as_float(h01 & 0xFFFF0000u),
                                                 __uint_as_float(h23 << 16), __uint_as_float(h23 & 0xFFFF0000u)};
                             y0 = fmaf(h[0], w0.x, fmaf(h[1], w0.y, fmaf(h[2], w0.z, fmaf(h[3], w0.w, y0))));
@@ -588,12 +623,33 @@ __global__ void __launch_bounds__(fused::THREADS, 1) mlp_infer_fused(fused::Args
                     // next layer's input written, accumulator read: hand the tile back
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     asm volatile("tcgen05.fence::before_thread_sync;");
-                    mbar_arrive(umma::smem_u32(&actr[t]));
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(umma::smem_u32(&actr[t]));
                 } else {
+                    // the head: the four column quarters' partial sums of row r meet in
+                    // the last 4 KiB of the tile's activations (K columns 240..255, not
+                    // written again before this tile's next layer-0 epilogue, which
+                    // follows every warp's next features) and are added in quarter order
                     asm volatile("tcgen05.fence::before_thread_sync;");
-                    if (live) {
-                        atomicAdd(&A.Y[2 * (size_t)i], half ? y0 : y0 + b50);
-                        atomicAdd(&A.Y[2 * (size_t)i + 1], half ? y1 : y1 + b51);
+                    float *part = reinterpret_cast<float *>(at + ACT_BYTES - 4096);  // [quarter][row][2]
+                    part[(cq * ROWS + r) * 2] = y0;
+                    part[(cq * ROWS + r) * 2 + 1] = y1;
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(umma::smem_u32(&hbar[quarter]));
+                    if (cq == 0) {
+                        ok = __all_sync(0xffffffffu, umma::mbar_wait_sleep(umma::smem_u32(&hbar[quarter]), hp & 1));
+                        ++hp;
+                        if (!ok) break;
+                        if (live) {
+                            float s0 = b50, s1 = b51;
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                s0 += part[(q * ROWS + r) * 2];
+                                s1 += part[(q * ROWS + r) * 2 + 1];
+                            }
+                            A.Y[2 * (size_t)i] = s0;
+                            A.Y[2 * (size_t)i + 1] = s1;
+                        }
                     }
                 }
             }
@@ -756,8 +812,6 @@ gf_status infer(gf_mlp_t m, int n, float *Y, cudaStream_t s)
     CUM(cudaFuncSetAttribute(mlp_infer_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, fused::SMEM));
     int tiles = (n + fused::NT * fused::ROWS - 1) / (fused::NT * fused::ROWS);
     int grid = tiles < m->nsm ? tiles : m->nsm;
-    // the head's two column halves are added into Y
-    CUM(cudaMemsetAsync(Y, 0, sizeof(float) * 2 * (size_t)n, s));
     mlp_infer_fused<<<grid, fused::THREADS, fused::SMEM, s>>>(A);
     gf_count_launch(1);
     CUM(cudaGetLastError());

@@ -111,6 +111,35 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
     return false;
 }
 
+// The same wait with a suspend-time hint: a thread whose phase is not complete
+// is suspended (it issues nothing) until the phase completes or the hint runs
+// out, so that waiting warps leave the issue slots to the working ones.  Bounded
+// in time by the global timer (2 s), not by a poll count, as a try may return
+// early or late.
+constexpr unsigned SUSPEND_NS = 20000;
+constexpr unsigned long long WAIT_NS = 2000000000ull;
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool mbar_wait_sleep(uint32_t mbar, uint32_t parity)
+{
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity), "r"(SUSPEND_NS)
+            : "memory");
+        if (done) return true;
+        if (global_ns() - t0 > WAIT_NS) return false;
+    }
+}
+
 // byte offset of element (r, k) of a stage (rows x KC) in the core-matrix layout
 // [r/8][k/8] of 128-byte core matrices: LBO (K direction) = 128, SBO (row groups) = KC/8 * 128
 __device__ __forceinline__ uint32_t core_off(int r, int k) { return ((r >> 3) * (KC / 8) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2; }
