@@ -95,6 +95,7 @@ struct SynthArgs {
     double k, a1, a2;   // wave number, alpha
     double ct;          // c~ (possibly perturbed)
     double qs;          // pi / c~: last-axis frequency q_b = freq(b) qs
+    float qsh, qsl;     // qs as a float pair (split plans' float coefficients)
     double gskip;       // evanescent |beta| above which e^{-|beta| c}/(2 |beta|^2) < 1e-20
     double gfloat;      // split plans (3D): evanescent |beta| from which a column's coefficients are formed in float
     double invV;        // 1 / |D|: 1/(8 pi^2 c~) in 3D, 1/(4 pi c~) in 2D

@@ -500,6 +500,8 @@ gf_status gf_plan(int dim, double k, const double *alpha, const int *M, const gf
         sa.a2 = a2;
         sa.ct = ct;
         sa.qs = GF_PI / ct;
+        sa.qsh = (float)sa.qs;
+        sa.qsl = (float)(sa.qs - (double)sa.qsh);
         // smallest g with e^{-g c}/(2 g^2) < 1e-20 (the function decreases in g)
         {
             double g = 1.0;

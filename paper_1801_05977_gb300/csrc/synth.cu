@@ -334,9 +334,13 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
     float2 *qqf = A2mkf + TJ;
     float *gcol = reinterpret_cast<float *>(qqf + n);
     int *cflag = reinterpret_cast<int *>(gcol + TJ);
+    // float copies of the quadrature weights and nodes [Q] each, q_b in float [n]
+    float *tWs = reinterpret_cast<float *>(cflag + TJ);
+    float *tts = tWs + Q;
+    float *qfs = tts + Q;
     // 2D derivative plans with a second wave number: its A_m [TJ][Q] and beta [TJ]
     const bool need_k2 = DERIV && a.k2 > 0.0;
-    double2 *Av2 = reinterpret_cast<double2 *>((reinterpret_cast<uintptr_t>(cflag + TJ) + 15) & ~(uintptr_t)15);
+    double2 *Av2 = reinterpret_cast<double2 *>((reinterpret_cast<uintptr_t>(qfs + n) + 15) & ~(uintptr_t)15);
     double2 *betas2 = Av2 + TJ * Q;
     const int ncols = (a.dim == 3) ? a.M1 * a.M2 : a.M1;
     // tiles alternately from both ends of the column range: the low frequencies
@@ -373,23 +377,40 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
             cflag[t] = (bt.y > a.gskip ? 1 : 0) | (bt.y >= a.gfloat ? 2 : 0);
         }
     }
-    if (fcoef)
+    if (fcoef) {
+        // q_b = j q_s and q_b^2 as float pairs from q_s's pair (qsh, qsl), with no
+        // double operation: j q_sh by TwoProd (j is an integer below 2^12), then the
+        // square of the pair (its l^2 term dropped), about 2^-46 relative
         for (int b = threadIdx.x; b < n; b += blockDim.x) {
-            const double q = (double)freq_of(b, n) * a.qs;
-            const double q2 = q * q;
-            qq[b] = q2;
-            const float h = (float)q2;
-            qqf[b] = make_float2(h, (float)(q2 - (double)h));
+            const float jf = (float)freq_of(b, n);
+            const float ph = jf * a.qsh;
+            const float pl = __fmaf_rn(jf, a.qsh, -ph) + jf * a.qsl;
+            const float h = ph * ph;
+            const float l = __fmaf_rn(ph, ph, -h) + 2.0f * ph * pl;
+            const float s = h + l;
+            qqf[b] = make_float2(s, l - (s - h));
+            qfs[b] = ph + pl;
         }
+        for (int m = threadIdx.x; m < Q; m += blockDim.x) {
+            tWs[m] = (float)a.tW[m];
+            tts[m] = (float)a.tt[m];
+        }
+    }
+    (void)qq;
     __syncthreads();
     for (int i = threadIdx.x; i < TJ * Q; i += blockDim.x) {
         int t = i / Q, m = i - t * Q;
+        if (fcoef) {
+            // the column's flags: bit 0 skipped X'-integrals, bit 1 float coefficient
+            const int f = cflag[t];
+            if (f & 1) continue;
+            if (f & 2) {
+                Avf[i] = tWs[m] * expf(-gcol[t] * tts[m]);
+                continue;
+            }
+        }
         double2 b = betas[t];
         if (b.y > a.gskip) continue;  // this column's X'-integrals are not used
-        if (fcoef && b.y >= a.gfloat) {
-            Avf[i] = (float)a.tW[m] * expf(-(float)b.y * (float)a.tt[m]);
-            continue;
-        }
         double tm = a.tt[m];
         double2 e;
         if (b.y == 0.0) {
@@ -421,16 +442,19 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
 
     const double k2 = a.k * a.k, ik2 = 1.0 / k2;
     // the float branch's constants, converted once
-    const float qsf = (float)a.qs, ihpanf = (float)a.ihpan, hpanf = (float)a.hpan, invVf = (float)a.invV;
+    const float ihpanf = (float)a.ihpan, hpanf = (float)a.hpan, invVf = (float)a.invV;
     // The coefficients are even in the last-axis index j (they depend on q_j
     // through q_j^2, and the two X' terms of Eqs. (fck-coef)/(kdj1) trade places
     // under q -> -q), except the Maxwell xz and yz fields, whose factor c^3 = q_j
     // makes them odd (Sec. 4).  Only b = 0 .. n/2 (j = 0 .. n/2 - 1 and the
     // Nyquist index j = -n/2) are formed here; b > n/2 (j = b - n) is filled
     // below from b' = n - b (j' = -j).
-    const int nh = (n >> 1) + 1;
+    // items: (t, b) for b < n/2 by shift and mask, then the Nyquist b = n/2 of each column
+    const int nh = (n >> 1) + 1, lgh = lg - 1, nlow = TJ << lgh;
+    const float hmaxf = (float)(a.hnpan - 1);
     for (int i = threadIdx.x; i < TJ * nh; i += blockDim.x) {
-        int t = i / nh, b = i - t * nh;
+        const bool low = i < nlow;
+        const int t = low ? (i >> lgh) : i - nlow, b = low ? (i & ((n >> 1) - 1)) : (n >> 1);
         int col = col0 + t;
         int jl = freq_of(b, n);
         if (fcoef && (cflag[t] & 2)) {
@@ -440,7 +464,7 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
             // to ~2^-46 relative to its terms (Knuth's TwoSum), then rounded: since
             // |D| >= 1e-6 k^2 (the resonance rule), this is below float rounding of D.
             // Every other factor is O(1) in relative terms.
-            const float qf = (float)jl * qsf;
+            const float qf = qfs[b];
             const float g = gcol[t];
             float T12f = 0.f;
             if (!(cflag[t] & 1)) {
@@ -471,15 +495,19 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
                     s1 = fmaf(A, E.x, s1);
                     s3 = fmaf(A, E.y, s3);
                 }
-                T12f = (g * s1 - qf * s3) / (g * (g * g + qf * qf));
+                T12f = (g * s1 - qf * s3) * __frcp_rn(g * (g * g + qf * qf));
             }
             const float2 Ad = A2mkf[t], Qd = qqf[b];
             const float dh = __fadd_rn(Ad.x, Qd.x), dv = __fsub_rn(dh, Ad.x);
             const float de = __fadd_rn(__fsub_rn(Ad.x, __fsub_rn(dh, dv)), __fsub_rn(Qd.x, dv));
-            const float iD = 1.0f / __fadd_rn(dh, __fadd_rn(de, __fadd_rn(Ad.y, Qd.y)));
-            const float sf = sqrtf(A2f[t] + qf * qf);
-            const int pnl = min((int)(sf * ihpanf), a.hnpan - 1);
-            const float x = (sf - ((float)pnl + 0.5f) * hpanf) * (2.0f / hpanf);
+            const float iD = __frcp_rn(__fadd_rn(dh, __fadd_rn(de, __fadd_rn(Ad.y, Qd.y))));
+            // |xi| by the hardware reciprocal square root (its ~2^-23 relative error moves
+            // the Chebyshev point by less than the float rounding of h)
+            const float s2 = fmaf(qf, qf, A2f[t]);
+            const float sf = s2 > 0.f ? s2 * rsqrtf(s2) : 0.f;
+            const float pf = fminf(floorf(sf * ihpanf), hmaxf);
+            const int pnl = (int)pf;
+            const float x = (sf - (pf + 0.5f) * hpanf) * (2.0f / hpanf);
             const float2 *cc = a.hchebf + (size_t)pnl * (a.hdeg + 1);
             float b1r = 0.f, b1i = 0.f, b2r = 0.f, b2i = 0.f;
             for (int kk = a.hdeg; kk >= 1; --kk) {
@@ -977,12 +1005,14 @@ void synth_config_t(SynthArgs &a, int tj_max, size_t sm[3])
     const int ncols = (a.dim == 3) ? a.M1 * a.M2 : a.M1;
     // per column: A_m (double2 and float), beta, |alpha|^2 (double), |alpha|^2 - k^2, its float;
     // float-column data (|alpha|^2 - k^2 as a float pair, g, flags); per b: twiddles, q_b^2
-    // and its float pair; plus the two line buffers
+    // and its float pair, q_b in float; the quadrature weights and nodes in float; plus the
+    // two line buffers
     auto bytes = [&](int TJ) {
         return sizeof(C) * (a.Mlast / 2) + sizeof(double) * a.Mlast + sizeof(float2) * a.Mlast +
                TJ * (sizeof(double2) * a.Q + sizeof(double2) + 2 * sizeof(double) + sizeof(float)) +
                TJ * (sizeof(float2) + sizeof(float) + sizeof(int)) +
                sizeof(float) * ((TJ * a.Q + 3) & ~3) + sizeof(C) * (a.nf + 1) * TJ * a.Mlast + 64 +
+               sizeof(float) * (2 * a.Q + a.Mlast) + 16 +
                (a.deriv && a.k2 > 0.0 ? TJ * sizeof(double2) * (a.Q + 1) + 16 : 0);
     };
     int TJ = tj_max;
