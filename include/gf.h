@@ -198,9 +198,13 @@ gf_status gf_eval_points(gf_plan_t plan, const double *dev_xyz, int64_t n, int w
                          void *dev_out, void *cuda_stream);
 
 /* As gf_eval_points, with HOST input and output buffers: copies the targets to
- * the device, evaluates and copies the results back, all on cuda_stream, then
- * synchronises the stream.  The device staging buffers are taken from the
- * library's memory pool per call. */
+ * the device, evaluates and copies the results back, then synchronises
+ * cuda_stream.  The upload runs on a copy stream the library owns (one per
+ * device) and the evaluation on cuda_stream waits for it, so the upload overlaps
+ * work already queued on cuda_stream (for example the synthesis of a plan just
+ * created); host_xyz is therefore read as soon as the call is made, not in
+ * cuda_stream's order.  The device staging buffers are taken from the library's
+ * memory pool per call. */
 gf_status gf_eval_points_host(gf_plan_t plan, const double *host_xyz, int64_t n, int which,
                               void *host_out, void *cuda_stream);
 

@@ -300,6 +300,7 @@ cudaError_t gf_launch_eval(const EvalArgs &a, int precision, cudaStream_t s, cud
                            const EvalFork *fork = nullptr);
 // per-device side stream of the library (non-blocking, lives until the process exits)
 cudaStream_t gf_aux_stream();
+cudaStream_t gf_copy_stream();
 
 void gf_count_launch(int n);
 gf_status gf_plan_eval_args(gf_plan_t p, const double *dev_xyz, int64_t n, int which, void *dev_out, EvalArgs *a,

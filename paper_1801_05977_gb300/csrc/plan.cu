@@ -893,12 +893,31 @@ gf_status gf_eval_points_host(gf_plan_t p, const double *host_xyz, int64_t n, in
     int ne = gf_out_entries(which);
     size_t xb = sizeof(double) * p->dim * (size_t)n, ob = p->elem * ne * (size_t)n;
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    // device staging per call from the stream-ordered pool (pool hits after the first call)
+    // device staging per call from the stream-ordered pool (pool hits after the first call).
+    // The targets go up on the library's copy stream, allocated there and joined to
+    // cuda_stream by an event, so the upload overlaps work already queued on cuda_stream
+    // (a plan's synthesis); without that stream, on cuda_stream itself.
+    cudaStream_t cs = gf_copy_stream();
+    cudaEvent_t up = nullptr;
+    if (cs && cudaEventCreateWithFlags(&up, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        up = nullptr;
+    }
+    if (!up) cs = st;
     void *dx = nullptr, *dout = nullptr;
-    CU(gf_dev_alloc(&dx, xb, st));
-    cudaError_t e = gf_dev_alloc(&dout, ob, st);
+    cudaError_t e = gf_dev_alloc(&dx, xb, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dx, host_xyz, xb, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess && up) {
+        e = cudaEventRecord(up, cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, up, 0);
+    }
+    if (up) cudaEventDestroy(up);  // released once its work completes
+    if (e != cudaSuccess) {
+        if (dx) gf_dev_free(dx, cs);
+        CU(e);
+    }
+    e = gf_dev_alloc(&dout, ob, st);
     gf_status s = GF_OK;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dx, host_xyz, xb, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) {
         s = gf_eval_points(p, (const double *)dx, n, which, dout, cuda_stream);
         if (s == GF_OK) e = cudaMemcpyAsync(host_out, dout, ob, cudaMemcpyDeviceToHost, st);

@@ -115,6 +115,26 @@ cudaStream_t gf_aux_stream()
     return s;
 }
 
+// One non-blocking stream per device for the host-buffer entry point's uploads,
+// which then overlap work already queued on the caller's stream (null on failure).
+cudaStream_t gf_copy_stream()
+{
+    static std::mutex mu;
+    static std::map<int, cudaStream_t> streams;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = streams.find(dev);
+    if (it != streams.end()) return it->second;
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    streams[dev] = s;
+    return s;
+}
+
 cudaError_t gf_trim_pool()
 {
     cudaMemPool_t pool = pool_for_current_device();
