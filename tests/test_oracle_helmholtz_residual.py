@@ -10,9 +10,9 @@ beta^2 = k^2 - |alpha_n|^2 with the alpha_n of its own phase (a wrong index, alp
 leaves a residual of the size of that term; the branch of beta and the 1/beta factor,
 which each term's equation leaves free, are pinned by the image expansion and the
 singularity tests instead.  (The near branch is pinned by its values
-against the exact series instead: its cubic gather reproduces values to fourth order in
-the grid step but second derivatives only to second order, with a constant that makes a
-residual test there weak.)
+against the exact series instead: its values converge to the series, but its second
+derivatives converge slowly, being those of a cubic gather of a periodised remainder
+that carries the slab's cutoff; measured residual ~0.1 of k^2 max|G| at 64^2 in 2D.)
 """
 import numpy as np
 import pytest
