@@ -240,3 +240,19 @@ def test_full_size_config2_sampled():
     print(f"config-2 full size: pointwise {e_pt:.2e}, normwise {e_nw:.2e} vs the FP64 oracle")
     assert e_pt < TOL64
     assert np.isfinite(got_all).all()
+
+
+def test_host_entry_right_after_plan_on_a_side_stream():
+    """The host-buffer entry point uploads on the library's copy stream while the
+    plan's synthesis may still be running on the caller's stream (no synchronisation
+    in between, a non-default stream): the result equals the device entry's bit for
+    bit."""
+    x = W.targets_3d(50_001, seed=9)
+    s = torch.cuda.Stream()
+    xp = torch.from_numpy(x).pin_memory()
+    host = torch.empty((x.shape[0], 1), dtype=torch.complex128).pin_memory()
+    plan = gf.Plan(3, 2.5, (0.1, 0.3), (64, 64, 32), stream=s)
+    plan.eval_points_host(xp, host, gf.GF_OUT_GD, stream=s)
+    ref = gpu_eval(plan, x, gf.GF_OUT_GD)
+    assert np.array_equal(host.numpy(), ref)
+    plan.close()
