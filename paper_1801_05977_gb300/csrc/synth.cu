@@ -322,12 +322,10 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
     C *buf0 = tw + (n >> 1);                             // [nf][TJ][n]
     C *buf1 = buf0 + nf * TJ * n;                      // [TJ][n] scratch of the transforms
     double *A2s = reinterpret_cast<double *>(buf1 + TJ * n); // [TJ]
-    // split plans, float coefficients: A_m [TJ][Q], |alpha_j|^2 - k^2 and its float [TJ], q_b^2 [n]
-    // (16-byte aligned so that the X'-integral loop reads it four nodes at a time)
+    // split plans, float coefficients: A_m [TJ][Q] (16-byte aligned so that the X'-integral
+    // loop reads it four nodes at a time), |alpha_j|^2 in float [TJ]
     float *Avf = reinterpret_cast<float *>(reinterpret_cast<uintptr_t>(A2s + TJ + 1) & ~(uintptr_t)15);
-    double *A2mk = reinterpret_cast<double *>(Avf + ((TJ * Q + 3) & ~3));
-    double *qq = A2mk + TJ;
-    float *A2f = reinterpret_cast<float *>(qq + n);
+    float *A2f = Avf + ((TJ * Q + 3) & ~3);
     // float-column data: |alpha_j|^2 - k^2 and q_b^2 as float pairs (hi, lo), g in
     // float, and per column bit 0 = X'-integrals skipped, bit 1 = float coefficient
     float2 *A2mkf = reinterpret_cast<float2 *>((reinterpret_cast<uintptr_t>(A2f + TJ) + 15) & ~(uintptr_t)15);
@@ -369,7 +367,6 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
         if (need_k2) betas2[t] = beta_of(a.k2, A2);
         if (fcoef) {
             const double d = A2 - a.k * a.k;
-            A2mk[t] = d;
             A2f[t] = (float)A2;
             const float h = (float)d;
             A2mkf[t] = make_float2(h, (float)(d - (double)h));
@@ -396,7 +393,6 @@ __device__ void synth_first_pass_body(const SynthArgs &a, int blk, unsigned char
             tts[m] = (float)a.tt[m];
         }
     }
-    (void)qq;
     __syncthreads();
     for (int i = threadIdx.x; i < TJ * Q; i += blockDim.x) {
         int t = i / Q, m = i - t * Q;
